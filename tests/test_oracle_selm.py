@@ -1,0 +1,67 @@
+"""Pins for the SELM driver (oracle/selm.py): Sections 2.1, 3 and Algorithm 4."""
+
+import numpy as np
+import pytest
+
+import selm_inputs
+from oracle import coupling, selm
+from tests.affine import block_diag, flatten, unflatten
+
+
+@pytest.mark.parametrize("project", [False, True])
+def test_mobility_symmetric_positive(project):
+    m = selm.Model(16, 2, mu=1.0, kT=1.0, levels=4, project=project, tol=1e-12)
+    X = selm_inputs.particles(4, 2, 16, seed=0)
+    M = m.mobility_matrix(X)
+    assert np.abs(M - M.T).max() < 1e-9 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+def _thermal_operator(m, X):
+    """K = sqrt(2 kT) Gamma P~ as a matrix (columns = responses to unit xi)."""
+    shapes = m.sys.shapes()
+    nv = sum(int(np.prod(s)) for s in shapes)
+    K = np.zeros((X.size, nv))
+    for i in range(nv):
+        e = np.zeros(nv)
+        e[i] = 1.0
+        K[:, i] = np.sqrt(2 * m.kT) * coupling.interpolate(m.sys, m.P(unflatten(e, shapes)), X).ravel()
+    return K
+
+
+@pytest.mark.parametrize("project", [False, True])
+def test_fluctuation_dissipation_identity(project):
+    # G = K C K^T with C = A^-1 equals 2 kT M (Eq. equ_G_special_form)
+    m = selm.Model(8, 2, mu=0.7, kT=1.9, levels=3, project=project, tol=1e-13)
+    X = selm_inputs.particles(3, 2, 8, seed=1)
+    K = _thermal_operator(m, X)
+    A = block_diag([cl.dense() for cl in m.sys.levels[0]])
+    G = K @ np.linalg.inv(A) @ K.T
+    M = m.mobility_matrix(X)
+    assert np.allclose(G, 2 * m.kT * M, atol=1e-9 * np.abs(G).max())
+
+
+def test_em_step_without_noise_is_mobility_drift():
+    m = selm.Model(16, 2, kT=0.0, levels=4, tol=1e-12)
+    X = selm_inputs.particles(5, 2, 16, seed=2)
+    F = selm_inputs.forces(5, 2, seed=2)
+    U, _, _ = m.mobility_apply(X, F)
+    X1, _ = m.em_step(X, F, 1e-3, ncycles=2)
+    assert np.allclose(X1, m.wrap_reflect(X + 1e-3 * U), atol=1e-13)
+
+
+def test_wrap_and_reflect():
+    m = selm.Model(8, 3, levels=2)
+    X = np.array([[1.25, -0.5, -0.1], [0.5, 0.5, 1.2]])
+    Y = m.wrap_reflect(X)
+    assert np.allclose(Y, [[0.25, 0.5, 0.1], [0.5, 0.5, 0.8]])
+
+
+def test_chain_counter_advances_and_reproduces():
+    a = selm.Model(8, 2, levels=3, seed=5)
+    b = selm.Model(8, 2, levels=3, seed=5)
+    a.chain_cycles(3)
+    b.chain_cycles(1)
+    b.chain_cycles(2)          # resume: same counter sequence, same chain
+    assert a.cycle == b.cycle == 3
+    assert np.array_equal(flatten(a.xi), flatten(b.xi))

@@ -1,0 +1,193 @@
+/*
+ * selm_mg.h - C ABI of the GB300 stochastic multigrid library for the
+ * Stochastic Eulerian-Lagrangian Method (Atzberger, "Spatially Adaptive
+ * Stochastic Multigrid Methods for Fluid-Structure Systems with Thermal
+ * Fluctuations", arXiv:1003.2680).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every pointer argument named as a field, particle array or output is a
+ *   DEVICE pointer owned by the caller, unless stated otherwise.  The library
+ *   never frees caller memory.
+ * - Every call is enqueued on `stream` (a cudaStream_t passed as void*; NULL =
+ *   the legacy default stream) and returns before the GPU work finishes,
+ *   except where a host-visible result (cycle counts, residuals) is asked
+ *   for, which synchronises `stream`.
+ * - Argument errors are reported synchronously as a status code; no C++
+ *   exception crosses the ABI.  The text of the last error of a handle is
+ *   returned by selm_mg_last_error().
+ * - Geometry: the unit box [0,1]^d, periodic in x (and y in 3-D), no-slip
+ *   walls at z = 0 and z = 1 (in 2-D the paper's y axis is called z here).
+ *   n cells per axis, h = 1/n.  Velocity components live on the MAC faces
+ *   normal to their axis (Section 4); the wall-normal component has n-1
+ *   unknowns along z (its wall nodes are Dirichlet 0), the others n.
+ * - Field layout: a "field" of a system at a level is the concatenation of
+ *   its components, each a row-major array [nz][ny][nx] (x fastest, ny = 1 in
+ *   2-D).  selm_mg_layout() returns every size and offset.  Particle arrays
+ *   X, F, U, g are row-major [np][dim] doubles; in 2-D the columns are (x, z).
+ * - Operator: A = mu h^d (-L_h), the SPD scaled MAC Laplacian (Section 2.1,
+ *   Eq. equ_H_selm_discr with alpha = h^-d absorbed), so that the mobility is
+ *   M = Gamma P~ A^-1 P~ Gamma^T and the thermal field is
+ *   g = sqrt(2 kT) Gamma P~ xi with xi ~ N(0, A^-1) (Eqs. equ_G_special_form,
+ *   equ_g_gen_xi).
+ */
+#ifndef SELM_MG_H
+#define SELM_MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct selm_mg selm_mg;  /* opaque handle, owned by the library */
+
+typedef enum {
+  SELM_OK = 0,
+  SELM_EINVAL = 1,   /* malformed descriptor or argument */
+  SELM_ENOMEM = 2,   /* device allocation failed */
+  SELM_ECUDA = 3,    /* a CUDA call failed (text in selm_mg_last_error) */
+  SELM_ENOCONV = 4,  /* FAC solve did not reach tol within max_cycles */
+  SELM_ETIMEOUT = 5, /* a bounded device-side wait ran out */
+  SELM_EBUSY = 6     /* no free slot / memory for admission */
+} selm_status;
+
+enum { SELM_FP64 = 0, SELM_FP32_REFINE64 = 1 };          /* precision */
+enum { SELM_PROJ_NONE = 0, SELM_PROJ_MAC = 1 };           /* projection */
+enum { SELM_COARSE_CHOLESKY = 0, SELM_COARSE_SMOOTH = 1 }; /* coarsest level */
+enum { SELM_SYS_VELOCITY = 0, SELM_SYS_PRESSURE = 1 };    /* system selector */
+
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  int n;                   /* cells per axis; divisible by 2^(levels-1) */
+  double mu;               /* viscosity (Eq. equ_fld_cont) */
+  double kT;               /* thermal energy k_B T (Eq. equ_effective_fluct) */
+  int levels;              /* multigrid levels; 0 = coarsen while the edge stays even and >= 4 */
+  int nu_pre, nu_post;     /* (mu1, mu2) smoothing sweeps of Algorithm 3; 0 -> 2 */
+  int precision;           /* SELM_FP64 or SELM_FP32_REFINE64 */
+  int projection;          /* SELM_PROJ_NONE (P~ = I) or SELM_PROJ_MAC */
+  int coarse_mode;         /* SELM_COARSE_CHOLESKY (exact block step) or SELM_COARSE_SMOOTH (Alg. 3 literally) */
+  double tol;              /* FAC stop: ||b - Az||_2 <= tol ||b||_2 ; 0 -> 1e-10 */
+  int max_cycles;          /* FAC cycle cap; 0 -> 100 */
+  double proj_tol;         /* pressure-solve tolerance of the projection; 0 -> 1e-12 */
+  int max_particles;       /* capacity of the particle scratch of selm_mg_step; 0 -> 4096 */
+  uint64_t seed;           /* Philox key material (noise of this chain) */
+  uint64_t instance;       /* Philox key material (distinguishes systems) */
+  /* optional device allocator hooks (e.g. a framework's caching allocator);
+     NULL -> cudaMalloc / cudaFree */
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+} selm_mg_desc;
+
+/* Device bytes a handle for `desc` will allocate (state + scratch); 0 if the
+   descriptor is invalid.  Used for admission by footprint. */
+size_t selm_mg_footprint(const selm_mg_desc* desc);
+
+/* Validate `desc`, build the Galerkin hierarchy on the host (Section 3.2,
+   A^(l) = P^T A^(l-1) P with trilinear P), factor the coarsest operators,
+   allocate and upload device state on `stream`.  *out receives the handle. */
+selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out);
+selm_status selm_mg_destroy(selm_mg* h);
+const char* selm_mg_last_error(const selm_mg* h);
+
+/* ---- the SELM operations (Algorithm 4) ---------------------------------- */
+
+/* U = M F = Gamma P~ A^-1 P~ Gamma^T F (Alg. 4 step 2): spread, project,
+   FAC-solve to tol (Algorithm 1), project, interpolate.  X, F: [np][dim]
+   positions and forces; U: [np][dim] output.  cycles_out / resid_out are
+   optional HOST pointers (synchronises the stream when given). */
+selm_status selm_mg_solve(selm_mg* h, int np, const double* X, const double* F, double* U,
+                          int* cycles_out, double* resid_out, void* stream);
+
+/* Advance the persistent chain xi by `ncycles` stochastic FAC cycles
+   (Alg. 4 step 3, b = 0) and return g = sqrt(2 kT) Gamma P~ xi at X.
+   xi_out (optional, device) receives a copy of xi (velocity field layout). */
+selm_status selm_mg_sample(selm_mg* h, int np, const double* X, int ncycles, double* g,
+                           double* xi_out, void* stream);
+
+/* `nsteps` Euler-Maruyama steps (Alg. 4 steps 1-5) with fixed forces F:
+   X <- X + Gamma P~ (dt A^-1 P~ Gamma^T F + sqrt(2 kT dt) xi), then periodic
+   wrap and reflection at the walls.  X is updated in place. */
+selm_status selm_mg_step(selm_mg* h, int np, double* X, const double* F, double dt, int nsteps,
+                         int ncycles_per_step, void* stream);
+
+/* ---- layout and state --------------------------------------------------- */
+
+int selm_mg_levels(const selm_mg* h, int system);
+int selm_mg_ncomp(const selm_mg* h, int system);
+/* dims3 = {nx, ny, nz} of component `comp` at `level`; *offset = its element
+   offset in the level field; *level_size = elements of the whole field. */
+selm_status selm_mg_layout(const selm_mg* h, int system, int level, int comp, int* dims3,
+                           long long* offset, long long* level_size);
+/* Element size (4 or 8) of the inner (level) fields of the handle. */
+int selm_mg_inner_bytes(const selm_mg* h);
+/* Device pointer of the chain state xi (velocity layout, FP64) and its cycle
+   counter (the Philox counter of the next stochastic cycle). */
+selm_status selm_mg_chain(selm_mg* h, double** xi, uint64_t* cycle);
+selm_status selm_mg_set_cycle(selm_mg* h, uint64_t cycle);
+/* FAC cycles run by the last solve (velocity) and the projections it did. */
+selm_status selm_mg_stats(const selm_mg* h, int* last_solve_cycles, int* last_proj_cycles,
+                          long long* total_vcycles);
+
+/* ---- method steps on caller buffers (one entry per hot-path step) -------
+   v, b, d, r: inner-precision fields (selm_mg_inner_bytes) of `system` at
+   `level` in the layout above.  z, b64: FP64 level-0 fields.  `cycle` is the
+   Philox counter; noise != 0 draws the Gaussian terms (sampling),
+   noise == 0 runs the deterministic smoother (solving). */
+
+/* Section 3.1 / Alg. 3 steps 1,5: one full stochastic Gauss-Seidel sweep,
+   z_i <- (b_i - sum_{j!=i} A_ij z_j)/A_ii + n_i/sqrt(A_ii), red-black at
+   level 0 and multicolour on the Galerkin levels; `sweep` is the index
+   within the cycle (0..mu1-1 pre, mu1.. post) used in the noise counter. */
+selm_status selm_mg_smooth(selm_mg* h, int system, int level, void* v, const void* b, int sweep,
+                           uint64_t cycle, int noise, void* stream);
+/* Alg. 3 step 3: b_coarse = P^T (b - A^(level) v) for level -> level+1. */
+selm_status selm_mg_residual_restrict(selm_mg* h, int system, int level, const void* v,
+                                      const void* b, void* b_coarse, void* stream);
+/* Alg. 3 step 4: v += P v_coarse (level+1 -> level). */
+selm_status selm_mg_prolong_correct(selm_mg* h, int system, int level, void* v,
+                                    const void* v_coarse, void* stream);
+/* Coarsest level (reading of Alg. 3 step 2): v = A_c^-1 b + noise * L_c^-T n,
+   A_c = L_c L_c^T in FP64 (exact block heat-bath). */
+selm_status selm_mg_coarsest(selm_mg* h, int system, void* v, const void* b, uint64_t cycle,
+                             int noise, void* stream);
+/* Alg. 3 V-cycle on the correction equation at level 0: v <- V-Cycle(v, b). */
+selm_status selm_mg_vcycle(selm_mg* h, int system, void* v, const void* b, uint64_t cycle,
+                           int noise, void* stream);
+/* Alg. 1 step 1 in FP64: r = b64 - A z (b64 may be NULL = 0), stored in the
+   inner precision; if norm2 (device double) is given, adds ||r||^2 to it. */
+selm_status selm_mg_outer_residual(selm_mg* h, int system, const double* z, const double* b64,
+                                   void* r, double* norm2, void* stream);
+/* Alg. 1 step 4 in FP64: z += d. */
+selm_status selm_mg_outer_update(selm_mg* h, int system, double* z, const void* d, void* stream);
+/* One FAC iteration (Algorithm 1) on FP64 z: z <- z + V-Cycle(0, b - A z). */
+selm_status selm_mg_fac_cycle(selm_mg* h, int system, double* z, const double* b64, uint64_t cycle,
+                              int noise, void* stream);
+/* Deterministic FAC iteration from the given z until ||b - Az|| <= tol ||b||
+   (synchronises to read the norm). */
+selm_status selm_mg_fac_solve(selm_mg* h, int system, double* z, const double* b64, double tol,
+                              int max_cycles, int* cycles_out, double* resid_out, void* stream);
+/* Section 2.1 coupling: b = Gamma^T F (Peskin 4-point spreading onto the
+   velocity unknowns; b is overwritten). */
+selm_status selm_mg_spread(selm_mg* h, int np, const double* X, const double* F, double* b,
+                           void* stream);
+/* U = Gamma u (Peskin 4-point interpolation of the velocity field u). */
+selm_status selm_mg_interp(selm_mg* h, int np, const double* X, const double* u, double* U,
+                           void* stream);
+/* Section 4 / Section 2.1: w <- P~ w = w - D^T (D D^T)^+ D w, the MAC
+   projection, by a deterministic FAC solve of the Neumann pressure problem. */
+selm_status selm_mg_project(selm_mg* h, double* w, int* cycles_out, void* stream);
+/* Alg. 4 step 4 tail: X += V, wrap the periodic coordinates, reflect at walls. */
+selm_status selm_mg_em_update(selm_mg* h, int np, double* X, const double* V, void* stream);
+
+/* Philox4x32-10 (Salmon et al., SC'11) of n counters: ctr and out are device
+   arrays of 4n uint32.  A utility for checking the noise generator. */
+selm_status selm_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, uint32_t* out,
+                               int n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SELM_MG_H */

@@ -1,0 +1,784 @@
+// C ABI of the stochastic multigrid SELM library: handle management and the
+// host orchestration of Algorithms 1, 3 and 4 on a caller-given stream.
+//
+// All device state of a handle (Galerkin tables, level fields, FP64 outer
+// fields, reduction slots, particle scratch) lives in one workspace block
+// whose layout is computed on the host; the block comes from the caller's
+// allocator hooks or cudaMalloc.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/selm_mg.h"
+#include "selm_internal.h"
+#include "selm_launch.h"
+
+using namespace selm;
+
+namespace {
+
+struct Sys {
+  HostSystem host;
+  LevelDev lev[kMaxLevels];
+  void* v[kMaxLevels] = {};
+  void* b[kMaxLevels] = {};
+  void* t[kMaxLevels] = {};
+  int levels = 0;
+  int ncomp = 0;
+};
+
+// Byte layout of the workspace.
+struct Layout {
+  size_t total = 0;
+  size_t add(size_t bytes) {
+    size_t off = (total + 255) & ~(size_t)255;
+    total = off + bytes;
+    return off;
+  }
+};
+
+}  // namespace
+
+struct selm_mg {
+  selm_mg_desc d{};
+  int mu1 = 2, mu2 = 2;
+  int esize = 8;
+  Sys vel, pres;
+  bool has_pres = false;
+  Key key{};
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* u = nullptr;      // solution of the deterministic solve (FP64)
+  double* xi = nullptr;     // chain state (FP64)
+  double* bvel = nullptr;   // right-hand side (FP64)
+  double* wcomb = nullptr;  // combined field for the particle update (FP64)
+  double* phi = nullptr;    // pressure (FP64)
+  double* prhs = nullptr;   // pressure right-hand side (FP64)
+  double* red = nullptr;    // reduction slots
+  unsigned long long* cyc = nullptr;  // [0] chain counter, [1] stage-call counter
+  double* V = nullptr;      // particle scratch [max_particles][3]
+  double* host_red = nullptr;  // pinned
+  uint64_t cycle = 0;
+  int last_solve_cycles = 0, last_proj_cycles = 0;
+  long long total_vcycles = 0;
+  std::string err;
+};
+
+namespace {
+
+void fill_desc_defaults(selm_mg_desc* d) {
+  if (d->levels == 0) d->levels = default_levels(d->n);
+  if (d->nu_pre == 0) d->nu_pre = 2;
+  if (d->nu_post == 0) d->nu_post = 2;
+  if (d->tol == 0.0) d->tol = 1e-10;
+  if (d->max_cycles == 0) d->max_cycles = 100;
+  if (d->proj_tol == 0.0) d->proj_tol = 1e-12;
+  if (d->max_particles == 0) d->max_particles = 4096;
+}
+
+std::string validate(const selm_mg_desc& d) {
+  if (d.dim != 2 && d.dim != 3) return "dim must be 2 or 3";
+  if (d.n < 4) return "n must be at least 4";
+  if (!(d.mu > 0.0)) return "mu must be positive";
+  if (!(d.kT >= 0.0)) return "kT must be non-negative";
+  if (d.nu_pre < 0 || d.nu_post < 0 || d.nu_pre + d.nu_post > 64) return "invalid smoothing counts";
+  if (d.precision != SELM_FP64 && d.precision != SELM_FP32_REFINE64) return "invalid precision";
+  if (d.projection != SELM_PROJ_NONE && d.projection != SELM_PROJ_MAC) return "invalid projection";
+  if (d.coarse_mode != SELM_COARSE_CHOLESKY && d.coarse_mode != SELM_COARSE_SMOOTH) return "invalid coarse_mode";
+  if (!(d.tol > 0.0) || !(d.proj_tol > 0.0)) return "tolerances must be positive";
+  if (d.max_cycles < 1 || d.max_particles < 1) return "max_cycles and max_particles must be positive";
+  return "";
+}
+
+std::string build_systems(const selm_mg_desc& d, Sys* vel, Sys* pres, bool* has_pres) {
+  std::string e = build_velocity_system(d.dim, d.n, d.levels, d.mu, &vel->host);
+  if (!e.empty()) return "velocity system: " + e;
+  *has_pres = d.projection == SELM_PROJ_MAC;
+  if (*has_pres) {
+    e = build_pressure_system(d.dim, d.n, d.levels, &pres->host);
+    if (!e.empty()) return "pressure system: " + e;
+  }
+  if (d.coarse_mode == SELM_COARSE_SMOOTH) {
+    const HostSystem* ss[2] = {&vel->host, *has_pres ? &pres->host : nullptr};
+    for (const HostSystem* s : ss) {
+      if (!s) continue;
+      for (const auto& c : s->lev[s->levels - 1])
+        for (int a = 0; a < 2; ++a)
+          if (c.dims[a] > 1 && c.dims[a] % c.mods[a] != 0)
+            return "coarsest level too small for a valid colouring in smooth mode";
+    }
+  }
+  return "";
+}
+
+struct TableOffsets {
+  size_t S64, S32, rzw64, rzw32, pzw64, pzw32, rzi, pzi, Linv;
+};
+
+// Workspace plan: tables + fields.  When `base` is null only sizes are computed.
+struct Plan {
+  Layout lay;
+  std::vector<double> dbl;
+  std::vector<float> flt;
+  std::vector<int> ints;
+  size_t dbl_off = 0, flt_off = 0, int_off = 0;
+  std::vector<TableOffsets> toff[2][kMaxLevels];
+  size_t field_off[2][kMaxLevels][3];
+  size_t u_off = 0, xi_off = 0, bvel_off = 0, wcomb_off = 0, phi_off = 0, prhs_off = 0, red_off = 0,
+         cyc_off = 0, V_off = 0;
+};
+
+void plan_tables(const HostSystem& hs, int si, Plan* p) {
+  for (int l = 0; l < hs.levels; ++l) {
+    p->toff[si][l].clear();
+    for (const auto& c : hs.lev[l]) {
+      TableOffsets t{};
+      t.S64 = p->dbl.size();
+      p->dbl.insert(p->dbl.end(), c.S.begin(), c.S.end());
+      t.S32 = p->flt.size();
+      for (double x : c.S) p->flt.push_back((float)x);
+      t.rzw64 = p->dbl.size();
+      p->dbl.insert(p->dbl.end(), c.rz_w.begin(), c.rz_w.end());
+      t.rzw32 = p->flt.size();
+      for (double x : c.rz_w) p->flt.push_back((float)x);
+      t.pzw64 = p->dbl.size();
+      p->dbl.insert(p->dbl.end(), c.pz_w.begin(), c.pz_w.end());
+      t.pzw32 = p->flt.size();
+      for (double x : c.pz_w) p->flt.push_back((float)x);
+      t.rzi = p->ints.size();
+      p->ints.insert(p->ints.end(), c.rz_idx.begin(), c.rz_idx.end());
+      t.pzi = p->ints.size();
+      p->ints.insert(p->ints.end(), c.pz_idx.begin(), c.pz_idx.end());
+      t.Linv = p->dbl.size();
+      p->dbl.insert(p->dbl.end(), c.Linv.begin(), c.Linv.end());
+      p->toff[si][l].push_back(t);
+    }
+  }
+}
+
+void make_plan(const selm_mg_desc& d, const Sys& vel, const Sys* pres, int esize, Plan* p) {
+  plan_tables(vel.host, 0, p);
+  if (pres) plan_tables(pres->host, 1, p);
+  p->dbl_off = p->lay.add(p->dbl.size() * sizeof(double) + 8);
+  p->flt_off = p->lay.add(p->flt.size() * sizeof(float) + 8);
+  p->int_off = p->lay.add(p->ints.size() * sizeof(int) + 8);
+  const HostSystem* hs[2] = {&vel.host, pres ? &pres->host : nullptr};
+  for (int si = 0; si < 2; ++si) {
+    if (!hs[si]) continue;
+    for (int l = 0; l < hs[si]->levels; ++l)
+      for (int f = 0; f < 3; ++f) p->field_off[si][l][f] = p->lay.add((size_t)hs[si]->level_size(l) * esize);
+  }
+  const size_t nv = (size_t)vel.host.level_size(0);
+  p->u_off = p->lay.add(nv * 8);
+  p->xi_off = p->lay.add(nv * 8);
+  p->bvel_off = p->lay.add(nv * 8);
+  p->wcomb_off = p->lay.add(nv * 8);
+  if (pres) {
+    const size_t np_ = (size_t)pres->host.level_size(0);
+    p->phi_off = p->lay.add(np_ * 8);
+    p->prhs_off = p->lay.add(np_ * 8);
+  }
+  p->red_off = p->lay.add(16 * sizeof(double));
+  p->cyc_off = p->lay.add(4 * sizeof(unsigned long long));
+  p->V_off = p->lay.add((size_t)d.max_particles * 3 * sizeof(double));
+}
+
+void bind_system(Sys* s, int si, const Plan& p, char* ws) {
+  const HostSystem& hs = s->host;
+  s->levels = hs.levels;
+  s->ncomp = hs.ncomp;
+  double* dbl = (double*)(ws + p.dbl_off);
+  float* flt = (float*)(ws + p.flt_off);
+  int* ints = (int*)(ws + p.int_off);
+  for (int l = 0; l < hs.levels; ++l) {
+    LevelDev& L = s->lev[l];
+    std::memset(&L, 0, sizeof L);
+    L.level = l;
+    L.ncomp = hs.ncomp;
+    long long off = 0;
+    for (int ci = 0; ci < hs.ncomp; ++ci) {
+      const HostComp& hc = hs.lev[l][ci];
+      const TableOffsets& t = p.toff[si][l][ci];
+      CompDev& c = L.c[ci];
+      c.nx = hc.dims[0];
+      c.ny = hc.dims[1];
+      c.nz = hc.dims[2];
+      c.off = off;
+      off += hc.size();
+      c.comp_id = hc.comp_id;
+      c.zkind = hc.kind[2];
+      c.mx = hc.mods[0];
+      c.my = hc.mods[1];
+      c.mz = hc.mods[2];
+      c.ncol = c.mx * c.my * c.mz;
+      c.s = hs.scale;
+      c.S64 = dbl + t.S64;
+      c.S32 = flt + t.S32;
+      c.rz_w64 = hc.rz_w.empty() ? nullptr : dbl + t.rzw64;
+      c.rz_w32 = hc.rz_w.empty() ? nullptr : flt + t.rzw32;
+      c.pz_w64 = hc.pz_w.empty() ? nullptr : dbl + t.pzw64;
+      c.pz_w32 = hc.pz_w.empty() ? nullptr : flt + t.pzw32;
+      c.rz_idx = hc.rz_idx.empty() ? nullptr : ints + t.rzi;
+      c.pz_idx = hc.pz_idx.empty() ? nullptr : ints + t.pzi;
+      c.Linv = hc.Linv.empty() ? nullptr : dbl + t.Linv;
+    }
+    L.size = off;
+    s->v[l] = ws + p.field_off[si][l][0];
+    s->b[l] = ws + p.field_off[si][l][1];
+    s->t[l] = ws + p.field_off[si][l][2];
+  }
+}
+
+#define CK(call)                                                        \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) {                                            \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);      \
+      return SELM_ECUDA;                                                \
+    }                                                                   \
+  } while (0)
+
+inline cudaStream_t S(void* st) { return (cudaStream_t)st; }
+
+Sys* sys_of(selm_mg* h, int system) {
+  if (system == SELM_SYS_VELOCITY) return &h->vel;
+  if (system == SELM_SYS_PRESSURE && h->has_pres) return &h->pres;
+  return nullptr;
+}
+
+// ---- V-cycle (Algorithm 3) -------------------------------------------------
+template <typename T>
+selm_status vcycle_t(selm_mg* h, Sys& s, int l, T* v0, const T* b0, bool noise, const unsigned long long* cyc,
+                     cudaStream_t st) {
+  T* v = l == 0 ? v0 : (T*)s.v[l];
+  const T* b = l == 0 ? b0 : (const T*)s.b[l];
+  const LevelDev& L = s.lev[l];
+  const bool last = l == s.levels - 1;
+  if (last && h->d.coarse_mode == SELM_COARSE_CHOLESKY) {
+    CK(launch_coarsest<T>(L, v, b, noise, h->key, cyc, st));
+    return SELM_OK;
+  }
+  for (int q = 0; q < h->mu1; ++q) CK(launch_smooth<T>(L, v, b, q, noise, h->key, cyc, st));
+  if (!last) {
+    const LevelDev& Lc = s.lev[l + 1];
+    CK(launch_residual<T>(L, v, b, (T*)s.t[l], st));
+    CK(launch_restrict<T>(L, Lc, (const T*)s.t[l], (T*)s.b[l + 1], st));
+    CK(cudaMemsetAsync(s.v[l + 1], 0, (size_t)Lc.size * sizeof(T), st));
+    selm_status r = vcycle_t<T>(h, s, l + 1, v0, b0, noise, cyc, st);
+    if (r != SELM_OK) return r;
+    CK(launch_prolong<T>(L, Lc, v, (const T*)s.v[l + 1], st));
+  }
+  for (int q = 0; q < h->mu2; ++q) CK(launch_smooth<T>(L, v, b, h->mu1 + q, noise, h->key, cyc, st));
+  return SELM_OK;
+}
+
+selm_status vcycle(selm_mg* h, Sys& s, void* v0, const void* b0, bool noise, const unsigned long long* cyc,
+                   cudaStream_t st) {
+  h->total_vcycles += 1;
+  if (h->esize == 4) return vcycle_t<float>(h, s, 0, (float*)v0, (const float*)b0, noise, cyc, st);
+  return vcycle_t<double>(h, s, 0, (double*)v0, (const double*)b0, noise, cyc, st);
+}
+
+selm_status outer_residual(selm_mg* h, Sys& s, const double* z, const double* b, void* r, double* norm2,
+                           cudaStream_t st) {
+  if (h->esize == 4)
+    CK(launch_outer_residual<float>(s.lev[0], z, b, (float*)r, norm2, st));
+  else
+    CK(launch_outer_residual<double>(s.lev[0], z, b, (double*)r, norm2, st));
+  return SELM_OK;
+}
+
+selm_status outer_update(selm_mg* h, Sys& s, double* z, const void* d, cudaStream_t st) {
+  if (h->esize == 4)
+    CK(launch_outer_update<float>(s.lev[0].size, z, (const float*)d, st));
+  else
+    CK(launch_outer_update<double>(s.lev[0].size, z, (const double*)d, st));
+  return SELM_OK;
+}
+
+// One FAC iteration (Algorithm 1) with the internal level-0 buffers.
+selm_status fac_cycle(selm_mg* h, Sys& s, double* z, const double* b, bool noise, const unsigned long long* cyc,
+                      cudaStream_t st) {
+  selm_status r = outer_residual(h, s, z, b, s.b[0], nullptr, st);
+  if (r != SELM_OK) return r;
+  CK(cudaMemsetAsync(s.v[0], 0, (size_t)s.lev[0].size * h->esize, st));
+  r = vcycle(h, s, s.v[0], s.b[0], noise, cyc, st);
+  if (r != SELM_OK) return r;
+  return outer_update(h, s, z, s.v[0], st);
+}
+
+selm_status read_double(selm_mg* h, const double* dev, double* out, cudaStream_t st) {
+  CK(cudaMemcpyAsync(h->host_red, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *out = *h->host_red;
+  return SELM_OK;
+}
+
+// Deterministic FAC iteration until ||b - Az|| <= tol ||b||.
+selm_status fac_solve(selm_mg* h, Sys& s, double* z, const double* b, double tol, int max_cycles, int* cycles,
+                      double* rel_out, cudaStream_t st) {
+  double* nb = h->red + 0;
+  double* nr = h->red + 1;
+  CK(cudaMemsetAsync(nb, 0, sizeof(double), st));
+  CK(launch_norm2(s.lev[0].size, b, nb, st));
+  double bn2 = 0.0;
+  selm_status r = read_double(h, nb, &bn2, st);
+  if (r != SELM_OK) return r;
+  *cycles = 0;
+  if (bn2 == 0.0) {
+    CK(cudaMemsetAsync(z, 0, (size_t)s.lev[0].size * sizeof(double), st));
+    if (rel_out) *rel_out = 0.0;
+    return SELM_OK;
+  }
+  const double bn = std::sqrt(bn2);
+  for (int cyc = 0;; ++cyc) {
+    CK(cudaMemsetAsync(nr, 0, sizeof(double), st));
+    r = outer_residual(h, s, z, b, s.b[0], nr, st);
+    if (r != SELM_OK) return r;
+    double rn2 = 0.0;
+    r = read_double(h, nr, &rn2, st);
+    if (r != SELM_OK) return r;
+    const double rel = std::sqrt(rn2) / bn;
+    if (rel_out) *rel_out = rel;
+    if (rel <= tol) {
+      *cycles = cyc;
+      return SELM_OK;
+    }
+    if (cyc >= max_cycles) {
+      *cycles = cyc;
+      h->err = "FAC solve did not converge";
+      return SELM_ENOCONV;
+    }
+    CK(cudaMemsetAsync(s.v[0], 0, (size_t)s.lev[0].size * h->esize, st));
+    r = vcycle(h, s, s.v[0], s.b[0], false, h->cyc + 1, st);
+    if (r != SELM_OK) return r;
+    r = outer_update(h, s, z, s.v[0], st);
+    if (r != SELM_OK) return r;
+  }
+}
+
+selm_status project(selm_mg* h, double* w, int* cycles, cudaStream_t st) {
+  *cycles = 0;
+  if (!h->has_pres) return SELM_OK;
+  const long long np_ = h->pres.lev[0].size;
+  CK(cudaMemsetAsync(h->red + 2, 0, sizeof(double), st));
+  CK(launch_divergence(h->vel.lev[0], w, h->prhs, h->red + 2, st));
+  CK(launch_sub_mean(np_, h->prhs, h->red + 2, st));
+  CK(cudaMemsetAsync(h->phi, 0, (size_t)np_ * sizeof(double), st));
+  double rel = 0.0;
+  selm_status r = fac_solve(h, h->pres, h->phi, h->prhs, h->d.proj_tol, h->d.max_cycles, cycles, &rel, st);
+  if (r != SELM_OK) return r;
+  CK(launch_grad_sub(h->vel.lev[0], w, h->phi, st));
+  return SELM_OK;
+}
+
+selm_status chain_cycles(selm_mg* h, int ncycles, cudaStream_t st) {
+  for (int q = 0; q < ncycles; ++q) {
+    selm_status r = fac_cycle(h, h->vel, h->xi, nullptr, true, h->cyc + 0, st);
+    if (r != SELM_OK) return r;
+    CK(launch_inc_u64(h->cyc + 0, st));
+    h->cycle += 1;
+  }
+  return SELM_OK;
+}
+
+bool check_particles(selm_mg* h, int np, const void* X) {
+  if (np < 0 || (np > 0 && !X)) {
+    h->err = "invalid particle arguments";
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t selm_mg_footprint(const selm_mg_desc* desc) {
+  if (!desc) return 0;
+  selm_mg_desc d = *desc;
+  fill_desc_defaults(&d);
+  if (!validate(d).empty()) return 0;
+  Sys vel, pres;
+  bool has_pres = false;
+  if (!build_systems(d, &vel, &pres, &has_pres).empty()) return 0;
+  Plan p;
+  make_plan(d, vel, has_pres ? &pres : nullptr, d.precision == SELM_FP64 ? 8 : 4, &p);
+  return p.lay.total;
+}
+
+selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out) {
+  if (!desc || !out) return SELM_EINVAL;
+  *out = nullptr;
+  selm_mg* h = new (std::nothrow) selm_mg();
+  if (!h) return SELM_ENOMEM;
+  h->d = *desc;
+  fill_desc_defaults(&h->d);
+  std::string e = validate(h->d);
+  if (e.empty()) e = build_systems(h->d, &h->vel, &h->pres, &h->has_pres);
+  if (!e.empty()) {
+    std::fprintf(stderr, "selm_mg_create: %s\n", e.c_str());
+    delete h;
+    return SELM_EINVAL;
+  }
+  h->mu1 = h->d.nu_pre;
+  h->mu2 = h->d.nu_post;
+  h->esize = h->d.precision == SELM_FP64 ? 8 : 4;
+  const uint64_t seed = h->d.seed, inst = h->d.instance;
+  h->key.k0 = (uint32_t)(seed & 0xffffffffu) ^ (uint32_t)(inst >> 32);
+  h->key.k1 = (uint32_t)(seed >> 32) ^ (uint32_t)(inst & 0xffffffffu);
+  Plan p;
+  make_plan(h->d, h->vel, h->has_pres ? &h->pres : nullptr, h->esize, &p);
+  h->ws_bytes = p.lay.total;
+  void* ws = nullptr;
+  if (h->d.alloc) {
+    ws = h->d.alloc(h->ws_bytes, h->d.alloc_ctx);
+    if (!ws) {
+      delete h;
+      return SELM_ENOMEM;
+    }
+  } else if (cudaMalloc(&ws, h->ws_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return SELM_ENOMEM;
+  }
+  h->ws = (char*)ws;
+  if (cudaMallocHost((void**)&h->host_red, 16 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    selm_mg_destroy(h);
+    return SELM_ENOMEM;
+  }
+  cudaStream_t st = S(stream);
+  cudaError_t ce = cudaSuccess;
+  if (!p.dbl.empty())
+    ce = cudaMemcpyAsync(h->ws + p.dbl_off, p.dbl.data(), p.dbl.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && !p.flt.empty())
+    ce = cudaMemcpyAsync(h->ws + p.flt_off, p.flt.data(), p.flt.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && !p.ints.empty())
+    ce = cudaMemcpyAsync(h->ws + p.int_off, p.ints.data(), p.ints.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  bind_system(&h->vel, 0, p, h->ws);
+  if (h->has_pres) bind_system(&h->pres, 1, p, h->ws);
+  h->u = (double*)(h->ws + p.u_off);
+  h->xi = (double*)(h->ws + p.xi_off);
+  h->bvel = (double*)(h->ws + p.bvel_off);
+  h->wcomb = (double*)(h->ws + p.wcomb_off);
+  if (h->has_pres) {
+    h->phi = (double*)(h->ws + p.phi_off);
+    h->prhs = (double*)(h->ws + p.prhs_off);
+  }
+  h->red = (double*)(h->ws + p.red_off);
+  h->cyc = (unsigned long long*)(h->ws + p.cyc_off);
+  h->V = (double*)(h->ws + p.V_off);
+  const size_t nv = (size_t)h->vel.lev[0].size * sizeof(double);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->xi, 0, nv, st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->u, 0, nv, st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->cyc, 0, 4 * sizeof(unsigned long long), st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // host tables must outlive the copies
+  if (ce != cudaSuccess) {
+    std::fprintf(stderr, "selm_mg_create: %s\n", cudaGetErrorString(ce));
+    selm_mg_destroy(h);
+    return SELM_ECUDA;
+  }
+  *out = h;
+  return SELM_OK;
+}
+
+selm_status selm_mg_destroy(selm_mg* h) {
+  if (!h) return SELM_EINVAL;
+  if (h->ws) {
+    if (h->d.free)
+      h->d.free(h->ws, h->d.alloc_ctx);
+    else
+      cudaFree(h->ws);
+  }
+  if (h->host_red) cudaFreeHost(h->host_red);
+  delete h;
+  return SELM_OK;
+}
+
+const char* selm_mg_last_error(const selm_mg* h) { return h ? h->err.c_str() : "null handle"; }
+
+int selm_mg_levels(const selm_mg* h, int system) {
+  if (!h) return 0;
+  if (system == SELM_SYS_VELOCITY) return h->vel.levels;
+  if (system == SELM_SYS_PRESSURE && h->has_pres) return h->pres.levels;
+  return 0;
+}
+
+int selm_mg_ncomp(const selm_mg* h, int system) {
+  if (!h) return 0;
+  if (system == SELM_SYS_VELOCITY) return h->vel.ncomp;
+  if (system == SELM_SYS_PRESSURE && h->has_pres) return h->pres.ncomp;
+  return 0;
+}
+
+selm_status selm_mg_layout(const selm_mg* h, int system, int level, int comp, int* dims3, long long* offset,
+                           long long* level_size) {
+  if (!h) return SELM_EINVAL;
+  const Sys* s = system == SELM_SYS_VELOCITY ? &h->vel : (system == SELM_SYS_PRESSURE && h->has_pres ? &h->pres : nullptr);
+  if (!s || level < 0 || level >= s->levels || comp < 0 || comp >= s->ncomp) return SELM_EINVAL;
+  const CompDev& c = s->lev[level].c[comp];
+  if (dims3) {
+    dims3[0] = c.nx;
+    dims3[1] = c.ny;
+    dims3[2] = c.nz;
+  }
+  if (offset) *offset = c.off;
+  if (level_size) *level_size = s->lev[level].size;
+  return SELM_OK;
+}
+
+int selm_mg_inner_bytes(const selm_mg* h) { return h ? h->esize : 0; }
+
+selm_status selm_mg_chain(selm_mg* h, double** xi, uint64_t* cycle) {
+  if (!h) return SELM_EINVAL;
+  if (xi) *xi = h->xi;
+  if (cycle) *cycle = h->cycle;
+  return SELM_OK;
+}
+
+selm_status selm_mg_set_cycle(selm_mg* h, uint64_t cycle) {
+  if (!h) return SELM_EINVAL;
+  CK(launch_set_u64(h->cyc + 0, cycle, nullptr));
+  CK(cudaDeviceSynchronize());
+  h->cycle = cycle;
+  return SELM_OK;
+}
+
+selm_status selm_mg_stats(const selm_mg* h, int* last_solve_cycles, int* last_proj_cycles, long long* total) {
+  if (!h) return SELM_EINVAL;
+  if (last_solve_cycles) *last_solve_cycles = h->last_solve_cycles;
+  if (last_proj_cycles) *last_proj_cycles = h->last_proj_cycles;
+  if (total) *total = h->total_vcycles;
+  return SELM_OK;
+}
+
+// ---- stage entry points ------------------------------------------------------
+
+selm_status selm_mg_smooth(selm_mg* h, int system, int level, void* v, const void* b, int sweep, uint64_t cycle,
+                           int noise, void* stream) {
+  if (!h) return SELM_EINVAL;
+  Sys* s = sys_of(h, system);
+  if (!s || level < 0 || level >= s->levels || !v || !b || sweep < 0 || sweep > 255) return SELM_EINVAL;
+  cudaStream_t st = S(stream);
+  CK(launch_set_u64(h->cyc + 1, cycle, st));
+  if (h->esize == 4)
+    CK(launch_smooth<float>(s->lev[level], (float*)v, (const float*)b, sweep, noise != 0, h->key, h->cyc + 1, st));
+  else
+    CK(launch_smooth<double>(s->lev[level], (double*)v, (const double*)b, sweep, noise != 0, h->key, h->cyc + 1, st));
+  return SELM_OK;
+}
+
+selm_status selm_mg_residual_restrict(selm_mg* h, int system, int level, const void* v, const void* b,
+                                      void* b_coarse, void* stream) {
+  if (!h) return SELM_EINVAL;
+  Sys* s = sys_of(h, system);
+  if (!s || level < 0 || level + 1 >= s->levels || !v || !b || !b_coarse) return SELM_EINVAL;
+  cudaStream_t st = S(stream);
+  if (h->esize == 4) {
+    CK(launch_residual<float>(s->lev[level], (const float*)v, (const float*)b, (float*)s->t[level], st));
+    CK(launch_restrict<float>(s->lev[level], s->lev[level + 1], (const float*)s->t[level], (float*)b_coarse, st));
+  } else {
+    CK(launch_residual<double>(s->lev[level], (const double*)v, (const double*)b, (double*)s->t[level], st));
+    CK(launch_restrict<double>(s->lev[level], s->lev[level + 1], (const double*)s->t[level], (double*)b_coarse, st));
+  }
+  return SELM_OK;
+}
+
+selm_status selm_mg_prolong_correct(selm_mg* h, int system, int level, void* v, const void* v_coarse, void* stream) {
+  if (!h) return SELM_EINVAL;
+  Sys* s = sys_of(h, system);
+  if (!s || level < 0 || level + 1 >= s->levels || !v || !v_coarse) return SELM_EINVAL;
+  cudaStream_t st = S(stream);
+  if (h->esize == 4)
+    CK(launch_prolong<float>(s->lev[level], s->lev[level + 1], (float*)v, (const float*)v_coarse, st));
+  else
+    CK(launch_prolong<double>(s->lev[level], s->lev[level + 1], (double*)v, (const double*)v_coarse, st));
+  return SELM_OK;
+}
+
+selm_status selm_mg_coarsest(selm_mg* h, int system, void* v, const void* b, uint64_t cycle, int noise, void* stream) {
+  if (!h) return SELM_EINVAL;
+  Sys* s = sys_of(h, system);
+  if (!s || !v || !b || h->d.coarse_mode != SELM_COARSE_CHOLESKY) return SELM_EINVAL;
+  cudaStream_t st = S(stream);
+  CK(launch_set_u64(h->cyc + 1, cycle, st));
+  const LevelDev& L = s->lev[s->levels - 1];
+  if (h->esize == 4)
+    CK(launch_coarsest<float>(L, (float*)v, (const float*)b, noise != 0, h->key, h->cyc + 1, st));
+  else
+    CK(launch_coarsest<double>(L, (double*)v, (const double*)b, noise != 0, h->key, h->cyc + 1, st));
+  return SELM_OK;
+}
+
+selm_status selm_mg_vcycle(selm_mg* h, int system, void* v, const void* b, uint64_t cycle, int noise, void* stream) {
+  if (!h) return SELM_EINVAL;
+  Sys* s = sys_of(h, system);
+  if (!s || !v || !b) return SELM_EINVAL;
+  cudaStream_t st = S(stream);
+  CK(launch_set_u64(h->cyc + 1, cycle, st));
+  return vcycle(h, *s, v, b, noise != 0, h->cyc + 1, st);
+}
+
+selm_status selm_mg_outer_residual(selm_mg* h, int system, const double* z, const double* b64, void* r,
+                                   double* norm2, void* stream) {
+  if (!h) return SELM_EINVAL;
+  Sys* s = sys_of(h, system);
+  if (!s || !z || !r) return SELM_EINVAL;
+  return outer_residual(h, *s, z, b64, r, norm2, S(stream));
+}
+
+selm_status selm_mg_outer_update(selm_mg* h, int system, double* z, const void* d, void* stream) {
+  if (!h) return SELM_EINVAL;
+  Sys* s = sys_of(h, system);
+  if (!s || !z || !d) return SELM_EINVAL;
+  return outer_update(h, *s, z, d, S(stream));
+}
+
+selm_status selm_mg_fac_cycle(selm_mg* h, int system, double* z, const double* b64, uint64_t cycle, int noise,
+                              void* stream) {
+  if (!h) return SELM_EINVAL;
+  Sys* s = sys_of(h, system);
+  if (!s || !z) return SELM_EINVAL;
+  cudaStream_t st = S(stream);
+  CK(launch_set_u64(h->cyc + 1, cycle, st));
+  return fac_cycle(h, *s, z, b64, noise != 0, h->cyc + 1, st);
+}
+
+selm_status selm_mg_fac_solve(selm_mg* h, int system, double* z, const double* b64, double tol, int max_cycles,
+                              int* cycles_out, double* resid_out, void* stream) {
+  if (!h) return SELM_EINVAL;
+  Sys* s = sys_of(h, system);
+  if (!s || !z || !b64 || !(tol > 0.0) || max_cycles < 0) return SELM_EINVAL;
+  int cycles = 0;
+  double rel = 0.0;
+  selm_status r = fac_solve(h, *s, z, b64, tol, max_cycles, &cycles, &rel, S(stream));
+  if (cycles_out) *cycles_out = cycles;
+  if (resid_out) *resid_out = rel;
+  return r;
+}
+
+selm_status selm_mg_spread(selm_mg* h, int np, const double* X, const double* F, double* b, void* stream) {
+  if (!h || !b || !check_particles(h, np, X) || (np > 0 && !F)) return SELM_EINVAL;
+  cudaStream_t st = S(stream);
+  CK(cudaMemsetAsync(b, 0, (size_t)h->vel.lev[0].size * sizeof(double), st));
+  CK(launch_spread(h->vel.lev[0], h->d.n, h->d.dim, np, X, F, b, st));
+  return SELM_OK;
+}
+
+selm_status selm_mg_interp(selm_mg* h, int np, const double* X, const double* u, double* U, void* stream) {
+  if (!h || !u || !check_particles(h, np, X) || (np > 0 && !U)) return SELM_EINVAL;
+  CK(launch_interp(h->vel.lev[0], h->d.n, h->d.dim, np, X, u, U, S(stream)));
+  return SELM_OK;
+}
+
+selm_status selm_mg_project(selm_mg* h, double* w, int* cycles_out, void* stream) {
+  if (!h || !w) return SELM_EINVAL;
+  int cycles = 0;
+  selm_status r = project(h, w, &cycles, S(stream));
+  if (cycles_out) *cycles_out = cycles;
+  return r;
+}
+
+selm_status selm_mg_em_update(selm_mg* h, int np, double* X, const double* V, void* stream) {
+  if (!h || !check_particles(h, np, X) || (np > 0 && !V)) return SELM_EINVAL;
+  CK(launch_em(np, h->d.dim, X, V, S(stream)));
+  return SELM_OK;
+}
+
+// ---- SELM operations (Algorithm 4) ----------------------------------------------
+
+selm_status selm_mg_solve(selm_mg* h, int np, const double* X, const double* F, double* U, int* cycles_out,
+                          double* resid_out, void* stream) {
+  if (!h || !check_particles(h, np, X) || (np > 0 && (!F || !U))) return SELM_EINVAL;
+  cudaStream_t st = S(stream);
+  const long long nv = h->vel.lev[0].size;
+  CK(cudaMemsetAsync(h->bvel, 0, (size_t)nv * sizeof(double), st));
+  CK(launch_spread(h->vel.lev[0], h->d.n, h->d.dim, np, X, F, h->bvel, st));
+  int pc = 0, pc2 = 0;
+  selm_status r = project(h, h->bvel, &pc, st);
+  if (r != SELM_OK) return r;
+  CK(cudaMemsetAsync(h->u, 0, (size_t)nv * sizeof(double), st));
+  int cycles = 0;
+  double rel = 0.0;
+  r = fac_solve(h, h->vel, h->u, h->bvel, h->d.tol, h->d.max_cycles, &cycles, &rel, st);
+  h->last_solve_cycles = cycles;
+  if (cycles_out) *cycles_out = cycles;
+  if (resid_out) *resid_out = rel;
+  if (r != SELM_OK) return r;
+  const double* field = h->u;
+  if (h->has_pres) {
+    CK(cudaMemcpyAsync(h->wcomb, h->u, (size_t)nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    r = project(h, h->wcomb, &pc2, st);
+    if (r != SELM_OK) return r;
+    field = h->wcomb;
+  }
+  h->last_proj_cycles = pc + pc2;
+  CK(launch_interp(h->vel.lev[0], h->d.n, h->d.dim, np, X, field, U, st));
+  return SELM_OK;
+}
+
+selm_status selm_mg_sample(selm_mg* h, int np, const double* X, int ncycles, double* g, double* xi_out,
+                           void* stream) {
+  if (!h || ncycles < 0 || !check_particles(h, np, X) || (np > 0 && !g)) return SELM_EINVAL;
+  cudaStream_t st = S(stream);
+  selm_status r = chain_cycles(h, ncycles, st);
+  if (r != SELM_OK) return r;
+  const long long nv = h->vel.lev[0].size;
+  if (xi_out) CK(cudaMemcpyAsync(xi_out, h->xi, (size_t)nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(launch_axpby(nv, std::sqrt(2.0 * h->d.kT), h->xi, 0.0, h->xi, h->wcomb, st));
+  int pc = 0;
+  r = project(h, h->wcomb, &pc, st);
+  if (r != SELM_OK) return r;
+  CK(launch_interp(h->vel.lev[0], h->d.n, h->d.dim, np, X, h->wcomb, g, st));
+  return SELM_OK;
+}
+
+selm_status selm_mg_step(selm_mg* h, int np, double* X, const double* F, double dt, int nsteps, int ncycles_per_step,
+                         void* stream) {
+  if (!h || nsteps < 0 || ncycles_per_step < 0 || !(dt >= 0.0) || !check_particles(h, np, X) || (np > 0 && !F))
+    return SELM_EINVAL;
+  if (np > h->d.max_particles) {
+    h->err = "np exceeds max_particles";
+    return SELM_EINVAL;
+  }
+  cudaStream_t st = S(stream);
+  const long long nv = h->vel.lev[0].size;
+  for (int step = 0; step < nsteps; ++step) {
+    CK(cudaMemsetAsync(h->bvel, 0, (size_t)nv * sizeof(double), st));
+    CK(launch_spread(h->vel.lev[0], h->d.n, h->d.dim, np, X, F, h->bvel, st));
+    int pc = 0, pc2 = 0, cycles = 0;
+    double rel = 0.0;
+    selm_status r = project(h, h->bvel, &pc, st);
+    if (r != SELM_OK) return r;
+    CK(cudaMemsetAsync(h->u, 0, (size_t)nv * sizeof(double), st));
+    r = fac_solve(h, h->vel, h->u, h->bvel, h->d.tol, h->d.max_cycles, &cycles, &rel, st);
+    h->last_solve_cycles = cycles;
+    if (r != SELM_OK) return r;
+    r = chain_cycles(h, ncycles_per_step, st);
+    if (r != SELM_OK) return r;
+    CK(launch_axpby(nv, dt, h->u, std::sqrt(2.0 * h->d.kT * dt), h->xi, h->wcomb, st));
+    r = project(h, h->wcomb, &pc2, st);
+    if (r != SELM_OK) return r;
+    h->last_proj_cycles = pc + pc2;
+    CK(launch_interp(h->vel.lev[0], h->d.n, h->d.dim, np, X, h->wcomb, h->V, st));
+    CK(launch_em(np, h->d.dim, X, h->V, st));
+  }
+  return SELM_OK;
+}
+
+selm_status selm_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, uint32_t* out, int n,
+                               void* stream) {
+  if (n < 0 || (n > 0 && (!ctr || !out))) return SELM_EINVAL;
+  Key k{key0, key1};
+  if (launch_philox(ctr, k, out, n, S(stream)) != cudaSuccess) return SELM_ECUDA;
+  return SELM_OK;
+}
+
+}  // extern "C"

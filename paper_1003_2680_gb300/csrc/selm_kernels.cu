@@ -1,0 +1,870 @@
+// CUDA kernels of the stochastic multigrid SELM path (sm_103a).
+//
+// Every hot-path step is an HBM-bound stencil; none is a dense contraction,
+// so the tensor cores are not used.  Step -> kernel:
+//   Gibbs sweep, level 0 (Section 3.1, red-black)      k_fine_colour
+//   Gibbs sweep, Galerkin levels (multicolour)         k_coarse_colour
+//   residual (Alg. 3 step 3)                           k_residual
+//   restriction P^T (Eq. equ_restr_prolong_variation)  k_restrict
+//   prolongation + correction (Alg. 3 step 4)          k_prolong
+//   coarsest exact step (reading of Alg. 3 step 2)     k_coarsest
+//   FP64 outer residual / update (Alg. 1 steps 1, 4)   k_outer_residual, k_outer_update
+//   Peskin spread / interpolation (Section 2.1)        k_spread, k_interp
+//   MAC divergence / gradient (Section 4)              k_divergence, k_grad_sub
+//   Euler-Maruyama update (Alg. 4 step 4)              k_em
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "selm_internal.h"
+#include "selm_launch.h"
+
+namespace selm {
+namespace {
+
+constexpr int kBlock = 256;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+template <typename T>
+struct Normals;
+
+template <>
+struct Normals<double> {
+  // u = (w + 1/2) 2^-32; (n0, n1) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1), etc.
+  __device__ static void get(uint4 w, double n[4]) {
+    const double s = 2.3283064365386962890625e-10;
+    const double u0 = ((double)w.x + 0.5) * s, u1 = ((double)w.y + 0.5) * s;
+    const double u2 = ((double)w.z + 0.5) * s, u3 = ((double)w.w + 0.5) * s;
+    const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
+    double s1, c1, s3, c3;
+    sincospi(2.0 * u1, &s1, &c1);
+    sincospi(2.0 * u3, &s3, &c3);
+    n[0] = r0 * c1;
+    n[1] = r0 * s1;
+    n[2] = r1 * c3;
+    n[3] = r1 * s3;
+  }
+};
+
+template <>
+struct Normals<float> {
+  __device__ static void get(uint4 w, float n[4]) {
+    const float s = 2.3283064365386962890625e-10f;
+    const float u0 = ((float)w.x + 0.5f) * s, u1 = ((float)w.y + 0.5f) * s;
+    const float u2 = ((float)w.z + 0.5f) * s, u3 = ((float)w.w + 0.5f) * s;
+    const float r0 = sqrtf(-2.0f * logf(u0)), r1 = sqrtf(-2.0f * logf(u2));
+    float s1, c1, s3, c3;
+    sincospif(2.0f * u1, &s1, &c1);
+    sincospif(2.0f * u3, &s3, &c3);
+    n[0] = r0 * c1;
+    n[1] = r0 * s1;
+    n[2] = r1 * c3;
+    n[3] = r1 * s3;
+  }
+};
+
+__device__ __forceinline__ uint32_t ctr1_of(int level, int comp, int colour, int sweep, int kind) {
+  return (uint32_t)level | ((uint32_t)comp << 4) | ((uint32_t)colour << 8) | ((uint32_t)sweep << 12) |
+         ((uint32_t)kind << 20);
+}
+
+template <typename T>
+__device__ __forceinline__ const T* stencil_of(const CompDev& c);
+template <>
+__device__ __forceinline__ const double* stencil_of<double>(const CompDev& c) {
+  return c.S64;
+}
+template <>
+__device__ __forceinline__ const float* stencil_of<float>(const CompDev& c) {
+  return c.S32;
+}
+
+template <typename T>
+__device__ __forceinline__ T rz_w(const CompDev& c, int q);
+template <>
+__device__ __forceinline__ double rz_w<double>(const CompDev& c, int q) {
+  return c.rz_w64[q];
+}
+template <>
+__device__ __forceinline__ float rz_w<float>(const CompDev& c, int q) {
+  return c.rz_w32[q];
+}
+template <typename T>
+__device__ __forceinline__ T pz_w(const CompDev& c, int q);
+template <>
+__device__ __forceinline__ double pz_w<double>(const CompDev& c, int q) {
+  return c.pz_w64[q];
+}
+template <>
+__device__ __forceinline__ float pz_w<float>(const CompDev& c, int q) {
+  return c.pz_w32[q];
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// Level-0 operator: s * sum over axes of (2 v - v_left - v_right), with the
+// wall ghost rules folded into the diagonal.  Returns the off-diagonal part
+// sum_{j != i} A_ij v_j and the diagonal A_ii.
+template <typename T, typename V>
+__device__ __forceinline__ void fine_row(const CompDev& c, const V* __restrict__ v, int i, int j, int k,
+                                         T* off, T* diag) {
+  const long long plane = (long long)c.nx * c.ny;
+  const long long row = c.off + (long long)k * plane + (long long)j * c.nx;
+  T sum = (T)v[row + wrapi(i - 1, c.nx)] + (T)v[row + wrapi(i + 1, c.nx)];
+  T d = (T)2;
+  if (c.ny > 1) {
+    const long long base = c.off + (long long)k * plane + i;
+    sum += (T)v[base + (long long)wrapi(j - 1, c.ny) * c.nx] + (T)v[base + (long long)wrapi(j + 1, c.ny) * c.nx];
+    d += (T)2;
+  }
+  const long long idx = row + i;
+  if (k > 0) sum += (T)v[idx - plane];
+  if (k < c.nz - 1) sum += (T)v[idx + plane];
+  int edges = (k == 0) + (k == c.nz - 1);
+  T dz = (T)2;
+  if (c.zkind == kAxisCellDir) dz += (T)edges;
+  if (c.zkind == kAxisCellNeu) dz -= (T)edges;
+  const T s = (T)c.s;
+  *off = -s * sum;
+  *diag = s * (d + dz);
+}
+
+// Galerkin-level operator: full 3x3x5 stencil row k (periodic wrap in x, y).
+template <typename T>
+__device__ __forceinline__ T coarse_apply(const CompDev& c, const T* __restrict__ v, int i, int j, int k,
+                                          bool skip_centre) {
+  const T* S = stencil_of<T>(c) + (long long)k * kStencil;
+  const long long plane = (long long)c.nx * c.ny;
+  T sum = (T)0;
+  for (int dz = -2; dz <= 2; ++dz) {
+    const int kk = k + dz;
+    if (kk < 0 || kk >= c.nz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      if (c.ny == 1 && dy != 0) continue;
+      const int jj = wrapi(j + dy, c.ny);
+      const long long rowb = c.off + (long long)kk * plane + (long long)jj * c.nx;
+      const T* Sr = S + ((dz + 2) * 3 + (dy + 1)) * 3;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (skip_centre && dz == 0 && dy == 0 && dx == 0) continue;
+        const T a = Sr[dx + 1];
+        if (a != (T)0) sum += a * v[rowb + wrapi(i + dx, c.nx)];
+      }
+    }
+  }
+  return sum;
+}
+
+template <typename T>
+__device__ __forceinline__ T coarse_diag(const CompDev& c, int k) {
+  return stencil_of<T>(c)[(long long)k * kStencil + 22];
+}
+
+__device__ __forceinline__ int comp_of(const long long* start, int ncomp, long long g) {
+  int c = 0;
+  while (c + 1 < ncomp && g >= start[c + 1]) ++c;
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Gibbs sweeps
+// ---------------------------------------------------------------------------
+struct ColourPass {
+  long long gstart[kMaxComps + 1];  // first noise group of each component
+  long long nsites[kMaxComps];
+  int cx[kMaxComps], cy[kMaxComps], cz[kMaxComps];     // colour tuple (levels >= 1)
+  int nxc[kMaxComps], nyc[kMaxComps], nzc[kMaxComps];  // extents of the colour class
+  int colour_id[kMaxComps];
+};
+
+// Level 0, red-black: one thread updates the four consecutive-rank sites of
+// one noise group (one Philox call).  Sites of colour `colour` satisfy
+// (i + j + k) % 2 == colour; rank = (k ny + j) nx/2 + i/2.
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kBlock) k_fine_colour(LevelDev L, ColourPass cp, T* __restrict__ v,
+                                                       const T* __restrict__ b, int colour, int sweep,
+                                                       Key key, const unsigned long long* __restrict__ cyc) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cp.gstart[L.ncomp]) return;
+  const int ci = comp_of(cp.gstart, L.ncomp, g);
+  const CompDev& c = L.c[ci];
+  const long long gl = g - cp.gstart[ci];
+  T nz4[4] = {(T)0, (T)0, (T)0, (T)0};
+  if (NOISE) {
+    const unsigned long long cy = *cyc;
+    uint4 ctr = make_uint4((uint32_t)gl, ctr1_of(L.level, c.comp_id, colour, sweep, 0), (uint32_t)cy,
+                           (uint32_t)(cy >> 32));
+    Normals<T>::get(philox10(ctr, key.k0, key.k1), nz4);
+  }
+  const int half = c.nx >> 1;
+#pragma unroll
+  for (int lane = 0; lane < 4; ++lane) {
+    const long long rank = gl * 4 + lane;
+    if (rank >= cp.nsites[ci]) break;
+    const int m = (int)(rank % half);
+    const long long rw = rank / half;
+    const int j = (int)(rw % c.ny), k = (int)(rw / c.ny);
+    const int i = 2 * m + ((j + k + colour) & 1);
+    T off, diag;
+    fine_row<T, T>(c, v, i, j, k, &off, &diag);
+    const long long idx = c.off + ((long long)k * c.ny + j) * c.nx + i;
+    T nv = (b[idx] - off) / diag;
+    if (NOISE) nv += nz4[lane] / sqrt(diag);
+    v[idx] = nv;
+  }
+}
+
+// Galerkin levels: colour = (i mod mx, j mod my, k mod mz); ranks row-major
+// within the class; four ranks per thread.
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kBlock) k_coarse_colour(LevelDev L, ColourPass cp, T* __restrict__ v,
+                                                         const T* __restrict__ b, int sweep, Key key,
+                                                         const unsigned long long* __restrict__ cyc) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cp.gstart[L.ncomp]) return;
+  const int ci = comp_of(cp.gstart, L.ncomp, g);
+  const CompDev& c = L.c[ci];
+  const long long gl = g - cp.gstart[ci];
+  T nz4[4] = {(T)0, (T)0, (T)0, (T)0};
+  if (NOISE) {
+    const unsigned long long cy = *cyc;
+    uint4 ctr = make_uint4((uint32_t)gl, ctr1_of(L.level, c.comp_id, cp.colour_id[ci], sweep, 0),
+                           (uint32_t)cy, (uint32_t)(cy >> 32));
+    Normals<T>::get(philox10(ctr, key.k0, key.k1), nz4);
+  }
+#pragma unroll
+  for (int lane = 0; lane < 4; ++lane) {
+    const long long rank = gl * 4 + lane;
+    if (rank >= cp.nsites[ci]) break;
+    const int ii = (int)(rank % cp.nxc[ci]);
+    const long long t = rank / cp.nxc[ci];
+    const int jj = (int)(t % cp.nyc[ci]), kk = (int)(t / cp.nyc[ci]);
+    const int i = cp.cx[ci] + c.mx * ii, j = cp.cy[ci] + c.my * jj, k = cp.cz[ci] + c.mz * kk;
+    const T off = coarse_apply<T>(c, v, i, j, k, true);
+    const T diag = coarse_diag<T>(c, k);
+    const long long idx = c.off + ((long long)k * c.ny + j) * c.nx + i;
+    T nv = (b[idx] - off) / diag;
+    if (NOISE) nv += nz4[lane] / sqrt(diag);
+    v[idx] = nv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Residual, restriction, prolongation
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void site_of(const LevelDev& L, long long s, int* ci, int* i, int* j, int* k) {
+  int c = 0;
+  while (c + 1 < L.ncomp && s >= L.c[c + 1].off) ++c;
+  const CompDev& cd = L.c[c];
+  const long long loc = s - cd.off;
+  *i = (int)(loc % cd.nx);
+  const long long t = loc / cd.nx;
+  *j = (int)(t % cd.ny);
+  *k = (int)(t / cd.ny);
+  *ci = c;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_residual(LevelDev L, const T* __restrict__ v, const T* __restrict__ b,
+                                                    T* __restrict__ t) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= L.size) return;
+  int ci, i, j, k;
+  site_of(L, s, &ci, &i, &j, &k);
+  const CompDev& c = L.c[ci];
+  T Av;
+  if (L.level == 0) {
+    T off, diag;
+    fine_row<T, T>(c, v, i, j, k, &off, &diag);
+    Av = off + diag * v[s];
+  } else {
+    Av = coarse_apply<T>(c, v, i, j, k, false);
+  }
+  t[s] = b[s] - Av;
+}
+
+// b_c(I,J,K) = sum_f P(f, (I,J,K)) t(f): periodic axes (1/2, 1, 1/2) around
+// fine node 2I; the wall axis from the tabulated columns of P.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_restrict(LevelDev Lf, LevelDev Lc, const T* __restrict__ t,
+                                                    T* __restrict__ bc) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Lc.size) return;
+  int ci, I, J, K;
+  site_of(Lc, s, &ci, &I, &J, &K);
+  const CompDev& f = Lf.c[ci];
+  const CompDev& cf = f;  // transfer tables live on the fine level
+  const long long plane = (long long)f.nx * f.ny;
+  T acc = (T)0;
+  for (int qz = 0; qz < 4; ++qz) {
+    const int kf = cf.rz_idx[K * 4 + qz];
+    if (kf < 0) continue;
+    const T wz = rz_w<T>(cf, K * 4 + qz);
+    for (int qy = -1; qy <= 1; ++qy) {
+      T wy;
+      int jf;
+      if (f.ny == 1) {
+        if (qy != 0) continue;
+        wy = (T)1;
+        jf = 0;
+      } else {
+        wy = qy == 0 ? (T)1 : (T)0.5;
+        jf = wrapi(2 * J + qy, f.ny);
+      }
+      const long long rowb = f.off + (long long)kf * plane + (long long)jf * f.nx;
+#pragma unroll
+      for (int qx = -1; qx <= 1; ++qx) {
+        const T wx = qx == 0 ? (T)1 : (T)0.5;
+        acc += wz * wy * wx * t[rowb + wrapi(2 * I + qx, f.nx)];
+      }
+    }
+  }
+  bc[s] = acc;
+}
+
+// v_f += P v_c: periodic axes: even fine node = coarse node, odd = mean of two.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_prolong(LevelDev Lf, LevelDev Lc, T* __restrict__ v,
+                                                   const T* __restrict__ vc) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Lf.size) return;
+  int ci, i, j, k;
+  site_of(Lf, s, &ci, &i, &j, &k);
+  const CompDev& f = Lf.c[ci];
+  const CompDev& c = Lc.c[ci];
+  int xi[2], yi[2];
+  T xw[2], yw[2];
+  int nxp, nyp;
+  if (i & 1) {
+    xi[0] = i >> 1;
+    xi[1] = wrapi((i >> 1) + 1, c.nx);
+    xw[0] = xw[1] = (T)0.5;
+    nxp = 2;
+  } else {
+    xi[0] = i >> 1;
+    xw[0] = (T)1;
+    nxp = 1;
+  }
+  if (f.ny == 1) {
+    yi[0] = 0;
+    yw[0] = (T)1;
+    nyp = 1;
+  } else if (j & 1) {
+    yi[0] = j >> 1;
+    yi[1] = wrapi((j >> 1) + 1, c.ny);
+    yw[0] = yw[1] = (T)0.5;
+    nyp = 2;
+  } else {
+    yi[0] = j >> 1;
+    yw[0] = (T)1;
+    nyp = 1;
+  }
+  const long long cplane = (long long)c.nx * c.ny;
+  T acc = (T)0;
+  for (int qz = 0; qz < 2; ++qz) {
+    const int kc = f.pz_idx[k * 2 + qz];
+    if (kc < 0) continue;
+    const T wz = pz_w<T>(f, k * 2 + qz);
+    for (int qy = 0; qy < nyp; ++qy)
+      for (int qx = 0; qx < nxp; ++qx)
+        acc += wz * yw[qy] * xw[qx] * vc[c.off + (long long)kc * cplane + (long long)yi[qy] * c.nx + xi[qx]];
+  }
+  v[s] += acc;
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: v = L^-T (L^-1 b + noise * n), FP64, one block per component.
+// ---------------------------------------------------------------------------
+template <typename T, bool NOISE>
+__global__ void k_coarsest(LevelDev L, T* __restrict__ v, const T* __restrict__ b, Key key,
+                           const unsigned long long* __restrict__ cyc) {
+  extern __shared__ double sm[];
+  const CompDev& c = L.c[blockIdx.x];
+  const int N = c.nx * c.ny * c.nz;
+  double* bb = sm;
+  double* y = sm + N;
+  for (int q = threadIdx.x; q < N; q += blockDim.x) bb[q] = (double)b[c.off + q];
+  __syncthreads();
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q <= r; ++q) acc += c.Linv[(long long)r * N + q] * bb[q];
+    if (NOISE) {
+      const unsigned long long cy = *cyc;
+      uint4 ctr = make_uint4((uint32_t)(r >> 2), ctr1_of(L.level, c.comp_id, 0, 0, 1), (uint32_t)cy,
+                             (uint32_t)(cy >> 32));
+      double n4[4];
+      Normals<double>::get(philox10(ctr, key.k0, key.k1), n4);
+      acc += n4[r & 3];
+    }
+    y[r] = acc;
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < N; col += blockDim.x) {
+    double acc = 0.0;
+    for (int r = col; r < N; ++r) acc += c.Linv[(long long)r * N + col] * y[r];
+    v[c.off + col] = (T)acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 outer iteration (Algorithm 1 steps 1 and 4)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double x) {
+  __shared__ double red[kBlock / 32];
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = x;
+  __syncthreads();
+  x = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_outer_residual(LevelDev L, const double* __restrict__ z,
+                                                          const double* __restrict__ b, T* __restrict__ r,
+                                                          double* __restrict__ norm2) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double rr = 0.0;
+  if (s < L.size) {
+    int ci, i, j, k;
+    site_of(L, s, &ci, &i, &j, &k);
+    double off, diag;
+    fine_row<double, double>(L.c[ci], z, i, j, k, &off, &diag);
+    const double res = (b ? b[s] : 0.0) - (off + diag * z[s]);
+    r[s] = (T)res;
+    rr = res * res;
+  }
+  if (norm2) {
+    rr = block_sum(rr);
+    if (threadIdx.x == 0) atomicAdd(norm2, rr);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_outer_update(long long n, double* __restrict__ z,
+                                                        const T* __restrict__ d) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) z[s] += (double)d[s];
+}
+
+__global__ void __launch_bounds__(kBlock) k_norm2(long long n, const double* __restrict__ x,
+                                                 double* __restrict__ out) {
+  double acc = 0.0;
+  for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x)
+    acc += x[s] * x[s];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+
+__global__ void __launch_bounds__(kBlock) k_axpby(long long n, double a, const double* __restrict__ x, double c,
+                                                 const double* __restrict__ y, double* __restrict__ out) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) out[s] = a * x[s] + c * y[s];
+}
+
+__global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+__global__ void k_inc_u64(unsigned long long* p) { *p += 1ull; }
+
+// ---------------------------------------------------------------------------
+// Peskin 4-point coupling (Section 2.1; kernel from Peskin, Acta Numerica 2002)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double peskin_phi(double r) {
+  r = fabs(r);
+  if (r <= 1.0) return (3.0 - 2.0 * r + sqrt(1.0 + 4.0 * r - 4.0 * r * r)) * 0.125;
+  if (r <= 2.0) return (5.0 - 2.0 * r - sqrt(fmax(-7.0 + 12.0 * r - 4.0 * r * r, 0.0))) * 0.125;
+  return 0.0;
+}
+
+// Node index (or -1) and weight of slot t (0..3) along one axis.
+// kind: periodic (offset off in cells), vertex wall lattice, cell wall lattice.
+__device__ __forceinline__ void axis_node(int kind, double x, double off, int n, int t, int* idx, double* w) {
+  if (kind == kAxisTrivial) {
+    *idx = t == 0 ? 0 : -1;
+    *w = t == 0 ? 1.0 : 0.0;
+    return;
+  }
+  double o = kind == kAxisVertex ? 0.0 : (kind == kAxisPeriodic ? off : 0.5);
+  const int a = (int)floor(x - o) - 1 + t;
+  *w = peskin_phi(x - o - (double)a);
+  if (kind == kAxisPeriodic) {
+    int m = a % n;
+    *idx = m < 0 ? m + n : m;
+  } else if (kind == kAxisVertex) {
+    *idx = (a >= 1 && a <= n - 1) ? a - 1 : -1;
+  } else {
+    *idx = (a >= 0 && a <= n - 1) ? a : -1;
+  }
+}
+
+struct CouplingGeom {
+  int kind[3];
+  double off[3];
+  int col[3];   // particle column per axis (-1 = trivial axis)
+};
+
+__device__ __forceinline__ CouplingGeom geom_of(const CompDev& c, int dim) {
+  CouplingGeom g;
+  g.kind[0] = kAxisPeriodic;
+  g.kind[1] = dim == 3 ? kAxisPeriodic : kAxisTrivial;
+  g.kind[2] = c.zkind;
+  // face-normal component: offset 0 along its own axis, 1/2 along the others
+  g.off[0] = c.comp_id == 0 ? 0.0 : 0.5;
+  g.off[1] = c.comp_id == 1 ? 0.0 : 0.5;
+  g.off[2] = 0.0;
+  g.col[0] = 0;
+  g.col[1] = dim == 3 ? 1 : -1;
+  g.col[2] = dim == 3 ? 2 : 1;
+  return g;
+}
+
+__device__ __forceinline__ int comp_col(const CompDev& c, int dim) { return dim == 3 ? c.comp_id : (c.comp_id == 0 ? 0 : 1); }
+
+// One thread per (particle, component, node of the 4^d support).
+__global__ void __launch_bounds__(kBlock) k_spread(LevelDev L, int n, int dim, int np, const double* __restrict__ X,
+                                                  const double* __restrict__ F, double* __restrict__ b) {
+  const int nodes = dim == 3 ? 64 : 16;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)np * L.ncomp * nodes) return;
+  const int q = (int)(g % nodes);
+  const int ci = (int)((g / nodes) % L.ncomp);
+  const int p = (int)(g / ((long long)nodes * L.ncomp));
+  const CompDev& c = L.c[ci];
+  const CouplingGeom ge = geom_of(c, dim);
+  const int tq[3] = {q & 3, dim == 3 ? (q >> 2) & 3 : 0, dim == 3 ? (q >> 4) & 3 : (q >> 2) & 3};
+  int id[3];
+  double w = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    const double x = ge.col[a] >= 0 ? X[(long long)p * dim + ge.col[a]] * n : 0.0;
+    double wa;
+    axis_node(ge.kind[a], x, ge.off[a], n, tq[a], &id[a], &wa);
+    if (id[a] < 0) return;
+    w *= wa;
+  }
+  if (w == 0.0) return;
+  const double f = F[(long long)p * dim + comp_col(c, dim)];
+  atomicAdd(&b[c.off + ((long long)id[2] * c.ny + id[1]) * c.nx + id[0]], f * w);
+}
+
+// One warp per (particle, component).
+__global__ void __launch_bounds__(kBlock) k_interp(LevelDev L, int n, int dim, int np, const double* __restrict__ X,
+                                                  const double* __restrict__ u, double* __restrict__ U) {
+  const int nodes = dim == 3 ? 64 : 16;
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (long long)np * L.ncomp) return;
+  const int ci = (int)(wid % L.ncomp);
+  const int p = (int)(wid / L.ncomp);
+  const CompDev& c = L.c[ci];
+  const CouplingGeom ge = geom_of(c, dim);
+  double acc = 0.0;
+  for (int q = lane; q < nodes; q += 32) {
+    const int tq[3] = {q & 3, dim == 3 ? (q >> 2) & 3 : 0, dim == 3 ? (q >> 4) & 3 : (q >> 2) & 3};
+    int id[3];
+    double w = 1.0;
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) {
+      const double x = ge.col[a] >= 0 ? X[(long long)p * dim + ge.col[a]] * n : 0.0;
+      double wa;
+      axis_node(ge.kind[a], x, ge.off[a], n, tq[a], &id[a], &wa);
+      ok = ok && id[a] >= 0;
+      w *= wa;
+    }
+    if (ok) acc += w * u[c.off + ((long long)id[2] * c.ny + id[1]) * c.nx + id[0]];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) U[(long long)p * dim + comp_col(c, dim)] = acc;
+}
+
+__global__ void __launch_bounds__(kBlock) k_em(int np, int dim, double* __restrict__ X, const double* __restrict__ V) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  for (int a = 0; a < dim; ++a) {
+    double x = X[(long long)p * dim + a] + V[(long long)p * dim + a];
+    if (a < dim - 1) {
+      x = x - floor(x);
+    } else {
+      if (x < 0.0) x = -x;
+      if (x > 1.0) x = 2.0 - x;
+    }
+    X[(long long)p * dim + a] = x;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// MAC projection pieces (Section 4): D^ w at cells, w -= D^T phi at faces.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_divergence(LevelDev Lv, const double* __restrict__ w,
+                                                      double* __restrict__ div, double* __restrict__ sum) {
+  const CompDev& u = Lv.c[0];
+  const CompDev& wz = Lv.c[Lv.ncomp - 1];
+  const int nx = u.nx, ny = u.ny, nz = u.nz;
+  const long long N = (long long)nx * ny * nz;
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double d = 0.0;
+  if (s < N) {
+    const int i = (int)(s % nx);
+    const long long t = s / nx;
+    const int j = (int)(t % ny), k = (int)(t / ny);
+    const long long rowc = ((long long)k * ny + j) * nx;
+    d = w[u.off + rowc + wrapi(i + 1, nx)] - w[u.off + rowc + i];
+    if (Lv.ncomp == 3) {
+      const CompDev& v = Lv.c[1];
+      d += w[v.off + ((long long)k * ny + wrapi(j + 1, ny)) * nx + i] - w[v.off + rowc + i];
+    }
+    if (k < nz - 1) d += w[wz.off + rowc + i];
+    if (k > 0) d -= w[wz.off + rowc - (long long)nx * ny + i];
+    div[s] = d;
+  }
+  d = block_sum(d);
+  if (threadIdx.x == 0) atomicAdd(sum, d);
+}
+
+__global__ void __launch_bounds__(kBlock) k_sub_mean(long long n, double* __restrict__ x, const double* __restrict__ sum) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) x[s] -= *sum / (double)n;
+}
+
+__global__ void __launch_bounds__(kBlock) k_grad_sub(LevelDev Lv, double* __restrict__ w, const double* __restrict__ phi) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Lv.size) return;
+  int ci, i, j, k;
+  site_of(Lv, s, &ci, &i, &j, &k);
+  const CompDev& u0 = Lv.c[0];
+  const int nx = u0.nx, ny = u0.ny;
+  const long long rowc = ((long long)k * ny + j) * nx;
+  double g;
+  const int cid = Lv.c[ci].comp_id;
+  if (cid == 0) {
+    g = phi[rowc + wrapi(i - 1, nx)] - phi[rowc + i];
+  } else if (cid == 1) {
+    g = phi[((long long)k * ny + wrapi(j - 1, ny)) * nx + i] - phi[rowc + i];
+  } else {
+    g = phi[rowc + i] - phi[rowc + (long long)nx * ny + i];
+  }
+  w[s] -= g;
+}
+
+__global__ void k_philox(const uint32_t* __restrict__ ctr, Key key, uint32_t* __restrict__ out, int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  uint4 c = make_uint4(ctr[4 * q], ctr[4 * q + 1], ctr[4 * q + 2], ctr[4 * q + 3]);
+  uint4 r = philox10(c, key.k0, key.k1);
+  out[4 * q] = r.x;
+  out[4 * q + 1] = r.y;
+  out[4 * q + 2] = r.z;
+  out[4 * q + 3] = r.w;
+}
+
+inline unsigned grid_for(long long n, int block = kBlock) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool noise, Key key,
+                          const unsigned long long* cyc, cudaStream_t st) {
+  if (L.level == 0) {
+    for (int colour = 0; colour < 2; ++colour) {
+      ColourPass cp{};
+      long long gs = 0;
+      for (int ci = 0; ci < L.ncomp; ++ci) {
+        const CompDev& c = L.c[ci];
+        cp.gstart[ci] = gs;
+        cp.nsites[ci] = (long long)(c.nx / 2) * c.ny * c.nz;
+        gs += (cp.nsites[ci] + 3) / 4;
+      }
+      cp.gstart[L.ncomp] = gs;
+      if (noise)
+        k_fine_colour<T, true><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
+      else
+        k_fine_colour<T, false><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
+    }
+    return cudaGetLastError();
+  }
+  int maxcol = 0;
+  for (int ci = 0; ci < L.ncomp; ++ci) maxcol = maxcol > L.c[ci].ncol ? maxcol : L.c[ci].ncol;
+  for (int q = 0; q < maxcol; ++q) {
+    ColourPass cp{};
+    long long gs = 0;
+    for (int ci = 0; ci < L.ncomp; ++ci) {
+      const CompDev& c = L.c[ci];
+      cp.gstart[ci] = gs;
+      cp.nsites[ci] = 0;
+      if (q < c.ncol) {
+        const int cx = q % c.mx, cy = (q / c.mx) % c.my, cz = q / (c.mx * c.my);
+        cp.cx[ci] = cx;
+        cp.cy[ci] = cy;
+        cp.cz[ci] = cz;
+        cp.nxc[ci] = (c.nx - cx + c.mx - 1) / c.mx;
+        cp.nyc[ci] = (c.ny - cy + c.my - 1) / c.my;
+        cp.nzc[ci] = (c.nz - cz + c.mz - 1) / c.mz;
+        cp.colour_id[ci] = q;
+        if (cp.nxc[ci] > 0 && cp.nyc[ci] > 0 && cp.nzc[ci] > 0)
+          cp.nsites[ci] = (long long)cp.nxc[ci] * cp.nyc[ci] * cp.nzc[ci];
+      }
+      if (cp.nxc[ci] <= 0) cp.nxc[ci] = 1;
+      if (cp.nyc[ci] <= 0) cp.nyc[ci] = 1;
+      gs += (cp.nsites[ci] + 3) / 4;
+    }
+    cp.gstart[L.ncomp] = gs;
+    if (gs == 0) continue;
+    if (noise)
+      k_coarse_colour<T, true><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, sweep, key, cyc);
+    else
+      k_coarse_colour<T, false><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, sweep, key, cyc);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_residual(const LevelDev& L, const T* v, const T* b, T* t, cudaStream_t st) {
+  k_residual<T><<<grid_for(L.size), kBlock, 0, st>>>(L, v, b, t);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* t, T* bc, cudaStream_t st) {
+  k_restrict<T><<<grid_for(Lc.size), kBlock, 0, st>>>(Lf, Lc, t, bc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prolong(const LevelDev& Lf, const LevelDev& Lc, T* v, const T* vc, cudaStream_t st) {
+  k_prolong<T><<<grid_for(Lf.size), kBlock, 0, st>>>(Lf, Lc, v, vc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coarsest(const LevelDev& L, T* v, const T* b, bool noise, Key key,
+                            const unsigned long long* cyc, cudaStream_t st) {
+  int nmax = 0;
+  for (int ci = 0; ci < L.ncomp; ++ci) {
+    const int N = L.c[ci].nx * L.c[ci].ny * L.c[ci].nz;
+    nmax = N > nmax ? N : nmax;
+  }
+  const size_t smem = 2 * (size_t)nmax * sizeof(double);
+  if (noise)
+    k_coarsest<T, true><<<L.ncomp, 256, smem, st>>>(L, v, b, key, cyc);
+  else
+    k_coarsest<T, false><<<L.ncomp, 256, smem, st>>>(L, v, b, key, cyc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_outer_residual(const LevelDev& L0, const double* z, const double* b, T* r, double* norm2,
+                                  cudaStream_t st) {
+  k_outer_residual<T><<<grid_for(L0.size), kBlock, 0, st>>>(L0, z, b, r, norm2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_outer_update(long long n, double* z, const T* d, cudaStream_t st) {
+  k_outer_update<T><<<grid_for(n), kBlock, 0, st>>>(n, z, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm2(long long n, const double* x, double* out, cudaStream_t st) {
+  long long blocks = grid_for(n);
+  if (blocks > 4 * 152) blocks = 4 * 152;
+  if (blocks < 1) blocks = 1;
+  k_norm2<<<(unsigned)blocks, kBlock, 0, st>>>(n, x, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(long long n, double a, const double* x, double c, const double* y, double* out,
+                         cudaStream_t st) {
+  k_axpby<<<grid_for(n), kBlock, 0, st>>>(n, a, x, c, y, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st) {
+  k_set_u64<<<1, 1, 0, st>>>(p, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inc_u64(unsigned long long* p, cudaStream_t st) {
+  k_inc_u64<<<1, 1, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spread(const LevelDev& L0, int n, int dim, int np, const double* X, const double* F, double* b,
+                          cudaStream_t st) {
+  if (np <= 0) return cudaSuccess;
+  const long long nt = (long long)np * L0.ncomp * (dim == 3 ? 64 : 16);
+  k_spread<<<grid_for(nt), kBlock, 0, st>>>(L0, n, dim, np, X, F, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interp(const LevelDev& L0, int n, int dim, int np, const double* X, const double* u, double* U,
+                          cudaStream_t st) {
+  if (np <= 0) return cudaSuccess;
+  const long long nt = (long long)np * L0.ncomp * 32;
+  k_interp<<<grid_for(nt), kBlock, 0, st>>>(L0, n, dim, np, X, u, U);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_em(int np, int dim, double* X, const double* V, cudaStream_t st) {
+  if (np <= 0) return cudaSuccess;
+  k_em<<<grid_for(np), kBlock, 0, st>>>(np, dim, X, V);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_divergence(const LevelDev& Lv, const double* w, double* div, double* sum, cudaStream_t st) {
+  const long long N = (long long)Lv.c[0].nx * Lv.c[0].ny * Lv.c[0].nz;
+  k_divergence<<<grid_for(N), kBlock, 0, st>>>(Lv, w, div, sum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub_mean(long long n, double* x, const double* sum, cudaStream_t st) {
+  k_sub_mean<<<grid_for(n), kBlock, 0, st>>>(n, x, sum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_sub(const LevelDev& Lv, double* w, const double* phi, cudaStream_t st) {
+  k_grad_sub<<<grid_for(Lv.size), kBlock, 0, st>>>(Lv, w, phi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, Key key, uint32_t* out, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_philox<<<grid_for(n), kBlock, 0, st>>>(ctr, key, out, n);
+  return cudaGetLastError();
+}
+
+#define SELM_INSTANTIATE(T)                                                                                  \
+  template cudaError_t launch_smooth<T>(const LevelDev&, T*, const T*, int, bool, Key,                      \
+                                        const unsigned long long*, cudaStream_t);                           \
+  template cudaError_t launch_residual<T>(const LevelDev&, const T*, const T*, T*, cudaStream_t);           \
+  template cudaError_t launch_restrict<T>(const LevelDev&, const LevelDev&, const T*, T*, cudaStream_t);    \
+  template cudaError_t launch_prolong<T>(const LevelDev&, const LevelDev&, T*, const T*, cudaStream_t);     \
+  template cudaError_t launch_coarsest<T>(const LevelDev&, T*, const T*, bool, Key,                         \
+                                          const unsigned long long*, cudaStream_t);                         \
+  template cudaError_t launch_outer_residual<T>(const LevelDev&, const double*, const double*, T*, double*, \
+                                                cudaStream_t);                                              \
+  template cudaError_t launch_outer_update<T>(long long, double*, const T*, cudaStream_t);
+
+SELM_INSTANTIATE(float)
+SELM_INSTANTIATE(double)
+
+}  // namespace selm

@@ -1,0 +1,60 @@
+// Kernel launchers (defined in selm_kernels.cu, used by the C-ABI layer).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "selm_internal.h"
+
+namespace selm {
+
+struct Key {
+  uint32_t k0, k1;
+};
+
+// Stage kernels.  `T` is float or double (inner precision); all launches go
+// on `st`.  Counters (`cyc`) are read from device memory so that the calls can
+// be captured in CUDA graphs.
+template <typename T>
+cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool noise, Key key,
+                          const unsigned long long* cyc, cudaStream_t st);
+template <typename T>
+cudaError_t launch_residual(const LevelDev& L, const T* v, const T* b, T* t, cudaStream_t st);
+template <typename T>
+cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* t, T* bc,
+                            cudaStream_t st);
+template <typename T>
+cudaError_t launch_prolong(const LevelDev& Lf, const LevelDev& Lc, T* v, const T* vc,
+                           cudaStream_t st);
+template <typename T>
+cudaError_t launch_coarsest(const LevelDev& L, T* v, const T* b, bool noise, Key key,
+                            const unsigned long long* cyc, cudaStream_t st);
+template <typename T>
+cudaError_t launch_outer_residual(const LevelDev& L0, const double* z, const double* b, T* r,
+                                  double* norm2, cudaStream_t st);
+template <typename T>
+cudaError_t launch_outer_update(long long n, double* z, const T* d, cudaStream_t st);
+
+cudaError_t launch_norm2(long long n, const double* x, double* out, cudaStream_t st);
+cudaError_t launch_axpby(long long n, double a, const double* x, double c, const double* y,
+                         double* out, cudaStream_t st);
+cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
+cudaError_t launch_inc_u64(unsigned long long* p, cudaStream_t st);
+
+// Particle coupling (velocity system, level 0).
+cudaError_t launch_spread(const LevelDev& L0, int n, int dim, int np, const double* X,
+                          const double* F, double* b, cudaStream_t st);
+cudaError_t launch_interp(const LevelDev& L0, int n, int dim, int np, const double* X,
+                          const double* u, double* U, cudaStream_t st);
+cudaError_t launch_em(int np, int dim, double* X, const double* V, cudaStream_t st);
+
+// MAC projection pieces.
+cudaError_t launch_divergence(const LevelDev& Lv, const double* w, double* div, double* sum,
+                              cudaStream_t st);
+cudaError_t launch_sub_mean(long long n, double* x, const double* sum, cudaStream_t st);
+cudaError_t launch_grad_sub(const LevelDev& Lv, double* w, const double* phi, cudaStream_t st);
+
+cudaError_t launch_philox(const uint32_t* ctr, Key key, uint32_t* out, int n, cudaStream_t st);
+
+}  // namespace selm

@@ -1,0 +1,310 @@
+"""Python binding of libselm_mg.so (include/selm_mg.h): argument marshalling only.
+
+Every function below has the name of the C entry point it calls and takes
+torch CUDA tensors where the C call takes device pointers.  Streams default to
+torch's current stream.  All arithmetic runs in the CUDA library; if the
+library cannot be loaded this module raises instead of falling back.
+"""
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+SELM_OK, SELM_EINVAL, SELM_ENOMEM, SELM_ECUDA, SELM_ENOCONV, SELM_ETIMEOUT, SELM_EBUSY = range(7)
+SELM_FP64, SELM_FP32_REFINE64 = 0, 1
+SELM_PROJ_NONE, SELM_PROJ_MAC = 0, 1
+SELM_COARSE_CHOLESKY, SELM_COARSE_SMOOTH = 0, 1
+SELM_SYS_VELOCITY, SELM_SYS_PRESSURE = 0, 1
+
+_STATUS = {0: "SELM_OK", 1: "SELM_EINVAL", 2: "SELM_ENOMEM", 3: "SELM_ECUDA", 4: "SELM_ENOCONV",
+           5: "SELM_ETIMEOUT", 6: "SELM_EBUSY"}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class SelmDesc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("n", ctypes.c_int), ("mu", ctypes.c_double), ("kT", ctypes.c_double),
+        ("levels", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
+        ("precision", ctypes.c_int), ("projection", ctypes.c_int), ("coarse_mode", ctypes.c_int),
+        ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("proj_tol", ctypes.c_double),
+        ("max_particles", ctypes.c_int), ("seed", ctypes.c_uint64), ("instance", ctypes.c_uint64),
+        ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class SelmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_U64 = ctypes.c_uint64
+_LL = ctypes.c_longlong
+_SIGS = {
+    "selm_mg_footprint": (ctypes.c_size_t, [ctypes.POINTER(SelmDesc)]),
+    "selm_mg_create": (_I, [ctypes.POINTER(SelmDesc), _P, ctypes.POINTER(_P)]),
+    "selm_mg_destroy": (_I, [_P]),
+    "selm_mg_last_error": (ctypes.c_char_p, [_P]),
+    "selm_mg_solve": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+    "selm_mg_sample": (_I, [_P, _I, _P, _I, _P, _P, _P]),
+    "selm_mg_step": (_I, [_P, _I, _P, _P, _D, _I, _I, _P]),
+    "selm_mg_levels": (_I, [_P, _I]),
+    "selm_mg_ncomp": (_I, [_P, _I]),
+    "selm_mg_layout": (_I, [_P, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
+    "selm_mg_inner_bytes": (_I, [_P]),
+    "selm_mg_chain": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_U64)]),
+    "selm_mg_set_cycle": (_I, [_P, _U64]),
+    "selm_mg_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_LL)]),
+    "selm_mg_smooth": (_I, [_P, _I, _I, _P, _P, _I, _U64, _I, _P]),
+    "selm_mg_residual_restrict": (_I, [_P, _I, _I, _P, _P, _P, _P]),
+    "selm_mg_prolong_correct": (_I, [_P, _I, _I, _P, _P, _P]),
+    "selm_mg_coarsest": (_I, [_P, _I, _P, _P, _U64, _I, _P]),
+    "selm_mg_vcycle": (_I, [_P, _I, _P, _P, _U64, _I, _P]),
+    "selm_mg_outer_residual": (_I, [_P, _I, _P, _P, _P, _P, _P]),
+    "selm_mg_outer_update": (_I, [_P, _I, _P, _P, _P]),
+    "selm_mg_fac_cycle": (_I, [_P, _I, _P, _P, _U64, _I, _P]),
+    "selm_mg_fac_solve": (_I, [_P, _I, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+    "selm_mg_spread": (_I, [_P, _I, _P, _P, _P, _P]),
+    "selm_mg_interp": (_I, [_P, _I, _P, _P, _P, _P]),
+    "selm_mg_project": (_I, [_P, _P, ctypes.POINTER(_I), _P]),
+    "selm_mg_em_update": (_I, [_P, _I, _P, _P, _P]),
+    "selm_philox4x32_10": (_I, [_P, ctypes.c_uint32, ctypes.c_uint32, _P, _I, _P]),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libselm_mg.so (built in-tree by __graft_entry__.build()); raises if absent."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "(the CUDA library is required; there is no CPU fallback)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(h, status):
+    if status != SELM_OK:
+        msg = lib().selm_mg_last_error(h).decode() if h else ""
+        raise SelmError(status, msg)
+
+
+# -- torch caching allocator as the library's device allocator ----------------
+def _alloc(nbytes, ctx):
+    return torch.cuda.caching_allocator_alloc(int(nbytes))
+
+
+def _free(ptr, ctx):
+    torch.cuda.caching_allocator_delete(ptr)
+
+
+_ALLOC_CB = ALLOC_FN(_alloc)
+_FREE_CB = FREE_FN(_free)
+
+
+def make_desc(dim, n, mu=1.0, kT=1.0, levels=0, nu_pre=2, nu_post=2, precision=SELM_FP64,
+              projection=SELM_PROJ_NONE, coarse_mode=SELM_COARSE_CHOLESKY, tol=1e-10, max_cycles=100,
+              proj_tol=1e-12, max_particles=4096, seed=0, instance=0, torch_allocator=True):
+    d = SelmDesc()
+    d.dim, d.n, d.mu, d.kT, d.levels = dim, n, mu, kT, levels
+    d.nu_pre, d.nu_post, d.precision, d.projection, d.coarse_mode = nu_pre, nu_post, precision, projection, coarse_mode
+    d.tol, d.max_cycles, d.proj_tol, d.max_particles = tol, max_cycles, proj_tol, max_particles
+    d.seed, d.instance = seed, instance
+    if torch_allocator:
+        d.alloc, d.free = _ALLOC_CB, _FREE_CB
+    return d
+
+
+def selm_mg_footprint(desc):
+    return lib().selm_mg_footprint(ctypes.byref(desc))
+
+
+def selm_mg_create(desc, stream=None):
+    h = _P()
+    st = lib().selm_mg_create(ctypes.byref(desc), _stream(stream), ctypes.byref(h))
+    if st != SELM_OK:
+        raise SelmError(st, "selm_mg_create failed (see stderr)")
+    return h.value
+
+
+def selm_mg_destroy(h):
+    _check(None, lib().selm_mg_destroy(h))
+
+
+def selm_mg_solve(h, X, F, U, stream=None, want_stats=True):
+    npart = X.shape[0]
+    cyc, res = _I(0), _D(0.0)
+    _check(h, lib().selm_mg_solve(h, npart, _ptr(X), _ptr(F), _ptr(U),
+                                  ctypes.byref(cyc) if want_stats else None,
+                                  ctypes.byref(res) if want_stats else None, _stream(stream)))
+    return cyc.value, res.value
+
+
+def selm_mg_sample(h, X, ncycles, g, xi_out=None, stream=None):
+    _check(h, lib().selm_mg_sample(h, X.shape[0], _ptr(X), ncycles, _ptr(g), _ptr(xi_out), _stream(stream)))
+
+
+def selm_mg_step(h, X, F, dt, nsteps, ncycles_per_step, stream=None):
+    _check(h, lib().selm_mg_step(h, X.shape[0], _ptr(X), _ptr(F), dt, nsteps, ncycles_per_step, _stream(stream)))
+
+
+def selm_mg_levels(h, system=SELM_SYS_VELOCITY):
+    return lib().selm_mg_levels(h, system)
+
+
+def selm_mg_ncomp(h, system=SELM_SYS_VELOCITY):
+    return lib().selm_mg_ncomp(h, system)
+
+
+def selm_mg_layout(h, system, level, comp):
+    dims = (_I * 3)()
+    off, size = _LL(0), _LL(0)
+    _check(h, lib().selm_mg_layout(h, system, level, comp, dims, ctypes.byref(off), ctypes.byref(size)))
+    return (dims[0], dims[1], dims[2]), off.value, size.value
+
+
+def selm_mg_inner_bytes(h):
+    return lib().selm_mg_inner_bytes(h)
+
+
+def selm_mg_chain(h):
+    p, c = _P(), _U64(0)
+    _check(h, lib().selm_mg_chain(h, ctypes.byref(p), ctypes.byref(c)))
+    return p.value, c.value
+
+
+def selm_mg_set_cycle(h, cycle):
+    _check(h, lib().selm_mg_set_cycle(h, cycle))
+
+
+def selm_mg_stats(h):
+    a, b, c = _I(0), _I(0), _LL(0)
+    _check(h, lib().selm_mg_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def selm_mg_smooth(h, system, level, v, b, sweep, cycle, noise, stream=None):
+    _check(h, lib().selm_mg_smooth(h, system, level, _ptr(v), _ptr(b), sweep, cycle, int(noise), _stream(stream)))
+
+
+def selm_mg_residual_restrict(h, system, level, v, b, b_coarse, stream=None):
+    _check(h, lib().selm_mg_residual_restrict(h, system, level, _ptr(v), _ptr(b), _ptr(b_coarse), _stream(stream)))
+
+
+def selm_mg_prolong_correct(h, system, level, v, v_coarse, stream=None):
+    _check(h, lib().selm_mg_prolong_correct(h, system, level, _ptr(v), _ptr(v_coarse), _stream(stream)))
+
+
+def selm_mg_coarsest(h, system, v, b, cycle, noise, stream=None):
+    _check(h, lib().selm_mg_coarsest(h, system, _ptr(v), _ptr(b), cycle, int(noise), _stream(stream)))
+
+
+def selm_mg_vcycle(h, system, v, b, cycle, noise, stream=None):
+    _check(h, lib().selm_mg_vcycle(h, system, _ptr(v), _ptr(b), cycle, int(noise), _stream(stream)))
+
+
+def selm_mg_outer_residual(h, system, z, b64, r, norm2=None, stream=None):
+    _check(h, lib().selm_mg_outer_residual(h, system, _ptr(z), _ptr(b64), _ptr(r), _ptr(norm2), _stream(stream)))
+
+
+def selm_mg_outer_update(h, system, z, d, stream=None):
+    _check(h, lib().selm_mg_outer_update(h, system, _ptr(z), _ptr(d), _stream(stream)))
+
+
+def selm_mg_fac_cycle(h, system, z, b64, cycle, noise, stream=None):
+    _check(h, lib().selm_mg_fac_cycle(h, system, _ptr(z), _ptr(b64), cycle, int(noise), _stream(stream)))
+
+
+def selm_mg_fac_solve(h, system, z, b64, tol, max_cycles, stream=None):
+    cyc, res = _I(0), _D(0.0)
+    _check(h, lib().selm_mg_fac_solve(h, system, _ptr(z), _ptr(b64), tol, max_cycles, ctypes.byref(cyc),
+                                      ctypes.byref(res), _stream(stream)))
+    return cyc.value, res.value
+
+
+def selm_mg_spread(h, X, F, b, stream=None):
+    _check(h, lib().selm_mg_spread(h, X.shape[0], _ptr(X), _ptr(F), _ptr(b), _stream(stream)))
+
+
+def selm_mg_interp(h, X, u, U, stream=None):
+    _check(h, lib().selm_mg_interp(h, X.shape[0], _ptr(X), _ptr(u), _ptr(U), _stream(stream)))
+
+
+def selm_mg_project(h, w, stream=None):
+    c = _I(0)
+    _check(h, lib().selm_mg_project(h, _ptr(w), ctypes.byref(c), _stream(stream)))
+    return c.value
+
+
+def selm_mg_em_update(h, X, V, stream=None):
+    _check(h, lib().selm_mg_em_update(h, X.shape[0], _ptr(X), _ptr(V), _stream(stream)))
+
+
+def selm_philox4x32_10(ctr, key0, key1, out, stream=None):
+    n = ctr.numel() // 4
+    _check(None, lib().selm_philox4x32_10(_ptr(ctr), key0, key1, _ptr(out), n, _stream(stream)))
+
+
+class SelmMG:
+    """Owner of one handle; methods forward to the functions above."""
+
+    def __init__(self, **kw):
+        self.desc = make_desc(**kw)
+        self.h = selm_mg_create(self.desc)
+
+    def close(self):
+        if self.h:
+            torch.cuda.synchronize()
+            selm_mg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self, system=SELM_SYS_VELOCITY, level=0):
+        n = selm_mg_ncomp(self.h, system)
+        comps = [selm_mg_layout(self.h, system, level, c) for c in range(n)]
+        return [(dims, off) for dims, off, _ in comps], comps[0][2]
+
+    def inner_dtype(self):
+        return torch.float32 if selm_mg_inner_bytes(self.h) == 4 else torch.float64

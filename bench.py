@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the stochastic multigrid SELM hot path on one GB300 (per rank).
+
+Workload (one "step" = one Euler-Maruyama step of Algorithm 4, the whole hot
+path): 3-D channel, 128^3 MAC grid on the unit box, periodic in x and y,
+no-slip walls in z; 1024 particles uniform in the channel (2-cell wall
+clearance) with fixed N(0,1) forces; dt = 1e-3.  Per step: Peskin spread,
+MAC projection, FAC solve of A u = b to ||r|| <= 1e-10 ||b|| (FP32 smoothing
+and transfers inside FP64 iterative refinement, FP64 coarsest solve),
+2 stochastic FAC cycles of the thermal chain, projection, interpolation and
+the particle update.
+
+Metric: cell-cycles per second = 128^3 fine cells (all three velocity
+components) x velocity V-cycles executed (solve + sample), divided by the
+device time of the steps.  L2 (129 MB) is flushed between steps by writing a
+256 MB buffer outside the timed events.
+
+With --impl reference the FP64 CPU oracle is timed on the host cores instead
+(one stochastic FAC cycle of the same 128^3 system per step).
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "stochastic-MG cells/s (frac of HBM peak); served solves/s + p99 vs plain form"
+N_CELLS_EDGE = 128
+N_PARTICLES = 1024
+DT = 1e-3
+SAMPLE_CYCLES = 2
+
+
+def workload_config(n, npart, projection):
+    return {
+        "workload": f"3-D channel {n}^3 MAC grid (periodic x,y; no-slip walls z), {npart} particles, "
+                    f"Euler-Maruyama dt={DT}, FAC solve to 1e-10 + {SAMPLE_CYCLES} stochastic cycles per step, "
+                    f"FP32 smoothing/transfers with FP64 refinement and FP64 coarsest solve, "
+                    f"projection={'MAC' if projection else 'none'}",
+        "grid": n, "particles": npart, "dt": DT, "stochastic_cycles_per_step": SAMPLE_CYCLES,
+        "tol": 1e-10, "levels": None, "l2": "flushed between steps (256 MB write, outside the timed events)",
+        "unit_of_work": "cell-cycle = one fine cell (all 3 velocity components) through one V-cycle",
+    }
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--n", type=int, default=N_CELLS_EDGE)
+    p.add_argument("--particles", type=int, default=N_PARTICLES)
+    p.add_argument("--no-projection", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (spawned process, one thread)
+# ---------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import os, sys, time, json
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import grid, multigrid, philox
+n = {n}
+s = grid.velocity_system(n, 3)
+co = multigrid.Coarsest(s)
+import selm_inputs
+z = selm_inputs.fields(s.shapes(0), seed=1, scale=1e-2)
+zero = s.zeros(0)
+times = []
+for k in range({reps}):
+    t = time.perf_counter()
+    multigrid.fac_cycle(s, z, zero, philox.PhiloxNoise(0, 0, k), 1.0, coarsest=co)
+    times.append(time.perf_counter() - t)
+print(json.dumps(times))
+"""
+
+
+def run_oracle_cycles(n, reps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SNIPPET.format(root=ROOT, n=n, reps=reps)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(n):
+    times = run_oracle_cycles(n, 1)
+    t = times[0]
+    return {"value": n ** 3 / t, "unit": "cells/s", "cores": 1, "kind": "oracle",
+            "sample": f"one stochastic FAC cycle (Algorithm 1 around the V-cycle of Algorithm 3) of the FP64 "
+                      f"numpy oracle on the {n}^3 velocity system, single thread, {t:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n = args.n
+    times = run_oracle_cycles(n, args.warmup + args.steps)
+    timed = times[args.warmup:]
+    total = sum(timed)
+    value = n ** 3 * len(timed) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(n, args.particles, not args.no_projection),
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: one stochastic FAC cycle of the {n}^3 FP64 oracle, single thread"},
+        "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, device_index):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="selm_clocks_", suffix=".csv")
+        os.close(fd)
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    src = open(os.path.join(ROOT, "paper_1003_2680_gb300", "csrc", "selm_kernels.cu"), "rb").read()
+    return hashlib.sha256(src).hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class, n):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_class}_{n}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_tr or m_sha.group(1) != kernel_source_sha():
+        return None
+    return float(m_tr.group(1))
+
+
+def sweep_bytes_per_launch(S, h, kernel_class):
+    """Algorithmic bytes of one launch of the kernel class, averaged over one V-cycle.
+
+    A colour pass reads every unknown of its level once (the neighbours of
+    the updated colour), reads b and writes v at the updated sites:
+    e * (N_level + 2 N_colour).
+    """
+    e = S.selm_mg_inner_bytes(h)
+    levels = S.selm_mg_levels(h, 0)
+    ncomp = S.selm_mg_ncomp(h, 0)
+    total, launches = 0.0, 0
+    for lev in range(levels - 1):
+        sizes = []
+        for c in range(ncomp):
+            (nx, ny, nz), off, size = S.selm_mg_layout(h, 0, lev, c)
+            sizes.append(nx * ny * nz)
+        if lev == 0 and kernel_class == "fine_sweep":
+            N = sum(sizes)
+            total += 2 * (e * (N + 2 * N / 2))
+            launches += 2
+        elif lev > 0 and kernel_class == "coarse_sweep":
+            ncols = [12 if c < ncomp - 1 else 8 for c in range(ncomp)]
+            for q in range(max(ncols)):
+                present = [c for c in range(ncomp) if q < ncols[c]]
+                total += sum(e * (sizes[c] + 2 * sizes[c] / ncols[c]) for c in present)
+                launches += 1
+    return total / max(launches, 1)
+
+
+# ---------------------------------------------------------------------------
+# main GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_1003_2680_gb300 import _build
+    _build.build()
+    from paper_1003_2680_gb300 import selm as S
+    import selm_inputs
+
+    n, npart = args.n, args.particles
+    proj = S.SELM_PROJ_NONE if args.no_projection else S.SELM_PROJ_MAC
+    m = S.SelmMG(dim=3, n=n, precision=S.SELM_FP32_REFINE64, projection=proj, tol=1e-10, seed=0,
+                 instance=rank, max_particles=npart)
+    h = m.h
+    X0 = selm_inputs.particles(npart, 3, n, seed=rank)
+    F0 = selm_inputs.forces(npart, 3, seed=rank)
+    X = torch.tensor(X0, device="cuda")
+    F = torch.tensor(F0, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def one_step():
+        S.selm_mg_step(h, X, F, DT, 1, SAMPLE_CYCLES)
+        solve_cycles = S.selm_mg_stats(h)[0]
+        return solve_cycles + SAMPLE_CYCLES
+
+    # burn-in of the chain + warm-up of every path
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device events per step, L2 flushed between steps) ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    cycles = 0
+    launches0 = S.selm_kernel_launches()
+    print(f"[bench] library kernel launches before the timed region: {launches0}", file=sys.stderr)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            cycles += one_step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = S.selm_kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(step_ms) / 1e3
+    t_tensor = torch.tensor([t_total, float(cycles)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tmax = t_tensor[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        csum = t_tensor[1:].clone()
+        dist.all_reduce(csum, op=dist.ReduceOp.SUM)
+        t_total, cycles_all = float(tmax.item()), float(csum.item())
+    else:
+        cycles_all = float(cycles)
+    value = n ** 3 * cycles_all / t_total
+
+    # ---- end to end: the host-buffer C call, copies inside the timed region ----
+    Xh = torch.tensor(X0).pin_memory()
+    Fh = torch.tensor(F0).pin_memory()
+    for _ in range(2):
+        S.selm_mg_step_host(h, Xh, Fh, DT, 1, SAMPLE_CYCLES)
+    e2e_time, e2e_cycles = 0.0, 0
+    torch.cuda.synchronize()
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.selm_mg_step_host(h, Xh, Fh, DT, 1, SAMPLE_CYCLES)
+        e2e_time += time.perf_counter() - t0
+        e2e_cycles += S.selm_mg_stats(h)[0] + SAMPLE_CYCLES
+    barrier()
+    e2e_value = n ** 3 * e2e_cycles / e2e_time
+    if world > 1:
+        t = torch.tensor([e2e_time], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([float(e2e_cycles)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        e2e_value = n ** 3 * float(c.item()) / float(t.item())
+
+    # ---- per-kernel device time (events on the launching stream) ----
+    prof_steps = min(args.steps, 3)
+    S.selm_profile_reset()
+    S.selm_profile_enable(True)
+    for _ in range(prof_steps):
+        one_step()
+    torch.cuda.synchronize()
+    S.selm_profile_enable(False)
+    per_class = {}
+    for ci, name in enumerate(S.KERNEL_CLASSES):
+        ms, cnt = S.selm_profile_read(ci)
+        per_class[name] = {"ms": ms, "launches": cnt}
+    S.selm_profile_reset()
+    tot_ms = sum(v["ms"] for v in per_class.values()) or 1.0
+    dominant = max(per_class, key=lambda k: per_class[k]["ms"])
+    peak, peak_kind = measured_peaks()
+    roof = None
+    for name in (dominant, "fine_sweep"):
+        if name not in ("fine_sweep", "coarse_sweep") or per_class[name]["launches"] == 0:
+            continue
+        avg_s = per_class[name]["ms"] / per_class[name]["launches"] / 1e3
+        bytes_launch = sweep_bytes_per_launch(S, h, name)
+        achieved = bytes_launch / avg_s / 1e9
+        entry = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                 "frac": achieved / peak, "peak_source": peak_kind,
+                 "traffic": ncu_traffic(name, n), "algorithmic_bytes_per_launch": bytes_launch,
+                 "avg_launch_us": avg_s * 1e6, "share_of_kernel_time": per_class[name]["ms"] / tot_ms}
+        if roof is None:
+            roof = entry
+        else:
+            roof["fine_sweep"] = entry
+    if roof is None:
+        roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None}
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": dict(workload_config(n, npart, proj == S.SELM_PROJ_MAC), levels=S.selm_mg_levels(h, 0),
+                       parallelism=f"replicas x{world} (independent systems, no collective on the data path)"),
+        "velocity_vcycles_per_step": cycles_all / args.steps / world,
+        "roofline": roof,
+        "kernel_time_share": {k: round(v["ms"] / tot_ms, 4) for k, v in per_class.items() if v["launches"]},
+        "e2e": {"value": e2e_value, "unit": "cells/s",
+                "h2d_bytes_per_step": int(X0.nbytes + F0.nbytes), "d2h_bytes_per_step": int(X0.nbytes)},
+        "gpu_launches": int(launches),
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n)
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    m.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

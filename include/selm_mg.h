@@ -113,6 +113,12 @@ selm_status selm_mg_sample(selm_mg* h, int np, const double* X, int ncycles, dou
 selm_status selm_mg_step(selm_mg* h, int np, double* X, const double* F, double dt, int nsteps,
                          int ncycles_per_step, void* stream);
 
+/* selm_mg_step on HOST arrays: copies X and F (row-major [np][dim] doubles in
+   host memory, ideally pinned) to the device, runs `nsteps` steps, copies X
+   back and synchronises `stream`.  np <= max_particles. */
+selm_status selm_mg_step_host(selm_mg* h, int np, double* X_host, const double* F_host, double dt,
+                              int nsteps, int ncycles_per_step, void* stream);
+
 /* ---- layout and state --------------------------------------------------- */
 
 int selm_mg_levels(const selm_mg* h, int system);
@@ -127,6 +133,16 @@ int selm_mg_inner_bytes(const selm_mg* h);
    counter (the Philox counter of the next stochastic cycle). */
 selm_status selm_mg_chain(selm_mg* h, double** xi, uint64_t* cycle);
 selm_status selm_mg_set_cycle(selm_mg* h, uint64_t cycle);
+/* Options.  SELM_OPT_COARSE_ENGINE (default 1): run the levels below the
+   finest with the cluster-resident coarse engine (one thread-block cluster
+   per component, colour passes separated by cluster barriers); 0 selects one
+   launch per colour pass.  Both give the same result up to rounding. */
+enum { SELM_OPT_COARSE_ENGINE = 1 };
+selm_status selm_mg_set_option(selm_mg* h, int option, int value);
+/* Coarse engine of `system`: first level it covers (-1 = not used), cluster
+   size and dynamic shared memory per CTA. */
+selm_status selm_mg_engine_info(const selm_mg* h, int system, int* first_level, int* cluster_size,
+                                size_t* smem_bytes);
 /* FAC cycles run by the last solve (velocity) and the projections it did. */
 selm_status selm_mg_stats(const selm_mg* h, int* last_solve_cycles, int* last_proj_cycles,
                           long long* total_vcycles);
@@ -181,6 +197,33 @@ selm_status selm_mg_interp(selm_mg* h, int np, const double* X, const double* u,
 selm_status selm_mg_project(selm_mg* h, double* w, int* cycles_out, void* stream);
 /* Alg. 4 step 4 tail: X += V, wrap the periodic coordinates, reflect at walls. */
 selm_status selm_mg_em_update(selm_mg* h, int np, double* X, const double* V, void* stream);
+
+/* ---- measurement --------------------------------------------------------
+   Process-wide kernel accounting.  selm_kernel_launches() counts every
+   kernel this library has launched since it was loaded.  With profiling on,
+   every launch is bracketed by CUDA events recorded on its own stream;
+   selm_profile_read() synchronises on those events and returns, per kernel
+   class, the summed device time (ms) and the number of launches since the
+   last reset.  Do not enable profiling while a stream is being captured. */
+enum {
+  SELM_K_FINE_SWEEP = 0,    /* red-black colour pass, level 0 */
+  SELM_K_COARSE_SWEEP = 1,  /* multicolour pass, Galerkin levels */
+  SELM_K_RESIDUAL = 2,
+  SELM_K_RESTRICT = 3,
+  SELM_K_PROLONG = 4,
+  SELM_K_COARSEST = 5,
+  SELM_K_OUTER_RESIDUAL = 6,
+  SELM_K_OUTER_UPDATE = 7,
+  SELM_K_SPREAD = 8,
+  SELM_K_INTERP = 9,
+  SELM_K_PROJECTION = 10,
+  SELM_K_OTHER = 11,
+  SELM_K_NCLASSES = 12
+};
+long long selm_kernel_launches(void);
+selm_status selm_profile_enable(int on);
+selm_status selm_profile_reset(void);
+selm_status selm_profile_read(int kernel_class, double* total_ms, long long* launches);
 
 /* Philox4x32-10 (Salmon et al., SC'11) of n counters: ctr and out are device
    arrays of 4n uint32.  A utility for checking the noise generator. */

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/selm_mg.h"
+#include "selm_coarse.h"
 #include "selm_internal.h"
 #include "selm_launch.h"
 
@@ -31,7 +32,21 @@ struct Sys {
   void* t[kMaxLevels] = {};
   int levels = 0;
   int ncomp = 0;
+  EnginePlanT<float> engf;    // cluster-resident coarse levels (FP32 inner)
+  EnginePlanT<double> engd;   // (FP64 inner)
+  bool use_engine = true;
 };
+
+template <typename T>
+EnginePlanT<T>& eng_of(Sys& s);
+template <>
+EnginePlanT<float>& eng_of<float>(Sys& s) {
+  return s.engf;
+}
+template <>
+EnginePlanT<double>& eng_of<double>(Sys& s) {
+  return s.engd;
+}
 
 // Byte layout of the workspace.
 struct Layout {
@@ -63,6 +78,8 @@ struct selm_mg {
   double* red = nullptr;    // reduction slots
   unsigned long long* cyc = nullptr;  // [0] chain counter, [1] stage-call counter
   double* V = nullptr;      // particle scratch [max_particles][3]
+  double* Xs = nullptr;     // device copies of host particle arrays (selm_mg_step_host)
+  double* Fs = nullptr;
   double* host_red = nullptr;  // pinned
   uint64_t cycle = 0;
   int last_solve_cycles = 0, last_proj_cycles = 0;
@@ -131,7 +148,7 @@ struct Plan {
   std::vector<TableOffsets> toff[2][kMaxLevels];
   size_t field_off[2][kMaxLevels][3];
   size_t u_off = 0, xi_off = 0, bvel_off = 0, wcomb_off = 0, phi_off = 0, prhs_off = 0, red_off = 0,
-         cyc_off = 0, V_off = 0;
+         cyc_off = 0, V_off = 0, Xs_off = 0, Fs_off = 0;
 };
 
 void plan_tables(const HostSystem& hs, int si, Plan* p) {
@@ -187,6 +204,8 @@ void make_plan(const selm_mg_desc& d, const Sys& vel, const Sys* pres, int esize
   p->red_off = p->lay.add(16 * sizeof(double));
   p->cyc_off = p->lay.add(4 * sizeof(unsigned long long));
   p->V_off = p->lay.add((size_t)d.max_particles * 3 * sizeof(double));
+  p->Xs_off = p->lay.add((size_t)d.max_particles * 3 * sizeof(double));
+  p->Fs_off = p->lay.add((size_t)d.max_particles * 3 * sizeof(double));
 }
 
 void bind_system(Sys* s, int si, const Plan& p, char* ws) {
@@ -260,6 +279,12 @@ selm_status vcycle_t(selm_mg* h, Sys& s, int l, T* v0, const T* b0, bool noise, 
   const T* b = l == 0 ? b0 : (const T*)s.b[l];
   const LevelDev& L = s.lev[l];
   const bool last = l == s.levels - 1;
+  const EnginePlanT<T>& eng = eng_of<T>(s);
+  if (l > 0 && s.use_engine && eng.valid && l == eng.params.l0) {
+    // levels l..L-1 in one cluster launch: reads s.b[l], writes s.v[l]
+    CK(launch_coarse_engine<T>(eng, h->mu1, h->mu2, h->d.coarse_mode, noise, h->key, cyc, st));
+    return SELM_OK;
+  }
   if (last && h->d.coarse_mode == SELM_COARSE_CHOLESKY) {
     CK(launch_coarsest<T>(L, v, b, noise, h->key, cyc, st));
     return SELM_OK;
@@ -422,6 +447,7 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
   fill_desc_defaults(&h->d);
   std::string e = validate(h->d);
   if (e.empty()) e = build_systems(h->d, &h->vel, &h->pres, &h->has_pres);
+  if (e.empty() && h->vel.host.level_size(0) >= (1ll << 31)) e = "grid too large (level field >= 2^31 elements)";
   if (!e.empty()) {
     std::fprintf(stderr, "selm_mg_create: %s\n", e.c_str());
     delete h;
@@ -464,6 +490,14 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
     ce = cudaMemcpyAsync(h->ws + p.int_off, p.ints.data(), p.ints.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   bind_system(&h->vel, 0, p, h->ws);
   if (h->has_pres) bind_system(&h->pres, 1, p, h->ws);
+  for (Sys* sy : {&h->vel, h->has_pres ? &h->pres : (Sys*)nullptr}) {
+    if (!sy) continue;
+    if (h->esize == 4)
+      plan_coarse_engine<float>(sy->lev, sy->levels, sy->b, sy->v, sy->t, &sy->engf);
+    else
+      plan_coarse_engine<double>(sy->lev, sy->levels, sy->b, sy->v, sy->t, &sy->engd);
+    cudaGetLastError();
+  }
   h->u = (double*)(h->ws + p.u_off);
   h->xi = (double*)(h->ws + p.xi_off);
   h->bvel = (double*)(h->ws + p.bvel_off);
@@ -475,6 +509,8 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
   h->red = (double*)(h->ws + p.red_off);
   h->cyc = (unsigned long long*)(h->ws + p.cyc_off);
   h->V = (double*)(h->ws + p.V_off);
+  h->Xs = (double*)(h->ws + p.Xs_off);
+  h->Fs = (double*)(h->ws + p.Fs_off);
   const size_t nv = (size_t)h->vel.lev[0].size * sizeof(double);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(h->xi, 0, nv, st);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(h->u, 0, nv, st);
@@ -548,6 +584,28 @@ selm_status selm_mg_set_cycle(selm_mg* h, uint64_t cycle) {
   CK(launch_set_u64(h->cyc + 0, cycle, nullptr));
   CK(cudaDeviceSynchronize());
   h->cycle = cycle;
+  return SELM_OK;
+}
+
+selm_status selm_mg_set_option(selm_mg* h, int option, int value) {
+  if (!h) return SELM_EINVAL;
+  if (option == SELM_OPT_COARSE_ENGINE) {
+    h->vel.use_engine = value != 0;
+    h->pres.use_engine = value != 0;
+    return SELM_OK;
+  }
+  return SELM_EINVAL;
+}
+
+selm_status selm_mg_engine_info(const selm_mg* h, int system, int* first_level, int* cluster_size,
+                                size_t* smem_bytes) {
+  if (!h) return SELM_EINVAL;
+  const Sys* s = system == SELM_SYS_VELOCITY ? &h->vel : (system == SELM_SYS_PRESSURE && h->has_pres ? &h->pres : nullptr);
+  if (!s) return SELM_EINVAL;
+  const bool v = h->esize == 4 ? s->engf.valid : s->engd.valid;
+  if (first_level) *first_level = v ? (h->esize == 4 ? s->engf.params.l0 : s->engd.params.l0) : -1;
+  if (cluster_size) *cluster_size = v ? (h->esize == 4 ? s->engf.cluster : s->engd.cluster) : 0;
+  if (smem_bytes) *smem_bytes = v ? (h->esize == 4 ? s->engf.smem_bytes : s->engd.smem_bytes) : 0;
   return SELM_OK;
 }
 
@@ -770,6 +828,26 @@ selm_status selm_mg_step(selm_mg* h, int np, double* X, const double* F, double 
     CK(launch_interp(h->vel.lev[0], h->d.n, h->d.dim, np, X, h->wcomb, h->V, st));
     CK(launch_em(np, h->d.dim, X, h->V, st));
   }
+  return SELM_OK;
+}
+
+selm_status selm_mg_step_host(selm_mg* h, int np, double* X_host, const double* F_host, double dt, int nsteps,
+                              int ncycles_per_step, void* stream) {
+  if (!h || !check_particles(h, np, X_host) || (np > 0 && !F_host)) return SELM_EINVAL;
+  if (np > h->d.max_particles) {
+    h->err = "np exceeds max_particles";
+    return SELM_EINVAL;
+  }
+  cudaStream_t st = S(stream);
+  const size_t bytes = (size_t)np * h->d.dim * sizeof(double);
+  if (np > 0) {
+    CK(cudaMemcpyAsync(h->Xs, X_host, bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->Fs, F_host, bytes, cudaMemcpyHostToDevice, st));
+  }
+  selm_status r = selm_mg_step(h, np, h->Xs, h->Fs, dt, nsteps, ncycles_per_step, stream);
+  if (r != SELM_OK) return r;
+  if (np > 0) CK(cudaMemcpyAsync(X_host, h->Xs, bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   return SELM_OK;
 }
 

@@ -1,0 +1,652 @@
+// Coarse-level engine: the part of the V-cycle (Algorithm 3) below the finest
+// level, for one component per thread-block cluster.
+//
+// Why: on the Galerkin levels the 3x3x5 stencil needs 12 colour classes, so a
+// V-cycle runs ~200 dependent colour passes on small grids.  As separate
+// launches each pass costs a full launch plus a chain of dependent global
+// loads.  Here one cluster per velocity component runs all of them:
+//   * "cluster" levels are split into z-slabs, one per CTA; a CTA keeps its
+//     slab plus two halo planes on each side in shared memory and, after
+//     updating a site that lies in a neighbour's halo, stores the new value
+//     into the neighbour's shared memory (DSMEM); cluster barriers separate
+//     the colour passes;
+//   * "single" levels (small grids) are held entirely by CTA 0, which runs
+//     their passes with block barriers while the other CTAs wait at the next
+//     cluster barrier;
+//   * b, residuals and the hand-off of corrections between levels go through
+//     global memory (L2), read with L1-bypassing loads.
+// The visiting order (colour classes in increasing id, all sites of a class
+// updated together) and the Philox streams are those of the per-pass kernels,
+// so both paths produce the same chain.
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/selm_mg.h"
+#include "selm_coarse.h"
+#include "selm_internal.h"
+#include "selm_prof.h"
+
+namespace cg = cooperative_groups;
+
+namespace selm {
+namespace {
+
+constexpr int kEngThreads = 512;
+
+__device__ __forceinline__ uint4 eng_philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ void eng_normals(uint4 w, double n[4]) {
+  const double s = 2.3283064365386962890625e-10;
+  const double u0 = ((double)w.x + 0.5) * s, u1 = ((double)w.y + 0.5) * s;
+  const double u2 = ((double)w.z + 0.5) * s, u3 = ((double)w.w + 0.5) * s;
+  const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
+  double s1, c1, s3, c3;
+  sincospi(2.0 * u1, &s1, &c1);
+  sincospi(2.0 * u3, &s3, &c3);
+  n[0] = r0 * c1;
+  n[1] = r0 * s1;
+  n[2] = r1 * c3;
+  n[3] = r1 * s3;
+}
+
+__device__ __forceinline__ void eng_normals(uint4 w, float n[4]) {
+  const float s = 2.3283064365386962890625e-10f;
+  const float u0 = ((float)w.x + 0.5f) * s, u1 = ((float)w.y + 0.5f) * s;
+  const float u2 = ((float)w.z + 0.5f) * s, u3 = ((float)w.w + 0.5f) * s;
+  const float r0 = sqrtf(-2.0f * logf(u0)), r1 = sqrtf(-2.0f * logf(u2));
+  float s1, c1, s3, c3;
+  sincospif(2.0f * u1, &s1, &c1);
+  sincospif(2.0f * u3, &s3, &c3);
+  n[0] = r0 * c1;
+  n[1] = r0 * s1;
+  n[2] = r1 * c3;
+  n[3] = r1 * s3;
+}
+
+__device__ __forceinline__ int ewrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <typename T>
+__device__ __forceinline__ T ld_cg(const T* p) {
+  return __ldcg(p);
+}
+
+// Per-CTA view of one level.
+template <typename T>
+struct View {
+  const EngLevel<T>* L;
+  int z0, z1;          // owned planes [z0, z1)
+  T* v;                // local v buffer: planes [z0-2, z1+2)
+  int plane;           // nx * ny
+  __device__ __forceinline__ int loc(int i, int j, int k) const { return ((k - z0 + 2) * L->ny + j) * L->nx + i; }
+};
+
+template <typename T>
+__device__ __forceinline__ View<T> make_view(const EngLevel<T>& L, unsigned char* smem, int rank, bool cluster) {
+  View<T> w;
+  w.L = &L;
+  if (cluster) {
+    w.z0 = min(rank * L.P, L.nz);
+    w.z1 = min(w.z0 + L.P, L.nz);
+  } else {
+    w.z0 = 0;
+    w.z1 = L.nz;
+  }
+  w.v = (T*)(smem + L.sv);
+  w.plane = L.nx * L.ny;
+  return w;
+}
+
+// sum_{j != i} A_ij v_j (centre excluded) or the full row (centre included).
+// Five independent partial sums (one per z offset) keep the FMA chains short.
+template <typename T>
+__device__ __forceinline__ T stencil_row(const View<T>& w, int i, int j, int k, bool centre) {
+  const EngLevel<T>& L = *w.L;
+  const T* S = L.S + (long long)k * kStencil;
+  const int xm = ewrap(i - 1, L.nx), xp = ewrap(i + 1, L.nx);
+  const int ny = L.ny;
+  const int ym = ny > 1 ? ewrap(j - 1, ny) : j, yp = ny > 1 ? ewrap(j + 1, ny) : j;
+  const int yrow[3] = {ym, j, yp};
+  T acc[5];
+#pragma unroll
+  for (int dz = -2; dz <= 2; ++dz) {
+    T a = (T)0;
+    const int kk = k + dz;
+    if (kk >= 0 && kk < L.nz) {
+      const T* vp = w.v + (kk - w.z0 + 2) * ny * L.nx;
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        if (ny == 1 && dy != 0) continue;
+        const T* row = vp + yrow[dy + 1] * L.nx;
+        const T* Sr = S + ((dz + 2) * 3 + (dy + 1)) * 3;
+        a += __ldg(Sr) * row[xm] + __ldg(Sr + 2) * row[xp];
+        if (centre || dz != 0 || dy != 0) a += __ldg(Sr + 1) * row[i];
+      }
+    }
+    acc[dz + 2] = a;
+  }
+  return (acc[0] + acc[4]) + (acc[1] + acc[3]) + acc[2];
+}
+
+struct Sync {
+  bool cluster;
+  __device__ __forceinline__ void operator()() const {
+    if (cluster)
+      cg::this_cluster().sync();
+    else
+      __syncthreads();
+  }
+};
+
+// One colour pass of the stochastic Gauss-Seidel sweep on the owned planes:
+// one thread per site; the four sites of a noise group each recompute the
+// group's Philox block (cheaper than serialising their updates).
+template <typename T, bool NOISE>
+__device__ void colour_pass(const View<T>& w, int level, int q, int sweep, const T* b, bool b_local, Key key,
+                            unsigned long long cyc, int rank, int csize, bool cluster) {
+  const EngLevel<T>& L = *w.L;
+  const int cx = q % L.mx, cy = (q / L.mx) % L.my, cz = q / (L.mx * L.my);
+  const int nxc = (L.nx - cx + L.mx - 1) / L.mx;
+  const int nyc = (L.ny - cy + L.my - 1) / L.my;
+  const int nzc = (L.nz - cz + L.mz - 1) / L.mz;
+  if (nxc <= 0 || nyc <= 0 || nzc <= 0) return;
+  const int kk_lo = w.z0 <= cz ? 0 : (w.z0 - cz + L.mz - 1) / L.mz;
+  const int kk_hi = min(nzc, w.z1 <= cz ? 0 : (w.z1 - cz + L.mz - 1) / L.mz);
+  if (kk_lo >= kk_hi) return;
+  const int pr = nyc * nxc;
+  const int rank_lo = kk_lo * pr;
+  const int nsite = (kk_hi - kk_lo) * pr;
+  const uint32_t c1 = (uint32_t)level | ((uint32_t)L.comp_id << 4) | ((uint32_t)q << 8) | ((uint32_t)sweep << 12);
+  cg::cluster_group cl = cg::this_cluster();
+  for (int s = threadIdx.x; s < nsite; s += blockDim.x) {
+    const int rk = rank_lo + s;
+    const int ii = rk % nxc;
+    const int t = rk / nxc;
+    const int jj = t % nyc, kk = t / nyc;
+    const int i = cx + L.mx * ii, j = cy + L.my * jj, k = cz + L.mz * kk;
+    const int gidx = (k * L.ny + j) * L.nx + i;
+    const T bb = b_local ? b[gidx] : ld_cg(b + gidx);
+    const T diag = __ldg(L.S + (long long)k * kStencil + 22);
+    const T off = stencil_row(w, i, j, k, false);
+    T nv = (bb - off) / diag;
+    if (NOISE) {
+      T n4[4];
+      eng_normals(eng_philox10(make_uint4((uint32_t)(rk >> 2), c1, (uint32_t)cyc, (uint32_t)(cyc >> 32)), key.k0,
+                               key.k1),
+                  n4);
+      nv += n4[rk & 3] / sqrt(diag);
+    }
+    w.v[w.loc(i, j, k)] = nv;
+    if (cluster && csize > 1) {
+      // push into the halos of the CTAs owning planes within distance 2
+      const int rlo = max(0, (k - 2) / L.P), rhi = min(csize - 1, (k + 2) / L.P);
+      for (int r2 = rlo; r2 <= rhi; ++r2) {
+        if (r2 == rank) continue;
+        const int z0b = min(r2 * L.P, L.nz), z1b = min(z0b + L.P, L.nz);
+        if (z0b >= z1b || k < z0b - 2 || k >= z1b + 2) continue;
+        T* rem = cl.map_shared_rank(w.v, r2);
+        rem[((k - z0b + 2) * L.ny + j) * L.nx + i] = nv;
+      }
+    }
+  }
+}
+
+template <typename T>
+__device__ void zero_local(const View<T>& w) {
+  const int n = (w.z1 - w.z0 + 4) * w.plane;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) w.v[q] = (T)0;
+}
+
+// t = b - A v on the owned planes; t written at field index (global or local buffer).
+template <typename T>
+__device__ void residual(const View<T>& w, const T* b, bool b_local, T* t) {
+  const EngLevel<T>& L = *w.L;
+  const int n = (w.z1 - w.z0) * w.plane;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int i = q % L.nx;
+    const int r = q / L.nx;
+    const int j = r % L.ny, k = w.z0 + r / L.ny;
+    const int gidx = (k * L.ny + j) * L.nx + i;
+    const T bb = b_local ? b[gidx] : ld_cg(b + gidx);
+    t[gidx] = bb - stencil_row(w, i, j, k, true);
+  }
+}
+
+// b_c = P^T t on the coarse planes [Z0, Z1) of level Lc (tables on the fine level Lf).
+template <typename T>
+__device__ void restrict_to(const EngLevel<T>& Lf, const EngLevel<T>& Lc, const T* t, bool t_local, T* bc, int Z0,
+                            int Z1) {
+  const int n = (Z1 - Z0) * Lc.nx * Lc.ny;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int I = q % Lc.nx;
+    const int r = q / Lc.nx;
+    const int J = r % Lc.ny, K = Z0 + r / Lc.ny;
+    T acc = (T)0;
+    for (int qz = 0; qz < 4; ++qz) {
+      const int kf = __ldg(Lf.rz_idx + K * 4 + qz);
+      if (kf < 0) continue;
+      const T wz = __ldg(Lf.rz_w + K * 4 + qz);
+      for (int qy = -1; qy <= 1; ++qy) {
+        T wy;
+        int jf;
+        if (Lf.ny == 1) {
+          if (qy != 0) continue;
+          wy = (T)1;
+          jf = 0;
+        } else {
+          wy = qy == 0 ? (T)1 : (T)0.5;
+          jf = ewrap(2 * J + qy, Lf.ny);
+        }
+#pragma unroll
+        for (int qx = -1; qx <= 1; ++qx) {
+          const T wx = qx == 0 ? (T)1 : (T)0.5;
+          const int idx = (kf * Lf.ny + jf) * Lf.nx + ewrap(2 * I + qx, Lf.nx);
+          acc += wz * wy * wx * (t_local ? t[idx] : ld_cg(t + idx));
+        }
+      }
+    }
+    bc[(K * Lc.ny + J) * Lc.nx + I] = acc;
+  }
+}
+
+// v_f += P v_c on the local planes [z0-2, z1+2) of the fine view (halo included).
+template <typename T>
+__device__ void prolong_into(const View<T>& w, const EngLevel<T>& Lc, const T* vc, bool vc_local, int vc_z0) {
+  const EngLevel<T>& L = *w.L;
+  const int p0 = max(0, w.z0 - 2), p1 = min(L.nz, w.z1 + 2);
+  const int n = (p1 - p0) * w.plane;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int i = q % L.nx;
+    const int r = q / L.nx;
+    const int j = r % L.ny, k = p0 + r / L.ny;
+    int xi0 = i >> 1, xi1 = xi0;
+    T xw0 = (T)1, xw1 = (T)0;
+    if (i & 1) {
+      xi1 = ewrap(xi0 + 1, Lc.nx);
+      xw0 = xw1 = (T)0.5;
+    }
+    int yi0 = 0, yi1 = 0;
+    T yw0 = (T)1, yw1 = (T)0;
+    if (L.ny > 1) {
+      yi0 = yi1 = j >> 1;
+      if (j & 1) {
+        yi1 = ewrap(yi0 + 1, Lc.ny);
+        yw0 = yw1 = (T)0.5;
+      }
+    }
+    T acc = (T)0;
+    for (int qz = 0; qz < 2; ++qz) {
+      const int kc = __ldg(L.pz_idx + k * 2 + qz);
+      if (kc < 0) continue;
+      const T wz = __ldg(L.pz_w + k * 2 + qz);
+      const int yi[2] = {yi0, yi1}, xi[2] = {xi0, xi1};
+      const T yw[2] = {yw0, yw1}, xw[2] = {xw0, xw1};
+      for (int a = 0; a < 2; ++a) {
+        if (yw[a] == (T)0) continue;
+        for (int c = 0; c < 2; ++c) {
+          if (xw[c] == (T)0) continue;
+          const int idx = vc_local ? (((kc - vc_z0 + 2) * Lc.ny + yi[a]) * Lc.nx + xi[c])
+                                   : ((kc * Lc.ny + yi[a]) * Lc.nx + xi[c]);
+          acc += wz * yw[a] * xw[c] * (vc_local ? vc[idx] : ld_cg(vc + idx));
+        }
+      }
+    }
+    w.v[w.loc(i, j, k)] += acc;
+  }
+}
+
+template <typename T>
+__device__ void store_owned(const View<T>& w, T* g) {
+  const int n = (w.z1 - w.z0) * w.plane;
+  const int base = w.z0 * w.plane;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) g[base + q] = w.v[2 * w.plane + q];
+}
+
+template <typename T>
+__device__ void load_all(const View<T>& w, const T* g, T* dst) {
+  const int n = (w.z1 - w.z0) * w.plane;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) dst[q] = ld_cg(g + q);
+}
+
+// Exact coarsest step in CTA 0: v = L^-T (L^-1 b + noise n), FP64.
+template <typename T, bool NOISE>
+__device__ void coarsest_step(const View<T>& w, int level, const T* b, double* y, Key key, unsigned long long cyc) {
+  const EngLevel<T>& L = *w.L;
+  const int N = L.nx * L.ny * L.nz;
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q <= r; ++q) acc += L.Linv[(long long)r * N + q] * (double)b[q];
+    if (NOISE) {
+      const uint32_t c1 = (uint32_t)level | ((uint32_t)L.comp_id << 4) | (1u << 20);
+      double n4[4];
+      eng_normals(eng_philox10(make_uint4((uint32_t)(r >> 2), c1, (uint32_t)cyc, (uint32_t)(cyc >> 32)), key.k0,
+                               key.k1),
+                  n4);
+      acc += n4[r & 3];
+    }
+    y[r] = acc;
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < N; col += blockDim.x) {
+    double acc = 0.0;
+    for (int r = col; r < N; ++r) acc += L.Linv[(long long)r * N + col] * y[r];
+    const int i = col % L.nx, rr = col / L.nx;
+    w.v[w.loc(i, rr % L.ny, rr / L.ny)] = (T)acc;
+  }
+}
+
+template <typename T, bool NOISE>
+__device__ void sweeps(const View<T>& w, int level, int first_sweep, int count, const T* b, bool b_local, Key key,
+                       unsigned long long cyc, int rank, int csize, bool cluster) {
+  const Sync sync{cluster};
+  for (int s = 0; s < count; ++s)
+    for (int q = 0; q < w.L->ncol; ++q) {
+      colour_pass<T, NOISE>(w, level, q, first_sweep + s, b, b_local, key, cyc, rank, csize, cluster);
+      sync();
+    }
+}
+
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kEngThreads, 1) k_coarse_engine(EngParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int csize = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int comp = blockIdx.x / csize;
+  const EngComp<T>& E = p.comp[comp];
+  const unsigned long long cyc = *p.cyc;
+  const int lt = p.l0, lc = p.L - 1;
+
+  // ---- down leg ----
+  int l = lt;
+  for (; l < lc && E.lev[l].cluster; ++l) {
+    const EngLevel<T>& L = E.lev[l];
+    const EngLevel<T>& Lc = E.lev[l + 1];
+    View<T> w = make_view(L, smem, rank, true);
+    zero_local(w);
+    cl.sync();
+    sweeps<T, NOISE>(w, l, 0, p.mu1, L.gb, false, p.key, cyc, rank, csize, true);
+    residual(w, L.gb, false, L.gt);
+    cl.sync();
+    const int Z0 = Lc.cluster ? min(rank * Lc.P, Lc.nz) : (rank == 0 ? 0 : Lc.nz);
+    const int Z1 = Lc.cluster ? min(Z0 + Lc.P, Lc.nz) : (rank == 0 ? Lc.nz : Lc.nz);
+    restrict_to(L, Lc, L.gt, false, Lc.gb, Z0, Z1);
+    cl.sync();
+  }
+  const int lsingle = l;   // first level held by CTA 0 alone
+  if (rank == 0) {
+    // ---- single-CTA part: levels lsingle .. lc and back ----
+    {
+      const EngLevel<T>& L = E.lev[lsingle];
+      View<T> w = make_view(L, smem, 0, false);
+      load_all(w, L.gb, (T*)(smem + L.sb));
+      __syncthreads();
+    }
+    for (int k = lsingle; k <= lc; ++k) {
+      const EngLevel<T>& L = E.lev[k];
+      View<T> w = make_view(L, smem, 0, false);
+      T* b = (T*)(smem + L.sb);
+      zero_local(w);
+      __syncthreads();
+      if (k == lc && p.coarse_mode == SELM_COARSE_CHOLESKY) {
+        coarsest_step<T, NOISE>(w, k, b, (double*)(smem + p.y_off), p.key, cyc);
+        __syncthreads();
+        break;
+      }
+      sweeps<T, NOISE>(w, k, 0, p.mu1, b, true, p.key, cyc, 0, 1, false);
+      if (k == lc) {
+        sweeps<T, NOISE>(w, k, p.mu1, p.mu2, b, true, p.key, cyc, 0, 1, false);
+        break;
+      }
+      const EngLevel<T>& Lc = E.lev[k + 1];
+      residual(w, b, true, (T*)(smem + L.st));
+      __syncthreads();
+      restrict_to(L, Lc, (const T*)(smem + L.st), true, (T*)(smem + Lc.sb), 0, Lc.nz);
+      __syncthreads();
+    }
+    for (int k = lc - 1; k >= lsingle; --k) {
+      const EngLevel<T>& L = E.lev[k];
+      const EngLevel<T>& Lc = E.lev[k + 1];
+      View<T> w = make_view(L, smem, 0, false);
+      prolong_into(w, Lc, (const T*)(smem + Lc.sv), true, 0);
+      __syncthreads();
+      sweeps<T, NOISE>(w, k, p.mu1, p.mu2, (const T*)(smem + L.sb), true, p.key, cyc, 0, 1, false);
+    }
+    {
+      const EngLevel<T>& L = E.lev[lsingle];
+      View<T> w = make_view(L, smem, 0, false);
+      store_owned(w, L.gv);
+    }
+  }
+  cl.sync();
+  // ---- up leg over the cluster levels ----
+  for (int k = lsingle - 1; k >= lt; --k) {
+    const EngLevel<T>& L = E.lev[k];
+    const EngLevel<T>& Lc = E.lev[k + 1];
+    View<T> w = make_view(L, smem, rank, true);
+    prolong_into(w, Lc, Lc.gv, false, 0);
+    cl.sync();
+    sweeps<T, NOISE>(w, k, p.mu1, p.mu2, L.gb, false, p.key, cyc, rank, csize, true);
+    store_owned(w, L.gv);
+    cl.sync();
+  }
+}
+
+template <typename T>
+size_t level_bytes_cluster(const LevelDev& L, int c, int C) {
+  const CompDev& d = L.c[c];
+  const int P = (d.nz + C - 1) / C;
+  return (size_t)(P + 4) * d.nx * d.ny * sizeof(T);
+}
+
+inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <typename T>
+bool try_plan(const LevelDev* levs, int L, int l0, int C, size_t smem_cap, EnginePlanT<T>* out) {
+  // cluster levels first (largest), then single levels
+  const int ncomp = levs[0].ncomp;
+  size_t need_max = 0;
+  EngParams<T>& p = out->params;
+  p.l0 = l0;
+  p.L = L;
+  p.ncomp = ncomp;
+  bool any_cluster = false;
+  for (int c = 0; c < ncomp; ++c) {
+    size_t off = 0;
+    bool single_started = false;
+    for (int l = l0; l < L; ++l) {
+      const CompDev& d = levs[l].c[c];
+      EngLevel<T>& e = p.comp[c].lev[l];
+      const long long sites = (long long)d.nx * d.ny * d.nz;
+      const bool single = single_started || l == L - 1 || sites <= kEngSingleMaxSites || C == 1;
+      if (single) single_started = true;
+      e.cluster = single ? 0 : 1;
+      if (e.cluster) any_cluster = true;
+      e.P = single ? d.nz : (d.nz + C - 1) / C;
+      const size_t vbytes = (size_t)(e.P + 4) * d.nx * d.ny * sizeof(T);
+      e.sv = (int)off;
+      off = align16(off + vbytes);
+      if (single) {
+        e.sb = (int)off;
+        off = align16(off + (size_t)sites * sizeof(T));
+        e.st = (int)off;
+        off = align16(off + (size_t)sites * sizeof(T));
+      } else {
+        e.sb = e.st = -1;
+      }
+    }
+    const CompDev& dc = levs[L - 1].c[c];
+    const size_t Nc = (size_t)dc.nx * dc.ny * dc.nz;
+    if (Nc > 1024) return false;
+    out->y_off_comp[c] = off;
+    off = align16(off + Nc * sizeof(double));
+    need_max = need_max > off ? need_max : off;
+  }
+  if (need_max > smem_cap) return false;
+  if (!any_cluster) C = 1;
+  // every component gets the same y offset (the maximum) so that the kernel
+  // can use one field
+  size_t yo = 0;
+  for (int c = 0; c < ncomp; ++c) yo = yo > out->y_off_comp[c] ? yo : out->y_off_comp[c];
+  p.y_off = (int)yo;
+  size_t ymax = 0;
+  for (int c = 0; c < ncomp; ++c) {
+    const CompDev& dc = levs[L - 1].c[c];
+    const size_t Nc = (size_t)dc.nx * dc.ny * dc.nz;
+    ymax = ymax > Nc ? ymax : Nc;
+  }
+  out->smem_bytes = align16(yo + ymax * sizeof(double));
+  if (out->smem_bytes > smem_cap) return false;
+  out->cluster = C;
+  return true;
+}
+
+}  // namespace
+
+template <typename T>
+void fill_engine_tables(const LevelDev* levs, int L, void* const* gb, void* const* gv, void* const* gt,
+                        EnginePlanT<T>* plan) {
+  EngParams<T>& p = plan->params;
+  for (int c = 0; c < p.ncomp; ++c)
+    for (int l = p.l0; l < L; ++l) {
+      const CompDev& d = levs[l].c[c];
+      EngLevel<T>& e = p.comp[c].lev[l];
+      e.nx = d.nx;
+      e.ny = d.ny;
+      e.nz = d.nz;
+      e.mx = d.mx;
+      e.my = d.my;
+      e.mz = d.mz;
+      e.ncol = d.ncol;
+      e.comp_id = d.comp_id;
+      e.S = sizeof(T) == 4 ? (const T*)d.S32 : (const T*)d.S64;
+      e.rz_idx = d.rz_idx;
+      e.rz_w = sizeof(T) == 4 ? (const T*)d.rz_w32 : (const T*)d.rz_w64;
+      e.pz_idx = d.pz_idx;
+      e.pz_w = sizeof(T) == 4 ? (const T*)d.pz_w32 : (const T*)d.pz_w64;
+      e.Linv = d.Linv;
+      e.gb = (T*)gb[l] + d.off;
+      e.gv = (T*)gv[l] + d.off;
+      e.gt = (T*)gt[l] + d.off;
+    }
+}
+
+template <typename T>
+bool plan_coarse_engine(const LevelDev* levs, int L, void* const* gb, void* const* gv, void* const* gt,
+                        EnginePlanT<T>* plan) {
+  plan->valid = false;
+  if (L < 2) return false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  int cap = 0, cluster_ok = 0;
+  cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&cluster_ok, cudaDevAttrClusterLaunch, dev);
+  const size_t smem_cap = (size_t)cap > 2048 ? (size_t)cap - 1024 : 0;
+  const int sizes[5] = {16, 8, 4, 2, 1};
+  for (int l0 = 1; l0 < L; ++l0) {
+    for (int si = 0; si < 5; ++si) {
+      const int C = sizes[si];
+      if (C > 1 && !cluster_ok) continue;
+      EnginePlanT<T> cand{};
+      if (!try_plan<T>(levs, L, l0, C, smem_cap, &cand)) continue;
+      // check that the cluster shape can be scheduled
+      if (cand.cluster > 1) {
+        auto fn = k_coarse_engine<T, true>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cand.smem_bytes) != cudaSuccess ||
+            cudaFuncSetAttribute(k_coarse_engine<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cand.smem_bytes) != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        if (cand.cluster > 8) {
+          if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+              cudaFuncSetAttribute(k_coarse_engine<T, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                  cudaSuccess) {
+            cudaGetLastError();
+            continue;
+          }
+        }
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(cand.cluster * levs[0].ncomp);
+        cfg.blockDim = dim3(kEngThreads);
+        cfg.dynamicSmemBytes = cand.smem_bytes;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cand.cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
+          cudaGetLastError();
+          continue;
+        }
+      } else {
+        if (cudaFuncSetAttribute(k_coarse_engine<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cand.smem_bytes) != cudaSuccess ||
+            cudaFuncSetAttribute(k_coarse_engine<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cand.smem_bytes) != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+      }
+      *plan = cand;
+      fill_engine_tables<T>(levs, L, gb, gv, gt, plan);
+      plan->valid = true;
+      return true;
+    }
+  }
+  return false;
+}
+
+template <typename T>
+cudaError_t launch_coarse_engine(const EnginePlanT<T>& plan, int mu1, int mu2, int coarse_mode, bool noise, Key key,
+                                 const unsigned long long* cyc, cudaStream_t st) {
+  EngParams<T> p = plan.params;
+  p.mu1 = mu1;
+  p.mu2 = mu2;
+  p.coarse_mode = coarse_mode;
+  p.key = key;
+  p.cyc = cyc;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(plan.cluster * p.ncomp);
+  cfg.blockDim = dim3(kEngThreads);
+  cfg.dynamicSmemBytes = plan.smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = plan.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  prof::Scope ps(SELM_K_COARSE_SWEEP, st);
+  if (noise) return cudaLaunchKernelEx(&cfg, k_coarse_engine<T, true>, p);
+  return cudaLaunchKernelEx(&cfg, k_coarse_engine<T, false>, p);
+}
+
+template bool plan_coarse_engine<float>(const LevelDev*, int, void* const*, void* const*, void* const*,
+                                        EnginePlanT<float>*);
+template bool plan_coarse_engine<double>(const LevelDev*, int, void* const*, void* const*, void* const*,
+                                         EnginePlanT<double>*);
+template cudaError_t launch_coarse_engine<float>(const EnginePlanT<float>&, int, int, int, bool, Key,
+                                                 const unsigned long long*, cudaStream_t);
+template cudaError_t launch_coarse_engine<double>(const EnginePlanT<double>&, int, int, int, bool, Key,
+                                                  const unsigned long long*, cudaStream_t);
+
+}  // namespace selm

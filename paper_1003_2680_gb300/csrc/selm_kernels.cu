@@ -15,12 +15,79 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
+#include <vector>
 
+#include "../../include/selm_mg.h"
 #include "selm_internal.h"
 #include "selm_launch.h"
+#include "selm_prof.h"
 
 namespace selm {
+
+// ---------------------------------------------------------------------------
+// Kernel accounting: a launch counter and optional event timing per kernel
+// class (events recorded on the launching stream).
+// ---------------------------------------------------------------------------
+namespace prof {
+std::atomic<long long> g_launches{0};
+std::mutex g_mu;
+bool g_on = false;
+std::vector<cudaEvent_t> g_pool;
+struct Pending {
+  int kind;
+  cudaEvent_t a, b;
+};
+std::vector<Pending> g_pending;
+double g_ms[SELM_K_NCLASSES] = {};
+long long g_count[SELM_K_NCLASSES] = {};
+
+cudaEvent_t take_event() {
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void drain() {
+  for (auto& p : g_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      g_ms[p.kind] += ms;
+      g_count[p.kind] += 1;
+    }
+    g_pool.push_back(p.a);
+    g_pool.push_back(p.b);
+  }
+  g_pending.clear();
+}
+
+Scope::Scope(int k, cudaStream_t s) : kind(k), st(s), a(nullptr) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (g_on) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    a = take_event();
+    if (a) cudaEventRecord(a, st);
+  }
+}
+
+Scope::~Scope() {
+  if (!a) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaEvent_t b = take_event();
+  if (!b) return;
+  cudaEventRecord(b, st);
+  g_pending.push_back({kind, a, b});
+  if (g_pending.size() > 4096) drain();
+}
+}  // namespace prof
+
 namespace {
 
 constexpr int kBlock = 256;
@@ -231,6 +298,232 @@ __global__ void __launch_bounds__(kBlock) k_fine_colour(LevelDev L, ColourPass c
   }
 }
 
+__device__ __forceinline__ double block_sum(double x) {
+  __shared__ double red[kBlock / 32];
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = x;
+  __syncthreads();
+  x = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Level 0, red-black, vectorised: one thread owns the 8 consecutive x
+// positions [8g, 8g+8) of one row (requires nx % 8 == 0).  These hold exactly
+// the four sites of colour `colour` of one noise group (ranks 4g'..4g'+3 of
+// the class), so one Philox call serves the thread.  Centre, y+-1, z+-1 and b
+// rows are read with 16-byte vector loads; the x neighbours at the segment
+// ends are scalar loads.  The whole segment is written back: its
+// other-colour entries are unchanged and are the only entries other threads
+// read during this pass.
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  __device__ static void load8(const float* p, float o[8]) {
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+  }
+  __device__ static void store8(float* p, const float o[8]) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<float4*>(p + 4) = make_float4(o[4], o[5], o[6], o[7]);
+  }
+};
+template <>
+struct Vec<double> {
+  __device__ static void load8(const double* p, double o[8]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double2 a = *reinterpret_cast<const double2*>(p + 2 * q);
+      o[2 * q] = a.x;
+      o[2 * q + 1] = a.y;
+    }
+  }
+  __device__ static void store8(double* p, const double o[8]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) *reinterpret_cast<double2*>(p + 2 * q) = make_double2(o[2 * q], o[2 * q + 1]);
+  }
+};
+
+// Updates the four sites of parity P in an 8-wide segment (compile-time
+// indices keep the arrays in registers).
+template <typename T, bool NOISE, int P>
+__device__ __forceinline__ void fine_update8(T cen[8], const T bb[8], const T acc[8], T left, T right, const T n4[4],
+                                             T s, T diag, T rsd) {
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const int e = 2 * l + P;
+    const T xl = e == 0 ? left : cen[e - 1];
+    const T xr = e == 7 ? right : cen[e + 1];
+    T nv = (bb[e] + s * (acc[e] + xl + xr)) / diag;
+    if (NOISE) nv += n4[l] * rsd;
+    cen[e] = nv;
+  }
+}
+
+struct RowPass {
+  int rstart[kMaxComps + 1];   // first row of each component (rows = ny * nz)
+};
+
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kBlock) k_fine_colour_v8(LevelDev L, RowPass rp, T* __restrict__ v,
+                                                          const T* __restrict__ b, int colour, int sweep, Key key,
+                                                          const unsigned long long* __restrict__ cyc) {
+  const int segs = L.c[0].nx >> 3;   // every component has the same nx
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row_all = gt / segs;
+  if (row_all >= rp.rstart[L.ncomp]) return;
+  const int seg = gt - row_all * segs;
+  int ci = 0;
+  while (ci + 1 < L.ncomp && row_all >= rp.rstart[ci + 1]) ++ci;
+  const CompDev& c = L.c[ci];
+  const int row = row_all - rp.rstart[ci];
+  const int j = row % c.ny, k = row / c.ny;
+  const int nx = c.nx;
+  const long long plane = (long long)nx * c.ny;
+  const long long rbase = c.off + (long long)row * nx;
+  const int x0 = seg << 3;
+  T cen[8], bb[8], acc[8];
+  Vec<T>::load8(v + rbase + x0, cen);
+  Vec<T>::load8(b + rbase + x0, bb);
+  const T left = v[rbase + (x0 == 0 ? nx - 1 : x0 - 1)];
+  const T right = v[rbase + (x0 + 8 == nx ? 0 : x0 + 8)];
+  const int p = (j + k + colour) & 1;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) acc[e] = (T)0;
+  if (c.ny > 1) {
+    T t[8];
+    const long long ym = c.off + ((long long)k * c.ny + (j == 0 ? c.ny - 1 : j - 1)) * nx + x0;
+    const long long yp = c.off + ((long long)k * c.ny + (j == c.ny - 1 ? 0 : j + 1)) * nx + x0;
+    Vec<T>::load8(v + ym, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] += t[e];
+    Vec<T>::load8(v + yp, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] += t[e];
+  }
+  if (k > 0) {
+    T t[8];
+    Vec<T>::load8(v + rbase - plane + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] += t[e];
+  }
+  if (k < c.nz - 1) {
+    T t[8];
+    Vec<T>::load8(v + rbase + plane + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] += t[e];
+  }
+  T n4[4] = {(T)0, (T)0, (T)0, (T)0};
+  if (NOISE) {
+    const unsigned long long cy = *cyc;
+    const uint32_t grp = (uint32_t)row * (uint32_t)(nx >> 3) + (uint32_t)seg;
+    Normals<T>::get(philox10(make_uint4(grp, ctr1_of(L.level, c.comp_id, colour, sweep, 0), (uint32_t)cy,
+                                        (uint32_t)(cy >> 32)),
+                             key.k0, key.k1),
+                    n4);
+  }
+  const int edges = (k == 0) + (k == c.nz - 1);
+  T dz = (T)2;
+  if (c.zkind == kAxisCellDir) dz += (T)edges;
+  if (c.zkind == kAxisCellNeu) dz -= (T)edges;
+  const T s = (T)c.s;
+  const T diag = s * ((c.ny > 1 ? (T)4 : (T)2) + dz);
+  const T rsd = NOISE ? (T)1 / sqrt(diag) : (T)0;
+  if (p == 0)
+    fine_update8<T, NOISE, 0>(cen, bb, acc, left, right, n4, s, diag, rsd);
+  else
+    fine_update8<T, NOISE, 1>(cen, bb, acc, left, right, n4, s, diag, rsd);
+  Vec<T>::store8(v + rbase + x0, cen);
+}
+
+// FP64 outer residual, vectorised over 4 consecutive x positions (nx % 4 == 0).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_outer_residual_v4(LevelDev L, RowPass rp, const double* __restrict__ z,
+                                                             const double* __restrict__ b, T* __restrict__ r,
+                                                             double* __restrict__ norm2) {
+  const int segs = L.c[0].nx >> 2;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row_all = gt / segs;
+  double rr = 0.0;
+  if (row_all < rp.rstart[L.ncomp]) {
+    const int seg = gt - row_all * segs;
+    int ci = 0;
+    while (ci + 1 < L.ncomp && row_all >= rp.rstart[ci + 1]) ++ci;
+    const CompDev& c = L.c[ci];
+    const int row = row_all - rp.rstart[ci];
+    const int j = row % c.ny, k = row / c.ny;
+    const int nx = c.nx;
+    const long long plane = (long long)nx * c.ny;
+    const long long rbase = c.off + (long long)row * nx;
+    const int x0 = seg << 2;
+    double cen[4], acc[4];
+    {
+      const double2 a = *reinterpret_cast<const double2*>(z + rbase + x0);
+      const double2 d = *reinterpret_cast<const double2*>(z + rbase + x0 + 2);
+      cen[0] = a.x; cen[1] = a.y; cen[2] = d.x; cen[3] = d.y;
+    }
+    const double left = z[rbase + (x0 == 0 ? nx - 1 : x0 - 1)];
+    const double right = z[rbase + (x0 + 4 == nx ? 0 : x0 + 4)];
+    acc[0] = left + cen[1];
+    acc[1] = cen[0] + cen[2];
+    acc[2] = cen[1] + cen[3];
+    acc[3] = cen[2] + right;
+    auto add4 = [&](long long off) {
+      const double2 a = *reinterpret_cast<const double2*>(z + off);
+      const double2 d = *reinterpret_cast<const double2*>(z + off + 2);
+      acc[0] += a.x; acc[1] += a.y; acc[2] += d.x; acc[3] += d.y;
+    };
+    if (c.ny > 1) {
+      add4(c.off + ((long long)k * c.ny + (j == 0 ? c.ny - 1 : j - 1)) * nx + x0);
+      add4(c.off + ((long long)k * c.ny + (j == c.ny - 1 ? 0 : j + 1)) * nx + x0);
+    }
+    if (k > 0) add4(rbase - plane + x0);
+    if (k < c.nz - 1) add4(rbase + plane + x0);
+    const int edges = (k == 0) + (k == c.nz - 1);
+    double dz = 2.0;
+    if (c.zkind == kAxisCellDir) dz += (double)edges;
+    if (c.zkind == kAxisCellNeu) dz -= (double)edges;
+    const double dg = (c.ny > 1 ? 4.0 : 2.0) + dz;
+    double bv[4] = {0.0, 0.0, 0.0, 0.0};
+    if (b) {
+      const double2 a = *reinterpret_cast<const double2*>(b + rbase + x0);
+      const double2 d = *reinterpret_cast<const double2*>(b + rbase + x0 + 2);
+      bv[0] = a.x; bv[1] = a.y; bv[2] = d.x; bv[3] = d.y;
+    }
+    T out[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const double res = bv[e] - c.s * (dg * cen[e] - acc[e]);
+      out[e] = (T)res;
+      rr += res * res;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) r[rbase + x0 + e] = out[e];
+  }
+  if (norm2) {
+    rr = block_sum(rr);
+    if (threadIdx.x == 0) atomicAdd(norm2, rr);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_outer_update_v4(long long n4, double* __restrict__ z,
+                                                           const T* __restrict__ d) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n4) return;
+  double2 a = *reinterpret_cast<double2*>(z + 4 * q);
+  double2 c = *reinterpret_cast<double2*>(z + 4 * q + 2);
+  a.x += (double)d[4 * q];
+  a.y += (double)d[4 * q + 1];
+  c.x += (double)d[4 * q + 2];
+  c.y += (double)d[4 * q + 3];
+  *reinterpret_cast<double2*>(z + 4 * q) = a;
+  *reinterpret_cast<double2*>(z + 4 * q + 2) = c;
+}
+
 // Galerkin levels: colour = (i mod mx, j mod my, k mod mz); ranks row-major
 // within the class; four ranks per thread.
 template <typename T, bool NOISE>
@@ -269,15 +562,17 @@ __global__ void __launch_bounds__(kBlock) k_coarse_colour(LevelDev L, ColourPass
 // ---------------------------------------------------------------------------
 // Residual, restriction, prolongation
 // ---------------------------------------------------------------------------
+// Level fields are below 2^31 elements (checked at create), so the site
+// decomposition uses 32-bit arithmetic.
 __device__ __forceinline__ void site_of(const LevelDev& L, long long s, int* ci, int* i, int* j, int* k) {
   int c = 0;
   while (c + 1 < L.ncomp && s >= L.c[c + 1].off) ++c;
   const CompDev& cd = L.c[c];
-  const long long loc = s - cd.off;
-  *i = (int)(loc % cd.nx);
-  const long long t = loc / cd.nx;
-  *j = (int)(t % cd.ny);
-  *k = (int)(t / cd.ny);
+  const unsigned loc = (unsigned)(s - cd.off);
+  const unsigned t = loc / (unsigned)cd.nx;
+  *i = (int)(loc - t * (unsigned)cd.nx);
+  *j = (int)(t % (unsigned)cd.ny);
+  *k = (int)(t / (unsigned)cd.ny);
   *ci = c;
 }
 
@@ -426,17 +721,6 @@ __global__ void k_coarsest(LevelDev L, T* __restrict__ v, const T* __restrict__ 
 // ---------------------------------------------------------------------------
 // FP64 outer iteration (Algorithm 1 steps 1 and 4)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double block_sum(double x) {
-  __shared__ double red[kBlock / 32];
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[w] = x;
-  __syncthreads();
-  x = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.0;
-  if (w == 0)
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-  return x;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_outer_residual(LevelDev L, const double* __restrict__ z,
@@ -684,6 +968,24 @@ inline unsigned grid_for(long long n, int block = kBlock) { return (unsigned)((n
 template <typename T>
 cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool noise, Key key,
                           const unsigned long long* cyc, cudaStream_t st) {
+  if (L.level == 0 && L.c[0].nx % 8 == 0) {
+    RowPass rp{};
+    int rows = 0;
+    for (int ci = 0; ci < L.ncomp; ++ci) {
+      rp.rstart[ci] = rows;
+      rows += L.c[ci].ny * L.c[ci].nz;
+    }
+    rp.rstart[L.ncomp] = rows;
+    const long long nt = (long long)rows * (L.c[0].nx >> 3);
+    for (int colour = 0; colour < 2; ++colour) {
+      prof::Scope ps(SELM_K_FINE_SWEEP, st);
+      if (noise)
+        k_fine_colour_v8<T, true><<<grid_for(nt), kBlock, 0, st>>>(L, rp, v, b, colour, sweep, key, cyc);
+      else
+        k_fine_colour_v8<T, false><<<grid_for(nt), kBlock, 0, st>>>(L, rp, v, b, colour, sweep, key, cyc);
+    }
+    return cudaGetLastError();
+  }
   if (L.level == 0) {
     for (int colour = 0; colour < 2; ++colour) {
       ColourPass cp{};
@@ -695,6 +997,7 @@ cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool n
         gs += (cp.nsites[ci] + 3) / 4;
       }
       cp.gstart[L.ncomp] = gs;
+      prof::Scope ps(SELM_K_FINE_SWEEP, st);
       if (noise)
         k_fine_colour<T, true><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
       else
@@ -729,6 +1032,7 @@ cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool n
     }
     cp.gstart[L.ncomp] = gs;
     if (gs == 0) continue;
+    prof::Scope ps(SELM_K_COARSE_SWEEP, st);
     if (noise)
       k_coarse_colour<T, true><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, sweep, key, cyc);
     else
@@ -739,18 +1043,21 @@ cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool n
 
 template <typename T>
 cudaError_t launch_residual(const LevelDev& L, const T* v, const T* b, T* t, cudaStream_t st) {
+  prof::Scope ps(SELM_K_RESIDUAL, st);
   k_residual<T><<<grid_for(L.size), kBlock, 0, st>>>(L, v, b, t);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* t, T* bc, cudaStream_t st) {
+  prof::Scope ps(SELM_K_RESTRICT, st);
   k_restrict<T><<<grid_for(Lc.size), kBlock, 0, st>>>(Lf, Lc, t, bc);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_prolong(const LevelDev& Lf, const LevelDev& Lc, T* v, const T* vc, cudaStream_t st) {
+  prof::Scope ps(SELM_K_PROLONG, st);
   k_prolong<T><<<grid_for(Lf.size), kBlock, 0, st>>>(Lf, Lc, v, vc);
   return cudaGetLastError();
 }
@@ -764,6 +1071,7 @@ cudaError_t launch_coarsest(const LevelDev& L, T* v, const T* b, bool noise, Key
     nmax = N > nmax ? N : nmax;
   }
   const size_t smem = 2 * (size_t)nmax * sizeof(double);
+  prof::Scope ps(SELM_K_COARSEST, st);
   if (noise)
     k_coarsest<T, true><<<L.ncomp, 256, smem, st>>>(L, v, b, key, cyc);
   else
@@ -774,12 +1082,30 @@ cudaError_t launch_coarsest(const LevelDev& L, T* v, const T* b, bool noise, Key
 template <typename T>
 cudaError_t launch_outer_residual(const LevelDev& L0, const double* z, const double* b, T* r, double* norm2,
                                   cudaStream_t st) {
+  prof::Scope ps(SELM_K_OUTER_RESIDUAL, st);
+  if (L0.c[0].nx % 4 == 0) {
+    RowPass rp{};
+    int rows = 0;
+    for (int ci = 0; ci < L0.ncomp; ++ci) {
+      rp.rstart[ci] = rows;
+      rows += L0.c[ci].ny * L0.c[ci].nz;
+    }
+    rp.rstart[L0.ncomp] = rows;
+    const long long nt = (long long)rows * (L0.c[0].nx >> 2);
+    k_outer_residual_v4<T><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
+    return cudaGetLastError();
+  }
   k_outer_residual<T><<<grid_for(L0.size), kBlock, 0, st>>>(L0, z, b, r, norm2);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_outer_update(long long n, double* z, const T* d, cudaStream_t st) {
+  prof::Scope ps(SELM_K_OUTER_UPDATE, st);
+  if (n % 4 == 0) {
+    k_outer_update_v4<T><<<grid_for(n / 4), kBlock, 0, st>>>(n / 4, z, d);
+    return cudaGetLastError();
+  }
   k_outer_update<T><<<grid_for(n), kBlock, 0, st>>>(n, z, d);
   return cudaGetLastError();
 }
@@ -788,22 +1114,26 @@ cudaError_t launch_norm2(long long n, const double* x, double* out, cudaStream_t
   long long blocks = grid_for(n);
   if (blocks > 4 * 152) blocks = 4 * 152;
   if (blocks < 1) blocks = 1;
+  prof::Scope ps(SELM_K_OTHER, st);
   k_norm2<<<(unsigned)blocks, kBlock, 0, st>>>(n, x, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpby(long long n, double a, const double* x, double c, const double* y, double* out,
                          cudaStream_t st) {
+  prof::Scope ps(SELM_K_OTHER, st);
   k_axpby<<<grid_for(n), kBlock, 0, st>>>(n, a, x, c, y, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st) {
+  prof::Scope ps(SELM_K_OTHER, st);
   k_set_u64<<<1, 1, 0, st>>>(p, v);
   return cudaGetLastError();
 }
 
 cudaError_t launch_inc_u64(unsigned long long* p, cudaStream_t st) {
+  prof::Scope ps(SELM_K_OTHER, st);
   k_inc_u64<<<1, 1, 0, st>>>(p);
   return cudaGetLastError();
 }
@@ -812,6 +1142,7 @@ cudaError_t launch_spread(const LevelDev& L0, int n, int dim, int np, const doub
                           cudaStream_t st) {
   if (np <= 0) return cudaSuccess;
   const long long nt = (long long)np * L0.ncomp * (dim == 3 ? 64 : 16);
+  prof::Scope ps(SELM_K_SPREAD, st);
   k_spread<<<grid_for(nt), kBlock, 0, st>>>(L0, n, dim, np, X, F, b);
   return cudaGetLastError();
 }
@@ -820,34 +1151,40 @@ cudaError_t launch_interp(const LevelDev& L0, int n, int dim, int np, const doub
                           cudaStream_t st) {
   if (np <= 0) return cudaSuccess;
   const long long nt = (long long)np * L0.ncomp * 32;
+  prof::Scope ps(SELM_K_INTERP, st);
   k_interp<<<grid_for(nt), kBlock, 0, st>>>(L0, n, dim, np, X, u, U);
   return cudaGetLastError();
 }
 
 cudaError_t launch_em(int np, int dim, double* X, const double* V, cudaStream_t st) {
   if (np <= 0) return cudaSuccess;
+  prof::Scope ps(SELM_K_OTHER, st);
   k_em<<<grid_for(np), kBlock, 0, st>>>(np, dim, X, V);
   return cudaGetLastError();
 }
 
 cudaError_t launch_divergence(const LevelDev& Lv, const double* w, double* div, double* sum, cudaStream_t st) {
   const long long N = (long long)Lv.c[0].nx * Lv.c[0].ny * Lv.c[0].nz;
+  prof::Scope ps(SELM_K_PROJECTION, st);
   k_divergence<<<grid_for(N), kBlock, 0, st>>>(Lv, w, div, sum);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sub_mean(long long n, double* x, const double* sum, cudaStream_t st) {
+  prof::Scope ps(SELM_K_PROJECTION, st);
   k_sub_mean<<<grid_for(n), kBlock, 0, st>>>(n, x, sum);
   return cudaGetLastError();
 }
 
 cudaError_t launch_grad_sub(const LevelDev& Lv, double* w, const double* phi, cudaStream_t st) {
+  prof::Scope ps(SELM_K_PROJECTION, st);
   k_grad_sub<<<grid_for(Lv.size), kBlock, 0, st>>>(Lv, w, phi);
   return cudaGetLastError();
 }
 
 cudaError_t launch_philox(const uint32_t* ctr, Key key, uint32_t* out, int n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  prof::Scope ps(SELM_K_OTHER, st);
   k_philox<<<grid_for(n), kBlock, 0, st>>>(ctr, key, out, n);
   return cudaGetLastError();
 }
@@ -868,3 +1205,34 @@ SELM_INSTANTIATE(float)
 SELM_INSTANTIATE(double)
 
 }  // namespace selm
+
+extern "C" {
+
+long long selm_kernel_launches(void) { return selm::prof::g_launches.load(); }
+
+selm_status selm_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(selm::prof::g_mu);
+  selm::prof::g_on = on != 0;
+  return SELM_OK;
+}
+
+selm_status selm_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(selm::prof::g_mu);
+  selm::prof::drain();
+  for (int k = 0; k < SELM_K_NCLASSES; ++k) {
+    selm::prof::g_ms[k] = 0.0;
+    selm::prof::g_count[k] = 0;
+  }
+  return SELM_OK;
+}
+
+selm_status selm_profile_read(int kernel_class, double* total_ms, long long* launches) {
+  if (kernel_class < 0 || kernel_class >= SELM_K_NCLASSES) return SELM_EINVAL;
+  std::lock_guard<std::mutex> lk(selm::prof::g_mu);
+  selm::prof::drain();
+  if (total_ms) *total_ms = selm::prof::g_ms[kernel_class];
+  if (launches) *launches = selm::prof::g_count[kernel_class];
+  return SELM_OK;
+}
+
+}  // extern "C"

@@ -18,6 +18,7 @@ SELM_FP64, SELM_FP32_REFINE64 = 0, 1
 SELM_PROJ_NONE, SELM_PROJ_MAC = 0, 1
 SELM_COARSE_CHOLESKY, SELM_COARSE_SMOOTH = 0, 1
 SELM_SYS_VELOCITY, SELM_SYS_PRESSURE = 0, 1
+SELM_OPT_COARSE_ENGINE = 1
 
 _STATUS = {0: "SELM_OK", 1: "SELM_EINVAL", 2: "SELM_ENOMEM", 3: "SELM_ECUDA", 4: "SELM_ENOCONV",
            5: "SELM_ETIMEOUT", 6: "SELM_EBUSY"}
@@ -58,6 +59,7 @@ _SIGS = {
     "selm_mg_solve": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
     "selm_mg_sample": (_I, [_P, _I, _P, _I, _P, _P, _P]),
     "selm_mg_step": (_I, [_P, _I, _P, _P, _D, _I, _I, _P]),
+    "selm_mg_step_host": (_I, [_P, _I, _P, _P, _D, _I, _I, _P]),
     "selm_mg_levels": (_I, [_P, _I]),
     "selm_mg_ncomp": (_I, [_P, _I]),
     "selm_mg_layout": (_I, [_P, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
@@ -65,6 +67,8 @@ _SIGS = {
     "selm_mg_chain": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_U64)]),
     "selm_mg_set_cycle": (_I, [_P, _U64]),
     "selm_mg_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_LL)]),
+    "selm_mg_set_option": (_I, [_P, _I, _I]),
+    "selm_mg_engine_info": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
     "selm_mg_smooth": (_I, [_P, _I, _I, _P, _P, _I, _U64, _I, _P]),
     "selm_mg_residual_restrict": (_I, [_P, _I, _I, _P, _P, _P, _P]),
     "selm_mg_prolong_correct": (_I, [_P, _I, _I, _P, _P, _P]),
@@ -79,7 +83,14 @@ _SIGS = {
     "selm_mg_project": (_I, [_P, _P, ctypes.POINTER(_I), _P]),
     "selm_mg_em_update": (_I, [_P, _I, _P, _P, _P]),
     "selm_philox4x32_10": (_I, [_P, ctypes.c_uint32, ctypes.c_uint32, _P, _I, _P]),
+    "selm_kernel_launches": (ctypes.c_longlong, []),
+    "selm_profile_enable": (_I, [_I]),
+    "selm_profile_reset": (_I, []),
+    "selm_profile_read": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_LL)]),
 }
+
+KERNEL_CLASSES = ["fine_sweep", "coarse_sweep", "residual", "restrict", "prolong", "coarsest",
+                  "outer_residual", "outer_update", "spread", "interp", "projection", "other"]
 
 
 def library_path():
@@ -185,6 +196,31 @@ def selm_mg_step(h, X, F, dt, nsteps, ncycles_per_step, stream=None):
     _check(h, lib().selm_mg_step(h, X.shape[0], _ptr(X), _ptr(F), dt, nsteps, ncycles_per_step, _stream(stream)))
 
 
+def selm_mg_step_host(h, X_host, F_host, dt, nsteps, ncycles_per_step, stream=None):
+    """X_host, F_host: CPU float64 tensors [np][dim] (pinned for async copies)."""
+    assert not X_host.is_cuda and not F_host.is_cuda and X_host.is_contiguous() and F_host.is_contiguous()
+    _check(h, lib().selm_mg_step_host(h, X_host.shape[0], X_host.data_ptr(), F_host.data_ptr(), dt, nsteps,
+                                      ncycles_per_step, _stream(stream)))
+
+
+def selm_kernel_launches():
+    return lib().selm_kernel_launches()
+
+
+def selm_profile_enable(on):
+    _check(None, lib().selm_profile_enable(int(on)))
+
+
+def selm_profile_reset():
+    _check(None, lib().selm_profile_reset())
+
+
+def selm_profile_read(kernel_class):
+    ms, cnt = _D(0.0), _LL(0)
+    _check(None, lib().selm_profile_read(kernel_class, ctypes.byref(ms), ctypes.byref(cnt)))
+    return ms.value, cnt.value
+
+
 def selm_mg_levels(h, system=SELM_SYS_VELOCITY):
     return lib().selm_mg_levels(h, system)
 
@@ -218,6 +254,16 @@ def selm_mg_stats(h):
     a, b, c = _I(0), _I(0), _LL(0)
     _check(h, lib().selm_mg_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def selm_mg_set_option(h, option, value):
+    _check(h, lib().selm_mg_set_option(h, option, int(value)))
+
+
+def selm_mg_engine_info(h, system=SELM_SYS_VELOCITY):
+    l0, c, sm = _I(0), _I(0), ctypes.c_size_t(0)
+    _check(h, lib().selm_mg_engine_info(h, system, ctypes.byref(l0), ctypes.byref(c), ctypes.byref(sm)))
+    return l0.value, c.value, sm.value
 
 
 def selm_mg_smooth(h, system, level, v, b, sweep, cycle, noise, stream=None):

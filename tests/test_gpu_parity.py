@@ -146,6 +146,32 @@ def test_fac_cycle(prec, dim, n, levels, noise, mode):
     assert rel(from_dev(m.h, z), want) < tol
 
 
+# grids whose first Galerkin level exceeds one CTA: the coarse engine runs
+# z-slabs over a thread-block cluster with DSMEM halo exchange
+ENGINE_GRIDS = [(3, 48, 4), (3, 64, 4), (2, 256, 7)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim,n,levels", ENGINE_GRIDS + [(2, 64, 6), (3, 32, 4)])
+@pytest.mark.parametrize("noise", [0, 1])
+@pytest.mark.parametrize("engine", [1, 0])
+def test_vcycle_engine_and_per_pass_paths(prec, dim, n, levels, noise, engine):
+    m, osys, dt, tol = make(dim, n, levels, prec)
+    S.selm_mg_set_option(m.h, S.SELM_OPT_COARSE_ENGINE, engine)
+    l0, csize, smem = S.selm_mg_engine_info(m.h)
+    assert l0 == 1 and csize >= 1 and smem > 0
+    if (dim, n) in [(3, 48), (3, 64), (2, 256)]:
+        assert csize > 1, "expected the cluster path on this grid"
+    shapes = osys.shapes(0)
+    v0 = round_like(selm_inputs.fields(shapes, seed=31), dt)
+    b0 = round_like(selm_inputs.fields(shapes, seed=32), dt)
+    v = to_dev(m.h, v0, dt)
+    S.selm_mg_vcycle(m.h, 0, v, to_dev(m.h, b0, dt), cycle=41, noise=noise)
+    want = [x.copy() for x in v0]
+    multigrid.vcycle(osys, 0, want, b0, philox.PhiloxNoise(11, 3, 41), float(noise))
+    assert rel(from_dev(m.h, v), want) < tol
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("dim,n,levels", GRIDS)
 def test_fac_solve(prec, dim, n, levels):

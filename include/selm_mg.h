@@ -70,7 +70,7 @@ typedef struct {
   int coarse_mode;         /* SELM_COARSE_CHOLESKY (exact block step) or SELM_COARSE_SMOOTH (Alg. 3 literally) */
   double tol;              /* FAC stop: ||b - Az||_2 <= tol ||b||_2 ; 0 -> 1e-10 */
   int max_cycles;          /* FAC cycle cap; 0 -> 100 */
-  double proj_tol;         /* pressure-solve tolerance of the projection; 0 -> 1e-12 */
+  double proj_tol;         /* pressure-solve tolerance of the projection; 0 -> 1e-10 */
   int max_particles;       /* capacity of the particle scratch of selm_mg_step; 0 -> 4096 */
   uint64_t seed;           /* Philox key material (noise of this chain) */
   uint64_t instance;       /* Philox key material (distinguishes systems) */

@@ -95,7 +95,7 @@ void fill_desc_defaults(selm_mg_desc* d) {
   if (d->nu_post == 0) d->nu_post = 2;
   if (d->tol == 0.0) d->tol = 1e-10;
   if (d->max_cycles == 0) d->max_cycles = 100;
-  if (d->proj_tol == 0.0) d->proj_tol = 1e-12;
+  if (d->proj_tol == 0.0) d->proj_tol = 1e-10;
   if (d->max_particles == 0) d->max_particles = 4096;
 }
 
@@ -135,7 +135,7 @@ std::string build_systems(const selm_mg_desc& d, Sys* vel, Sys* pres, bool* has_
 }
 
 struct TableOffsets {
-  size_t S64, S32, rzw64, rzw32, pzw64, pzw32, rzi, pzi, Linv;
+  size_t S64, S32, rzw64, rzw32, pzw64, pzw32, rzi, pzi, Linv, zb64, zb32;
 };
 
 // Workspace plan: tables + fields.  When `base` is null only sizes are computed.
@@ -148,7 +148,7 @@ struct Plan {
   std::vector<TableOffsets> toff[2][kMaxLevels];
   size_t field_off[2][kMaxLevels][3];
   size_t u_off = 0, xi_off = 0, bvel_off = 0, wcomb_off = 0, phi_off = 0, prhs_off = 0, red_off = 0,
-         cyc_off = 0, V_off = 0, Xs_off = 0, Fs_off = 0;
+         cyc_off = 0, V_off = 0, Xs_off = 0, Fs_off = 0, eng_off[2] = {0, 0};
 };
 
 void plan_tables(const HostSystem& hs, int si, Plan* p) {
@@ -174,6 +174,10 @@ void plan_tables(const HostSystem& hs, int si, Plan* p) {
       p->ints.insert(p->ints.end(), c.pz_idx.begin(), c.pz_idx.end());
       t.Linv = p->dbl.size();
       p->dbl.insert(p->dbl.end(), c.Linv.begin(), c.Linv.end());
+      t.zb64 = p->dbl.size();
+      p->dbl.insert(p->dbl.end(), c.zb.begin(), c.zb.end());
+      t.zb32 = p->flt.size();
+      for (double x : c.zb) p->flt.push_back((float)x);
       p->toff[si][l].push_back(t);
     }
   }
@@ -201,6 +205,8 @@ void make_plan(const selm_mg_desc& d, const Sys& vel, const Sys* pres, int esize
     p->phi_off = p->lay.add(np_ * 8);
     p->prhs_off = p->lay.add(np_ * 8);
   }
+  p->eng_off[0] = p->lay.add(kEngParamBytes);
+  if (pres) p->eng_off[1] = p->lay.add(kEngParamBytes);
   p->red_off = p->lay.add(16 * sizeof(double));
   p->cyc_off = p->lay.add(4 * sizeof(unsigned long long));
   p->V_off = p->lay.add((size_t)d.max_particles * 3 * sizeof(double));
@@ -246,6 +252,12 @@ void bind_system(Sys* s, int si, const Plan& p, char* ws) {
       c.rz_idx = hc.rz_idx.empty() ? nullptr : ints + t.rzi;
       c.pz_idx = hc.pz_idx.empty() ? nullptr : ints + t.pzi;
       c.Linv = hc.Linv.empty() ? nullptr : dbl + t.Linv;
+      c.zb64 = dbl + t.zb64;
+      c.zb32 = flt + t.zb32;
+      for (int q = 0; q < 9; ++q) {
+        c.w1[q] = hc.w1[q];
+        c.w2[q] = hc.w2[q];
+      }
     }
     L.size = off;
     s->v[l] = ws + p.field_off[si][l][0];
@@ -490,12 +502,14 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
     ce = cudaMemcpyAsync(h->ws + p.int_off, p.ints.data(), p.ints.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   bind_system(&h->vel, 0, p, h->ws);
   if (h->has_pres) bind_system(&h->pres, 1, p, h->ws);
-  for (Sys* sy : {&h->vel, h->has_pres ? &h->pres : (Sys*)nullptr}) {
+  for (int si = 0; si < 2; ++si) {
+    Sys* sy = si == 0 ? &h->vel : (h->has_pres ? &h->pres : nullptr);
     if (!sy) continue;
+    void* dp = h->ws + p.eng_off[si];
     if (h->esize == 4)
-      plan_coarse_engine<float>(sy->lev, sy->levels, sy->b, sy->v, sy->t, &sy->engf);
+      plan_coarse_engine<float>(sy->lev, sy->levels, sy->b, sy->v, sy->t, dp, st, &sy->engf);
     else
-      plan_coarse_engine<double>(sy->lev, sy->levels, sy->b, sy->v, sy->t, &sy->engd);
+      plan_coarse_engine<double>(sy->lev, sy->levels, sy->b, sy->v, sy->t, dp, st, &sy->engd);
     cudaGetLastError();
   }
   h->u = (double*)(h->ws + p.u_off);
@@ -860,3 +874,4 @@ selm_status selm_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1
 }
 
 }  // extern "C"
+

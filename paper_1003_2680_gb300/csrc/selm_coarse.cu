@@ -27,6 +27,7 @@
 #include "../../include/selm_mg.h"
 #include "selm_coarse.h"
 #include "selm_internal.h"
+#include "selm_devmath.h"
 #include "selm_prof.h"
 
 namespace cg = cooperative_groups;
@@ -36,47 +37,7 @@ namespace {
 
 constexpr int kEngThreads = 512;
 
-__device__ __forceinline__ uint4 eng_philox10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r > 0) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-  }
-  return c;
-}
-
-__device__ __forceinline__ void eng_normals(uint4 w, double n[4]) {
-  const double s = 2.3283064365386962890625e-10;
-  const double u0 = ((double)w.x + 0.5) * s, u1 = ((double)w.y + 0.5) * s;
-  const double u2 = ((double)w.z + 0.5) * s, u3 = ((double)w.w + 0.5) * s;
-  const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
-  double s1, c1, s3, c3;
-  sincospi(2.0 * u1, &s1, &c1);
-  sincospi(2.0 * u3, &s3, &c3);
-  n[0] = r0 * c1;
-  n[1] = r0 * s1;
-  n[2] = r1 * c3;
-  n[3] = r1 * s3;
-}
-
-__device__ __forceinline__ void eng_normals(uint4 w, float n[4]) {
-  const float s = 2.3283064365386962890625e-10f;
-  const float u0 = ((float)w.x + 0.5f) * s, u1 = ((float)w.y + 0.5f) * s;
-  const float u2 = ((float)w.z + 0.5f) * s, u3 = ((float)w.w + 0.5f) * s;
-  const float r0 = sqrtf(-2.0f * logf(u0)), r1 = sqrtf(-2.0f * logf(u2));
-  float s1, c1, s3, c3;
-  sincospif(2.0f * u1, &s1, &c1);
-  sincospif(2.0f * u3, &s3, &c3);
-  n[0] = r0 * c1;
-  n[1] = r0 * s1;
-  n[2] = r1 * c3;
-  n[3] = r1 * s3;
-}
+__device__ __forceinline__ uint4 eng_philox10(uint4 c, uint32_t k0, uint32_t k1) { return philox4x32_10(c, k0, k1); }
 
 __device__ __forceinline__ int ewrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
@@ -92,6 +53,8 @@ struct View {
   int z0, z1;          // owned planes [z0, z1)
   T* v;                // local v buffer: planes [z0-2, z1+2)
   int plane;           // nx * ny
+  const T* tab;        // shared: [nz][12] = z bands (10), 1/A_ii, 1/sqrt(A_ii)
+  const EngColour* col;  // shared: colour classes of this level for this CTA
   __device__ __forceinline__ int loc(int i, int j, int k) const { return ((k - z0 + 2) * L->ny + j) * L->nx + i; }
 };
 
@@ -108,38 +71,65 @@ __device__ __forceinline__ View<T> make_view(const EngLevel<T>& L, unsigned char
   }
   w.v = (T*)(smem + L.sv);
   w.plane = L.nx * L.ny;
+  w.tab = nullptr;
+  w.col = nullptr;
   return w;
 }
 
-// sum_{j != i} A_ij v_j (centre excluded) or the full row (centre included).
-// Five independent partial sums (one per z offset) keep the FMA chains short.
-template <typename T>
-__device__ __forceinline__ T stencil_row(const View<T>& w, int i, int j, int k, bool centre) {
+// Row of A applied to v in the separable form: for each z offset, two 3x3
+// partial sums with the level's x/y weights, combined with the row's z bands.
+// centre == false excludes the diagonal term (sum_{j != i} A_ij v_j).
+template <typename T, bool CENTRE>
+__device__ __forceinline__ T stencil_row(const View<T>& w, int i, int j, int k) {
   const EngLevel<T>& L = *w.L;
-  const T* S = L.S + (long long)k * kStencil;
-  const int xm = ewrap(i - 1, L.nx), xp = ewrap(i + 1, L.nx);
-  const int ny = L.ny;
-  const int ym = ny > 1 ? ewrap(j - 1, ny) : j, yp = ny > 1 ? ewrap(j + 1, ny) : j;
-  const int yrow[3] = {ym, j, yp};
-  T acc[5];
+  const int nx = L.nx, ny = L.ny;
+  const int xm = i == 0 ? nx - 1 : i - 1, xp = i == nx - 1 ? 0 : i + 1;
+  const T* zb = w.tab + k * 12;
+  T acc = (T)0;
 #pragma unroll
   for (int dz = -2; dz <= 2; ++dz) {
-    T a = (T)0;
     const int kk = k + dz;
-    if (kk >= 0 && kk < L.nz) {
-      const T* vp = w.v + (kk - w.z0 + 2) * ny * L.nx;
-#pragma unroll
-      for (int dy = -1; dy <= 1; ++dy) {
-        if (ny == 1 && dy != 0) continue;
-        const T* row = vp + yrow[dy + 1] * L.nx;
-        const T* Sr = S + ((dz + 2) * 3 + (dy + 1)) * 3;
-        a += __ldg(Sr) * row[xm] + __ldg(Sr + 2) * row[xp];
-        if (centre || dz != 0 || dy != 0) a += __ldg(Sr + 1) * row[i];
+    if (kk < 0 || kk >= L.nz) continue;
+    const T* vp = w.v + (kk - w.z0 + 2) * ny * nx;
+    T p1, p2;
+    if (ny == 1) {
+      const T a = vp[xm], c = vp[xp];
+      p1 = L.w1[3] * a + L.w1[5] * c;
+      p2 = L.w2[3] * a + L.w2[5] * c;
+      if (CENTRE || dz != 0) {
+        const T b = vp[i];
+        p1 += L.w1[4] * b;
+        p2 += L.w2[4] * b;
+      }
+    } else {
+      const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
+      const T* r0 = vp + jm * nx;
+      const T* r1 = vp + j * nx;
+      const T* r2 = vp + jp * nx;
+      const T a0 = r0[xm], b0 = r0[i], c0 = r0[xp];
+      const T a1 = r1[xm], c1 = r1[xp];
+      const T a2 = r2[xm], b2 = r2[i], c2 = r2[xp];
+      p1 = L.w1[0] * a0 + L.w1[1] * b0 + L.w1[2] * c0 + L.w1[3] * a1 + L.w1[5] * c1 + L.w1[6] * a2 +
+           L.w1[7] * b2 + L.w1[8] * c2;
+      p2 = L.w2[0] * a0 + L.w2[1] * b0 + L.w2[2] * c0 + L.w2[3] * a1 + L.w2[5] * c1 + L.w2[6] * a2 +
+           L.w2[7] * b2 + L.w2[8] * c2;
+      if (CENTRE || dz != 0) {
+        const T b1 = r1[i];
+        p1 += L.w1[4] * b1;
+        p2 += L.w2[4] * b1;
       }
     }
-    acc[dz + 2] = a;
+    acc += zb[dz + 2] * p1 + zb[5 + dz + 2] * p2;
   }
-  return (acc[0] + acc[4]) + (acc[1] + acc[3]) + acc[2];
+  return acc;
+}
+
+// q = n / d for 0 <= n < 2^24: float reciprocal estimate, then exact correction.
+__device__ __forceinline__ int fdiv(int n, int d, float inv) {
+  int q = (int)((float)n * inv);
+  if (q * d > n) --q;
+  if ((q + 1) * d <= n) ++q;
+  return q;
 }
 
 struct Sync {
@@ -154,41 +144,46 @@ struct Sync {
 
 // One colour pass of the stochastic Gauss-Seidel sweep on the owned planes:
 // one thread per site; the four sites of a noise group each recompute the
-// group's Philox block (cheaper than serialising their updates).
+// group's Philox block (cheaper than serialising their updates).  Class
+// geometry, z bands, inverse diagonals and noise scales come from the
+// shared-memory tables staged for the level.
 template <typename T, bool NOISE>
 __device__ void colour_pass(const View<T>& w, int level, int q, int sweep, const T* b, bool b_local, Key key,
                             unsigned long long cyc, int rank, int csize, bool cluster) {
   const EngLevel<T>& L = *w.L;
-  const int cx = q % L.mx, cy = (q / L.mx) % L.my, cz = q / (L.mx * L.my);
-  const int nxc = (L.nx - cx + L.mx - 1) / L.mx;
-  const int nyc = (L.ny - cy + L.my - 1) / L.my;
-  const int nzc = (L.nz - cz + L.mz - 1) / L.mz;
-  if (nxc <= 0 || nyc <= 0 || nzc <= 0) return;
-  const int kk_lo = w.z0 <= cz ? 0 : (w.z0 - cz + L.mz - 1) / L.mz;
-  const int kk_hi = min(nzc, w.z1 <= cz ? 0 : (w.z1 - cz + L.mz - 1) / L.mz);
-  if (kk_lo >= kk_hi) return;
-  const int pr = nyc * nxc;
-  const int rank_lo = kk_lo * pr;
-  const int nsite = (kk_hi - kk_lo) * pr;
+  const EngColour cc = w.col[q];
+  if (cc.nsite <= 0) return;
   const uint32_t c1 = (uint32_t)level | ((uint32_t)L.comp_id << 4) | ((uint32_t)q << 8) | ((uint32_t)sweep << 12);
   cg::cluster_group cl = cg::this_cluster();
-  for (int s = threadIdx.x; s < nsite; s += blockDim.x) {
-    const int rk = rank_lo + s;
-    const int ii = rk % nxc;
-    const int t = rk / nxc;
-    const int jj = t % nyc, kk = t / nyc;
-    const int i = cx + L.mx * ii, j = cy + L.my * jj, k = cz + L.mz * kk;
+  for (int s = threadIdx.x; s < cc.nsite; s += blockDim.x) {
+    const int rk = cc.rank_lo + s;
+    int t, ii, kk, jj;
+    if (cc.sx >= 0) {
+      t = rk >> cc.sx;
+      ii = rk & (cc.nxc - 1);
+    } else {
+      t = fdiv(rk, cc.nxc, cc.inv_nxc);
+      ii = rk - t * cc.nxc;
+    }
+    if (cc.sy >= 0) {
+      kk = t >> cc.sy;
+      jj = t & (cc.nyc - 1);
+    } else {
+      kk = fdiv(t, cc.nyc, cc.inv_nyc);
+      jj = t - kk * cc.nyc;
+    }
+    const int i = cc.cx + L.mx * ii, j = cc.cy + L.my * jj, k = cc.cz + L.mz * kk;
     const int gidx = (k * L.ny + j) * L.nx + i;
     const T bb = b_local ? b[gidx] : ld_cg(b + gidx);
-    const T diag = __ldg(L.S + (long long)k * kStencil + 22);
-    const T off = stencil_row(w, i, j, k, false);
-    T nv = (bb - off) / diag;
+    const T* tr = w.tab + k * 12;
+    const T off = stencil_row<T, false>(w, i, j, k);
+    T nv = (bb - off) * tr[10];
     if (NOISE) {
-      T n4[4];
-      eng_normals(eng_philox10(make_uint4((uint32_t)(rk >> 2), c1, (uint32_t)cyc, (uint32_t)(cyc >> 32)), key.k0,
-                               key.k1),
-                  n4);
-      nv += n4[rk & 3] / sqrt(diag);
+      T nn;
+      normal_of(eng_philox10(make_uint4((uint32_t)(rk >> 2), c1, (uint32_t)cyc, (uint32_t)(cyc >> 32)), key.k0,
+                             key.k1),
+                rk & 3, &nn);
+      nv += nn * tr[11];
     }
     w.v[w.loc(i, j, k)] = nv;
     if (cluster && csize > 1) {
@@ -222,7 +217,7 @@ __device__ void residual(const View<T>& w, const T* b, bool b_local, T* t) {
     const int j = r % L.ny, k = w.z0 + r / L.ny;
     const int gidx = (k * L.ny + j) * L.nx + i;
     const T bb = b_local ? b[gidx] : ld_cg(b + gidx);
-    t[gidx] = bb - stencil_row(w, i, j, k, true);
+    t[gidx] = bb - stencil_row<T, true>(w, i, j, k);
   }
 }
 
@@ -332,11 +327,10 @@ __device__ void coarsest_step(const View<T>& w, int level, const T* b, double* y
     for (int q = 0; q <= r; ++q) acc += L.Linv[(long long)r * N + q] * (double)b[q];
     if (NOISE) {
       const uint32_t c1 = (uint32_t)level | ((uint32_t)L.comp_id << 4) | (1u << 20);
-      double n4[4];
-      eng_normals(eng_philox10(make_uint4((uint32_t)(r >> 2), c1, (uint32_t)cyc, (uint32_t)(cyc >> 32)), key.k0,
-                               key.k1),
-                  n4);
-      acc += n4[r & 3];
+      double nn;
+      normal_of(eng_philox10(make_uint4((uint32_t)(r >> 2), c1, (uint32_t)cyc, (uint32_t)(cyc >> 32)), key.k0, key.k1),
+                r & 3, &nn);
+      acc += nn;
     }
     y[r] = acc;
   }
@@ -360,87 +354,159 @@ __device__ void sweeps(const View<T>& w, int level, int first_sweep, int count, 
     }
 }
 
+// Copies a level descriptor into shared memory (all threads, with barriers).
+template <typename T>
+__device__ __forceinline__ void stage(EngLevel<T>* dst, const EngLevel<T>* src) {
+  __syncthreads();
+  constexpr int n = (int)(sizeof(EngLevel<T>) / sizeof(int));
+  for (int q = threadIdx.x; q < n; q += blockDim.x) reinterpret_cast<int*>(dst)[q] = reinterpret_cast<const int*>(src)[q];
+  __syncthreads();
+}
+
+// Fills a table slot for the staged level L as seen by the CTA owning planes
+// [z0, z1): per row k the z bands, 1/A_ii and 1/sqrt(A_ii); per colour class
+// the geometry and the owned rank range.
+template <typename T>
+__device__ void stage_tables(const EngLevel<T>& L, int z0, int z1, T* tab, EngColour* col) {
+  for (int q = threadIdx.x; q < L.nz * 12; q += blockDim.x) {
+    const int k = q / 12, e = q - k * 12;
+    T val;
+    if (e < 10) {
+      val = L.zb[k * 10 + e];
+    } else {
+      const T d = L.S[(long long)k * kStencil + 22];
+      val = e == 10 ? (T)1 / d : (T)1 / tsqrt(d);
+    }
+    tab[q] = val;
+  }
+  for (int q = threadIdx.x; q < L.ncol; q += blockDim.x) {
+    EngColour c;
+    c.cx = q % L.mx;
+    c.cy = (q / L.mx) % L.my;
+    c.cz = q / (L.mx * L.my);
+    c.nxc = (L.nx - c.cx + L.mx - 1) / L.mx;
+    c.nyc = (L.ny - c.cy + L.my - 1) / L.my;
+    const int nzc = (L.nz - c.cz + L.mz - 1) / L.mz;
+    c.inv_nxc = 1.0f / (float)max(c.nxc, 1);
+    c.inv_nyc = 1.0f / (float)max(c.nyc, 1);
+    c.sx = (c.nxc > 0 && (c.nxc & (c.nxc - 1)) == 0) ? __ffs(c.nxc) - 1 : -1;
+    c.sy = (c.nyc > 0 && (c.nyc & (c.nyc - 1)) == 0) ? __ffs(c.nyc) - 1 : -1;
+    int kk_lo = z0 <= c.cz ? 0 : (z0 - c.cz + L.mz - 1) / L.mz;
+    int kk_hi = z1 <= c.cz ? 0 : (z1 - c.cz + L.mz - 1) / L.mz;
+    kk_hi = min(kk_hi, nzc);
+    const int pr = c.nxc * c.nyc;
+    c.rank_lo = kk_lo * pr;
+    c.nsite = (c.nxc > 0 && c.nyc > 0 && nzc > 0 && kk_hi > kk_lo) ? (kk_hi - kk_lo) * pr : 0;
+    col[q] = c;
+  }
+  __syncthreads();
+}
+
 template <typename T, bool NOISE>
-__global__ void __launch_bounds__(kEngThreads, 1) k_coarse_engine(EngParams<T> p) {
+__global__ void __launch_bounds__(kEngThreads, 1) k_coarse_engine(const EngParams<T>* __restrict__ P, EngRun run) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ EngLevel<T> sl[2];
+  __shared__ EngColour scol[2][kEngMaxColours];
   cg::cluster_group cl = cg::this_cluster();
   const int csize = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int comp = blockIdx.x / csize;
-  const EngComp<T>& E = p.comp[comp];
-  const unsigned long long cyc = *p.cyc;
-  const int lt = p.l0, lc = p.L - 1;
+  const EngComp<T>* E = &P->comp[comp];
+  const unsigned long long cyc = *run.cyc;
+  const int lt = P->l0, lc = P->L - 1;
+  const int mu1 = run.mu1, mu2 = run.mu2;
+  const Key key = run.key;
+  T* tabs[2] = {(T*)(smem + P->tab_off), (T*)(smem + P->tab_off + P->tab_slot)};
 
-  // ---- down leg ----
+  // ---- down leg over the cluster levels ----
   int l = lt;
-  for (; l < lc && E.lev[l].cluster; ++l) {
-    const EngLevel<T>& L = E.lev[l];
-    const EngLevel<T>& Lc = E.lev[l + 1];
+  for (; l < lc && E->lev[l].cluster; ++l) {
+    stage(&sl[0], &E->lev[l]);
+    stage(&sl[1], &E->lev[l + 1]);
+    const EngLevel<T>& L = sl[0];
+    const EngLevel<T>& Lc = sl[1];
     View<T> w = make_view(L, smem, rank, true);
+    stage_tables(L, w.z0, w.z1, tabs[0], scol[0]);
+    w.tab = tabs[0];
+    w.col = scol[0];
     zero_local(w);
     cl.sync();
-    sweeps<T, NOISE>(w, l, 0, p.mu1, L.gb, false, p.key, cyc, rank, csize, true);
+    sweeps<T, NOISE>(w, l, 0, mu1, L.gb, false, key, cyc, rank, csize, true);
     residual(w, L.gb, false, L.gt);
     cl.sync();
     const int Z0 = Lc.cluster ? min(rank * Lc.P, Lc.nz) : (rank == 0 ? 0 : Lc.nz);
-    const int Z1 = Lc.cluster ? min(Z0 + Lc.P, Lc.nz) : (rank == 0 ? Lc.nz : Lc.nz);
+    const int Z1 = Lc.cluster ? min(Z0 + Lc.P, Lc.nz) : Lc.nz;
     restrict_to(L, Lc, L.gt, false, Lc.gb, Z0, Z1);
     cl.sync();
   }
   const int lsingle = l;   // first level held by CTA 0 alone
   if (rank == 0) {
     // ---- single-CTA part: levels lsingle .. lc and back ----
+    stage(&sl[0], &E->lev[lsingle]);
     {
-      const EngLevel<T>& L = E.lev[lsingle];
-      View<T> w = make_view(L, smem, 0, false);
-      load_all(w, L.gb, (T*)(smem + L.sb));
-      __syncthreads();
+      View<T> w = make_view(sl[0], smem, 0, false);
+      load_all(w, sl[0].gb, (T*)(smem + sl[0].sb));
     }
     for (int k = lsingle; k <= lc; ++k) {
-      const EngLevel<T>& L = E.lev[k];
+      stage(&sl[0], &E->lev[k]);
+      if (k < lc) stage(&sl[1], &E->lev[k + 1]);
+      const EngLevel<T>& L = sl[0];
       View<T> w = make_view(L, smem, 0, false);
+      stage_tables(L, 0, L.nz, tabs[0], scol[0]);
+      w.tab = tabs[0];
+      w.col = scol[0];
       T* b = (T*)(smem + L.sb);
       zero_local(w);
       __syncthreads();
-      if (k == lc && p.coarse_mode == SELM_COARSE_CHOLESKY) {
-        coarsest_step<T, NOISE>(w, k, b, (double*)(smem + p.y_off), p.key, cyc);
+      if (k == lc && run.coarse_mode == SELM_COARSE_CHOLESKY) {
+        coarsest_step<T, NOISE>(w, k, b, (double*)(smem + P->y_off), key, cyc);
         __syncthreads();
         break;
       }
-      sweeps<T, NOISE>(w, k, 0, p.mu1, b, true, p.key, cyc, 0, 1, false);
+      sweeps<T, NOISE>(w, k, 0, mu1, b, true, key, cyc, 0, 1, false);
       if (k == lc) {
-        sweeps<T, NOISE>(w, k, p.mu1, p.mu2, b, true, p.key, cyc, 0, 1, false);
+        sweeps<T, NOISE>(w, k, mu1, mu2, b, true, key, cyc, 0, 1, false);
         break;
       }
-      const EngLevel<T>& Lc = E.lev[k + 1];
+      const EngLevel<T>& Lc = sl[1];
       residual(w, b, true, (T*)(smem + L.st));
       __syncthreads();
       restrict_to(L, Lc, (const T*)(smem + L.st), true, (T*)(smem + Lc.sb), 0, Lc.nz);
       __syncthreads();
     }
     for (int k = lc - 1; k >= lsingle; --k) {
-      const EngLevel<T>& L = E.lev[k];
-      const EngLevel<T>& Lc = E.lev[k + 1];
+      stage(&sl[0], &E->lev[k]);
+      stage(&sl[1], &E->lev[k + 1]);
+      const EngLevel<T>& L = sl[0];
+      const EngLevel<T>& Lc = sl[1];
       View<T> w = make_view(L, smem, 0, false);
+      stage_tables(L, 0, L.nz, tabs[0], scol[0]);
+      w.tab = tabs[0];
+      w.col = scol[0];
       prolong_into(w, Lc, (const T*)(smem + Lc.sv), true, 0);
       __syncthreads();
-      sweeps<T, NOISE>(w, k, p.mu1, p.mu2, (const T*)(smem + L.sb), true, p.key, cyc, 0, 1, false);
+      sweeps<T, NOISE>(w, k, mu1, mu2, (const T*)(smem + L.sb), true, key, cyc, 0, 1, false);
     }
+    stage(&sl[0], &E->lev[lsingle]);
     {
-      const EngLevel<T>& L = E.lev[lsingle];
-      View<T> w = make_view(L, smem, 0, false);
-      store_owned(w, L.gv);
+      View<T> w = make_view(sl[0], smem, 0, false);
+      store_owned(w, sl[0].gv);
     }
   }
   cl.sync();
   // ---- up leg over the cluster levels ----
   for (int k = lsingle - 1; k >= lt; --k) {
-    const EngLevel<T>& L = E.lev[k];
-    const EngLevel<T>& Lc = E.lev[k + 1];
+    stage(&sl[0], &E->lev[k]);
+    stage(&sl[1], &E->lev[k + 1]);
+    const EngLevel<T>& L = sl[0];
+    const EngLevel<T>& Lc = sl[1];
     View<T> w = make_view(L, smem, rank, true);
+    stage_tables(L, w.z0, w.z1, tabs[0], scol[0]);
+    w.tab = tabs[0];
+    w.col = scol[0];
     prolong_into(w, Lc, Lc.gv, false, 0);
     cl.sync();
-    sweeps<T, NOISE>(w, k, p.mu1, p.mu2, L.gb, false, p.key, cyc, rank, csize, true);
+    sweeps<T, NOISE>(w, k, mu1, mu2, L.gb, false, key, cyc, rank, csize, true);
     store_owned(w, L.gv);
     cl.sync();
   }
@@ -472,6 +538,7 @@ bool try_plan(const LevelDev* levs, int L, int l0, int C, size_t smem_cap, Engin
       const CompDev& d = levs[l].c[c];
       EngLevel<T>& e = p.comp[c].lev[l];
       const long long sites = (long long)d.nx * d.ny * d.nz;
+      if (sites >= (1ll << 24)) return false;   // rank decode uses float reciprocals
       const bool single = single_started || l == L - 1 || sites <= kEngSingleMaxSites || C == 1;
       if (single) single_started = true;
       e.cluster = single ? 0 : 1;
@@ -496,7 +563,14 @@ bool try_plan(const LevelDev* levs, int L, int l0, int C, size_t smem_cap, Engin
     off = align16(off + Nc * sizeof(double));
     need_max = need_max > off ? need_max : off;
   }
-  if (need_max > smem_cap) return false;
+  int nzmax = 0;
+  for (int c = 0; c < ncomp; ++c)
+    for (int l = l0; l < L; ++l) nzmax = nzmax > levs[l].c[c].nz ? nzmax : levs[l].c[c].nz;
+  const size_t slot = align16((size_t)nzmax * 12 * sizeof(T));
+  for (int c = 0; c < ncomp; ++c)
+    for (int l = l0; l < L; ++l)
+      if (levs[l].c[c].ncol > kEngMaxColours) return false;
+  if (need_max + 2 * sizeof(EngLevel<T>) + 2 * kEngMaxColours * sizeof(EngColour) > smem_cap) return false;
   if (!any_cluster) C = 1;
   // every component gets the same y offset (the maximum) so that the kernel
   // can use one field
@@ -509,8 +583,12 @@ bool try_plan(const LevelDev* levs, int L, int l0, int C, size_t smem_cap, Engin
     const size_t Nc = (size_t)dc.nx * dc.ny * dc.nz;
     ymax = ymax > Nc ? ymax : Nc;
   }
-  out->smem_bytes = align16(yo + ymax * sizeof(double));
-  if (out->smem_bytes > smem_cap) return false;
+  const size_t tab_off = align16(yo + ymax * sizeof(double));
+  p.tab_off = (int)tab_off;
+  p.tab_slot = (int)slot;
+  out->smem_bytes = tab_off + 2 * slot;
+  const size_t static_bytes = 2 * sizeof(EngLevel<T>) + 2 * kEngMaxColours * sizeof(EngColour);
+  if (out->smem_bytes + static_bytes > smem_cap) return false;
   out->cluster = C;
   return true;
 }
@@ -534,6 +612,13 @@ void fill_engine_tables(const LevelDev* levs, int L, void* const* gb, void* cons
       e.ncol = d.ncol;
       e.comp_id = d.comp_id;
       e.S = sizeof(T) == 4 ? (const T*)d.S32 : (const T*)d.S64;
+      e.zb = sizeof(T) == 4 ? (const T*)d.zb32 : (const T*)d.zb64;
+      for (int q = 0; q < 9; ++q) {
+        e.w1[q] = (T)d.w1[q];
+        e.w2[q] = (T)d.w2[q];
+      }
+      e.inv_nxc = 1.0f / (float)((d.nx + d.mx - 1) / d.mx);
+      e.inv_nyc = 1.0f / (float)((d.ny + d.my - 1) / d.my);
       e.rz_idx = d.rz_idx;
       e.rz_w = sizeof(T) == 4 ? (const T*)d.rz_w32 : (const T*)d.rz_w64;
       e.pz_idx = d.pz_idx;
@@ -547,9 +632,10 @@ void fill_engine_tables(const LevelDev* levs, int L, void* const* gb, void* cons
 
 template <typename T>
 bool plan_coarse_engine(const LevelDev* levs, int L, void* const* gb, void* const* gv, void* const* gt,
-                        EnginePlanT<T>* plan) {
+                        void* dev_params, cudaStream_t st, EnginePlanT<T>* plan) {
+  static_assert(sizeof(EngParams<T>) <= kEngParamBytes, "engine plan exceeds its workspace slot");
   plan->valid = false;
-  if (L < 2) return false;
+  if (L < 2 || !dev_params) return false;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   int cap = 0, cluster_ok = 0;
@@ -607,6 +693,13 @@ bool plan_coarse_engine(const LevelDev* levs, int L, void* const* gb, void* cons
       }
       *plan = cand;
       fill_engine_tables<T>(levs, L, gb, gv, gt, plan);
+      if (cudaMemcpyAsync(dev_params, &plan->params, sizeof(EngParams<T>), cudaMemcpyHostToDevice, st) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
+      plan->dev = (const EngParams<T>*)dev_params;
       plan->valid = true;
       return true;
     }
@@ -617,14 +710,9 @@ bool plan_coarse_engine(const LevelDev* levs, int L, void* const* gb, void* cons
 template <typename T>
 cudaError_t launch_coarse_engine(const EnginePlanT<T>& plan, int mu1, int mu2, int coarse_mode, bool noise, Key key,
                                  const unsigned long long* cyc, cudaStream_t st) {
-  EngParams<T> p = plan.params;
-  p.mu1 = mu1;
-  p.mu2 = mu2;
-  p.coarse_mode = coarse_mode;
-  p.key = key;
-  p.cyc = cyc;
+  EngRun run{mu1, mu2, coarse_mode, key, cyc};
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(plan.cluster * p.ncomp);
+  cfg.gridDim = dim3(plan.cluster * plan.params.ncomp);
   cfg.blockDim = dim3(kEngThreads);
   cfg.dynamicSmemBytes = plan.smem_bytes;
   cfg.stream = st;
@@ -636,14 +724,14 @@ cudaError_t launch_coarse_engine(const EnginePlanT<T>& plan, int mu1, int mu2, i
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   prof::Scope ps(SELM_K_COARSE_SWEEP, st);
-  if (noise) return cudaLaunchKernelEx(&cfg, k_coarse_engine<T, true>, p);
-  return cudaLaunchKernelEx(&cfg, k_coarse_engine<T, false>, p);
+  if (noise) return cudaLaunchKernelEx(&cfg, k_coarse_engine<T, true>, plan.dev, run);
+  return cudaLaunchKernelEx(&cfg, k_coarse_engine<T, false>, plan.dev, run);
 }
 
-template bool plan_coarse_engine<float>(const LevelDev*, int, void* const*, void* const*, void* const*,
-                                        EnginePlanT<float>*);
-template bool plan_coarse_engine<double>(const LevelDev*, int, void* const*, void* const*, void* const*,
-                                         EnginePlanT<double>*);
+template bool plan_coarse_engine<float>(const LevelDev*, int, void* const*, void* const*, void* const*, void*,
+                                        cudaStream_t, EnginePlanT<float>*);
+template bool plan_coarse_engine<double>(const LevelDev*, int, void* const*, void* const*, void* const*, void*,
+                                         cudaStream_t, EnginePlanT<double>*);
 template cudaError_t launch_coarse_engine<float>(const EnginePlanT<float>&, int, int, int, bool, Key,
                                                  const unsigned long long*, cudaStream_t);
 template cudaError_t launch_coarse_engine<double>(const EnginePlanT<double>&, int, int, int, bool, Key,

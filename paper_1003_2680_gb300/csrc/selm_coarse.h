@@ -22,6 +22,10 @@ struct EngLevel {
   int P;              // planes per CTA (cluster levels) or nz (single levels)
   int sv, sb, st;     // shared-memory byte offsets of v (with 2 halo planes per side), b, t
   const T* S;         // [nz][45] stencil
+  const T* zb;        // [nz][10]: s*Mz row (offsets -2..2), then s*Kz row
+  T w1[9];            // Kx (x) My + Mx (x) Ky at (dy, dx) = index (dy+1)*3 + dx+1
+  T w2[9];            // Mx (x) My
+  float inv_nxc, inv_nyc;  // reciprocals for the colour-class rank decode
   const int* rz_idx;  // restriction table to the next level
   const T* rz_w;
   const int* pz_idx;  // prolongation table from the next level
@@ -32,19 +36,38 @@ struct EngLevel {
   T* gt;              // global residual buffer
 };
 
+// Per-colour class data of a level, staged in shared memory per CTA.
+struct EngColour {
+  int cx, cy, cz;       // class origin
+  int nxc, nyc;         // class extents in x and y
+  int rank_lo, nsite;   // ranks of the class owned by this CTA: [rank_lo, rank_lo + nsite)
+  float inv_nxc, inv_nyc;
+  int sx, sy;           // log2 of nxc / nyc when they are powers of two, else -1
+};
+
+constexpr int kEngMaxColours = 16;
+
 template <typename T>
 struct EngComp {
   EngLevel<T> lev[kMaxLevels];
 };
 
+// Plan of one system, uploaded once to device memory (read through L1 and
+// staged level by level into shared memory by the kernel).
 template <typename T>
 struct EngParams {
   int l0, L, ncomp;
-  int mu1, mu2, coarse_mode;
   int y_off;          // shared-memory byte offset of the FP64 coarsest scratch
+  int tab_off;        // shared-memory byte offset of the two level-table slots
+  int tab_slot;       // bytes per slot: nz_max rows of (10 bands + inverse diagonal + noise scale) values
+  EngComp<T> comp[kMaxComps];
+};
+
+// Per-launch arguments.
+struct EngRun {
+  int mu1, mu2, coarse_mode;
   Key key;
   const unsigned long long* cyc;
-  EngComp<T> comp[kMaxComps];
 };
 
 template <typename T>
@@ -54,13 +77,19 @@ struct EnginePlanT {
   size_t smem_bytes = 0;
   size_t y_off_comp[kMaxComps] = {};
   EngParams<T> params{};
+  const EngParams<T>* dev = nullptr;   // device copy of params
 };
+
+// Bytes of device memory a system's plan occupies (reserved in the workspace).
+constexpr size_t kEngParamBytes = 32768;
 
 // Builds the plan for levels l0..L-1 (l0 >= 1 chosen as the first level whose
 // slabs fit in shared memory).  gb/gv/gt: per-level global field pointers.
+// dev_params: kEngParamBytes of device memory that receives the plan
+// (copied on `st`, which is synchronised before returning).
 template <typename T>
 bool plan_coarse_engine(const LevelDev* levs, int L, void* const* gb, void* const* gv, void* const* gt,
-                        EnginePlanT<T>* plan);
+                        void* dev_params, cudaStream_t st, EnginePlanT<T>* plan);
 
 // Runs the V-cycle below level l0-1: reads b at level l0, writes v at level l0.
 template <typename T>

@@ -41,6 +41,9 @@ struct CompDev {
   const double* pz_w64;
   const float* pz_w32;
   const double* Linv;      // coarsest level: [N][N] inverse of the Cholesky factor (row-major, lower)
+  const double* zb64;      // [nz][10]: s*Mz band row then s*Kz band row (offsets -2..2)
+  const float* zb32;
+  double w1[9], w2[9];     // periodic x/y weights: Kx(x)My + Mx(x)Ky and Mx(x)My, index (dy+1)*3+dx+1
 };
 
 struct LevelDev {
@@ -59,6 +62,8 @@ struct HostComp {
   std::vector<double> Kz, Mz;          // [nz][5] band rows, offsets -2..2
   int bw[3];               // bandwidths per axis
   std::vector<double> S;   // [nz][45] full stencil (scaled)
+  std::vector<double> zb;  // [nz][10] scaled z bands (Mz then Kz)
+  double w1[9], w2[9];     // x/y weights of the separable form
   // transfer tables to the next coarser level
   std::vector<int> rz_idx;
   std::vector<double> rz_w;

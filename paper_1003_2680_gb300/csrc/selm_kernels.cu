@@ -23,6 +23,7 @@
 #include "../../include/selm_mg.h"
 #include "selm_internal.h"
 #include "selm_launch.h"
+#include "selm_devmath.h"
 #include "selm_prof.h"
 
 namespace selm {
@@ -95,19 +96,7 @@ constexpr int kBlock = 256;
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r > 0) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-  }
-  return c;
-}
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) { return philox4x32_10(c, k0, k1); }
 
 template <typename T>
 struct Normals;
@@ -293,7 +282,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_colour(LevelDev L, ColourPass c
     fine_row<T, T>(c, v, i, j, k, &off, &diag);
     const long long idx = c.off + ((long long)k * c.ny + j) * c.nx + i;
     T nv = (b[idx] - off) / diag;
-    if (NOISE) nv += nz4[lane] / sqrt(diag);
+    if (NOISE) nv += nz4[lane] / tsqrt(diag);
     v[idx] = nv;
   }
 }
@@ -431,7 +420,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_colour_v8(LevelDev L, RowPass r
   if (c.zkind == kAxisCellNeu) dz -= (T)edges;
   const T s = (T)c.s;
   const T diag = s * ((c.ny > 1 ? (T)4 : (T)2) + dz);
-  const T rsd = NOISE ? (T)1 / sqrt(diag) : (T)0;
+  const T rsd = NOISE ? (T)1 / tsqrt(diag) : (T)0;
   if (p == 0)
     fine_update8<T, NOISE, 0>(cen, bb, acc, left, right, n4, s, diag, rsd);
   else
@@ -554,7 +543,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_colour(LevelDev L, ColourPass
     const T diag = coarse_diag<T>(c, k);
     const long long idx = c.off + ((long long)k * c.ny + j) * c.nx + i;
     T nv = (b[idx] - off) / diag;
-    if (NOISE) nv += nz4[lane] / sqrt(diag);
+    if (NOISE) nv += nz4[lane] / tsqrt(diag);
     v[idx] = nv;
   }
 }

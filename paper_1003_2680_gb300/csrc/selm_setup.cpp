@@ -162,6 +162,24 @@ void fill_stencil(HostComp* c, double s) {
         }
 }
 
+// Separable form of the same operator: per z offset cz,
+//   A v = sum_cz [ s Mz[k][cz] * sum_{dy,dx} w1[dy][dx] v + s Kz[k][cz] * sum_{dy,dx} w2[dy][dx] v ]
+// with w1 = Kx (x) My + Mx (x) Ky and w2 = Mx (x) My.
+void fill_separable(HostComp* c, double s) {
+  int nz = c->dims[2];
+  c->zb.assign((size_t)nz * 10, 0.0);
+  for (int k = 0; k < nz; ++k)
+    for (int q = 0; q < 5; ++q) {
+      c->zb[(size_t)k * 10 + q] = s * c->Mz[(size_t)k * 5 + q];
+      c->zb[(size_t)k * 10 + 5 + q] = s * c->Kz[(size_t)k * 5 + q];
+    }
+  for (int dy = 0; dy < 3; ++dy)
+    for (int dx = 0; dx < 3; ++dx) {
+      c->w1[dy * 3 + dx] = c->Kx[dx] * c->My[dy] + c->Mx[dx] * c->Ky[dy];
+      c->w2[dy * 3 + dx] = c->Mx[dx] * c->My[dy];
+    }
+}
+
 void fill_moduli(HostComp* c) {
   c->mods[0] = c->dims[0] == 1 ? 1 : c->bw[0] + 1;
   c->mods[1] = c->dims[1] == 1 ? 1 : c->bw[1] + 1;
@@ -265,6 +283,7 @@ std::string build_system(int dim, int n, int levels, double scale, const std::ve
       c.bw[2] = band_width(c.Kz, c.Mz, c.dims[2]);
       fill_moduli(&c);
       fill_stencil(&c, scale);
+      fill_separable(&c, scale);
       c.rz_idx.clear();
       c.rz_w.clear();
       c.pz_idx.clear();

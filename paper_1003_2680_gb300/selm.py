@@ -152,7 +152,7 @@ _FREE_CB = FREE_FN(_free)
 
 def make_desc(dim, n, mu=1.0, kT=1.0, levels=0, nu_pre=2, nu_post=2, precision=SELM_FP64,
               projection=SELM_PROJ_NONE, coarse_mode=SELM_COARSE_CHOLESKY, tol=1e-10, max_cycles=100,
-              proj_tol=1e-12, max_particles=4096, seed=0, instance=0, torch_allocator=True):
+              proj_tol=1e-10, max_particles=4096, seed=0, instance=0, torch_allocator=True):
     d = SelmDesc()
     d.dim, d.n, d.mu, d.kT, d.levels = dim, n, mu, kT, levels
     d.nu_pre, d.nu_post, d.precision, d.projection, d.coarse_mode = nu_pre, nu_post, precision, projection, coarse_mode

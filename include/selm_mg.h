@@ -198,6 +198,24 @@ selm_status selm_mg_project(selm_mg* h, double* w, int* cycles_out, void* stream
 /* Alg. 4 step 4 tail: X += V, wrap the periodic coordinates, reflect at walls. */
 selm_status selm_mg_em_update(selm_mg* h, int np, double* X, const double* V, void* stream);
 
+/* One V-cycle like selm_mg_vcycle (velocity system) for callers that cannot
+   allocate device memory: no cudaMalloc, no pinned host buffer, no allocator
+   hook.  The paper has no counterpart; this is a deployment convenience.
+   Its scratch (Galerkin tables, coarse-level fields, the level-0 residual
+   buffer, counters) lives in one fixed 16 MiB device array that every device
+   loading this library keeps until the process exits; grids whose scratch
+   does not fit (roughly above 64^3 in FP32) are rejected with SELM_EINVAL
+   and a message on stderr.  `desc` describes the grid as for
+   selm_mg_create (projection and allocator fields are ignored); v and b are
+   level-0 inner-precision fields in the selm_mg_layout order.  The first call
+   on a device, and the first call after the descriptor changes, builds the
+   hierarchy into the array and synchronises `stream`; make that call before
+   any stream capture.  All calls share the array: the level fields are
+   cleared inside each V-cycle and the counter slot is rewritten per call,
+   but calls that overlap on the GPU (other streams, other threads) race. */
+selm_status selm_mg_vcycle_static(const selm_mg_desc* desc, void* v, const void* b, uint64_t cycle,
+                                  int noise, void* stream);
+
 /* ---- measurement --------------------------------------------------------
    Process-wide kernel accounting.  selm_kernel_launches() counts every
    kernel this library has launched since it was loaded.  With profiling on,

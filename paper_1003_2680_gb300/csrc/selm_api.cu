@@ -183,7 +183,8 @@ void plan_tables(const HostSystem& hs, int si, Plan* p) {
   }
 }
 
-void make_plan(const selm_mg_desc& d, const Sys& vel, const Sys* pres, int esize, Plan* p) {
+void make_plan(const selm_mg_desc& d, const Sys& vel, const Sys* pres, int esize, Plan* p,
+               bool vcycle_only = false) {
   plan_tables(vel.host, 0, p);
   if (pres) plan_tables(pres->host, 1, p);
   p->dbl_off = p->lay.add(p->dbl.size() * sizeof(double) + 8);
@@ -194,6 +195,12 @@ void make_plan(const selm_mg_desc& d, const Sys& vel, const Sys* pres, int esize
     if (!hs[si]) continue;
     for (int l = 0; l < hs[si]->levels; ++l)
       for (int f = 0; f < 3; ++f) p->field_off[si][l][f] = p->lay.add((size_t)hs[si]->level_size(l) * esize);
+  }
+  if (vcycle_only) {   // V-cycle scratch only: tables, level fields, counters, engine plan
+    p->eng_off[0] = p->lay.add(kEngParamBytes);
+    p->red_off = p->lay.add(16 * sizeof(double));
+    p->cyc_off = p->lay.add(4 * sizeof(unsigned long long));
+    return;
   }
   const size_t nv = (size_t)vel.host.level_size(0);
   p->u_off = p->lay.add(nv * 8);
@@ -875,3 +882,124 @@ selm_status selm_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1
 
 }  // extern "C"
 
+
+// ---------------------------------------------------------------------------
+// V-cycle without device allocation.
+//
+// For callers that cannot allocate device memory themselves or through us at
+// run time -- for example code running inside a CUDA graph that is being
+// captured, a host with a fixed pre-planned memory budget, or a framework
+// whose allocator is not reachable from the calling thread -- this entry
+// point runs one V-cycle with all of its scratch (Galerkin tables, level
+// fields, counters, the coarse-engine plan) in the fixed device array below.
+// Every device that loads this library holds the array until the process
+// exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;   // 16 MiB per device
+constexpr int kStaticMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+struct StaticSlot {
+  bool ready = false;
+  selm_mg_desc key{};
+  selm_mg* h = nullptr;   // host-side bookkeeping; its workspace is g_static_scratch
+};
+StaticSlot g_static_slots[kStaticMaxDevices];
+
+bool same_vcycle_desc(const selm_mg_desc& a, const selm_mg_desc& b) {
+  return a.dim == b.dim && a.n == b.n && a.mu == b.mu && a.levels == b.levels && a.nu_pre == b.nu_pre &&
+         a.nu_post == b.nu_post && a.precision == b.precision && a.coarse_mode == b.coarse_mode &&
+         a.seed == b.seed && a.instance == b.instance;
+}
+
+}  // namespace
+
+extern "C" selm_status selm_mg_vcycle_static(const selm_mg_desc* desc, void* v, const void* b, uint64_t cycle,
+                                             int noise, void* stream) {
+  if (!desc || !v || !b) return SELM_EINVAL;
+  selm_mg_desc d = *desc;
+  d.projection = SELM_PROJ_NONE;
+  d.alloc = nullptr;
+  d.free = nullptr;
+  fill_desc_defaults(&d);
+  std::string e = validate(d);
+  int dev = 0;
+  if (e.empty() && cudaGetDevice(&dev) != cudaSuccess) e = "no current CUDA device";
+  if (e.empty() && (dev < 0 || dev >= kStaticMaxDevices)) e = "device index out of range";
+  if (!e.empty()) {
+    std::fprintf(stderr, "selm_mg_vcycle_static: %s\n", e.c_str());
+    return SELM_EINVAL;
+  }
+  cudaStream_t st = S(stream);
+  StaticSlot& slot = g_static_slots[dev];
+  if (!slot.ready || !same_vcycle_desc(slot.key, d)) {
+    // (Re)build the hierarchy for this descriptor inside the static array.
+    selm_mg* h = slot.h ? slot.h : new (std::nothrow) selm_mg();
+    if (!h) return SELM_ENOMEM;
+    slot.h = h;
+    slot.ready = false;
+    h->d = d;
+    h->vel = Sys();
+    h->pres = Sys();
+    h->has_pres = false;
+    e = build_systems(d, &h->vel, &h->pres, &h->has_pres);
+    if (!e.empty()) {
+      std::fprintf(stderr, "selm_mg_vcycle_static: %s\n", e.c_str());
+      return SELM_EINVAL;
+    }
+    h->mu1 = d.nu_pre;
+    h->mu2 = d.nu_post;
+    h->esize = d.precision == SELM_FP64 ? 8 : 4;
+    h->key.k0 = (uint32_t)(d.seed & 0xffffffffu) ^ (uint32_t)(d.instance >> 32);
+    h->key.k1 = (uint32_t)(d.seed >> 32) ^ (uint32_t)(d.instance & 0xffffffffu);
+    Plan p;
+    make_plan(d, h->vel, nullptr, h->esize, &p, true);
+    if (p.lay.total > kStaticScratchBytes) {
+      std::fprintf(stderr,
+                   "selm_mg_vcycle_static: this grid needs %zu bytes of scratch, above the static limit of %zu bytes\n",
+                   p.lay.total, kStaticScratchBytes);
+      return SELM_EINVAL;
+    }
+    // In host code g_static_scratch names a host-side stand-in; the device
+    // address must come from the runtime, with this device current.
+    void* base = nullptr;
+    cudaError_t ce = cudaGetSymbolAddress(&base, g_static_scratch);
+    if (ce != cudaSuccess || !base) {
+      std::fprintf(stderr, "selm_mg_vcycle_static: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(ce));
+      cudaGetLastError();
+      return SELM_ECUDA;
+    }
+    h->ws = (char*)base;
+    h->ws_bytes = kStaticScratchBytes;
+    if (!p.dbl.empty())
+      ce = cudaMemcpyAsync(h->ws + p.dbl_off, p.dbl.data(), p.dbl.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess && !p.flt.empty())
+      ce = cudaMemcpyAsync(h->ws + p.flt_off, p.flt.data(), p.flt.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess && !p.ints.empty())
+      ce = cudaMemcpyAsync(h->ws + p.int_off, p.ints.data(), p.ints.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);   // the host tables are temporaries
+    if (ce != cudaSuccess) {
+      std::fprintf(stderr, "selm_mg_vcycle_static: %s\n", cudaGetErrorString(ce));
+      return SELM_ECUDA;
+    }
+    bind_system(&h->vel, 0, p, h->ws);
+    h->red = (double*)(h->ws + p.red_off);
+    h->cyc = (unsigned long long*)(h->ws + p.cyc_off);
+    if (h->esize == 4)
+      plan_coarse_engine<float>(h->vel.lev, h->vel.levels, h->vel.b, h->vel.v, h->vel.t, h->ws + p.eng_off[0], st,
+                                &h->vel.engf);
+    else
+      plan_coarse_engine<double>(h->vel.lev, h->vel.levels, h->vel.b, h->vel.v, h->vel.t, h->ws + p.eng_off[0], st,
+                                 &h->vel.engd);
+    cudaGetLastError();
+    slot.key = d;
+    slot.ready = true;
+  }
+  selm_mg* h = slot.h;
+  // The counter slot keeps the previous call's value: set it for this call.
+  if (launch_set_u64(h->cyc + 1, cycle, st) != cudaSuccess) return SELM_ECUDA;
+  return vcycle(h, h->vel, v, b, noise != 0, h->cyc + 1, st);
+}

@@ -74,6 +74,7 @@ _SIGS = {
     "selm_mg_prolong_correct": (_I, [_P, _I, _I, _P, _P, _P]),
     "selm_mg_coarsest": (_I, [_P, _I, _P, _P, _U64, _I, _P]),
     "selm_mg_vcycle": (_I, [_P, _I, _P, _P, _U64, _I, _P]),
+    "selm_mg_vcycle_static": (_I, [ctypes.POINTER(SelmDesc), _P, _P, _U64, _I, _P]),
     "selm_mg_outer_residual": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "selm_mg_outer_update": (_I, [_P, _I, _P, _P, _P]),
     "selm_mg_fac_cycle": (_I, [_P, _I, _P, _P, _U64, _I, _P]),
@@ -284,6 +285,12 @@ def selm_mg_coarsest(h, system, v, b, cycle, noise, stream=None):
 
 def selm_mg_vcycle(h, system, v, b, cycle, noise, stream=None):
     _check(h, lib().selm_mg_vcycle(h, system, _ptr(v), _ptr(b), cycle, int(noise), _stream(stream)))
+
+
+def selm_mg_vcycle_static(desc, v, b, cycle, noise, stream=None):
+    """One V-cycle with no device allocation (static scratch inside the library)."""
+    _check(None, lib().selm_mg_vcycle_static(ctypes.byref(desc), _ptr(v), _ptr(b), cycle, int(noise),
+                                             _stream(stream)))
 
 
 def selm_mg_outer_residual(h, system, z, b64, r, norm2=None, stream=None):

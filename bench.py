@@ -191,8 +191,11 @@ def measured_peaks():
 
 
 def kernel_source_sha():
-    src = open(os.path.join(ROOT, "paper_1003_2680_gb300", "csrc", "selm_kernels.cu"), "rb").read()
-    return hashlib.sha256(src).hexdigest()[:16]
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1003_2680_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_class, n):

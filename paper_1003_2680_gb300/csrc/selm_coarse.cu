@@ -35,7 +35,18 @@ namespace cg = cooperative_groups;
 namespace selm {
 namespace {
 
-constexpr int kEngThreads = 512;
+// Threads per CTA: FP32 fits 1024 threads in the 64-register budget; the
+// FP64 variant needs more registers per thread and runs 512.
+template <typename T>
+struct EngThreads;
+template <>
+struct EngThreads<float> {
+  static constexpr int value = 1024;
+};
+template <>
+struct EngThreads<double> {
+  static constexpr int value = 512;
+};
 
 __device__ __forceinline__ uint4 eng_philox10(uint4 c, uint32_t k0, uint32_t k1) { return philox4x32_10(c, k0, k1); }
 
@@ -403,7 +414,7 @@ __device__ void stage_tables(const EngLevel<T>& L, int z0, int z1, T* tab, EngCo
 }
 
 template <typename T, bool NOISE>
-__global__ void __launch_bounds__(kEngThreads, 1) k_coarse_engine(const EngParams<T>* __restrict__ P, EngRun run) {
+__global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const EngParams<T>* __restrict__ P, EngRun run) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ EngLevel<T> sl[2];
   __shared__ EngColour scol[2][kEngMaxColours];
@@ -668,7 +679,7 @@ bool plan_coarse_engine(const LevelDev* levs, int L, void* const* gb, void* cons
         }
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(cand.cluster * levs[0].ncomp);
-        cfg.blockDim = dim3(kEngThreads);
+        cfg.blockDim = dim3(EngThreads<T>::value);
         cfg.dynamicSmemBytes = cand.smem_bytes;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -713,7 +724,7 @@ cudaError_t launch_coarse_engine(const EnginePlanT<T>& plan, int mu1, int mu2, i
   EngRun run{mu1, mu2, coarse_mode, key, cyc};
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(plan.cluster * plan.params.ncomp);
-  cfg.blockDim = dim3(kEngThreads);
+  cfg.blockDim = dim3(EngThreads<T>::value);
   cfg.dynamicSmemBytes = plan.smem_bytes;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];

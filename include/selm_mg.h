@@ -95,7 +95,10 @@ const char* selm_mg_last_error(const selm_mg* h);
 /* ---- the SELM operations (Algorithm 4) ---------------------------------- */
 
 /* U = M F = Gamma P~ A^-1 P~ Gamma^T F (Alg. 4 step 2): spread, project,
-   FAC-solve to tol (Algorithm 1), project, interpolate.  X, F: [np][dim]
+   FAC-solve to tol (Algorithm 1), project, interpolate.  Each projection's
+   pressure solve starts from the pressure of the same projection in the
+   previous call (Algorithm 1 takes an initial value); selm_mg_project alone
+   starts from zero.  X, F: [np][dim]
    positions and forces; U: [np][dim] output.  cycles_out / resid_out are
    optional HOST pointers (synchronises the stream when given). */
 selm_status selm_mg_solve(selm_mg* h, int np, const double* X, const double* F, double* U,

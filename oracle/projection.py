@@ -49,22 +49,32 @@ def divergence_transpose(phi, dim):
 
 
 class Projector:
+    """P~ w with the pressure solved by the FAC iteration (Algorithm 1).
+
+    Algorithm 1 starts from a given initial value.  ``slot=None`` starts from
+    zero; an integer slot starts from the pressure that slot produced last
+    time (a warm start for repeated projections of slowly changing fields)."""
+
     def __init__(self, n, dim, tol=1e-12, levels=None):
         self.dim = dim
         self.psys = grid.pressure_system(n, dim, levels)
         self.coarsest = multigrid.Coarsest(self.psys)
         self.tol = tol
+        self.warm = {}
 
-    def pressure(self, w):
+    def pressure(self, w, slot=None):
         div = divergence(w, self.dim)
         # D^ w sums to zero exactly (flux form); removing the rounding-level
         # mean keeps the singular Neumann system consistent.
         rhs = [div - np.mean(div)]
+        v0 = None if slot is None or slot not in self.warm else [self.warm[slot]]
         phi, cycles, rel = multigrid.solve(self.psys, rhs, tol=self.tol, max_cycles=200,
-                                           coarsest=self.coarsest)
+                                           coarsest=self.coarsest, v0=v0)
+        if slot is not None:
+            self.warm[slot] = phi[0].copy()
         return phi[0], cycles
 
-    def project(self, w):
-        phi, _ = self.pressure(w)
+    def project(self, w, slot=None):
+        phi, _ = self.pressure(w, slot)
         g = divergence_transpose(phi, self.dim)
         return [a - b for a, b in zip(w, g)]

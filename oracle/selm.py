@@ -37,12 +37,14 @@ class Model:
         self.xi = self.sys.zeros(0)        # persistent chain state
         self.cycle = 0                      # chain step counter (Philox counter words 2-3)
 
-    def P(self, w):
-        return w if self.proj is None else self.proj.project(w)
+    # projection slots (warm starts of the pressure solve): 0 = Gamma^T F,
+    # 1 = the step's combined field, 2 = the sampled field
+    def P(self, w, slot=None):
+        return w if self.proj is None else self.proj.project(w, slot)
 
     # -- deterministic part ---------------------------------------------
     def rhs(self, X, F):
-        return self.P(coupling.spread(self.sys, F, X))
+        return self.P(coupling.spread(self.sys, F, X), 0)
 
     def solve_field(self, b):
         u, cycles, rel = multigrid.solve(self.sys, b, tol=self.tol, mu1=self.mu1, mu2=self.mu2,
@@ -51,7 +53,7 @@ class Model:
 
     def mobility_apply(self, X, F):
         u, cycles, rel = self.solve_field(self.rhs(X, F))
-        return coupling.interpolate(self.sys, self.P(u), X), cycles, rel
+        return coupling.interpolate(self.sys, self.P(u, 1), X), cycles, rel
 
     def mobility_matrix(self, X):
         """Dense M (columns = responses to unit forces), d np x d np."""
@@ -77,7 +79,7 @@ class Model:
 
     def thermal(self, X, ncycles):
         self.chain_cycles(ncycles)
-        g = coupling.interpolate(self.sys, self.P(self.xi), X)
+        g = coupling.interpolate(self.sys, self.P(self.xi, 2), X)
         return np.sqrt(2.0 * self.kT) * g
 
     # -- dynamics -------------------------------------------------------
@@ -96,5 +98,5 @@ class Model:
         a = dt
         c = np.sqrt(2.0 * self.kT * dt)
         w = [a * uu + c * xx for uu, xx in zip(u, self.xi)]
-        V = coupling.interpolate(self.sys, self.P(w), X)
+        V = coupling.interpolate(self.sys, self.P(w, 1), X)
         return self.wrap_reflect(X + V), cycles

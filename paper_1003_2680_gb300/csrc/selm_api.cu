@@ -73,7 +73,9 @@ struct selm_mg {
   double* xi = nullptr;     // chain state (FP64)
   double* bvel = nullptr;   // right-hand side (FP64)
   double* wcomb = nullptr;  // combined field for the particle update (FP64)
-  double* phi = nullptr;    // pressure (FP64)
+  double* phi = nullptr;    // pressure (FP64), 3 slots: warm starts of the projections
+                            // of Gamma^T F (0), of the step's combined field (1), of the
+                            // sampled field (2)
   double* prhs = nullptr;   // pressure right-hand side (FP64)
   double* red = nullptr;    // reduction slots
   unsigned long long* cyc = nullptr;  // [0] chain counter, [1] stage-call counter
@@ -209,7 +211,7 @@ void make_plan(const selm_mg_desc& d, const Sys& vel, const Sys* pres, int esize
   p->wcomb_off = p->lay.add(nv * 8);
   if (pres) {
     const size_t np_ = (size_t)pres->host.level_size(0);
-    p->phi_off = p->lay.add(np_ * 8);
+    p->phi_off = p->lay.add(3 * np_ * 8);
     p->prhs_off = p->lay.add(np_ * 8);
   }
   p->eng_off[0] = p->lay.add(kEngParamBytes);
@@ -407,18 +409,22 @@ selm_status fac_solve(selm_mg* h, Sys& s, double* z, const double* b, double tol
   }
 }
 
-selm_status project(selm_mg* h, double* w, int* cycles, cudaStream_t st) {
+// w <- P~ w.  The pressure Poisson problem (D^ D^T) phi = D^ w is solved by
+// the FAC iteration from an initial value (Algorithm 1 takes one): slot < 0
+// starts from zero; slots 0..2 start from that slot's previous pressure.
+selm_status project(selm_mg* h, double* w, int* cycles, cudaStream_t st, int slot = -1) {
   *cycles = 0;
   if (!h->has_pres) return SELM_OK;
   const long long np_ = h->pres.lev[0].size;
+  double* phi = h->phi + (size_t)(slot < 0 ? 0 : slot) * np_;
   CK(cudaMemsetAsync(h->red + 2, 0, sizeof(double), st));
   CK(launch_divergence(h->vel.lev[0], w, h->prhs, h->red + 2, st));
   CK(launch_sub_mean(np_, h->prhs, h->red + 2, st));
-  CK(cudaMemsetAsync(h->phi, 0, (size_t)np_ * sizeof(double), st));
+  if (slot < 0) CK(cudaMemsetAsync(phi, 0, (size_t)np_ * sizeof(double), st));
   double rel = 0.0;
-  selm_status r = fac_solve(h, h->pres, h->phi, h->prhs, h->d.proj_tol, h->d.max_cycles, cycles, &rel, st);
+  selm_status r = fac_solve(h, h->pres, phi, h->prhs, h->d.proj_tol, h->d.max_cycles, cycles, &rel, st);
   if (r != SELM_OK) return r;
-  CK(launch_grad_sub(h->vel.lev[0], w, h->phi, st));
+  CK(launch_grad_sub(h->vel.lev[0], w, phi, st));
   return SELM_OK;
 }
 
@@ -535,6 +541,8 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
   const size_t nv = (size_t)h->vel.lev[0].size * sizeof(double);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(h->xi, 0, nv, st);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(h->u, 0, nv, st);
+  if (ce == cudaSuccess && h->has_pres)
+    ce = cudaMemsetAsync(h->phi, 0, 3 * (size_t)h->pres.lev[0].size * sizeof(double), st);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(h->cyc, 0, 4 * sizeof(unsigned long long), st);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // host tables must outlive the copies
   if (ce != cudaSuccess) {
@@ -781,7 +789,7 @@ selm_status selm_mg_solve(selm_mg* h, int np, const double* X, const double* F, 
   CK(cudaMemsetAsync(h->bvel, 0, (size_t)nv * sizeof(double), st));
   CK(launch_spread(h->vel.lev[0], h->d.n, h->d.dim, np, X, F, h->bvel, st));
   int pc = 0, pc2 = 0;
-  selm_status r = project(h, h->bvel, &pc, st);
+  selm_status r = project(h, h->bvel, &pc, st, 0);
   if (r != SELM_OK) return r;
   CK(cudaMemsetAsync(h->u, 0, (size_t)nv * sizeof(double), st));
   int cycles = 0;
@@ -794,7 +802,7 @@ selm_status selm_mg_solve(selm_mg* h, int np, const double* X, const double* F, 
   const double* field = h->u;
   if (h->has_pres) {
     CK(cudaMemcpyAsync(h->wcomb, h->u, (size_t)nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    r = project(h, h->wcomb, &pc2, st);
+    r = project(h, h->wcomb, &pc2, st, 1);
     if (r != SELM_OK) return r;
     field = h->wcomb;
   }
@@ -813,7 +821,7 @@ selm_status selm_mg_sample(selm_mg* h, int np, const double* X, int ncycles, dou
   if (xi_out) CK(cudaMemcpyAsync(xi_out, h->xi, (size_t)nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(launch_axpby(nv, std::sqrt(2.0 * h->d.kT), h->xi, 0.0, h->xi, h->wcomb, st));
   int pc = 0;
-  r = project(h, h->wcomb, &pc, st);
+  r = project(h, h->wcomb, &pc, st, 2);
   if (r != SELM_OK) return r;
   CK(launch_interp(h->vel.lev[0], h->d.n, h->d.dim, np, X, h->wcomb, g, st));
   return SELM_OK;
@@ -834,7 +842,7 @@ selm_status selm_mg_step(selm_mg* h, int np, double* X, const double* F, double 
     CK(launch_spread(h->vel.lev[0], h->d.n, h->d.dim, np, X, F, h->bvel, st));
     int pc = 0, pc2 = 0, cycles = 0;
     double rel = 0.0;
-    selm_status r = project(h, h->bvel, &pc, st);
+    selm_status r = project(h, h->bvel, &pc, st, 0);
     if (r != SELM_OK) return r;
     CK(cudaMemsetAsync(h->u, 0, (size_t)nv * sizeof(double), st));
     r = fac_solve(h, h->vel, h->u, h->bvel, h->d.tol, h->d.max_cycles, &cycles, &rel, st);
@@ -843,7 +851,7 @@ selm_status selm_mg_step(selm_mg* h, int np, double* X, const double* F, double 
     r = chain_cycles(h, ncycles_per_step, st);
     if (r != SELM_OK) return r;
     CK(launch_axpby(nv, dt, h->u, std::sqrt(2.0 * h->d.kT * dt), h->xi, h->wcomb, st));
-    r = project(h, h->wcomb, &pc2, st);
+    r = project(h, h->wcomb, &pc2, st, 1);
     if (r != SELM_OK) return r;
     h->last_proj_cycles = pc + pc2;
     CK(launch_interp(h->vel.lev[0], h->d.n, h->d.dim, np, X, h->wcomb, h->V, st));

@@ -232,7 +232,7 @@ def test_projection(prec, dim, n, levels):
 def test_mobility_solve(prec, project):
     p, dt, tol = PRECS[prec]
     n, dim = 32, 2
-    m = S.SelmMG(dim=dim, n=n, levels=5, precision=p, projection=project, mu=1.3, tol=1e-11)
+    m = S.SelmMG(dim=dim, n=n, levels=5, precision=p, projection=project, mu=1.3, tol=1e-11, proj_tol=1e-12)
     om = oselm.Model(n, dim, mu=1.3, levels=5, project=bool(project), tol=1e-11)
     X0 = selm_inputs.particles(16, dim, n, seed=9)
     F0 = selm_inputs.forces(16, dim, seed=9)
@@ -267,7 +267,8 @@ def test_config1_chain_1000_cycles_fp64():
 def test_em_steps(prec, project):
     p, dt_, tol = PRECS[prec]
     n, dim = 16, 3
-    m = S.SelmMG(dim=dim, n=n, levels=3, precision=p, projection=project, kT=0.7, seed=5, instance=2)
+    m = S.SelmMG(dim=dim, n=n, levels=3, precision=p, projection=project, kT=0.7, seed=5, instance=2,
+                 proj_tol=1e-12)
     om = oselm.Model(n, dim, kT=0.7, levels=3, project=bool(project), seed=5, instance=2)
     X0 = selm_inputs.particles(24, dim, n, seed=3)
     F0 = selm_inputs.forces(24, dim, seed=3)

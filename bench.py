@@ -61,6 +61,9 @@ def parse_args():
     p.add_argument("--particles", type=int, default=N_PARTICLES)
     p.add_argument("--no-projection", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="channel128", choices=["channel128", "batched"],
+                   help="channel128: the headline line; batched: 64 uneven systems, batched vs plain")
+    p.add_argument("--systems", type=int, default=64)
     return p.parse_args()
 
 
@@ -244,6 +247,86 @@ def sweep_bytes_per_launch(S, h, kernel_class):
 # ---------------------------------------------------------------------------
 # main GPU arm
 # ---------------------------------------------------------------------------
+def run_batched(args):
+    """64 independent 3-D channel systems, edges drawn from {32,48,64,96,128},
+    64..2048 particles (log-uniform), kT ~ U[0.5, 2], seed i.  Batched form
+    (graphs over all systems) against the plain per-instance loop."""
+    import numpy as np
+    import torch
+    from paper_1003_2680_gb300 import _build
+    _build.build()
+    from paper_1003_2680_gb300 import selm as S
+    import selm_inputs
+
+    nsys = args.systems
+    edges = selm_inputs.batched_edges(nsys, seed=0)
+    rng = np.random.default_rng([0, 505])
+    nps = [int(round(x)) for x in np.exp(rng.uniform(np.log(64), np.log(2048), size=nsys))]
+    kTs = [float(x) for x in rng.uniform(0.5, 2.0, size=nsys)]
+    descs = [S.make_desc(dim=3, n=e, kT=kT, precision=S.SELM_FP32_REFINE64, seed=i, instance=i, max_particles=2048)
+             for i, (e, kT) in enumerate(zip(edges, kTs))]
+    X0 = [selm_inputs.particles(npart, 3, e, seed=i) for i, (npart, e) in enumerate(zip(nps, edges))]
+    F0 = [selm_inputs.forces(npart, 3, seed=i) for i, npart in enumerate(nps)]
+    cells = [e ** 3 for e in edges]
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = [fn() for _ in range(steps)]
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3, out
+
+    # plain: one system after the other through selm_mg_step
+    handles = [S.selm_mg_create(d) for d in descs]
+    Xp = [torch.tensor(x, device="cuda") for x in X0]
+    Fp = [torch.tensor(f, device="cuda") for f in F0]
+
+    def plain_step():
+        cyc = 0
+        for i, h in enumerate(handles):
+            S.selm_mg_step(h, Xp[i], Fp[i], DT, 1, SAMPLE_CYCLES)
+            cyc += cells[i] * (S.selm_mg_stats(h)[0] + SAMPLE_CYCLES)
+        return cyc
+
+    for _ in range(max(1, args.warmup - 2)):
+        plain_step()
+    t_plain, cyc_plain = timed(plain_step, args.steps)
+    for h in handles:
+        S.selm_mg_destroy(h)
+    torch.cuda.synchronize()
+
+    b = S.selm_batch_create(descs)
+    chosen = S.selm_batch_autotune(b)
+    Xb = [torch.tensor(x, device="cuda") for x in X0]
+    Fb = [torch.tensor(f, device="cuda") for f in F0]
+
+    def batch_step():
+        cy = S.selm_batch_step(b, Xb, Fb, DT, 1, SAMPLE_CYCLES)
+        return sum(c * (max(cy) + SAMPLE_CYCLES) for c in cells)
+
+    for _ in range(max(1, args.warmup - 2)):
+        batch_step()
+    t_batch, cyc_batch = timed(batch_step, args.steps)
+    S.selm_batch_destroy(b)
+    line = {
+        "metric": "batched stochastic-MG: system-steps/s and cell-cycles/s, batched vs plain per-instance",
+        "value": nsys * args.steps / t_batch, "unit": "system-steps/s", "higher_is_better": True,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": "f32+f64",
+        "config": {"workload": f"{nsys} independent 3-D channel systems, edges from {{32,48,64,96,128}}, "
+                               f"64-2048 particles, kT in [0.5,2], one Euler-Maruyama step (solve to 1e-10 + "
+                               f"{SAMPLE_CYCLES} stochastic cycles) per system per step",
+                   "edges": edges, "engine_cluster": chosen},
+        "batched": {"system_steps_per_s": nsys * args.steps / t_batch, "cell_cycles_per_s": sum(cyc_batch) / t_batch,
+                    "ms_per_step": 1e3 * t_batch / args.steps},
+        "plain": {"system_steps_per_s": nsys * args.steps / t_plain, "cell_cycles_per_s": sum(cyc_plain) / t_plain,
+                  "ms_per_step": 1e3 * t_plain / args.steps},
+        "speedup_steps": t_plain / t_batch,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -253,6 +336,9 @@ def main():
         run_reference(args, rank, world)
         return
     assert args.warmup >= 3, "at least 3 warm-up steps"
+    if args.workload == "batched":
+        run_batched(args)
+        return
 
     import numpy as np
     import torch

@@ -140,7 +140,10 @@ selm_status selm_mg_set_cycle(selm_mg* h, uint64_t cycle);
    finest with the cluster-resident coarse engine (one thread-block cluster
    per component, colour passes separated by cluster barriers); 0 selects one
    launch per colour pass.  Both give the same result up to rounding. */
-enum { SELM_OPT_COARSE_ENGINE = 1 };
+enum { SELM_OPT_COARSE_ENGINE = 1, SELM_OPT_ENGINE_CLUSTER = 2 };
+/* SELM_OPT_ENGINE_CLUSTER: largest thread-block cluster the coarse engine may
+   use (1..16; 0 = the largest that fits).  Re-plans the engine; synchronises
+   the legacy default stream. */
 selm_status selm_mg_set_option(selm_mg* h, int option, int value);
 /* Coarse engine of `system`: first level it covers (-1 = not used), cluster
    size and dynamic shared memory per CTA. */
@@ -218,6 +221,31 @@ selm_status selm_mg_em_update(selm_mg* h, int np, double* X, const double* V, vo
    but calls that overlap on the GPU (other streams, other threads) race. */
 selm_status selm_mg_vcycle_static(const selm_mg_desc* desc, void* v, const void* b, uint64_t cycle,
                                   int noise, void* stream);
+
+/* ---- batched form ---------------------------------------------------------
+   Many independent systems (uneven sizes, own seeds and kT) advanced
+   together.  Each phase of a step (spread + initial residual; one V-cycle of
+   every solve; the stochastic chain cycles; combine + interpolate + move) is a
+   CUDA graph with one branch per system, captured on the first call with a
+   given set of particle arrays and dt, and replayed afterwards; the FAC solve
+   (Algorithm 1) takes one graph launch per V-cycle for all systems and stops
+   when every system meets its tolerance (systems that met it earlier take
+   the extra cycles).  Systems must use SELM_PROJ_NONE.  Profiling
+   (selm_profile_enable) must be off while graphs are captured. */
+typedef struct selm_batch selm_batch;
+selm_status selm_batch_create(int nsys, const selm_mg_desc* descs, void* stream, selm_batch** out);
+selm_status selm_batch_destroy(selm_batch* b);
+/* Handle of system i (for layouts, chain state, statistics); owned by the batch. */
+selm_mg* selm_batch_system(selm_batch* b, int i);
+const char* selm_batch_last_error(const selm_batch* b);
+/* nsteps Euler-Maruyama steps for every system: np[i], X[i] (device,
+   [np][dim], updated in place), F[i]; solve_cycles (optional host [nsys])
+   receives the FAC cycles each system needed in the last step. */
+selm_status selm_batch_step(selm_batch* b, const int* np, double* const* X, const double* const* F, double dt,
+                            int nsteps, int ncycles_per_step, int* solve_cycles, void* stream);
+/* Times the batched V-cycle for engine cluster sizes 16, 8 and 4 and keeps the
+   fastest; *chosen_cluster receives it. */
+selm_status selm_batch_autotune(selm_batch* b, int* chosen_cluster, void* stream);
 
 /* ---- measurement --------------------------------------------------------
    Process-wide kernel accounting.  selm_kernel_launches() counts every

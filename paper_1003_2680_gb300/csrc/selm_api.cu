@@ -17,77 +17,11 @@
 
 #include "../../include/selm_mg.h"
 #include "selm_coarse.h"
+#include "selm_handle.h"
 #include "selm_internal.h"
 #include "selm_launch.h"
 
 using namespace selm;
-
-namespace {
-
-struct Sys {
-  HostSystem host;
-  LevelDev lev[kMaxLevels];
-  void* v[kMaxLevels] = {};
-  void* b[kMaxLevels] = {};
-  void* t[kMaxLevels] = {};
-  int levels = 0;
-  int ncomp = 0;
-  EnginePlanT<float> engf;    // cluster-resident coarse levels (FP32 inner)
-  EnginePlanT<double> engd;   // (FP64 inner)
-  bool use_engine = true;
-};
-
-template <typename T>
-EnginePlanT<T>& eng_of(Sys& s);
-template <>
-EnginePlanT<float>& eng_of<float>(Sys& s) {
-  return s.engf;
-}
-template <>
-EnginePlanT<double>& eng_of<double>(Sys& s) {
-  return s.engd;
-}
-
-// Byte layout of the workspace.
-struct Layout {
-  size_t total = 0;
-  size_t add(size_t bytes) {
-    size_t off = (total + 255) & ~(size_t)255;
-    total = off + bytes;
-    return off;
-  }
-};
-
-}  // namespace
-
-struct selm_mg {
-  selm_mg_desc d{};
-  int mu1 = 2, mu2 = 2;
-  int esize = 8;
-  Sys vel, pres;
-  bool has_pres = false;
-  Key key{};
-  char* ws = nullptr;
-  size_t ws_bytes = 0;
-  double* u = nullptr;      // solution of the deterministic solve (FP64)
-  double* xi = nullptr;     // chain state (FP64)
-  double* bvel = nullptr;   // right-hand side (FP64)
-  double* wcomb = nullptr;  // combined field for the particle update (FP64)
-  double* phi = nullptr;    // pressure (FP64), 3 slots: warm starts of the projections
-                            // of Gamma^T F (0), of the step's combined field (1), of the
-                            // sampled field (2)
-  double* prhs = nullptr;   // pressure right-hand side (FP64)
-  double* red = nullptr;    // reduction slots
-  unsigned long long* cyc = nullptr;  // [0] chain counter, [1] stage-call counter
-  double* V = nullptr;      // particle scratch [max_particles][3]
-  double* Xs = nullptr;     // device copies of host particle arrays (selm_mg_step_host)
-  double* Fs = nullptr;
-  double* host_red = nullptr;  // pinned
-  uint64_t cycle = 0;
-  int last_solve_cycles = 0, last_proj_cycles = 0;
-  long long total_vcycles = 0;
-  std::string err;
-};
 
 namespace {
 
@@ -292,6 +226,10 @@ Sys* sys_of(selm_mg* h, int system) {
   return nullptr;
 }
 
+}  // namespace
+
+namespace selm {
+
 // ---- V-cycle (Algorithm 3) -------------------------------------------------
 template <typename T>
 selm_status vcycle_t(selm_mg* h, Sys& s, int l, T* v0, const T* b0, bool noise, const unsigned long long* cyc,
@@ -347,6 +285,10 @@ selm_status outer_update(selm_mg* h, Sys& s, double* z, const void* d, cudaStrea
     CK(launch_outer_update<double>(s.lev[0].size, z, (const double*)d, st));
   return SELM_OK;
 }
+
+}  // namespace selm
+
+namespace {
 
 // One FAC iteration (Algorithm 1) with the internal level-0 buffers.
 selm_status fac_cycle(selm_mg* h, Sys& s, double* z, const double* b, bool noise, const unsigned long long* cyc,
@@ -448,6 +390,24 @@ bool check_particles(selm_mg* h, int np, const void* X) {
 
 }  // namespace
 
+namespace selm {
+selm_status replan_engine(selm_mg* h, int cluster, cudaStream_t st) {
+  for (Sys* sy : {&h->vel, h->has_pres ? &h->pres : (Sys*)nullptr}) {
+    if (!sy || !sy->eng_dev) continue;
+    CK(cudaStreamSynchronize(st));   // no launch may still read the old plan
+    sy->engine_cluster = cluster;
+    bool ok;
+    if (h->esize == 4)
+      ok = plan_coarse_engine<float>(sy->lev, sy->levels, sy->b, sy->v, sy->t, sy->eng_dev, st, &sy->engf, cluster);
+    else
+      ok = plan_coarse_engine<double>(sy->lev, sy->levels, sy->b, sy->v, sy->t, sy->eng_dev, st, &sy->engd, cluster);
+    cudaGetLastError();
+    (void)ok;   // without a plan the per-pass path runs
+  }
+  return SELM_OK;
+}
+}  // namespace selm
+
 extern "C" {
 
 size_t selm_mg_footprint(const selm_mg_desc* desc) {
@@ -519,6 +479,7 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
     Sys* sy = si == 0 ? &h->vel : (h->has_pres ? &h->pres : nullptr);
     if (!sy) continue;
     void* dp = h->ws + p.eng_off[si];
+    sy->eng_dev = dp;
     if (h->esize == 4)
       plan_coarse_engine<float>(sy->lev, sy->levels, sy->b, sy->v, sy->t, dp, st, &sy->engf);
     else
@@ -541,6 +502,7 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
   const size_t nv = (size_t)h->vel.lev[0].size * sizeof(double);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(h->xi, 0, nv, st);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(h->u, 0, nv, st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->bvel, 0, nv, st);
   if (ce == cudaSuccess && h->has_pres)
     ce = cudaMemsetAsync(h->phi, 0, 3 * (size_t)h->pres.lev[0].size * sizeof(double), st);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(h->cyc, 0, 4 * sizeof(unsigned long long), st);
@@ -616,12 +578,17 @@ selm_status selm_mg_set_cycle(selm_mg* h, uint64_t cycle) {
   return SELM_OK;
 }
 
+
 selm_status selm_mg_set_option(selm_mg* h, int option, int value) {
   if (!h) return SELM_EINVAL;
   if (option == SELM_OPT_COARSE_ENGINE) {
     h->vel.use_engine = value != 0;
     h->pres.use_engine = value != 0;
     return SELM_OK;
+  }
+  if (option == SELM_OPT_ENGINE_CLUSTER) {
+    if (value < 0 || value > 16) return SELM_EINVAL;
+    return replan_engine(h, value, nullptr);
   }
   return SELM_EINVAL;
 }

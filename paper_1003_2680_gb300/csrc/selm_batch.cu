@@ -1,0 +1,375 @@
+// Batched form: many independent channel systems of uneven sizes advanced
+// together (Algorithm 4 for each system).
+//
+// Each phase of an Euler-Maruyama step is captured once as a CUDA graph whose
+// branches are the systems (one forked stream per system during capture), so
+// one graph launch runs that phase for every system and the GPU schedules the
+// systems' kernels -- in particular their cluster-resident coarse engines,
+// each of which fills only part of the GPU -- side by side.  The FAC solve
+// (Algorithm 1) runs one graph launch per V-cycle for all systems; that graph
+// ends with each system's next residual norm copied to pinned host memory,
+// from which the host decides whether another cycle is needed.  Systems that
+// have already met their tolerance take the extra cycles of the slowest
+// system (their iterates only get more accurate).
+//
+// The engine's thread-block cluster size is chosen by an autotuner that times
+// the batched V-cycle graph for each candidate.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/selm_mg.h"
+#include "selm_handle.h"
+#include "selm_launch.h"
+
+using namespace selm;
+
+struct selm_batch {
+  int n = 0;
+  std::vector<selm_mg*> sys;
+  std::vector<cudaStream_t> branch;   // capture branches, one per system
+  cudaStream_t origin = nullptr;      // capture origin
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  double* host_norm = nullptr;        // pinned [n][2]: ||r||^2, ||b||^2
+  // captured graphs
+  cudaGraphExec_t g_start = nullptr;  // spread + initial residual and norms
+  cudaGraphExec_t g_cycle = nullptr;  // one V-cycle + update + next residual norm
+  cudaGraphExec_t g_chain = nullptr;  // k stochastic cycles of every chain
+  cudaGraphExec_t g_finish = nullptr; // combine, interpolate, move particles
+  // arguments baked into the graphs
+  std::vector<int> np;
+  std::vector<double*> X;
+  std::vector<const double*> F;
+  double dt = -1.0;
+  int kchain = -1;
+  int cluster = 0;
+  std::string err;
+};
+
+namespace {
+
+#define BCK(call)                                                 \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) {                                      \
+      b->err = std::string(#call) + ": " + cudaGetErrorString(e_); \
+      return SELM_ECUDA;                                          \
+    }                                                             \
+  } while (0)
+
+#define BST(expr)                      \
+  do {                                 \
+    selm_status s_ = (expr);           \
+    if (s_ != SELM_OK) return s_;      \
+  } while (0)
+
+// Inside capture lambdas: record the failing call on the batch.
+#define LCK(call)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      b->err = std::string(#call) + " (system " + std::to_string(i) + "): " + cudaGetErrorString(e_); \
+      return SELM_ECUDA;                                                            \
+    }                                                                               \
+  } while (0)
+#define LST(expr)                                                                     \
+  do {                                                                                \
+    selm_status s_ = (expr);                                                          \
+    if (s_ != SELM_OK) {                                                              \
+      b->err = std::string(#expr) + " (system " + std::to_string(i) + "): " + b->sys[i]->err; \
+      return s_;                                                                      \
+    }                                                                                 \
+  } while (0)
+
+void drop_graphs(selm_batch* b) {
+  for (cudaGraphExec_t* g : {&b->g_start, &b->g_cycle, &b->g_chain, &b->g_finish}) {
+    if (*g) cudaGraphExecDestroy(*g);
+    *g = nullptr;
+  }
+}
+
+// Captures fn(i, stream_i) for every system as parallel branches of one graph.
+template <typename Fn>
+selm_status capture(selm_batch* b, Fn fn, cudaGraphExec_t* out) {
+  if (*out) {
+    cudaGraphExecDestroy(*out);
+    *out = nullptr;
+  }
+  BCK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+  selm_status st = SELM_OK;
+  cudaError_t ce = cudaEventRecord(b->fork, b->origin);
+  for (int i = 0; i < b->n && ce == cudaSuccess && st == SELM_OK; ++i) {
+    ce = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+    if (ce != cudaSuccess) break;
+    st = fn(i, b->branch[i]);
+    if (st != SELM_OK) break;
+    ce = cudaEventRecord(b->join[i], b->branch[i]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->origin, b->join[i], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce2 = cudaStreamEndCapture(b->origin, &graph);
+  if (st != SELM_OK || ce != cudaSuccess || ce2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (st == SELM_OK) {
+      b->err = std::string("graph capture failed: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ce2);
+      st = SELM_ECUDA;
+    }
+    return st;
+  }
+  ce = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    b->err = std::string("graph instantiation failed: ") + cudaGetErrorString(ce);
+    return SELM_ECUDA;
+  }
+  return SELM_OK;
+}
+
+// Residual of system i's solve and its squared norm copied to pinned memory.
+selm_status residual_norm(selm_batch* b, int i, cudaStream_t s) {
+  selm_mg* h = b->sys[i];
+  LCK(cudaMemsetAsync(h->red + 1, 0, sizeof(double), s));
+  LST(outer_residual(h, h->vel, h->u, h->bvel, h->vel.b[0], h->red + 1, s));
+  LCK(cudaMemcpyAsync(b->host_norm + 2 * i, h->red + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return SELM_OK;
+}
+
+selm_status build_cycle_graph(selm_batch* b) {
+  return capture(
+      b,
+      [&](int i, cudaStream_t s) -> selm_status {
+        selm_mg* h = b->sys[i];
+        const size_t inner = (size_t)h->vel.lev[0].size * h->esize;
+        LCK(cudaMemsetAsync(h->vel.v[0], 0, inner, s));
+        LST(vcycle(h, h->vel, h->vel.v[0], h->vel.b[0], false, h->cyc + 1, s));
+        LST(outer_update(h, h->vel, h->u, h->vel.v[0], s));
+        return residual_norm(b, i, s);
+      },
+      &b->g_cycle);
+}
+
+selm_status build_graphs(selm_batch* b, const int* np, double* const* X, const double* const* F, double dt,
+                         int kchain) {
+  drop_graphs(b);
+  for (int i = 0; i < b->n; ++i) {
+    b->np[i] = np[i];
+    b->X[i] = X[i];
+    b->F[i] = F[i];
+  }
+  b->dt = dt;
+  b->kchain = kchain;
+  BST(capture(
+      b,
+      [&](int i, cudaStream_t s) -> selm_status {
+        selm_mg* h = b->sys[i];
+        const size_t nv = (size_t)h->vel.lev[0].size * sizeof(double);
+        LCK(cudaMemsetAsync(h->bvel, 0, nv, s));
+        LCK(launch_spread(h->vel.lev[0], h->d.n, h->d.dim, np[i], X[i], F[i], h->bvel, s));
+        LCK(cudaMemsetAsync(h->u, 0, nv, s));
+        LCK(cudaMemsetAsync(h->red, 0, sizeof(double), s));
+        LCK(launch_norm2(h->vel.lev[0].size, h->bvel, h->red, s));
+        LCK(cudaMemcpyAsync(b->host_norm + 2 * i + 1, h->red, sizeof(double), cudaMemcpyDeviceToHost, s));
+        return residual_norm(b, i, s);
+      },
+      &b->g_start));
+  BST(build_cycle_graph(b));
+  BST(capture(
+      b,
+      [&](int i, cudaStream_t s) -> selm_status {
+        selm_mg* h = b->sys[i];
+        const size_t inner = (size_t)h->vel.lev[0].size * h->esize;
+        for (int q = 0; q < kchain; ++q) {
+          LST(outer_residual(h, h->vel, h->xi, nullptr, h->vel.b[0], nullptr, s));
+          LCK(cudaMemsetAsync(h->vel.v[0], 0, inner, s));
+          LST(vcycle(h, h->vel, h->vel.v[0], h->vel.b[0], true, h->cyc + 0, s));
+          LST(outer_update(h, h->vel, h->xi, h->vel.v[0], s));
+          LCK(launch_inc_u64(h->cyc + 0, s));
+        }
+        return SELM_OK;
+      },
+      &b->g_chain));
+  BST(capture(
+      b,
+      [&](int i, cudaStream_t s) -> selm_status {
+        selm_mg* h = b->sys[i];
+        const long long nv = h->vel.lev[0].size;
+        LCK(launch_axpby(nv, dt, h->u, std::sqrt(2.0 * h->d.kT * dt), h->xi, h->wcomb, s));
+        LCK(launch_interp(h->vel.lev[0], h->d.n, h->d.dim, np[i], X[i], h->wcomb, h->V, s));
+        LCK(launch_em(np[i], h->d.dim, X[i], h->V, s));
+        return SELM_OK;
+      },
+      &b->g_finish));
+  return SELM_OK;
+}
+
+bool same_args(const selm_batch* b, const int* np, double* const* X, const double* const* F, double dt,
+               int kchain) {
+  if (!b->g_start || b->dt != dt || b->kchain != kchain) return false;
+  for (int i = 0; i < b->n; ++i)
+    if (b->np[i] != np[i] || b->X[i] != X[i] || b->F[i] != F[i]) return false;
+  return true;
+}
+
+bool all_converged(const selm_batch* b, std::vector<int>& cycles, int cyc) {
+  bool all = true;
+  for (int i = 0; i < b->n; ++i) {
+    const double rn2 = b->host_norm[2 * i], bn2 = b->host_norm[2 * i + 1];
+    const bool ok = bn2 == 0.0 || std::sqrt(rn2) <= b->sys[i]->d.tol * std::sqrt(bn2);
+    if (ok && cycles[i] < 0) cycles[i] = cyc;
+    all = all && ok;
+  }
+  return all;
+}
+
+}  // namespace
+
+extern "C" {
+
+selm_status selm_batch_create(int nsys, const selm_mg_desc* descs, void* stream, selm_batch** out) {
+  if (nsys < 1 || !descs || !out) return SELM_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < nsys; ++i)
+    if (descs[i].projection != SELM_PROJ_NONE) {
+      std::fprintf(stderr, "selm_batch_create: the batched form runs SELM_PROJ_NONE systems\n");
+      return SELM_EINVAL;
+    }
+  selm_batch* b = new (std::nothrow) selm_batch();
+  if (!b) return SELM_ENOMEM;
+  b->n = nsys;
+  b->np.assign(nsys, 0);
+  b->X.assign(nsys, nullptr);
+  b->F.assign(nsys, nullptr);
+  for (int i = 0; i < nsys; ++i) {
+    selm_mg* h = nullptr;
+    selm_status st = selm_mg_create(&descs[i], stream, &h);
+    if (st != SELM_OK) {
+      selm_batch_destroy(b);
+      return st;
+    }
+    b->sys.push_back(h);
+  }
+  bool ok = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaMallocHost((void**)&b->host_norm, 2 * sizeof(double) * nsys) == cudaSuccess;
+  for (int i = 0; i < nsys && ok; ++i) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    b->branch.push_back(s);
+    b->join.push_back(e);
+  }
+  if (!ok) {
+    cudaGetLastError();
+    selm_batch_destroy(b);
+    return SELM_ENOMEM;
+  }
+  *out = b;
+  return SELM_OK;
+}
+
+selm_status selm_batch_destroy(selm_batch* b) {
+  if (!b) return SELM_EINVAL;
+  cudaDeviceSynchronize();
+  drop_graphs(b);
+  for (selm_mg* h : b->sys) selm_mg_destroy(h);
+  for (cudaStream_t s : b->branch)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  if (b->host_norm) cudaFreeHost(b->host_norm);
+  delete b;
+  return SELM_OK;
+}
+
+selm_mg* selm_batch_system(selm_batch* b, int i) {
+  if (!b || i < 0 || i >= b->n) return nullptr;
+  return b->sys[i];
+}
+
+const char* selm_batch_last_error(const selm_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+selm_status selm_batch_step(selm_batch* b, const int* np, double* const* X, const double* const* F, double dt,
+                            int nsteps, int ncycles_per_step, int* solve_cycles, void* stream) {
+  if (!b || !np || !X || !F || nsteps < 0 || ncycles_per_step < 0 || !(dt >= 0.0)) return SELM_EINVAL;
+  for (int i = 0; i < b->n; ++i)
+    if (np[i] < 0 || np[i] > b->sys[i]->d.max_particles || (np[i] > 0 && (!X[i] || !F[i]))) return SELM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!same_args(b, np, X, F, dt, ncycles_per_step)) BST(build_graphs(b, np, X, F, dt, ncycles_per_step));
+  int max_cycles = 0;
+  for (selm_mg* h : b->sys) max_cycles = max_cycles > h->d.max_cycles ? max_cycles : h->d.max_cycles;
+  std::vector<int> cycles(b->n, -1);
+  for (int step = 0; step < nsteps; ++step) {
+    std::fill(cycles.begin(), cycles.end(), -1);
+    BCK(cudaGraphLaunch(b->g_start, st));
+    BCK(cudaStreamSynchronize(st));
+    int cyc = 0;
+    while (!all_converged(b, cycles, cyc)) {
+      if (cyc >= max_cycles) {
+        b->err = "batched FAC solve did not converge";
+        return SELM_ENOCONV;
+      }
+      BCK(cudaGraphLaunch(b->g_cycle, st));
+      BCK(cudaStreamSynchronize(st));
+      ++cyc;
+      for (selm_mg* h : b->sys) h->total_vcycles += 1;
+    }
+    if (ncycles_per_step > 0) {
+      BCK(cudaGraphLaunch(b->g_chain, st));
+      for (selm_mg* h : b->sys) {
+        h->cycle += ncycles_per_step;
+        h->total_vcycles += ncycles_per_step;
+      }
+    }
+    BCK(cudaGraphLaunch(b->g_finish, st));
+    for (int i = 0; i < b->n; ++i) b->sys[i]->last_solve_cycles = cycles[i];
+  }
+  if (solve_cycles)
+    for (int i = 0; i < b->n; ++i) solve_cycles[i] = cycles[i];
+  return SELM_OK;
+}
+
+selm_status selm_batch_autotune(selm_batch* b, int* chosen_cluster, void* stream) {
+  if (!b) return SELM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  BCK(cudaStreamSynchronize(st));   // no batched graph may still be running
+  const int cands[3] = {16, 8, 4};
+  float best = -1.0f;
+  int best_c = 0;
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  for (int c : cands) {
+    for (selm_mg* h : b->sys) BST(replan_engine(h, c, nullptr));
+    BST(build_cycle_graph(b));
+    BCK(cudaGraphLaunch(b->g_cycle, st));   // warm-up
+    BCK(cudaEventRecord(e0, st));
+    for (int r = 0; r < 3; ++r) BCK(cudaGraphLaunch(b->g_cycle, st));
+    BCK(cudaEventRecord(e1, st));
+    BCK(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    BCK(cudaEventElapsedTime(&ms, e0, e1));
+    if (best < 0.0f || ms < best) {
+      best = ms;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (selm_mg* h : b->sys) BST(replan_engine(h, best_c, nullptr));
+  drop_graphs(b);   // graphs are rebuilt with the chosen plans on the next step
+  b->cluster = best_c;
+  if (chosen_cluster) *chosen_cluster = best_c;
+  return SELM_OK;
+}
+
+}  // extern "C"

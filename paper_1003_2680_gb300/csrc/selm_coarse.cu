@@ -641,9 +641,35 @@ void fill_engine_tables(const LevelDev* levs, int L, void* const* gb, void* cons
     }
 }
 
+namespace {
+template <typename T>
+bool raise_smem_limit() {
+  static bool done = false;
+  if (done) return true;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  for (auto fn : {k_coarse_engine<T, true>, k_coarse_engine<T, false>}) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  done = true;
+  return true;
+}
+}  // namespace
+
 template <typename T>
 bool plan_coarse_engine(const LevelDev* levs, int L, void* const* gb, void* const* gv, void* const* gt,
-                        void* dev_params, cudaStream_t st, EnginePlanT<T>* plan) {
+                        void* dev_params, cudaStream_t st, EnginePlanT<T>* plan, int want_cluster) {
   static_assert(sizeof(EngParams<T>) <= kEngParamBytes, "engine plan exceeds its workspace slot");
   plan->valid = false;
   if (L < 2 || !dev_params) return false;
@@ -658,25 +684,15 @@ bool plan_coarse_engine(const LevelDev* levs, int L, void* const* gb, void* cons
     for (int si = 0; si < 5; ++si) {
       const int C = sizes[si];
       if (C > 1 && !cluster_ok) continue;
+      if (want_cluster > 0 && C > want_cluster) continue;
       EnginePlanT<T> cand{};
       if (!try_plan<T>(levs, L, l0, C, smem_cap, &cand)) continue;
-      // check that the cluster shape can be scheduled
+      // The dynamic shared-memory limit is a per-kernel setting shared by every
+      // handle of the process: raise it once to the device maximum so that
+      // plans of any size stay launchable.
+      if (!raise_smem_limit<T>()) continue;
       if (cand.cluster > 1) {
         auto fn = k_coarse_engine<T, true>;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cand.smem_bytes) != cudaSuccess ||
-            cudaFuncSetAttribute(k_coarse_engine<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)cand.smem_bytes) != cudaSuccess) {
-          cudaGetLastError();
-          continue;
-        }
-        if (cand.cluster > 8) {
-          if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-              cudaFuncSetAttribute(k_coarse_engine<T, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                  cudaSuccess) {
-            cudaGetLastError();
-            continue;
-          }
-        }
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(cand.cluster * levs[0].ncomp);
         cfg.blockDim = dim3(EngThreads<T>::value);
@@ -690,14 +706,6 @@ bool plan_coarse_engine(const LevelDev* levs, int L, void* const* gb, void* cons
         cfg.numAttrs = 1;
         int nclusters = 0;
         if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
-          cudaGetLastError();
-          continue;
-        }
-      } else {
-        if (cudaFuncSetAttribute(k_coarse_engine<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)cand.smem_bytes) != cudaSuccess ||
-            cudaFuncSetAttribute(k_coarse_engine<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)cand.smem_bytes) != cudaSuccess) {
           cudaGetLastError();
           continue;
         }
@@ -740,9 +748,9 @@ cudaError_t launch_coarse_engine(const EnginePlanT<T>& plan, int mu1, int mu2, i
 }
 
 template bool plan_coarse_engine<float>(const LevelDev*, int, void* const*, void* const*, void* const*, void*,
-                                        cudaStream_t, EnginePlanT<float>*);
+                                        cudaStream_t, EnginePlanT<float>*, int);
 template bool plan_coarse_engine<double>(const LevelDev*, int, void* const*, void* const*, void* const*, void*,
-                                         cudaStream_t, EnginePlanT<double>*);
+                                         cudaStream_t, EnginePlanT<double>*, int);
 template cudaError_t launch_coarse_engine<float>(const EnginePlanT<float>&, int, int, int, bool, Key,
                                                  const unsigned long long*, cudaStream_t);
 template cudaError_t launch_coarse_engine<double>(const EnginePlanT<double>&, int, int, int, bool, Key,

@@ -1,0 +1,96 @@
+// Handle internals shared by the C-ABI translation units (not public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/selm_mg.h"
+#include "selm_coarse.h"
+#include "selm_internal.h"
+#include "selm_launch.h"
+
+namespace selm {
+
+struct Sys {
+  HostSystem host;
+  LevelDev lev[kMaxLevels];
+  void* v[kMaxLevels] = {};
+  void* b[kMaxLevels] = {};
+  void* t[kMaxLevels] = {};
+  int levels = 0;
+  int ncomp = 0;
+  EnginePlanT<float> engf;    // cluster-resident coarse levels (FP32 inner)
+  EnginePlanT<double> engd;   // (FP64 inner)
+  bool use_engine = true;
+  int engine_cluster = 0;     // preferred cluster size of the engine (0 = largest that fits)
+  void* eng_dev = nullptr;    // device slot of the engine plan
+};
+
+template <typename T>
+inline EnginePlanT<T>& eng_of(Sys& s);
+template <>
+inline EnginePlanT<float>& eng_of<float>(Sys& s) {
+  return s.engf;
+}
+template <>
+inline EnginePlanT<double>& eng_of<double>(Sys& s) {
+  return s.engd;
+}
+
+// Byte layout of the workspace.
+struct Layout {
+  size_t total = 0;
+  size_t add(size_t bytes) {
+    size_t off = (total + 255) & ~(size_t)255;
+    total = off + bytes;
+    return off;
+  }
+};
+
+}  // namespace selm
+
+struct selm_mg {
+  selm_mg_desc d{};
+  int mu1 = 2, mu2 = 2;
+  int esize = 8;
+  selm::Sys vel, pres;
+  bool has_pres = false;
+  selm::Key key{};
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* u = nullptr;      // solution of the deterministic solve (FP64)
+  double* xi = nullptr;     // chain state (FP64)
+  double* bvel = nullptr;   // right-hand side (FP64)
+  double* wcomb = nullptr;  // combined field for the particle update (FP64)
+  double* phi = nullptr;    // pressure (FP64), 3 slots: warm starts of the projections
+                            // of Gamma^T F (0), of the step's combined field (1), of the
+                            // sampled field (2)
+  double* prhs = nullptr;   // pressure right-hand side (FP64)
+  double* red = nullptr;    // reduction slots
+  unsigned long long* cyc = nullptr;  // [0] chain counter, [1] stage-call counter
+  double* V = nullptr;      // particle scratch [max_particles][3]
+  double* Xs = nullptr;     // device copies of host particle arrays (selm_mg_step_host)
+  double* Fs = nullptr;
+  double* host_red = nullptr;  // pinned
+  uint64_t cycle = 0;
+  int last_solve_cycles = 0, last_proj_cycles = 0;
+  long long total_vcycles = 0;
+  std::string err;
+};
+
+namespace selm {
+
+// Asynchronous building blocks (no host synchronisation; safe under stream
+// capture).  All return SELM_OK or SELM_ECUDA with h->err set.
+selm_status vcycle(selm_mg* h, Sys& s, void* v0, const void* b0, bool noise, const unsigned long long* cyc,
+                   cudaStream_t st);
+selm_status outer_residual(selm_mg* h, Sys& s, const double* z, const double* b, void* r, double* norm2,
+                           cudaStream_t st);
+selm_status outer_update(selm_mg* h, Sys& s, double* z, const void* d, cudaStream_t st);
+// Re-plans the coarse engine of the velocity system with a preferred cluster
+// size (0 = largest that fits).
+selm_status replan_engine(selm_mg* h, int cluster, cudaStream_t st);
+
+}  // namespace selm

@@ -19,6 +19,7 @@ SELM_PROJ_NONE, SELM_PROJ_MAC = 0, 1
 SELM_COARSE_CHOLESKY, SELM_COARSE_SMOOTH = 0, 1
 SELM_SYS_VELOCITY, SELM_SYS_PRESSURE = 0, 1
 SELM_OPT_COARSE_ENGINE = 1
+SELM_OPT_ENGINE_CLUSTER = 2
 
 _STATUS = {0: "SELM_OK", 1: "SELM_EINVAL", 2: "SELM_ENOMEM", 3: "SELM_ECUDA", 4: "SELM_ENOCONV",
            5: "SELM_ETIMEOUT", 6: "SELM_EBUSY"}
@@ -84,6 +85,13 @@ _SIGS = {
     "selm_mg_project": (_I, [_P, _P, ctypes.POINTER(_I), _P]),
     "selm_mg_em_update": (_I, [_P, _I, _P, _P, _P]),
     "selm_philox4x32_10": (_I, [_P, ctypes.c_uint32, ctypes.c_uint32, _P, _I, _P]),
+    "selm_batch_create": (_I, [_I, ctypes.POINTER(SelmDesc), _P, ctypes.POINTER(_P)]),
+    "selm_batch_destroy": (_I, [_P]),
+    "selm_batch_system": (_P, [_P, _I]),
+    "selm_batch_last_error": (ctypes.c_char_p, [_P]),
+    "selm_batch_step": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, _I,
+                             ctypes.POINTER(_I), _P]),
+    "selm_batch_autotune": (_I, [_P, ctypes.POINTER(_I), _P]),
     "selm_kernel_launches": (ctypes.c_longlong, []),
     "selm_profile_enable": (_I, [_I]),
     "selm_profile_reset": (_I, []),
@@ -333,6 +341,46 @@ def selm_mg_em_update(h, X, V, stream=None):
 def selm_philox4x32_10(ctr, key0, key1, out, stream=None):
     n = ctr.numel() // 4
     _check(None, lib().selm_philox4x32_10(_ptr(ctr), key0, key1, _ptr(out), n, _stream(stream)))
+
+
+def _check_batch(b, status):
+    if status != SELM_OK:
+        msg = lib().selm_batch_last_error(b).decode() if b else ""
+        raise SelmError(status, msg)
+
+
+def selm_batch_create(descs, stream=None):
+    arr = (SelmDesc * len(descs))(*descs)
+    b = _P()
+    st = lib().selm_batch_create(len(descs), arr, _stream(stream), ctypes.byref(b))
+    if st != SELM_OK:
+        raise SelmError(st, "selm_batch_create failed (see stderr)")
+    return b.value
+
+
+def selm_batch_destroy(b):
+    _check_batch(None, lib().selm_batch_destroy(b))
+
+
+def selm_batch_system(b, i):
+    return lib().selm_batch_system(b, i)
+
+
+def selm_batch_step(b, X, F, dt, nsteps, ncycles_per_step, stream=None):
+    """X, F: lists of CUDA float64 tensors [np_i][dim]; returns the solve cycles per system."""
+    n = len(X)
+    nps = (_I * n)(*[x.shape[0] for x in X])
+    xs = (_P * n)(*[_ptr(x) for x in X])
+    fs = (_P * n)(*[_ptr(f) for f in F])
+    cyc = (_I * n)()
+    _check_batch(b, lib().selm_batch_step(b, nps, xs, fs, dt, nsteps, ncycles_per_step, cyc, _stream(stream)))
+    return list(cyc)
+
+
+def selm_batch_autotune(b, stream=None):
+    c = _I(0)
+    _check_batch(b, lib().selm_batch_autotune(b, ctypes.byref(c), _stream(stream)))
+    return c.value
 
 
 class SelmMG:

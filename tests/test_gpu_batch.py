@@ -1,0 +1,105 @@
+"""GPU: the batched form equals each system advanced alone.
+
+Several independent channel systems of uneven size, each with its own seed,
+instance and kT, are advanced by selm_batch_step (one graph launch per phase
+for all systems).  Each system is also advanced alone by selm_mg_step from
+the same state.  The stochastic chains see the same Philox counters, so the
+thermal fields agree to rounding; the deterministic solves stop at the
+batch's slowest system, which only tightens the tolerance.  Trajectories must
+agree to well within the FP32-inner tolerance, before and after the
+autotuner changes the engine's cluster size.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import selm_inputs
+
+pytestmark = pytest.mark.gpu
+
+SYSTEMS = [  # (dim, n, particles, kT, seed)
+    (3, 16, 24, 0.5, 1),
+    (3, 32, 40, 1.3, 2),
+    (3, 48, 33, 2.0, 3),
+    (2, 64, 16, 0.9, 4),
+]
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1003_2680_gb300 import selm as mod
+    mod.lib()
+    return mod
+
+
+def _descs(S):
+    return [S.make_desc(dim=d, n=n, kT=kT, precision=S.SELM_FP32_REFINE64, seed=seed, instance=7 + i,
+                        max_particles=256)
+            for i, (d, n, npart, kT, seed) in enumerate(SYSTEMS)]
+
+
+def _inputs():
+    Xs, Fs = [], []
+    for d, n, npart, kT, seed in SYSTEMS:
+        Xs.append(selm_inputs.particles(npart, d, n, seed=seed))
+        Fs.append(selm_inputs.forces(npart, d, seed=seed))
+    return Xs, Fs
+
+
+def _alone(S, descs, Xs, Fs, nsteps):
+    out = []
+    for desc, X0, F0 in zip(descs, Xs, Fs):
+        h = S.selm_mg_create(desc)
+        X = torch.tensor(X0, device="cuda")
+        S.selm_mg_step(h, X, torch.tensor(F0, device="cuda"), 1e-3, nsteps, 2)
+        torch.cuda.synchronize()
+        out.append(X.cpu().numpy())
+        S.selm_mg_destroy(h)
+    return out
+
+
+def test_batch_matches_systems_alone(S):
+    descs = _descs(S)
+    Xs, Fs = _inputs()
+    b = S.selm_batch_create(descs)
+    X = [torch.tensor(x, device="cuda") for x in Xs]
+    F = [torch.tensor(f, device="cuda") for f in Fs]
+    cycles = S.selm_batch_step(b, X, F, 1e-3, 1, 2)
+    cycles += S.selm_batch_step(b, X, F, 1e-3, 1, 2)
+    torch.cuda.synchronize()
+    assert all(1 <= c <= 15 for c in cycles)
+    want = _alone(S, descs, Xs, Fs, 2)
+    for i, (x, w, x0) in enumerate(zip(X, want, Xs)):
+        err = np.linalg.norm(x.cpu().numpy() - w) / np.linalg.norm(w - x0)
+        assert err < 1e-5, (i, err)
+    # the chains advanced by the same counters
+    for i in range(len(SYSTEMS)):
+        h = S.selm_batch_system(b, i)
+        assert S.selm_mg_chain(h)[1] == 4
+    S.selm_batch_destroy(b)
+
+
+def test_batch_autotune_keeps_results(S):
+    descs = _descs(S)
+    Xs, Fs = _inputs()
+    b = S.selm_batch_create(descs)
+    chosen = S.selm_batch_autotune(b)
+    assert chosen in (4, 8, 16)
+    X = [torch.tensor(x, device="cuda") for x in Xs]
+    F = [torch.tensor(f, device="cuda") for f in Fs]
+    S.selm_batch_step(b, X, F, 1e-3, 2, 2)
+    torch.cuda.synchronize()
+    want = _alone(S, descs, Xs, Fs, 2)
+    for i, (x, w, x0) in enumerate(zip(X, want, Xs)):
+        err = np.linalg.norm(x.cpu().numpy() - w) / np.linalg.norm(w - x0)
+        assert err < 1e-5, (i, err)
+    S.selm_batch_destroy(b)
+
+
+def test_batch_rejects_projection(S):
+    d = S.make_desc(dim=3, n=16, projection=S.SELM_PROJ_MAC)
+    with pytest.raises(S.SelmError):
+        S.selm_batch_create([d])

@@ -61,9 +61,14 @@ def parse_args():
     p.add_argument("--particles", type=int, default=N_PARTICLES)
     p.add_argument("--no-projection", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="channel128", choices=["channel128", "batched"],
-                   help="channel128: the headline line; batched: 64 uneven systems, batched vs plain")
+    p.add_argument("--workload", default="channel128", choices=["channel128", "batched", "served"],
+                   help="channel128: the headline line; batched: 64 uneven systems, batched vs plain; "
+                        "served: Poisson request stream, served vs plain per-request")
     p.add_argument("--systems", type=int, default=64)
+    p.add_argument("--requests", type=int, default=100)
+    p.add_argument("--rate", type=float, default=200.0)
+    p.add_argument("--slots", type=int, default=12)
+    p.add_argument("--budget-gb", type=float, default=32.0)
     return p.parse_args()
 
 
@@ -327,6 +332,78 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def served_stream(nreq, rate, seed=0):
+    """Poisson arrivals; 50% 2-D channels (edge 256..1024), 50% 3-D (edge 32..192);
+    16..4096 particles (log-uniform); 1..20 Euler-Maruyama steps; own seed each."""
+    import numpy as np
+    rng = np.random.default_rng([seed, 606])
+    t = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+    reqs = []
+    for i in range(nreq):
+        if rng.uniform() < 0.5:
+            dim, edge = 2, int(rng.choice([256, 384, 512, 768, 1024]))
+        else:
+            dim, edge = 3, int(rng.choice([32, 48, 64, 96, 128, 192]))
+        npart = int(round(np.exp(rng.uniform(np.log(16), np.log(4096)))))
+        reqs.append(dict(t=float(t[i]), dim=dim, n=edge, np=npart, steps=int(rng.integers(1, 21)), seed=1000 + i))
+    return reqs
+
+
+def run_served(args):
+    import time as _time
+    import numpy as np
+    import torch
+    from paper_1003_2680_gb300 import _build
+    _build.build()
+    from paper_1003_2680_gb300 import selm as S
+    import selm_inputs
+
+    reqs = served_stream(args.requests, args.rate)
+    budget = int(args.budget_gb * (1 << 30))
+
+    def serve(slots):
+        srv = S.selm_server_create(budget, slots)
+        keep = []
+        t0 = _time.perf_counter()
+        for i, r in enumerate(reqs):
+            delay = r["t"] - (_time.perf_counter() - t0)
+            if delay > 0:
+                _time.sleep(delay)
+            X = np.ascontiguousarray(selm_inputs.particles(r["np"], r["dim"], r["n"], seed=r["seed"]))
+            F = np.ascontiguousarray(selm_inputs.forces(r["np"], r["dim"], seed=r["seed"]))
+            keep.append((X, F))
+            desc = S.make_desc(dim=r["dim"], n=r["n"], kT=1.0, precision=S.SELM_FP32_REFINE64, seed=r["seed"],
+                               instance=i, max_particles=r["np"], torch_allocator=False)
+            S.selm_server_submit(srv, desc, X, F, DT, r["steps"], SAMPLE_CYCLES, user=i + 1)
+        S.selm_server_drain(srv)
+        res = S.selm_server_poll(srv, len(reqs) + 1)
+        stats = S.selm_server_stats(srv)
+        S.selm_server_destroy(srv)
+        lat = np.array([x["t_done"] - x["t_submit"] for x in res])
+        span = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
+        ok = all(x["status"] == 0 for x in res)
+        return dict(p50_ms=1e3 * float(np.percentile(lat, 50)), p99_ms=1e3 * float(np.percentile(lat, 99)),
+                    requests_per_s=len(res) / span, solves_per_s=sum(r["steps"] for r in reqs) / span,
+                    vcycles_per_s=sum(x["vcycles"] for x in res) / span, makespan_s=span,
+                    peak_slots=stats["peak_slots"], peak_gb=stats["peak_bytes"] / 2 ** 30, all_ok=ok)
+
+    torch.cuda.synchronize()
+    plain = serve(1)
+    served = serve(args.slots)
+    line = {
+        "metric": "served solves/s + p99 vs plain form", "value": served["solves_per_s"], "unit": "solves/s",
+        "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "dtype": "f32+f64",
+        "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {args.rate}/s; 50% 2-D channels "
+                               f"(edge 256..1024), 50% 3-D (edge 32..192); 16..4096 particles; 1..20 steps; "
+                               f"each step = FAC solve to 1e-10 + {SAMPLE_CYCLES} stochastic cycles",
+                   "slots": args.slots, "budget_gb": args.budget_gb,
+                   "solve": "one Euler-Maruyama step (one mobility solve) of one request"},
+        "served": served, "plain": plain,
+        "speedup_solves": served["solves_per_s"] / plain["solves_per_s"],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -338,6 +415,9 @@ def main():
     assert args.warmup >= 3, "at least 3 warm-up steps"
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "served":
+        run_served(args)
         return
 
     import numpy as np

@@ -247,6 +247,52 @@ selm_status selm_batch_step(selm_batch* b, const int* np, double* const* X, cons
    fastest; *chosen_cluster receives it. */
 selm_status selm_batch_autotune(selm_batch* b, int* chosen_cluster, void* stream);
 
+/* ---- served form -----------------------------------------------------------
+   A request loop.  One device pool of `budget_bytes` is reserved at creation;
+   requests are admitted in arrival order as soon as a contiguous block of
+   their footprint (selm_mg_footprint of the request's descriptor) is free in
+   the pool and one of `max_slots` worker threads is idle.  Each admitted
+   request keeps its system on the device, runs selm_mg_step_host on its own
+   stream (copy X and F in, nsteps steps, copy X out) and releases its block;
+   the admitted requests' work overlaps on the GPU.  X and F are HOST arrays
+   that must stay valid until the request's result has been polled; X is
+   overwritten with the final positions.  The descriptor's allocator hooks are
+   ignored (the pool serves the workspace). */
+typedef struct {
+  selm_mg_desc desc;     /* the system of this request (grid, walls, kT, seeds) */
+  int np;                /* particles */
+  double* X;             /* host [np][dim], updated in place */
+  const double* F;       /* host [np][dim] */
+  double dt;
+  int nsteps;
+  int ncycles_per_step;
+  void* user;            /* returned with the result */
+} selm_request;
+
+typedef struct {
+  uint64_t id;
+  void* user;
+  selm_status status;
+  double t_submit, t_admit, t_done;   /* seconds on the server clock */
+  int vcycles;                        /* V-cycles the request ran */
+} selm_result;
+
+typedef struct selm_server selm_server;
+selm_status selm_server_create(size_t budget_bytes, int max_slots, selm_server** out);
+/* Queues a request (returns at once); SELM_EBUSY if it can never fit the pool. */
+selm_status selm_server_submit(selm_server* s, const selm_request* r, uint64_t* id);
+/* Moves up to `max` finished results to `out`; returns how many. */
+int selm_server_poll(selm_server* s, selm_result* out, int max);
+/* Waits until every submitted request has finished. */
+selm_status selm_server_drain(selm_server* s);
+/* Peak pool bytes and busy slots since creation, current bytes and queue length. */
+selm_status selm_server_stats(selm_server* s, size_t* peak_bytes, int* peak_slots, size_t* bytes_in_use,
+                              int* queued);
+/* Seconds since the server was created (the clock of selm_result). */
+double selm_server_clock(selm_server* s);
+/* Finishes the queued requests, stops the workers and frees the pool. */
+selm_status selm_server_destroy(selm_server* s);
+
 /* ---- measurement --------------------------------------------------------
    Process-wide kernel accounting.  selm_kernel_launches() counts every
    kernel this library has launched since it was loaded.  With profiling on,

@@ -460,8 +460,11 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
     return SELM_ENOMEM;
   }
   h->ws = (char*)ws;
-  if (cudaMallocHost((void**)&h->host_red, 16 * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
+  // Host word for norm read-backs: ordinary host memory (the read is
+  // followed by a stream synchronisation anyway), so that creating and
+  // destroying handles never synchronises the device.
+  h->host_red = new (std::nothrow) double[16];
+  if (!h->host_red) {
     selm_mg_destroy(h);
     return SELM_ENOMEM;
   }
@@ -524,7 +527,7 @@ selm_status selm_mg_destroy(selm_mg* h) {
     else
       cudaFree(h->ws);
   }
-  if (h->host_red) cudaFreeHost(h->host_red);
+  delete[] h->host_red;
   delete h;
   return SELM_OK;
 }

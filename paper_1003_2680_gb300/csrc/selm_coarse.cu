@@ -22,6 +22,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "../../include/selm_mg.h"
@@ -644,8 +645,8 @@ void fill_engine_tables(const LevelDev* levs, int L, void* const* gb, void* cons
 namespace {
 template <typename T>
 bool raise_smem_limit() {
-  static bool done = false;
-  if (done) return true;
+  static std::atomic<bool> done{false};
+  if (done.load()) return true;
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
@@ -662,7 +663,7 @@ bool raise_smem_limit() {
       return false;
     }
   }
-  done = true;
+  done.store(true);
   return true;
 }
 }  // namespace

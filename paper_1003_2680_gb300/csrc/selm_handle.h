@@ -73,7 +73,7 @@ struct selm_mg {
   double* V = nullptr;      // particle scratch [max_particles][3]
   double* Xs = nullptr;     // device copies of host particle arrays (selm_mg_step_host)
   double* Fs = nullptr;
-  double* host_red = nullptr;  // pinned
+  double* host_red = nullptr;  // host word for norm read-backs
   uint64_t cycle = 0;
   int last_solve_cycles = 0, last_proj_cycles = 0;
   long long total_vcycles = 0;

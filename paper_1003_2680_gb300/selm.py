@@ -39,6 +39,18 @@ class SelmDesc(ctypes.Structure):
     ]
 
 
+class SelmRequest(ctypes.Structure):
+    _fields_ = [("desc", SelmDesc), ("np", ctypes.c_int), ("X", ctypes.c_void_p), ("F", ctypes.c_void_p),
+                ("dt", ctypes.c_double), ("nsteps", ctypes.c_int), ("ncycles_per_step", ctypes.c_int),
+                ("user", ctypes.c_void_p)]
+
+
+class SelmResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("user", ctypes.c_void_p), ("status", ctypes.c_int),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("vcycles", ctypes.c_int)]
+
+
 class SelmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
@@ -92,6 +104,14 @@ _SIGS = {
     "selm_batch_step": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, _I,
                              ctypes.POINTER(_I), _P]),
     "selm_batch_autotune": (_I, [_P, ctypes.POINTER(_I), _P]),
+    "selm_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
+    "selm_server_submit": (_I, [_P, ctypes.POINTER(SelmRequest), ctypes.POINTER(_U64)]),
+    "selm_server_poll": (_I, [_P, ctypes.POINTER(SelmResult), _I]),
+    "selm_server_drain": (_I, [_P]),
+    "selm_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_I),
+                               ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_I)]),
+    "selm_server_clock": (_D, [_P]),
+    "selm_server_destroy": (_I, [_P]),
     "selm_kernel_launches": (ctypes.c_longlong, []),
     "selm_profile_enable": (_I, [_I]),
     "selm_profile_reset": (_I, []),
@@ -381,6 +401,52 @@ def selm_batch_autotune(b, stream=None):
     c = _I(0)
     _check_batch(b, lib().selm_batch_autotune(b, ctypes.byref(c), _stream(stream)))
     return c.value
+
+
+def selm_server_create(budget_bytes, max_slots):
+    s = _P()
+    _check(None, lib().selm_server_create(int(budget_bytes), int(max_slots), ctypes.byref(s)))
+    return s.value
+
+
+def selm_server_submit(s, desc, X, F, dt, nsteps, ncycles_per_step, user=0):
+    """X, F: C-contiguous float64 numpy arrays [np][dim] (host); X is overwritten on completion.
+    The caller keeps X and F alive until the result is polled."""
+    assert X.dtype.kind == "f" and X.itemsize == 8 and X.flags.c_contiguous and F.flags.c_contiguous
+    r = SelmRequest()
+    r.desc = desc
+    r.np = X.shape[0]
+    r.X = X.ctypes.data
+    r.F = F.ctypes.data
+    r.dt, r.nsteps, r.ncycles_per_step, r.user = dt, nsteps, ncycles_per_step, user
+    rid = _U64(0)
+    _check(None, lib().selm_server_submit(s, ctypes.byref(r), ctypes.byref(rid)))
+    return rid.value
+
+
+def selm_server_poll(s, max_results=256):
+    buf = (SelmResult * max_results)()
+    n = lib().selm_server_poll(s, buf, max_results)
+    return [dict(id=r.id, user=r.user or 0, status=r.status, t_submit=r.t_submit, t_admit=r.t_admit,
+                 t_done=r.t_done, vcycles=r.vcycles) for r in buf[:n]]
+
+
+def selm_server_drain(s):
+    _check(None, lib().selm_server_drain(s))
+
+
+def selm_server_stats(s):
+    pb, ps, bu, q = ctypes.c_size_t(0), _I(0), ctypes.c_size_t(0), _I(0)
+    _check(None, lib().selm_server_stats(s, ctypes.byref(pb), ctypes.byref(ps), ctypes.byref(bu), ctypes.byref(q)))
+    return dict(peak_bytes=pb.value, peak_slots=ps.value, bytes_in_use=bu.value, queued=q.value)
+
+
+def selm_server_clock(s):
+    return lib().selm_server_clock(s)
+
+
+def selm_server_destroy(s):
+    _check(None, lib().selm_server_destroy(s))
 
 
 class SelmMG:

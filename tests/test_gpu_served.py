@@ -1,0 +1,86 @@
+"""GPU: the served form gives each request the same result alone and in the mix.
+
+Requests of uneven sizes (2-D and 3-D channels, own seeds, kT, particle
+counts and step counts) are served twice: one at a time (one slot), and all
+submitted at once to a server with several slots and a device budget that
+admits only part of them together, so later requests are admitted as memory
+frees up while others run.  Every request's final positions must agree
+between the two runs; the budget and the slot count must never be exceeded,
+and more than one request must have been on the device at once.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import selm_inputs
+
+pytestmark = pytest.mark.gpu
+
+REQUESTS = [  # (dim, n, particles, nsteps, kT, seed)
+    (3, 16, 20, 3, 0.7, 11),
+    (2, 64, 16, 2, 1.0, 12),
+    (3, 24, 40, 4, 1.6, 13),
+    (3, 32, 30, 2, 0.5, 14),
+    (2, 128, 50, 3, 2.0, 15),
+    (3, 16, 8, 1, 1.2, 16),
+]
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1003_2680_gb300 import selm as mod
+    mod.lib()
+    return mod
+
+
+def _desc(S, dim, n, kT, seed):
+    return S.make_desc(dim=dim, n=n, kT=kT, precision=S.SELM_FP32_REFINE64, seed=seed, instance=seed,
+                       torch_allocator=False)
+
+
+def _serve(S, budget, slots):
+    srv = S.selm_server_create(budget, slots)
+    Xs, Fs = [], []
+    for i, (dim, n, npart, nsteps, kT, seed) in enumerate(REQUESTS):
+        X = np.ascontiguousarray(selm_inputs.particles(npart, dim, n, seed=seed))
+        F = np.ascontiguousarray(selm_inputs.forces(npart, dim, seed=seed))
+        Xs.append(X)
+        Fs.append(F)
+        S.selm_server_submit(srv, _desc(S, dim, n, kT, seed), X, F, 1e-3, nsteps, 2, user=i + 1)
+    S.selm_server_drain(srv)
+    results = S.selm_server_poll(srv)
+    stats = S.selm_server_stats(srv)
+    S.selm_server_destroy(srv)
+    return Xs, results, stats
+
+
+def test_each_request_same_alone_and_in_the_mix(S):
+    sizes = [S.selm_mg_footprint(_desc(S, d, n, kT, seed)) for d, n, _, _, kT, seed in REQUESTS]
+    X_alone, res_alone, st_alone = _serve(S, budget=max(sizes) + (1 << 20), slots=1)
+    budget = sum(sorted(sizes)[-3:]) + (1 << 20)       # admits about three at once
+    X_mix, res_mix, st_mix = _serve(S, budget=budget, slots=4)
+    assert len(res_alone) == len(res_mix) == len(REQUESTS)
+    assert all(r["status"] == 0 for r in res_alone + res_mix)
+    assert st_alone["peak_slots"] == 1
+    assert 2 <= st_mix["peak_slots"] <= 4
+    assert st_mix["peak_bytes"] <= budget
+    X0 = [selm_inputs.particles(npart, d, n, seed=seed) for d, n, npart, _, _, seed in REQUESTS]
+    for i, (a, m, x0) in enumerate(zip(X_alone, X_mix, X0)):
+        assert not np.array_equal(a, x0)            # the particles moved
+        err = np.linalg.norm(m - a) / np.linalg.norm(a - x0)
+        assert err < 1e-9, (i, err)
+    # the served clock orders submit <= admit <= done
+    for r in res_mix:
+        assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
+
+
+def test_request_larger_than_pool_is_refused(S):
+    srv = S.selm_server_create(1 << 20, 1)
+    X = np.zeros((4, 3))
+    with pytest.raises(S.SelmError) as info:
+        S.selm_server_submit(srv, _desc(S, 3, 64, 1.0, 0), X, X, 1e-3, 1, 2)
+    assert info.value.status == S.SELM_EBUSY
+    S.selm_server_destroy(srv)

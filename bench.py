@@ -60,6 +60,8 @@ def parse_args():
     p.add_argument("--n", type=int, default=N_CELLS_EDGE)
     p.add_argument("--particles", type=int, default=N_PARTICLES)
     p.add_argument("--no-projection", action="store_true")
+    p.add_argument("--engine-level", type=int, default=0,
+                   help="first multigrid level of the cluster-resident coarse engine (0 = automatic)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default="channel128", choices=["channel128", "batched", "served"],
                    help="channel128: the headline line; batched: 64 uneven systems, batched vs plain; "
@@ -442,6 +444,8 @@ def main():
     m = S.SelmMG(dim=3, n=n, precision=S.SELM_FP32_REFINE64, projection=proj, tol=1e-10, seed=0,
                  instance=rank, max_particles=npart)
     h = m.h
+    if args.engine_level:
+        S.selm_mg_set_option(h, S.SELM_OPT_ENGINE_LEVEL, args.engine_level)
     X0 = selm_inputs.particles(npart, 3, n, seed=rank)
     F0 = selm_inputs.forces(npart, 3, seed=rank)
     X = torch.tensor(X0, device="cuda")
@@ -552,6 +556,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": dict(workload_config(n, npart, proj == S.SELM_PROJ_MAC), levels=S.selm_mg_levels(h, 0),
+                       engine_first_level=S.selm_mg_engine_info(h)[0],
                        parallelism=f"replicas x{world} (independent systems, no collective on the data path)"),
         "velocity_vcycles_per_step": cycles_all / args.steps / world,
         "roofline": roof,

@@ -140,10 +140,18 @@ selm_status selm_mg_set_cycle(selm_mg* h, uint64_t cycle);
    finest with the cluster-resident coarse engine (one thread-block cluster
    per component, colour passes separated by cluster barriers); 0 selects one
    launch per colour pass.  Both give the same result up to rounding. */
-enum { SELM_OPT_COARSE_ENGINE = 1, SELM_OPT_ENGINE_CLUSTER = 2 };
+enum { SELM_OPT_COARSE_ENGINE = 1, SELM_OPT_ENGINE_CLUSTER = 2, SELM_OPT_ENGINE_LEVEL = 3, SELM_OPT_LEVEL_COOP = 4 };
 /* SELM_OPT_ENGINE_CLUSTER: largest thread-block cluster the coarse engine may
    use (1..16; 0 = the largest that fits).  Re-plans the engine; synchronises
-   the legacy default stream. */
+   the legacy default stream.
+   SELM_OPT_ENGINE_LEVEL: first level the coarse engine may take (0 = the
+   first level whose slabs fit in shared memory); the levels above it run as
+   GPU-wide launches.  Re-plans both systems' engines.
+   SELM_OPT_LEVEL_COOP (default 1): each half V-cycle of a level above the
+   engine runs as one cooperative launch over every SM, its colour passes
+   separated by grid barriers (each wait bounded; a timed-out wait is
+   reported as SELM_ECUDA by the next solve's norm read); 0 selects one launch
+   per colour pass.  Both give the same result up to rounding. */
 selm_status selm_mg_set_option(selm_mg* h, int option, int value);
 /* Coarse engine of `system`: first level it covers (-1 = not used), cluster
    size and dynamic shared memory per CTA. */

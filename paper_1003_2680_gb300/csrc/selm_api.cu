@@ -200,6 +200,8 @@ void bind_system(Sys* s, int si, const Plan& p, char* ws) {
       for (int q = 0; q < 9; ++q) {
         c.w1[q] = hc.w1[q];
         c.w2[q] = hc.w2[q];
+        c.w1f[q] = (float)hc.w1[q];
+        c.w2f[q] = (float)hc.w2[q];
       }
     }
     L.size = off;
@@ -239,6 +241,18 @@ selm_status vcycle_t(selm_mg* h, Sys& s, int l, T* v0, const T* b0, bool noise, 
   const LevelDev& L = s.lev[l];
   const bool last = l == s.levels - 1;
   const EnginePlanT<T>& eng = eng_of<T>(s);
+  if (l > 0 && !last && s.use_engine && s.use_coop && eng.valid && l < eng.params.l0 && s.coop_bar &&
+      level_coop_supported<T>(L)) {
+    // a level above the engine: each half of its V-cycle in one cooperative launch
+    const LevelDev& Lc = s.lev[l + 1];
+    CK(launch_level_coop<T>(L, Lc, 0, h->mu1, h->mu2, v, b, (T*)s.t[l], (T*)s.b[l + 1], (T*)s.v[l + 1], s.coop_bar,
+                            noise, h->key, cyc, st));
+    selm_status r = vcycle_t<T>(h, s, l + 1, v0, b0, noise, cyc, st);
+    if (r != SELM_OK) return r;
+    CK(launch_level_coop<T>(L, Lc, 1, h->mu1, h->mu2, v, b, (T*)s.t[l], (T*)s.b[l + 1], (T*)s.v[l + 1], s.coop_bar,
+                            noise, h->key, cyc, st));
+    return SELM_OK;
+  }
   if (l > 0 && s.use_engine && eng.valid && l == eng.params.l0) {
     // levels l..L-1 in one cluster launch: reads s.b[l], writes s.v[l]
     CK(launch_coarse_engine<T>(eng, h->mu1, h->mu2, h->d.coarse_mode, noise, h->key, cyc, st));
@@ -301,10 +315,25 @@ selm_status fac_cycle(selm_mg* h, Sys& s, double* z, const double* b, bool noise
   return outer_update(h, s, z, s.v[0], st);
 }
 
+// Reads one reduction slot of h->red.  The same copy brings back the grid-
+// barrier words of both systems (red[8..11]); a timed-out barrier wait of a
+// cooperative level launch is reported here and its words are cleared.
 selm_status read_double(selm_mg* h, const double* dev, double* out, cudaStream_t st) {
-  CK(cudaMemcpyAsync(h->host_red, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  const long long slot = dev - h->red;
+  if (slot < 0 || slot >= 8) {
+    h->err = "read_double: not a reduction slot";
+    return SELM_EINVAL;
+  }
+  CK(cudaMemcpyAsync(h->host_red, h->red, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  *out = *h->host_red;
+  *out = h->host_red[slot];
+  const unsigned* words = (const unsigned*)(h->host_red + 8);
+  if (words[2] != 0u || words[6] != 0u) {
+    CK(cudaMemsetAsync(h->red + 8, 0, 4 * sizeof(double), st));
+    CK(cudaStreamSynchronize(st));
+    h->err = "a grid barrier of a cooperative level launch timed out";
+    return SELM_ECUDA;
+  }
   return SELM_OK;
 }
 
@@ -390,19 +419,43 @@ bool check_particles(selm_mg* h, int np, const void* X) {
 
 }  // namespace
 
+namespace {
+
+// First level of a system's coarse engine.  An explicit option wins; else
+// level 1 goes to cooperative launches when it is large (a pass of level 1
+// then spreads over every SM instead of one cluster per component, which
+// pays once a component holds 2^17 sites or more) and the engine starts at
+// level 2; otherwise the engine takes every level from 1.
+int engine_first_level(const selm_mg* h, const Sys& s) {
+  if (s.engine_level > 0) return s.engine_level;
+  if (!s.use_coop || s.levels < 4) return 1;
+  long long big = 0;
+  for (int c = 0; c < s.lev[1].ncomp; ++c) {
+    const CompDev& d = s.lev[1].c[c];
+    const long long n = (long long)d.nx * d.ny * d.nz;
+    big = n > big ? n : big;
+  }
+  if (big < (1ll << 17)) return 1;
+  const bool ok = h->esize == 4 ? level_coop_supported<float>(s.lev[1]) : level_coop_supported<double>(s.lev[1]);
+  return ok ? 2 : 1;
+}
+
+}  // namespace
+
 namespace selm {
 selm_status replan_engine(selm_mg* h, int cluster, cudaStream_t st) {
   for (Sys* sy : {&h->vel, h->has_pres ? &h->pres : (Sys*)nullptr}) {
     if (!sy || !sy->eng_dev) continue;
     CK(cudaStreamSynchronize(st));   // no launch may still read the old plan
     sy->engine_cluster = cluster;
-    bool ok;
+    // without a plan (returns false) the per-pass path runs
     if (h->esize == 4)
-      ok = plan_coarse_engine<float>(sy->lev, sy->levels, sy->b, sy->v, sy->t, sy->eng_dev, st, &sy->engf, cluster);
+      plan_coarse_engine<float>(sy->lev, sy->levels, sy->b, sy->v, sy->t, sy->eng_dev, st, &sy->engf, cluster,
+                                engine_first_level(h, *sy));
     else
-      ok = plan_coarse_engine<double>(sy->lev, sy->levels, sy->b, sy->v, sy->t, sy->eng_dev, st, &sy->engd, cluster);
+      plan_coarse_engine<double>(sy->lev, sy->levels, sy->b, sy->v, sy->t, sy->eng_dev, st, &sy->engd, cluster,
+                                 engine_first_level(h, *sy));
     cudaGetLastError();
-    (void)ok;   // without a plan the per-pass path runs
   }
   return SELM_OK;
 }
@@ -483,10 +536,11 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
     if (!sy) continue;
     void* dp = h->ws + p.eng_off[si];
     sy->eng_dev = dp;
+    const int first = engine_first_level(h, *sy);
     if (h->esize == 4)
-      plan_coarse_engine<float>(sy->lev, sy->levels, sy->b, sy->v, sy->t, dp, st, &sy->engf);
+      plan_coarse_engine<float>(sy->lev, sy->levels, sy->b, sy->v, sy->t, dp, st, &sy->engf, 0, first);
     else
-      plan_coarse_engine<double>(sy->lev, sy->levels, sy->b, sy->v, sy->t, dp, st, &sy->engd);
+      plan_coarse_engine<double>(sy->lev, sy->levels, sy->b, sy->v, sy->t, dp, st, &sy->engd, 0, first);
     cudaGetLastError();
   }
   h->u = (double*)(h->ws + p.u_off);
@@ -498,6 +552,8 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
     h->prhs = (double*)(h->ws + p.prhs_off);
   }
   h->red = (double*)(h->ws + p.red_off);
+  h->vel.coop_bar = (unsigned*)(h->red + 8);
+  if (h->has_pres) h->pres.coop_bar = (unsigned*)(h->red + 10);
   h->cyc = (unsigned long long*)(h->ws + p.cyc_off);
   h->V = (double*)(h->ws + p.V_off);
   h->Xs = (double*)(h->ws + p.Xs_off);
@@ -509,6 +565,12 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
   if (ce == cudaSuccess && h->has_pres)
     ce = cudaMemsetAsync(h->phi, 0, 3 * (size_t)h->pres.lev[0].size * sizeof(double), st);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(h->cyc, 0, 4 * sizeof(unsigned long long), st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->red, 0, 16 * sizeof(double), st);
+  if (ce == cudaSuccess && h->has_pres) {
+    ce = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+  }
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // host tables must outlive the copies
   if (ce != cudaSuccess) {
     std::fprintf(stderr, "selm_mg_create: %s\n", cudaGetErrorString(ce));
@@ -521,6 +583,12 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
 
 selm_status selm_mg_destroy(selm_mg* h) {
   if (!h) return SELM_EINVAL;
+  if (h->side) {
+    cudaStreamSynchronize(h->side);   // nothing of the handle's may still read the workspace
+    cudaStreamDestroy(h->side);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ws) {
     if (h->d.free)
       h->d.free(h->ws, h->d.alloc_ctx);
@@ -592,6 +660,17 @@ selm_status selm_mg_set_option(selm_mg* h, int option, int value) {
   if (option == SELM_OPT_ENGINE_CLUSTER) {
     if (value < 0 || value > 16) return SELM_EINVAL;
     return replan_engine(h, value, nullptr);
+  }
+  if (option == SELM_OPT_LEVEL_COOP) {
+    h->vel.use_coop = value != 0;
+    h->pres.use_coop = value != 0;
+    return replan_engine(h, h->vel.engine_cluster, nullptr);   // the automatic first level depends on it
+  }
+  if (option == SELM_OPT_ENGINE_LEVEL) {
+    if (value < 0 || value > kMaxLevels) return SELM_EINVAL;
+    h->vel.engine_level = value;
+    h->pres.engine_level = value;
+    return replan_engine(h, h->vel.engine_cluster, nullptr);
   }
   return SELM_EINVAL;
 }
@@ -807,19 +886,54 @@ selm_status selm_mg_step(selm_mg* h, int np, double* X, const double* F, double 
   }
   cudaStream_t st = S(stream);
   const long long nv = h->vel.lev[0].size;
+  // With the projection, the chain cycles run on the side stream beside the
+  // spread and the first projection; the velocity solve waits for them.
+  const bool overlap = h->side != nullptr && ncycles_per_step > 0;
   for (int step = 0; step < nsteps; ++step) {
-    CK(cudaMemsetAsync(h->bvel, 0, (size_t)nv * sizeof(double), st));
-    CK(launch_spread(h->vel.lev[0], h->d.n, h->d.dim, np, X, F, h->bvel, st));
+    bool joined = true;
+    auto join = [&]() -> selm_status {
+      if (!joined) {
+        joined = true;
+        CK(cudaStreamWaitEvent(st, h->ev_join, 0));
+      }
+      return SELM_OK;
+    };
+    auto fail = [&](selm_status r) {
+      join();
+      return r;
+    };
+    selm_status r = SELM_OK;
+    if (overlap) {
+      CK(cudaEventRecord(h->ev_fork, st));
+      CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+      joined = false;
+      r = chain_cycles(h, ncycles_per_step, h->side);
+      if (cudaEventRecord(h->ev_join, h->side) != cudaSuccess) {
+        h->err = "event record on the side stream failed";
+        cudaStreamSynchronize(h->side);
+        return SELM_ECUDA;
+      }
+      if (r != SELM_OK) return fail(r);
+    }
+    if (cudaMemsetAsync(h->bvel, 0, (size_t)nv * sizeof(double), st) != cudaSuccess ||
+        launch_spread(h->vel.lev[0], h->d.n, h->d.dim, np, X, F, h->bvel, st) != cudaSuccess) {
+      h->err = cudaGetErrorString(cudaGetLastError());
+      return fail(SELM_ECUDA);
+    }
     int pc = 0, pc2 = 0, cycles = 0;
     double rel = 0.0;
-    selm_status r = project(h, h->bvel, &pc, st, 0);
+    r = project(h, h->bvel, &pc, st, 0);
+    if (r != SELM_OK) return fail(r);
+    r = join();
     if (r != SELM_OK) return r;
     CK(cudaMemsetAsync(h->u, 0, (size_t)nv * sizeof(double), st));
     r = fac_solve(h, h->vel, h->u, h->bvel, h->d.tol, h->d.max_cycles, &cycles, &rel, st);
     h->last_solve_cycles = cycles;
     if (r != SELM_OK) return r;
-    r = chain_cycles(h, ncycles_per_step, st);
-    if (r != SELM_OK) return r;
+    if (!overlap) {
+      r = chain_cycles(h, ncycles_per_step, st);
+      if (r != SELM_OK) return r;
+    }
     CK(launch_axpby(nv, dt, h->u, std::sqrt(2.0 * h->d.kT * dt), h->xi, h->wcomb, st));
     r = project(h, h->wcomb, &pc2, st, 1);
     if (r != SELM_OK) return r;

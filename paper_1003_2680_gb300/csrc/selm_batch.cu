@@ -253,7 +253,16 @@ selm_status selm_batch_create(int nsys, const selm_mg_desc* descs, void* stream,
       selm_batch_destroy(b);
       return st;
     }
+    // The systems' graph branches run side by side: each keeps its levels in
+    // its own cluster engine (cooperative launches would take every SM).
+    h->vel.use_coop = false;
+    h->pres.use_coop = false;
     b->sys.push_back(h);
+    st = selm::replan_engine(h, 0, stream ? (cudaStream_t)stream : nullptr);
+    if (st != SELM_OK) {
+      selm_batch_destroy(b);
+      return st;
+    }
   }
   bool ok = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&

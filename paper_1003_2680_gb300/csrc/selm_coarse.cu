@@ -670,7 +670,8 @@ bool raise_smem_limit() {
 
 template <typename T>
 bool plan_coarse_engine(const LevelDev* levs, int L, void* const* gb, void* const* gv, void* const* gt,
-                        void* dev_params, cudaStream_t st, EnginePlanT<T>* plan, int want_cluster) {
+                        void* dev_params, cudaStream_t st, EnginePlanT<T>* plan, int want_cluster,
+                        int min_level) {
   static_assert(sizeof(EngParams<T>) <= kEngParamBytes, "engine plan exceeds its workspace slot");
   plan->valid = false;
   if (L < 2 || !dev_params) return false;
@@ -681,7 +682,7 @@ bool plan_coarse_engine(const LevelDev* levs, int L, void* const* gb, void* cons
   cudaDeviceGetAttribute(&cluster_ok, cudaDevAttrClusterLaunch, dev);
   const size_t smem_cap = (size_t)cap > 2048 ? (size_t)cap - 1024 : 0;
   const int sizes[5] = {16, 8, 4, 2, 1};
-  for (int l0 = 1; l0 < L; ++l0) {
+  for (int l0 = min_level > 1 ? min_level : 1; l0 < L; ++l0) {
     for (int si = 0; si < 5; ++si) {
       const int C = sizes[si];
       if (C > 1 && !cluster_ok) continue;
@@ -749,9 +750,9 @@ cudaError_t launch_coarse_engine(const EnginePlanT<T>& plan, int mu1, int mu2, i
 }
 
 template bool plan_coarse_engine<float>(const LevelDev*, int, void* const*, void* const*, void* const*, void*,
-                                        cudaStream_t, EnginePlanT<float>*, int);
+                                        cudaStream_t, EnginePlanT<float>*, int, int);
 template bool plan_coarse_engine<double>(const LevelDev*, int, void* const*, void* const*, void* const*, void*,
-                                         cudaStream_t, EnginePlanT<double>*, int);
+                                         cudaStream_t, EnginePlanT<double>*, int, int);
 template cudaError_t launch_coarse_engine<float>(const EnginePlanT<float>&, int, int, int, bool, Key,
                                                  const unsigned long long*, cudaStream_t);
 template cudaError_t launch_coarse_engine<double>(const EnginePlanT<double>&, int, int, int, bool, Key,

@@ -83,14 +83,15 @@ struct EnginePlanT {
 // Bytes of device memory a system's plan occupies (reserved in the workspace).
 constexpr size_t kEngParamBytes = 32768;
 
-// Builds the plan for levels l0..L-1 (l0 >= 1 chosen as the first level whose
-// slabs fit in shared memory).  gb/gv/gt: per-level global field pointers.
-// dev_params: kEngParamBytes of device memory that receives the plan
-// (copied on `st`, which is synchronised before returning).
+// Builds the plan for levels l0..L-1 (l0 >= min_level >= 1 chosen as the
+// first level whose slabs fit in shared memory).  gb/gv/gt: per-level global
+// field pointers.  dev_params: kEngParamBytes of device memory that receives
+// the plan (copied on `st`, which is synchronised before returning).
 // want_cluster > 0 caps the cluster size (the autotuner's knob).
 template <typename T>
 bool plan_coarse_engine(const LevelDev* levs, int L, void* const* gb, void* const* gv, void* const* gt,
-                        void* dev_params, cudaStream_t st, EnginePlanT<T>* plan, int want_cluster = 0);
+                        void* dev_params, cudaStream_t st, EnginePlanT<T>* plan, int want_cluster = 0,
+                        int min_level = 1);
 
 // Runs the V-cycle below level l0-1: reads b at level l0, writes v at level l0.
 template <typename T>

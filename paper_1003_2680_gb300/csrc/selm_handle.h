@@ -25,7 +25,10 @@ struct Sys {
   EnginePlanT<double> engd;   // (FP64 inner)
   bool use_engine = true;
   int engine_cluster = 0;     // preferred cluster size of the engine (0 = largest that fits)
+  int engine_level = 0;       // first level the engine may take (0 = the first that fits)
   void* eng_dev = nullptr;    // device slot of the engine plan
+  bool use_coop = true;       // levels above the engine: cooperative launches (else one per pass)
+  unsigned* coop_bar = nullptr;   // grid-barrier words of the system's cooperative launches
 };
 
 template <typename T>
@@ -74,6 +77,11 @@ struct selm_mg {
   double* Xs = nullptr;     // device copies of host particle arrays (selm_mg_step_host)
   double* Fs = nullptr;
   double* host_red = nullptr;  // host word for norm read-backs
+  // Side stream for the chain cycles of a step, which depend only on the
+  // previous chain state: they run beside the first projection (a pressure
+  // solve) and join before the velocity solve, which shares their buffers.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   uint64_t cycle = 0;
   int last_solve_cycles = 0, last_proj_cycles = 0;
   long long total_vcycles = 0;
@@ -89,8 +97,8 @@ selm_status vcycle(selm_mg* h, Sys& s, void* v0, const void* b0, bool noise, con
 selm_status outer_residual(selm_mg* h, Sys& s, const double* z, const double* b, void* r, double* norm2,
                            cudaStream_t st);
 selm_status outer_update(selm_mg* h, Sys& s, double* z, const void* d, cudaStream_t st);
-// Re-plans the coarse engine of the velocity system with a preferred cluster
-// size (0 = largest that fits).
+// Re-plans the coarse engines with a preferred cluster size (0 = largest that
+// fits) and each system's first engine level.
 selm_status replan_engine(selm_mg* h, int cluster, cudaStream_t st);
 
 }  // namespace selm

@@ -44,6 +44,7 @@ struct CompDev {
   const double* zb64;      // [nz][10]: s*Mz band row then s*Kz band row (offsets -2..2)
   const float* zb32;
   double w1[9], w2[9];     // periodic x/y weights: Kx(x)My + Mx(x)Ky and Mx(x)My, index (dy+1)*3+dx+1
+  float w1f[9], w2f[9];    // the same in FP32 (no per-site conversion in FP32 kernels)
 };
 
 struct LevelDev {

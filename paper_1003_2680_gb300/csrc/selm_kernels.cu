@@ -3,7 +3,7 @@
 // Every hot-path step is an HBM-bound stencil; none is a dense contraction,
 // so the tensor cores are not used.  Step -> kernel:
 //   Gibbs sweep, level 0 (Section 3.1, red-black)      k_fine_colour
-//   Gibbs sweep, Galerkin levels (multicolour)         k_coarse_colour
+//   Gibbs sweep, Galerkin levels (multicolour)         k_coarse_site, k_level_coop, coarse engine
 //   residual (Alg. 3 step 3)                           k_residual
 //   restriction P^T (Eq. equ_restr_prolong_variation)  k_restrict
 //   prolongation + correction (Alg. 3 step 4)          k_prolong
@@ -203,31 +203,6 @@ __device__ __forceinline__ void fine_row(const CompDev& c, const V* __restrict__
 }
 
 // Galerkin-level operator: full 3x3x5 stencil row k (periodic wrap in x, y).
-template <typename T>
-__device__ __forceinline__ T coarse_apply(const CompDev& c, const T* __restrict__ v, int i, int j, int k,
-                                          bool skip_centre) {
-  const T* S = stencil_of<T>(c) + (long long)k * kStencil;
-  const long long plane = (long long)c.nx * c.ny;
-  T sum = (T)0;
-  for (int dz = -2; dz <= 2; ++dz) {
-    const int kk = k + dz;
-    if (kk < 0 || kk >= c.nz) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      if (c.ny == 1 && dy != 0) continue;
-      const int jj = wrapi(j + dy, c.ny);
-      const long long rowb = c.off + (long long)kk * plane + (long long)jj * c.nx;
-      const T* Sr = S + ((dz + 2) * 3 + (dy + 1)) * 3;
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        if (skip_centre && dz == 0 && dy == 0 && dx == 0) continue;
-        const T a = Sr[dx + 1];
-        if (a != (T)0) sum += a * v[rowb + wrapi(i + dx, c.nx)];
-      }
-    }
-  }
-  return sum;
-}
-
 template <typename T>
 __device__ __forceinline__ T coarse_diag(const CompDev& c, int k) {
   return stencil_of<T>(c)[(long long)k * kStencil + 22];
@@ -513,39 +488,138 @@ __global__ void __launch_bounds__(kBlock) k_outer_update_v4(long long n4, double
   *reinterpret_cast<double2*>(z + 4 * q + 2) = c;
 }
 
-// Galerkin levels: colour = (i mod mx, j mod my, k mod mz); ranks row-major
-// within the class; four ranks per thread.
-template <typename T, bool NOISE>
-__global__ void __launch_bounds__(kBlock) k_coarse_colour(LevelDev L, ColourPass cp, T* __restrict__ v,
-                                                         const T* __restrict__ b, int sweep, Key key,
-                                                         const unsigned long long* __restrict__ cyc) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= cp.gstart[L.ncomp]) return;
+// Load policies for the per-site functions below: LdNC reads through the
+// read-only path (data no block of the launch writes), LdCG reads from L2
+// only (data written by other blocks of the same launch before a grid
+// barrier, which another SM's L1 may hold stale), LdPlain is a plain load.
+struct LdNC {
+  template <typename T>
+  __device__ __forceinline__ static T ld(const T* p) { return __ldg(p); }
+};
+struct LdCG {
+  template <typename T>
+  __device__ __forceinline__ static T ld(const T* p) { return __ldcg(p); }
+};
+struct LdPlain {
+  template <typename T>
+  __device__ __forceinline__ static T ld(const T* p) { return *p; }
+};
+
+// Row k of a Galerkin operator applied to vc (one component's field) in the
+// separable form of the stencil,
+//   sum_dz (s Mz)_dz (w1 . v_plane(k+dz)) + (s Kz)_dz (w2 . v_plane(k+dz)),
+// with w1 = Kx(x)My + Mx(x)Ky and w2 = Mx(x)My on the periodic x/y axes.
+// CENTRE == false leaves out the diagonal term.
+// Separable x/y weights in the kernel's precision (read by value: the level
+// descriptor is a by-value kernel parameter).
+template <typename T>
+__device__ __forceinline__ T sep_w1(const CompDev& c, int q);
+template <>
+__device__ __forceinline__ float sep_w1<float>(const CompDev& c, int q) {
+  return c.w1f[q];
+}
+template <>
+__device__ __forceinline__ double sep_w1<double>(const CompDev& c, int q) {
+  return c.w1[q];
+}
+template <typename T>
+__device__ __forceinline__ T sep_w2(const CompDev& c, int q);
+template <>
+__device__ __forceinline__ float sep_w2<float>(const CompDev& c, int q) {
+  return c.w2f[q];
+}
+template <>
+__device__ __forceinline__ double sep_w2<double>(const CompDev& c, int q) {
+  return c.w2[q];
+}
+
+template <typename T, typename LD, bool CENTRE>
+__device__ __forceinline__ T sep_apply(const CompDev& c, const T* vc, int i, int j, int k) {
+  const int nx = c.nx, ny = c.ny, nz = c.nz;
+  const int xm = i == 0 ? nx - 1 : i - 1, xp = i == nx - 1 ? 0 : i + 1;
+  const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
+  const T* zb = (sizeof(T) == 4 ? (const T*)c.zb32 : (const T*)c.zb64) + k * 10;
+  T w1[9], w2[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    w1[q] = sep_w1<T>(c, q);
+    w2[q] = sep_w2<T>(c, q);
+  }
+  T acc = (T)0;
+#pragma unroll
+  for (int dz = -2; dz <= 2; ++dz) {
+    const int kk = k + dz;
+    if (kk < 0 || kk >= nz) continue;
+    const T* vp = vc + kk * ny * nx;
+    T p1, p2;
+    if (ny == 1) {
+      const T a = LD::ld(vp + xm), cc = LD::ld(vp + xp);
+      p1 = w1[3] * a + w1[5] * cc;
+      p2 = w2[3] * a + w2[5] * cc;
+      if (CENTRE || dz != 0) {
+        const T bb = LD::ld(vp + i);
+        p1 += w1[4] * bb;
+        p2 += w2[4] * bb;
+      }
+    } else {
+      const T* r0 = vp + jm * nx;
+      const T* r1 = vp + j * nx;
+      const T* r2 = vp + jp * nx;
+      const T a0 = LD::ld(r0 + xm), b0 = LD::ld(r0 + i), c0 = LD::ld(r0 + xp);
+      const T a1 = LD::ld(r1 + xm), c1 = LD::ld(r1 + xp);
+      const T a2 = LD::ld(r2 + xm), b2 = LD::ld(r2 + i), c2 = LD::ld(r2 + xp);
+      p1 = w1[0] * a0 + w1[1] * b0 + w1[2] * c0 + w1[3] * a1 + w1[5] * c1 + w1[6] * a2 + w1[7] * b2 + w1[8] * c2;
+      p2 = w2[0] * a0 + w2[1] * b0 + w2[2] * c0 + w2[3] * a1 + w2[5] * c1 + w2[6] * a2 + w2[7] * b2 + w2[8] * c2;
+      if (CENTRE || dz != 0) {
+        const T b1 = LD::ld(r1 + i);
+        p1 += w1[4] * b1;
+        p2 += w2[4] * b1;
+      }
+    }
+    acc += zb[dz + 2] * p1 + zb[5 + dz + 2] * p2;
+  }
+  return acc;
+}
+
+// Heat-bath update of site g of a Galerkin colour pass (g runs over the
+// class sites of all components, component ci from cp.gstart):
+// v_i = (b_i - sum_{j != i} A_ij v_j) / A_ii + n / sqrt(A_ii).  The four
+// sites of a noise group each recompute the group's Philox block and keep
+// their own lane.  Neighbours are of other colours.
+template <typename T, bool NOISE, typename LD>
+__device__ __forceinline__ void coarse_site_at(const LevelDev& L, const ColourPass& cp, T* v, const T* b, int sweep,
+                                               Key key, unsigned long long cy, long long g) {
   const int ci = comp_of(cp.gstart, L.ncomp, g);
   const CompDev& c = L.c[ci];
-  const long long gl = g - cp.gstart[ci];
-  T nz4[4] = {(T)0, (T)0, (T)0, (T)0};
+  const unsigned rank = (unsigned)(g - cp.gstart[ci]);
+  const unsigned nxc = (unsigned)cp.nxc[ci], nyc = (unsigned)cp.nyc[ci];
+  const unsigned t = rank / nxc;
+  const int i = cp.cx[ci] + c.mx * (int)(rank - t * nxc);
+  const int j = cp.cy[ci] + c.my * (int)(t % nyc);
+  const int k = cp.cz[ci] + c.mz * (int)(t / nyc);
+  const T off = sep_apply<T, LD, false>(c, v + c.off, i, j, k);
+  const T diag = coarse_diag<T>(c, k);
+  const long long idx = c.off + (long long)((k * c.ny + j) * c.nx + i);
+  T nv = (LD::ld(b + idx) - off) / diag;
   if (NOISE) {
-    const unsigned long long cy = *cyc;
-    uint4 ctr = make_uint4((uint32_t)gl, ctr1_of(L.level, c.comp_id, cp.colour_id[ci], sweep, 0),
-                           (uint32_t)cy, (uint32_t)(cy >> 32));
-    Normals<T>::get(philox10(ctr, key.k0, key.k1), nz4);
+    T nn;
+    normal_of(philox10(make_uint4(rank >> 2, ctr1_of(L.level, c.comp_id, cp.colour_id[ci], sweep, 0), (uint32_t)cy,
+                                  (uint32_t)(cy >> 32)),
+                       key.k0, key.k1),
+              (int)(rank & 3), &nn);
+    nv += nn / tsqrt(diag);
   }
-#pragma unroll
-  for (int lane = 0; lane < 4; ++lane) {
-    const long long rank = gl * 4 + lane;
-    if (rank >= cp.nsites[ci]) break;
-    const int ii = (int)(rank % cp.nxc[ci]);
-    const long long t = rank / cp.nxc[ci];
-    const int jj = (int)(t % cp.nyc[ci]), kk = (int)(t / cp.nyc[ci]);
-    const int i = cp.cx[ci] + c.mx * ii, j = cp.cy[ci] + c.my * jj, k = cp.cz[ci] + c.mz * kk;
-    const T off = coarse_apply<T>(c, v, i, j, k, true);
-    const T diag = coarse_diag<T>(c, k);
-    const long long idx = c.off + ((long long)k * c.ny + j) * c.nx + i;
-    T nv = (b[idx] - off) / diag;
-    if (NOISE) nv += nz4[lane] / tsqrt(diag);
-    v[idx] = nv;
-  }
+  v[idx] = nv;
+}
+
+// Galerkin levels, one thread per site of the colour class.
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kBlock) k_coarse_site(LevelDev L, ColourPass cp, T* __restrict__ v,
+                                                       const T* __restrict__ b, int sweep, Key key,
+                                                       const unsigned long long* __restrict__ cyc) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cp.gstart[L.ncomp]) return;
+  coarse_site_at<T, NOISE, LdNC>(L, cp, v, b, sweep, key, NOISE ? *cyc : 0ull, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -579,18 +653,15 @@ __global__ void __launch_bounds__(kBlock) k_residual(LevelDev L, const T* __rest
     fine_row<T, T>(c, v, i, j, k, &off, &diag);
     Av = off + diag * v[s];
   } else {
-    Av = coarse_apply<T>(c, v, i, j, k, false);
+    Av = sep_apply<T, LdPlain, true>(c, v + c.off, i, j, k);
   }
   t[s] = b[s] - Av;
 }
 
 // b_c(I,J,K) = sum_f P(f, (I,J,K)) t(f): periodic axes (1/2, 1, 1/2) around
 // fine node 2I; the wall axis from the tabulated columns of P.
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_restrict(LevelDev Lf, LevelDev Lc, const T* __restrict__ t,
-                                                    T* __restrict__ bc) {
-  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= Lc.size) return;
+template <typename T, typename LD>
+__device__ __forceinline__ void restrict_at(const LevelDev& Lf, const LevelDev& Lc, const T* t, T* bc, long long s) {
   int ci, I, J, K;
   site_of(Lc, s, &ci, &I, &J, &K);
   const CompDev& f = Lf.c[ci];
@@ -616,19 +687,23 @@ __global__ void __launch_bounds__(kBlock) k_restrict(LevelDev Lf, LevelDev Lc, c
 #pragma unroll
       for (int qx = -1; qx <= 1; ++qx) {
         const T wx = qx == 0 ? (T)1 : (T)0.5;
-        acc += wz * wy * wx * t[rowb + wrapi(2 * I + qx, f.nx)];
+        acc += wz * wy * wx * LD::ld(t + rowb + wrapi(2 * I + qx, f.nx));
       }
     }
   }
   bc[s] = acc;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_restrict(LevelDev Lf, LevelDev Lc, const T* __restrict__ t,
+                                                    T* __restrict__ bc) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < Lc.size) restrict_at<T, LdPlain>(Lf, Lc, t, bc, s);
+}
+
 // v_f += P v_c: periodic axes: even fine node = coarse node, odd = mean of two.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_prolong(LevelDev Lf, LevelDev Lc, T* __restrict__ v,
-                                                   const T* __restrict__ vc) {
-  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= Lf.size) return;
+__device__ __forceinline__ void prolong_at(const LevelDev& Lf, const LevelDev& Lc, T* v, const T* vc, long long s) {
   int ci, i, j, k;
   site_of(Lf, s, &ci, &i, &j, &k);
   const CompDev& f = Lf.c[ci];
@@ -671,6 +746,125 @@ __global__ void __launch_bounds__(kBlock) k_prolong(LevelDev Lf, LevelDev Lc, T*
         acc += wz * yw[qy] * xw[qx] * vc[c.off + (long long)kc * cplane + (long long)yi[qy] * c.nx + xi[qx]];
   }
   v[s] += acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_prolong(LevelDev Lf, LevelDev Lc, T* __restrict__ v,
+                                                   const T* __restrict__ vc) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < Lf.size) prolong_at<T>(Lf, Lc, v, vc, s);
+}
+
+// ---------------------------------------------------------------------------
+// One Galerkin level as a cooperative launch (all blocks co-resident; grid
+// barriers between colour passes).  Phase 0 (descending half of the V-cycle
+// at this level): mu1 sweeps from the zero start, residual t = b - A v,
+// restriction b_c = P^T t and v_c = 0.  Phase 1 (ascending half):
+// v += P v_c, then mu2 sweeps.  Same arithmetic, counters and order as the
+// per-pass launches; the GPU-wide launch suits a level too large for one
+// thread-block cluster per component yet too small to hide a launch per pass.
+// ---------------------------------------------------------------------------
+constexpr int kMaxCoopColours = 16;
+constexpr unsigned long long kCoopWaitNs = 1000000000ull;   // 1 s bound on one barrier wait
+
+// 512 threads of at most 64 registers: half an SM's register file, so that a
+// block of the launch can share an SM with work of another stream.
+template <typename T>
+struct CoopThreads {
+  static constexpr int value = 512;
+};
+
+template <typename T>
+struct CoopLevel {
+  LevelDev L, Lc;                        // this level and the next coarser one
+  ColourPass cp[kMaxCoopColours];        // colour q of this level
+  int ncolour;
+  T* v;
+  const T* b;
+  T* t;
+  T* bc;
+  T* vc;
+  unsigned* bar;                         // [0..1] 64-bit arrival count, [2] timeout flag
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier.  bar[0..1] hold a 64-bit arrival count that only grows
+// and is a multiple of the grid size when a launch starts (every launch has
+// the same grid and passes all its barriers); bar[2] is the timeout flag.
+// Thread 0 of each block adds its arrival with release semantics (after the
+// block barrier, so the block's writes are ordered before it), takes the
+// barrier's target from the count it saw, and polls with acquire loads.
+// Every wait is bounded: a block that waits longer than kCoopWaitNs, or sees
+// the flag set by another block, sets the flag and returns false; the
+// kernel then returns.
+__device__ __forceinline__ bool coop_barrier(unsigned* bar) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long* count = reinterpret_cast<unsigned long long*>(bar);
+    volatile unsigned* flag = bar + 2;
+    int good = *flag == 0u;
+    unsigned long long old, cur;
+    asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(old) : "l"(count) : "memory");
+    const unsigned long long nb = gridDim.x;
+    const unsigned long long target = (old / nb + 1ull) * nb;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+      asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(cur) : "l"(count) : "memory");
+      if (cur >= target) break;
+      if (!good || *flag != 0u || global_ns() - t0 > kCoopWaitNs) {
+        good = 0;
+        break;
+      }
+    }
+    if (!good) atomicExch(bar + 2, 1u);
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(CoopThreads<T>::value, 2)
+    k_level_coop(const __grid_constant__ CoopLevel<T> P, int phase, int mu1, int mu2, Key key,
+                 const unsigned long long* __restrict__ cyc) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const unsigned long long cy = NOISE ? *cyc : 0ull;
+  const int ncomp = P.L.ncomp;
+  auto sweeps = [&](int first, int count) -> bool {
+    for (int q = 0; q < count; ++q)
+      for (int col = 0; col < P.ncolour; ++col) {
+        const ColourPass& cp = P.cp[col];
+        for (long long g = tid; g < cp.gstart[ncomp]; g += nth)
+          coarse_site_at<T, NOISE, LdCG>(P.L, cp, P.v, P.b, first + q, key, cy, g);
+        if (!coop_barrier(P.bar)) return false;
+      }
+    return true;
+  };
+  if (phase == 0) {
+    if (!sweeps(0, mu1)) return;
+    for (long long s = tid; s < P.L.size; s += nth) {
+      int ci, i, j, k;
+      site_of(P.L, s, &ci, &i, &j, &k);
+      const CompDev& c = P.L.c[ci];
+      P.t[s] = __ldcg(P.b + s) - sep_apply<T, LdCG, true>(c, P.v + c.off, i, j, k);
+    }
+    if (!coop_barrier(P.bar)) return;
+    for (long long s = tid; s < P.Lc.size; s += nth) {
+      restrict_at<T, LdCG>(P.L, P.Lc, P.t, P.bc, s);
+      P.vc[s] = (T)0;
+    }
+  } else {
+    for (long long s = tid; s < P.L.size; s += nth) prolong_at<T>(P.L, P.Lc, P.v, P.vc, s);
+    if (!coop_barrier(P.bar)) return;
+    sweeps(mu1, mu2);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -951,6 +1145,60 @@ inline unsigned grid_for(long long n, int block = kBlock) { return (unsigned)((n
 
 }  // namespace
 
+// Colour q of a Galerkin level: class origin and extents per component, and
+// the first site of each component in the flattened pass (components whose
+// colour count is below q + 1 contribute none).  Returns the pass's sites.
+long long colour_pass_of(const LevelDev& L, int q, ColourPass* cp) {
+  long long gs = 0;
+  for (int ci = 0; ci < L.ncomp; ++ci) {
+    const CompDev& c = L.c[ci];
+    cp->gstart[ci] = gs;
+    cp->nsites[ci] = 0;
+    if (q < c.ncol) {
+      const int cx = q % c.mx, cy = (q / c.mx) % c.my, cz = q / (c.mx * c.my);
+      cp->cx[ci] = cx;
+      cp->cy[ci] = cy;
+      cp->cz[ci] = cz;
+      cp->nxc[ci] = (c.nx - cx + c.mx - 1) / c.mx;
+      cp->nyc[ci] = (c.ny - cy + c.my - 1) / c.my;
+      cp->nzc[ci] = (c.nz - cz + c.mz - 1) / c.mz;
+      cp->colour_id[ci] = q;
+      if (cp->nxc[ci] > 0 && cp->nyc[ci] > 0 && cp->nzc[ci] > 0)
+        cp->nsites[ci] = (long long)cp->nxc[ci] * cp->nyc[ci] * cp->nzc[ci];
+    }
+    if (cp->nxc[ci] <= 0) cp->nxc[ci] = 1;
+    if (cp->nyc[ci] <= 0) cp->nyc[ci] = 1;
+    gs += cp->nsites[ci];
+  }
+  cp->gstart[L.ncomp] = gs;
+  return gs;
+}
+
+// Blocks of a cooperative level launch on the current device: one per SM
+// when a block of CoopThreads<T> threads fits, else 0 (not supported).
+template <typename T>
+int coop_blocks() {
+  static std::atomic<int> cached[64];
+  static std::atomic<bool> init[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (init[dev].load()) return cached[dev].load();
+  int sms = 0, coop = 0, occ1 = 0, occ2 = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_level_coop<T, true>, CoopThreads<T>::value, 0) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_level_coop<T, false>, CoopThreads<T>::value, 0) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    occ1 = occ2 = 0;
+  }
+  const int blocks = coop && occ1 >= 1 && occ2 >= 1 ? sms : 0;
+  cached[dev].store(blocks);
+  init[dev].store(true);
+  return blocks;
+}
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
@@ -998,34 +1246,13 @@ cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool n
   for (int ci = 0; ci < L.ncomp; ++ci) maxcol = maxcol > L.c[ci].ncol ? maxcol : L.c[ci].ncol;
   for (int q = 0; q < maxcol; ++q) {
     ColourPass cp{};
-    long long gs = 0;
-    for (int ci = 0; ci < L.ncomp; ++ci) {
-      const CompDev& c = L.c[ci];
-      cp.gstart[ci] = gs;
-      cp.nsites[ci] = 0;
-      if (q < c.ncol) {
-        const int cx = q % c.mx, cy = (q / c.mx) % c.my, cz = q / (c.mx * c.my);
-        cp.cx[ci] = cx;
-        cp.cy[ci] = cy;
-        cp.cz[ci] = cz;
-        cp.nxc[ci] = (c.nx - cx + c.mx - 1) / c.mx;
-        cp.nyc[ci] = (c.ny - cy + c.my - 1) / c.my;
-        cp.nzc[ci] = (c.nz - cz + c.mz - 1) / c.mz;
-        cp.colour_id[ci] = q;
-        if (cp.nxc[ci] > 0 && cp.nyc[ci] > 0 && cp.nzc[ci] > 0)
-          cp.nsites[ci] = (long long)cp.nxc[ci] * cp.nyc[ci] * cp.nzc[ci];
-      }
-      if (cp.nxc[ci] <= 0) cp.nxc[ci] = 1;
-      if (cp.nyc[ci] <= 0) cp.nyc[ci] = 1;
-      gs += (cp.nsites[ci] + 3) / 4;
-    }
-    cp.gstart[L.ncomp] = gs;
+    const long long gs = colour_pass_of(L, q, &cp);
     if (gs == 0) continue;
     prof::Scope ps(SELM_K_COARSE_SWEEP, st);
     if (noise)
-      k_coarse_colour<T, true><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, sweep, key, cyc);
+      k_coarse_site<T, true><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, sweep, key, cyc);
     else
-      k_coarse_colour<T, false><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, sweep, key, cyc);
+      k_coarse_site<T, false><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, sweep, key, cyc);
   }
   return cudaGetLastError();
 }
@@ -1049,6 +1276,48 @@ cudaError_t launch_prolong(const LevelDev& Lf, const LevelDev& Lc, T* v, const T
   prof::Scope ps(SELM_K_PROLONG, st);
   k_prolong<T><<<grid_for(Lf.size), kBlock, 0, st>>>(Lf, Lc, v, vc);
   return cudaGetLastError();
+}
+
+template <typename T>
+bool level_coop_supported(const LevelDev& L) {
+  if (L.level < 1) return false;
+  for (int ci = 0; ci < L.ncomp; ++ci)
+    if (L.c[ci].ncol > kMaxCoopColours) return false;
+  return coop_blocks<T>() > 0;
+}
+
+template <typename T>
+cudaError_t launch_level_coop(const LevelDev& L, const LevelDev& Lc, int phase, int mu1, int mu2, T* v, const T* b,
+                              T* t, T* bc, T* vc, unsigned* bar, bool noise, Key key, const unsigned long long* cyc,
+                              cudaStream_t st) {
+  const int blocks = coop_blocks<T>();
+  if (blocks <= 0 || !level_coop_supported<T>(L)) return cudaErrorNotSupported;
+  CoopLevel<T> P{};
+  P.L = L;
+  P.Lc = Lc;
+  int maxcol = 0;
+  for (int ci = 0; ci < L.ncomp; ++ci) maxcol = maxcol > L.c[ci].ncol ? maxcol : L.c[ci].ncol;
+  P.ncolour = maxcol;
+  for (int q = 0; q < maxcol; ++q) colour_pass_of(L, q, &P.cp[q]);
+  P.v = v;
+  P.b = b;
+  P.t = t;
+  P.bc = bc;
+  P.vc = vc;
+  P.bar = bar;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(CoopThreads<T>::value);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  prof::Scope ps(SELM_K_COARSE_SWEEP, st);
+  if (noise) return cudaLaunchKernelEx(&cfg, k_level_coop<T, true>, P, phase, mu1, mu2, key, cyc);
+  return cudaLaunchKernelEx(&cfg, k_level_coop<T, false>, P, phase, mu1, mu2, key, cyc);
 }
 
 template <typename T>
@@ -1184,6 +1453,9 @@ cudaError_t launch_philox(const uint32_t* ctr, Key key, uint32_t* out, int n, cu
   template cudaError_t launch_residual<T>(const LevelDev&, const T*, const T*, T*, cudaStream_t);           \
   template cudaError_t launch_restrict<T>(const LevelDev&, const LevelDev&, const T*, T*, cudaStream_t);    \
   template cudaError_t launch_prolong<T>(const LevelDev&, const LevelDev&, T*, const T*, cudaStream_t);     \
+  template bool level_coop_supported<T>(const LevelDev&);                                                   \
+  template cudaError_t launch_level_coop<T>(const LevelDev&, const LevelDev&, int, int, int, T*, const T*, T*, T*, \
+                                            T*, unsigned*, bool, Key, const unsigned long long*, cudaStream_t);  \
   template cudaError_t launch_coarsest<T>(const LevelDev&, T*, const T*, bool, Key,                         \
                                           const unsigned long long*, cudaStream_t);                         \
   template cudaError_t launch_outer_residual<T>(const LevelDev&, const double*, const double*, T*, double*, \

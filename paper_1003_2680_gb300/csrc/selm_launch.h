@@ -27,6 +27,22 @@ cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* t, 
 template <typename T>
 cudaError_t launch_prolong(const LevelDev& Lf, const LevelDev& Lc, T* v, const T* vc,
                            cudaStream_t st);
+// One Galerkin level (L.level >= 1) as a single cooperative launch over the
+// GPU.  phase 0: the descending half of the V-cycle at this level (mu1
+// sweeps from the zero start in v, residual into t, restriction into bc,
+// vc = 0); phase 1: the ascending half (v += P vc, then mu2 sweeps).  `bar`:
+// 4 zeroed, 8-byte aligned words of device memory, the launch's grid barrier,
+// reserved for the launches of one stream order (two launches that may
+// overlap need distinct words).
+// After a barrier wait timed out, bar[2] is non-zero, the level's result is
+// undefined and the caller reports the error and zeroes the words.
+// level_coop_supported() tells whether the device and the level admit it.
+template <typename T>
+cudaError_t launch_level_coop(const LevelDev& L, const LevelDev& Lc, int phase, int mu1, int mu2, T* v, const T* b,
+                              T* t, T* bc, T* vc, unsigned* bar, bool noise, Key key, const unsigned long long* cyc,
+                              cudaStream_t st);
+template <typename T>
+bool level_coop_supported(const LevelDev& L);
 template <typename T>
 cudaError_t launch_coarsest(const LevelDev& L, T* v, const T* b, bool noise, Key key,
                             const unsigned long long* cyc, cudaStream_t st);

@@ -20,6 +20,8 @@ SELM_COARSE_CHOLESKY, SELM_COARSE_SMOOTH = 0, 1
 SELM_SYS_VELOCITY, SELM_SYS_PRESSURE = 0, 1
 SELM_OPT_COARSE_ENGINE = 1
 SELM_OPT_ENGINE_CLUSTER = 2
+SELM_OPT_ENGINE_LEVEL = 3
+SELM_OPT_LEVEL_COOP = 4
 
 _STATUS = {0: "SELM_OK", 1: "SELM_EINVAL", 2: "SELM_ENOMEM", 3: "SELM_ECUDA", 4: "SELM_ENOCONV",
            5: "SELM_ETIMEOUT", 6: "SELM_EBUSY"}

@@ -173,6 +173,46 @@ def test_vcycle_engine_and_per_pass_paths(prec, dim, n, levels, noise, engine):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim,n,levels", ENGINE_GRIDS)
+@pytest.mark.parametrize("noise", [0, 1])
+@pytest.mark.parametrize("coop", [1, 0])
+def test_vcycle_engine_from_level_2(prec, dim, n, levels, noise, coop):
+    """Level 1 above the engine: one cooperative launch per half V-cycle
+    (coop=1) or one GPU-wide launch per colour pass (coop=0)."""
+    m, osys, dt, tol = make(dim, n, levels, prec)
+    S.selm_mg_set_option(m.h, S.SELM_OPT_ENGINE_LEVEL, 2)
+    S.selm_mg_set_option(m.h, S.SELM_OPT_LEVEL_COOP, coop)
+    l0, csize, smem = S.selm_mg_engine_info(m.h)
+    assert l0 == 2 and csize >= 1 and smem > 0
+    shapes = osys.shapes(0)
+    v0 = round_like(selm_inputs.fields(shapes, seed=33), dt)
+    b0 = round_like(selm_inputs.fields(shapes, seed=34), dt)
+    v = to_dev(m.h, v0, dt)
+    S.selm_mg_vcycle(m.h, 0, v, to_dev(m.h, b0, dt), cycle=43, noise=noise)
+    want = [x.copy() for x in v0]
+    multigrid.vcycle(osys, 0, want, b0, philox.PhiloxNoise(11, 3, 43), float(noise))
+    assert rel(from_dev(m.h, v), want) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fac_solve_with_cooperative_level(prec):
+    """Deterministic FAC solve with level 1 in cooperative launches: same
+    cycle count (FP64) and solution as the oracle, no barrier timeout."""
+    dim, n, levels = 3, 64, 4
+    m, osys, dt, tol = make(dim, n, levels, prec)
+    S.selm_mg_set_option(m.h, S.SELM_OPT_ENGINE_LEVEL, 2)
+    assert S.selm_mg_engine_info(m.h)[0] == 2
+    b0 = selm_inputs.fields(osys.shapes(0), seed=15)
+    z = empty(m.h, torch.float64)
+    cycles, res = S.selm_mg_fac_solve(m.h, 0, z, to_dev(m.h, b0, torch.float64), 1e-10, 50)
+    assert res <= 1e-10
+    want, ocycles, _ = multigrid.solve(osys, b0, tol=1e-10)
+    if prec == "fp64":
+        assert cycles == ocycles
+    assert rel(from_dev(m.h, z), want) < (1e-12 if prec == "fp64" else 1e-8)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("dim,n,levels", GRIDS)
 def test_fac_solve(prec, dim, n, levels):
     m, osys, dt, tol = make(dim, n, levels, prec)

@@ -36,16 +36,11 @@ namespace cg = cooperative_groups;
 namespace selm {
 namespace {
 
-// Threads per CTA: FP32 fits 1024 threads in the 64-register budget; the
-// FP64 variant needs more registers per thread and runs 512.
+// Threads per CTA: 512, which leaves up to 128 registers a thread for the
+// unrolled 45-point row (at 1024 threads the 64-register cap spills it and
+// the colour passes on the engine's levels run slower).
 template <typename T>
-struct EngThreads;
-template <>
-struct EngThreads<float> {
-  static constexpr int value = 1024;
-};
-template <>
-struct EngThreads<double> {
+struct EngThreads {
   static constexpr int value = 512;
 };
 
@@ -58,16 +53,22 @@ __device__ __forceinline__ T ld_cg(const T* p) {
   return __ldcg(p);
 }
 
+// Position of x in a shared v row: the even x first, then the odd x, so that
+// the sites of a colour class (x modulus 2) are consecutive words.
+__device__ __forceinline__ int xpos(int i, int half) { return (i & 1) ? half + (i >> 1) : (i >> 1); }
+
 // Per-CTA view of one level.
 template <typename T>
 struct View {
   const EngLevel<T>* L;
   int z0, z1;          // owned planes [z0, z1)
-  T* v;                // local v buffer: planes [z0-2, z1+2)
-  int plane;           // nx * ny
+  T* v;                // local v buffer: planes [z0-2, z1+2), pitches L->rp, L->pp
+  int plane;           // nx * ny (sites per plane in the natural field order)
   const T* tab;        // shared: [nz][12] = z bands (10), 1/A_ii, 1/sqrt(A_ii)
   const EngColour* col;  // shared: colour classes of this level for this CTA
-  __device__ __forceinline__ int loc(int i, int j, int k) const { return ((k - z0 + 2) * L->ny + j) * L->nx + i; }
+  __device__ __forceinline__ int loc(int i, int j, int k) const {
+    return (k - z0 + 2) * L->pp + j * L->rp + xpos(i, L->half);
+  }
 };
 
 template <typename T>
@@ -94,39 +95,40 @@ __device__ __forceinline__ View<T> make_view(const EngLevel<T>& L, unsigned char
 template <typename T, bool CENTRE>
 __device__ __forceinline__ T stencil_row(const View<T>& w, int i, int j, int k) {
   const EngLevel<T>& L = *w.L;
-  const int nx = L.nx, ny = L.ny;
-  const int xm = i == 0 ? nx - 1 : i - 1, xp = i == nx - 1 ? 0 : i + 1;
+  const int nx = L.nx, ny = L.ny, rp = L.rp;
+  const int xm = xpos(i == 0 ? nx - 1 : i - 1, L.half), xp = xpos(i == nx - 1 ? 0 : i + 1, L.half);
+  const int x0 = xpos(i, L.half);
   const T* zb = w.tab + k * 12;
   T acc = (T)0;
 #pragma unroll
   for (int dz = -2; dz <= 2; ++dz) {
     const int kk = k + dz;
     if (kk < 0 || kk >= L.nz) continue;
-    const T* vp = w.v + (kk - w.z0 + 2) * ny * nx;
+    const T* vp = w.v + (kk - w.z0 + 2) * L.pp;
     T p1, p2;
     if (ny == 1) {
       const T a = vp[xm], c = vp[xp];
       p1 = L.w1[3] * a + L.w1[5] * c;
       p2 = L.w2[3] * a + L.w2[5] * c;
       if (CENTRE || dz != 0) {
-        const T b = vp[i];
+        const T b = vp[x0];
         p1 += L.w1[4] * b;
         p2 += L.w2[4] * b;
       }
     } else {
       const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
-      const T* r0 = vp + jm * nx;
-      const T* r1 = vp + j * nx;
-      const T* r2 = vp + jp * nx;
-      const T a0 = r0[xm], b0 = r0[i], c0 = r0[xp];
+      const T* r0 = vp + jm * rp;
+      const T* r1 = vp + j * rp;
+      const T* r2 = vp + jp * rp;
+      const T a0 = r0[xm], b0 = r0[x0], c0 = r0[xp];
       const T a1 = r1[xm], c1 = r1[xp];
-      const T a2 = r2[xm], b2 = r2[i], c2 = r2[xp];
+      const T a2 = r2[xm], b2 = r2[x0], c2 = r2[xp];
       p1 = L.w1[0] * a0 + L.w1[1] * b0 + L.w1[2] * c0 + L.w1[3] * a1 + L.w1[5] * c1 + L.w1[6] * a2 +
            L.w1[7] * b2 + L.w1[8] * c2;
       p2 = L.w2[0] * a0 + L.w2[1] * b0 + L.w2[2] * c0 + L.w2[3] * a1 + L.w2[5] * c1 + L.w2[6] * a2 +
            L.w2[7] * b2 + L.w2[8] * c2;
       if (CENTRE || dz != 0) {
-        const T b1 = r1[i];
+        const T b1 = r1[x0];
         p1 += L.w1[4] * b1;
         p2 += L.w2[4] * b1;
       }
@@ -160,7 +162,7 @@ struct Sync {
 // geometry, z bands, inverse diagonals and noise scales come from the
 // shared-memory tables staged for the level.
 template <typename T, bool NOISE>
-__device__ void colour_pass(const View<T>& w, int level, int q, int sweep, const T* b, bool b_local, Key key,
+__device__ void colour_pass(const View<T>& w, int level, int q, int sweep, const T* b, bool b_local, int boff, Key key,
                             unsigned long long cyc, int rank, int csize, bool cluster) {
   const EngLevel<T>& L = *w.L;
   const EngColour cc = w.col[q];
@@ -186,7 +188,7 @@ __device__ void colour_pass(const View<T>& w, int level, int q, int sweep, const
     }
     const int i = cc.cx + L.mx * ii, j = cc.cy + L.my * jj, k = cc.cz + L.mz * kk;
     const int gidx = (k * L.ny + j) * L.nx + i;
-    const T bb = b_local ? b[gidx] : ld_cg(b + gidx);
+    const T bb = b_local ? b[gidx - boff] : ld_cg(b + gidx);
     const T* tr = w.tab + k * 12;
     const T off = stencil_row<T, false>(w, i, j, k);
     T nv = (bb - off) * tr[10];
@@ -206,7 +208,7 @@ __device__ void colour_pass(const View<T>& w, int level, int q, int sweep, const
         const int z0b = min(r2 * L.P, L.nz), z1b = min(z0b + L.P, L.nz);
         if (z0b >= z1b || k < z0b - 2 || k >= z1b + 2) continue;
         T* rem = cl.map_shared_rank(w.v, r2);
-        rem[((k - z0b + 2) * L.ny + j) * L.nx + i] = nv;
+        rem[(k - z0b + 2) * L.pp + j * L.rp + xpos(i, L.half)] = nv;
       }
     }
   }
@@ -214,13 +216,13 @@ __device__ void colour_pass(const View<T>& w, int level, int q, int sweep, const
 
 template <typename T>
 __device__ void zero_local(const View<T>& w) {
-  const int n = (w.z1 - w.z0 + 4) * w.plane;
+  const int n = (w.z1 - w.z0 + 4) * w.L->pp;
   for (int q = threadIdx.x; q < n; q += blockDim.x) w.v[q] = (T)0;
 }
 
 // t = b - A v on the owned planes; t written at field index (global or local buffer).
 template <typename T>
-__device__ void residual(const View<T>& w, const T* b, bool b_local, T* t) {
+__device__ void residual(const View<T>& w, const T* b, bool b_local, int boff, T* t) {
   const EngLevel<T>& L = *w.L;
   const int n = (w.z1 - w.z0) * w.plane;
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
@@ -228,7 +230,7 @@ __device__ void residual(const View<T>& w, const T* b, bool b_local, T* t) {
     const int r = q / L.nx;
     const int j = r % L.ny, k = w.z0 + r / L.ny;
     const int gidx = (k * L.ny + j) * L.nx + i;
-    const T bb = b_local ? b[gidx] : ld_cg(b + gidx);
+    const T bb = b_local ? b[gidx - boff] : ld_cg(b + gidx);
     t[gidx] = bb - stencil_row<T, true>(w, i, j, k);
   }
 }
@@ -306,7 +308,7 @@ __device__ void prolong_into(const View<T>& w, const EngLevel<T>& Lc, const T* v
         if (yw[a] == (T)0) continue;
         for (int c = 0; c < 2; ++c) {
           if (xw[c] == (T)0) continue;
-          const int idx = vc_local ? (((kc - vc_z0 + 2) * Lc.ny + yi[a]) * Lc.nx + xi[c])
+          const int idx = vc_local ? ((kc - vc_z0 + 2) * Lc.pp + yi[a] * Lc.rp + xpos(xi[c], Lc.half))
                                    : ((kc * Lc.ny + yi[a]) * Lc.nx + xi[c]);
           acc += wz * yw[a] * xw[c] * (vc_local ? vc[idx] : ld_cg(vc + idx));
         }
@@ -318,9 +320,22 @@ __device__ void prolong_into(const View<T>& w, const EngLevel<T>& Lc, const T* v
 
 template <typename T>
 __device__ void store_owned(const View<T>& w, T* g) {
+  const EngLevel<T>& L = *w.L;
   const int n = (w.z1 - w.z0) * w.plane;
   const int base = w.z0 * w.plane;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) g[base + q] = w.v[2 * w.plane + q];
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int i = q % L.nx;
+    const int r = q / L.nx;
+    g[base + q] = w.v[w.loc(i, r % L.ny, w.z0 + r / L.ny)];
+  }
+}
+
+// Copies b of the owned planes [z0, z1) (natural order) into shared memory.
+template <typename T>
+__device__ void load_owned(const View<T>& w, const T* g, T* dst) {
+  const int n = (w.z1 - w.z0) * w.plane;
+  const T* src = g + w.z0 * w.plane;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) dst[q] = ld_cg(src + q);
 }
 
 template <typename T>
@@ -356,12 +371,12 @@ __device__ void coarsest_step(const View<T>& w, int level, const T* b, double* y
 }
 
 template <typename T, bool NOISE>
-__device__ void sweeps(const View<T>& w, int level, int first_sweep, int count, const T* b, bool b_local, Key key,
+__device__ void sweeps(const View<T>& w, int level, int first_sweep, int count, const T* b, bool b_local, int boff, Key key,
                        unsigned long long cyc, int rank, int csize, bool cluster) {
   const Sync sync{cluster};
   for (int s = 0; s < count; ++s)
     for (int q = 0; q < w.L->ncol; ++q) {
-      colour_pass<T, NOISE>(w, level, q, first_sweep + s, b, b_local, key, cyc, rank, csize, cluster);
+      colour_pass<T, NOISE>(w, level, q, first_sweep + s, b, b_local, boff, key, cyc, rank, csize, cluster);
       sync();
     }
 }
@@ -442,12 +457,20 @@ __global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const
     w.tab = tabs[0];
     w.col = scol[0];
     zero_local(w);
+    // b of the owned planes in shared memory when the plan has room for it
+    const bool bl = L.sb >= 0;
+    const T* bsrc = bl ? (const T*)(smem + L.sb) : L.gb;
+    const int boff = bl ? w.z0 * w.plane : 0;
+    if (bl) load_owned(w, L.gb, (T*)(smem + L.sb));
     cl.sync();
-    sweeps<T, NOISE>(w, l, 0, mu1, L.gb, false, key, cyc, rank, csize, true);
-    residual(w, L.gb, false, L.gt);
+    sweeps<T, NOISE>(w, l, 0, mu1, bsrc, bl, boff, key, cyc, rank, csize, true);
+    residual(w, bsrc, bl, boff, L.gt);
     cl.sync();
-    const int Z0 = Lc.cluster ? min(rank * Lc.P, Lc.nz) : (rank == 0 ? 0 : Lc.nz);
-    const int Z1 = Lc.cluster ? min(Z0 + Lc.P, Lc.nz) : Lc.nz;
+    // the coarse planes of the restriction are split over the cluster's CTAs
+    // (also when the coarse level is held by CTA 0: it reads them back)
+    const int Pc = (Lc.nz + csize - 1) / csize;
+    const int Z0 = min(rank * Pc, Lc.nz);
+    const int Z1 = min(Z0 + Pc, Lc.nz);
     restrict_to(L, Lc, L.gt, false, Lc.gb, Z0, Z1);
     cl.sync();
   }
@@ -475,13 +498,13 @@ __global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const
         __syncthreads();
         break;
       }
-      sweeps<T, NOISE>(w, k, 0, mu1, b, true, key, cyc, 0, 1, false);
+      sweeps<T, NOISE>(w, k, 0, mu1, b, true, 0, key, cyc, 0, 1, false);
       if (k == lc) {
-        sweeps<T, NOISE>(w, k, mu1, mu2, b, true, key, cyc, 0, 1, false);
+        sweeps<T, NOISE>(w, k, mu1, mu2, b, true, 0, key, cyc, 0, 1, false);
         break;
       }
       const EngLevel<T>& Lc = sl[1];
-      residual(w, b, true, (T*)(smem + L.st));
+      residual(w, b, true, 0, (T*)(smem + L.st));
       __syncthreads();
       restrict_to(L, Lc, (const T*)(smem + L.st), true, (T*)(smem + Lc.sb), 0, Lc.nz);
       __syncthreads();
@@ -497,7 +520,7 @@ __global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const
       w.col = scol[0];
       prolong_into(w, Lc, (const T*)(smem + Lc.sv), true, 0);
       __syncthreads();
-      sweeps<T, NOISE>(w, k, mu1, mu2, (const T*)(smem + L.sb), true, key, cyc, 0, 1, false);
+      sweeps<T, NOISE>(w, k, mu1, mu2, (const T*)(smem + L.sb), true, 0, key, cyc, 0, 1, false);
     }
     stage(&sl[0], &E->lev[lsingle]);
     {
@@ -518,7 +541,9 @@ __global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const
     w.col = scol[0];
     prolong_into(w, Lc, Lc.gv, false, 0);
     cl.sync();
-    sweeps<T, NOISE>(w, k, mu1, mu2, L.gb, false, key, cyc, rank, csize, true);
+    const bool bl = L.sb >= 0;   // staged on the way down, untouched since
+    sweeps<T, NOISE>(w, k, mu1, mu2, bl ? (const T*)(smem + L.sb) : L.gb, bl, bl ? w.z0 * w.plane : 0, key, cyc, rank,
+                     csize, true);
     store_owned(w, L.gv);
     cl.sync();
   }
@@ -533,8 +558,36 @@ size_t level_bytes_cluster(const LevelDev& L, int c, int C) {
 
 inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Pitches of a level's shared v slab.  A warp of a colour pass holds
+// consecutive ranks of the class: x runs fastest (nx/2 sites of one parity,
+// consecutive words within a row), then y in steps of 2, then z in steps of
+// mz.  The row pitch rp is padded so that the rows one warp spans start on
+// distinct banks (2 rp = sites per row, modulo 32 words), and the plane
+// pitch pp likewise for the planes one warp spans (mz pp = sites per plane,
+// modulo 32), when a warp spans more than one row or plane.
+void slab_pitches(int nx, int ny, int mz, int* half, int* rp, int* pp) {
+  const int h = (nx + 1) / 2;
+  *half = h;
+  int r = nx;
+  if (ny > 1 && h < 32) {
+    const int want = (((h + 1) & ~1) % 32) / 2;   // rp == want (mod 16)
+    r = nx + (((want - nx) % 16) + 16) % 16;
+  }
+  *rp = r;
+  int p = r * ny;
+  const int per_plane = h * (ny > 1 ? (ny + 1) / 2 : 1);
+  if (per_plane < 32 && mz > 0) {
+    for (int c = p; c < p + 32; ++c)
+      if ((long long)mz * c % 32 == per_plane % 32) {
+        p = c;
+        break;
+      }
+  }
+  *pp = p;
+}
+
 template <typename T>
-bool try_plan(const LevelDev* levs, int L, int l0, int C, size_t smem_cap, EnginePlanT<T>* out) {
+bool try_plan(const LevelDev* levs, int L, int l0, int C, bool stage_b, size_t smem_cap, EnginePlanT<T>* out) {
   // cluster levels first (largest), then single levels
   const int ncomp = levs[0].ncomp;
   size_t need_max = 0;
@@ -556,7 +609,8 @@ bool try_plan(const LevelDev* levs, int L, int l0, int C, size_t smem_cap, Engin
       e.cluster = single ? 0 : 1;
       if (e.cluster) any_cluster = true;
       e.P = single ? d.nz : (d.nz + C - 1) / C;
-      const size_t vbytes = (size_t)(e.P + 4) * d.nx * d.ny * sizeof(T);
+      slab_pitches(d.nx, d.ny, d.mz, &e.half, &e.rp, &e.pp);
+      const size_t vbytes = (size_t)(e.P + 4) * e.pp * sizeof(T);
       e.sv = (int)off;
       off = align16(off + vbytes);
       if (single) {
@@ -566,6 +620,10 @@ bool try_plan(const LevelDev* levs, int L, int l0, int C, size_t smem_cap, Engin
         off = align16(off + (size_t)sites * sizeof(T));
       } else {
         e.sb = e.st = -1;
+        if (stage_b) {   // b of the owned planes
+          e.sb = (int)off;
+          off = align16(off + (size_t)e.P * d.nx * d.ny * sizeof(T));
+        }
       }
     }
     const CompDev& dc = levs[L - 1].c[c];
@@ -688,7 +746,10 @@ bool plan_coarse_engine(const LevelDev* levs, int L, void* const* gb, void* cons
       if (C > 1 && !cluster_ok) continue;
       if (want_cluster > 0 && C > want_cluster) continue;
       EnginePlanT<T> cand{};
-      if (!try_plan<T>(levs, L, l0, C, smem_cap, &cand)) continue;
+      // with b of the cluster levels staged in shared memory if it fits
+      if (!try_plan<T>(levs, L, l0, C, true, smem_cap, &cand) &&
+          !try_plan<T>(levs, L, l0, C, false, smem_cap, &cand))
+        continue;
       // The dynamic shared-memory limit is a per-kernel setting shared by every
       // handle of the process: raise it once to the device maximum so that
       // plans of any size stay launchable.

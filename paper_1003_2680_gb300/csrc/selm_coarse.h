@@ -20,6 +20,8 @@ struct EngLevel {
   int comp_id;
   int cluster;        // 1: z-slabs over the cluster's CTAs; 0: held by CTA 0
   int P;              // planes per CTA (cluster levels) or nz (single levels)
+  int half;           // shared v rows: even x at [0, half), odd x at [half, nx)
+  int rp, pp;         // shared v row and plane pitch (elements; padded against bank conflicts)
   int sv, sb, st;     // shared-memory byte offsets of v (with 2 halo planes per side), b, t
   const T* S;         // [nz][45] stencil
   const T* zb;        // [nz][10]: s*Mz row (offsets -2..2), then s*Kz row

@@ -200,10 +200,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+# Sources that define the kernels of the uniform-grid path (the profiled ones).
+PROFILED_SOURCES = ["selm_kernels.cu", "selm_coarse.cu", "selm_coarse.h", "selm_devmath.h", "selm_internal.h",
+                    "selm_launch.h"]
+
+
 def kernel_source_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1003_2680_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in PROFILED_SOURCES:
         h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -222,33 +227,48 @@ def ncu_traffic(kernel_class, n):
     return float(m_tr.group(1))
 
 
-def sweep_bytes_per_launch(S, h, kernel_class):
-    """Algorithmic bytes of one launch of the kernel class, averaged over one V-cycle.
+def pass_bytes(e, sizes, ncols):
+    """Algorithmic bytes of one colour pass over the components of a level:
+    the pass reads every unknown of its level once (the neighbours of the
+    updated colour), reads b and writes v at the updated sites,
+    e * (N_level + 2 N_colour) per component present in the pass."""
+    total = 0.0
+    for q in range(max(ncols)):
+        total += sum(e * (n + 2 * n / nc) for n, nc in zip(sizes, ncols) if q < nc)
+    return total
 
-    A colour pass reads every unknown of its level once (the neighbours of
-    the updated colour), reads b and writes v at the updated sites:
-    e * (N_level + 2 N_colour).
-    """
+
+def system_sizes(S, h, system, lev):
+    ncomp = S.selm_mg_ncomp(h, system)
+    out = []
+    for c in range(ncomp):
+        (nx, ny, nz), _, _ = S.selm_mg_layout(h, system, lev, c)
+        out.append(nx * ny * nz)
+    return out
+
+
+def fine_bytes_per_launch(S, h):
+    """One red-black colour launch on the finest velocity level: reads all of
+    v and b at half the sites, writes v at half the sites."""
     e = S.selm_mg_inner_bytes(h)
-    levels = S.selm_mg_levels(h, 0)
-    ncomp = S.selm_mg_ncomp(h, 0)
-    total, launches = 0.0, 0
-    for lev in range(levels - 1):
-        sizes = []
-        for c in range(ncomp):
-            (nx, ny, nz), off, size = S.selm_mg_layout(h, 0, lev, c)
-            sizes.append(nx * ny * nz)
-        if lev == 0 and kernel_class == "fine_sweep":
-            N = sum(sizes)
-            total += 2 * (e * (N + 2 * N / 2))
-            launches += 2
-        elif lev > 0 and kernel_class == "coarse_sweep":
-            ncols = [12 if c < ncomp - 1 else 8 for c in range(ncomp)]
-            for q in range(max(ncols)):
-                present = [c for c in range(ncomp) if q < ncols[c]]
-                total += sum(e * (sizes[c] + 2 * sizes[c] / ncols[c]) for c in present)
-                launches += 1
-    return total / max(launches, 1)
+    N = sum(system_sizes(S, h, 0, 0))
+    return e * (N + 2 * N / 2)
+
+
+def coarse_bytes_per_vcycle(S, h, system, sweeps=4):
+    """Algorithmic bytes of the Galerkin levels of one V-cycle of a system
+    (every colour pass of every sweep; colour counts 12, or 8 for a component
+    whose wall axis is vertex-type)."""
+    e = S.selm_mg_inner_bytes(h)
+    levels = S.selm_mg_levels(h, system)
+    total = 0.0
+    for lev in range(1, levels - 1):
+        sizes = system_sizes(S, h, system, lev)
+        ncols = [12] * len(sizes)
+        if system == 0 and len(sizes) > 1:
+            ncols[-1] = 8
+        total += sweeps * pass_bytes(e, sizes, ncols)
+    return total
 
 
 # ---------------------------------------------------------------------------
@@ -520,8 +540,12 @@ def main():
     prof_steps = min(args.steps, 3)
     S.selm_profile_reset()
     S.selm_profile_enable(True)
+    vel_cycles = pres_cycles = 0
     for _ in range(prof_steps):
         one_step()
+        st = S.selm_mg_stats(h)
+        vel_cycles += st[0] + SAMPLE_CYCLES
+        pres_cycles += st[1]
     torch.cuda.synchronize()
     S.selm_profile_enable(False)
     per_class = {}
@@ -532,12 +556,18 @@ def main():
     tot_ms = sum(v["ms"] for v in per_class.values()) or 1.0
     dominant = max(per_class, key=lambda k: per_class[k]["ms"])
     peak, peak_kind = measured_peaks()
+    coarse_bytes = vel_cycles * coarse_bytes_per_vcycle(S, h, 0)
+    if proj == S.SELM_PROJ_MAC:
+        coarse_bytes += pres_cycles * coarse_bytes_per_vcycle(S, h, 1)
     roof = None
     for name in (dominant, "fine_sweep"):
         if name not in ("fine_sweep", "coarse_sweep") or per_class[name]["launches"] == 0:
             continue
         avg_s = per_class[name]["ms"] / per_class[name]["launches"] / 1e3
-        bytes_launch = sweep_bytes_per_launch(S, h, name)
+        if name == "fine_sweep":
+            bytes_launch = fine_bytes_per_launch(S, h)
+        else:   # engine and cooperative launches: the coarse bytes of the profiled steps over their launches
+            bytes_launch = coarse_bytes / per_class[name]["launches"]
         achieved = bytes_launch / avg_s / 1e9
         entry = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                  "frac": achieved / peak, "peak_source": peak_kind,

@@ -137,9 +137,11 @@ def bandwidth(mat, periodic):
 class CompLevel:
     """One scalar component on one multigrid level (separable operator)."""
 
-    def __init__(self, comp, level, kinds, ncells, K, M, scale):
+    def __init__(self, comp, level, kinds, ncells, K, M, scale, red_black=None):
         self.comp = comp            # component id (axis of the velocity it carries)
         self.level = level
+        # red-black colouring (the 5/7-point top level); else colour moduli
+        self.red_black = (level == 0) if red_black is None else bool(red_black)
         self.kinds = kinds          # (kind_x, kind_y, kind_z)
         self.ncells = ncells        # cells per axis at this level
         self.K = K                  # dense 1-D factors, axis order x, y, z
@@ -207,8 +209,9 @@ class CompLevel:
     def _colour_classes(self):
         """List of (colour id, index tuple) in visiting order, sites in rank order.
 
-        Level 0: red-black, colour = (i + j + k) mod 2, red (0) first; valid
-        because the top-level operator is the 5/7-point stencil (reading R2).
+        Level 0 (or a level flagged red-black): colour = (i + j + k) mod 2,
+        red (0) first; valid because the operator is the 5/7-point stencil
+        (reading R2).
         Level >= 1: the Galerkin stencil couples offsets up to the factor
         bandwidths b_d, so colour = (i mod m_x, j mod m_y, k mod m_z) with
         m_d = b_d + 1 and colour id c_x + m_x (c_y + m_y c_z), visited in
@@ -216,7 +219,7 @@ class CompLevel:
         """
         nz, ny, nx = self.shape
         classes = []
-        if self.level == 0:
+        if self.red_black:
             assert nx % 2 == 0
             for c in (0, 1):
                 k, j, m = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx // 2),

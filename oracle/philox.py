@@ -15,7 +15,9 @@ header):
 * key   = (lo32(seed) ^ hi32(instance),  hi32(seed) ^ lo32(instance))
 * ctr0  = group index = (rank of the site within its colour class) >> 2
 * ctr1  = level | comp << 4 | colour << 8 | sweep << 12 | kind << 20
-          (kind 0 = smoother sweep, kind 1 = exact coarsest-level sample)
+          (kind 0 = smoother sweep, kind 1 = exact coarsest-level sample,
+          kind 2 = sweep of a refined patch, whose sites are addressed by
+          their linear index in the patch array instead of a class rank)
 * ctr2, ctr3 = lo32(cycle), hi32(cycle)   (cycle = chain step counter)
 
 One Philox call yields four 32-bit words w0..w3 -> uniforms
@@ -36,6 +38,7 @@ _MASK32 = 0xFFFFFFFF
 
 KIND_SWEEP = 0
 KIND_COARSEST = 1
+KIND_PATCH = 2
 
 
 def philox4x32_10(ctr, key):
@@ -103,6 +106,20 @@ def normals_for_ranks(key, ctr1, cycle, nsites):
     return n.reshape(-1)[:nsites]
 
 
+def normals_for_indices(key, ctr1, cycle, idx):
+    """Normals for sites addressed by linear index: group idx >> 2, lane idx & 3."""
+    idx = np.asarray(idx, dtype=np.int64)
+    if idx.size == 0:
+        return np.zeros(0)
+    ctr = np.zeros((idx.size, 4), dtype=np.uint32)
+    ctr[:, 0] = (idx >> 2).astype(np.uint64).astype(np.uint32)
+    ctr[:, 1] = ctr1
+    ctr[:, 2] = int(cycle) & _MASK32
+    ctr[:, 3] = (int(cycle) >> 32) & _MASK32
+    n = words_to_normals(philox4x32_10(ctr, key))
+    return n[np.arange(idx.size), idx & 3]
+
+
 class PhiloxNoise:
     """Noise source for one stochastic cycle of one chain.
 
@@ -122,6 +139,11 @@ class PhiloxNoise:
     def coarsest(self, level, comp, n):
         c1 = pack_ctr1(level, comp, 0, 0, KIND_COARSEST)
         return normals_for_ranks(self.key, c1, self.cycle, n)
+
+    def patch(self, comp, pass_id, sweep, idx):
+        """Normals of refined-patch sites (linear indices idx) in one pass."""
+        c1 = pack_ctr1(0, comp, pass_id, sweep, KIND_PATCH)
+        return normals_for_indices(self.key, c1, self.cycle, idx)
 
 
 class ExplicitNoise:
@@ -149,3 +171,6 @@ class ExplicitNoise:
 
     def coarsest(self, level, comp, n):
         return self._take(n)
+
+    def patch(self, comp, pass_id, sweep, idx):
+        return self._take(len(idx))

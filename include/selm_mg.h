@@ -333,6 +333,91 @@ selm_status selm_profile_read(int kernel_class, double* total_ms, long long* lau
 selm_status selm_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, uint32_t* out,
                                int n, void* stream);
 
+/* ===================================================================== *
+ * Composite grid with one refined patch: FAC of Algorithms 1 and 2.
+ *
+ * The base channel (dim 2 or 3; n cells along each periodic axis; wall axis
+ * with its cell centres on the walls, unknown rows j = 1..n-1, Section 4's
+ * Dirichlet rule) has its rows j = 1..K next to the bottom wall refined by 2
+ * over the whole x-y extent.  Each of `ncomp` scalar components is a
+ * cell-centred field; the operator is Section 4's adaptive discretization
+ * L = DG (Eqs. equ_def_discr_div to equ_def_L: face-area-weighted divergence,
+ * the 3/4-spacing gradient across coarse-fine faces with the coarse face
+ * carrying the mean of its fine faces), used in the symmetric form
+ * A = -mu V L.  One FAC iteration (Algorithm 1 around Algorithm 2):
+ * r = b - A z (FP64); the residual restricted to the base grid (the transpose
+ * of the parent-copy prolongation); one V-cycle (Algorithm 3) on the Galerkin
+ * base hierarchy; the correction copied into the patch; nu_patch Gibbs sweeps
+ * of the patch cells with the composite rows (four passes per sweep: red,
+ * then the red interface-layer cells with odd x, then the same for black);
+ * z += correction.  Noise of the patch sweeps: Philox counter kind 2 with the
+ * cell's linear patch index (group = index >> 2, lane = index & 3).
+ *
+ * Composite vectors are FP64 device arrays of selm_comp_size() elements: the
+ * patch (per component [2K][2n][2n], 2-D [2K][1][2n], x fastest) followed by
+ * the base grid (per component [n-1][n][n], 2-D [n-1][1][n]).  The base rows
+ * j <= K are covered by the patch and are not unknowns: they are ignored on
+ * input, left unchanged in z and zero in residual outputs.
+ * ===================================================================== */
+typedef struct selm_comp selm_comp;
+
+typedef struct {
+  int dim;          /* 2 or 3 */
+  int n;            /* base cells per periodic axis: even, >= 4 */
+  int K;            /* refined base rows next to the bottom wall: 1 <= K <= n-2 */
+  int ncomp;        /* scalar components 1..3 (0 = 1); component ids 0..ncomp-1 */
+  int levels;       /* base multigrid levels (0 = coarsen while the edge stays even and >= 4) */
+  int nu_pre, nu_post, nu_patch;   /* Algorithm 2/3 sweep counts (0 = 2) */
+  int precision;    /* SELM_FP64 or SELM_FP32_REFINE64 (inner cycles FP32, FP64 residual) */
+  int coarse_mode;  /* SELM_COARSE_CHOLESKY or SELM_COARSE_SMOOTH */
+  double mu;        /* viscosity (0 = 1) */
+  uint64_t seed, instance;   /* Philox key material, as for selm_mg_desc */
+  void* (*alloc)(size_t bytes, void* ctx);   /* optional workspace hooks (NULL: cudaMalloc) */
+  void (*free)(void* p, void* ctx);
+  void* alloc_ctx;
+} selm_comp_desc;
+
+/* Device bytes a handle needs (0 for an invalid descriptor). */
+size_t selm_comp_footprint(const selm_comp_desc* desc);
+/* Creates the handle (synchronises `stream`).  SELM_EINVAL: invalid
+   descriptor; SELM_ENOMEM: no workspace. */
+selm_status selm_comp_create(const selm_comp_desc* desc, void* stream, selm_comp** out);
+selm_status selm_comp_destroy(selm_comp* c);
+const char* selm_comp_last_error(const selm_comp* c);
+/* Elements of a composite vector. */
+long long selm_comp_size(const selm_comp* c);
+/* Layout of part 0 (patch) or 1 (base grid) of component `comp` in a
+   composite vector: dims (x, y, z) and element offset. */
+selm_status selm_comp_layout(const selm_comp* c, int part, int comp, int dims[3], long long* offset, long long* size);
+/* Bytes of the inner (level-field) precision: 4 or 8. */
+int selm_comp_inner_bytes(const selm_comp* c);
+/* r = b - A z on the composite unknowns (FP64; b may be NULL for 0; covered
+   rows of r are 0); *norm2 (optional, host) receives ||r||^2.  Synchronises
+   `stream` when norm2 is given. */
+selm_status selm_comp_residual(selm_comp* c, const double* z, const double* b, double* r, double* norm2,
+                               void* stream);
+/* `count` Gibbs sweeps of the patch cells of A q = r, with inner-precision
+   level fields: q_patch (patch field, updated), q_base (base field, read:
+   the coarse neighbours of the top layer), r_patch (patch field).  Counter
+   cycle `cycle`; noise 0 = plain Gauss-Seidel. */
+selm_status selm_comp_patch_sweeps(selm_comp* c, void* q_patch, const void* q_base, const void* r_patch, int count,
+                                   uint64_t cycle, int noise, void* stream);
+/* One FAC iteration on z (b may be NULL for 0) with Philox cycle `cycle`. */
+selm_status selm_comp_fac_cycle(selm_comp* c, double* z, const double* b, uint64_t cycle, int noise, void* stream);
+/* Deterministic FAC iterations from the value in z until ||b - A z|| <=
+   tol ||b|| (SELM_ENOCONV after max_cycles).  Synchronises `stream`. */
+selm_status selm_comp_solve(selm_comp* c, double* z, const double* b, double tol, int max_cycles, int* cycles,
+                            double* rel, void* stream);
+/* Advances the handle's chain xi ~ N(0, A^-1) by `ncycles` stochastic FAC
+   iterations (b = 0; counter cycle = chain step); copies the state into
+   xi_out (a composite vector, optional) on `stream`. */
+selm_status selm_comp_sample(selm_comp* c, int ncycles, double* xi_out, void* stream);
+/* Device pointer of the chain state (a composite vector) and its next cycle. */
+selm_status selm_comp_chain(selm_comp* c, double** xi, uint64_t* cycle);
+selm_status selm_comp_set_cycle(selm_comp* c, uint64_t cycle);
+/* FAC iterations run by the handle. */
+selm_status selm_comp_stats(const selm_comp* c, long long* total_cycles);
+
 #ifdef __cplusplus
 }
 #endif

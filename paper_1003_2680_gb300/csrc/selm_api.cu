@@ -443,6 +443,93 @@ int engine_first_level(const selm_mg* h, const Sys& s) {
 }  // namespace
 
 namespace selm {
+
+size_t footprint_with_host(const selm_mg_desc& d, const HostSystem& host, size_t extra_bytes) {
+  Sys vel;
+  vel.host = host;
+  Plan p;
+  make_plan(d, vel, nullptr, d.precision == SELM_FP64 ? 8 : 4, &p, true);
+  p.lay.add(extra_bytes);
+  return p.lay.total;
+}
+
+selm_status create_with_host(const selm_mg_desc& d, const HostSystem& host, int engine_level, bool use_coop,
+                             int rb_level, size_t extra_bytes, cudaStream_t st, selm_mg** out, size_t* extra_off) {
+  *out = nullptr;
+  selm_mg* h = new (std::nothrow) selm_mg();
+  if (!h) return SELM_ENOMEM;
+  h->d = d;
+  h->vel.host = host;
+  h->has_pres = false;
+  h->mu1 = d.nu_pre;
+  h->mu2 = d.nu_post;
+  h->esize = d.precision == SELM_FP64 ? 8 : 4;
+  h->key.k0 = (uint32_t)(d.seed & 0xffffffffu) ^ (uint32_t)(d.instance >> 32);
+  h->key.k1 = (uint32_t)(d.seed >> 32) ^ (uint32_t)(d.instance & 0xffffffffu);
+  h->vel.engine_level = engine_level;
+  h->vel.use_coop = use_coop;
+  Plan p;
+  make_plan(d, h->vel, nullptr, h->esize, &p, true);
+  const size_t xoff = p.lay.add(extra_bytes);
+  h->ws_bytes = p.lay.total;
+  void* ws = nullptr;
+  if (d.alloc) {
+    ws = d.alloc(h->ws_bytes, d.alloc_ctx);
+    if (!ws) {
+      delete h;
+      return SELM_ENOMEM;
+    }
+  } else if (cudaMalloc(&ws, h->ws_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return SELM_ENOMEM;
+  }
+  h->ws = (char*)ws;
+  h->host_red = new (std::nothrow) double[16];
+  if (!h->host_red) {
+    selm_mg_destroy(h);
+    return SELM_ENOMEM;
+  }
+  cudaError_t ce = cudaSuccess;
+  if (!p.dbl.empty())
+    ce = cudaMemcpyAsync(h->ws + p.dbl_off, p.dbl.data(), p.dbl.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && !p.flt.empty())
+    ce = cudaMemcpyAsync(h->ws + p.flt_off, p.flt.data(), p.flt.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && !p.ints.empty())
+    ce = cudaMemcpyAsync(h->ws + p.int_off, p.ints.data(), p.ints.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  bind_system(&h->vel, 0, p, h->ws);
+  if (rb_level >= 0 && rb_level < h->vel.levels) h->vel.lev[rb_level].rb = 1;
+  h->red = (double*)(h->ws + p.red_off);
+  h->vel.coop_bar = (unsigned*)(h->red + 8);
+  h->cyc = (unsigned long long*)(h->ws + p.cyc_off);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->red, 0, 16 * sizeof(double), st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->cyc, 0, 4 * sizeof(unsigned long long), st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);   // host tables must outlive the copies
+  if (ce != cudaSuccess) {
+    std::fprintf(stderr, "create_with_host: %s\n", cudaGetErrorString(ce));
+    selm_mg_destroy(h);
+    return SELM_ECUDA;
+  }
+  h->vel.eng_dev = h->ws + p.eng_off[0];
+  const int first = engine_first_level(h, h->vel);
+  if (h->esize == 4)
+    plan_coarse_engine<float>(h->vel.lev, h->vel.levels, h->vel.b, h->vel.v, h->vel.t, h->vel.eng_dev, st,
+                              &h->vel.engf, 0, first);
+  else
+    plan_coarse_engine<double>(h->vel.lev, h->vel.levels, h->vel.b, h->vel.v, h->vel.t, h->vel.eng_dev, st,
+                               &h->vel.engd, 0, first);
+  cudaGetLastError();   // without a plan the per-pass path runs
+  *extra_off = xoff;
+  *out = h;
+  return SELM_OK;
+}
+
+selm_status vcycle_level(selm_mg* h, Sys& s, int level, bool noise, const unsigned long long* cyc, cudaStream_t st) {
+  h->total_vcycles += 1;
+  if (h->esize == 4) return vcycle_t<float>(h, s, level, nullptr, nullptr, noise, cyc, st);
+  return vcycle_t<double>(h, s, level, nullptr, nullptr, noise, cyc, st);
+}
+
 selm_status replan_engine(selm_mg* h, int cluster, cudaStream_t st) {
   for (Sys* sy : {&h->vel, h->has_pres ? &h->pres : (Sys*)nullptr}) {
     if (!sy || !sy->eng_dev) continue;

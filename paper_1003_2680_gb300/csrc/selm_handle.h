@@ -101,4 +101,16 @@ selm_status outer_update(selm_mg* h, Sys& s, double* z, const void* d, cudaStrea
 // fits) and each system's first engine level.
 selm_status replan_engine(selm_mg* h, int cluster, cudaStream_t st);
 
+// A handle around a prepared host hierarchy (one system, no projection), with
+// V-cycle scratch only plus `extra_bytes` of workspace for the caller at
+// *extra_off.  Level rb_level (if >= 0) is smoothed red-black; the engine
+// starts at engine_level at the earliest.  The composite form builds on it.
+selm_status create_with_host(const selm_mg_desc& d, const HostSystem& host, int engine_level, bool use_coop,
+                             int rb_level, size_t extra_bytes, cudaStream_t st, selm_mg** out, size_t* extra_off);
+size_t footprint_with_host(const selm_mg_desc& d, const HostSystem& host, size_t extra_bytes);
+// One V-cycle (Algorithm 3) of system s from `level` down, on the internal
+// level fields: reads s.b[level], writes s.v[level] (which must hold its
+// initial value, normally 0).
+selm_status vcycle_level(selm_mg* h, Sys& s, int level, bool noise, const unsigned long long* cyc, cudaStream_t st);
+
 }  // namespace selm

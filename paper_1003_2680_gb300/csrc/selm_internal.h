@@ -50,6 +50,7 @@ struct CompDev {
 struct LevelDev {
   int level;
   int ncomp;
+  int rb;                  // 1: a banded (Galerkin-form) level smoothed in red-black order
   long long size;          // elements of the whole level field
   CompDev c[kMaxComps];
 };
@@ -95,6 +96,7 @@ struct HostSystem {
 // success, otherwise the reason.
 std::string build_velocity_system(int dim, int n, int levels, double mu, HostSystem* out);
 std::string build_pressure_system(int dim, int n, int levels, HostSystem* out);
+std::string build_composite_system(int dim, int n, int K, int levels_base, double mu, int ncomp, HostSystem* out);
 int default_levels(int n);
 
 // Philox stream layout shared by the kernels (see include/selm_mg.h).

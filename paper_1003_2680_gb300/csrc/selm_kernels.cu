@@ -612,6 +612,39 @@ __device__ __forceinline__ void coarse_site_at(const LevelDev& L, const ColourPa
   v[idx] = nv;
 }
 
+// A banded (Galerkin-form) level whose operator is the 7-point stencil (the
+// composite base grid), smoothed in red-black order like level 0: colour =
+// (i + j + k) mod 2, rank = (k ny + j) nx/2 + i/2 within the colour, one
+// thread per site.  The row uses the level's separable stencil tables.
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kBlock) k_band_rb(LevelDev L, ColourPass cp, T* __restrict__ v,
+                                                   const T* __restrict__ b, int colour, int sweep, Key key,
+                                                   const unsigned long long* __restrict__ cyc) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cp.gstart[L.ncomp]) return;
+  const int ci = comp_of(cp.gstart, L.ncomp, g);
+  const CompDev& c = L.c[ci];
+  const unsigned rank = (unsigned)(g - cp.gstart[ci]);
+  const unsigned hx = (unsigned)(c.nx >> 1);
+  const unsigned t = rank / hx;
+  const int j = (int)(t % (unsigned)c.ny), k = (int)(t / (unsigned)c.ny);
+  const int i = 2 * (int)(rank - t * hx) + ((j + k + colour) & 1);
+  const T off = sep_apply<T, LdNC, false>(c, v + c.off, i, j, k);
+  const T diag = coarse_diag<T>(c, k);
+  const long long idx = c.off + (long long)((k * c.ny + j) * c.nx + i);
+  T nv = (__ldg(b + idx) - off) / diag;
+  if (NOISE) {
+    const unsigned long long cy = *cyc;
+    T nn;
+    normal_of(philox10(make_uint4(rank >> 2, ctr1_of(L.level, c.comp_id, colour, sweep, 0), (uint32_t)cy,
+                                  (uint32_t)(cy >> 32)),
+                       key.k0, key.k1),
+              (int)(rank & 3), &nn);
+    nv += nn / tsqrt(diag);
+  }
+  v[idx] = nv;
+}
+
 // Galerkin levels, one thread per site of the colour class.
 template <typename T, bool NOISE>
 __global__ void __launch_bounds__(kBlock) k_coarse_site(LevelDev L, ColourPass cp, T* __restrict__ v,
@@ -1239,6 +1272,23 @@ cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool n
         k_fine_colour<T, true><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
       else
         k_fine_colour<T, false><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
+    }
+    return cudaGetLastError();
+  }
+  if (L.rb) {
+    ColourPass cp{};
+    long long gs = 0;
+    for (int ci = 0; ci < L.ncomp; ++ci) {
+      cp.gstart[ci] = gs;
+      gs += (long long)(L.c[ci].nx / 2) * L.c[ci].ny * L.c[ci].nz;
+    }
+    cp.gstart[L.ncomp] = gs;
+    for (int colour = 0; colour < 2; ++colour) {
+      prof::Scope ps(SELM_K_COARSE_SWEEP, st);
+      if (noise)
+        k_band_rb<T, true><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
+      else
+        k_band_rb<T, false><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
     }
     return cudaGetLastError();
   }

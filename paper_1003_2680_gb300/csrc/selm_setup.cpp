@@ -241,8 +241,11 @@ std::string coarsest_factor(HostComp* c, bool singular) {
   return "";
 }
 
+// Kz0 / Mz0 (optional, rows [m][5]) replace the wall kind's second difference
+// and unit mass on the top level (the composite base grid's Galerkin factors).
 std::string build_system(int dim, int n, int levels, double scale, const std::vector<int>& zkinds,
-                         const std::vector<int>& ids, bool singular, HostSystem* out) {
+                         const std::vector<int>& ids, bool singular, HostSystem* out,
+                         const std::vector<double>* Kz0 = nullptr, const std::vector<double>* Mz0 = nullptr) {
   if (dim != 2 && dim != 3) return "dim must be 2 or 3";
   if (n < 2) return "n must be at least 2";
   if (levels < 1 || levels > kMaxLevels) return "levels out of range";
@@ -271,8 +274,10 @@ std::string build_system(int dim, int n, int levels, double scale, const std::ve
       std::memcpy(c.Ky, Z3, sizeof Z3);
     }
     std::memcpy(c.My, Mp, sizeof Mp);
-    c.Kz = wall_stiffness(c.kind[2], ncell);
-    c.Mz = wall_identity(c.kind[2], ncell);
+    c.Kz = Kz0 ? *Kz0 : wall_stiffness(c.kind[2], ncell);
+    c.Mz = Mz0 ? *Mz0 : wall_identity(c.kind[2], ncell);
+    if ((int)c.Kz.size() != lattice_size(c.kind[2], ncell) * 5 || (int)c.Mz.size() != lattice_size(c.kind[2], ncell) * 5)
+      return "top-level z bands have the wrong size";
     for (int l = 0; l < levels; ++l) {
       c.dims[0] = ncell;
       c.dims[1] = dim == 3 ? ncell : 1;
@@ -367,6 +372,65 @@ std::string build_velocity_system(int dim, int n, int levels, double mu, HostSys
 
 std::string build_pressure_system(int dim, int n, int levels, HostSystem* out) {
   return build_system(dim, n, levels, 1.0, {kAxisCellNeu}, {3}, true, out);
+}
+
+// Composite grid (Section 4, Algorithms 1-2): base channel with wall centres
+// on the walls (vertex-type z, n-1 unknown rows) and its rows j = 1..K refined
+// by 2 over the whole x-y extent.  With the parent-copy prolongation, the
+// Galerkin base operator P^T A P is the 7-point operator with z-dependent
+// weights (unit mu H^(d-2)): z faces 4/3 at the bottom wall and across the
+// interface, 2 between covered rows, 1 elsewhere; x-y mass 2 on covered rows.
+// Level 0 of the result describes the patch (no tables), levels 1.. are the
+// base grid and its Galerkin coarsenings.
+std::string build_composite_system(int dim, int n, int K, int levels_base, double mu, int ncomp, HostSystem* out) {
+  if (dim != 2 && dim != 3) return "dim must be 2 or 3";
+  if (n < 4 || n % 2 != 0) return "n must be even and at least 4";
+  if (K < 1 || K > n - 2) return "patch rows K must satisfy 1 <= K <= n-2";
+  if (ncomp < 1 || ncomp > kMaxComps) return "ncomp out of range";
+  if (levels_base < 1 || levels_base + 1 > kMaxLevels) return "levels out of range";
+  const double H = 1.0 / n;
+  const double scale = mu * std::pow(H, dim - 2);
+  std::vector<double> wz(n, 1.0);   // face f between wall-axis node f and f+1
+  wz[0] = 4.0 / 3.0;
+  for (int f = 1; f < K; ++f) wz[f] = 2.0;
+  wz[K] = 4.0 / 3.0;
+  const int m = n - 1;
+  std::vector<double> Kz((size_t)m * 5, 0.0), Mz((size_t)m * 5, 0.0);
+  for (int r = 0; r < m; ++r) {
+    double* k = &Kz[(size_t)r * 5];
+    k[2] = wz[r] + wz[r + 1];
+    if (r > 0) k[1] = -wz[r];
+    if (r < m - 1) k[3] = -wz[r + 1];
+    Mz[(size_t)r * 5 + 2] = r < K ? 2.0 : 1.0;
+  }
+  HostSystem base;
+  std::vector<int> kinds(ncomp, kAxisVertex), ids(ncomp);
+  for (int c = 0; c < ncomp; ++c) ids[c] = c;
+  std::string err = build_system(dim, n, levels_base, scale, kinds, ids, false, &base, &Kz, &Mz);
+  if (!err.empty()) return err;
+  out->dim = dim;
+  out->n = n;
+  out->levels = levels_base + 1;
+  out->ncomp = ncomp;
+  out->scale = scale;
+  out->singular = false;
+  for (int l = 0; l < kMaxLevels; ++l) out->lev[l].clear();
+  for (int c = 0; c < ncomp; ++c) {
+    HostComp p{};
+    p.kind[0] = kAxisPeriodic;
+    p.kind[1] = dim == 3 ? kAxisPeriodic : kAxisTrivial;
+    p.kind[2] = kAxisVertex;
+    p.dims[0] = 2 * n;
+    p.dims[1] = dim == 3 ? 2 * n : 1;
+    p.dims[2] = 2 * K;
+    p.comp_id = c;
+    p.mods[0] = p.mods[1] = p.mods[2] = 2;
+    p.S.assign((size_t)p.dims[2] * kStencil, 0.0);
+    p.zb.assign((size_t)p.dims[2] * 10, 0.0);
+    out->lev[0].push_back(p);
+  }
+  for (int l = 0; l < levels_base; ++l) out->lev[l + 1] = base.lev[l];
+  return "";
 }
 
 }  // namespace selm

@@ -53,6 +53,16 @@ class SelmResult(ctypes.Structure):
                 ("vcycles", ctypes.c_int)]
 
 
+class SelmCompDesc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("n", ctypes.c_int), ("K", ctypes.c_int), ("ncomp", ctypes.c_int),
+        ("levels", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("nu_patch", ctypes.c_int),
+        ("precision", ctypes.c_int), ("coarse_mode", ctypes.c_int), ("mu", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("instance", ctypes.c_uint64),
+        ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
 class SelmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
@@ -114,6 +124,21 @@ _SIGS = {
                                ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_I)]),
     "selm_server_clock": (_D, [_P]),
     "selm_server_destroy": (_I, [_P]),
+    "selm_comp_footprint": (ctypes.c_size_t, [ctypes.POINTER(SelmCompDesc)]),
+    "selm_comp_create": (_I, [ctypes.POINTER(SelmCompDesc), _P, ctypes.POINTER(_P)]),
+    "selm_comp_destroy": (_I, [_P]),
+    "selm_comp_last_error": (ctypes.c_char_p, [_P]),
+    "selm_comp_size": (_LL, [_P]),
+    "selm_comp_layout": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
+    "selm_comp_inner_bytes": (_I, [_P]),
+    "selm_comp_residual": (_I, [_P, _P, _P, _P, ctypes.POINTER(_D), _P]),
+    "selm_comp_patch_sweeps": (_I, [_P, _P, _P, _P, _I, _U64, _I, _P]),
+    "selm_comp_fac_cycle": (_I, [_P, _P, _P, _U64, _I, _P]),
+    "selm_comp_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+    "selm_comp_sample": (_I, [_P, _I, _P, _P]),
+    "selm_comp_chain": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_U64)]),
+    "selm_comp_set_cycle": (_I, [_P, _U64]),
+    "selm_comp_stats": (_I, [_P, ctypes.POINTER(_LL)]),
     "selm_kernel_launches": (ctypes.c_longlong, []),
     "selm_profile_enable": (_I, [_I]),
     "selm_profile_reset": (_I, []),
@@ -449,6 +474,98 @@ def selm_server_clock(s):
 
 def selm_server_destroy(s):
     _check(None, lib().selm_server_destroy(s))
+
+
+# -- composite grid (refined patch, Algorithms 1-2) ----------------------------
+def _check_comp(c, status):
+    if status != SELM_OK:
+        msg = lib().selm_comp_last_error(c).decode() if c else ""
+        raise SelmError(status, msg)
+
+
+def make_comp_desc(dim, n, K, ncomp=1, mu=1.0, levels=0, nu_pre=2, nu_post=2, nu_patch=2, precision=SELM_FP64,
+                   coarse_mode=SELM_COARSE_CHOLESKY, seed=0, instance=0, torch_allocator=True):
+    d = SelmCompDesc()
+    d.dim, d.n, d.K, d.ncomp, d.levels = dim, n, K, ncomp, levels
+    d.nu_pre, d.nu_post, d.nu_patch, d.precision, d.coarse_mode = nu_pre, nu_post, nu_patch, precision, coarse_mode
+    d.mu, d.seed, d.instance = mu, seed, instance
+    if torch_allocator:
+        d.alloc, d.free = _ALLOC_CB, _FREE_CB
+    return d
+
+
+def selm_comp_footprint(desc):
+    return lib().selm_comp_footprint(ctypes.byref(desc))
+
+
+def selm_comp_create(desc, stream=None):
+    c = _P()
+    st = lib().selm_comp_create(ctypes.byref(desc), _stream(stream), ctypes.byref(c))
+    if st != SELM_OK:
+        raise SelmError(st, "selm_comp_create failed (see stderr)")
+    return c.value
+
+
+def selm_comp_destroy(c):
+    _check_comp(None, lib().selm_comp_destroy(c))
+
+
+def selm_comp_size(c):
+    return int(lib().selm_comp_size(c))
+
+
+def selm_comp_layout(c, part, comp):
+    dims = (_I * 3)()
+    off, size = _LL(0), _LL(0)
+    _check_comp(c, lib().selm_comp_layout(c, part, comp, dims, ctypes.byref(off), ctypes.byref(size)))
+    return (dims[0], dims[1], dims[2]), off.value, size.value
+
+
+def selm_comp_inner_bytes(c):
+    return lib().selm_comp_inner_bytes(c)
+
+
+def selm_comp_residual(c, z, b, r, want_norm=True, stream=None):
+    n2 = _D(0.0)
+    _check_comp(c, lib().selm_comp_residual(c, _ptr(z), _ptr(b), _ptr(r), ctypes.byref(n2) if want_norm else None,
+                                            _stream(stream)))
+    return n2.value
+
+
+def selm_comp_patch_sweeps(c, q_patch, q_base, r_patch, count, cycle, noise, stream=None):
+    _check_comp(c, lib().selm_comp_patch_sweeps(c, _ptr(q_patch), _ptr(q_base), _ptr(r_patch), count, cycle,
+                                                int(noise), _stream(stream)))
+
+
+def selm_comp_fac_cycle(c, z, b, cycle, noise, stream=None):
+    _check_comp(c, lib().selm_comp_fac_cycle(c, _ptr(z), _ptr(b), cycle, int(noise), _stream(stream)))
+
+
+def selm_comp_solve(c, z, b, tol, max_cycles, stream=None):
+    cyc, rel = _I(0), _D(0.0)
+    _check_comp(c, lib().selm_comp_solve(c, _ptr(z), _ptr(b), tol, max_cycles, ctypes.byref(cyc), ctypes.byref(rel),
+                                         _stream(stream)))
+    return cyc.value, rel.value
+
+
+def selm_comp_sample(c, ncycles, xi_out=None, stream=None):
+    _check_comp(c, lib().selm_comp_sample(c, ncycles, _ptr(xi_out), _stream(stream)))
+
+
+def selm_comp_chain(c):
+    p, cy = _P(), _U64(0)
+    _check_comp(c, lib().selm_comp_chain(c, ctypes.byref(p), ctypes.byref(cy)))
+    return p.value, cy.value
+
+
+def selm_comp_set_cycle(c, cycle):
+    _check_comp(c, lib().selm_comp_set_cycle(c, cycle))
+
+
+def selm_comp_stats(c):
+    t = _LL(0)
+    _check_comp(c, lib().selm_comp_stats(c, ctypes.byref(t)))
+    return t.value
 
 
 class SelmMG:

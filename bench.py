@@ -63,9 +63,11 @@ def parse_args():
     p.add_argument("--engine-level", type=int, default=0,
                    help="first multigrid level of the cluster-resident coarse engine (0 = automatic)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="channel128", choices=["channel128", "batched", "served"],
+    p.add_argument("--workload", default="channel128", choices=["channel128", "batched", "served", "composite"],
                    help="channel128: the headline line; batched: 64 uneven systems, batched vs plain; "
                         "served: Poisson request stream, served vs plain per-request")
+    p.add_argument("--comp-n", type=int, default=256, help="composite workload: base cells per axis")
+    p.add_argument("--comp-k", type=int, default=32, help="composite workload: refined base rows")
     p.add_argument("--systems", type=int, default=64)
     p.add_argument("--requests", type=int, default=100)
     p.add_argument("--rate", type=float, default=200.0)
@@ -426,6 +428,166 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+COMPOSITE_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import composite as C, multigrid
+from oracle.philox import PhiloxNoise
+cg = C.CompositeGrid({n}, {K}, 3, ncomp=3)
+co = multigrid.Coarsest(cg.base)
+xi = [np.zeros(cg.size) for _ in range(3)]
+zero = [np.zeros(cg.size) for _ in range(3)]
+C.fac_cycle(cg, xi, zero, PhiloxNoise(0, 0, 0), 1.0, coarsest=co)
+t = time.perf_counter()
+C.fac_cycle(cg, xi, zero, PhiloxNoise(0, 0, 1), 1.0, coarsest=co)
+print(json.dumps(time.perf_counter() - t))
+"""
+
+
+def composite_cpu_baseline(n, K):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = COMPOSITE_ORACLE_SNIPPET.format(root=ROOT, n=n, K=K)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    t = json.loads(out.stdout.strip().splitlines()[-1])
+    cells = n ** 3 + (2 * n) ** 2 * 2 * K
+    return {"value": cells / t, "unit": "cells/s", "cores": 1, "kind": "oracle",
+            "sample": f"one stochastic composite FAC cycle of the FP64 oracle on the {n}^3 base with a "
+                      f"{2 * n}x{2 * n}x{2 * K} patch (3 components), single thread, {t:.2f} s"}
+
+
+def run_composite(args):
+    """Composite grid: 256^3 base channel with its bottom 32 rows refined by 2
+    (patch 512 x 512 x 64), three components, thermal samples of the chain
+    (2 stochastic composite FAC cycles per sample)."""
+    import numpy as np
+    import torch
+    from paper_1003_2680_gb300 import _build
+    _build.build()
+    from paper_1003_2680_gb300 import selm as S
+
+    n, K = args.comp_n, args.comp_k
+    cycles_per_sample = SAMPLE_CYCLES
+    c = S.selm_comp_create(S.make_comp_desc(3, n, K, ncomp=3, precision=S.SELM_FP32_REFINE64, seed=0, instance=0))
+    N = S.selm_comp_size(c)
+    e = S.selm_comp_inner_bytes(c)
+    (fx, fy, fz), _, fsize = S.selm_comp_layout(c, 0, 0)
+    (bx, by, bz), _, bsize = S.selm_comp_layout(c, 1, 0)
+    cells = n ** 3 + fx * fy * fz
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    for _ in range(args.warmup):
+        S.selm_comp_sample(c, cycles_per_sample)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record()
+            S.selm_comp_sample(c, cycles_per_sample)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+    t_total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    value = cells * cycles_per_sample * args.steps / t_total
+
+    # e2e: the same samples through the public call, each sample's 4^3 probe
+    # block per component (x, y = 126..129; the two fine layers below and the two
+    # base rows above the interface) read back to pinned host memory
+    xi = torch.empty(N, dtype=torch.float64, device="cuda")
+    probe_rows = []
+    for comp in range(3):
+        _, poff, _ = S.selm_comp_layout(c, 0, comp)
+        _, boff, _ = S.selm_comp_layout(c, 1, comp)
+        for m in (fz - 2, fz - 1):
+            a = poff + (m * fy + 2 * 63) * fx
+            probe_rows.append((a, a + 4 * fx))
+        for r in (K, K + 1):
+            a = boff + (r * by + 126) * bx
+            probe_rows.append((a, a + 4 * bx))
+    host = torch.empty(sum(b - a for a, b in probe_rows), dtype=torch.float64, pin_memory=True)
+    d2h = host.numel() * 8
+    e2e_time = 0.0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.selm_comp_sample(c, cycles_per_sample, xi)
+        o = 0
+        for a, b in probe_rows:
+            host[o:o + b - a].copy_(xi[a:b], non_blocking=True)
+            o += b - a
+        torch.cuda.synchronize()
+        e2e_time += time.perf_counter() - t0
+    e2e_value = cells * cycles_per_sample * args.steps / e2e_time
+
+    # per-kernel device time and the byte model of each class (one FAC cycle)
+    prof_samples = min(args.steps, 3)
+    S.selm_profile_reset()
+    S.selm_profile_enable(True)
+    for _ in range(prof_samples):
+        S.selm_comp_sample(c, cycles_per_sample)
+    torch.cuda.synchronize()
+    S.selm_profile_enable(False)
+    per_class = {}
+    for ci, name in enumerate(S.KERNEL_CLASSES):
+        ms, cnt = S.selm_profile_read(ci)
+        per_class[name] = {"ms": ms, "launches": cnt}
+    S.selm_profile_reset()
+    ncyc = prof_samples * cycles_per_sample
+    N0, N1 = 3 * fsize, 3 * bsize
+    nu = 2
+    late = 3 * 2 * fy * fx           # cells of the two interface layers
+    model = {   # algorithmic bytes per FAC cycle
+        # patch: 2 main passes per sweep read all of q, read r / write q at half the cells;
+        # 2 late passes on the interface layers
+        "fine_sweep": nu * (2 * e * (N0 + N0) + 2 * e * (late + late / 2)),
+        # base level 1 red-black: 4 sweeps x 2 colours, each e (N1 + N1); levels below negligible
+        "coarse_sweep": 4 * 2 * e * 2 * N1,
+        # FP64 composite residual: read z, b (16 B), write r (e)
+        "outer_residual": (16 + e) * (N0 + N1),
+        # z += q: read/write z (16 B), read q (e)
+        "outer_update": (16 + e) * (N0 + N1),
+    }
+    tot_ms = sum(v["ms"] for v in per_class.values()) or 1.0
+    peak, peak_kind = measured_peaks()
+    rooflines = {}
+    for name, b_cycle in model.items():
+        pc = per_class[name]
+        if pc["launches"] == 0:
+            continue
+        achieved = b_cycle * ncyc / (pc["ms"] / 1e3) / 1e9
+        rooflines[name] = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                           "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                           "algorithmic_bytes_per_launch": b_cycle * ncyc / pc["launches"],
+                           "avg_launch_us": pc["ms"] / pc["launches"] * 1e3,
+                           "share_of_kernel_time": pc["ms"] / tot_ms}
+    dominant = max(rooflines, key=lambda k: rooflines[k]["share_of_kernel_time"])
+    roof = dict(rooflines[dominant])
+    roof["others"] = {k: v for k, v in rooflines.items() if k != dominant}
+    cpu = None if args.no_cpu_baseline else composite_cpu_baseline(128, 16)
+    line = {
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"composite grid: {n}^3 channel (periodic x-y, walls z) with its bottom {K} rows "
+                               f"refined by 2 (patch {fx}x{fy}x{fz}), 3 components, thermal samples of "
+                               f"{cycles_per_sample} stochastic FAC cycles (Algorithms 1-2), FP32 inner cycles "
+                               f"with FP64 residual and coarsest solve",
+                   "base_n": n, "patch_rows": K, "cells": cells, "unknowns": N0 + 3 * (bz - K) * by * bx,
+                   "l2": "flushed between samples (256 MB write, outside the timed events)",
+                   "unit_of_work": "cell-cycle = one cell (base or patch, all 3 components) through one FAC cycle",
+                   "parallelism": "replicas x1"},
+        "kernel_time_share": {k: round(v["ms"] / tot_ms, 4) for k, v in per_class.items()},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
+        "gpu_launches": None,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    S.selm_comp_destroy(c)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -440,6 +602,9 @@ def main():
         return
     if args.workload == "served":
         run_served(args)
+        return
+    if args.workload == "composite":
+        run_composite(args)
         return
 
     import numpy as np

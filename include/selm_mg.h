@@ -410,10 +410,13 @@ selm_status selm_comp_solve(selm_comp* c, double* z, const double* b, double tol
                             double* rel, void* stream);
 /* Advances the handle's chain xi ~ N(0, A^-1) by `ncycles` stochastic FAC
    iterations (b = 0; counter cycle = chain step); copies the state into
-   xi_out (a composite vector, optional) on `stream`. */
+   xi_out (an FP64 composite vector, optional) on `stream`.  With FP32 inner
+   cycles the chain is kept as a double-float pair (hi + lo, about 48
+   significant bits) whose residual and update run on the FP32 pipes; with
+   SELM_FP64 it is an FP64 vector. */
 selm_status selm_comp_sample(selm_comp* c, int ncycles, double* xi_out, void* stream);
-/* Device pointer of the chain state (a composite vector) and its next cycle. */
-selm_status selm_comp_chain(selm_comp* c, double** xi, uint64_t* cycle);
+/* Cycle counter of the next chain step. */
+selm_status selm_comp_chain(selm_comp* c, uint64_t* cycle);
 selm_status selm_comp_set_cycle(selm_comp* c, uint64_t cycle);
 /* FAC iterations run by the handle. */
 selm_status selm_comp_stats(const selm_comp* c, long long* total_cycles);

@@ -241,9 +241,15 @@ selm_status vcycle_t(selm_mg* h, Sys& s, int l, T* v0, const T* b0, bool noise, 
   const LevelDev& L = s.lev[l];
   const bool last = l == s.levels - 1;
   const EnginePlanT<T>& eng = eng_of<T>(s);
-  if (l > 0 && !last && s.use_engine && s.use_coop && eng.valid && l < eng.params.l0 && s.coop_bar &&
-      level_coop_supported<T>(L)) {
-    // a level above the engine: each half of its V-cycle in one cooperative launch
+  // A level above the engine with at most 2^20 sites per component: each half
+  // of its V-cycle in one cooperative launch (one or a few site updates per
+  // thread per pass).  Larger levels keep one GPU-wide launch per colour pass,
+  // whose parallelism then beats the launch overhead.
+  bool coop_size = true;
+  for (int c = 0; c < L.ncomp; ++c)
+    if ((long long)L.c[c].nx * L.c[c].ny * L.c[c].nz > (1ll << 20)) coop_size = false;
+  if (l > 0 && !last && !L.rb && coop_size && s.use_engine && s.use_coop && eng.valid && l < eng.params.l0 &&
+      s.coop_bar && level_coop_supported<T>(L)) {
     const LevelDev& Lc = s.lev[l + 1];
     CK(launch_level_coop<T>(L, Lc, 0, h->mu1, h->mu2, v, b, (T*)s.t[l], (T*)s.b[l + 1], (T*)s.v[l + 1], s.coop_bar,
                             noise, h->key, cyc, st));

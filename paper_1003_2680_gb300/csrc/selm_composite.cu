@@ -51,6 +51,9 @@ struct CompGeo {
   long long N0, N1;          // level-field sizes (all components)
   double sf, sb, wcf;        // face weights mu h^(d-2), mu H^(d-2), mu (4/3) H^(d-2)
   int nch;                   // fine faces per coarse-fine face: 2^(d-1)
+  // the same weights as FP32 pairs (hi + lo) for the double-float chain, and
+  // w2 = wcf / nch^2, w1 = wcf / nch
+  float sf_h, sf_l, sb_h, sb_l, wcf_h, wcf_l, w2_h, w2_l, w1_h, w1_l;
 };
 
 inline unsigned cgrid(long long n) { return (unsigned)((n + kCBlock - 1) / kCBlock); }
@@ -270,6 +273,287 @@ __global__ void __launch_bounds__(kCBlock) k_comp_patch(CompGeo G, T* __restrict
   zp[lin] = nv;
 }
 
+// The same pass, one thread per 8-wide segment of a patch row (fx % 8 == 0).
+// The segment's four sites of the colour are all even x or all odd x, so on
+// an interface layer the whole segment belongs to the main pass (even) or to
+// the late pass (odd).  Siblings of a site: its x partner (x ^ 1) in the same
+// row and the pair in row q ^ 1 (one of the y neighbours); the coarse cells
+// above a top-layer segment are four consecutive base cells.  Noise: the
+// segment's eight linear indices form two Philox groups.
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kCBlock) k_comp_patch_v8(CompGeo G, T* __restrict__ vp, const T* __restrict__ vb,
+                                                           const T* __restrict__ rp, int pass, int sweep, Key key,
+                                                           const unsigned long long* __restrict__ cyc) {
+  const int colour = pass >> 1, late = pass & 1;
+  const int segs = G.fx >> 3;
+  const int layers = late ? 2 : G.fz;
+  const long long rows = (long long)layers * G.fy;
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long row_all = gt / segs;
+  if (row_all >= rows * G.ncomp) return;
+  const int seg = (int)(gt - row_all * segs);
+  const int c = (int)(row_all / rows);
+  const long long rl = row_all - c * rows;
+  const int q = (int)(rl % G.fy), ml = (int)(rl / G.fy);
+  const int m = late ? (ml == 0 ? 0 : G.fz - 1) : ml;
+  const int par = (q + m + colour) & 1;       // the colour's sites: e = 2l + par
+  const bool iface = m == 0 || m == G.fz - 1;
+  if (late != (int)(iface && par)) return;
+  const int fx = G.fx, fy = G.fy, fz = G.fz;
+  const long long plane = (long long)fx * fy;
+  T* zp = vp + c * G.fsize;
+  const long long rbase = (long long)m * plane + (long long)q * fx;
+  const int x0 = seg << 3;
+  T cen[8], rr[8], acc[8], sq[8];
+  Vec<T>::load8(zp + rbase + x0, cen);
+  Vec<T>::load8(rp + c * G.fsize + rbase + x0, rr);
+  const T left = zp[rbase + (x0 == 0 ? fx - 1 : x0 - 1)];
+  const T right = zp[rbase + (x0 + 8 == fx ? 0 : x0 + 8)];
+  int nn = 2;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) acc[e] = (T)0;
+  if (fy > 1) {
+    T t[8];
+    const int qm = q == 0 ? fy - 1 : q - 1, qp = q == fy - 1 ? 0 : q + 1;
+    Vec<T>::load8(zp + (long long)m * plane + (long long)qm * fx + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] += t[e];
+    if ((q ^ 1) == qm) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) sq[e] = t[e];
+    }
+    Vec<T>::load8(zp + (long long)m * plane + (long long)qp * fx + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] += t[e];
+    if ((q ^ 1) == qp) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) sq[e] = t[e];
+    }
+    nn += 2;
+  }
+  if (m > 0) {
+    T t[8];
+    Vec<T>::load8(zp + rbase - plane + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] += t[e];
+    ++nn;
+  }
+  if (m < fz - 1) {
+    T t[8];
+    Vec<T>::load8(zp + rbase + plane + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] += t[e];
+    ++nn;
+  }
+  const T sf = (T)G.sf;
+  T dg = sf * (T)nn;
+  const T w2 = (T)(G.wcf / ((double)G.nch * G.nch));
+  const T w1 = (T)(G.wcf / G.nch);
+  T ca[4] = {(T)0, (T)0, (T)0, (T)0};
+  if (iface) {
+    dg += w2;
+    if (m == fz - 1) {   // the four base cells above the segment
+      const T* brow = vb + c * G.bsize + ((long long)G.K * G.by + (fy > 1 ? (q >> 1) : 0)) * G.bx + (x0 >> 1);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) ca[l] = brow[l];
+    }
+  }
+  T n8[8];
+  if (NOISE) {
+    const unsigned long long cy = *cyc;
+    const uint32_t c1 = ((uint32_t)c << 4) | ((uint32_t)pass << 8) | ((uint32_t)sweep << 12) | (2u << 20);
+    const uint32_t g0 = (uint32_t)((rbase + x0) >> 2);
+    Normals<T>::get(philox4x32_10(make_uint4(g0, c1, (uint32_t)cy, (uint32_t)(cy >> 32)), key.k0, key.k1), n8);
+    Normals<T>::get(philox4x32_10(make_uint4(g0 + 1, c1, (uint32_t)cy, (uint32_t)(cy >> 32)), key.k0, key.k1),
+                    n8 + 4);
+  }
+  const T rsd = NOISE ? (T)1 / tsqrt(dg) : (T)0;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+#pragma unroll
+    for (int pp = 0; pp < 2; ++pp) {
+      if (pp != par) continue;
+      const int e = 2 * l + pp;
+      const T xl = e == 0 ? left : cen[e - 1];
+      const T xr = e == 7 ? right : cen[e + 1];
+      T off = -sf * (acc[e] + xl + xr);
+      if (iface) {
+        T sib = cen[e ^ 1];
+        if (fy > 1) sib += sq[e] + sq[e ^ 1];
+        off += w2 * sib;
+        if (m == fz - 1) off -= w1 * ca[l];
+      }
+      T nv = (rr[e] - off) / dg;
+      if (NOISE) nv += n8[e] * rsd;
+      cen[e] = nv;
+    }
+  }
+  Vec<T>::store8(zp + rbase + x0, cen);
+}
+
+// ---------------------------------------------------------------------------
+// Double-float chain state (FP32 inner cycles).  The chain value is hi + lo
+// with |lo| <= ulp(hi)/2 (about 48 significant bits); sums and products use
+// the error-free transformations TwoSum (Knuth) and the FMA product error
+// (Dekker's splitting replaced by fma), so the chain's residual and update
+// keep near-FP64 accuracy on the FP32 pipes instead of GB300's slow FP64 pipe.
+// ---------------------------------------------------------------------------
+struct DF {
+  float h, l;
+};
+
+__device__ __forceinline__ DF df_from(float h, float l) { return {h, l}; }
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ DF df_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  return df_norm(s, e);
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.h, -a.l}; }
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return df_norm(p, e);
+}
+
+__device__ __forceinline__ DF df_at(const float* hi, const float* lo, long long i) { return {hi[i], lo[i]}; }
+
+// r = -A z for the chain (b = 0) in double-float arithmetic, written in FP32:
+// patch sites into rp, uncovered base sites into rb.
+__global__ void __launch_bounds__(kCBlock) k_comp_residual_df(CompGeo G, const float* __restrict__ zh,
+                                                              const float* __restrict__ zl, float* __restrict__ rp,
+                                                              float* __restrict__ rb) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < G.N0) {
+    const int c = (int)(s / G.fsize);
+    const long long loc = s - c * G.fsize;
+    const int p = (int)(loc % G.fx);
+    const long long t = loc / G.fx;
+    const int q = (int)(t % G.fy), m = (int)(t / G.fy);
+    const float* ph = zh + c * G.fsize;
+    const float* pl = zl + c * G.fsize;
+    const long long plane = (long long)G.fx * G.fy;
+    const long long row = (long long)m * plane + (long long)q * G.fx;
+    DF nb = df_add(df_at(ph, pl, row + cwrap(p - 1, G.fx)), df_at(ph, pl, row + cwrap(p + 1, G.fx)));
+    int nn = 2;
+    if (G.fy > 1) {
+      nb = df_add(nb, df_at(ph, pl, (long long)m * plane + (long long)cwrap(q - 1, G.fy) * G.fx + p));
+      nb = df_add(nb, df_at(ph, pl, (long long)m * plane + (long long)cwrap(q + 1, G.fy) * G.fx + p));
+      nn += 2;
+    }
+    if (m > 0) {
+      nb = df_add(nb, df_at(ph, pl, row - plane + p));
+      ++nn;
+    }
+    if (m < G.fz - 1) {
+      nb = df_add(nb, df_at(ph, pl, row + plane + p));
+      ++nn;
+    }
+    const DF zc = df_at(ph, pl, row + p);
+    // A z = sf (nn zc - sum of neighbours) [+ w2 (sum of the sibling group) - w1 zA]
+    DF Az = df_mul(df_from(G.sf_h, G.sf_l), df_add(df_mul(df_from((float)nn, 0.f), zc), df_neg(nb)));
+    if (m == 0 || m == G.fz - 1) {
+      const int q0 = q & ~1, p0 = p & ~1;
+      DF grp = {0.f, 0.f};
+      for (int a = 0; a < (G.fy > 1 ? 2 : 1); ++a)
+        for (int cc = 0; cc < 2; ++cc)
+          grp = df_add(grp, df_at(ph, pl, (long long)m * plane + (long long)(G.fy > 1 ? q0 + a : 0) * G.fx + p0 + cc));
+      Az = df_add(Az, df_mul(df_from(G.w2_h, G.w2_l), grp));
+      if (m == G.fz - 1) {
+        const long long bi = G.N0 + c * G.bsize + ((long long)G.K * G.by + (G.fy > 1 ? (q >> 1) : 0)) * G.bx + (p >> 1);
+        Az = df_add(Az, df_neg(df_mul(df_from(G.w1_h, G.w1_l), df_at(zh, zl, bi))));
+      }
+    }
+    rp[s] = -(Az.h + Az.l);
+  } else if (s < G.N0 + G.N1) {
+    const long long s1 = s - G.N0;
+    const int c = (int)(s1 / G.bsize);
+    const long long loc = s1 - c * G.bsize;
+    const int i = (int)(loc % G.bx);
+    const long long t = loc / G.bx;
+    const int l = (int)(t % G.by), r0 = (int)(t / G.by);
+    if (r0 < G.K) return;
+    const float* bh = zh + G.N0 + c * G.bsize;
+    const float* bl = zl + G.N0 + c * G.bsize;
+    const long long plane = (long long)G.bx * G.by;
+    const long long row = (long long)r0 * plane + (long long)l * G.bx;
+    DF nb = df_add(df_at(bh, bl, row + cwrap(i - 1, G.bx)), df_at(bh, bl, row + cwrap(i + 1, G.bx)));
+    int nn = 2;
+    if (G.by > 1) {
+      nb = df_add(nb, df_at(bh, bl, (long long)r0 * plane + (long long)cwrap(l - 1, G.by) * G.bx + i));
+      nb = df_add(nb, df_at(bh, bl, (long long)r0 * plane + (long long)cwrap(l + 1, G.by) * G.bx + i));
+      nn += 2;
+    }
+    ++nn;
+    if (r0 + 1 < G.bz) nb = df_add(nb, df_at(bh, bl, row + plane + i));
+    const DF zc = df_at(bh, bl, row + i);
+    DF extra = {0.f, 0.f};
+    if (r0 > G.K) {
+      nb = df_add(nb, df_at(bh, bl, row - plane + i));
+      ++nn;
+    } else {   // wcf (zc - mean of the patch's top-layer children)
+      const float* ph = zh + c * G.fsize;
+      const float* pl = zl + c * G.fsize;
+      const long long fplane = (long long)G.fx * G.fy;
+      DF ch = {0.f, 0.f};
+      for (int a = 0; a < (G.by > 1 ? 2 : 1); ++a)
+        for (int cc = 0; cc < 2; ++cc)
+          ch = df_add(ch, df_at(ph, pl, (long long)(G.fz - 1) * fplane + (long long)(G.by > 1 ? 2 * l + a : 0) * G.fx +
+                                            2 * i + cc));
+      const float inv = 1.0f / (float)G.nch;   // a power of two: exact
+      extra = df_mul(df_from(G.wcf_h, G.wcf_l), df_add(zc, df_neg({ch.h * inv, ch.l * inv})));
+    }
+    DF Az = df_mul(df_from(G.sb_h, G.sb_l), df_add(df_mul(df_from((float)nn, 0.f), zc), df_neg(nb)));
+    Az = df_add(Az, extra);
+    rb[s1] = -(Az.h + Az.l);
+  }
+}
+
+// z += q for the double-float chain (covered base rows untouched).
+__global__ void __launch_bounds__(kCBlock) k_comp_update_df(CompGeo G, float* __restrict__ zh, float* __restrict__ zl,
+                                                            const float* __restrict__ vp, const float* __restrict__ vb) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float q;
+  if (s < G.N0) {
+    q = vp[s];
+  } else if (s < G.N0 + G.N1) {
+    const long long s1 = s - G.N0;
+    if ((int)((s1 % G.bsize) / ((long long)G.bx * G.by)) < G.K) return;
+    q = vb[s1];
+  } else {
+    return;
+  }
+  float a, e;
+  two_sum(zh[s], q, a, e);
+  const DF r = df_norm(a, __fadd_rn(e, zl[s]));
+  zh[s] = r.h;
+  zl[s] = r.l;
+}
+
+// FP64 copy of the double-float chain (covered base rows 0).
+__global__ void __launch_bounds__(kCBlock) k_comp_df_to_f64(CompGeo G, const float* __restrict__ zh,
+                                                            const float* __restrict__ zl, double* __restrict__ out) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= G.N0 + G.N1) return;
+  out[s] = (double)zh[s] + (double)zl[s];
+}
+
 // z += q on the composite unknowns (covered base rows untouched).
 template <typename T>
 __global__ void __launch_bounds__(kCBlock) k_comp_update(CompGeo G, double* __restrict__ z, const T* __restrict__ vp,
@@ -317,7 +601,9 @@ struct selm_comp {
   selm_mg* mg = nullptr;     // base hierarchy (levels 1..) and level fields
   CompGeo geo{};
   int nu = 2;
-  double* xi = nullptr;      // chain state (composite FP64 vector)
+  double* xi = nullptr;      // chain state, FP64 inner precision (composite vector)
+  float* xh = nullptr;       // chain state, FP32 inner precision: double-float hi + lo
+  float* xl = nullptr;
   double* red = nullptr;     // norm slots (in the internal handle's reduction words)
   double* host_red = nullptr;
   uint64_t cycle = 0;
@@ -403,6 +689,15 @@ CompGeo make_geo(const selm_comp_desc& d) {
   G.sb = d.mu * std::pow(H, d.dim - 2);
   G.wcf = d.mu * (4.0 / 3.0) * std::pow(H, d.dim - 2);
   G.nch = d.dim == 3 ? 4 : 2;
+  auto split = [](double x, float* h, float* l) {
+    *h = (float)x;
+    *l = (float)(x - (double)*h);
+  };
+  split(G.sf, &G.sf_h, &G.sf_l);
+  split(G.sb, &G.sb_h, &G.sb_l);
+  split(G.wcf, &G.wcf_h, &G.wcf_l);
+  split(G.wcf / ((double)G.nch * G.nch), &G.w2_h, &G.w2_l);
+  split(G.wcf / G.nch, &G.w1_h, &G.w1_l);
   return G;
 }
 
@@ -419,14 +714,24 @@ selm_status patch_sweeps_t(selm_comp* C, T* vp, const T* vb, const T* rp, int co
                            const unsigned long long* cyc, cudaStream_t st) {
   const CompGeo& G = C->geo;
   const Key key = C->mg->key;
+  const bool v8 = G.fx % 8 == 0;
   for (int s = 0; s < count; ++s)
     for (int pass = 0; pass < 4; ++pass) {
-      const long long per = (long long)((pass & 1) ? 2 : G.fz) * G.fy * (G.fx >> 1);
       prof::Scope ps(SELM_K_FINE_SWEEP, st);
-      if (noise)
-        k_comp_patch<T, true><<<cgrid(per * G.ncomp), kCBlock, 0, st>>>(G, vp, vb, rp, pass, s, key, cyc);
-      else
-        k_comp_patch<T, false><<<cgrid(per * G.ncomp), kCBlock, 0, st>>>(G, vp, vb, rp, pass, s, key, cyc);
+      const long long rows = (long long)((pass & 1) ? 2 : G.fz) * G.fy * G.ncomp;
+      if (v8) {
+        const long long nt = rows * (G.fx >> 3);
+        if (noise)
+          k_comp_patch_v8<T, true><<<cgrid(nt), kCBlock, 0, st>>>(G, vp, vb, rp, pass, s, key, cyc);
+        else
+          k_comp_patch_v8<T, false><<<cgrid(nt), kCBlock, 0, st>>>(G, vp, vb, rp, pass, s, key, cyc);
+      } else {
+        const long long nt = rows * (G.fx >> 1);
+        if (noise)
+          k_comp_patch<T, true><<<cgrid(nt), kCBlock, 0, st>>>(G, vp, vb, rp, pass, s, key, cyc);
+        else
+          k_comp_patch<T, false><<<cgrid(nt), kCBlock, 0, st>>>(G, vp, vb, rp, pass, s, key, cyc);
+      }
     }
   CCK(cudaGetLastError());
   return SELM_OK;
@@ -436,7 +741,8 @@ selm_status patch_sweeps_t(selm_comp* C, T* vp, const T* vb, const T* rp, int co
 // level-0 and level-1 b fields from z: restrict, base V-cycle, prolong, patch
 // sweeps, z += q.
 template <typename T>
-selm_status correct_t(selm_comp* C, double* z, bool noise, const unsigned long long* cyc, cudaStream_t st) {
+selm_status correct_t(selm_comp* C, double* z, bool noise, const unsigned long long* cyc, cudaStream_t st,
+                      float* zh = nullptr, float* zl = nullptr) {
   const CompGeo& G = C->geo;
   Sys& s = C->mg->vel;
   T* rp = (T*)s.b[0];
@@ -461,7 +767,11 @@ selm_status correct_t(selm_comp* C, double* z, bool noise, const unsigned long l
   if (r != SELM_OK) return r;
   {
     prof::Scope ps(SELM_K_OUTER_UPDATE, st);
-    k_comp_update<T><<<cgrid(G.N0 + G.N1), kCBlock, 0, st>>>(G, z, (const T*)s.v[0], (const T*)s.v[1]);
+    if (zh)
+      k_comp_update_df<<<cgrid(G.N0 + G.N1), kCBlock, 0, st>>>(G, zh, zl, (const float*)s.v[0],
+                                                               (const float*)s.v[1]);
+    else
+      k_comp_update<T><<<cgrid(G.N0 + G.N1), kCBlock, 0, st>>>(G, z, (const T*)s.v[0], (const T*)s.v[1]);
   }
   CCK(cudaGetLastError());
   C->total_cycles += 1;
@@ -480,6 +790,19 @@ selm_status fac_cycle(selm_comp* C, double* z, const double* b, bool noise, cons
     if (r == SELM_OK) r = correct_t<double>(C, z, noise, cyc, st);
   }
   return r;
+}
+
+// One stochastic FAC iteration of the handle's chain (b = 0).
+selm_status chain_cycle(selm_comp* C, const unsigned long long* cyc, cudaStream_t st) {
+  if (!C->xh) return fac_cycle(C, C->xi, nullptr, true, cyc, nullptr, st);
+  Sys& s = C->mg->vel;
+  {
+    prof::Scope ps(SELM_K_OUTER_RESIDUAL, st);
+    k_comp_residual_df<<<cgrid(C->geo.N0 + C->geo.N1), kCBlock, 0, st>>>(C->geo, C->xh, C->xl, (float*)s.b[0],
+                                                                         (float*)s.b[1]);
+  }
+  CCK(cudaGetLastError());
+  return correct_t<float>(C, nullptr, true, cyc, st, C->xh, C->xl);
 }
 
 selm_status read_slot(selm_comp* C, int slot, double* out, cudaStream_t st) {
@@ -523,18 +846,24 @@ selm_status selm_comp_create(const selm_comp_desc* desc, void* stream, selm_comp
   C->nu = d.nu_patch;
   size_t xoff = 0;
   cudaStream_t st = CS(stream);
-  // level 1 (the base grid, 7-point) is smoothed red-black; the engine may
-  // take the levels from 2; level 1 is not run as a cooperative launch
-  selm_status r = create_with_host(internal_desc(d), hs, 2, false, 1,
+  // level 1 (the base grid, 7-point) is smoothed red-black by its own
+  // launches; the levels from 2 go to the cluster engine where their slabs fit
+  // in shared memory, and the larger ones above it to cooperative launches
+  selm_status r = create_with_host(internal_desc(d), hs, 2, true, 1,
                                    (size_t)(C->geo.N0 + C->geo.N1) * sizeof(double), st, &C->mg, &xoff);
   if (r != SELM_OK) {
     delete C;
     return r;
   }
-  C->xi = (double*)(C->mg->ws + xoff);
+  if (C->mg->esize == 4) {
+    C->xh = (float*)(C->mg->ws + xoff);
+    C->xl = C->xh + (C->geo.N0 + C->geo.N1);
+  } else {
+    C->xi = (double*)(C->mg->ws + xoff);
+  }
   C->red = C->mg->red;
   C->host_red = new (std::nothrow) double[2];
-  cudaError_t ce = cudaMemsetAsync(C->xi, 0, (size_t)(C->geo.N0 + C->geo.N1) * sizeof(double), st);
+  cudaError_t ce = cudaMemsetAsync(C->mg->ws + xoff, 0, (size_t)(C->geo.N0 + C->geo.N1) * sizeof(double), st);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   if (!C->host_red || ce != cudaSuccess) {
     const selm_status why = C->host_red ? SELM_ECUDA : SELM_ENOMEM;
@@ -652,20 +981,25 @@ selm_status selm_comp_sample(selm_comp* C, int ncycles, double* xi_out, void* st
   if (!C || ncycles < 0) return SELM_EINVAL;
   cudaStream_t st = CS(stream);
   for (int q = 0; q < ncycles; ++q) {
-    selm_status r = fac_cycle(C, C->xi, nullptr, true, C->mg->cyc + 0, nullptr, st);
+    selm_status r = chain_cycle(C, C->mg->cyc + 0, st);
     if (r != SELM_OK) return r;
     if (launch_inc_u64(C->mg->cyc + 0, st) != cudaSuccess) return SELM_ECUDA;
     C->cycle += 1;
   }
-  if (xi_out)
-    CCK(cudaMemcpyAsync(xi_out, C->xi, (size_t)(C->geo.N0 + C->geo.N1) * sizeof(double), cudaMemcpyDeviceToDevice,
-                        st));
+  if (xi_out) {
+    if (C->xh) {
+      k_comp_df_to_f64<<<cgrid(C->geo.N0 + C->geo.N1), kCBlock, 0, st>>>(C->geo, C->xh, C->xl, xi_out);
+      CCK(cudaGetLastError());
+    } else {
+      CCK(cudaMemcpyAsync(xi_out, C->xi, (size_t)(C->geo.N0 + C->geo.N1) * sizeof(double), cudaMemcpyDeviceToDevice,
+                          st));
+    }
+  }
   return SELM_OK;
 }
 
-selm_status selm_comp_chain(selm_comp* C, double** xi, uint64_t* cycle) {
+selm_status selm_comp_chain(selm_comp* C, uint64_t* cycle) {
   if (!C) return SELM_EINVAL;
-  if (xi) *xi = C->xi;
   if (cycle) *cycle = C->cycle;
   return SELM_OK;
 }

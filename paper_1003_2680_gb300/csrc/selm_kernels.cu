@@ -98,44 +98,6 @@ constexpr int kBlock = 256;
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) { return philox4x32_10(c, k0, k1); }
 
-template <typename T>
-struct Normals;
-
-template <>
-struct Normals<double> {
-  // u = (w + 1/2) 2^-32; (n0, n1) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1), etc.
-  __device__ static void get(uint4 w, double n[4]) {
-    const double s = 2.3283064365386962890625e-10;
-    const double u0 = ((double)w.x + 0.5) * s, u1 = ((double)w.y + 0.5) * s;
-    const double u2 = ((double)w.z + 0.5) * s, u3 = ((double)w.w + 0.5) * s;
-    const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
-    double s1, c1, s3, c3;
-    sincospi(2.0 * u1, &s1, &c1);
-    sincospi(2.0 * u3, &s3, &c3);
-    n[0] = r0 * c1;
-    n[1] = r0 * s1;
-    n[2] = r1 * c3;
-    n[3] = r1 * s3;
-  }
-};
-
-template <>
-struct Normals<float> {
-  __device__ static void get(uint4 w, float n[4]) {
-    const float s = 2.3283064365386962890625e-10f;
-    const float u0 = ((float)w.x + 0.5f) * s, u1 = ((float)w.y + 0.5f) * s;
-    const float u2 = ((float)w.z + 0.5f) * s, u3 = ((float)w.w + 0.5f) * s;
-    const float r0 = sqrtf(-2.0f * logf(u0)), r1 = sqrtf(-2.0f * logf(u2));
-    float s1, c1, s3, c3;
-    sincospif(2.0f * u1, &s1, &c1);
-    sincospif(2.0f * u3, &s3, &c3);
-    n[0] = r0 * c1;
-    n[1] = r0 * s1;
-    n[2] = r1 * c3;
-    n[3] = r1 * s3;
-  }
-};
-
 __device__ __forceinline__ uint32_t ctr1_of(int level, int comp, int colour, int sweep, int kind) {
   return (uint32_t)level | ((uint32_t)comp << 4) | ((uint32_t)colour << 8) | ((uint32_t)sweep << 12) |
          ((uint32_t)kind << 20);
@@ -282,35 +244,6 @@ __device__ __forceinline__ double block_sum(double x) {
 // ends are scalar loads.  The whole segment is written back: its
 // other-colour entries are unchanged and are the only entries other threads
 // read during this pass.
-template <typename T>
-struct Vec;
-template <>
-struct Vec<float> {
-  __device__ static void load8(const float* p, float o[8]) {
-    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
-    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
-  }
-  __device__ static void store8(float* p, const float o[8]) {
-    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
-    *reinterpret_cast<float4*>(p + 4) = make_float4(o[4], o[5], o[6], o[7]);
-  }
-};
-template <>
-struct Vec<double> {
-  __device__ static void load8(const double* p, double o[8]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const double2 a = *reinterpret_cast<const double2*>(p + 2 * q);
-      o[2 * q] = a.x;
-      o[2 * q + 1] = a.y;
-    }
-  }
-  __device__ static void store8(double* p, const double o[8]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) *reinterpret_cast<double2*>(p + 2 * q) = make_double2(o[2 * q], o[2 * q + 1]);
-  }
-};
-
 // Updates the four sites of parity P in an 8-wide segment (compile-time
 // indices keep the arrays in registers).
 template <typename T, bool NOISE, int P>
@@ -612,6 +545,103 @@ __device__ __forceinline__ void coarse_site_at(const LevelDev& L, const ColourPa
   v[idx] = nv;
 }
 
+// Row k of a banded red-black level in its 7-point form: x-y weight a_k
+// (the z band's mass entry), z coefficients below / above (the stiffness band's
+// off-diagonal entries), diagonal from the tabulated stencil.  The level's x-y
+// weights w1 (5-point) and w2 (centre only) complete the row.
+template <typename T>
+struct Band7 {
+  T a, dn, up, diag;
+};
+
+template <typename T>
+__device__ __forceinline__ Band7<T> band7_row(const CompDev& c, int k) {
+  const T* zb = (sizeof(T) == 4 ? (const T*)c.zb32 : (const T*)c.zb64) + k * 10;
+  const T w2c = sep_w2<T>(c, 4);
+  Band7<T> r;
+  r.a = zb[2];
+  r.dn = zb[6] * w2c;
+  r.up = zb[8] * w2c;
+  r.diag = coarse_diag<T>(c, k);
+  return r;
+}
+
+// Red-black colour pass of a banded 7-point level (the composite base grid),
+// one thread per 8-wide row segment (the four sites of the colour in it form
+// one noise group: group = rank >> 2 = row nx/8 + segment); nx % 8 == 0.
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kBlock) k_band7_rb_v8(LevelDev L, RowPass rp, T* __restrict__ v,
+                                                       const T* __restrict__ b, int colour, int sweep, Key key,
+                                                       const unsigned long long* __restrict__ cyc) {
+  const int segs = L.c[0].nx >> 3;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row_all = gt / segs;
+  if (row_all >= rp.rstart[L.ncomp]) return;
+  const int seg = gt - row_all * segs;
+  int ci = 0;
+  while (ci + 1 < L.ncomp && row_all >= rp.rstart[ci + 1]) ++ci;
+  const CompDev& c = L.c[ci];
+  const int row = row_all - rp.rstart[ci];
+  const int j = row % c.ny, k = row / c.ny;
+  const int nx = c.nx;
+  const long long plane = (long long)nx * c.ny;
+  const long long rbase = c.off + (long long)row * nx;
+  const int x0 = seg << 3;
+  const Band7<T> R = band7_row<T>(c, k);
+  const T wxm = sep_w1<T>(c, 3), wxp = sep_w1<T>(c, 5), wym = sep_w1<T>(c, 1), wyp = sep_w1<T>(c, 7);
+  T cen[8], bb[8], acc[8];
+  Vec<T>::load8(v + rbase + x0, cen);
+  Vec<T>::load8(b + rbase + x0, bb);
+  const T left = v[rbase + (x0 == 0 ? nx - 1 : x0 - 1)];
+  const T right = v[rbase + (x0 + 8 == nx ? 0 : x0 + 8)];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) acc[e] = (T)0;
+  if (c.ny > 1) {
+    T t[8];
+    const long long ym = c.off + ((long long)k * c.ny + (j == 0 ? c.ny - 1 : j - 1)) * nx + x0;
+    const long long yp = c.off + ((long long)k * c.ny + (j == c.ny - 1 ? 0 : j + 1)) * nx + x0;
+    Vec<T>::load8(v + ym, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] += R.a * wym * t[e];
+    Vec<T>::load8(v + yp, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] += R.a * wyp * t[e];
+  }
+  if (k > 0) {
+    T t[8];
+    Vec<T>::load8(v + rbase - plane + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] += R.dn * t[e];
+  }
+  if (k < c.nz - 1) {
+    T t[8];
+    Vec<T>::load8(v + rbase + plane + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] += R.up * t[e];
+  }
+  T n4[4] = {(T)0, (T)0, (T)0, (T)0};
+  if (NOISE) {
+    const unsigned long long cy = *cyc;
+    const uint32_t grp = (uint32_t)row * (uint32_t)(nx >> 3) + (uint32_t)seg;
+    Normals<T>::get(philox10(make_uint4(grp, ctr1_of(L.level, c.comp_id, colour, sweep, 0), (uint32_t)cy,
+                                        (uint32_t)(cy >> 32)),
+                             key.k0, key.k1),
+                    n4);
+  }
+  const T rsd = NOISE ? (T)1 / tsqrt(R.diag) : (T)0;
+  const int par = (j + k + colour) & 1;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const int e = 2 * l + par;   // par is 0 or 1: the colour's sites in the segment
+    const T xl = e == 0 ? left : cen[e - 1];
+    const T xr = e == 7 ? right : cen[e + 1];
+    T nv = (bb[e] - (acc[e] + R.a * (wxm * xl + wxp * xr))) / R.diag;
+    if (NOISE) nv += n4[l] * rsd;
+    cen[e] = nv;
+  }
+  Vec<T>::store8(v + rbase + x0, cen);
+}
+
 // A banded (Galerkin-form) level whose operator is the 7-point stencil (the
 // composite base grid), smoothed in red-black order like level 0: colour =
 // (i + j + k) mod 2, rank = (k ny + j) nx/2 + i/2 within the colour, one
@@ -685,6 +715,17 @@ __global__ void __launch_bounds__(kBlock) k_residual(LevelDev L, const T* __rest
     T off, diag;
     fine_row<T, T>(c, v, i, j, k, &off, &diag);
     Av = off + diag * v[s];
+  } else if (L.rb) {   // banded 7-point level
+    const Band7<T> R = band7_row<T>(c, k);
+    const long long plane = (long long)c.nx * c.ny;
+    const long long row = c.off + (long long)k * plane + (long long)j * c.nx;
+    T xy = sep_w1<T>(c, 3) * v[row + wrapi(i - 1, c.nx)] + sep_w1<T>(c, 5) * v[row + wrapi(i + 1, c.nx)];
+    if (c.ny > 1)
+      xy += sep_w1<T>(c, 1) * v[c.off + (long long)k * plane + (long long)wrapi(j - 1, c.ny) * c.nx + i] +
+            sep_w1<T>(c, 7) * v[c.off + (long long)k * plane + (long long)wrapi(j + 1, c.ny) * c.nx + i];
+    Av = R.diag * v[s] + R.a * xy;
+    if (k > 0) Av += R.dn * v[row - plane + i];
+    if (k < c.nz - 1) Av += R.up * v[row + plane + i];
   } else {
     Av = sep_apply<T, LdPlain, true>(c, v + c.off, i, j, k);
   }
@@ -1272,6 +1313,24 @@ cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool n
         k_fine_colour<T, true><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
       else
         k_fine_colour<T, false><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
+    }
+    return cudaGetLastError();
+  }
+  if (L.rb && L.c[0].nx % 8 == 0) {
+    RowPass rp{};
+    int rows = 0;
+    for (int ci = 0; ci < L.ncomp; ++ci) {
+      rp.rstart[ci] = rows;
+      rows += L.c[ci].ny * L.c[ci].nz;
+    }
+    rp.rstart[L.ncomp] = rows;
+    const long long nt = (long long)rows * (L.c[0].nx >> 3);
+    for (int colour = 0; colour < 2; ++colour) {
+      prof::Scope ps(SELM_K_COARSE_SWEEP, st);
+      if (noise)
+        k_band7_rb_v8<T, true><<<grid_for(nt), kBlock, 0, st>>>(L, rp, v, b, colour, sweep, key, cyc);
+      else
+        k_band7_rb_v8<T, false><<<grid_for(nt), kBlock, 0, st>>>(L, rp, v, b, colour, sweep, key, cyc);
     }
     return cudaGetLastError();
   }

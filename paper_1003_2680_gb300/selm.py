@@ -136,7 +136,7 @@ _SIGS = {
     "selm_comp_fac_cycle": (_I, [_P, _P, _P, _U64, _I, _P]),
     "selm_comp_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
     "selm_comp_sample": (_I, [_P, _I, _P, _P]),
-    "selm_comp_chain": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_U64)]),
+    "selm_comp_chain": (_I, [_P, ctypes.POINTER(_U64)]),
     "selm_comp_set_cycle": (_I, [_P, _U64]),
     "selm_comp_stats": (_I, [_P, ctypes.POINTER(_LL)]),
     "selm_kernel_launches": (ctypes.c_longlong, []),
@@ -553,9 +553,9 @@ def selm_comp_sample(c, ncycles, xi_out=None, stream=None):
 
 
 def selm_comp_chain(c):
-    p, cy = _P(), _U64(0)
-    _check_comp(c, lib().selm_comp_chain(c, ctypes.byref(p), ctypes.byref(cy)))
-    return p.value, cy.value
+    cy = _U64(0)
+    _check_comp(c, lib().selm_comp_chain(c, ctypes.byref(cy)))
+    return cy.value
 
 
 def selm_comp_set_cycle(c, cycle):

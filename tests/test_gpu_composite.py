@@ -16,8 +16,9 @@ from oracle.philox import PhiloxNoise
 pytestmark = pytest.mark.gpu
 
 # (dim, n, K): small grids span several tiles, the n = 32 grid runs the base
-# levels from 2 in the cluster engine
-GRIDS = [(2, 16, 2), (3, 8, 2), (3, 16, 3), (3, 32, 4)]
+# levels from 2 in the cluster engine, n = 12 takes the scalar red-black path
+# of the base grid and n = 10 the scalar patch sweep (2n not a multiple of 8)
+GRIDS = [(2, 16, 2), (3, 8, 2), (3, 16, 3), (3, 32, 4), (2, 12, 2), (2, 10, 2)]
 
 
 @pytest.fixture(scope="module")
@@ -96,7 +97,7 @@ def test_composite_residual(S, dim, n, K):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("noise", [0, 1])
-@pytest.mark.parametrize("dim,n,K", GRIDS[:3])
+@pytest.mark.parametrize("dim,n,K", GRIDS[:3] + GRIDS[5:])
 def test_patch_sweeps(S, prec, noise, dim, n, K):
     c, cg = handle(S, dim, n, K, prec)
     dt = torch.float64 if prec == "fp64" else torch.float32
@@ -156,18 +157,21 @@ def test_solve(S, prec, dim, n, K):
     S.selm_comp_destroy(c)
 
 
-@pytest.mark.parametrize("dim,n,K", [(2, 16, 2), (3, 8, 2)])
-def test_chain(S, dim, n, K):
-    c, cg = handle(S, dim, n, K, "fp64", seed=9, instance=4)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim,n,K", [(2, 16, 2), (3, 8, 2), (3, 16, 3)])
+def test_chain(S, prec, dim, n, K):
+    """Five stochastic cycles of the chain; with FP32 inner cycles the chain
+    state is a double-float pair, compared at the FP32 tolerance."""
+    c, cg = handle(S, dim, n, K, prec, seed=9, instance=4)
     S.selm_comp_set_cycle(c, 3)
     buf = torch.zeros(S.selm_comp_size(c), dtype=torch.float64, device="cuda")
     S.selm_comp_sample(c, 5, buf)
-    assert S.selm_comp_chain(c)[1] == 8
+    assert S.selm_comp_chain(c) == 8
     want = [np.zeros(cg.size) for _ in range(cg.ncomp)]
     zero = [np.zeros(cg.size) for _ in range(cg.ncomp)]
     for k in range(3, 8):
         OC.fac_cycle(cg, want, zero, PhiloxNoise(9, 4, k), 1.0)
-    assert rel(from_gpu(cg, buf.cpu().numpy()), want) < 1e-12
+    assert rel(from_gpu(cg, buf.cpu().numpy()), want) < (1e-12 if prec == "fp64" else 1e-5)
     assert S.selm_comp_stats(c) == 5
     S.selm_comp_destroy(c)
 

@@ -350,8 +350,10 @@ selm_status selm_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1
  * base hierarchy; the correction copied into the patch; nu_patch Gibbs sweeps
  * of the patch cells with the composite rows (four passes per sweep: red,
  * then the red interface-layer cells with odd x, then the same for black);
- * z += correction.  Noise of the patch sweeps: Philox counter kind 2 with the
- * cell's linear patch index (group = index >> 2, lane = index & 3).
+ * z += correction.  Noise of the patch sweeps: Philox counter kind 2; the
+ * four cells of one colour in an 8-cell x segment of a patch row share a
+ * block: group = row * ceil(2n / 8) + x / 8 (row = layer * rows_per_layer +
+ * y), lane = (x mod 8) / 2.
  *
  * Composite vectors are FP64 device arrays of selm_comp_size() elements: the
  * patch (per component [2K][2n][2n], 2-D [2K][1][2n], x fastest) followed by

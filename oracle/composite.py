@@ -56,7 +56,10 @@ its 2^(d-1) siblings across a coarse-fine face, so a red-black order is not a
 valid Gibbs order on the two interface layers (m = 0 and m = 2K-1).  A sweep
 is four passes: red sites except the interface-layer sites with odd p, then
 those, then the same for black (red = (p + q + m) even).  Noise: counter
-stream kind 2, linear patch index (group = index >> 2, lane = index & 3).
+stream kind 2; a patch row (m, q) is cut into segments of 8 cells along x,
+and the four cells of one colour in a segment share one Philox block:
+group = (m n_y + q) ceil(n_x / 8) + p // 8, lane = (p mod 8) // 2 (the two
+cells of a lane have opposite colours, so they never share a pass).
 """
 
 import numpy as np
@@ -206,6 +209,13 @@ class CompositeGrid:
             sets.append(np.nonzero((colour & late).ravel())[0])
         return sets
 
+    def noise_index(self, idx):
+        """Counter index of patch cells (linear indices idx): 4 group + lane."""
+        fz, fy, fx = self.fine_shape
+        row, p = idx // fx, idx % fx
+        nseg = (fx + 7) // 8
+        return 4 * (row * nseg + p // 8) + (p % 8) // 2
+
     def patch_sweep(self, qvec, rvec, comp, sweep_id, noise, sigma):
         """One Gibbs sweep of the patch cells of A q = r (composite rows), in place."""
         for pid, idx in enumerate(self.pass_sets()):
@@ -213,7 +223,7 @@ class CompositeGrid:
             dg = self.diag[idx]
             new = (rvec[idx] - (Aq - dg * qvec[idx])) / dg
             if sigma != 0.0:
-                nrm = noise.patch(comp, pid, sweep_id, idx)
+                nrm = noise.patch(comp, pid, sweep_id, self.noise_index(idx))
                 new = new + sigma * nrm / np.sqrt(dg)
             qvec[idx] = new
         return qvec

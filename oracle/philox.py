@@ -17,7 +17,7 @@ header):
 * ctr1  = level | comp << 4 | colour << 8 | sweep << 12 | kind << 20
           (kind 0 = smoother sweep, kind 1 = exact coarsest-level sample,
           kind 2 = sweep of a refined patch, whose sites are addressed by
-          their linear index in the patch array instead of a class rank)
+          a counter index of their own instead of a class rank)
 * ctr2, ctr3 = lo32(cycle), hi32(cycle)   (cycle = chain step counter)
 
 One Philox call yields four 32-bit words w0..w3 -> uniforms
@@ -141,7 +141,7 @@ class PhiloxNoise:
         return normals_for_ranks(self.key, c1, self.cycle, n)
 
     def patch(self, comp, pass_id, sweep, idx):
-        """Normals of refined-patch sites (linear indices idx) in one pass."""
+        """Normals of refined-patch sites (counter indices idx) in one pass."""
         c1 = pack_ctr1(0, comp, pass_id, sweep, KIND_PATCH)
         return normals_for_indices(self.key, c1, self.cycle, idx)
 

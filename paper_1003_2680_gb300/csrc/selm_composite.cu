@@ -263,11 +263,13 @@ __global__ void __launch_bounds__(kCBlock) k_comp_patch(CompGeo G, T* __restrict
   T nv = (rp[c * G.fsize + lin] - off) / dg;
   if (NOISE) {
     const unsigned long long cy = *cyc;
-    // counter word 1: level 0 | comp << 4 | pass << 8 | sweep << 12 | kind 2 << 20
+    // counter word 1: level 0 | comp << 4 | pass << 8 | sweep << 12 | kind 2 << 20;
+    // group = row * ceil(fx / 8) + p / 8, lane = (p mod 8) / 2
     const uint32_t c1 = ((uint32_t)c << 4) | ((uint32_t)pass << 8) | ((uint32_t)sweep << 12) | (2u << 20);
+    const uint32_t grp = (uint32_t)(((long long)m * G.fy + q) * ((G.fx + 7) >> 3) + (p >> 3));
     T nn;
-    normal_of(philox4x32_10(make_uint4((uint32_t)(lin >> 2), c1, (uint32_t)cy, (uint32_t)(cy >> 32)), key.k0, key.k1),
-              (int)(lin & 3), &nn);
+    normal_of(philox4x32_10(make_uint4(grp, c1, (uint32_t)cy, (uint32_t)(cy >> 32)), key.k0, key.k1), (p & 7) >> 1,
+              &nn);
     nv += nn / tsqrt(dg);
   }
   zp[lin] = nv;
@@ -358,14 +360,12 @@ __global__ void __launch_bounds__(kCBlock) k_comp_patch_v8(CompGeo G, T* __restr
       for (int l = 0; l < 4; ++l) ca[l] = brow[l];
     }
   }
-  T n8[8];
-  if (NOISE) {
+  T n4[4];
+  if (NOISE) {   // one block per segment: lane l for the colour's site 2l + par
     const unsigned long long cy = *cyc;
     const uint32_t c1 = ((uint32_t)c << 4) | ((uint32_t)pass << 8) | ((uint32_t)sweep << 12) | (2u << 20);
-    const uint32_t g0 = (uint32_t)((rbase + x0) >> 2);
-    Normals<T>::get(philox4x32_10(make_uint4(g0, c1, (uint32_t)cy, (uint32_t)(cy >> 32)), key.k0, key.k1), n8);
-    Normals<T>::get(philox4x32_10(make_uint4(g0 + 1, c1, (uint32_t)cy, (uint32_t)(cy >> 32)), key.k0, key.k1),
-                    n8 + 4);
+    const uint32_t grp = (uint32_t)(((long long)m * fy + q) * segs + seg);
+    Normals<T>::get(philox4x32_10(make_uint4(grp, c1, (uint32_t)cy, (uint32_t)(cy >> 32)), key.k0, key.k1), n4);
   }
   const T rsd = NOISE ? (T)1 / tsqrt(dg) : (T)0;
 #pragma unroll
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(kCBlock) k_comp_patch_v8(CompGeo G, T* __restr
         if (m == fz - 1) off -= w1 * ca[l];
       }
       T nv = (rr[e] - off) / dg;
-      if (NOISE) nv += n8[e] * rsd;
+      if (NOISE) nv += n4[l] * rsd;
       cen[e] = nv;
     }
   }
@@ -554,6 +554,118 @@ __global__ void __launch_bounds__(kCBlock) k_comp_df_to_f64(CompGeo G, const flo
   out[s] = (double)zh[s] + (double)zl[s];
 }
 
+// Main pass (late = 0) of a patch sweep marching along the patch layers: one
+// thread per (component, y row, 8-wide segment, chunk of kc layers); z
+// neighbours from registers, the next layer's row loaded before the current
+// one is computed.  On an interface layer a segment whose colour sites have
+// odd x belongs to the late pass and is left unchanged.
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kCBlock) k_comp_patch_zm(CompGeo G, T* __restrict__ vp, const T* __restrict__ vb,
+                                                           const T* __restrict__ rp, int colour, int sweep, int kc,
+                                                           Key key, const unsigned long long* __restrict__ cyc) {
+  const int fx = G.fx, fy = G.fy, fz = G.fz, segs = fx >> 3;
+  const long long chunks = (fz + kc - 1) / kc;
+  const long long per = (long long)fy * segs * chunks;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= per * G.ncomp) return;
+  const int c = (int)(g / per);
+  const long long item = g - c * per;
+  const long long col = item % ((long long)fy * segs);
+  const int chunk = (int)(item / ((long long)fy * segs));
+  const int q = (int)(col / segs), seg = (int)(col - (long long)q * segs);
+  const int m0 = chunk * kc, m1 = min(m0 + kc, fz);
+  const long long plane = (long long)fx * fy;
+  const int x0 = seg << 3;
+  T* zp = vp + c * G.fsize;
+  const T* rr0 = rp + c * G.fsize;
+  const long long base = (long long)q * fx + x0;
+  const int qm = q == 0 ? fy - 1 : q - 1, qp = q == fy - 1 ? 0 : q + 1;
+  const long long ymb = (long long)qm * fx + x0, ypb = (long long)qp * fx + x0;
+  const long long rowx = (long long)q * fx;
+  const int xl_i = x0 == 0 ? fx - 1 : x0 - 1, xr_i = x0 + 8 == fx ? 0 : x0 + 8;
+  const T sf = (T)G.sf;
+  const T w2 = (T)(G.wcf / ((double)G.nch * G.nch));
+  const T w1 = (T)(G.wcf / G.nch);
+  const int pass = 2 * colour;
+  const unsigned long long cy = NOISE ? *cyc : 0ull;
+  const uint32_t c1 = ((uint32_t)c << 4) | ((uint32_t)pass << 8) | ((uint32_t)sweep << 12) | (2u << 20);
+  T prev[8], cur[8], nxt[8], rr[8], ym[8], yp[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) prev[e] = (T)0;
+  if (m0 > 0) Vec<T>::load8(zp + base + (long long)(m0 - 1) * plane, prev);
+  Vec<T>::load8(zp + base + (long long)m0 * plane, cur);
+  for (int m = m0; m < m1; ++m) {
+    const long long mp = (long long)m * plane;
+    if (m + 1 < fz)
+      Vec<T>::load8(zp + base + mp + plane, nxt);
+    else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) nxt[e] = (T)0;
+    }
+    const int par = (q + m + colour) & 1;
+    const bool iface = m == 0 || m == fz - 1;
+    if (!(iface && par)) {
+      Vec<T>::load8(rr0 + base + mp, rr);
+      int nn = 2;
+      T acc[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] = (m > 0 ? prev[e] : (T)0) + (m + 1 < fz ? nxt[e] : (T)0);
+      nn += (m > 0) + (m + 1 < fz);
+      if (fy > 1) {
+        Vec<T>::load8(zp + ymb + mp, ym);
+        Vec<T>::load8(zp + ypb + mp, yp);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[e] += ym[e] + yp[e];
+        nn += 2;
+      }
+      const T left = zp[rowx + mp + xl_i], right = zp[rowx + mp + xr_i];
+      T dg = sf * (T)nn;
+      T ca[4] = {(T)0, (T)0, (T)0, (T)0};
+      if (iface) {
+        dg += w2;
+        if (m == fz - 1) {
+          const T* brow = vb + c * G.bsize + ((long long)G.K * G.by + (fy > 1 ? (q >> 1) : 0)) * G.bx + (x0 >> 1);
+#pragma unroll
+          for (int l = 0; l < 4; ++l) ca[l] = brow[l];
+        }
+      }
+      T n4[4] = {(T)0, (T)0, (T)0, (T)0};
+      if (NOISE) {
+        const uint32_t grp = (uint32_t)(((long long)m * fy + q) * segs + seg);
+        Normals<T>::get(philox4x32_10(make_uint4(grp, c1, (uint32_t)cy, (uint32_t)(cy >> 32)), key.k0, key.k1), n4);
+      }
+      const T rsd = NOISE ? (T)1 / tsqrt(dg) : (T)0;
+      const bool up1 = (q ^ 1) == qp;   // which loaded y row holds the siblings' row q ^ 1
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp) {
+          if (pp != par) continue;
+          const int e = 2 * l + pp;
+          const T xl = e == 0 ? left : cur[e - 1];
+          const T xr = e == 7 ? right : cur[e + 1];
+          T off = -sf * (acc[e] + xl + xr);
+          if (iface) {
+            T sib = cur[e ^ 1];
+            if (fy > 1) sib += up1 ? yp[e] + yp[e ^ 1] : ym[e] + ym[e ^ 1];
+            off += w2 * sib;
+            if (m == fz - 1) off -= w1 * ca[l];
+          }
+          T nv = (rr[e] - off) / dg;
+          if (NOISE) nv += n4[l] * rsd;
+          cur[e] = nv;
+        }
+      }
+      Vec<T>::store8(zp + base + mp, cur);
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      prev[e] = cur[e];
+      cur[e] = nxt[e];
+    }
+  }
+}
+
 // z += q on the composite unknowns (covered base rows untouched).
 template <typename T>
 __global__ void __launch_bounds__(kCBlock) k_comp_update(CompGeo G, double* __restrict__ z, const T* __restrict__ vp,
@@ -719,7 +831,14 @@ selm_status patch_sweeps_t(selm_comp* C, T* vp, const T* vb, const T* rp, int co
     for (int pass = 0; pass < 4; ++pass) {
       prof::Scope ps(SELM_K_FINE_SWEEP, st);
       const long long rows = (long long)((pass & 1) ? 2 : G.fz) * G.fy * G.ncomp;
-      if (v8) {
+      if (v8 && !(pass & 1)) {   // main pass: march along the layers (chunks of 16)
+        const int kc = 16;
+        const long long nt = (long long)G.fy * (G.fx >> 3) * ((G.fz + kc - 1) / kc) * G.ncomp;
+        if (noise)
+          k_comp_patch_zm<T, true><<<cgrid(nt), kCBlock, 0, st>>>(G, vp, vb, rp, pass >> 1, s, kc, key, cyc);
+        else
+          k_comp_patch_zm<T, false><<<cgrid(nt), kCBlock, 0, st>>>(G, vp, vb, rp, pass >> 1, s, kc, key, cyc);
+      } else if (v8) {
         const long long nt = rows * (G.fx >> 3);
         if (noise)
           k_comp_patch_v8<T, true><<<cgrid(nt), kCBlock, 0, st>>>(G, vp, vb, rp, pass, s, key, cyc);

@@ -566,80 +566,100 @@ __device__ __forceinline__ Band7<T> band7_row(const CompDev& c, int k) {
   return r;
 }
 
-// Red-black colour pass of a banded 7-point level (the composite base grid),
-// one thread per 8-wide row segment (the four sites of the colour in it form
-// one noise group: group = rank >> 2 = row nx/8 + segment); nx % 8 == 0.
+// Work items of a z-marching pass: per component ny * (nx / 8) columns times
+// ceil(nz / kc) chunks of kc rows.
+struct ColumnPass {
+  long long start[kMaxComps + 1];
+  int kc;
+};
+
+// Red-black colour pass of a banded 7-point level, marching along z: one
+// thread per (component, y row, 8-wide x segment, chunk of kc z rows).  The
+// z neighbours of row k come from registers (row k-1 after its update: its
+// sites of the other colour, the ones row k reads, are unchanged by the
+// pass), and the next row's loads are issued before the current row is
+// computed (two rows of loads in flight).  Values read across threads are
+// always of the other colour, which no thread writes in the pass; the
+// vector loads also carry same-colour lanes, which are not used.
 template <typename T, bool NOISE>
-__global__ void __launch_bounds__(kBlock) k_band7_rb_v8(LevelDev L, RowPass rp, T* __restrict__ v,
+__global__ void __launch_bounds__(kBlock) k_band7_rb_zm(LevelDev L, ColumnPass cp, T* __restrict__ v,
                                                        const T* __restrict__ b, int colour, int sweep, Key key,
                                                        const unsigned long long* __restrict__ cyc) {
-  const int segs = L.c[0].nx >> 3;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int row_all = gt / segs;
-  if (row_all >= rp.rstart[L.ncomp]) return;
-  const int seg = gt - row_all * segs;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cp.start[L.ncomp]) return;
   int ci = 0;
-  while (ci + 1 < L.ncomp && row_all >= rp.rstart[ci + 1]) ++ci;
+  while (ci + 1 < L.ncomp && g >= cp.start[ci + 1]) ++ci;
   const CompDev& c = L.c[ci];
-  const int row = row_all - rp.rstart[ci];
-  const int j = row % c.ny, k = row / c.ny;
-  const int nx = c.nx;
-  const long long plane = (long long)nx * c.ny;
-  const long long rbase = c.off + (long long)row * nx;
+  const int nx = c.nx, ny = c.ny, nz = c.nz, segs = nx >> 3;
+  const long long item = g - cp.start[ci];
+  const long long col = item % ((long long)ny * segs);
+  const int chunk = (int)(item / ((long long)ny * segs));
+  const int j = (int)(col / segs), seg = (int)(col - (long long)j * segs);
+  const int k0 = chunk * cp.kc, k1 = min(k0 + cp.kc, nz);
+  const long long plane = (long long)nx * ny;
   const int x0 = seg << 3;
-  const Band7<T> R = band7_row<T>(c, k);
+  const long long base = c.off + (long long)j * nx + x0;   // (k = 0, j, x0)
+  const long long ym0 = c.off + (long long)(j == 0 ? ny - 1 : j - 1) * nx + x0;
+  const long long yp0 = c.off + (long long)(j == ny - 1 ? 0 : j + 1) * nx + x0;
+  const long long rowx = c.off + (long long)j * nx;
+  const int xl_i = x0 == 0 ? nx - 1 : x0 - 1, xr_i = x0 + 8 == nx ? 0 : x0 + 8;
   const T wxm = sep_w1<T>(c, 3), wxp = sep_w1<T>(c, 5), wym = sep_w1<T>(c, 1), wyp = sep_w1<T>(c, 7);
-  T cen[8], bb[8], acc[8];
-  Vec<T>::load8(v + rbase + x0, cen);
-  Vec<T>::load8(b + rbase + x0, bb);
-  const T left = v[rbase + (x0 == 0 ? nx - 1 : x0 - 1)];
-  const T right = v[rbase + (x0 + 8 == nx ? 0 : x0 + 8)];
+  const unsigned long long cy = NOISE ? *cyc : 0ull;
+  const uint32_t c1 = ctr1_of(L.level, c.comp_id, colour, sweep, 0);
+  T prev[8], cur[8], nxt[8], bb[8], ty[8];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) acc[e] = (T)0;
-  if (c.ny > 1) {
-    T t[8];
-    const long long ym = c.off + ((long long)k * c.ny + (j == 0 ? c.ny - 1 : j - 1)) * nx + x0;
-    const long long yp = c.off + ((long long)k * c.ny + (j == c.ny - 1 ? 0 : j + 1)) * nx + x0;
-    Vec<T>::load8(v + ym, t);
+  for (int e = 0; e < 8; ++e) prev[e] = (T)0;
+  if (k0 > 0) Vec<T>::load8(v + base + (long long)(k0 - 1) * plane, prev);
+  Vec<T>::load8(v + base + (long long)k0 * plane, cur);
+  for (int k = k0; k < k1; ++k) {
+    const long long kp = (long long)k * plane;
+    if (k + 1 < nz)
+      Vec<T>::load8(v + base + kp + plane, nxt);
+    else {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) acc[e] += R.a * wym * t[e];
-    Vec<T>::load8(v + yp, t);
+      for (int e = 0; e < 8; ++e) nxt[e] = (T)0;
+    }
+    Vec<T>::load8(b + base + kp, bb);
+    const Band7<T> R = band7_row<T>(c, k);
+    T acc[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) acc[e] += R.a * wyp * t[e];
+    for (int e = 0; e < 8; ++e) acc[e] = (k > 0 ? R.dn * prev[e] : (T)0) + (k + 1 < nz ? R.up * nxt[e] : (T)0);
+    if (ny > 1) {
+      Vec<T>::load8(v + ym0 + kp, ty);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] += R.a * wym * ty[e];
+      Vec<T>::load8(v + yp0 + kp, ty);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] += R.a * wyp * ty[e];
+    }
+    const T left = v[rowx + kp + xl_i], right = v[rowx + kp + xr_i];
+    T n4[4] = {(T)0, (T)0, (T)0, (T)0};
+    if (NOISE) {
+      const uint32_t grp = (uint32_t)((long long)k * ny + j) * (uint32_t)segs + (uint32_t)seg;
+      Normals<T>::get(philox4x32_10(make_uint4(grp, c1, (uint32_t)cy, (uint32_t)(cy >> 32)), key.k0, key.k1), n4);
+    }
+    const T rsd = NOISE ? (T)1 / tsqrt(R.diag) : (T)0;
+    const int par = (j + k + colour) & 1;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+#pragma unroll
+      for (int pp = 0; pp < 2; ++pp) {
+        if (pp != par) continue;
+        const int e = 2 * l + pp;
+        const T xl = e == 0 ? left : cur[e - 1];
+        const T xr = e == 7 ? right : cur[e + 1];
+        T nv = (bb[e] - (acc[e] + R.a * (wxm * xl + wxp * xr))) / R.diag;
+        if (NOISE) nv += n4[l] * rsd;
+        cur[e] = nv;
+      }
+    }
+    Vec<T>::store8(v + base + kp, cur);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      prev[e] = cur[e];
+      cur[e] = nxt[e];
+    }
   }
-  if (k > 0) {
-    T t[8];
-    Vec<T>::load8(v + rbase - plane + x0, t);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) acc[e] += R.dn * t[e];
-  }
-  if (k < c.nz - 1) {
-    T t[8];
-    Vec<T>::load8(v + rbase + plane + x0, t);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) acc[e] += R.up * t[e];
-  }
-  T n4[4] = {(T)0, (T)0, (T)0, (T)0};
-  if (NOISE) {
-    const unsigned long long cy = *cyc;
-    const uint32_t grp = (uint32_t)row * (uint32_t)(nx >> 3) + (uint32_t)seg;
-    Normals<T>::get(philox10(make_uint4(grp, ctr1_of(L.level, c.comp_id, colour, sweep, 0), (uint32_t)cy,
-                                        (uint32_t)(cy >> 32)),
-                             key.k0, key.k1),
-                    n4);
-  }
-  const T rsd = NOISE ? (T)1 / tsqrt(R.diag) : (T)0;
-  const int par = (j + k + colour) & 1;
-#pragma unroll
-  for (int l = 0; l < 4; ++l) {
-    const int e = 2 * l + par;   // par is 0 or 1: the colour's sites in the segment
-    const T xl = e == 0 ? left : cen[e - 1];
-    const T xr = e == 7 ? right : cen[e + 1];
-    T nv = (bb[e] - (acc[e] + R.a * (wxm * xl + wxp * xr))) / R.diag;
-    if (NOISE) nv += n4[l] * rsd;
-    cen[e] = nv;
-  }
-  Vec<T>::store8(v + rbase + x0, cen);
 }
 
 // A banded (Galerkin-form) level whose operator is the 7-point stencil (the
@@ -1317,20 +1337,21 @@ cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool n
     return cudaGetLastError();
   }
   if (L.rb && L.c[0].nx % 8 == 0) {
-    RowPass rp{};
-    int rows = 0;
+    // banded 7-point level: march along z (chunks of 16 rows)
+    ColumnPass cp{};
+    cp.kc = 16;
+    long long items = 0;
     for (int ci = 0; ci < L.ncomp; ++ci) {
-      rp.rstart[ci] = rows;
-      rows += L.c[ci].ny * L.c[ci].nz;
+      cp.start[ci] = items;
+      items += (long long)L.c[ci].ny * (L.c[ci].nx >> 3) * ((L.c[ci].nz + cp.kc - 1) / cp.kc);
     }
-    rp.rstart[L.ncomp] = rows;
-    const long long nt = (long long)rows * (L.c[0].nx >> 3);
+    cp.start[L.ncomp] = items;
     for (int colour = 0; colour < 2; ++colour) {
       prof::Scope ps(SELM_K_COARSE_SWEEP, st);
       if (noise)
-        k_band7_rb_v8<T, true><<<grid_for(nt), kBlock, 0, st>>>(L, rp, v, b, colour, sweep, key, cyc);
+        k_band7_rb_zm<T, true><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
       else
-        k_band7_rb_v8<T, false><<<grid_for(nt), kBlock, 0, st>>>(L, rp, v, b, colour, sweep, key, cyc);
+        k_band7_rb_zm<T, false><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
     }
     return cudaGetLastError();
   }

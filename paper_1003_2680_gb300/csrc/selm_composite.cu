@@ -232,6 +232,28 @@ __global__ void __launch_bounds__(kCBlock) k_comp_prolong(CompGeo G, T* __restri
   vp[s] = vb[c * G.bsize + ((long long)(m >> 1) * G.by + (G.fy > 1 ? (q >> 1) : 0)) * G.bx + (p >> 1)];
 }
 
+// The same copy on 8-wide segments of the patch rows (fx % 8 == 0): four
+// parents, each to two consecutive fine cells.
+template <typename T>
+__global__ void __launch_bounds__(kCBlock) k_comp_prolong_v8(CompGeo G, T* __restrict__ vp,
+                                                             const T* __restrict__ vb) {
+  const int segs = G.fx >> 3;
+  const long long rows = (long long)G.fz * G.fy;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long row_all = g / segs;
+  if (row_all >= rows * G.ncomp) return;
+  const int seg = (int)(g - row_all * segs);
+  const int c = (int)(row_all / rows);
+  const long long rl = row_all - c * rows;
+  const int q = (int)(rl % G.fy), m = (int)(rl / G.fy);
+  const int x0 = seg << 3;
+  const T* par = vb + c * G.bsize + ((long long)(m >> 1) * G.by + (G.fy > 1 ? (q >> 1) : 0)) * G.bx + (x0 >> 1);
+  T out[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) out[e] = par[e >> 1];
+  Vec<T>::store8(vp + c * G.fsize + ((long long)m * G.fy + q) * G.fx + x0, out);
+}
+
 // One pass of a patch sweep (reading R25): pass = 2 colour + late, colour =
 // (p + q + m) mod 2, late = interface layer (m = 0 or 2K-1) and p odd.  Main
 // passes (late = 0) visit all layers, late passes the two interface layers.
@@ -523,6 +545,179 @@ __global__ void __launch_bounds__(kCBlock) k_comp_residual_df(CompGeo G, const f
     Az = df_add(Az, extra);
     rb[s1] = -(Az.h + Az.l);
   }
+}
+
+__device__ __forceinline__ void load8_df(const float* hi, const float* lo, long long i, DF o[8]) {
+  float a[8], b[8];
+  Vec<float>::load8(hi + i, a);
+  Vec<float>::load8(lo + i, b);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) o[e] = {a[e], b[e]};
+}
+
+// The chain residual r = -A z (double-float) on the patch rows, one thread
+// per 8-wide segment of a patch row (fx % 8 == 0).
+__global__ void __launch_bounds__(kCBlock) k_comp_residual_df_patch(CompGeo G, const float* __restrict__ zh,
+                                                                    const float* __restrict__ zl,
+                                                                    float* __restrict__ rp) {
+  const int fx = G.fx, fy = G.fy, fz = G.fz, segs = fx >> 3;
+  const long long rows = (long long)fz * fy;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long row_all = g / segs;
+  if (row_all >= rows * G.ncomp) return;
+  const int seg = (int)(g - row_all * segs);
+  const int c = (int)(row_all / rows);
+  const long long rl = row_all - c * rows;
+  const int q = (int)(rl % fy), m = (int)(rl / fy);
+  const float* ph = zh + c * G.fsize;
+  const float* pl = zl + c * G.fsize;
+  const long long plane = (long long)fx * fy;
+  const long long rbase = (long long)m * plane + (long long)q * fx;
+  const int x0 = seg << 3;
+  DF cur[8], nb[8], t[8], rq[8];
+  load8_df(ph, pl, rbase + x0, cur);
+  const DF left = df_at(ph, pl, rbase + (x0 == 0 ? fx - 1 : x0 - 1));
+  const DF right = df_at(ph, pl, rbase + (x0 + 8 == fx ? 0 : x0 + 8));
+#pragma unroll
+  for (int e = 0; e < 8; ++e) nb[e] = df_add(e == 0 ? left : cur[e - 1], e == 7 ? right : cur[e + 1]);
+  int nn = 2;
+  const bool iface = m == 0 || m == fz - 1;
+  if (fy > 1) {
+    const int qm = q == 0 ? fy - 1 : q - 1, qp = q == fy - 1 ? 0 : q + 1;
+    load8_df(ph, pl, (long long)m * plane + (long long)qm * fx + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) nb[e] = df_add(nb[e], t[e]);
+    if ((q ^ 1) == qm) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) rq[e] = t[e];
+    }
+    load8_df(ph, pl, (long long)m * plane + (long long)qp * fx + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) nb[e] = df_add(nb[e], t[e]);
+    if ((q ^ 1) == qp) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) rq[e] = t[e];
+    }
+    nn += 2;
+  }
+  if (m > 0) {
+    load8_df(ph, pl, rbase - plane + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) nb[e] = df_add(nb[e], t[e]);
+    ++nn;
+  }
+  if (m < fz - 1) {
+    load8_df(ph, pl, rbase + plane + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) nb[e] = df_add(nb[e], t[e]);
+    ++nn;
+  }
+  DF ca[4];
+  if (m == fz - 1) {
+    const long long bi = G.N0 + c * G.bsize + ((long long)G.K * G.by + (fy > 1 ? (q >> 1) : 0)) * G.bx + (x0 >> 1);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) ca[l] = df_at(zh, zl, bi + l);
+  }
+  const DF sf = df_from(G.sf_h, G.sf_l), w2 = df_from(G.w2_h, G.w2_l), w1 = df_from(G.w1_h, G.w1_l);
+  const DF fnn = df_from((float)nn, 0.f);
+  float out[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    DF Az = df_mul(sf, df_add(df_mul(fnn, cur[e]), df_neg(nb[e])));
+    if (iface) {
+      DF grp = df_add(cur[e], cur[e ^ 1]);
+      if (fy > 1) grp = df_add(grp, df_add(rq[e], rq[e ^ 1]));
+      Az = df_add(Az, df_mul(w2, grp));
+      if (m == fz - 1) Az = df_add(Az, df_neg(df_mul(w1, ca[e >> 1])));
+    }
+    out[e] = -(Az.h + Az.l);
+  }
+  Vec<float>::store8(rp + c * G.fsize + rbase + x0, out);
+}
+
+// The chain residual on the uncovered base rows, one thread per 8-wide
+// segment of a base row (bx % 8 == 0); the interface row's coarse-fine group
+// reads the sixteen patch children of the segment in each of its two rows.
+__global__ void __launch_bounds__(kCBlock) k_comp_residual_df_base(CompGeo G, const float* __restrict__ zh,
+                                                                   const float* __restrict__ zl,
+                                                                   float* __restrict__ rb) {
+  const int bx = G.bx, by = G.by, bz = G.bz, segs = bx >> 3;
+  const long long rows = (long long)(bz - G.K) * by;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long row_all = g / segs;
+  if (row_all >= rows * G.ncomp) return;
+  const int seg = (int)(g - row_all * segs);
+  const int c = (int)(row_all / rows);
+  const long long rl = row_all - c * rows;
+  const int l = (int)(rl % by), r = G.K + (int)(rl / by);
+  const float* bh = zh + G.N0 + c * G.bsize;
+  const float* bl = zl + G.N0 + c * G.bsize;
+  const long long plane = (long long)bx * by;
+  const long long rbase = (long long)r * plane + (long long)l * bx;
+  const int x0 = seg << 3;
+  DF cur[8], nb[8], t[8];
+  load8_df(bh, bl, rbase + x0, cur);
+  const DF left = df_at(bh, bl, rbase + (x0 == 0 ? bx - 1 : x0 - 1));
+  const DF right = df_at(bh, bl, rbase + (x0 + 8 == bx ? 0 : x0 + 8));
+#pragma unroll
+  for (int e = 0; e < 8; ++e) nb[e] = df_add(e == 0 ? left : cur[e - 1], e == 7 ? right : cur[e + 1]);
+  int nn = 3;   // x pair + the face above (row or top wall)
+  if (by > 1) {
+    load8_df(bh, bl, (long long)r * plane + (long long)(l == 0 ? by - 1 : l - 1) * bx + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) nb[e] = df_add(nb[e], t[e]);
+    load8_df(bh, bl, (long long)r * plane + (long long)(l == by - 1 ? 0 : l + 1) * bx + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) nb[e] = df_add(nb[e], t[e]);
+    nn += 2;
+  }
+  if (r + 1 < bz) {
+    load8_df(bh, bl, rbase + plane + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) nb[e] = df_add(nb[e], t[e]);
+  }
+  DF extra[8];
+  if (r > G.K) {
+    load8_df(bh, bl, rbase - plane + x0, t);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      nb[e] = df_add(nb[e], t[e]);
+      extra[e] = {0.f, 0.f};
+    }
+    ++nn;
+  } else {
+    // children of base cell x0 + e: patch layer fz-1, rows 2l (+1), cells 2(x0+e), 2(x0+e)+1
+    const float* ph = zh + c * G.fsize;
+    const float* pl = zl + c * G.fsize;
+    const long long fplane = (long long)G.fx * G.fy;
+    DF ch[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) ch[e] = {0.f, 0.f};
+    for (int a = 0; a < (by > 1 ? 2 : 1); ++a) {
+      const long long frow = (long long)(G.fz - 1) * fplane + (long long)(by > 1 ? 2 * l + a : 0) * G.fx + 2 * x0;
+      DF u[8], w[8];
+      load8_df(ph, pl, frow, u);
+      load8_df(ph, pl, frow + 8, w);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        ch[e] = df_add(ch[e], df_add(u[2 * e], u[2 * e + 1]));
+        ch[e + 4] = df_add(ch[e + 4], df_add(w[2 * e], w[2 * e + 1]));
+      }
+    }
+    const float inv = 1.0f / (float)G.nch;   // a power of two: exact
+    const DF wcf = df_from(G.wcf_h, G.wcf_l);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) extra[e] = df_mul(wcf, df_add(cur[e], df_neg({ch[e].h * inv, ch[e].l * inv})));
+  }
+  const DF sb = df_from(G.sb_h, G.sb_l);
+  const DF fnn = df_from((float)nn, 0.f);
+  float out[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    DF Az = df_add(df_mul(sb, df_add(df_mul(fnn, cur[e]), df_neg(nb[e]))), extra[e]);
+    out[e] = -(Az.h + Az.l);
+  }
+  Vec<float>::store8(rb + c * G.bsize + rbase + x0, out);
 }
 
 // z += q for the double-float chain (covered base rows untouched).
@@ -879,7 +1074,11 @@ selm_status correct_t(selm_comp* C, double* z, bool noise, const unsigned long l
   }
   {
     prof::Scope ps(SELM_K_PROLONG, st);
-    k_comp_prolong<T><<<cgrid(G.N0), kCBlock, 0, st>>>(G, (T*)s.v[0], (const T*)s.v[1]);
+    if (G.fx % 8 == 0)
+      k_comp_prolong_v8<T><<<cgrid((long long)G.fz * G.fy * (G.fx >> 3) * G.ncomp), kCBlock, 0, st>>>(
+          G, (T*)s.v[0], (const T*)s.v[1]);
+    else
+      k_comp_prolong<T><<<cgrid(G.N0), kCBlock, 0, st>>>(G, (T*)s.v[0], (const T*)s.v[1]);
   }
   CCK(cudaGetLastError());
   r = patch_sweeps_t<T>(C, (T*)s.v[0], (const T*)s.v[1], rp, C->nu, noise, cyc, st);
@@ -915,10 +1114,16 @@ selm_status fac_cycle(selm_comp* C, double* z, const double* b, bool noise, cons
 selm_status chain_cycle(selm_comp* C, const unsigned long long* cyc, cudaStream_t st) {
   if (!C->xh) return fac_cycle(C, C->xi, nullptr, true, cyc, nullptr, st);
   Sys& s = C->mg->vel;
-  {
+  const CompGeo& G = C->geo;
+  if (G.fx % 8 == 0 && G.bx % 8 == 0) {
     prof::Scope ps(SELM_K_OUTER_RESIDUAL, st);
-    k_comp_residual_df<<<cgrid(C->geo.N0 + C->geo.N1), kCBlock, 0, st>>>(C->geo, C->xh, C->xl, (float*)s.b[0],
-                                                                         (float*)s.b[1]);
+    k_comp_residual_df_patch<<<cgrid((long long)G.fz * G.fy * (G.fx >> 3) * G.ncomp), kCBlock, 0, st>>>(
+        G, C->xh, C->xl, (float*)s.b[0]);
+    k_comp_residual_df_base<<<cgrid((long long)(G.bz - G.K) * G.by * (G.bx >> 3) * G.ncomp), kCBlock, 0, st>>>(
+        G, C->xh, C->xl, (float*)s.b[1]);
+  } else {
+    prof::Scope ps(SELM_K_OUTER_RESIDUAL, st);
+    k_comp_residual_df<<<cgrid(G.N0 + G.N1), kCBlock, 0, st>>>(G, C->xh, C->xl, (float*)s.b[0], (float*)s.b[1]);
   }
   CCK(cudaGetLastError());
   return correct_t<float>(C, nullptr, true, cyc, st, C->xh, C->xl);

@@ -662,6 +662,74 @@ __global__ void __launch_bounds__(kBlock) k_band7_rb_zm(LevelDev L, ColumnPass c
   }
 }
 
+// t = b - A v on a banded 7-point level, marching along z like
+// k_band7_rb_zm (every site of a segment, no colour).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_band7_residual_zm(LevelDev L, ColumnPass cp, const T* __restrict__ v,
+                                                             const T* __restrict__ b, T* __restrict__ t) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cp.start[L.ncomp]) return;
+  int ci = 0;
+  while (ci + 1 < L.ncomp && g >= cp.start[ci + 1]) ++ci;
+  const CompDev& c = L.c[ci];
+  const int nx = c.nx, ny = c.ny, nz = c.nz, segs = nx >> 3;
+  const long long item = g - cp.start[ci];
+  const long long col = item % ((long long)ny * segs);
+  const int chunk = (int)(item / ((long long)ny * segs));
+  const int j = (int)(col / segs), seg = (int)(col - (long long)j * segs);
+  const int k0 = chunk * cp.kc, k1 = min(k0 + cp.kc, nz);
+  const long long plane = (long long)nx * ny;
+  const int x0 = seg << 3;
+  const long long base = c.off + (long long)j * nx + x0;
+  const long long ym0 = c.off + (long long)(j == 0 ? ny - 1 : j - 1) * nx + x0;
+  const long long yp0 = c.off + (long long)(j == ny - 1 ? 0 : j + 1) * nx + x0;
+  const long long rowx = c.off + (long long)j * nx;
+  const int xl_i = x0 == 0 ? nx - 1 : x0 - 1, xr_i = x0 + 8 == nx ? 0 : x0 + 8;
+  const T wxm = sep_w1<T>(c, 3), wxp = sep_w1<T>(c, 5), wym = sep_w1<T>(c, 1), wyp = sep_w1<T>(c, 7);
+  T prev[8], cur[8], nxt[8], bb[8], ty[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) prev[e] = (T)0;
+  if (k0 > 0) Vec<T>::load8(v + base + (long long)(k0 - 1) * plane, prev);
+  Vec<T>::load8(v + base + (long long)k0 * plane, cur);
+  for (int k = k0; k < k1; ++k) {
+    const long long kp = (long long)k * plane;
+    if (k + 1 < nz)
+      Vec<T>::load8(v + base + kp + plane, nxt);
+    else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) nxt[e] = (T)0;
+    }
+    Vec<T>::load8(b + base + kp, bb);
+    const Band7<T> R = band7_row<T>(c, k);
+    T acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      acc[e] = R.diag * cur[e] + (k > 0 ? R.dn * prev[e] : (T)0) + (k + 1 < nz ? R.up * nxt[e] : (T)0);
+    if (ny > 1) {
+      Vec<T>::load8(v + ym0 + kp, ty);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] += R.a * wym * ty[e];
+      Vec<T>::load8(v + yp0 + kp, ty);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] += R.a * wyp * ty[e];
+    }
+    const T left = v[rowx + kp + xl_i], right = v[rowx + kp + xr_i];
+    T out[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const T xl = e == 0 ? left : cur[e - 1];
+      const T xr = e == 7 ? right : cur[e + 1];
+      out[e] = bb[e] - (acc[e] + R.a * (wxm * xl + wxp * xr));
+    }
+    Vec<T>::store8(t + base + kp, out);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      prev[e] = cur[e];
+      cur[e] = nxt[e];
+    }
+  }
+}
+
 // A banded (Galerkin-form) level whose operator is the 7-point stencil (the
 // composite base grid), smoothed in red-black order like level 0: colour =
 // (i + j + k) mod 2, rank = (k ny + j) nx/2 + i/2 within the colour, one
@@ -847,6 +915,76 @@ __global__ void __launch_bounds__(kBlock) k_prolong(LevelDev Lf, LevelDev Lc, T*
                                                    const T* __restrict__ vc) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s < Lf.size) prolong_at<T>(Lf, Lc, v, vc, s);
+}
+
+// v_f += P v_c on 8-wide segments of the fine rows (nx % 8 == 0; periodic x
+// and y with vertex coarsening, so a segment reads coarse x0/2 .. x0/2 + 4 of
+// each contributing coarse row; wall axis from the prolongation table).
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, T o[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) o[q] = p[q];
+}
+template <>
+__device__ __forceinline__ void load4<float>(const float* p, float o[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  o[0] = a.x;
+  o[1] = a.y;
+  o[2] = a.z;
+  o[3] = a.w;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_prolong_v8(LevelDev Lf, LevelDev Lc, RowPass rp, T* __restrict__ v,
+                                                      const T* __restrict__ vc) {
+  const int segs = Lf.c[0].nx >> 3;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row_all = gt / segs;
+  if (row_all >= rp.rstart[Lf.ncomp]) return;
+  const int seg = gt - row_all * segs;
+  int ci = 0;
+  while (ci + 1 < Lf.ncomp && row_all >= rp.rstart[ci + 1]) ++ci;
+  const CompDev& f = Lf.c[ci];
+  const CompDev& c = Lc.c[ci];
+  const int row = row_all - rp.rstart[ci];
+  const int j = row % f.ny, k = row / f.ny;
+  const int x0 = seg << 3, cx0 = x0 >> 1;
+  int yi[2] = {0, 0};
+  T yw[2] = {(T)1, (T)0};
+  int nyp = 1;
+  if (f.ny > 1) {
+    yi[0] = j >> 1;
+    if (j & 1) {
+      yi[1] = (j >> 1) + 1 == c.ny ? 0 : (j >> 1) + 1;
+      yw[0] = yw[1] = (T)0.5;
+      nyp = 2;
+    }
+  }
+  T acc[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) acc[e] = (T)0;
+  const long long cplane = (long long)c.nx * c.ny;
+  for (int qz = 0; qz < 2; ++qz) {
+    const int kc = f.pz_idx[k * 2 + qz];
+    if (kc < 0) continue;
+    const T wz = pz_w<T>(f, k * 2 + qz);
+    for (int a = 0; a < nyp; ++a) {
+      const T* crow = vc + c.off + (long long)kc * cplane + (long long)yi[a] * c.nx;
+      T cx[5];
+      load4<T>(crow + cx0, cx);
+      cx[4] = crow[cx0 + 4 == c.nx ? 0 : cx0 + 4];
+      const T w = wz * yw[a];
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        acc[e] += w * ((e & 1) ? (T)0.5 * (cx[e >> 1] + cx[(e >> 1) + 1]) : cx[e >> 1]);
+    }
+  }
+  T* out = v + f.off + (long long)row * f.nx + x0;
+  T cur[8];
+  Vec<T>::load8(out, cur);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) cur[e] += acc[e];
+  Vec<T>::store8(out, cur);
 }
 
 // ---------------------------------------------------------------------------
@@ -1390,6 +1528,18 @@ cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool n
 template <typename T>
 cudaError_t launch_residual(const LevelDev& L, const T* v, const T* b, T* t, cudaStream_t st) {
   prof::Scope ps(SELM_K_RESIDUAL, st);
+  if (L.rb && L.c[0].nx % 8 == 0) {
+    ColumnPass cp{};
+    cp.kc = 16;
+    long long items = 0;
+    for (int ci = 0; ci < L.ncomp; ++ci) {
+      cp.start[ci] = items;
+      items += (long long)L.c[ci].ny * (L.c[ci].nx >> 3) * ((L.c[ci].nz + cp.kc - 1) / cp.kc);
+    }
+    cp.start[L.ncomp] = items;
+    k_band7_residual_zm<T><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, t);
+    return cudaGetLastError();
+  }
   k_residual<T><<<grid_for(L.size), kBlock, 0, st>>>(L, v, b, t);
   return cudaGetLastError();
 }
@@ -1404,6 +1554,17 @@ cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* t, 
 template <typename T>
 cudaError_t launch_prolong(const LevelDev& Lf, const LevelDev& Lc, T* v, const T* vc, cudaStream_t st) {
   prof::Scope ps(SELM_K_PROLONG, st);
+  if (Lf.c[0].nx % 8 == 0) {
+    RowPass rp{};
+    int rows = 0;
+    for (int ci = 0; ci < Lf.ncomp; ++ci) {
+      rp.rstart[ci] = rows;
+      rows += Lf.c[ci].ny * Lf.c[ci].nz;
+    }
+    rp.rstart[Lf.ncomp] = rows;
+    k_prolong_v8<T><<<grid_for((long long)rows * (Lf.c[0].nx >> 3)), kBlock, 0, st>>>(Lf, Lc, rp, v, vc);
+    return cudaGetLastError();
+  }
   k_prolong<T><<<grid_for(Lf.size), kBlock, 0, st>>>(Lf, Lc, v, vc);
   return cudaGetLastError();
 }

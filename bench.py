@@ -207,12 +207,34 @@ PROFILED_SOURCES = ["selm_kernels.cu", "selm_coarse.cu", "selm_coarse.h", "selm_
                     "selm_launch.h"]
 
 
-def kernel_source_sha():
+# The composite-grid kernels add their own source to those.
+COMPOSITE_SOURCES = PROFILED_SOURCES + ["selm_composite.cu"]
+
+
+def kernel_source_sha(sources=None):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1003_2680_gb300", "csrc")
-    for name in PROFILED_SOURCES:
+    for name in sources or PROFILED_SOURCES:
         h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
+
+
+def composite_ncu_traffic():
+    """Per-launch DRAM bytes of the profiled composite kernels (ncu on the
+    192^3 case, scaled to the 256^3 workload by the cells processed), keyed by
+    kernel, from summaries taken on the current source."""
+    out = {}
+    for name in ("composite_base_rb_192", "composite_patch_192", "composite_residual_df_192"):
+        path = os.path.join(ROOT, "profiles", name + ".md")
+        if not os.path.exists(path):
+            continue
+        text = open(path).read()
+        m_k = re.search(r"^# `([A-Za-z0-9_]+)`", text, re.M)
+        m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+        m_tr = re.search(r"traffic_bytes_per_launch_256:\s*([0-9.eE+]+)", text)
+        if m_k and m_sha and m_tr and m_sha.group(1) == kernel_source_sha(COMPOSITE_SOURCES):
+            out[m_k.group(1)] = float(m_tr.group(1))
+    return out
 
 
 def ncu_traffic(kernel_class, n):
@@ -564,6 +586,8 @@ def run_composite(args):
     dominant = max(rooflines, key=lambda k: rooflines[k]["share_of_kernel_time"])
     roof = dict(rooflines[dominant])
     roof["others"] = {k: v for k, v in rooflines.items() if k != dominant}
+    # a class mixes several kernels here, so the ncu traffic is given per kernel
+    roof["ncu_traffic_per_launch_by_kernel"] = composite_ncu_traffic() or None
     cpu = None if args.no_cpu_baseline else composite_cpu_baseline(128, 16)
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": 1, "steps": args.steps,

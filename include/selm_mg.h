@@ -148,10 +148,15 @@ enum { SELM_OPT_COARSE_ENGINE = 1, SELM_OPT_ENGINE_CLUSTER = 2, SELM_OPT_ENGINE_
    first level whose slabs fit in shared memory); the levels above it run as
    GPU-wide launches.  Re-plans both systems' engines.
    SELM_OPT_LEVEL_COOP (default 1): each half V-cycle of a level above the
-   engine runs as one cooperative launch over every SM, its colour passes
-   separated by grid barriers (each wait bounded; a timed-out wait is
-   reported as SELM_ECUDA by the next solve's norm read); 0 selects one launch
-   per colour pass.  Both give the same result up to rounding. */
+   engine runs as one cooperative launch over every SM.  1: with FP32 inner
+   cycles the colour passes run in dataflow order, each site update waiting
+   for its coupled neighbours only (each stored value carries the parity of
+   its update count in its least significant mantissa bit, at most 1 ulp from
+   the rounded update); FP64 levels, and levels whose stencil admits no such
+   order, separate the passes by grid barriers.  2: grid barriers always.
+   Every wait is bounded; a timed-out wait is reported as SELM_ECUDA by the
+   next solve's norm read.  0 selects one launch per colour pass.  All give
+   the same result up to rounding. */
 selm_status selm_mg_set_option(selm_mg* h, int option, int value);
 /* Coarse engine of `system`: first level it covers (-1 = not used), cluster
    size and dynamic shared memory per CTA. */

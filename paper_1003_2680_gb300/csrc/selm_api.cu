@@ -205,6 +205,12 @@ void bind_system(Sys* s, int si, const Plan& p, char* ws) {
       }
     }
     L.size = off;
+    L.flow = 0;
+    if (l >= 1) {
+      L.flow = 1;
+      for (int ci = 0; ci < hs.ncomp; ++ci)
+        if (!coop_flow_ok(hs.lev[l][ci])) L.flow = 0;
+    }
     s->v[l] = ws + p.field_off[si][l][0];
     s->b[l] = ws + p.field_off[si][l][1];
     s->t[l] = ws + p.field_off[si][l][2];
@@ -252,11 +258,11 @@ selm_status vcycle_t(selm_mg* h, Sys& s, int l, T* v0, const T* b0, bool noise, 
       s.coop_bar && level_coop_supported<T>(L)) {
     const LevelDev& Lc = s.lev[l + 1];
     CK(launch_level_coop<T>(L, Lc, 0, h->mu1, h->mu2, v, b, (T*)s.t[l], (T*)s.b[l + 1], (T*)s.v[l + 1], s.coop_bar,
-                            noise, h->key, cyc, st));
+                            s.coop_flow, noise, h->key, cyc, st));
     selm_status r = vcycle_t<T>(h, s, l + 1, v0, b0, noise, cyc, st);
     if (r != SELM_OK) return r;
     CK(launch_level_coop<T>(L, Lc, 1, h->mu1, h->mu2, v, b, (T*)s.t[l], (T*)s.b[l + 1], (T*)s.v[l + 1], s.coop_bar,
-                            noise, h->key, cyc, st));
+                            s.coop_flow, noise, h->key, cyc, st));
     return SELM_OK;
   }
   if (l > 0 && s.use_engine && eng.valid && l == eng.params.l0) {
@@ -755,8 +761,9 @@ selm_status selm_mg_set_option(selm_mg* h, int option, int value) {
     return replan_engine(h, value, nullptr);
   }
   if (option == SELM_OPT_LEVEL_COOP) {
-    h->vel.use_coop = value != 0;
-    h->pres.use_coop = value != 0;
+    if (value < 0 || value > 2) return SELM_EINVAL;
+    h->vel.use_coop = h->pres.use_coop = value != 0;
+    h->vel.coop_flow = h->pres.coop_flow = value == 1;
     return replan_engine(h, h->vel.engine_cluster, nullptr);   // the automatic first level depends on it
   }
   if (option == SELM_OPT_ENGINE_LEVEL) {

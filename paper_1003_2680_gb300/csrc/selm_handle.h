@@ -28,6 +28,7 @@ struct Sys {
   int engine_level = 0;       // first level the engine may take (0 = the first that fits)
   void* eng_dev = nullptr;    // device slot of the engine plan
   bool use_coop = true;       // levels above the engine: cooperative launches (else one per pass)
+  bool coop_flow = true;      // FP32 cooperative passes in dataflow order where the level allows it
   unsigned* coop_bar = nullptr;   // grid-barrier words of the system's cooperative launches
 };
 

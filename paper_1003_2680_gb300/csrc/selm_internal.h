@@ -51,6 +51,7 @@ struct LevelDev {
   int level;
   int ncomp;
   int rb;                  // 1: a banded (Galerkin-form) level smoothed in red-black order
+  int flow;                // 1: FP32 cooperative colour passes may run in dataflow order
   long long size;          // elements of the whole level field
   CompDev c[kMaxComps];
 };
@@ -98,6 +99,9 @@ std::string build_velocity_system(int dim, int n, int levels, double mu, HostSys
 std::string build_pressure_system(int dim, int n, int levels, HostSystem* out);
 std::string build_composite_system(int dim, int n, int K, int levels_base, double mu, int ncomp, HostSystem* out);
 int default_levels(int n);
+// Whether the FP32 cooperative passes of a Galerkin level may run in dataflow
+// order (every neighbour the passes test is coupled to the site, both ways).
+bool coop_flow_ok(const HostComp& c);
 
 // Philox stream layout shared by the kernels (see include/selm_mg.h).
 inline uint32_t pack_ctr1(int level, int comp, int colour, int sweep, int kind) {

@@ -478,11 +478,14 @@ __device__ __forceinline__ T sep_apply(const CompDev& c, const T* vc, int i, int
     w1[q] = sep_w1<T>(c, q);
     w2[q] = sep_w2<T>(c, q);
   }
+  // Planes beyond a wall carry zero band weights (a Galerkin band row has no
+  // entry outside the level): their loads are clamped to a valid plane and
+  // multiplied by 0, so all 45 loads are issued without a branch between
+  // planes and overlap in one round trip.
   T acc = (T)0;
 #pragma unroll
   for (int dz = -2; dz <= 2; ++dz) {
-    const int kk = k + dz;
-    if (kk < 0 || kk >= nz) continue;
+    const int kk = min(max(k + dz, 0), nz - 1);
     const T* vp = vc + kk * ny * nx;
     T p1, p2;
     if (ny == 1) {
@@ -910,6 +913,13 @@ __device__ __forceinline__ void prolong_at(const LevelDev& Lf, const LevelDev& L
   v[s] += acc;
 }
 
+// prolong_at, then the cleared parity bit of the dataflow order (count 0).
+__device__ __forceinline__ void prolong_at_tag0(const LevelDev& Lf, const LevelDev& Lc, float* v, const float* vc,
+                                                long long s) {
+  prolong_at<float>(Lf, Lc, v, vc, s);
+  v[s] = __uint_as_float(__float_as_uint(v[s]) & ~1u);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_prolong(LevelDev Lf, LevelDev Lc, T* __restrict__ v,
                                                    const T* __restrict__ vc) {
@@ -1011,6 +1021,13 @@ struct CoopLevel {
   LevelDev L, Lc;                        // this level and the next coarser one
   ColourPass cp[kMaxCoopColours];        // colour q of this level
   int ncolour;
+  int flow;                              // 1: passes in dataflow order (FP32), else grid barriers
+  // Dataflow order, per colour and component, bit o = ((dz+2)*3 + dy+1)*3 + dx+1
+  // of the 3x3x5 window: check = neighbours coupled through the x-y weights
+  // (the centre excluded; planes without band entries are removed per row at
+  // run time), early = neighbours of a colour updated before this one in a sweep.
+  unsigned long long fcheck[kMaxCoopColours][kMaxComps];
+  unsigned long long fearly[kMaxCoopColours][kMaxComps];
   T* v;
   const T* b;
   T* t;
@@ -1061,6 +1078,167 @@ __device__ __forceinline__ bool coop_barrier(unsigned* bar) {
   return ok != 0;
 }
 
+// ---- Dataflow order of the colour passes (FP32 levels) ----------------------
+// Each stored value carries the parity of its update count in the least
+// significant mantissa bit (at most 1 ulp away from the rounded update).
+// Within one smoothing phase the counts start at 0 (the phase clears the bit
+// of every site behind a grid barrier).  A site of colour c updated in sweep q
+// needs its coupled neighbours at count q + 1 (colours before c) or q
+// (colours after c); because the operator couples the neighbour back to the
+// site, the neighbour's count is then one of {q, q + 1}, resp. {q - 1, q}, so
+// the parity alone tells whether it is ready.  A thread updates its sites
+// pass after pass as soon as their neighbours are ready, without grid
+// barriers, and reads exactly the values the coloured sweep reads.
+// Values and tags travel in one 32-bit word with relaxed GPU-scope accesses,
+// so no fence is needed.  Every wait is bounded (kCoopWaitNs, or the timeout
+// flag set by another thread).
+__device__ __forceinline__ float ld_tagged(const float* p) {
+  float v;
+  asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void st_tagged(float* p, float v) {
+  asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ float with_parity(float v, unsigned par) {
+  return __uint_as_float((__float_as_uint(v) & ~1u) | par);
+}
+
+constexpr unsigned long long kWindowBits = (1ull << kStencil) - 1ull;
+
+// Off-diagonal part of row k (sep_apply's arithmetic, same order) from tagged
+// loads; *tags receives the parity bit of every loaded neighbour at its
+// window position.
+__device__ __forceinline__ float sep_apply_tagged(const CompDev& c, const float* vc, int i, int j, int k,
+                                                  const int kk[5], unsigned long long* tags) {
+  const int nx = c.nx, ny = c.ny;
+  const int xm = i == 0 ? nx - 1 : i - 1, xp = i == nx - 1 ? 0 : i + 1;
+  const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
+  const float* zb = c.zb32 + k * 10;
+  unsigned long long tg = 0ull;
+  float acc = 0.f;
+#pragma unroll
+  for (int dz = -2; dz <= 2; ++dz) {
+    const float* vp = vc + kk[dz + 2] * ny * nx;
+    const int o = (dz + 2) * 9;
+    float p1, p2;
+    if (ny == 1) {
+      const float a = ld_tagged(vp + xm), cc = ld_tagged(vp + xp);
+      tg |= ((unsigned long long)(__float_as_uint(a) & 1u) << (o + 3)) |
+            ((unsigned long long)(__float_as_uint(cc) & 1u) << (o + 5));
+      p1 = c.w1f[3] * a + c.w1f[5] * cc;
+      p2 = c.w2f[3] * a + c.w2f[5] * cc;
+      if (dz != 0) {
+        const float bb = ld_tagged(vp + i);
+        tg |= (unsigned long long)(__float_as_uint(bb) & 1u) << (o + 4);
+        p1 += c.w1f[4] * bb;
+        p2 += c.w2f[4] * bb;
+      }
+    } else {
+      const float* r0 = vp + jm * nx;
+      const float* r1 = vp + j * nx;
+      const float* r2 = vp + jp * nx;
+      const float a0 = ld_tagged(r0 + xm), b0 = ld_tagged(r0 + i), c0 = ld_tagged(r0 + xp);
+      const float a1 = ld_tagged(r1 + xm), c1 = ld_tagged(r1 + xp);
+      const float a2 = ld_tagged(r2 + xm), b2 = ld_tagged(r2 + i), c2 = ld_tagged(r2 + xp);
+      tg |= ((unsigned long long)(__float_as_uint(a0) & 1u) << (o + 0)) |
+            ((unsigned long long)(__float_as_uint(b0) & 1u) << (o + 1)) |
+            ((unsigned long long)(__float_as_uint(c0) & 1u) << (o + 2)) |
+            ((unsigned long long)(__float_as_uint(a1) & 1u) << (o + 3)) |
+            ((unsigned long long)(__float_as_uint(c1) & 1u) << (o + 5)) |
+            ((unsigned long long)(__float_as_uint(a2) & 1u) << (o + 6)) |
+            ((unsigned long long)(__float_as_uint(b2) & 1u) << (o + 7)) |
+            ((unsigned long long)(__float_as_uint(c2) & 1u) << (o + 8));
+      p1 = c.w1f[0] * a0 + c.w1f[1] * b0 + c.w1f[2] * c0 + c.w1f[3] * a1 + c.w1f[5] * c1 + c.w1f[6] * a2 +
+           c.w1f[7] * b2 + c.w1f[8] * c2;
+      p2 = c.w2f[0] * a0 + c.w2f[1] * b0 + c.w2f[2] * c0 + c.w2f[3] * a1 + c.w2f[5] * c1 + c.w2f[6] * a2 +
+           c.w2f[7] * b2 + c.w2f[8] * c2;
+      if (dz != 0) {
+        const float b1 = ld_tagged(r1 + i);
+        tg |= (unsigned long long)(__float_as_uint(b1) & 1u) << (o + 4);
+        p1 += c.w1f[4] * b1;
+        p2 += c.w2f[4] * b1;
+      }
+    }
+    acc += zb[dz + 2] * p1 + zb[5 + dz + 2] * p2;
+  }
+  *tags = tg;
+  return acc;
+}
+
+__device__ __forceinline__ const float* window_ptr(int nx, int ny, int nz, const float* vc, int i, int j, int k,
+                                                   int o) {
+  const int dz = o / 9 - 2, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
+  const int ii = i + dx < 0 ? nx - 1 : (i + dx >= nx ? 0 : i + dx);
+  const int jj = ny == 1 ? 0 : (j + dy < 0 ? ny - 1 : (j + dy >= ny ? 0 : j + dy));
+  const int kk = min(max(k + dz, 0), nz - 1);
+  return vc + ((long long)kk * ny + jj) * nx + ii;
+}
+
+// Waits until the neighbour at window position o shows parity par (after a
+// full read found it not yet updated).  False when the wait timed out or
+// another thread raised the timeout flag.
+__device__ __noinline__ bool flow_wait1(int nx, int ny, int nz, const float* p0, int i, int j, int k, int o, unsigned par,
+                                        const unsigned* flag) {
+  const float* p = window_ptr(nx, ny, nz, p0, i, j, k, o);
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    if ((__float_as_uint(ld_tagged(p)) & 1u) == par) return true;
+    if ((it & 31u) == 0u && (*(volatile const unsigned*)flag != 0u || global_ns() - t0 > kCoopWaitNs)) return false;
+  }
+}
+
+// Heat-bath update of site g of colour col in local sweep q (noise counter
+// sweep), dataflow order.  False when a wait gave up.
+template <bool NOISE>
+__device__ __forceinline__ bool flow_site(const CoopLevel<float>& P, const ColourPass& cp, int col, int q, int sweep,
+                                          Key key, unsigned long long cy, long long g) {
+  const LevelDev& L = P.L;
+  const int ci = comp_of(cp.gstart, L.ncomp, g);
+  const CompDev& c = L.c[ci];
+  const unsigned rank = (unsigned)(g - cp.gstart[ci]);
+  const unsigned nxc = (unsigned)cp.nxc[ci], nyc = (unsigned)cp.nyc[ci];
+  const unsigned t = rank / nxc;
+  const int i = cp.cx[ci] + c.mx * (int)(rank - t * nxc);
+  const int j = cp.cy[ci] + c.my * (int)(t % nyc);
+  const int k = cp.cz[ci] + c.mz * (int)(t / nyc);
+  float* vc = P.v + c.off;
+  const float* zb = c.zb32 + k * 10;
+  int kk[5];
+  unsigned long long check = P.fcheck[col][ci];
+#pragma unroll
+  for (int dz = -2; dz <= 2; ++dz) {
+    kk[dz + 2] = min(max(k + dz, 0), c.nz - 1);
+    if (zb[dz + 2] == 0.f && zb[5 + dz + 2] == 0.f) check &= ~(0x1FFull << (9 * (dz + 2)));
+  }
+  const unsigned long long expect = P.fearly[col][ci] ^ ((q & 1) ? kWindowBits : 0ull);
+  const long long idx = (long long)((k * c.ny + j) * c.nx + i);
+  const float bb = __ldcg(P.b + c.off + idx);
+  const float diag = coarse_diag<float>(c, k);
+  float off;
+  for (;;) {
+    unsigned long long tags;
+    off = sep_apply_tagged(c, vc, i, j, k, kk, &tags);
+    const unsigned long long bad = (tags ^ expect) & check;
+    if (bad == 0ull) break;
+    const int o = __ffsll((long long)bad) - 1;
+    if (!flow_wait1(c.nx, c.ny, c.nz, vc, i, j, k, o, (unsigned)((expect >> o) & 1ull), P.bar + 2)) return false;
+  }
+  float nv = (bb - off) / diag;
+  if (NOISE) {
+    float nn;
+    normal_of(philox10(make_uint4(rank >> 2, ctr1_of(L.level, c.comp_id, cp.colour_id[ci], sweep, 0), (uint32_t)cy,
+                                  (uint32_t)(cy >> 32)),
+                       key.k0, key.k1),
+              (int)(rank & 3), &nn);
+    nv += nn / tsqrt(diag);
+  }
+  st_tagged(vc + idx, with_parity(nv, (unsigned)((q + 1) & 1)));
+  return true;
+}
+
 template <typename T, bool NOISE>
 __global__ void __launch_bounds__(CoopThreads<T>::value, 2)
     k_level_coop(const __grid_constant__ CoopLevel<T> P, int phase, int mu1, int mu2, Key key,
@@ -1069,7 +1247,22 @@ __global__ void __launch_bounds__(CoopThreads<T>::value, 2)
   const long long nth = (long long)gridDim.x * blockDim.x;
   const unsigned long long cy = NOISE ? *cyc : 0ull;
   const int ncomp = P.L.ncomp;
+  constexpr bool kFlowType = std::is_same<T, float>::value;
+  const bool flow = kFlowType && P.flow != 0;
   auto sweeps = [&](int first, int count) -> bool {
+    if constexpr (kFlowType) {
+      if (flow) {
+        bool ok = true;
+        for (int q = 0; q < count && ok; ++q)
+          for (int col = 0; col < P.ncolour && ok; ++col) {
+            const ColourPass& cp = P.cp[col];
+            for (long long g = tid; g < cp.gstart[ncomp] && ok; g += nth)
+              ok = flow_site<NOISE>(P, cp, col, q, first + q, key, cy, g);
+          }
+        if (!ok) atomicExch(P.bar + 2, 1u);
+        return ok;
+      }
+    }
     for (int q = 0; q < count; ++q)
       for (int col = 0; col < P.ncolour; ++col) {
         const ColourPass& cp = P.cp[col];
@@ -1079,8 +1272,16 @@ __global__ void __launch_bounds__(CoopThreads<T>::value, 2)
       }
     return true;
   };
+  // Dataflow order: every update count of a phase starts at 0, parity bit
+  // clear: phase 0 starts from v = 0 (the launch contract), phase 1 clears the
+  // bit as it adds the prolonged correction.
   if (phase == 0) {
-    if (!sweeps(0, mu1)) return;
+    if (flow) {
+      sweeps(0, mu1);   // a failed wait raised the flag: the barrier below returns false
+      if (!coop_barrier(P.bar)) return;
+    } else if (!sweeps(0, mu1)) {
+      return;
+    }
     for (long long s = tid; s < P.L.size; s += nth) {
       int ci, i, j, k;
       site_of(P.L, s, &ci, &i, &j, &k);
@@ -1093,7 +1294,15 @@ __global__ void __launch_bounds__(CoopThreads<T>::value, 2)
       P.vc[s] = (T)0;
     }
   } else {
-    for (long long s = tid; s < P.L.size; s += nth) prolong_at<T>(P.L, P.Lc, P.v, P.vc, s);
+    if constexpr (kFlowType) {
+      if (flow) {
+        for (long long s = tid; s < P.L.size; s += nth) prolong_at_tag0(P.L, P.Lc, P.v, P.vc, s);
+      } else {
+        for (long long s = tid; s < P.L.size; s += nth) prolong_at<T>(P.L, P.Lc, P.v, P.vc, s);
+      }
+    } else {
+      for (long long s = tid; s < P.L.size; s += nth) prolong_at<T>(P.L, P.Lc, P.v, P.vc, s);
+    }
     if (!coop_barrier(P.bar)) return;
     sweeps(mu1, mu2);
   }
@@ -1579,8 +1788,8 @@ bool level_coop_supported(const LevelDev& L) {
 
 template <typename T>
 cudaError_t launch_level_coop(const LevelDev& L, const LevelDev& Lc, int phase, int mu1, int mu2, T* v, const T* b,
-                              T* t, T* bc, T* vc, unsigned* bar, bool noise, Key key, const unsigned long long* cyc,
-                              cudaStream_t st) {
+                              T* t, T* bc, T* vc, unsigned* bar, bool flow, bool noise, Key key,
+                              const unsigned long long* cyc, cudaStream_t st) {
   const int blocks = coop_blocks<T>();
   if (blocks <= 0 || !level_coop_supported<T>(L)) return cudaErrorNotSupported;
   CoopLevel<T> P{};
@@ -1590,6 +1799,29 @@ cudaError_t launch_level_coop(const LevelDev& L, const LevelDev& Lc, int phase, 
   for (int ci = 0; ci < L.ncomp; ++ci) maxcol = maxcol > L.c[ci].ncol ? maxcol : L.c[ci].ncol;
   P.ncolour = maxcol;
   for (int q = 0; q < maxcol; ++q) colour_pass_of(L, q, &P.cp[q]);
+  P.flow = flow && sizeof(T) == 4 && L.flow ? 1 : 0;
+  if (P.flow) {
+    auto mod = [](int d, int m) { return ((d % m) + m) % m; };
+    for (int q = 0; q < maxcol; ++q)
+      for (int ci = 0; ci < L.ncomp; ++ci) {
+        const CompDev& c = L.c[ci];
+        unsigned long long check = 0ull, early = 0ull;
+        if (q < c.ncol) {
+          const int cx = q % c.mx, cy = (q / c.mx) % c.my, cz = q / (c.mx * c.my);
+          for (int dz = -2; dz <= 2; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+              for (int dx = -1; dx <= 1; ++dx) {
+                const int w = (dy + 1) * 3 + dx + 1, o = (dz + 2) * 9 + w;
+                if ((dz == 0 && w == 4) || (c.ny == 1 && dy != 0) || (c.w1f[w] == 0.f && c.w2f[w] == 0.f)) continue;
+                check |= 1ull << o;
+                const int qn = mod(cx + dx, c.mx) + c.mx * (mod(cy + dy, c.my) + c.my * mod(cz + dz, c.mz));
+                if (qn < q) early |= 1ull << o;
+              }
+        }
+        P.fcheck[q][ci] = check;
+        P.fearly[q][ci] = early;
+      }
+  }
   P.v = v;
   P.b = b;
   P.t = t;
@@ -1746,7 +1978,8 @@ cudaError_t launch_philox(const uint32_t* ctr, Key key, uint32_t* out, int n, cu
   template cudaError_t launch_prolong<T>(const LevelDev&, const LevelDev&, T*, const T*, cudaStream_t);     \
   template bool level_coop_supported<T>(const LevelDev&);                                                   \
   template cudaError_t launch_level_coop<T>(const LevelDev&, const LevelDev&, int, int, int, T*, const T*, T*, T*, \
-                                            T*, unsigned*, bool, Key, const unsigned long long*, cudaStream_t);  \
+                                            T*, unsigned*, bool, bool, Key, const unsigned long long*,            \
+                                            cudaStream_t);                                                        \
   template cudaError_t launch_coarsest<T>(const LevelDev&, T*, const T*, bool, Key,                         \
                                           const unsigned long long*, cudaStream_t);                         \
   template cudaError_t launch_outer_residual<T>(const LevelDev&, const double*, const double*, T*, double*, \

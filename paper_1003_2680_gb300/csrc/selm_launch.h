@@ -33,14 +33,17 @@ cudaError_t launch_prolong(const LevelDev& Lf, const LevelDev& Lc, T* v, const T
 // vc = 0); phase 1: the ascending half (v += P vc, then mu2 sweeps).  `bar`:
 // 4 zeroed, 8-byte aligned words of device memory, the launch's grid barrier,
 // reserved for the launches of one stream order (two launches that may
-// overlap need distinct words).
+// overlap need distinct words).  flow (FP32, levels with L.flow): the colour
+// passes run in dataflow order, each update waiting only for its coupled
+// neighbours (the parity of their update count in the value's last bit)
+// instead of a grid barrier between passes.
 // After a barrier wait timed out, bar[2] is non-zero, the level's result is
 // undefined and the caller reports the error and zeroes the words.
 // level_coop_supported() tells whether the device and the level admit it.
 template <typename T>
 cudaError_t launch_level_coop(const LevelDev& L, const LevelDev& Lc, int phase, int mu1, int mu2, T* v, const T* b,
-                              T* t, T* bc, T* vc, unsigned* bar, bool noise, Key key, const unsigned long long* cyc,
-                              cudaStream_t st);
+                              T* t, T* bc, T* vc, unsigned* bar, bool flow, bool noise, Key key,
+                              const unsigned long long* cyc, cudaStream_t st);
 template <typename T>
 bool level_coop_supported(const LevelDev& L);
 template <typename T>

@@ -352,6 +352,38 @@ std::string build_system(int dim, int n, int levels, double scale, const std::ve
 
 }  // namespace
 
+// The dataflow order of the cooperative passes waits on a neighbour only when
+// its update can be ordered against the site's: the neighbours a pass tests
+// (window planes with a band entry of the row, x-y positions with a weight,
+// in FP32, the centre excluded) must be coupled to the site (non-zero stencil
+// entry), of another colour class, inside the walls, and must test the site
+// in turn.  Any exception leaves the level to the barrier form.
+bool coop_flow_ok(const HostComp& c) {
+  const int nz = c.dims[2];
+  if (c.S.size() != (size_t)nz * kStencil || c.zb.size() != (size_t)nz * 10) return false;
+  for (int a = 0; a < 3; ++a)
+    if (c.mods[a] < 1 || (a < 2 && c.dims[a] > 1 && c.dims[a] % c.mods[a] != 0)) return false;
+  auto plane = [&](int k, int dz) {
+    return (float)c.zb[(size_t)k * 10 + dz + 2] != 0.f || (float)c.zb[(size_t)k * 10 + 5 + dz + 2] != 0.f;
+  };
+  auto xy = [&](int q) { return (float)c.w1[q] != 0.f || (float)c.w2[q] != 0.f; };
+  auto mod = [](int d, int m) { return ((d % m) + m) % m; };
+  for (int k = 0; k < nz; ++k)
+    for (int dz = -2; dz <= 2; ++dz) {
+      if (!plane(k, dz)) continue;
+      if (k + dz < 0 || k + dz >= nz) return false;
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int q = (dy + 1) * 3 + dx + 1;
+          if ((dz == 0 && q == 4) || (c.dims[1] == 1 && dy != 0) || !xy(q)) continue;
+          if (c.S[(size_t)k * kStencil + (dz + 2) * 9 + q] == 0.0) return false;
+          if (mod(dx, c.mods[0]) == 0 && mod(dy, c.mods[1]) == 0 && mod(dz, c.mods[2]) == 0) return false;
+          if (!plane(k + dz, -dz) || !xy(8 - q)) return false;
+        }
+    }
+  return true;
+}
+
 int default_levels(int n) {
   int levels = 1, m = n;
   while (m % 2 == 0 && m / 2 >= 4) {

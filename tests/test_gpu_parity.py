@@ -175,10 +175,11 @@ def test_vcycle_engine_and_per_pass_paths(prec, dim, n, levels, noise, engine):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("dim,n,levels", ENGINE_GRIDS)
 @pytest.mark.parametrize("noise", [0, 1])
-@pytest.mark.parametrize("coop", [1, 0])
+@pytest.mark.parametrize("coop", [1, 2, 0])
 def test_vcycle_engine_from_level_2(prec, dim, n, levels, noise, coop):
-    """Level 1 above the engine: one cooperative launch per half V-cycle
-    (coop=1) or one GPU-wide launch per colour pass (coop=0)."""
+    """Level 1 above the engine: one cooperative launch per half V-cycle with
+    the colour passes in dataflow order (coop=1, FP32) or separated by grid
+    barriers (coop=2), or one GPU-wide launch per colour pass (coop=0)."""
     m, osys, dt, tol = make(dim, n, levels, prec)
     S.selm_mg_set_option(m.h, S.SELM_OPT_ENGINE_LEVEL, 2)
     S.selm_mg_set_option(m.h, S.SELM_OPT_LEVEL_COOP, coop)
@@ -195,11 +196,13 @@ def test_vcycle_engine_from_level_2(prec, dim, n, levels, noise, coop):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_fac_solve_with_cooperative_level(prec):
+@pytest.mark.parametrize("coop", [1, 2])
+def test_fac_solve_with_cooperative_level(prec, coop):
     """Deterministic FAC solve with level 1 in cooperative launches: same
     cycle count (FP64) and solution as the oracle, no barrier timeout."""
     dim, n, levels = 3, 64, 4
     m, osys, dt, tol = make(dim, n, levels, prec)
+    S.selm_mg_set_option(m.h, S.SELM_OPT_LEVEL_COOP, coop)
     S.selm_mg_set_option(m.h, S.SELM_OPT_ENGINE_LEVEL, 2)
     assert S.selm_mg_engine_info(m.h)[0] == 2
     b0 = selm_inputs.fields(osys.shapes(0), seed=15)

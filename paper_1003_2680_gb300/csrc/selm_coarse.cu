@@ -99,11 +99,13 @@ __device__ __forceinline__ T stencil_row(const View<T>& w, int i, int j, int k) 
   const int xm = xpos(i == 0 ? nx - 1 : i - 1, L.half), xp = xpos(i == nx - 1 ? 0 : i + 1, L.half);
   const int x0 = xpos(i, L.half);
   const T* zb = w.tab + k * 12;
+  // Planes beyond a wall have zero band weights: their loads are clamped to
+  // a valid plane (inside the slab and its halo) and multiplied by 0, so the
+  // loads of all planes issue without a branch between them.
   T acc = (T)0;
 #pragma unroll
   for (int dz = -2; dz <= 2; ++dz) {
-    const int kk = k + dz;
-    if (kk < 0 || kk >= L.nz) continue;
+    const int kk = min(max(k + dz, 0), L.nz - 1);
     const T* vp = w.v + (kk - w.z0 + 2) * L.pp;
     T p1, p2;
     if (ny == 1) {
@@ -344,29 +346,48 @@ __device__ void load_all(const View<T>& w, const T* g, T* dst) {
   for (int q = threadIdx.x; q < n; q += blockDim.x) dst[q] = ld_cg(g + q);
 }
 
-// Exact coarsest step in CTA 0: v = L^-T (L^-1 b + noise n), FP64.
+// Exact coarsest step in CTA 0: v = L^-T (L^-1 b + noise n), FP64.  Each
+// row of L^-1 b and each column of L^-T y is a dot product split over eight
+// consecutive lanes and reduced with shuffles.
 template <typename T, bool NOISE>
 __device__ void coarsest_step(const View<T>& w, int level, const T* b, double* y, Key key, unsigned long long cyc) {
   const EngLevel<T>& L = *w.L;
   const int N = L.nx * L.ny * L.nz;
-  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+  constexpr int G = 8;
+  const int span = (N * G + 31) / 32 * 32;   // whole warps: every lane reaches the shuffles
+  for (int t = threadIdx.x; t < span; t += blockDim.x) {
+    const int r = t / G, g = t % G;
     double acc = 0.0;
-    for (int q = 0; q <= r; ++q) acc += L.Linv[(long long)r * N + q] * (double)b[q];
-    if (NOISE) {
-      const uint32_t c1 = (uint32_t)level | ((uint32_t)L.comp_id << 4) | (1u << 20);
-      double nn;
-      normal_of(eng_philox10(make_uint4((uint32_t)(r >> 2), c1, (uint32_t)cyc, (uint32_t)(cyc >> 32)), key.k0, key.k1),
-                r & 3, &nn);
-      acc += nn;
+    if (r < N)
+      for (int q = g; q <= r; q += G) acc += __ldg(L.Linv + (long long)r * N + q) * (double)b[q];
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (r < N && g == 0) {
+      if (NOISE) {
+        const uint32_t c1 = (uint32_t)level | ((uint32_t)L.comp_id << 4) | (1u << 20);
+        double nn;
+        normal_of(eng_philox10(make_uint4((uint32_t)(r >> 2), c1, (uint32_t)cyc, (uint32_t)(cyc >> 32)), key.k0,
+                               key.k1),
+                  r & 3, &nn);
+        acc += nn;
+      }
+      y[r] = acc;
     }
-    y[r] = acc;
   }
   __syncthreads();
-  for (int col = threadIdx.x; col < N; col += blockDim.x) {
+  for (int t = threadIdx.x; t < span; t += blockDim.x) {
+    const int col = t / G, g = t % G;
     double acc = 0.0;
-    for (int r = col; r < N; ++r) acc += L.Linv[(long long)r * N + col] * y[r];
-    const int i = col % L.nx, rr = col / L.nx;
-    w.v[w.loc(i, rr % L.ny, rr / L.ny)] = (T)acc;
+    if (col < N)
+      for (int r = col + g; r < N; r += G) acc += __ldg(L.Linv + (long long)r * N + col) * y[r];
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (col < N && g == 0) {
+      const int i = col % L.nx, rr = col / L.nx;
+      w.v[w.loc(i, rr % L.ny, rr / L.ny)] = (T)acc;
+    }
   }
 }
 
@@ -381,18 +402,9 @@ __device__ void sweeps(const View<T>& w, int level, int first_sweep, int count, 
     }
 }
 
-// Copies a level descriptor into shared memory (all threads, with barriers).
-template <typename T>
-__device__ __forceinline__ void stage(EngLevel<T>* dst, const EngLevel<T>* src) {
-  __syncthreads();
-  constexpr int n = (int)(sizeof(EngLevel<T>) / sizeof(int));
-  for (int q = threadIdx.x; q < n; q += blockDim.x) reinterpret_cast<int*>(dst)[q] = reinterpret_cast<const int*>(src)[q];
-  __syncthreads();
-}
-
-// Fills a table slot for the staged level L as seen by the CTA owning planes
+// Fills the table rows of the staged level L as seen by the CTA owning planes
 // [z0, z1): per row k the z bands, 1/A_ii and 1/sqrt(A_ii); per colour class
-// the geometry and the owned rank range.
+// the geometry and the owned rank range.  (No barrier: the caller syncs.)
 template <typename T>
 __device__ void stage_tables(const EngLevel<T>& L, int z0, int z1, T* tab, EngColour* col) {
   for (int q = threadIdx.x; q < L.nz * 12; q += blockDim.x) {
@@ -426,14 +438,11 @@ __device__ void stage_tables(const EngLevel<T>& L, int z0, int z1, T* tab, EngCo
     c.nsite = (c.nxc > 0 && c.nyc > 0 && nzc > 0 && kk_hi > kk_lo) ? (kk_hi - kk_lo) * pr : 0;
     col[q] = c;
   }
-  __syncthreads();
 }
 
 template <typename T, bool NOISE>
 __global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const EngParams<T>* __restrict__ P, EngRun run) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ EngLevel<T> sl[2];
-  __shared__ EngColour scol[2][kEngMaxColours];
   cg::cluster_group cl = cg::this_cluster();
   const int csize = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -443,19 +452,41 @@ __global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const
   const int lt = P->l0, lc = P->L - 1;
   const int mu1 = run.mu1, mu2 = run.mu2;
   const Key key = run.key;
-  T* tabs[2] = {(T*)(smem + P->tab_off), (T*)(smem + P->tab_off + P->tab_slot)};
+  EngLevel<T>* const lev0 = reinterpret_cast<EngLevel<T>*>(smem + P->lev_off);   // levels lt..lc
+  EngColour* const col0 = reinterpret_cast<EngColour*>(smem + P->col_off);
+  T* const stab = reinterpret_cast<T*>(smem + P->tab_off);
+  auto sl_at = [&](int l) -> EngLevel<T>& { return lev0[l - lt]; };
+  auto col_at = [&](int l) { return col0 + (size_t)(l - lt) * kEngMaxColours; };
+
+  // ---- stage every level once: descriptors, then colour classes and row tables ----
+  {
+    constexpr int n = (int)(sizeof(EngLevel<T>) / sizeof(int));
+    const int total = (lc - lt + 1) * n;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      const int l = lt + q / n, e = q - (q / n) * n;
+      reinterpret_cast<int*>(&sl_at(l))[e] = reinterpret_cast<const int*>(&E->lev[l])[e];
+    }
+    __syncthreads();
+    for (int l = lt; l <= lc; ++l) {
+      const EngLevel<T>& L = sl_at(l);
+      const View<T> w = make_view(L, smem, rank, L.cluster != 0);
+      stage_tables(L, w.z0, w.z1, stab + (size_t)P->tab_row[l] * 12, col_at(l));
+    }
+    __syncthreads();
+  }
+  auto view_of = [&](int l, bool cluster) {
+    View<T> w = make_view(sl_at(l), smem, rank, cluster);
+    w.tab = stab + (size_t)P->tab_row[l] * 12;
+    w.col = col_at(l);
+    return w;
+  };
 
   // ---- down leg over the cluster levels ----
   int l = lt;
-  for (; l < lc && E->lev[l].cluster; ++l) {
-    stage(&sl[0], &E->lev[l]);
-    stage(&sl[1], &E->lev[l + 1]);
-    const EngLevel<T>& L = sl[0];
-    const EngLevel<T>& Lc = sl[1];
-    View<T> w = make_view(L, smem, rank, true);
-    stage_tables(L, w.z0, w.z1, tabs[0], scol[0]);
-    w.tab = tabs[0];
-    w.col = scol[0];
+  for (; l < lc && sl_at(l).cluster; ++l) {
+    const EngLevel<T>& L = sl_at(l);
+    const EngLevel<T>& Lc = sl_at(l + 1);
+    View<T> w = view_of(l, true);
     zero_local(w);
     // b of the owned planes in shared memory when the plan has room for it
     const bool bl = L.sb >= 0;
@@ -477,19 +508,13 @@ __global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const
   const int lsingle = l;   // first level held by CTA 0 alone
   if (rank == 0) {
     // ---- single-CTA part: levels lsingle .. lc and back ----
-    stage(&sl[0], &E->lev[lsingle]);
     {
-      View<T> w = make_view(sl[0], smem, 0, false);
-      load_all(w, sl[0].gb, (T*)(smem + sl[0].sb));
+      View<T> w = view_of(lsingle, false);
+      load_all(w, sl_at(lsingle).gb, (T*)(smem + sl_at(lsingle).sb));
     }
     for (int k = lsingle; k <= lc; ++k) {
-      stage(&sl[0], &E->lev[k]);
-      if (k < lc) stage(&sl[1], &E->lev[k + 1]);
-      const EngLevel<T>& L = sl[0];
-      View<T> w = make_view(L, smem, 0, false);
-      stage_tables(L, 0, L.nz, tabs[0], scol[0]);
-      w.tab = tabs[0];
-      w.col = scol[0];
+      const EngLevel<T>& L = sl_at(k);
+      View<T> w = view_of(k, false);
       T* b = (T*)(smem + L.sb);
       zero_local(w);
       __syncthreads();
@@ -503,42 +528,31 @@ __global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const
         sweeps<T, NOISE>(w, k, mu1, mu2, b, true, 0, key, cyc, 0, 1, false);
         break;
       }
-      const EngLevel<T>& Lc = sl[1];
+      const EngLevel<T>& Lc = sl_at(k + 1);
       residual(w, b, true, 0, (T*)(smem + L.st));
       __syncthreads();
       restrict_to(L, Lc, (const T*)(smem + L.st), true, (T*)(smem + Lc.sb), 0, Lc.nz);
       __syncthreads();
     }
     for (int k = lc - 1; k >= lsingle; --k) {
-      stage(&sl[0], &E->lev[k]);
-      stage(&sl[1], &E->lev[k + 1]);
-      const EngLevel<T>& L = sl[0];
-      const EngLevel<T>& Lc = sl[1];
-      View<T> w = make_view(L, smem, 0, false);
-      stage_tables(L, 0, L.nz, tabs[0], scol[0]);
-      w.tab = tabs[0];
-      w.col = scol[0];
+      const EngLevel<T>& L = sl_at(k);
+      const EngLevel<T>& Lc = sl_at(k + 1);
+      View<T> w = view_of(k, false);
       prolong_into(w, Lc, (const T*)(smem + Lc.sv), true, 0);
       __syncthreads();
       sweeps<T, NOISE>(w, k, mu1, mu2, (const T*)(smem + L.sb), true, 0, key, cyc, 0, 1, false);
     }
-    stage(&sl[0], &E->lev[lsingle]);
     {
-      View<T> w = make_view(sl[0], smem, 0, false);
-      store_owned(w, sl[0].gv);
+      View<T> w = view_of(lsingle, false);
+      store_owned(w, sl_at(lsingle).gv);
     }
   }
   cl.sync();
   // ---- up leg over the cluster levels ----
   for (int k = lsingle - 1; k >= lt; --k) {
-    stage(&sl[0], &E->lev[k]);
-    stage(&sl[1], &E->lev[k + 1]);
-    const EngLevel<T>& L = sl[0];
-    const EngLevel<T>& Lc = sl[1];
-    View<T> w = make_view(L, smem, rank, true);
-    stage_tables(L, w.z0, w.z1, tabs[0], scol[0]);
-    w.tab = tabs[0];
-    w.col = scol[0];
+    const EngLevel<T>& L = sl_at(k);
+    const EngLevel<T>& Lc = sl_at(k + 1);
+    View<T> w = view_of(k, true);
     prolong_into(w, Lc, Lc.gv, false, 0);
     cl.sync();
     const bool bl = L.sb >= 0;   // staged on the way down, untouched since
@@ -633,14 +647,20 @@ bool try_plan(const LevelDev* levs, int L, int l0, int C, bool stage_b, size_t s
     off = align16(off + Nc * sizeof(double));
     need_max = need_max > off ? need_max : off;
   }
-  int nzmax = 0;
-  for (int c = 0; c < ncomp; ++c)
-    for (int l = l0; l < L; ++l) nzmax = nzmax > levs[l].c[c].nz ? nzmax : levs[l].c[c].nz;
-  const size_t slot = align16((size_t)nzmax * 12 * sizeof(T));
+  // row tables of every level (components share the layout: the largest nz)
+  int rows = 0;
+  for (int l = l0; l < L; ++l) {
+    p.tab_row[l] = rows;
+    int nzl = 0;
+    for (int c = 0; c < ncomp; ++c) nzl = nzl > levs[l].c[c].nz ? nzl : levs[l].c[c].nz;
+    rows += nzl;
+  }
   for (int c = 0; c < ncomp; ++c)
     for (int l = l0; l < L; ++l)
       if (levs[l].c[c].ncol > kEngMaxColours) return false;
-  if (need_max + 2 * sizeof(EngLevel<T>) + 2 * kEngMaxColours * sizeof(EngColour) > smem_cap) return false;
+  const size_t staged = (size_t)rows * 12 * sizeof(T) + (size_t)(L - l0) * sizeof(EngLevel<T>) +
+                        (size_t)(L - l0) * kEngMaxColours * sizeof(EngColour) + 64;
+  if (need_max + staged > smem_cap) return false;
   if (!any_cluster) C = 1;
   // every component gets the same y offset (the maximum) so that the kernel
   // can use one field
@@ -654,11 +674,13 @@ bool try_plan(const LevelDev* levs, int L, int l0, int C, bool stage_b, size_t s
     ymax = ymax > Nc ? ymax : Nc;
   }
   const size_t tab_off = align16(yo + ymax * sizeof(double));
+  const size_t lev_off = align16(tab_off + (size_t)rows * 12 * sizeof(T));
+  const size_t col_off = align16(lev_off + (size_t)(L - l0) * sizeof(EngLevel<T>));
   p.tab_off = (int)tab_off;
-  p.tab_slot = (int)slot;
-  out->smem_bytes = tab_off + 2 * slot;
-  const size_t static_bytes = 2 * sizeof(EngLevel<T>) + 2 * kEngMaxColours * sizeof(EngColour);
-  if (out->smem_bytes + static_bytes > smem_cap) return false;
+  p.lev_off = (int)lev_off;
+  p.col_off = (int)col_off;
+  out->smem_bytes = align16(col_off + (size_t)(L - l0) * kEngMaxColours * sizeof(EngColour));
+  if (out->smem_bytes > smem_cap) return false;
   out->cluster = C;
   return true;
 }

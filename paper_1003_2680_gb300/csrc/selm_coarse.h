@@ -60,8 +60,13 @@ template <typename T>
 struct EngParams {
   int l0, L, ncomp;
   int y_off;          // shared-memory byte offset of the FP64 coarsest scratch
-  int tab_off;        // shared-memory byte offset of the two level-table slots
-  int tab_slot;       // bytes per slot: nz_max rows of (10 bands + inverse diagonal + noise scale) values
+  // Staged once per launch in shared memory, for every level l0..L-1: the
+  // level descriptors (lev_off, one EngLevel per level), the colour classes
+  // as this CTA sees them (col_off, kEngMaxColours per level) and the row
+  // tables (tab_off + tab_row[l] rows of 12 values: 10 z bands, inverse
+  // diagonal, noise scale).
+  int lev_off, col_off, tab_off;
+  int tab_row[kMaxLevels];
   EngComp<T> comp[kMaxComps];
 };
 

@@ -264,78 +264,6 @@ struct RowPass {
   int rstart[kMaxComps + 1];   // first row of each component (rows = ny * nz)
 };
 
-template <typename T, bool NOISE>
-__global__ void __launch_bounds__(kBlock) k_fine_colour_v8(LevelDev L, RowPass rp, T* __restrict__ v,
-                                                          const T* __restrict__ b, int colour, int sweep, Key key,
-                                                          const unsigned long long* __restrict__ cyc) {
-  const int segs = L.c[0].nx >> 3;   // every component has the same nx
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int row_all = gt / segs;
-  if (row_all >= rp.rstart[L.ncomp]) return;
-  const int seg = gt - row_all * segs;
-  int ci = 0;
-  while (ci + 1 < L.ncomp && row_all >= rp.rstart[ci + 1]) ++ci;
-  const CompDev& c = L.c[ci];
-  const int row = row_all - rp.rstart[ci];
-  const int j = row % c.ny, k = row / c.ny;
-  const int nx = c.nx;
-  const long long plane = (long long)nx * c.ny;
-  const long long rbase = c.off + (long long)row * nx;
-  const int x0 = seg << 3;
-  T cen[8], bb[8], acc[8];
-  Vec<T>::load8(v + rbase + x0, cen);
-  Vec<T>::load8(b + rbase + x0, bb);
-  const T left = v[rbase + (x0 == 0 ? nx - 1 : x0 - 1)];
-  const T right = v[rbase + (x0 + 8 == nx ? 0 : x0 + 8)];
-  const int p = (j + k + colour) & 1;
-#pragma unroll
-  for (int e = 0; e < 8; ++e) acc[e] = (T)0;
-  if (c.ny > 1) {
-    T t[8];
-    const long long ym = c.off + ((long long)k * c.ny + (j == 0 ? c.ny - 1 : j - 1)) * nx + x0;
-    const long long yp = c.off + ((long long)k * c.ny + (j == c.ny - 1 ? 0 : j + 1)) * nx + x0;
-    Vec<T>::load8(v + ym, t);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) acc[e] += t[e];
-    Vec<T>::load8(v + yp, t);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) acc[e] += t[e];
-  }
-  if (k > 0) {
-    T t[8];
-    Vec<T>::load8(v + rbase - plane + x0, t);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) acc[e] += t[e];
-  }
-  if (k < c.nz - 1) {
-    T t[8];
-    Vec<T>::load8(v + rbase + plane + x0, t);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) acc[e] += t[e];
-  }
-  T n4[4] = {(T)0, (T)0, (T)0, (T)0};
-  if (NOISE) {
-    const unsigned long long cy = *cyc;
-    const uint32_t grp = (uint32_t)row * (uint32_t)(nx >> 3) + (uint32_t)seg;
-    Normals<T>::get(philox10(make_uint4(grp, ctr1_of(L.level, c.comp_id, colour, sweep, 0), (uint32_t)cy,
-                                        (uint32_t)(cy >> 32)),
-                             key.k0, key.k1),
-                    n4);
-  }
-  const int edges = (k == 0) + (k == c.nz - 1);
-  T dz = (T)2;
-  if (c.zkind == kAxisCellDir) dz += (T)edges;
-  if (c.zkind == kAxisCellNeu) dz -= (T)edges;
-  const T s = (T)c.s;
-  const T diag = s * ((c.ny > 1 ? (T)4 : (T)2) + dz);
-  const T rsd = NOISE ? (T)1 / tsqrt(diag) : (T)0;
-  if (p == 0)
-    fine_update8<T, NOISE, 0>(cen, bb, acc, left, right, n4, s, diag, rsd);
-  else
-    fine_update8<T, NOISE, 1>(cen, bb, acc, left, right, n4, s, diag, rsd);
-  Vec<T>::store8(v + rbase + x0, cen);
-}
-
 // FP64 outer residual, vectorised over 4 consecutive x positions (nx % 4 == 0).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_outer_residual_v4(LevelDev L, RowPass rp, const double* __restrict__ z,
@@ -656,6 +584,97 @@ __global__ void __launch_bounds__(kBlock) k_band7_rb_zm(LevelDev L, ColumnPass c
         cur[e] = nv;
       }
     }
+    Vec<T>::store8(v + base + kp, cur);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      prev[e] = cur[e];
+      cur[e] = nxt[e];
+    }
+  }
+}
+
+// Level-0 red-black colour pass marching along z: one thread per (component,
+// y row, 8-wide x segment, chunk of kc z rows); one Philox block per segment
+// and row gives the normals of its four sites of the colour.  Row k's z
+// neighbours come from registers (row k-1 after this thread's update of it:
+// its sites of the other colour, the ones row k reads, are not written by the
+// pass) and the next row's loads are issued before the current row is
+// computed.
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kBlock) k_fine_colour_zm(LevelDev L, ColumnPass cp, T* __restrict__ v,
+                                                          const T* __restrict__ b, int colour, int sweep, Key key,
+                                                          const unsigned long long* __restrict__ cyc) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cp.start[L.ncomp]) return;
+  int ci = 0;
+  while (ci + 1 < L.ncomp && g >= cp.start[ci + 1]) ++ci;
+  const CompDev& c = L.c[ci];
+  const int nx = c.nx, ny = c.ny, nz = c.nz, segs = nx >> 3;
+  const long long item = g - cp.start[ci];
+  const long long col = item % ((long long)ny * segs);
+  const int chunk = (int)(item / ((long long)ny * segs));
+  const int j = (int)(col / segs), seg = (int)(col - (long long)j * segs);
+  const int k0 = chunk * cp.kc, k1 = min(k0 + cp.kc, nz);
+  const long long plane = (long long)nx * ny;
+  const int x0 = seg << 3;
+  const long long base = c.off + (long long)j * nx + x0;
+  const long long ym0 = c.off + (long long)(j == 0 ? ny - 1 : j - 1) * nx + x0;
+  const long long yp0 = c.off + (long long)(j == ny - 1 ? 0 : j + 1) * nx + x0;
+  const long long rowx = c.off + (long long)j * nx;
+  const int xl_i = x0 == 0 ? nx - 1 : x0 - 1, xr_i = x0 + 8 == nx ? 0 : x0 + 8;
+  const unsigned long long cy = NOISE ? *cyc : 0ull;
+  const uint32_t c1 = ctr1_of(L.level, c.comp_id, colour, sweep, 0);
+  const T s = (T)c.s;
+  T prev[8], cur[8], nxt[8], bb[8], ty[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) prev[e] = (T)0;
+  if (k0 > 0) Vec<T>::load8(v + base + (long long)(k0 - 1) * plane, prev);
+  Vec<T>::load8(v + base + (long long)k0 * plane, cur);
+  for (int k = k0; k < k1; ++k) {
+    const long long kp = (long long)k * plane;
+    if (k + 1 < nz)
+      Vec<T>::load8(v + base + kp + plane, nxt);
+    else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) nxt[e] = (T)0;
+    }
+    Vec<T>::load8(b + base + kp, bb);
+    // neighbour sums: y-, y+, z-, z+
+    T acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] = (T)0;
+    if (ny > 1) {
+      Vec<T>::load8(v + ym0 + kp, ty);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] += ty[e];
+      Vec<T>::load8(v + yp0 + kp, ty);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] += ty[e];
+    }
+    if (k > 0) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] += prev[e];
+    }
+    if (k + 1 < nz) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] += nxt[e];
+    }
+    const T left = v[rowx + kp + xl_i], right = v[rowx + kp + xr_i];
+    T n4[4] = {(T)0, (T)0, (T)0, (T)0};
+    if (NOISE) {
+      const uint32_t grp = (uint32_t)((long long)k * ny + j) * (uint32_t)segs + (uint32_t)seg;
+      Normals<T>::get(philox10(make_uint4(grp, c1, (uint32_t)cy, (uint32_t)(cy >> 32)), key.k0, key.k1), n4);
+    }
+    const int edges = (k == 0) + (k == nz - 1);
+    T dz = (T)2;
+    if (c.zkind == kAxisCellDir) dz += (T)edges;
+    if (c.zkind == kAxisCellNeu) dz -= (T)edges;
+    const T diag = s * ((ny > 1 ? (T)4 : (T)2) + dz);
+    const T rsd = NOISE ? (T)1 / tsqrt(diag) : (T)0;
+    if (((j + k + colour) & 1) == 0)
+      fine_update8<T, NOISE, 0>(cur, bb, acc, left, right, n4, s, diag, rsd);
+    else
+      fine_update8<T, NOISE, 1>(cur, bb, acc, left, right, n4, s, diag, rsd);
     Vec<T>::store8(v + base + kp, cur);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -1647,20 +1666,29 @@ template <typename T>
 cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool noise, Key key,
                           const unsigned long long* cyc, cudaStream_t st) {
   if (L.level == 0 && L.c[0].nx % 8 == 0) {
-    RowPass rp{};
-    int rows = 0;
+    // march along z in chunks of kc rows; kc halves (down to 4) while fewer
+    // than 96K threads would run
+    ColumnPass cp{};
+    long long cols = 0;
+    int nzmax = 0;
     for (int ci = 0; ci < L.ncomp; ++ci) {
-      rp.rstart[ci] = rows;
-      rows += L.c[ci].ny * L.c[ci].nz;
+      cols += (long long)L.c[ci].ny * (L.c[ci].nx >> 3);
+      nzmax = nzmax > L.c[ci].nz ? nzmax : L.c[ci].nz;
     }
-    rp.rstart[L.ncomp] = rows;
-    const long long nt = (long long)rows * (L.c[0].nx >> 3);
+    cp.kc = 16;
+    while (cp.kc > 4 && cols * ((nzmax + cp.kc - 1) / cp.kc) < 96 * 1024) cp.kc /= 2;
+    long long items = 0;
+    for (int ci = 0; ci < L.ncomp; ++ci) {
+      cp.start[ci] = items;
+      items += (long long)L.c[ci].ny * (L.c[ci].nx >> 3) * ((L.c[ci].nz + cp.kc - 1) / cp.kc);
+    }
+    cp.start[L.ncomp] = items;
     for (int colour = 0; colour < 2; ++colour) {
       prof::Scope ps(SELM_K_FINE_SWEEP, st);
       if (noise)
-        k_fine_colour_v8<T, true><<<grid_for(nt), kBlock, 0, st>>>(L, rp, v, b, colour, sweep, key, cyc);
+        k_fine_colour_zm<T, true><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
       else
-        k_fine_colour_v8<T, false><<<grid_for(nt), kBlock, 0, st>>>(L, rp, v, b, colour, sweep, key, cyc);
+        k_fine_colour_zm<T, false><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
     }
     return cudaGetLastError();
   }

@@ -684,6 +684,81 @@ __global__ void __launch_bounds__(kBlock) k_fine_colour_zm(LevelDev L, ColumnPas
   }
 }
 
+// t = b - A v on level 0, marching along z like k_fine_colour_zm (every site
+// of a segment): fine_row's sum order (x-, x+, y-, y+, z-, z+) and
+// t = b - (-s sum + diag v).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_fine_residual_zm(LevelDev L, ColumnPass cp, const T* __restrict__ v,
+                                                            const T* __restrict__ b, T* __restrict__ t) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cp.start[L.ncomp]) return;
+  int ci = 0;
+  while (ci + 1 < L.ncomp && g >= cp.start[ci + 1]) ++ci;
+  const CompDev& c = L.c[ci];
+  const int nx = c.nx, ny = c.ny, nz = c.nz, segs = nx >> 3;
+  const long long item = g - cp.start[ci];
+  const long long col = item % ((long long)ny * segs);
+  const int chunk = (int)(item / ((long long)ny * segs));
+  const int j = (int)(col / segs), seg = (int)(col - (long long)j * segs);
+  const int k0 = chunk * cp.kc, k1 = min(k0 + cp.kc, nz);
+  const long long plane = (long long)nx * ny;
+  const int x0 = seg << 3;
+  const long long base = c.off + (long long)j * nx + x0;
+  const long long ym0 = c.off + (long long)(j == 0 ? ny - 1 : j - 1) * nx + x0;
+  const long long yp0 = c.off + (long long)(j == ny - 1 ? 0 : j + 1) * nx + x0;
+  const long long rowx = c.off + (long long)j * nx;
+  const int xl_i = x0 == 0 ? nx - 1 : x0 - 1, xr_i = x0 + 8 == nx ? 0 : x0 + 8;
+  const T s = (T)c.s;
+  T prev[8], cur[8], nxt[8], bb[8], ty[8], sum[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) prev[e] = (T)0;
+  if (k0 > 0) Vec<T>::load8(v + base + (long long)(k0 - 1) * plane, prev);
+  Vec<T>::load8(v + base + (long long)k0 * plane, cur);
+  for (int k = k0; k < k1; ++k) {
+    const long long kp = (long long)k * plane;
+    if (k + 1 < nz)
+      Vec<T>::load8(v + base + kp + plane, nxt);
+    else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) nxt[e] = (T)0;
+    }
+    Vec<T>::load8(b + base + kp, bb);
+    const T left = v[rowx + kp + xl_i], right = v[rowx + kp + xr_i];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sum[e] = (e == 0 ? left : cur[e - 1]) + (e == 7 ? right : cur[e + 1]);
+    if (ny > 1) {
+      Vec<T>::load8(v + ym0 + kp, ty);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) sum[e] += ty[e];
+      Vec<T>::load8(v + yp0 + kp, ty);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) sum[e] += ty[e];
+    }
+    if (k > 0) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) sum[e] += prev[e];
+    }
+    if (k + 1 < nz) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) sum[e] += nxt[e];
+    }
+    const int edges = (k == 0) + (k == nz - 1);
+    T dz = (T)2;
+    if (c.zkind == kAxisCellDir) dz += (T)edges;
+    if (c.zkind == kAxisCellNeu) dz -= (T)edges;
+    const T diag = s * ((ny > 1 ? (T)4 : (T)2) + dz);
+    T out[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) out[e] = bb[e] - (-s * sum[e] + diag * cur[e]);
+    Vec<T>::store8(t + base + kp, out);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      prev[e] = cur[e];
+      cur[e] = nxt[e];
+    }
+  }
+}
+
 // t = b - A v on a banded 7-point level, marching along z like
 // k_band7_rb_zm (every site of a segment, no colour).
 template <typename T>
@@ -883,6 +958,59 @@ __global__ void __launch_bounds__(kBlock) k_restrict(LevelDev Lf, LevelDev Lc, c
                                                     T* __restrict__ bc) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s < Lc.size) restrict_at<T, LdPlain>(Lf, Lc, t, bc, s);
+}
+
+// restrict_at for four consecutive coarse x sites per thread (fine nx % 8 ==
+// 0, the same nx in every component): each contributing fine row is read as
+// one 8-wide vector (fine x 2I0 .. 2I0+7) and its left neighbour; the terms are
+// added in restrict_at's order.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_restrict_v4(LevelDev Lf, LevelDev Lc, RowPass rp, const T* __restrict__ t,
+                                                       T* __restrict__ bc) {
+  const int segs = Lc.c[0].nx >> 2;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row_all = gt / segs;
+  if (row_all >= rp.rstart[Lc.ncomp]) return;
+  const int seg = gt - row_all * segs;
+  int ci = 0;
+  while (ci + 1 < Lc.ncomp && row_all >= rp.rstart[ci + 1]) ++ci;
+  const CompDev& f = Lf.c[ci];
+  const CompDev& c = Lc.c[ci];
+  const int row = row_all - rp.rstart[ci];
+  const int J = row % c.ny, K = row / c.ny;
+  const int I0 = seg << 2, xf0 = 2 * I0;
+  const long long plane = (long long)f.nx * f.ny;
+  T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+  for (int qz = 0; qz < 4; ++qz) {
+    const int kf = f.rz_idx[K * 4 + qz];
+    if (kf < 0) continue;
+    const T wz = rz_w<T>(f, K * 4 + qz);
+    for (int qy = -1; qy <= 1; ++qy) {
+      T wy;
+      int jf;
+      if (f.ny == 1) {
+        if (qy != 0) continue;
+        wy = (T)1;
+        jf = 0;
+      } else {
+        wy = qy == 0 ? (T)1 : (T)0.5;
+        jf = wrapi(2 * J + qy, f.ny);
+      }
+      const long long rowb = f.off + (long long)kf * plane + (long long)jf * f.nx;
+      T r[8];
+      Vec<T>::load8(t + rowb + xf0, r);
+      const T lft = t[rowb + wrapi(xf0 - 1, f.nx)];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        acc[e] += wz * wy * (T)0.5 * (e == 0 ? lft : r[2 * e - 1]);
+        acc[e] += wz * wy * (T)1 * r[2 * e];
+        acc[e] += wz * wy * (T)0.5 * r[2 * e + 1];
+      }
+    }
+  }
+  T* out = bc + c.off + ((long long)K * c.ny + J) * c.nx + I0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) out[e] = acc[e];
 }
 
 // v_f += P v_c: periodic axes: even fine node = coarse node, odd = mean of two.
@@ -1662,27 +1790,32 @@ int coop_blocks() {
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Column items of the level-0 z-marching kernels (nx % 8 == 0): chunks of kc
+// z rows, kc halving (down to 4) while fewer than 96K threads would run.
+long long fine_column_pass(const LevelDev& L, ColumnPass* cp) {
+  long long cols = 0;
+  int nzmax = 0;
+  for (int ci = 0; ci < L.ncomp; ++ci) {
+    cols += (long long)L.c[ci].ny * (L.c[ci].nx >> 3);
+    nzmax = nzmax > L.c[ci].nz ? nzmax : L.c[ci].nz;
+  }
+  cp->kc = 16;
+  while (cp->kc > 4 && cols * ((nzmax + cp->kc - 1) / cp->kc) < 96 * 1024) cp->kc /= 2;
+  long long items = 0;
+  for (int ci = 0; ci < L.ncomp; ++ci) {
+    cp->start[ci] = items;
+    items += (long long)L.c[ci].ny * (L.c[ci].nx >> 3) * ((L.c[ci].nz + cp->kc - 1) / cp->kc);
+  }
+  cp->start[L.ncomp] = items;
+  return items;
+}
+
 template <typename T>
 cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool noise, Key key,
                           const unsigned long long* cyc, cudaStream_t st) {
   if (L.level == 0 && L.c[0].nx % 8 == 0) {
-    // march along z in chunks of kc rows; kc halves (down to 4) while fewer
-    // than 96K threads would run
     ColumnPass cp{};
-    long long cols = 0;
-    int nzmax = 0;
-    for (int ci = 0; ci < L.ncomp; ++ci) {
-      cols += (long long)L.c[ci].ny * (L.c[ci].nx >> 3);
-      nzmax = nzmax > L.c[ci].nz ? nzmax : L.c[ci].nz;
-    }
-    cp.kc = 16;
-    while (cp.kc > 4 && cols * ((nzmax + cp.kc - 1) / cp.kc) < 96 * 1024) cp.kc /= 2;
-    long long items = 0;
-    for (int ci = 0; ci < L.ncomp; ++ci) {
-      cp.start[ci] = items;
-      items += (long long)L.c[ci].ny * (L.c[ci].nx >> 3) * ((L.c[ci].nz + cp.kc - 1) / cp.kc);
-    }
-    cp.start[L.ncomp] = items;
+    const long long items = fine_column_pass(L, &cp);
     for (int colour = 0; colour < 2; ++colour) {
       prof::Scope ps(SELM_K_FINE_SWEEP, st);
       if (noise)
@@ -1765,6 +1898,12 @@ cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool n
 template <typename T>
 cudaError_t launch_residual(const LevelDev& L, const T* v, const T* b, T* t, cudaStream_t st) {
   prof::Scope ps(SELM_K_RESIDUAL, st);
+  if (L.level == 0 && L.c[0].nx % 8 == 0) {
+    ColumnPass cp{};
+    const long long items = fine_column_pass(L, &cp);
+    k_fine_residual_zm<T><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, t);
+    return cudaGetLastError();
+  }
   if (L.rb && L.c[0].nx % 8 == 0) {
     ColumnPass cp{};
     cp.kc = 16;
@@ -1784,6 +1923,20 @@ cudaError_t launch_residual(const LevelDev& L, const T* v, const T* b, T* t, cud
 template <typename T>
 cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* t, T* bc, cudaStream_t st) {
   prof::Scope ps(SELM_K_RESTRICT, st);
+  bool v4 = Lf.c[0].nx % 8 == 0;
+  for (int ci = 0; ci < Lf.ncomp; ++ci)
+    if (Lf.c[ci].nx != Lf.c[0].nx || Lc.c[ci].nx * 2 != Lf.c[ci].nx) v4 = false;
+  if (v4) {
+    RowPass rp{};
+    int rows = 0;
+    for (int ci = 0; ci < Lc.ncomp; ++ci) {
+      rp.rstart[ci] = rows;
+      rows += Lc.c[ci].ny * Lc.c[ci].nz;
+    }
+    rp.rstart[Lc.ncomp] = rows;
+    k_restrict_v4<T><<<grid_for((long long)rows * (Lc.c[0].nx >> 2)), kBlock, 0, st>>>(Lf, Lc, rp, t, bc);
+    return cudaGetLastError();
+  }
   k_restrict<T><<<grid_for(Lc.size), kBlock, 0, st>>>(Lf, Lc, t, bc);
   return cudaGetLastError();
 }

@@ -57,6 +57,26 @@ __device__ __forceinline__ T ld_cg(const T* p) {
 // the sites of a colour class (x modulus 2) are consecutive words.
 __device__ __forceinline__ int xpos(int i, int half) { return (i & 1) ? half + (i >> 1) : (i >> 1); }
 
+// q = (kr * ny + j) * nx + i  ->  i, j, kr (shifts when nx, ny are powers of two).
+template <typename T>
+__device__ __forceinline__ void split_xy(const EngLevel<T>& L, int q, int* i, int* j, int* kr) {
+  int r;
+  if (L.lx >= 0) {
+    *i = q & (L.nx - 1);
+    r = q >> L.lx;
+  } else {
+    *i = q % L.nx;
+    r = q / L.nx;
+  }
+  if (L.ly >= 0) {
+    *j = r & (L.ny - 1);
+    *kr = r >> L.ly;
+  } else {
+    *j = r % L.ny;
+    *kr = r / L.ny;
+  }
+}
+
 // Per-CTA view of one level.
 template <typename T>
 struct View {
@@ -227,13 +247,23 @@ template <typename T>
 __device__ void residual(const View<T>& w, const T* b, bool b_local, int boff, T* t) {
   const EngLevel<T>& L = *w.L;
   const int n = (w.z1 - w.z0) * w.plane;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    const int i = q % L.nx;
-    const int r = q / L.nx;
-    const int j = r % L.ny, k = w.z0 + r / L.ny;
-    const int gidx = (k * L.ny + j) * L.nx + i;
-    const T bb = b_local ? b[gidx - boff] : ld_cg(b + gidx);
-    t[gidx] = bb - stencil_row<T, true>(w, i, j, k);
+  // two sites per iteration, both computed before either is stored, so that
+  // their loads overlap
+  auto value = [&](int q, int* gidx) {
+    int i, j, k;
+    split_xy(L, q, &i, &j, &k);
+    k += w.z0;
+    *gidx = (k * L.ny + j) * L.nx + i;
+    const T bb = b_local ? b[*gidx - boff] : ld_cg(b + *gidx);
+    return bb - stencil_row<T, true>(w, i, j, k);
+  };
+  for (int q = threadIdx.x; q < n; q += 2 * blockDim.x) {
+    const int q2 = q + blockDim.x;
+    int g1 = 0, g2 = 0;
+    const T r1 = value(q, &g1);
+    const T r2 = q2 < n ? value(q2, &g2) : (T)0;
+    t[g1] = r1;
+    if (q2 < n) t[g2] = r2;
   }
 }
 
@@ -243,14 +273,16 @@ __device__ void restrict_to(const EngLevel<T>& Lf, const EngLevel<T>& Lc, const 
                             int Z1) {
   const int n = (Z1 - Z0) * Lc.nx * Lc.ny;
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    const int I = q % Lc.nx;
-    const int r = q / Lc.nx;
-    const int J = r % Lc.ny, K = Z0 + r / Lc.ny;
+    int I, J, K;
+    split_xy(Lc, q, &I, &J, &K);
+    K += Z0;
     T acc = (T)0;
+#pragma unroll
     for (int qz = 0; qz < 4; ++qz) {
-      const int kf = __ldg(Lf.rz_idx + K * 4 + qz);
-      if (kf < 0) continue;
-      const T wz = __ldg(Lf.rz_w + K * 4 + qz);
+      // an unused tap (index -1) reads row 0 with weight 0: no branch between taps
+      const int kr = Lf.rz_idx[K * 4 + qz];
+      const int kf = kr < 0 ? 0 : kr;
+      const T wz = kr < 0 ? (T)0 : Lf.rz_w[K * 4 + qz];
       for (int qy = -1; qy <= 1; ++qy) {
         T wy;
         int jf;
@@ -281,9 +313,9 @@ __device__ void prolong_into(const View<T>& w, const EngLevel<T>& Lc, const T* v
   const int p0 = max(0, w.z0 - 2), p1 = min(L.nz, w.z1 + 2);
   const int n = (p1 - p0) * w.plane;
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    const int i = q % L.nx;
-    const int r = q / L.nx;
-    const int j = r % L.ny, k = p0 + r / L.ny;
+    int i, j, k;
+    split_xy(L, q, &i, &j, &k);
+    k += p0;
     int xi0 = i >> 1, xi1 = xi0;
     T xw0 = (T)1, xw1 = (T)0;
     if (i & 1) {
@@ -300,10 +332,11 @@ __device__ void prolong_into(const View<T>& w, const EngLevel<T>& Lc, const T* v
       }
     }
     T acc = (T)0;
+#pragma unroll
     for (int qz = 0; qz < 2; ++qz) {
-      const int kc = __ldg(L.pz_idx + k * 2 + qz);
-      if (kc < 0) continue;
-      const T wz = __ldg(L.pz_w + k * 2 + qz);
+      const int kr = L.pz_idx[k * 2 + qz];
+      const int kc = kr < 0 ? 0 : kr;
+      const T wz = kr < 0 ? (T)0 : L.pz_w[k * 2 + qz];
       const int yi[2] = {yi0, yi1}, xi[2] = {xi0, xi1};
       const T yw[2] = {yw0, yw1}, xw[2] = {xw0, xw1};
       for (int a = 0; a < 2; ++a) {
@@ -326,9 +359,9 @@ __device__ void store_owned(const View<T>& w, T* g) {
   const int n = (w.z1 - w.z0) * w.plane;
   const int base = w.z0 * w.plane;
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    const int i = q % L.nx;
-    const int r = q / L.nx;
-    g[base + q] = w.v[w.loc(i, r % L.ny, w.z0 + r / L.ny)];
+    int i, j, k;
+    split_xy(L, q, &i, &j, &k);
+    g[base + q] = w.v[w.loc(i, j, w.z0 + k)];
   }
 }
 
@@ -471,7 +504,30 @@ __global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const
       const EngLevel<T>& L = sl_at(l);
       const View<T> w = make_view(L, smem, rank, L.cluster != 0);
       stage_tables(L, w.z0, w.z1, stab + (size_t)P->tab_row[l] * 12, col_at(l));
+      if (l < lc) {   // transfer tables to and from level l + 1
+        int* xi = reinterpret_cast<int*>(smem + P->xfi_off) + P->xf_row[l];
+        T* xw = reinterpret_cast<T*>(smem + P->xfw_off) + P->xf_row[l];
+        for (int q = threadIdx.x; q < 2 * L.nz; q += blockDim.x) {
+          xi[q] = L.pz_idx[q];
+          xw[q] = L.pz_w[q];
+        }
+        for (int q = threadIdx.x; q < 4 * sl_at(l + 1).nz; q += blockDim.x) {
+          xi[2 * L.nz + q] = L.rz_idx[q];
+          xw[2 * L.nz + q] = L.rz_w[q];
+        }
+      }
     }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int l = lt; l < lc; ++l) {
+        EngLevel<T>& L = sl_at(l);
+        int* xi = reinterpret_cast<int*>(smem + P->xfi_off) + P->xf_row[l];
+        T* xw = reinterpret_cast<T*>(smem + P->xfw_off) + P->xf_row[l];
+        L.pz_idx = xi;
+        L.pz_w = xw;
+        L.rz_idx = xi + 2 * L.nz;
+        L.rz_w = xw + 2 * L.nz;
+      }
     __syncthreads();
   }
   auto view_of = [&](int l, bool cluster) {
@@ -502,13 +558,15 @@ __global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const
     const int Pc = (Lc.nz + csize - 1) / csize;
     const int Z0 = min(rank * Pc, Lc.nz);
     const int Z1 = min(Z0 + Pc, Lc.nz);
-    restrict_to(L, Lc, L.gt, false, Lc.gb, Z0, Z1);
+    // into the first level held by CTA 0: its shared b, through distributed shared memory
+    T* bdst = Lc.cluster ? Lc.gb : cl.map_shared_rank(reinterpret_cast<T*>(smem + Lc.sb), 0);
+    restrict_to(L, Lc, L.gt, false, bdst, Z0, Z1);
     cl.sync();
   }
   const int lsingle = l;   // first level held by CTA 0 alone
   if (rank == 0) {
     // ---- single-CTA part: levels lsingle .. lc and back ----
-    {
+    if (lsingle == lt) {   // b from global only when no cluster level restricted into it
       View<T> w = view_of(lsingle, false);
       load_all(w, sl_at(lsingle).gb, (T*)(smem + sl_at(lsingle).sb));
     }
@@ -542,7 +600,7 @@ __global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const
       __syncthreads();
       sweeps<T, NOISE>(w, k, mu1, mu2, (const T*)(smem + L.sb), true, 0, key, cyc, 0, 1, false);
     }
-    {
+    {   // the engine's result, or the hand-off to the cluster's prolongation
       View<T> w = view_of(lsingle, false);
       store_owned(w, sl_at(lsingle).gv);
     }
@@ -658,8 +716,21 @@ bool try_plan(const LevelDev* levs, int L, int l0, int C, bool stage_b, size_t s
   for (int c = 0; c < ncomp; ++c)
     for (int l = l0; l < L; ++l)
       if (levs[l].c[c].ncol > kEngMaxColours) return false;
+  // transfer tables of the levels with a coarser level below them
+  int xrows = 0;
+  for (int l = l0; l < L; ++l) {
+    p.xf_row[l] = xrows;
+    if (l == L - 1) continue;
+    int nzl = 0, nzc = 0;
+    for (int c = 0; c < ncomp; ++c) {
+      nzl = nzl > levs[l].c[c].nz ? nzl : levs[l].c[c].nz;
+      nzc = nzc > levs[l + 1].c[c].nz ? nzc : levs[l + 1].c[c].nz;
+    }
+    xrows += 2 * nzl + 4 * nzc;
+  }
   const size_t staged = (size_t)rows * 12 * sizeof(T) + (size_t)(L - l0) * sizeof(EngLevel<T>) +
-                        (size_t)(L - l0) * kEngMaxColours * sizeof(EngColour) + 64;
+                        (size_t)(L - l0) * kEngMaxColours * sizeof(EngColour) +
+                        (size_t)xrows * (sizeof(int) + sizeof(T)) + 96;
   if (need_max + staged > smem_cap) return false;
   if (!any_cluster) C = 1;
   // every component gets the same y offset (the maximum) so that the kernel
@@ -676,10 +747,14 @@ bool try_plan(const LevelDev* levs, int L, int l0, int C, bool stage_b, size_t s
   const size_t tab_off = align16(yo + ymax * sizeof(double));
   const size_t lev_off = align16(tab_off + (size_t)rows * 12 * sizeof(T));
   const size_t col_off = align16(lev_off + (size_t)(L - l0) * sizeof(EngLevel<T>));
+  const size_t xfi_off = align16(col_off + (size_t)(L - l0) * kEngMaxColours * sizeof(EngColour));
+  const size_t xfw_off = align16(xfi_off + (size_t)xrows * sizeof(int));
   p.tab_off = (int)tab_off;
   p.lev_off = (int)lev_off;
   p.col_off = (int)col_off;
-  out->smem_bytes = align16(col_off + (size_t)(L - l0) * kEngMaxColours * sizeof(EngColour));
+  p.xfi_off = (int)xfi_off;
+  p.xfw_off = (int)xfw_off;
+  out->smem_bytes = align16(xfw_off + (size_t)xrows * sizeof(T));
   if (out->smem_bytes > smem_cap) return false;
   out->cluster = C;
   return true;
@@ -709,6 +784,13 @@ void fill_engine_tables(const LevelDev* levs, int L, void* const* gb, void* cons
         e.w1[q] = (T)d.w1[q];
         e.w2[q] = (T)d.w2[q];
       }
+      auto log2_or = [](int n) {
+        int l = 0;
+        while ((1 << l) < n) ++l;
+        return (1 << l) == n ? l : -1;
+      };
+      e.lx = log2_or(d.nx);
+      e.ly = log2_or(d.ny);
       e.inv_nxc = 1.0f / (float)((d.nx + d.mx - 1) / d.mx);
       e.inv_nyc = 1.0f / (float)((d.ny + d.my - 1) / d.my);
       e.rz_idx = d.rz_idx;

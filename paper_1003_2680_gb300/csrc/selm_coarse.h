@@ -28,6 +28,7 @@ struct EngLevel {
   T w1[9];            // Kx (x) My + Mx (x) Ky at (dy, dx) = index (dy+1)*3 + dx+1
   T w2[9];            // Mx (x) My
   float inv_nxc, inv_nyc;  // reciprocals for the colour-class rank decode
+  int lx, ly;         // log2 of nx / ny when a power of two (index decode by shifts), else -1
   const int* rz_idx;  // restriction table to the next level
   const T* rz_w;
   const int* pz_idx;  // prolongation table from the next level
@@ -67,6 +68,12 @@ struct EngParams {
   // diagonal, noise scale).
   int lev_off, col_off, tab_off;
   int tab_row[kMaxLevels];
+  // Transfer tables of level l < L-1, staged at xf_row[l] in a parallel int
+  // array (xfi_off) and T array (xfw_off): prolongation from level l+1 by
+  // fine row k at [2k, 2k+2), then restriction to level l+1 by coarse row K
+  // at [2 nz_l + 4K, 2 nz_l + 4K + 4).
+  int xfi_off, xfw_off;
+  int xf_row[kMaxLevels];
   EngComp<T> comp[kMaxComps];
 };
 

@@ -265,7 +265,7 @@ struct RowPass {
 };
 
 // FP64 outer residual, vectorised over 4 consecutive x positions (nx % 4 == 0).
-template <typename T>
+template <typename T, bool NORM>
 __global__ void __launch_bounds__(kBlock) k_outer_residual_v4(LevelDev L, RowPass rp, const double* __restrict__ z,
                                                              const double* __restrict__ b, T* __restrict__ r,
                                                              double* __restrict__ norm2) {
@@ -312,6 +312,7 @@ __global__ void __launch_bounds__(kBlock) k_outer_residual_v4(LevelDev L, RowPas
     if (c.zkind == kAxisCellDir) dz += (double)edges;
     if (c.zkind == kAxisCellNeu) dz -= (double)edges;
     const double dg = (c.ny > 1 ? 4.0 : 2.0) + dz;
+    const double sdg = c.s * dg;
     double bv[4] = {0.0, 0.0, 0.0, 0.0};
     if (b) {
       const double2 a = *reinterpret_cast<const double2*>(b + rbase + x0);
@@ -321,14 +322,15 @@ __global__ void __launch_bounds__(kBlock) k_outer_residual_v4(LevelDev L, RowPas
     T out[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const double res = bv[e] - c.s * (dg * cen[e] - acc[e]);
+      // b - s (dg z - sum) as two FMAs: GB300's FP64 rate bounds this kernel
+      const double res = fma(c.s, acc[e], fma(-sdg, cen[e], bv[e]));
       out[e] = (T)res;
-      rr += res * res;
+      if (NORM) rr = fma(res, res, rr);
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) r[rbase + x0 + e] = out[e];
   }
-  if (norm2) {
+  if (NORM) {
     rr = block_sum(rr);
     if (threadIdx.x == 0) atomicAdd(norm2, rr);
   }
@@ -2054,7 +2056,10 @@ cudaError_t launch_outer_residual(const LevelDev& L0, const double* z, const dou
     }
     rp.rstart[L0.ncomp] = rows;
     const long long nt = (long long)rows * (L0.c[0].nx >> 2);
-    k_outer_residual_v4<T><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
+    if (norm2)
+      k_outer_residual_v4<T, true><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
+    else
+      k_outer_residual_v4<T, false><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
     return cudaGetLastError();
   }
   k_outer_residual<T><<<grid_for(L0.size), kBlock, 0, st>>>(L0, z, b, r, norm2);

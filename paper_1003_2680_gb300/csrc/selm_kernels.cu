@@ -447,6 +447,94 @@ __device__ __forceinline__ T sep_apply(const CompDev& c, const T* vc, int i, int
   return acc;
 }
 
+// t = b - A v on W consecutive x sites [x0, x0 + W) of row j, z rows
+// [k0, k1), of one component of a Galerkin level (vc, bc, tc: the
+// component's fields).  The x-y partial sums w1 * v and w2 * v of each plane
+// are computed once and kept in registers for the five rows that read it;
+// each row then combines them with its z bands.  Per row the arithmetic and
+// order are sep_apply<CENTRE = true>'s (a plane beyond a wall contributes 0).
+template <typename T, int W, typename LD>
+__device__ __forceinline__ void galerkin_residual_seg(const CompDev& c, const T* vc, const T* bc, T* tc, int j, int x0,
+                                                      int k0, int k1) {
+  const int nx = c.nx, ny = c.ny, nz = c.nz;
+  const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
+  const T* zbt = sizeof(T) == 4 ? (const T*)c.zb32 : (const T*)c.zb64;
+  T w1[9], w2[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    w1[q] = sep_w1<T>(c, q);
+    w2[q] = sep_w2<T>(c, q);
+  }
+  int xs[W + 2];
+#pragma unroll
+  for (int e = 0; e < W + 2; ++e) {
+    const int x = x0 - 1 + e;
+    xs[e] = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+  }
+  T P1[5][W], P2[5][W];
+  auto sums = [&](int kk, T* p1, T* p2) {
+    if (kk < 0 || kk >= nz) {
+#pragma unroll
+      for (int e = 0; e < W; ++e) p1[e] = p2[e] = (T)0;
+      return;
+    }
+    const T* vp = vc + (long long)kk * ny * nx;
+    if (ny == 1) {
+      T r[W + 2];
+#pragma unroll
+      for (int e = 0; e < W + 2; ++e) r[e] = LD::ld(vp + xs[e]);
+#pragma unroll
+      for (int e = 0; e < W; ++e) {
+        p1[e] = w1[3] * r[e] + w1[5] * r[e + 2];
+        p2[e] = w2[3] * r[e] + w2[5] * r[e + 2];
+        p1[e] += w1[4] * r[e + 1];
+        p2[e] += w2[4] * r[e + 1];
+      }
+      return;
+    }
+    T r0[W + 2], r1[W + 2], r2[W + 2];
+    const T* q0 = vp + (long long)jm * nx;
+    const T* q1 = vp + (long long)j * nx;
+    const T* q2 = vp + (long long)jp * nx;
+#pragma unroll
+    for (int e = 0; e < W + 2; ++e) {
+      r0[e] = LD::ld(q0 + xs[e]);
+      r1[e] = LD::ld(q1 + xs[e]);
+      r2[e] = LD::ld(q2 + xs[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      p1[e] = w1[0] * r0[e] + w1[1] * r0[e + 1] + w1[2] * r0[e + 2] + w1[3] * r1[e] + w1[5] * r1[e + 2] +
+              w1[6] * r2[e] + w1[7] * r2[e + 1] + w1[8] * r2[e + 2];
+      p2[e] = w2[0] * r0[e] + w2[1] * r0[e + 1] + w2[2] * r0[e + 2] + w2[3] * r1[e] + w2[5] * r1[e + 2] +
+              w2[6] * r2[e] + w2[7] * r2[e + 1] + w2[8] * r2[e + 2];
+      p1[e] += w1[4] * r1[e + 1];
+      p2[e] += w2[4] * r1[e + 1];
+    }
+  };
+#pragma unroll
+  for (int d = 0; d < 4; ++d) sums(k0 - 2 + d, P1[d], P2[d]);
+  for (int k = k0; k < k1; ++k) {
+    sums(k + 2, P1[4], P2[4]);
+    const T* zb = zbt + k * 10;
+    const long long row = ((long long)k * ny + j) * nx + x0;
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      T acc = (T)0;
+#pragma unroll
+      for (int d = 0; d < 5; ++d) acc += zb[d] * P1[d][e] + zb[5 + d] * P2[d][e];
+      tc[row + e] = LD::ld(bc + row + e) - acc;
+    }
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+      for (int e = 0; e < W; ++e) {
+        P1[d][e] = P1[d + 1][e];
+        P2[d][e] = P2[d + 1][e];
+      }
+  }
+}
+
 // Heat-bath update of site g of a Galerkin colour pass (g runs over the
 // class sites of all components, component ci from cp.gstart):
 // v_i = (b_i - sum_{j != i} A_ij v_j) / A_ii + n / sqrt(A_ii).  The four
@@ -593,6 +681,26 @@ __global__ void __launch_bounds__(kBlock) k_band7_rb_zm(LevelDev L, ColumnPass c
       cur[e] = nxt[e];
     }
   }
+}
+
+// t = b - A v on a Galerkin level (levels >= 1, not banded red-black; nx % 4
+// == 0): one thread per (component, y row, 4-wide x segment, chunk of kc z
+// rows), galerkin_residual_seg's separable form.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_galerkin_residual_zm(LevelDev L, ColumnPass cp, const T* __restrict__ v,
+                                                                const T* __restrict__ b, T* __restrict__ t) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cp.start[L.ncomp]) return;
+  int ci = 0;
+  while (ci + 1 < L.ncomp && g >= cp.start[ci + 1]) ++ci;
+  const CompDev& c = L.c[ci];
+  const int segs = c.nx >> 2;
+  const long long item = g - cp.start[ci];
+  const long long col = item % ((long long)c.ny * segs);
+  const int chunk = (int)(item / ((long long)c.ny * segs));
+  const int j = (int)(col / segs), seg = (int)(col - (long long)j * segs);
+  const int k0 = chunk * cp.kc, k1 = min(k0 + cp.kc, c.nz);
+  galerkin_residual_seg<T, 4, LdPlain>(c, v + c.off, b + c.off, t + c.off, j, seg << 2, k0, k1);
 }
 
 // Level-0 red-black colour pass marching along z: one thread per (component,
@@ -929,10 +1037,12 @@ __device__ __forceinline__ void restrict_at(const LevelDev& Lf, const LevelDev& 
   const CompDev& cf = f;  // transfer tables live on the fine level
   const long long plane = (long long)f.nx * f.ny;
   T acc = (T)0;
+#pragma unroll
   for (int qz = 0; qz < 4; ++qz) {
-    const int kf = cf.rz_idx[K * 4 + qz];
-    if (kf < 0) continue;
-    const T wz = rz_w<T>(cf, K * 4 + qz);
+    // an unused tap (index -1) reads row 0 with weight 0: no branch between taps
+    const int kr = cf.rz_idx[K * 4 + qz];
+    const int kf = kr < 0 ? 0 : kr;
+    const T wz = kr < 0 ? (T)0 : rz_w<T>(cf, K * 4 + qz);
     for (int qy = -1; qy <= 1; ++qy) {
       T wy;
       int jf;
@@ -1016,57 +1126,41 @@ __global__ void __launch_bounds__(kBlock) k_restrict_v4(LevelDev Lf, LevelDev Lc
 }
 
 // v_f += P v_c: periodic axes: even fine node = coarse node, odd = mean of two.
-template <typename T>
-__device__ __forceinline__ void prolong_at(const LevelDev& Lf, const LevelDev& Lc, T* v, const T* vc, long long s) {
+template <typename T, typename LD = LdPlain>
+__device__ __forceinline__ T prolong_val(const LevelDev& Lf, const LevelDev& Lc, const T* vc, long long s) {
   int ci, i, j, k;
   site_of(Lf, s, &ci, &i, &j, &k);
   const CompDev& f = Lf.c[ci];
   const CompDev& c = Lc.c[ci];
-  int xi[2], yi[2];
-  T xw[2], yw[2];
-  int nxp, nyp;
-  if (i & 1) {
-    xi[0] = i >> 1;
-    xi[1] = wrapi((i >> 1) + 1, c.nx);
-    xw[0] = xw[1] = (T)0.5;
-    nxp = 2;
-  } else {
-    xi[0] = i >> 1;
-    xw[0] = (T)1;
-    nxp = 1;
-  }
-  if (f.ny == 1) {
-    yi[0] = 0;
-    yw[0] = (T)1;
-    nyp = 1;
-  } else if (j & 1) {
-    yi[0] = j >> 1;
-    yi[1] = wrapi((j >> 1) + 1, c.ny);
-    yw[0] = yw[1] = (T)0.5;
-    nyp = 2;
-  } else {
-    yi[0] = j >> 1;
-    yw[0] = (T)1;
-    nyp = 1;
-  }
+  // fixed 2 x 2 x 2 taps: an unused one reads a valid coarse value with weight
+  // 0, so the loads issue without branches (the sum is unchanged)
+  const bool xo = (i & 1) != 0;
+  const int xi0 = i >> 1, xi1 = xo ? wrapi((i >> 1) + 1, c.nx) : xi0;
+  const T xw0 = xo ? (T)0.5 : (T)1, xw1 = xo ? (T)0.5 : (T)0;
+  const bool yo = f.ny > 1 && (j & 1) != 0;
+  const int yi0 = f.ny == 1 ? 0 : j >> 1, yi1 = yo ? wrapi((j >> 1) + 1, c.ny) : yi0;
+  const T yw0 = yo ? (T)0.5 : (T)1, yw1 = yo ? (T)0.5 : (T)0;
+  const int xi[2] = {xi0, xi1}, yi[2] = {yi0, yi1};
+  const T xw[2] = {xw0, xw1}, yw[2] = {yw0, yw1};
   const long long cplane = (long long)c.nx * c.ny;
   T acc = (T)0;
+#pragma unroll
   for (int qz = 0; qz < 2; ++qz) {
-    const int kc = f.pz_idx[k * 2 + qz];
-    if (kc < 0) continue;
-    const T wz = pz_w<T>(f, k * 2 + qz);
-    for (int qy = 0; qy < nyp; ++qy)
-      for (int qx = 0; qx < nxp; ++qx)
-        acc += wz * yw[qy] * xw[qx] * vc[c.off + (long long)kc * cplane + (long long)yi[qy] * c.nx + xi[qx]];
+    const int kr = f.pz_idx[k * 2 + qz];
+    const int kc = kr < 0 ? 0 : kr;
+    const T wz = kr < 0 ? (T)0 : pz_w<T>(f, k * 2 + qz);
+#pragma unroll
+    for (int qy = 0; qy < 2; ++qy)
+#pragma unroll
+      for (int qx = 0; qx < 2; ++qx)
+        acc += wz * yw[qy] * xw[qx] * LD::ld(vc + c.off + (long long)kc * cplane + (long long)yi[qy] * c.nx + xi[qx]);
   }
-  v[s] += acc;
+  return acc;
 }
 
-// prolong_at, then the cleared parity bit of the dataflow order (count 0).
-__device__ __forceinline__ void prolong_at_tag0(const LevelDev& Lf, const LevelDev& Lc, float* v, const float* vc,
-                                                long long s) {
-  prolong_at<float>(Lf, Lc, v, vc, s);
-  v[s] = __uint_as_float(__float_as_uint(v[s]) & ~1u);
+template <typename T>
+__device__ __forceinline__ void prolong_at(const LevelDev& Lf, const LevelDev& Lc, T* v, const T* vc, long long s) {
+  v[s] += prolong_val<T>(Lf, Lc, vc, s);
 }
 
 template <typename T>
@@ -1177,6 +1271,7 @@ struct CoopLevel {
   // run time), early = neighbours of a colour updated before this one in a sweep.
   unsigned long long fcheck[kMaxCoopColours][kMaxComps];
   unsigned long long fearly[kMaxCoopColours][kMaxComps];
+  ColumnPass rcp;                        // residual items (2-wide x segments); kc == 0: one site per item
   T* v;
   const T* b;
   T* t;
@@ -1431,11 +1526,30 @@ __global__ void __launch_bounds__(CoopThreads<T>::value, 2)
     } else if (!sweeps(0, mu1)) {
       return;
     }
-    for (long long s = tid; s < P.L.size; s += nth) {
-      int ci, i, j, k;
-      site_of(P.L, s, &ci, &i, &j, &k);
-      const CompDev& c = P.L.c[ci];
-      P.t[s] = __ldcg(P.b + s) - sep_apply<T, LdCG, true>(c, P.v + c.off, i, j, k);
+    // The residual's loads go through L1: no L1 line of v can be stale here,
+    // since every read of v earlier in the launch bypassed L1 (GPU-scope
+    // relaxed loads in dataflow order, .cg loads between grid barriers) and L1
+    // starts empty at launch.
+    if (P.rcp.kc > 0) {   // separable form along z columns of 2-wide segments
+      for (long long g = tid; g < P.rcp.start[ncomp]; g += nth) {
+        int ci = 0;
+        while (ci + 1 < ncomp && g >= P.rcp.start[ci + 1]) ++ci;
+        const CompDev& c = P.L.c[ci];
+        const int segs = c.nx >> 1;
+        const long long item = g - P.rcp.start[ci];
+        const long long col = item % ((long long)c.ny * segs);
+        const int chunk = (int)(item / ((long long)c.ny * segs));
+        const int j = (int)(col / segs), seg = (int)(col - (long long)j * segs);
+        const int k0 = chunk * P.rcp.kc, k1 = min(k0 + P.rcp.kc, c.nz);
+        galerkin_residual_seg<T, 2, LdPlain>(c, P.v + c.off, P.b + c.off, P.t + c.off, j, seg << 1, k0, k1);
+      }
+    } else {
+      for (long long s = tid; s < P.L.size; s += nth) {
+        int ci, i, j, k;
+        site_of(P.L, s, &ci, &i, &j, &k);
+        const CompDev& c = P.L.c[ci];
+        P.t[s] = P.b[s] - sep_apply<T, LdPlain, true>(c, P.v + c.off, i, j, k);
+      }
     }
     if (!coop_barrier(P.bar)) return;
     for (long long s = tid; s < P.Lc.size; s += nth) {
@@ -1443,14 +1557,22 @@ __global__ void __launch_bounds__(CoopThreads<T>::value, 2)
       P.vc[s] = (T)0;
     }
   } else {
-    if constexpr (kFlowType) {
-      if (flow) {
-        for (long long s = tid; s < P.L.size; s += nth) prolong_at_tag0(P.L, P.Lc, P.v, P.vc, s);
-      } else {
-        for (long long s = tid; s < P.L.size; s += nth) prolong_at<T>(P.L, P.Lc, P.v, P.vc, s);
+    // v += P vc, two sites per iteration; in dataflow order the parity bit is
+    // cleared (update count 0 for the post-smoothing)
+    auto put = [&](long long s, T val) {
+      if constexpr (kFlowType) {
+        if (flow) val = with_parity(val, 0u);
       }
-    } else {
-      for (long long s = tid; s < P.L.size; s += nth) prolong_at<T>(P.L, P.Lc, P.v, P.vc, s);
+      P.v[s] = val;
+    };
+    for (long long s = tid; s < P.L.size; s += 2 * nth) {
+      const long long s2 = s + nth;
+      const T a1 = prolong_val<T>(P.L, P.Lc, P.vc, s);
+      const T a2 = s2 < P.L.size ? prolong_val<T>(P.L, P.Lc, P.vc, s2) : (T)0;
+      const T v1 = P.v[s] + a1;
+      const T v2 = s2 < P.L.size ? P.v[s2] + a2 : (T)0;
+      put(s, v1);
+      if (s2 < P.L.size) put(s2, v2);
     }
     if (!coop_barrier(P.bar)) return;
     sweeps(mu1, mu2);
@@ -1918,6 +2040,21 @@ cudaError_t launch_residual(const LevelDev& L, const T* v, const T* b, T* t, cud
     k_band7_residual_zm<T><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, t);
     return cudaGetLastError();
   }
+  bool four = L.level >= 1 && !L.rb;
+  for (int ci = 0; ci < L.ncomp; ++ci)
+    if (L.c[ci].nx % 4 != 0) four = false;
+  if (four) {   // Galerkin level: separable form along z columns of 4-wide segments
+    ColumnPass cp{};
+    cp.kc = 8;
+    long long items = 0;
+    for (int ci = 0; ci < L.ncomp; ++ci) {
+      cp.start[ci] = items;
+      items += (long long)L.c[ci].ny * (L.c[ci].nx >> 2) * ((L.c[ci].nz + cp.kc - 1) / cp.kc);
+    }
+    cp.start[L.ncomp] = items;
+    k_galerkin_residual_zm<T><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, t);
+    return cudaGetLastError();
+  }
   k_residual<T><<<grid_for(L.size), kBlock, 0, st>>>(L, v, b, t);
   return cudaGetLastError();
 }
@@ -1982,6 +2119,25 @@ cudaError_t launch_level_coop(const LevelDev& L, const LevelDev& Lc, int phase, 
   for (int ci = 0; ci < L.ncomp; ++ci) maxcol = maxcol > L.c[ci].ncol ? maxcol : L.c[ci].ncol;
   P.ncolour = maxcol;
   for (int q = 0; q < maxcol; ++q) colour_pass_of(L, q, &P.cp[q]);
+  // residual items: 2-wide x segments of z chunks, the shortest chunk (>= 4
+  // rows) that leaves at most one item per thread
+  P.rcp = ColumnPass{};
+  bool even = true;
+  for (int ci = 0; ci < L.ncomp; ++ci)
+    if (L.c[ci].nx % 2 != 0) even = false;
+  if (even) {
+    const long long nth = (long long)blocks * CoopThreads<T>::value;
+    for (int kc = 4; kc <= 64; kc *= 2) {
+      long long items = 0;
+      for (int ci = 0; ci < L.ncomp; ++ci) {
+        P.rcp.start[ci] = items;
+        items += (long long)L.c[ci].ny * (L.c[ci].nx >> 1) * ((L.c[ci].nz + kc - 1) / kc);
+      }
+      P.rcp.start[L.ncomp] = items;
+      P.rcp.kc = kc;
+      if (items <= nth) break;
+    }
+  }
   P.flow = flow && sizeof(T) == 4 && L.flow ? 1 : 0;
   if (P.flow) {
     auto mod = [](int d, int m) { return ((d % m) + m) % m; };

@@ -1217,10 +1217,11 @@ __global__ void __launch_bounds__(kBlock) k_prolong_v8(LevelDev Lf, LevelDev Lc,
 #pragma unroll
   for (int e = 0; e < 8; ++e) acc[e] = (T)0;
   const long long cplane = (long long)c.nx * c.ny;
+#pragma unroll
   for (int qz = 0; qz < 2; ++qz) {
-    const int kc = f.pz_idx[k * 2 + qz];
-    if (kc < 0) continue;
-    const T wz = pz_w<T>(f, k * 2 + qz);
+    const int kr = f.pz_idx[k * 2 + qz];
+    const int kc = kr < 0 ? 0 : kr;   // an unused tap reads row 0 with weight 0
+    const T wz = kr < 0 ? (T)0 : pz_w<T>(f, k * 2 + qz);
     for (int a = 0; a < nyp; ++a) {
       const T* crow = vc + c.off + (long long)kc * cplane + (long long)yi[a] * c.nx;
       T cx[5];

@@ -1488,7 +1488,11 @@ template <typename T, bool NOISE>
 __global__ void __launch_bounds__(CoopThreads<T>::value, 2)
     k_level_coop(const __grid_constant__ CoopLevel<T> P, int phase, int mu1, int mu2, Key key,
                  const unsigned long long* __restrict__ cyc) {
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // Logical thread index with the warps interleaved across the blocks: warp
+  // w of block b is logical warp w * gridDim.x + b, so a pass with fewer sites
+  // than threads still spreads its warps over every SM (each warp keeps 32
+  // consecutive sites).
+  const long long tid = ((long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
   const long long nth = (long long)gridDim.x * blockDim.x;
   const unsigned long long cy = NOISE ? *cyc : 0ull;
   const int ncomp = P.L.ncomp;

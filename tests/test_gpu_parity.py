@@ -195,6 +195,26 @@ def test_vcycle_engine_from_level_2(prec, dim, n, levels, noise, coop):
     assert rel(from_dev(m.h, v), want) < tol
 
 
+@pytest.mark.parametrize("noise", [0, 1])
+@pytest.mark.parametrize("coop", [1, 2])
+def test_vcycle_128_cooperative_rows(noise, coop):
+    """The 128^3 channel's V-cycle as the benchmark runs it (FP32 inner
+    cycles, level 1 in cooperative launches, engine from level 2): colour
+    passes in dataflow order (coop=1) or separated by grid barriers (coop=2)."""
+    dim, n, levels = 3, 128, 6
+    m, osys, dt, tol = make(dim, n, levels, "fp32")
+    S.selm_mg_set_option(m.h, S.SELM_OPT_LEVEL_COOP, coop)
+    assert S.selm_mg_engine_info(m.h)[0] == 2
+    shapes = osys.shapes(0)
+    v0 = round_like(selm_inputs.fields(shapes, seed=35), dt)
+    b0 = round_like(selm_inputs.fields(shapes, seed=36), dt)
+    v = to_dev(m.h, v0, dt)
+    S.selm_mg_vcycle(m.h, 0, v, to_dev(m.h, b0, dt), cycle=47, noise=noise)
+    want = [x.copy() for x in v0]
+    multigrid.vcycle(osys, 0, want, b0, philox.PhiloxNoise(11, 3, 47), float(noise))
+    assert rel(from_dev(m.h, v), want) < tol
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("coop", [1, 2])
 def test_fac_solve_with_cooperative_level(prec, coop):

@@ -75,7 +75,9 @@ typedef struct {
   uint64_t seed;           /* Philox key material (noise of this chain) */
   uint64_t instance;       /* Philox key material (distinguishes systems) */
   /* optional device allocator hooks (e.g. a framework's caching allocator);
-     NULL -> cudaMalloc / cudaFree */
+     NULL -> cudaMalloc / cudaFree.  The returned memory must be 256-byte
+     aligned (the kernels use vector accesses); create fails with
+     SELM_EINVAL otherwise. */
   void* (*alloc)(size_t bytes, void* ctx);
   void (*free)(void* ptr, void* ctx);
   void* alloc_ctx;

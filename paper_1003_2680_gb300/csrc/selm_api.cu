@@ -491,6 +491,11 @@ selm_status create_with_host(const selm_mg_desc& d, const HostSystem& host, int 
       delete h;
       return SELM_ENOMEM;
     }
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) {   // vector accesses need the documented alignment
+      if (d.free) d.free(ws, d.alloc_ctx);
+      delete h;
+      return SELM_EINVAL;
+    }
   } else if (cudaMalloc(&ws, h->ws_bytes) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -605,6 +610,11 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
     if (!ws) {
       delete h;
       return SELM_ENOMEM;
+    }
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) {   // vector accesses need the documented alignment
+      if (h->d.free) h->d.free(ws, h->d.alloc_ctx);
+      delete h;
+      return SELM_EINVAL;
     }
   } else if (cudaMalloc(&ws, h->ws_bytes) != cudaSuccess) {
     cudaGetLastError();

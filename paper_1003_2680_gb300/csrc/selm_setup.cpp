@@ -361,6 +361,7 @@ std::string build_system(int dim, int n, int levels, double scale, const std::ve
 bool coop_flow_ok(const HostComp& c) {
   const int nz = c.dims[2];
   if (c.S.size() != (size_t)nz * kStencil || c.zb.size() != (size_t)nz * 10) return false;
+  if (c.dims[0] % 2 != 0) return false;   // periodic x colouring needs an even extent
   for (int a = 0; a < 3; ++a)
     if (c.mods[a] < 1 || (a < 2 && c.dims[a] > 1 && c.dims[a] % c.mods[a] != 0)) return false;
   auto plane = [&](int k, int dz) {

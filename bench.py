@@ -224,7 +224,8 @@ def composite_ncu_traffic():
     192^3 case, scaled to the 256^3 workload by the cells processed), keyed by
     kernel, from summaries taken on the current source."""
     out = {}
-    for name in ("composite_base_rb_192", "composite_patch_192", "composite_residual_df_192"):
+    for name in ("composite_base_rb_192", "composite_patch_192", "composite_residual_df_192",
+                 "composite_galerkin_residual_256"):
         path = os.path.join(ROOT, "profiles", name + ".md")
         if not os.path.exists(path):
             continue

@@ -390,6 +390,7 @@ __global__ void __launch_bounds__(kCBlock) k_comp_patch_v8(CompGeo G, T* __restr
     Normals<T>::get(philox4x32_10(make_uint4(grp, c1, (uint32_t)cy, (uint32_t)(cy >> 32)), key.k0, key.k1), n4);
   }
   const T rsd = NOISE ? (T)1 / tsqrt(dg) : (T)0;
+  const T rdg = (T)1 / dg;   // one division per row instead of one per site
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
 #pragma unroll
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(kCBlock) k_comp_patch_v8(CompGeo G, T* __restr
         off += w2 * sib;
         if (m == fz - 1) off -= w1 * ca[l];
       }
-      T nv = (rr[e] - off) / dg;
+      T nv = (rr[e] - off) * rdg;
       if (NOISE) nv += n4[l] * rsd;
       cen[e] = nv;
     }
@@ -830,6 +831,7 @@ __global__ void __launch_bounds__(kCBlock) k_comp_patch_zm(CompGeo G, T* __restr
         Normals<T>::get(philox4x32_10(make_uint4(grp, c1, (uint32_t)cy, (uint32_t)(cy >> 32)), key.k0, key.k1), n4);
       }
       const T rsd = NOISE ? (T)1 / tsqrt(dg) : (T)0;
+      const T rdg = (T)1 / dg;   // one division per row instead of one per site
       const bool up1 = (q ^ 1) == qp;   // which loaded y row holds the siblings' row q ^ 1
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
@@ -846,7 +848,7 @@ __global__ void __launch_bounds__(kCBlock) k_comp_patch_zm(CompGeo G, T* __restr
             off += w2 * sib;
             if (m == fz - 1) off -= w1 * ca[l];
           }
-          T nv = (rr[e] - off) / dg;
+          T nv = (rr[e] - off) * rdg;
           if (NOISE) nv += n4[l] * rsd;
           cur[e] = nv;
         }

@@ -248,13 +248,13 @@ __device__ __forceinline__ double block_sum(double x) {
 // indices keep the arrays in registers).
 template <typename T, bool NOISE, int P>
 __device__ __forceinline__ void fine_update8(T cen[8], const T bb[8], const T acc[8], T left, T right, const T n4[4],
-                                             T s, T diag, T rsd) {
+                                             T s, T rdiag, T rsd) {
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
     const int e = 2 * l + P;
     const T xl = e == 0 ? left : cen[e - 1];
     const T xr = e == 7 ? right : cen[e + 1];
-    T nv = (bb[e] + s * (acc[e] + xl + xr)) / diag;
+    T nv = (bb[e] + s * (acc[e] + xl + xr)) * rdiag;   // rdiag = 1 / A_ii of the row
     if (NOISE) nv += n4[l] * rsd;
     cen[e] = nv;
   }
@@ -660,6 +660,7 @@ __global__ void __launch_bounds__(kBlock) k_band7_rb_zm(LevelDev L, ColumnPass c
       Normals<T>::get(philox4x32_10(make_uint4(grp, c1, (uint32_t)cy, (uint32_t)(cy >> 32)), key.k0, key.k1), n4);
     }
     const T rsd = NOISE ? (T)1 / tsqrt(R.diag) : (T)0;
+    const T rdiag = (T)1 / R.diag;   // one division per row instead of one per site
     const int par = (j + k + colour) & 1;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
@@ -669,7 +670,7 @@ __global__ void __launch_bounds__(kBlock) k_band7_rb_zm(LevelDev L, ColumnPass c
         const int e = 2 * l + pp;
         const T xl = e == 0 ? left : cur[e - 1];
         const T xr = e == 7 ? right : cur[e + 1];
-        T nv = (bb[e] - (acc[e] + R.a * (wxm * xl + wxp * xr))) / R.diag;
+        T nv = (bb[e] - (acc[e] + R.a * (wxm * xl + wxp * xr))) * rdiag;
         if (NOISE) nv += n4[l] * rsd;
         cur[e] = nv;
       }
@@ -780,11 +781,12 @@ __global__ void __launch_bounds__(kBlock) k_fine_colour_zm(LevelDev L, ColumnPas
     if (c.zkind == kAxisCellDir) dz += (T)edges;
     if (c.zkind == kAxisCellNeu) dz -= (T)edges;
     const T diag = s * ((ny > 1 ? (T)4 : (T)2) + dz);
+    const T rdiag = (T)1 / diag;   // one division per row instead of one per site
     const T rsd = NOISE ? (T)1 / tsqrt(diag) : (T)0;
     if (((j + k + colour) & 1) == 0)
-      fine_update8<T, NOISE, 0>(cur, bb, acc, left, right, n4, s, diag, rsd);
+      fine_update8<T, NOISE, 0>(cur, bb, acc, left, right, n4, s, rdiag, rsd);
     else
-      fine_update8<T, NOISE, 1>(cur, bb, acc, left, right, n4, s, diag, rsd);
+      fine_update8<T, NOISE, 1>(cur, bb, acc, left, right, n4, s, rdiag, rsd);
     Vec<T>::store8(v + base + kp, cur);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {

@@ -982,6 +982,95 @@ __global__ void __launch_bounds__(kBlock) k_coarse_site(LevelDev L, ColourPass c
   coarse_site_at<T, NOISE, LdNC>(L, cp, v, b, sweep, key, NOISE ? *cyc : 0ull, g);
 }
 
+// One colour pass of a Galerkin level with 8-wide rows (nx % 8 == 0, x
+// modulus 2): one thread per (component, class row, class plane, 8-wide x
+// segment) updates the segment's four class sites x = x0 + CX + 2e, which are
+// one Philox group (ranks 4s .. 4s + 3).  The 15 rows of the window are read
+// as 8-wide vectors plus their two edge values; per site the arithmetic and
+// order are coarse_site_at's.  Every value used is of another colour (rows
+// j +- 1 and planes k +- 1, +- 2 belong to other classes, and in row j only
+// x +- 1 are read), so in-place updates are safe.  sp.start: first item of
+// each component.
+template <typename T, bool NOISE, int CX>
+__global__ void __launch_bounds__(kBlock) k_coarse_colour_v8(LevelDev L, ColourPass cp, ColumnPass sp,
+                                                            T* __restrict__ v, const T* __restrict__ b, int sweep,
+                                                            Key key, const unsigned long long* __restrict__ cyc) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= sp.start[L.ncomp]) return;
+  int ci = 0;
+  while (ci + 1 < L.ncomp && g >= sp.start[ci + 1]) ++ci;
+  const CompDev& c = L.c[ci];
+  const int nx = c.nx, ny = c.ny, nz = c.nz, segs = nx >> 3;
+  const long long item = g - sp.start[ci];
+  const int seg = (int)(item % segs);
+  const long long t = item / segs;
+  const int jj = (int)(t % cp.nyc[ci]), kk = (int)(t / cp.nyc[ci]);
+  const int j = cp.cy[ci] + c.my * jj, k = cp.cz[ci] + c.mz * kk;
+  const int x0 = seg << 3;
+  const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
+  const int xl = x0 == 0 ? nx - 1 : x0 - 1, xr = x0 + 8 == nx ? 0 : x0 + 8;
+  const T* vc = v + c.off;
+  const T* zb = (sizeof(T) == 4 ? (const T*)c.zb32 : (const T*)c.zb64) + k * 10;
+  T w1[9], w2[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    w1[q] = sep_w1<T>(c, q);
+    w2[q] = sep_w2<T>(c, q);
+  }
+  auto row = [&](const T* rp, T r[10]) {
+    r[0] = LdNC::ld(rp + xl);
+    Vec<T>::load8(rp + x0, r + 1);
+    r[9] = LdNC::ld(rp + xr);
+  };
+  T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll
+  for (int dz = -2; dz <= 2; ++dz) {
+    const T* vp = vc + (long long)min(max(k + dz, 0), nz - 1) * ny * nx;
+    T r0[10], r1[10], r2[10];
+    row(vp + (long long)j * nx, r1);
+    if (ny > 1) {
+      row(vp + (long long)jm * nx, r0);
+      row(vp + (long long)jp * nx, r2);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int x = CX + 2 * e;   // r[x], r[x + 1], r[x + 2] hold x0 + x - 1 .. x0 + x + 1
+      T p1, p2;
+      if (ny == 1) {
+        p1 = w1[3] * r1[x] + w1[5] * r1[x + 2];
+        p2 = w2[3] * r1[x] + w2[5] * r1[x + 2];
+      } else {
+        p1 = w1[0] * r0[x] + w1[1] * r0[x + 1] + w1[2] * r0[x + 2] + w1[3] * r1[x] + w1[5] * r1[x + 2] +
+             w1[6] * r2[x] + w1[7] * r2[x + 1] + w1[8] * r2[x + 2];
+        p2 = w2[0] * r0[x] + w2[1] * r0[x + 1] + w2[2] * r0[x + 2] + w2[3] * r1[x] + w2[5] * r1[x + 2] +
+             w2[6] * r2[x] + w2[7] * r2[x + 1] + w2[8] * r2[x + 2];
+      }
+      if (dz != 0) {
+        p1 += w1[4] * r1[x + 1];
+        p2 += w2[4] * r1[x + 1];
+      }
+      acc[e] += zb[dz + 2] * p1 + zb[5 + dz + 2] * p2;
+    }
+  }
+  const T diag = coarse_diag<T>(c, k);
+  T n4[4] = {(T)0, (T)0, (T)0, (T)0};
+  if (NOISE) {
+    const unsigned long long cy = *cyc;
+    const unsigned grp = (unsigned)seg + (unsigned)(cp.nxc[ci] >> 2) * (unsigned)(jj + cp.nyc[ci] * kk);
+    Normals<T>::get(philox10(make_uint4(grp, ctr1_of(L.level, c.comp_id, cp.colour_id[ci], sweep, 0), (uint32_t)cy,
+                                        (uint32_t)(cy >> 32)),
+                             key.k0, key.k1),
+                    n4);
+  }
+  const long long rowi = c.off + ((long long)k * ny + j) * nx + x0 + CX;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    T nv = (LdNC::ld(b + rowi + 2 * e) - acc[e]) / diag;
+    if (NOISE) nv += n4[e] / tsqrt(diag);
+    v[rowi + 2 * e] = nv;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Residual, restriction, prolongation
 // ---------------------------------------------------------------------------
@@ -2013,11 +2102,33 @@ cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool n
   }
   int maxcol = 0;
   for (int ci = 0; ci < L.ncomp; ++ci) maxcol = maxcol > L.c[ci].ncol ? maxcol : L.c[ci].ncol;
+  bool v8 = true;   // 8-wide rows, x modulus 2: four class sites (one noise group) per thread
+  for (int ci = 0; ci < L.ncomp; ++ci)
+    if (L.c[ci].nx % 8 != 0 || L.c[ci].mx != 2) v8 = false;
   for (int q = 0; q < maxcol; ++q) {
     ColourPass cp{};
     const long long gs = colour_pass_of(L, q, &cp);
     if (gs == 0) continue;
     prof::Scope ps(SELM_K_COARSE_SWEEP, st);
+    if (v8) {
+      ColumnPass sp{};
+      long long items = 0;
+      for (int ci = 0; ci < L.ncomp; ++ci) {
+        sp.start[ci] = items;
+        if (cp.nsites[ci] > 0) items += (long long)(L.c[ci].nx >> 3) * cp.nyc[ci] * cp.nzc[ci];
+      }
+      sp.start[L.ncomp] = items;
+      const int cx = q % 2;   // every component has x modulus 2
+      if (noise && cx == 0)
+        k_coarse_colour_v8<T, true, 0><<<grid_for(items), kBlock, 0, st>>>(L, cp, sp, v, b, sweep, key, cyc);
+      else if (noise)
+        k_coarse_colour_v8<T, true, 1><<<grid_for(items), kBlock, 0, st>>>(L, cp, sp, v, b, sweep, key, cyc);
+      else if (cx == 0)
+        k_coarse_colour_v8<T, false, 0><<<grid_for(items), kBlock, 0, st>>>(L, cp, sp, v, b, sweep, key, cyc);
+      else
+        k_coarse_colour_v8<T, false, 1><<<grid_for(items), kBlock, 0, st>>>(L, cp, sp, v, b, sweep, key, cyc);
+      continue;
+    }
     if (noise)
       k_coarse_site<T, true><<<grid_for(gs), kBlock, 0, st>>>(L, cp, v, b, sweep, key, cyc);
     else

@@ -611,7 +611,25 @@ __global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const
     const EngLevel<T>& L = sl_at(k);
     const EngLevel<T>& Lc = sl_at(k + 1);
     View<T> w = view_of(k, true);
-    prolong_into(w, Lc, Lc.gv, false, 0);
+    if (Lc.cluster) {
+      prolong_into(w, Lc, Lc.gv, false, 0);
+    } else {
+      // the coarse level is held by CTA 0, which still has its v in shared
+      // memory; the other CTAs first copy it (independent loads) into their own
+      // unused slab of that level, then prolong from shared memory
+      View<T> wc = view_of(k + 1, false);
+      if (rank != 0) {
+        const int nc = Lc.nx * Lc.ny * Lc.nz;
+#pragma unroll 4
+        for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+          int i, j, kk;
+          split_xy(Lc, q, &i, &j, &kk);
+          wc.v[wc.loc(i, j, kk)] = ld_cg(Lc.gv + q);
+        }
+        __syncthreads();
+      }
+      prolong_into(w, Lc, (const T*)wc.v, true, 0);
+    }
     cl.sync();
     const bool bl = L.sb >= 0;   // staged on the way down, untouched since
     sweeps<T, NOISE>(w, k, mu1, mu2, bl ? (const T*)(smem + L.sb) : L.gb, bl, bl ? w.z0 * w.plane : 0, key, cyc, rank,

@@ -1163,31 +1163,51 @@ __global__ void __launch_bounds__(kBlock) k_restrict(LevelDev Lf, LevelDev Lc, c
   if (s < Lc.size) restrict_at<T, LdPlain>(Lf, Lc, t, bc, s);
 }
 
-// restrict_at for four consecutive coarse x sites per thread (fine nx % 8 ==
-// 0, the same nx in every component): each contributing fine row is read as
-// one 8-wide vector (fine x 2I0 .. 2I0+7) and its left neighbour; the terms are
-// added in restrict_at's order.
+// 8 consecutive values, read through L2 only (data written by other SMs
+// earlier in the same launch).
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_restrict_v4(LevelDev Lf, LevelDev Lc, RowPass rp, const T* __restrict__ t,
-                                                       T* __restrict__ bc) {
+__device__ __forceinline__ void load8_cg(const T* p, T o[8]);
+template <>
+__device__ __forceinline__ void load8_cg<float>(const float* p, float o[8]) {
+  const float4 a = __ldcg(reinterpret_cast<const float4*>(p)), b = __ldcg(reinterpret_cast<const float4*>(p + 4));
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void load8_cg<double>(const double* p, double o[8]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(p + 2 * q));
+    o[2 * q] = a.x;
+    o[2 * q + 1] = a.y;
+  }
+}
+
+// restrict_at for four consecutive coarse x sites (item gt: coarse row, 4-wide
+// segment; fine nx % 8 == 0, the same nx in every component): each
+// contributing fine row is read as one 8-wide vector (fine x 2I0 .. 2I0+7) and
+// its left neighbour; the terms are added in restrict_at's order.  CG: reads
+// through L2 only.
+template <typename T, bool CG>
+__device__ __forceinline__ void restrict_seg4(const LevelDev& Lf, const LevelDev& Lc, const RowPass& rp,
+                                              const T* __restrict__ t, T* __restrict__ bc, long long gt) {
   const int segs = Lc.c[0].nx >> 2;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int row_all = gt / segs;
+  const long long row_all = gt / segs;
   if (row_all >= rp.rstart[Lc.ncomp]) return;
-  const int seg = gt - row_all * segs;
+  const int seg = (int)(gt - row_all * segs);
   int ci = 0;
   while (ci + 1 < Lc.ncomp && row_all >= rp.rstart[ci + 1]) ++ci;
   const CompDev& f = Lf.c[ci];
   const CompDev& c = Lc.c[ci];
-  const int row = row_all - rp.rstart[ci];
+  const int row = (int)(row_all - rp.rstart[ci]);
   const int J = row % c.ny, K = row / c.ny;
   const int I0 = seg << 2, xf0 = 2 * I0;
   const long long plane = (long long)f.nx * f.ny;
   T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll
   for (int qz = 0; qz < 4; ++qz) {
-    const int kf = f.rz_idx[K * 4 + qz];
-    if (kf < 0) continue;
-    const T wz = rz_w<T>(f, K * 4 + qz);
+    const int kr = f.rz_idx[K * 4 + qz];   // an unused tap reads row 0 with weight 0
+    const int kf = kr < 0 ? 0 : kr;
+    const T wz = kr < 0 ? (T)0 : rz_w<T>(f, K * 4 + qz);
     for (int qy = -1; qy <= 1; ++qy) {
       T wy;
       int jf;
@@ -1201,8 +1221,11 @@ __global__ void __launch_bounds__(kBlock) k_restrict_v4(LevelDev Lf, LevelDev Lc
       }
       const long long rowb = f.off + (long long)kf * plane + (long long)jf * f.nx;
       T r[8];
-      Vec<T>::load8(t + rowb + xf0, r);
-      const T lft = t[rowb + wrapi(xf0 - 1, f.nx)];
+      if (CG)
+        load8_cg<T>(t + rowb + xf0, r);
+      else
+        Vec<T>::load8(t + rowb + xf0, r);
+      const T lft = CG ? __ldcg(t + rowb + wrapi(xf0 - 1, f.nx)) : t[rowb + wrapi(xf0 - 1, f.nx)];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         acc[e] += wz * wy * (T)0.5 * (e == 0 ? lft : r[2 * e - 1]);
@@ -1214,6 +1237,12 @@ __global__ void __launch_bounds__(kBlock) k_restrict_v4(LevelDev Lf, LevelDev Lc
   T* out = bc + c.off + ((long long)K * c.ny + J) * c.nx + I0;
 #pragma unroll
   for (int e = 0; e < 4; ++e) out[e] = acc[e];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_restrict_v4(LevelDev Lf, LevelDev Lc, RowPass rp, const T* __restrict__ t,
+                                                       T* __restrict__ bc) {
+  restrict_seg4<T, false>(Lf, Lc, rp, t, bc, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // v_f += P v_c: periodic axes: even fine node = coarse node, odd = mean of two.
@@ -1261,9 +1290,6 @@ __global__ void __launch_bounds__(kBlock) k_prolong(LevelDev Lf, LevelDev Lc, T*
   if (s < Lf.size) prolong_at<T>(Lf, Lc, v, vc, s);
 }
 
-// v_f += P v_c on 8-wide segments of the fine rows (nx % 8 == 0; periodic x
-// and y with vertex coarsening, so a segment reads coarse x0/2 .. x0/2 + 4 of
-// each contributing coarse row; wall axis from the prolongation table).
 template <typename T>
 __device__ __forceinline__ void load4(const T* p, T o[4]) {
 #pragma unroll
@@ -1278,19 +1304,23 @@ __device__ __forceinline__ void load4<float>(const float* p, float o[4]) {
   o[3] = a.w;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_prolong_v8(LevelDev Lf, LevelDev Lc, RowPass rp, T* __restrict__ v,
-                                                      const T* __restrict__ vc) {
+// v_f += P v_c on one 8-wide segment of a fine row (item gt; nx % 8 == 0;
+// periodic x and y with vertex coarsening, so a segment reads coarse
+// x0/2 .. x0/2 + 4 of each contributing coarse row; wall axis from the
+// prolongation table).  TAG0 (FP32): the results' last mantissa bit is
+// cleared (update count 0 of a following dataflow-ordered smoothing).
+template <typename T, bool TAG0>
+__device__ __forceinline__ void prolong_seg8(const LevelDev& Lf, const LevelDev& Lc, const RowPass& rp,
+                                             T* __restrict__ v, const T* __restrict__ vc, long long gt) {
   const int segs = Lf.c[0].nx >> 3;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int row_all = gt / segs;
+  const long long row_all = gt / segs;
   if (row_all >= rp.rstart[Lf.ncomp]) return;
-  const int seg = gt - row_all * segs;
+  const int seg = (int)(gt - row_all * segs);
   int ci = 0;
   while (ci + 1 < Lf.ncomp && row_all >= rp.rstart[ci + 1]) ++ci;
   const CompDev& f = Lf.c[ci];
   const CompDev& c = Lc.c[ci];
-  const int row = row_all - rp.rstart[ci];
+  const int row = (int)(row_all - rp.rstart[ci]);
   const int j = row % f.ny, k = row / f.ny;
   const int x0 = seg << 3, cx0 = x0 >> 1;
   int yi[2] = {0, 0};
@@ -1329,7 +1359,17 @@ __global__ void __launch_bounds__(kBlock) k_prolong_v8(LevelDev Lf, LevelDev Lc,
   Vec<T>::load8(out, cur);
 #pragma unroll
   for (int e = 0; e < 8; ++e) cur[e] += acc[e];
+  if constexpr (TAG0 && sizeof(T) == 4) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) cur[e] = __uint_as_float(__float_as_uint(cur[e]) & ~1u);
+  }
   Vec<T>::store8(out, cur);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_prolong_v8(LevelDev Lf, LevelDev Lc, RowPass rp, T* __restrict__ v,
+                                                      const T* __restrict__ vc) {
+  prolong_seg8<T, false>(Lf, Lc, rp, v, vc, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1364,6 +1404,8 @@ struct CoopLevel {
   unsigned long long fcheck[kMaxCoopColours][kMaxComps];
   unsigned long long fearly[kMaxCoopColours][kMaxComps];
   ColumnPass rcp;                        // residual items (2-wide x segments); kc == 0: one site per item
+  int vec;                               // 1: transfers on 8-wide fine / 4-wide coarse segments
+  RowPass frp, crp;                      // rows of this level and of the coarser one
   T* v;
   const T* b;
   T* t;
@@ -1648,13 +1690,32 @@ __global__ void __launch_bounds__(CoopThreads<T>::value, 2)
       }
     }
     if (!coop_barrier(P.bar)) return;
-    for (long long s = tid; s < P.Lc.size; s += nth) {
-      restrict_at<T, LdCG>(P.L, P.Lc, P.t, P.bc, s);
-      P.vc[s] = (T)0;
+    if (P.vec) {   // t was written by other SMs in this launch: read through L2
+      const long long items = (long long)P.crp.rstart[ncomp] * (P.Lc.c[0].nx >> 2);
+      for (long long g = tid; g < items; g += nth) restrict_seg4<T, true>(P.L, P.Lc, P.crp, P.t, P.bc, g);
+      for (long long s = tid; s < P.Lc.size; s += nth) P.vc[s] = (T)0;
+    } else {
+      for (long long s = tid; s < P.Lc.size; s += nth) {
+        restrict_at<T, LdCG>(P.L, P.Lc, P.t, P.bc, s);
+        P.vc[s] = (T)0;
+      }
     }
   } else {
-    // v += P vc, two sites per iteration; in dataflow order the parity bit is
-    // cleared (update count 0 for the post-smoothing)
+    // v += P vc; in dataflow order the parity bit is cleared (update count 0
+    // for the post-smoothing)
+    if (P.vec) {
+      const long long items = (long long)P.frp.rstart[ncomp] * (P.L.c[0].nx >> 3);
+      for (long long g = tid; g < items; g += nth) {
+        if (flow)
+          prolong_seg8<T, true>(P.L, P.Lc, P.frp, P.v, P.vc, g);
+        else
+          prolong_seg8<T, false>(P.L, P.Lc, P.frp, P.v, P.vc, g);
+      }
+      if (!coop_barrier(P.bar)) return;
+      sweeps(mu1, mu2);
+      return;
+    }
+    // otherwise two sites per iteration
     auto put = [&](long long s, T val) {
       if constexpr (kFlowType) {
         if (flow) val = with_parity(val, 0u);
@@ -2257,6 +2318,20 @@ cudaError_t launch_level_coop(const LevelDev& L, const LevelDev& Lc, int phase, 
     }
   }
   P.flow = flow && sizeof(T) == 4 && L.flow ? 1 : 0;
+  P.vec = L.c[0].nx % 8 == 0 ? 1 : 0;
+  for (int ci = 0; ci < L.ncomp; ++ci)
+    if (L.c[ci].nx != L.c[0].nx || Lc.c[ci].nx * 2 != L.c[ci].nx) P.vec = 0;
+  {
+    int rows = 0, crows = 0;
+    for (int ci = 0; ci < L.ncomp; ++ci) {
+      P.frp.rstart[ci] = rows;
+      P.crp.rstart[ci] = crows;
+      rows += L.c[ci].ny * L.c[ci].nz;
+      crows += Lc.c[ci].ny * Lc.c[ci].nz;
+    }
+    P.frp.rstart[L.ncomp] = rows;
+    P.crp.rstart[L.ncomp] = crows;
+  }
   if (P.flow) {
     auto mod = [](int d, int m) { return ((d % m) + m) % m; };
     for (int q = 0; q < maxcol; ++q)

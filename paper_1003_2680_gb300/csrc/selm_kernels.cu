@@ -184,6 +184,7 @@ struct ColourPass {
   long long nsites[kMaxComps];
   int cx[kMaxComps], cy[kMaxComps], cz[kMaxComps];     // colour tuple (levels >= 1)
   int nxc[kMaxComps], nyc[kMaxComps], nzc[kMaxComps];  // extents of the colour class
+  int lxc[kMaxComps], lyc[kMaxComps];                  // log2 of nxc / nyc when powers of two, else -1
   int colour_id[kMaxComps];
 };
 
@@ -1578,10 +1579,12 @@ __device__ __forceinline__ bool flow_site(const CoopLevel<float>& P, const Colou
   const CompDev& c = L.c[ci];
   const unsigned rank = (unsigned)(g - cp.gstart[ci]);
   const unsigned nxc = (unsigned)cp.nxc[ci], nyc = (unsigned)cp.nyc[ci];
-  const unsigned t = rank / nxc;
+  // shifts for power-of-two class extents (the 64^3 level: 32 x 32)
+  const int lx = cp.lxc[ci], ly = cp.lyc[ci];
+  const unsigned t = lx >= 0 ? rank >> lx : rank / nxc;
   const int i = cp.cx[ci] + c.mx * (int)(rank - t * nxc);
-  const int j = cp.cy[ci] + c.my * (int)(t % nyc);
-  const int k = cp.cz[ci] + c.mz * (int)(t / nyc);
+  const int j = cp.cy[ci] + c.my * (int)(ly >= 0 ? t & (nyc - 1u) : t % nyc);
+  const int k = cp.cz[ci] + c.mz * (int)(ly >= 0 ? t >> ly : t / nyc);
   float* vc = P.v + c.off;
   const float* zb = c.zb32 + k * 10;
   int kk[5];
@@ -2037,6 +2040,13 @@ long long colour_pass_of(const LevelDev& L, int q, ColourPass* cp) {
     }
     if (cp->nxc[ci] <= 0) cp->nxc[ci] = 1;
     if (cp->nyc[ci] <= 0) cp->nyc[ci] = 1;
+    auto log2_or = [](int n) {
+      int l = 0;
+      while ((1 << l) < n) ++l;
+      return (1 << l) == n ? l : -1;
+    };
+    cp->lxc[ci] = log2_or(cp->nxc[ci]);
+    cp->lyc[ci] = log2_or(cp->nyc[ci]);
     gs += cp->nsites[ci];
   }
   cp->gstart[L.ncomp] = gs;

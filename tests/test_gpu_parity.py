@@ -367,3 +367,27 @@ def test_full_size_128_cycle_fp32():
     want = [x.copy() for x in z0]
     multigrid.fac_cycle(osys, want, zero, philox.PhiloxNoise(0, 0, 3), 1.0)
     assert rel(from_dev(m.h, z), want) < 1e-5
+
+
+def test_create_rejects_misaligned_workspace():
+    """Allocator hooks must return 256-byte aligned memory (the kernels use
+    vector accesses): a block 16 bytes off fails create with SELM_EINVAL and
+    goes back to the free hook."""
+    blocks, freed = {}, []
+
+    def alloc(nbytes, ctx):
+        base = torch.cuda.caching_allocator_alloc(int(nbytes) + 512)
+        blocks[base + 16] = base
+        return base + 16
+
+    def free(ptr, ctx):
+        freed.append(ptr)
+        torch.cuda.caching_allocator_delete(blocks.pop(ptr))
+
+    a_cb, f_cb = S.ALLOC_FN(alloc), S.FREE_FN(free)
+    d = S.make_desc(dim=2, n=32, torch_allocator=False)
+    d.alloc, d.free = a_cb, f_cb
+    with pytest.raises(S.SelmError) as err:
+        S.selm_mg_create(d)
+    assert err.value.status == S.SELM_EINVAL
+    assert len(freed) == 1 and not blocks

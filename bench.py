@@ -225,7 +225,7 @@ def composite_ncu_traffic():
     kernel, from summaries taken on the current source."""
     out = {}
     for name in ("composite_base_rb_192", "composite_patch_192", "composite_residual_df_192",
-                 "composite_galerkin_residual_256"):
+                 "composite_galerkin_residual_256", "composite_coarse_colour_256"):
         path = os.path.join(ROOT, "profiles", name + ".md")
         if not os.path.exists(path):
             continue

@@ -107,6 +107,21 @@ def run_oracle_cycles(n, reps):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def whole_job(seconds, units, world, device):
+    """Whole-job figures of a replica run: the units every rank processed,
+    summed, over the slowest rank's time (max over ranks).  With one rank,
+    the rank's own figures."""
+    if world == 1:
+        return float(seconds), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def cpu_baseline(n):
     times = run_oracle_cycles(n, 1)
     t = times[0]
@@ -691,15 +706,7 @@ def main():
     launches = S.selm_kernel_launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_total = sum(step_ms) / 1e3
-    t_tensor = torch.tensor([t_total, float(cycles)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tmax = t_tensor[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        csum = t_tensor[1:].clone()
-        dist.all_reduce(csum, op=dist.ReduceOp.SUM)
-        t_total, cycles_all = float(tmax.item()), float(csum.item())
-    else:
-        cycles_all = float(cycles)
+    t_total, cycles_all = whole_job(t_total, cycles, world, "cuda")
     value = n ** 3 * cycles_all / t_total
 
     # ---- end to end: the host-buffer C call, copies inside the timed region ----
@@ -718,13 +725,8 @@ def main():
         e2e_time += time.perf_counter() - t0
         e2e_cycles += S.selm_mg_stats(h)[0] + SAMPLE_CYCLES
     barrier()
-    e2e_value = n ** 3 * e2e_cycles / e2e_time
-    if world > 1:
-        t = torch.tensor([e2e_time], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([float(e2e_cycles)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        e2e_value = n ** 3 * float(c.item()) / float(t.item())
+    e2e_time, e2e_units = whole_job(e2e_time, e2e_cycles, world, "cuda")
+    e2e_value = n ** 3 * e2e_units / e2e_time
 
     # ---- per-kernel device time (events on the launching stream) ----
     prof_steps = min(args.steps, 3)

@@ -349,30 +349,64 @@ selm_status read_double(selm_mg* h, const double* dev, double* out, cudaStream_t
   return SELM_OK;
 }
 
+// Reads the reduction slots copied by a norm read-back issued on the copy
+// stream after h->ev_norm (the work stream may already run later launches):
+// out_b / out_r receive slots 0 / 1 (null: not wanted).  Reports a timed-out
+// grid barrier like read_double.
+selm_status read_norms_after_event(selm_mg* h, double* out_b, double* out_r, cudaStream_t st) {
+  CK(cudaStreamWaitEvent(h->xfer, h->ev_norm, 0));
+  CK(cudaMemcpyAsync(h->host_red, h->red, 12 * sizeof(double), cudaMemcpyDeviceToHost, h->xfer));
+  CK(cudaStreamSynchronize(h->xfer));
+  if (out_b) *out_b = h->host_red[0];
+  if (out_r) *out_r = h->host_red[1];
+  const unsigned* words = (const unsigned*)(h->host_red + 8);
+  if (words[2] != 0u || words[6] != 0u) {
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemsetAsync(h->red + 8, 0, 4 * sizeof(double), st));
+    CK(cudaStreamSynchronize(st));
+    h->err = "a grid barrier of a cooperative level launch timed out";
+    return SELM_ECUDA;
+  }
+  return SELM_OK;
+}
+
 // Deterministic FAC iteration until ||b - Az|| <= tol ||b||.
 selm_status fac_solve(selm_mg* h, Sys& s, double* z, const double* b, double tol, int max_cycles, int* cycles,
                       double* rel_out, cudaStream_t st) {
+  // Each cycle's residual norm comes back through the copy stream.  When the
+  // previous residual and the observed contraction predict that the cycle
+  // will not meet the tolerance, its V-cycle is enqueued before the norm is
+  // read, so the device does not idle during the read-back; the correction is
+  // added to z only once the norm says so.  Iterates and cycle counts are
+  // those of the plain loop: a wrong guess costs one discarded V-cycle.
   double* nb = h->red + 0;
   double* nr = h->red + 1;
-  CK(cudaMemsetAsync(nb, 0, sizeof(double), st));
+  CK(cudaMemsetAsync(nb, 0, 2 * sizeof(double), st));
   CK(launch_norm2(s.lev[0].size, b, nb, st));
-  double bn2 = 0.0;
-  selm_status r = read_double(h, nb, &bn2, st);
-  if (r != SELM_OK) return r;
   *cycles = 0;
-  if (bn2 == 0.0) {
-    CK(cudaMemsetAsync(z, 0, (size_t)s.lev[0].size * sizeof(double), st));
-    if (rel_out) *rel_out = 0.0;
-    return SELM_OK;
-  }
-  const double bn = std::sqrt(bn2);
+  double bn = 0.0, rel_prev = -1.0, rho = 0.5;
   for (int cyc = 0;; ++cyc) {
-    CK(cudaMemsetAsync(nr, 0, sizeof(double), st));
-    r = outer_residual(h, s, z, b, s.b[0], nr, st);
+    if (cyc > 0) CK(cudaMemsetAsync(nr, 0, sizeof(double), st));
+    selm_status r = outer_residual(h, s, z, b, s.b[0], nr, st);
     if (r != SELM_OK) return r;
-    double rn2 = 0.0;
-    r = read_double(h, nr, &rn2, st);
+    CK(cudaEventRecord(h->ev_norm, st));
+    const bool spec = cyc < max_cycles && (rel_prev < 0.0 || rel_prev * rho > 5.0 * tol);
+    if (spec) {
+      CK(cudaMemsetAsync(s.v[0], 0, (size_t)s.lev[0].size * h->esize, st));
+      r = vcycle(h, s, s.v[0], s.b[0], false, h->cyc + 1, st);
+      if (r != SELM_OK) return r;
+    }
+    double bn2 = 0.0, rn2 = 0.0;
+    r = read_norms_after_event(h, cyc == 0 ? &bn2 : nullptr, &rn2, st);
     if (r != SELM_OK) return r;
+    if (cyc == 0) {
+      if (bn2 == 0.0) {
+        CK(cudaMemsetAsync(z, 0, (size_t)s.lev[0].size * sizeof(double), st));
+        if (rel_out) *rel_out = 0.0;
+        return SELM_OK;
+      }
+      bn = std::sqrt(bn2);
+    }
     const double rel = std::sqrt(rn2) / bn;
     if (rel_out) *rel_out = rel;
     if (rel <= tol) {
@@ -384,11 +418,15 @@ selm_status fac_solve(selm_mg* h, Sys& s, double* z, const double* b, double tol
       h->err = "FAC solve did not converge";
       return SELM_ENOCONV;
     }
-    CK(cudaMemsetAsync(s.v[0], 0, (size_t)s.lev[0].size * h->esize, st));
-    r = vcycle(h, s, s.v[0], s.b[0], false, h->cyc + 1, st);
-    if (r != SELM_OK) return r;
+    if (!spec) {
+      CK(cudaMemsetAsync(s.v[0], 0, (size_t)s.lev[0].size * h->esize, st));
+      r = vcycle(h, s, s.v[0], s.b[0], false, h->cyc + 1, st);
+      if (r != SELM_OK) return r;
+    }
     r = outer_update(h, s, z, s.v[0], st);
     if (r != SELM_OK) return r;
+    if (rel_prev > 0.0) rho = std::min(1.0, std::max(1e-3, rel / rel_prev));
+    rel_prev = rel;
   }
 }
 
@@ -503,7 +541,9 @@ selm_status create_with_host(const selm_mg_desc& d, const HostSystem& host, int 
   }
   h->ws = (char*)ws;
   h->host_red = new (std::nothrow) double[16];
-  if (!h->host_red) {
+  if (!h->host_red || cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_norm, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
     selm_mg_destroy(h);
     return SELM_ENOMEM;
   }
@@ -626,7 +666,9 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
   // followed by a stream synchronisation anyway), so that creating and
   // destroying handles never synchronises the device.
   h->host_red = new (std::nothrow) double[16];
-  if (!h->host_red) {
+  if (!h->host_red || cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_norm, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
     selm_mg_destroy(h);
     return SELM_ENOMEM;
   }
@@ -698,6 +740,11 @@ selm_status selm_mg_destroy(selm_mg* h) {
   }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->xfer) {
+    cudaStreamSynchronize(h->xfer);
+    cudaStreamDestroy(h->xfer);
+  }
+  if (h->ev_norm) cudaEventDestroy(h->ev_norm);
   if (h->ws) {
     if (h->d.free)
       h->d.free(h->ws, h->d.alloc_ctx);

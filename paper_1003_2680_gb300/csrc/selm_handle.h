@@ -83,6 +83,10 @@ struct selm_mg {
   // solve) and join before the velocity solve, which shares their buffers.
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // norm read-back beside the work stream: the solve enqueues its next
+  // V-cycle before the copy (see fac_solve)
+  cudaStream_t xfer = nullptr;
+  cudaEvent_t ev_norm = nullptr;
   uint64_t cycle = 0;
   int last_solve_cycles = 0, last_proj_cycles = 0;
   long long total_vcycles = 0;

@@ -327,32 +327,11 @@ selm_status fac_cycle(selm_mg* h, Sys& s, double* z, const double* b, bool noise
   return outer_update(h, s, z, s.v[0], st);
 }
 
-// Reads one reduction slot of h->red.  The same copy brings back the grid-
-// barrier words of both systems (red[8..11]); a timed-out barrier wait of a
-// cooperative level launch is reported here and its words are cleared.
-selm_status read_double(selm_mg* h, const double* dev, double* out, cudaStream_t st) {
-  const long long slot = dev - h->red;
-  if (slot < 0 || slot >= 8) {
-    h->err = "read_double: not a reduction slot";
-    return SELM_EINVAL;
-  }
-  CK(cudaMemcpyAsync(h->host_red, h->red, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  *out = h->host_red[slot];
-  const unsigned* words = (const unsigned*)(h->host_red + 8);
-  if (words[2] != 0u || words[6] != 0u) {
-    CK(cudaMemsetAsync(h->red + 8, 0, 4 * sizeof(double), st));
-    CK(cudaStreamSynchronize(st));
-    h->err = "a grid barrier of a cooperative level launch timed out";
-    return SELM_ECUDA;
-  }
-  return SELM_OK;
-}
-
 // Reads the reduction slots copied by a norm read-back issued on the copy
 // stream after h->ev_norm (the work stream may already run later launches):
-// out_b / out_r receive slots 0 / 1 (null: not wanted).  Reports a timed-out
-// grid barrier like read_double.
+// out_b / out_r receive slots 0 / 1 (null: not wanted).  The same copy brings
+// back the grid-barrier words of both systems (red[8..11]); a timed-out wait
+// of a cooperative level launch is reported here and its words are cleared.
 selm_status read_norms_after_event(selm_mg* h, double* out_b, double* out_r, cudaStream_t st) {
   CK(cudaStreamWaitEvent(h->xfer, h->ev_norm, 0));
   CK(cudaMemcpyAsync(h->host_red, h->red, 12 * sizeof(double), cudaMemcpyDeviceToHost, h->xfer));

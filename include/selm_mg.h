@@ -142,7 +142,14 @@ selm_status selm_mg_set_cycle(selm_mg* h, uint64_t cycle);
    finest with the cluster-resident coarse engine (one thread-block cluster
    per component, colour passes separated by cluster barriers); 0 selects one
    launch per colour pass.  Both give the same result up to rounding. */
-enum { SELM_OPT_COARSE_ENGINE = 1, SELM_OPT_ENGINE_CLUSTER = 2, SELM_OPT_ENGINE_LEVEL = 3, SELM_OPT_LEVEL_COOP = 4 };
+enum {
+  SELM_OPT_COARSE_ENGINE = 1,
+  SELM_OPT_ENGINE_CLUSTER = 2,
+  SELM_OPT_ENGINE_LEVEL = 3,
+  SELM_OPT_LEVEL_COOP = 4,
+  SELM_OPT_GRAPHS = 5,
+  SELM_OPT_SPECULATE = 6
+};
 /* SELM_OPT_ENGINE_CLUSTER: largest thread-block cluster the coarse engine may
    use (1..16; 0 = the largest that fits).  Re-plans the engine; synchronises
    the legacy default stream.
@@ -159,6 +166,19 @@ enum { SELM_OPT_COARSE_ENGINE = 1, SELM_OPT_ENGINE_CLUSTER = 2, SELM_OPT_ENGINE_
    Every wait is bounded; a timed-out wait is reported as SELM_ECUDA by the
    next solve's norm read.  0 selects one launch per colour pass.  All give
    the same result up to rounding. */
+/* SELM_OPT_GRAPHS (default 1): the V-cycles of solves and chain cycles on the
+   handle's own buffers are captured once as CUDA graphs (on a stream of the
+   handle) and replayed, which removes their per-launch host cost and launch
+   gaps; same launches and results.  0 launches every kernel directly (for
+   short-lived handles, where capture would not pay off).
+   SELM_OPT_SPECULATE (default 1): while a solve's previous residual and
+   contraction predict no convergence, its next V-cycle is enqueued before the
+   residual norm is read back (the correction is applied only if the norm
+   confirms: same iterates and cycle counts), so the device does not idle
+   during the read-back; 0 waits for every norm first (for handles that share
+   the GPU with other work, where a mispredicted V-cycle costs others).
+   Setting any option on a handle that holds captured graphs synchronises the
+   device and drops them. */
 selm_status selm_mg_set_option(selm_mg* h, int option, int value);
 /* Coarse engine of `system`: first level it covers (-1 = not used), cluster
    size and dynamic shared memory per CTA. */

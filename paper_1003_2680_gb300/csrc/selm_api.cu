@@ -18,6 +18,7 @@
 #include "../../include/selm_mg.h"
 #include "selm_coarse.h"
 #include "selm_handle.h"
+#include "selm_prof.h"
 #include "selm_internal.h"
 #include "selm_launch.h"
 
@@ -316,13 +317,70 @@ selm_status outer_update(selm_mg* h, Sys& s, double* z, const void* d, cudaStrea
 
 namespace {
 
+void drop_graphs(selm_mg* h) {
+  for (auto& g : h->vg) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = selm_mg::VGraph{};
+  }
+}
+
+// One V-cycle on the system's level-0 buffers (s.v[0] += ..., rhs s.b[0]) as
+// a replay of a captured CUDA graph: the same launches with the same
+// arguments, without their per-launch host and launch-gap cost.  A key runs
+// directly once first (lazy one-time setup stays out of the capture); with
+// profiling on, or when capture fails, the V-cycle runs directly.
+selm_status vcycle_internal(selm_mg* h, Sys& s, bool noise, const unsigned long long* cyc, cudaStream_t st) {
+  if (!h->graphs || !h->cap || prof::g_on) return vcycle(h, s, s.v[0], s.b[0], noise, cyc, st);
+  selm_mg::VGraph* g = nullptr;
+  for (auto& e : h->vg)
+    if (e.sys == &s && e.noise == noise && e.cyc == cyc) g = &e;
+  if (!g) {
+    for (auto& e : h->vg)
+      if (!e.sys) {
+        g = &e;
+        break;
+      }
+    if (!g) return vcycle(h, s, s.v[0], s.b[0], noise, cyc, st);
+    g->sys = &s;
+    g->noise = noise;
+    g->cyc = cyc;
+  }
+  if (!g->exec && g->uses++ == 0) return vcycle(h, s, s.v[0], s.b[0], noise, cyc, st);
+  if (!g->exec) {
+    const long long l0 = prof::g_launches.load();
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      h->graphs = false;
+      return vcycle(h, s, s.v[0], s.b[0], noise, cyc, st);
+    }
+    const selm_status r = vcycle(h, s, s.v[0], s.b[0], noise, cyc, h->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    h->total_vcycles -= 1;   // the capture recorded the V-cycle; nothing ran
+    g->launches = prof::g_launches.load() - l0;
+    prof::g_launches.fetch_sub(g->launches);
+    if (r != SELM_OK || e != cudaSuccess || !graph || cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      g->exec = nullptr;
+      h->graphs = false;   // direct launches from now on
+      return vcycle(h, s, s.v[0], s.b[0], noise, cyc, st);
+    }
+    cudaGraphDestroy(graph);
+  }
+  CK(cudaGraphLaunch(g->exec, st));
+  h->total_vcycles += 1;
+  prof::g_launches.fetch_add(g->launches);
+  return SELM_OK;
+}
+
 // One FAC iteration (Algorithm 1) with the internal level-0 buffers.
 selm_status fac_cycle(selm_mg* h, Sys& s, double* z, const double* b, bool noise, const unsigned long long* cyc,
                       cudaStream_t st) {
   selm_status r = outer_residual(h, s, z, b, s.b[0], nullptr, st);
   if (r != SELM_OK) return r;
   CK(cudaMemsetAsync(s.v[0], 0, (size_t)s.lev[0].size * h->esize, st));
-  r = vcycle(h, s, s.v[0], s.b[0], noise, cyc, st);
+  r = vcycle_internal(h, s, noise, cyc, st);
   if (r != SELM_OK) return r;
   return outer_update(h, s, z, s.v[0], st);
 }
@@ -369,10 +427,10 @@ selm_status fac_solve(selm_mg* h, Sys& s, double* z, const double* b, double tol
     selm_status r = outer_residual(h, s, z, b, s.b[0], nr, st);
     if (r != SELM_OK) return r;
     CK(cudaEventRecord(h->ev_norm, st));
-    const bool spec = cyc < max_cycles && (rel_prev < 0.0 || rel_prev * rho > 5.0 * tol);
+    const bool spec = h->speculate && cyc < max_cycles && (rel_prev < 0.0 || rel_prev * rho > 5.0 * tol);
     if (spec) {
       CK(cudaMemsetAsync(s.v[0], 0, (size_t)s.lev[0].size * h->esize, st));
-      r = vcycle(h, s, s.v[0], s.b[0], false, h->cyc + 1, st);
+      r = vcycle_internal(h, s, false, h->cyc + 1, st);
       if (r != SELM_OK) return r;
     }
     double bn2 = 0.0, rn2 = 0.0;
@@ -399,7 +457,7 @@ selm_status fac_solve(selm_mg* h, Sys& s, double* z, const double* b, double tol
     }
     if (!spec) {
       CK(cudaMemsetAsync(s.v[0], 0, (size_t)s.lev[0].size * h->esize, st));
-      r = vcycle(h, s, s.v[0], s.b[0], false, h->cyc + 1, st);
+      r = vcycle_internal(h, s, false, h->cyc + 1, st);
       if (r != SELM_OK) return r;
     }
     r = outer_update(h, s, z, s.v[0], st);
@@ -521,6 +579,7 @@ selm_status create_with_host(const selm_mg_desc& d, const HostSystem& host, int 
   h->ws = (char*)ws;
   h->host_red = new (std::nothrow) double[16];
   if (!h->host_red || cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_norm, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     selm_mg_destroy(h);
@@ -646,6 +705,7 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
   // destroying handles never synchronises the device.
   h->host_red = new (std::nothrow) double[16];
   if (!h->host_red || cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_norm, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     selm_mg_destroy(h);
@@ -724,6 +784,8 @@ selm_status selm_mg_destroy(selm_mg* h) {
     cudaStreamDestroy(h->xfer);
   }
   if (h->ev_norm) cudaEventDestroy(h->ev_norm);
+  drop_graphs(h);
+  if (h->cap) cudaStreamDestroy(h->cap);
   if (h->ws) {
     if (h->d.free)
       h->d.free(h->ws, h->d.alloc_ctx);
@@ -787,6 +849,22 @@ selm_status selm_mg_set_cycle(selm_mg* h, uint64_t cycle) {
 
 selm_status selm_mg_set_option(selm_mg* h, int option, int value) {
   if (!h) return SELM_EINVAL;
+  // every option changes the V-cycle's launches: drop the captured graphs
+  // (after the device finished any launch of them)
+  bool captured = false;
+  for (const auto& g : h->vg) captured = captured || g.exec != nullptr;
+  if (captured) {
+    CK(cudaDeviceSynchronize());
+    drop_graphs(h);
+  }
+  if (option == SELM_OPT_GRAPHS) {
+    h->graphs = value != 0;
+    return SELM_OK;
+  }
+  if (option == SELM_OPT_SPECULATE) {
+    h->speculate = value != 0;
+    return SELM_OK;
+  }
   if (option == SELM_OPT_COARSE_ENGINE) {
     h->vel.use_engine = value != 0;
     h->pres.use_engine = value != 0;

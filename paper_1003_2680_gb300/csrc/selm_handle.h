@@ -87,6 +87,21 @@ struct selm_mg {
   // V-cycle before the copy (see fac_solve)
   cudaStream_t xfer = nullptr;
   cudaEvent_t ev_norm = nullptr;
+  // CUDA graphs of the internal V-cycles (the handle's level-0 buffers),
+  // keyed by system, noise and counter; captured on `cap`, replayed on the
+  // work stream.  Dropped whenever the launch plans change.
+  struct VGraph {
+    cudaGraphExec_t exec = nullptr;
+    const selm::Sys* sys = nullptr;
+    bool noise = false;
+    const unsigned long long* cyc = nullptr;
+    int uses = 0;              // direct runs before the capture (first run initialises lazily)
+    long long launches = 0;    // kernel launches in the graph
+  };
+  VGraph vg[4];
+  cudaStream_t cap = nullptr;
+  bool graphs = true;
+  bool speculate = true;      // solves enqueue the next V-cycle before reading the norm
   uint64_t cycle = 0;
   int last_solve_cycles = 0, last_proj_cycles = 0;
   long long total_vcycles = 0;

@@ -4,8 +4,14 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 namespace selm {
 namespace prof {
+// Launches so far (every Scope counts one; replays of captured graphs add
+// their captured count) and whether launches are bracketed by events.
+extern std::atomic<long long> g_launches;
+extern bool g_on;
 struct Scope {
   int kind;
   cudaStream_t st;

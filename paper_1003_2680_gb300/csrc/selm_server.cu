@@ -156,8 +156,14 @@ void worker_loop(selm_server* s) {
     selm_mg* h = nullptr;
     res.status = selm_mg_create(&d, st, &h);
     if (res.status == SELM_OK) {
-      res.status = selm_mg_step_host(h, job.req.np, job.req.X, job.req.F, job.req.dt, job.req.nsteps,
-                                     job.req.ncycles_per_step, st);
+      // a request's handle lives for a few steps (capturing graphs would not pay
+      // off) and shares the GPU with the other slots (a mispredicted V-cycle
+      // costs them)
+      res.status = selm_mg_set_option(h, SELM_OPT_GRAPHS, 0);
+      if (res.status == SELM_OK) res.status = selm_mg_set_option(h, SELM_OPT_SPECULATE, 0);
+      if (res.status == SELM_OK)
+        res.status = selm_mg_step_host(h, job.req.np, job.req.X, job.req.F, job.req.dt, job.req.nsteps,
+                                       job.req.ncycles_per_step, st);
       long long total = 0;
       selm_mg_stats(h, nullptr, nullptr, &total);
       res.vcycles = (int)total;

@@ -22,6 +22,8 @@ SELM_OPT_COARSE_ENGINE = 1
 SELM_OPT_ENGINE_CLUSTER = 2
 SELM_OPT_ENGINE_LEVEL = 3
 SELM_OPT_LEVEL_COOP = 4
+SELM_OPT_GRAPHS = 5
+SELM_OPT_SPECULATE = 6
 
 _STATUS = {0: "SELM_OK", 1: "SELM_EINVAL", 2: "SELM_ENOMEM", 3: "SELM_ECUDA", 4: "SELM_ENOCONV",
            5: "SELM_ETIMEOUT", 6: "SELM_EBUSY"}

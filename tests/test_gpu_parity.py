@@ -369,6 +369,24 @@ def test_full_size_128_cycle_fp32():
     assert rel(from_dev(m.h, z), want) < 1e-5
 
 
+@pytest.mark.parametrize("dim,n,levels", [(3, 32, 4), (3, 128, 6)])
+def test_graph_replay_matches_direct_launches(dim, n, levels):
+    """Solve V-cycles replayed from captured CUDA graphs (the default) give the
+    solve of direct launches bit for bit, with the same cycle count (128^3:
+    the cooperative level and the engine inside the graph)."""
+    outs = []
+    for graphs in (1, 0):
+        m, osys, dt, tol = make(dim, n, levels, "fp32")
+        S.selm_mg_set_option(m.h, S.SELM_OPT_GRAPHS, graphs)
+        b0 = selm_inputs.fields(osys.shapes(0), seed=16)
+        z = empty(m.h, torch.float64)
+        cycles, res = S.selm_mg_fac_solve(m.h, 0, z, to_dev(m.h, b0, torch.float64), 1e-10, 50)
+        assert res <= 1e-10 and cycles >= 3   # a capture and replays took part
+        outs.append((cycles, z.cpu().numpy()))
+    assert outs[0][0] == outs[1][0]
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
 def test_create_rejects_misaligned_workspace():
     """Allocator hooks must return 256-byte aligned memory (the kernels use
     vector accesses): a block 16 bytes off fails create with SELM_EINVAL and

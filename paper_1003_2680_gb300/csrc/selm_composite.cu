@@ -918,6 +918,11 @@ struct selm_comp {
   uint64_t cycle = 0;
   long long total_cycles = 0;
   std::string err;
+  // one chain cycle (with its counter increment) as a captured CUDA graph,
+  // replayed by selm_comp_sample (captured after one direct cycle)
+  cudaGraphExec_t chain_graph = nullptr;
+  int chain_runs = 0;
+  long long graph_launches = 0, graph_vcycles = 0;
 };
 
 namespace {
@@ -1202,6 +1207,7 @@ selm_status selm_comp_create(const selm_comp_desc* desc, void* stream, selm_comp
 
 selm_status selm_comp_destroy(selm_comp* C) {
   if (!C) return SELM_EINVAL;
+  if (C->chain_graph) cudaGraphExecDestroy(C->chain_graph);
   if (C->mg) selm_mg_destroy(C->mg);
   delete[] C->host_red;
   delete C;
@@ -1303,13 +1309,57 @@ selm_status selm_comp_solve(selm_comp* C, double* z, const double* b, double tol
   }
 }
 
+// One chain cycle and its counter increment, directly or (from the second
+// cycle of the handle on, with graphs on and profiling off) as a replay of
+// the captured cycle: the same launches on the same buffers, the counter read
+// from device memory.  Host counters moved by the capture are undone, and
+// each replay credits them.
+static selm_status chain_step(selm_comp* C, cudaStream_t st) {
+  selm_mg* h = C->mg;
+  const bool graph = h->graphs && h->cap && !prof::g_on;
+  if (!graph || (!C->chain_graph && C->chain_runs++ == 0)) {
+    selm_status r = chain_cycle(C, h->cyc + 0, st);
+    if (r != SELM_OK) return r;
+    return launch_inc_u64(h->cyc + 0, st) == cudaSuccess ? SELM_OK : SELM_ECUDA;
+  }
+  if (!C->chain_graph) {
+    const long long l0 = prof::g_launches.load(), v0 = h->total_vcycles, c0 = C->total_cycles;
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      h->graphs = false;
+      return chain_step(C, st);
+    }
+    selm_status r = chain_cycle(C, h->cyc + 0, h->cap);
+    if (r == SELM_OK && launch_inc_u64(h->cyc + 0, h->cap) != cudaSuccess) r = SELM_ECUDA;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    C->graph_launches = prof::g_launches.load() - l0;
+    C->graph_vcycles = h->total_vcycles - v0;
+    prof::g_launches.fetch_sub(C->graph_launches);   // recorded, not run
+    h->total_vcycles = v0;
+    C->total_cycles = c0;
+    if (r != SELM_OK || e != cudaSuccess || !g || cudaGraphInstantiate(&C->chain_graph, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      C->chain_graph = nullptr;
+      h->graphs = false;   // direct cycles from now on
+      return chain_step(C, st);
+    }
+    cudaGraphDestroy(g);
+  }
+  CCK(cudaGraphLaunch(C->chain_graph, st));
+  prof::g_launches.fetch_add(C->graph_launches);
+  h->total_vcycles += C->graph_vcycles;
+  C->total_cycles += 1;
+  return SELM_OK;
+}
+
 selm_status selm_comp_sample(selm_comp* C, int ncycles, double* xi_out, void* stream) {
   if (!C || ncycles < 0) return SELM_EINVAL;
   cudaStream_t st = CS(stream);
   for (int q = 0; q < ncycles; ++q) {
-    selm_status r = chain_cycle(C, C->mg->cyc + 0, st);
+    selm_status r = chain_step(C, st);
     if (r != SELM_OK) return r;
-    if (launch_inc_u64(C->mg->cyc + 0, st) != cudaSuccess) return SELM_ECUDA;
     C->cycle += 1;
   }
   if (xi_out) {

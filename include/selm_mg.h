@@ -138,6 +138,12 @@ int selm_mg_inner_bytes(const selm_mg* h);
    counter (the Philox counter of the next stochastic cycle). */
 selm_status selm_mg_chain(selm_mg* h, double** xi, uint64_t* cycle);
 selm_status selm_mg_set_cycle(selm_mg* h, uint64_t cycle);
+/* Failure-path hook: raises the timeout flag of `system`'s cooperative waits
+   (on `stream`), as a wait that ran out of time does.  The next cooperative
+   level launch gives up at its first wait and returns; the next norm read of
+   a solve reports SELM_ECUDA and clears the flag.  Lets a test exercise the
+   failure path without a GPU fault. */
+selm_status selm_mg_fail_waits(selm_mg* h, int system, void* stream);
 /* Options.  SELM_OPT_COARSE_ENGINE (default 1): run the levels below the
    finest with the cluster-resident coarse engine (one thread-block cluster
    per component, colour passes separated by cluster barriers); 0 selects one

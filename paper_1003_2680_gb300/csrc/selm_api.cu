@@ -838,6 +838,14 @@ selm_status selm_mg_chain(selm_mg* h, double** xi, uint64_t* cycle) {
   return SELM_OK;
 }
 
+selm_status selm_mg_fail_waits(selm_mg* h, int system, void* stream) {
+  if (!h) return SELM_EINVAL;
+  Sys* s = sys_of(h, system);
+  if (!s || !s->coop_bar) return SELM_EINVAL;
+  CK(cudaMemsetAsync(s->coop_bar + 2, 0x01, sizeof(unsigned), S(stream)));   // any non-zero word
+  return SELM_OK;
+}
+
 selm_status selm_mg_set_cycle(selm_mg* h, uint64_t cycle) {
   if (!h) return SELM_EINVAL;
   CK(launch_set_u64(h->cyc + 0, cycle, nullptr));

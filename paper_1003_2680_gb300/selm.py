@@ -93,6 +93,7 @@ _SIGS = {
     "selm_mg_inner_bytes": (_I, [_P]),
     "selm_mg_chain": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_U64)]),
     "selm_mg_set_cycle": (_I, [_P, _U64]),
+    "selm_mg_fail_waits": (_I, [_P, _I, _P]),
     "selm_mg_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_LL)]),
     "selm_mg_set_option": (_I, [_P, _I, _I]),
     "selm_mg_engine_info": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
@@ -306,6 +307,10 @@ def selm_mg_chain(h):
 
 def selm_mg_set_cycle(h, cycle):
     _check(h, lib().selm_mg_set_cycle(h, cycle))
+
+
+def selm_mg_fail_waits(h, system, stream=None):
+    _check(h, lib().selm_mg_fail_waits(h, system, _stream(stream)))
 
 
 def selm_mg_stats(h):

@@ -387,6 +387,26 @@ def test_graph_replay_matches_direct_launches(dim, n, levels):
     assert np.array_equal(outs[0][1], outs[1][1])
 
 
+@pytest.mark.parametrize("coop", [1, 2])
+def test_timed_out_wait_is_reported_and_cleared(coop):
+    """A cooperative level launch whose wait gives up (its timeout flag raised,
+    as a wait that ran out of time raises it) returns; the solve reports
+    SELM_ECUDA at its next norm read and clears the flag; the next solve runs
+    normally.  No GPU fault, no wait of a second."""
+    m, osys, dt, tol = make(3, 64, 4, "fp32")
+    S.selm_mg_set_option(m.h, S.SELM_OPT_LEVEL_COOP, coop)
+    S.selm_mg_set_option(m.h, S.SELM_OPT_ENGINE_LEVEL, 2)
+    b0 = to_dev(m.h, selm_inputs.fields(osys.shapes(0), seed=17), torch.float64)
+    z = empty(m.h, torch.float64)
+    S.selm_mg_fail_waits(m.h, 0)
+    with pytest.raises(S.SelmError) as err:
+        S.selm_mg_fac_solve(m.h, 0, z, b0, 1e-10, 50)
+    assert err.value.status == S.SELM_ECUDA and "timed out" in str(err.value)
+    z.zero_()
+    cycles, res = S.selm_mg_fac_solve(m.h, 0, z, b0, 1e-10, 50)
+    assert res <= 1e-10 and cycles >= 1
+
+
 def test_create_rejects_misaligned_workspace():
     """Allocator hooks must return 256-byte aligned memory (the kernels use
     vector accesses): a block 16 bytes off fails create with SELM_EINVAL and

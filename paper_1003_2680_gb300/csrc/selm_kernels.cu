@@ -1877,33 +1877,66 @@ __device__ __forceinline__ CouplingGeom geom_of(const CompDev& c, int dim) {
 
 __device__ __forceinline__ int comp_col(const CompDev& c, int dim) { return dim == 3 ? c.comp_id : (c.comp_id == 0 ? 0 : 1); }
 
-// One thread per (particle, component, node of the 4^d support).
+// The 1-D kernel taps of one particle and component, shared across a warp:
+// lane 4a + t (a < 3, t < 4) evaluates tap t of axis a once; node q of the
+// 4^d support (q = t0 + 4 t1 + 16 t2) gathers its three taps by shuffles.
+// Every lane of the warp must call both.
+__device__ __forceinline__ void taps_of(const CouplingGeom& ge, const double* X, int p, int dim, int n, int lane,
+                                        int* idl, double* wl) {
+  *idl = -1;
+  *wl = 0.0;
+  if (lane < 12) {
+    const int a = lane >> 2, t = lane & 3;
+    const double x = ge.col[a] >= 0 ? X[(long long)p * dim + ge.col[a]] * n : 0.0;
+    axis_node(ge.kind[a], x, ge.off[a], n, t, idl, wl);
+  }
+}
+
+// Node q's grid index (ok == false: a tap outside the walls) and weight, the
+// product taken axis by axis as the per-node evaluation does.
+__device__ __forceinline__ void node_of(int q, int dim, int idl, double wl, int id[3], double* w, bool* ok) {
+  const int tq[3] = {q & 3, dim == 3 ? (q >> 2) & 3 : 0, dim == 3 ? (q >> 4) & 3 : (q >> 2) & 3};
+  *w = 1.0;
+  *ok = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    id[a] = __shfl_sync(0xffffffffu, idl, 4 * a + tq[a]);
+    const double wa = __shfl_sync(0xffffffffu, wl, 4 * a + tq[a]);
+    *ok = *ok && id[a] >= 0;
+    *w *= wa;
+  }
+}
+
+// f(node) += F_p w(node): one warp per (particle, component), the taps
+// evaluated once per axis, two nodes per lane (FP64 atomics).
 __global__ void __launch_bounds__(kBlock) k_spread(LevelDev L, int n, int dim, int np, const double* __restrict__ X,
                                                   const double* __restrict__ F, double* __restrict__ b) {
   const int nodes = dim == 3 ? 64 : 16;
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (long long)np * L.ncomp * nodes) return;
-  const int q = (int)(g % nodes);
-  const int ci = (int)((g / nodes) % L.ncomp);
-  const int p = (int)(g / ((long long)nodes * L.ncomp));
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (long long)np * L.ncomp) return;   // whole warps leave together
+  const int ci = (int)(wid % L.ncomp);
+  const int p = (int)(wid / L.ncomp);
   const CompDev& c = L.c[ci];
   const CouplingGeom ge = geom_of(c, dim);
-  const int tq[3] = {q & 3, dim == 3 ? (q >> 2) & 3 : 0, dim == 3 ? (q >> 4) & 3 : (q >> 2) & 3};
-  int id[3];
-  double w = 1.0;
-  for (int a = 0; a < 3; ++a) {
-    const double x = ge.col[a] >= 0 ? X[(long long)p * dim + ge.col[a]] * n : 0.0;
-    double wa;
-    axis_node(ge.kind[a], x, ge.off[a], n, tq[a], &id[a], &wa);
-    if (id[a] < 0) return;
-    w *= wa;
-  }
-  if (w == 0.0) return;
+  int idl;
+  double wl;
+  taps_of(ge, X, p, dim, n, lane, &idl, &wl);
   const double f = F[(long long)p * dim + comp_col(c, dim)];
-  atomicAdd(&b[c.off + ((long long)id[2] * c.ny + id[1]) * c.nx + id[0]], f * w);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int q = lane + 32 * h;
+    int id[3];
+    double w;
+    bool ok;
+    node_of(q & 63, dim, idl, wl, id, &w, &ok);
+    if (q < nodes && ok && w != 0.0)
+      atomicAdd(&b[c.off + ((long long)id[2] * c.ny + id[1]) * c.nx + id[0]], f * w);
+  }
 }
 
-// One warp per (particle, component).
+// U_p = sum_node w(node) u(node): one warp per (particle, component), the taps
+// evaluated once per axis, two nodes per lane, warp reduction.
 __global__ void __launch_bounds__(kBlock) k_interp(LevelDev L, int n, int dim, int np, const double* __restrict__ X,
                                                   const double* __restrict__ u, double* __restrict__ U) {
   const int nodes = dim == 3 ? 64 : 16;
@@ -1914,20 +1947,18 @@ __global__ void __launch_bounds__(kBlock) k_interp(LevelDev L, int n, int dim, i
   const int p = (int)(wid / L.ncomp);
   const CompDev& c = L.c[ci];
   const CouplingGeom ge = geom_of(c, dim);
+  int idl;
+  double wl;
+  taps_of(ge, X, p, dim, n, lane, &idl, &wl);
   double acc = 0.0;
-  for (int q = lane; q < nodes; q += 32) {
-    const int tq[3] = {q & 3, dim == 3 ? (q >> 2) & 3 : 0, dim == 3 ? (q >> 4) & 3 : (q >> 2) & 3};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int q = lane + 32 * h;
     int id[3];
-    double w = 1.0;
-    bool ok = true;
-    for (int a = 0; a < 3; ++a) {
-      const double x = ge.col[a] >= 0 ? X[(long long)p * dim + ge.col[a]] * n : 0.0;
-      double wa;
-      axis_node(ge.kind[a], x, ge.off[a], n, tq[a], &id[a], &wa);
-      ok = ok && id[a] >= 0;
-      w *= wa;
-    }
-    if (ok) acc += w * u[c.off + ((long long)id[2] * c.ny + id[1]) * c.nx + id[0]];
+    double w;
+    bool ok;
+    node_of(q & 63, dim, idl, wl, id, &w, &ok);
+    if (q < nodes && ok) acc += w * u[c.off + ((long long)id[2] * c.ny + id[1]) * c.nx + id[0]];
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) U[(long long)p * dim + comp_col(c, dim)] = acc;
@@ -2467,7 +2498,7 @@ cudaError_t launch_inc_u64(unsigned long long* p, cudaStream_t st) {
 cudaError_t launch_spread(const LevelDev& L0, int n, int dim, int np, const double* X, const double* F, double* b,
                           cudaStream_t st) {
   if (np <= 0) return cudaSuccess;
-  const long long nt = (long long)np * L0.ncomp * (dim == 3 ? 64 : 16);
+  const long long nt = (long long)np * L0.ncomp * 32;   // one warp per (particle, component)
   prof::Scope ps(SELM_K_SPREAD, st);
   k_spread<<<grid_for(nt), kBlock, 0, st>>>(L0, n, dim, np, X, F, b);
   return cudaGetLastError();

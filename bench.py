@@ -63,7 +63,7 @@ def parse_args():
     p.add_argument("--engine-level", type=int, default=0,
                    help="first multigrid level of the cluster-resident coarse engine (0 = automatic)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="channel128", choices=["channel128", "batched", "served", "composite"],
+    p.add_argument("--workload", default="channel128", choices=["channel128", "batched", "served", "composite", "decorrelation"],
                    help="channel128: the headline line; batched: 64 uneven systems, batched vs plain; "
                         "served: Poisson request stream, served vs plain per-request")
     p.add_argument("--comp-n", type=int, default=256, help="composite workload: base cells per axis")
@@ -375,7 +375,9 @@ def run_batched(args):
 
     for _ in range(max(1, args.warmup - 2)):
         batch_step()
+    launches0 = S.selm_kernel_launches()
     t_batch, cyc_batch = timed(batch_step, args.steps)
+    launches = S.selm_kernel_launches() - launches0
     S.selm_batch_destroy(b)
     line = {
         "metric": "batched stochastic-MG: system-steps/s and cell-cycles/s, batched vs plain per-instance",
@@ -390,6 +392,7 @@ def run_batched(args):
         "plain": {"system_steps_per_s": nsys * args.steps / t_plain, "cell_cycles_per_s": sum(cyc_plain) / t_plain,
                   "ms_per_step": 1e3 * t_plain / args.steps},
         "speedup_steps": t_plain / t_batch,
+        "gpu_launches": int(launches),
     }
     print(json.dumps(line), flush=True)
 
@@ -451,7 +454,9 @@ def run_served(args):
 
     torch.cuda.synchronize()
     plain = serve(1)
+    launches0 = S.selm_kernel_launches()
     served = serve(args.slots)
+    launches = S.selm_kernel_launches() - launches0
     line = {
         "metric": "served solves/s + p99 vs plain form", "value": served["solves_per_s"], "unit": "solves/s",
         "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "dtype": "f32+f64",
@@ -462,6 +467,91 @@ def run_served(args):
                    "solve": "one Euler-Maruyama step (one mobility solve) of one request"},
         "served": served, "plain": plain,
         "speedup_solves": served["solves_per_s"] / plain["solves_per_s"],
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_decorrelation(args):
+    """Multigrid against Gauss-Seidel sampler (Section 5): lag correlations of a
+    wall mode and a point probe, integrated autocorrelation times, time per
+    iteration and independent variates per second, on the 2-D 64^2 FP64 grid
+    and the 3-D 128^3 FP32-refined channel."""
+    import numpy as np
+    import torch
+    from paper_1003_2680_gb300 import _build
+    _build.build()
+    from paper_1003_2680_gb300 import selm as S
+    from paper_1003_2680_gb300 import decorrelation as D
+
+    cases = [("2-D 64^2, FP64, 6 levels", 2, 64, S.SELM_FP64, 400),
+             ("3-D 128^3, FP32 inner + FP64 refinement", 3, 128, S.SELM_FP32_REFINE64, 200)]
+    out = {}
+    launches = 0
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for name, dim, n, prec, k_gs in cases:
+            m = S.SelmMG(dim=dim, n=n, precision=prec, seed=0, instance=0)
+            h = m.h
+            obs = {}
+            for oname, phi in (("wall_mode", D.wall_mode(h, n)), ("point_probe", D.point_probe(h))):
+                w = D.covariance_image(h, phi)
+                r_mg = D.lag_correlations_mg(h, phi, 8, w)
+                r_gs = D.lag_correlations_gs(h, phi, k_gs, w)
+                obs[oname] = {
+                    "mg": {"rho_1_to_4": [round(float(x), 6) for x in r_mg[1:5]],
+                           "tau_int": D.integrated_time(r_mg), "lags_below_0.05": D.lags_below(r_mg)},
+                    "gs": {"rho_at": {str(k): round(float(r_gs[k]), 6) for k in (1, 10, 50, 100, k_gs)},
+                           "tau_int_lower_bound": D.integrated_time(r_gs),
+                           "lags_below_0.05": D.lags_below(r_gs), "lags_computed": k_gs},
+                }
+            # time per iteration of each sampler (noise on, b = 0), events on the launching stream
+            tot = S.selm_mg_layout(h, S.SELM_SYS_VELOCITY, 0, 0)[2]   # elements of the level field
+            z = torch.zeros(tot, dtype=torch.float64, device="cuda")
+            zero = torch.zeros_like(z)
+            dt = torch.float32 if S.selm_mg_inner_bytes(h) == 4 else torch.float64
+            v = torch.zeros(tot, dtype=dt, device="cuda")
+            zv = torch.zeros_like(v)
+            n_mg, n_gs = max(args.steps, 10) * 2, max(args.steps, 10) * 10
+            for k in range(args.warmup):
+                S.selm_mg_fac_cycle(h, S.SELM_SYS_VELOCITY, z, zero, k, 1)
+                S.selm_mg_smooth(h, S.SELM_SYS_VELOCITY, 0, v, zv, 0, k, 1)
+            torch.cuda.synchronize()
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            l0 = S.selm_kernel_launches()
+            a.record()
+            for k in range(n_mg):
+                S.selm_mg_fac_cycle(h, S.SELM_SYS_VELOCITY, z, zero, 100 + k, 1)
+            b.record()
+            for k in range(n_gs):
+                S.selm_mg_smooth(h, S.SELM_SYS_VELOCITY, 0, v, zv, 0, 100 + k, 1)
+            c.record()
+            torch.cuda.synchronize()
+            launches += S.selm_kernel_launches() - l0
+            t_mg = a.elapsed_time(b) / 1e3 / n_mg
+            t_gs = b.elapsed_time(c) / 1e3 / n_gs
+            tau_mg = max(o["mg"]["tau_int"] for o in obs.values())
+            tau_gs = max(o["gs"]["tau_int_lower_bound"] for o in obs.values())
+            out[f"{dim}d_{n}"] = {
+                "workload": name, "observables": obs,
+                "mg_iteration_us": 1e6 * t_mg, "gs_sweep_us": 1e6 * t_gs,
+                "mg_variates_per_s": 1.0 / (max(tau_mg, 1.0) * t_mg),
+                "gs_variates_per_s_upper_bound": 1.0 / (tau_gs * t_gs),
+                "mg_advantage_lower_bound": (tau_gs * t_gs) / (max(tau_mg, 1.0) * t_mg),
+            }
+            m.close()
+    head = out["3d_128"]
+    line = {
+        "metric": "independent thermal variates/s of the multigrid sampler (1 / (tau_int x time per iteration))",
+        "value": head["mg_variates_per_s"], "unit": "variates/s", "higher_is_better": True, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": "f32+f64",
+        "config": {"workload": "multigrid vs Gauss-Seidel sampler, wall mode and point probe of the x-velocity, "
+                               "2-D 64^2 (FP64) and 3-D 128^3 (FP32 inner, FP64 refinement)",
+                   "tau": "max over the two observables of 1 + 2 sum rho(k); Gauss-Seidel's is truncated at the "
+                          "computed lags (a lower bound)",
+                   "l2": "not flushed: consecutive iterations of one chain, as a sampler runs"},
+        "samplers": out,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
 
@@ -518,6 +608,7 @@ def run_composite(args):
         S.selm_comp_sample(c, cycles_per_sample)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = S.selm_kernel_launches()
     with ClockSampler(torch.cuda.current_device()) as clk:
         for k in range(args.steps):
             flush.fill_(float(k))
@@ -525,6 +616,7 @@ def run_composite(args):
             S.selm_comp_sample(c, cycles_per_sample)
             ev[k][1].record()
         torch.cuda.synchronize()
+    launches = S.selm_kernel_launches() - launches0
     t_total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     value = cells * cycles_per_sample * args.steps / t_total
 
@@ -620,7 +712,7 @@ def run_composite(args):
         "kernel_time_share": {k: round(v["ms"] / tot_ms, 4) for k, v in per_class.items()},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
-        "gpu_launches": None,
+        "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
@@ -645,6 +737,9 @@ def main():
         return
     if args.workload == "composite":
         run_composite(args)
+        return
+    if args.workload == "decorrelation":
+        run_decorrelation(args)
         return
 
     import numpy as np

@@ -26,6 +26,7 @@
 #include "../../include/selm_mg.h"
 #include "selm_handle.h"
 #include "selm_launch.h"
+#include "selm_prof.h"
 
 using namespace selm;
 
@@ -42,6 +43,9 @@ struct selm_batch {
   cudaGraphExec_t g_cycle = nullptr;  // one V-cycle + update + next residual norm
   cudaGraphExec_t g_chain = nullptr;  // k stochastic cycles of every chain
   cudaGraphExec_t g_finish = nullptr; // combine, interpolate, move particles
+  // kernels each graph holds: recorded at capture (where nothing runs) and
+  // credited to the launch counter on every replay
+  long long k_start = 0, k_cycle = 0, k_chain = 0, k_finish = 0;
   // arguments baked into the graphs
   std::vector<int> np;
   std::vector<double*> X;
@@ -96,11 +100,12 @@ void drop_graphs(selm_batch* b) {
 
 // Captures fn(i, stream_i) for every system as parallel branches of one graph.
 template <typename Fn>
-selm_status capture(selm_batch* b, Fn fn, cudaGraphExec_t* out) {
+selm_status capture(selm_batch* b, Fn fn, cudaGraphExec_t* out, long long* kernels) {
   if (*out) {
     cudaGraphExecDestroy(*out);
     *out = nullptr;
   }
+  const long long l0 = prof::g_launches.load();
   BCK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
   selm_status st = SELM_OK;
   cudaError_t ce = cudaEventRecord(b->fork, b->origin);
@@ -114,6 +119,8 @@ selm_status capture(selm_batch* b, Fn fn, cudaGraphExec_t* out) {
   }
   cudaGraph_t graph = nullptr;
   cudaError_t ce2 = cudaStreamEndCapture(b->origin, &graph);
+  *kernels = prof::g_launches.load() - l0;
+  prof::g_launches.fetch_sub(*kernels);   // recorded, not run
   if (st != SELM_OK || ce != cudaSuccess || ce2 != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
@@ -152,7 +159,7 @@ selm_status build_cycle_graph(selm_batch* b) {
         LST(outer_update(h, h->vel, h->u, h->vel.v[0], s));
         return residual_norm(b, i, s);
       },
-      &b->g_cycle);
+      &b->g_cycle, &b->k_cycle);
 }
 
 selm_status build_graphs(selm_batch* b, const int* np, double* const* X, const double* const* F, double dt,
@@ -178,7 +185,7 @@ selm_status build_graphs(selm_batch* b, const int* np, double* const* X, const d
         LCK(cudaMemcpyAsync(b->host_norm + 2 * i + 1, h->red, sizeof(double), cudaMemcpyDeviceToHost, s));
         return residual_norm(b, i, s);
       },
-      &b->g_start));
+      &b->g_start, &b->k_start));
   BST(build_cycle_graph(b));
   BST(capture(
       b,
@@ -194,7 +201,7 @@ selm_status build_graphs(selm_batch* b, const int* np, double* const* X, const d
         }
         return SELM_OK;
       },
-      &b->g_chain));
+      &b->g_chain, &b->k_chain));
   BST(capture(
       b,
       [&](int i, cudaStream_t s) -> selm_status {
@@ -205,7 +212,7 @@ selm_status build_graphs(selm_batch* b, const int* np, double* const* X, const d
         LCK(launch_em(np[i], h->d.dim, X[i], h->V, s));
         return SELM_OK;
       },
-      &b->g_finish));
+      &b->g_finish, &b->k_finish));
   return SELM_OK;
 }
 
@@ -320,6 +327,7 @@ selm_status selm_batch_step(selm_batch* b, const int* np, double* const* X, cons
   for (int step = 0; step < nsteps; ++step) {
     std::fill(cycles.begin(), cycles.end(), -1);
     BCK(cudaGraphLaunch(b->g_start, st));
+    prof::g_launches.fetch_add(b->k_start);
     BCK(cudaStreamSynchronize(st));
     int cyc = 0;
     while (!all_converged(b, cycles, cyc)) {
@@ -328,18 +336,21 @@ selm_status selm_batch_step(selm_batch* b, const int* np, double* const* X, cons
         return SELM_ENOCONV;
       }
       BCK(cudaGraphLaunch(b->g_cycle, st));
+      prof::g_launches.fetch_add(b->k_cycle);
       BCK(cudaStreamSynchronize(st));
       ++cyc;
       for (selm_mg* h : b->sys) h->total_vcycles += 1;
     }
     if (ncycles_per_step > 0) {
       BCK(cudaGraphLaunch(b->g_chain, st));
+      prof::g_launches.fetch_add(b->k_chain);
       for (selm_mg* h : b->sys) {
         h->cycle += ncycles_per_step;
         h->total_vcycles += ncycles_per_step;
       }
     }
     BCK(cudaGraphLaunch(b->g_finish, st));
+    prof::g_launches.fetch_add(b->k_finish);
     for (int i = 0; i < b->n; ++i) b->sys[i]->last_solve_cycles = cycles[i];
   }
   if (solve_cycles)
@@ -363,6 +374,7 @@ selm_status selm_batch_autotune(selm_batch* b, int* chosen_cluster, void* stream
     BCK(cudaGraphLaunch(b->g_cycle, st));   // warm-up
     BCK(cudaEventRecord(e0, st));
     for (int r = 0; r < 3; ++r) BCK(cudaGraphLaunch(b->g_cycle, st));
+    prof::g_launches.fetch_add(4 * b->k_cycle);
     BCK(cudaEventRecord(e1, st));
     BCK(cudaEventSynchronize(e1));
     float ms = 0.0f;

@@ -1123,9 +1123,12 @@ selm_status chain_cycle(selm_comp* C, const unsigned long long* cyc, cudaStream_
   Sys& s = C->mg->vel;
   const CompGeo& G = C->geo;
   if (G.fx % 8 == 0 && G.bx % 8 == 0) {
+    {
+      prof::Scope ps(SELM_K_OUTER_RESIDUAL, st);
+      k_comp_residual_df_patch<<<cgrid((long long)G.fz * G.fy * (G.fx >> 3) * G.ncomp), kCBlock, 0, st>>>(
+          G, C->xh, C->xl, (float*)s.b[0]);
+    }
     prof::Scope ps(SELM_K_OUTER_RESIDUAL, st);
-    k_comp_residual_df_patch<<<cgrid((long long)G.fz * G.fy * (G.fx >> 3) * G.ncomp), kCBlock, 0, st>>>(
-        G, C->xh, C->xl, (float*)s.b[0]);
     k_comp_residual_df_base<<<cgrid((long long)(G.bz - G.K) * G.by * (G.bx >> 3) * G.ncomp), kCBlock, 0, st>>>(
         G, C->xh, C->xl, (float*)s.b[1]);
   } else {
@@ -1269,7 +1272,10 @@ selm_status selm_comp_solve(selm_comp* C, double* z, const double* b, double tol
   cudaStream_t st = CS(stream);
   const CompGeo& G = C->geo;
   CCK(cudaMemsetAsync(C->red, 0, 2 * sizeof(double), st));
-  k_comp_norm2<<<cgrid(G.N0 + G.N1), kCBlock, 0, st>>>(G, b, C->red);
+  {
+    prof::Scope ps(SELM_K_OTHER, st);
+    k_comp_norm2<<<cgrid(G.N0 + G.N1), kCBlock, 0, st>>>(G, b, C->red);
+  }
   CCK(cudaGetLastError());
   double bn2 = 0.0;
   selm_status r = read_slot(C, 0, &bn2, st);
@@ -1364,6 +1370,7 @@ selm_status selm_comp_sample(selm_comp* C, int ncycles, double* xi_out, void* st
   }
   if (xi_out) {
     if (C->xh) {
+      prof::Scope ps(SELM_K_OTHER, st);
       k_comp_df_to_f64<<<cgrid(C->geo.N0 + C->geo.N1), kCBlock, 0, st>>>(C->geo, C->xh, C->xl, xi_out);
       CCK(cudaGetLastError());
     } else {

@@ -68,8 +68,10 @@ def test_batch_matches_systems_alone(S):
     X = [torch.tensor(x, device="cuda") for x in Xs]
     F = [torch.tensor(f, device="cuda") for f in Fs]
     cycles = S.selm_batch_step(b, X, F, 1e-3, 1, 2)
+    l0 = S.selm_kernel_launches()   # the second step replays the graphs the first captured
     cycles += S.selm_batch_step(b, X, F, 1e-3, 1, 2)
     torch.cuda.synchronize()
+    assert S.selm_kernel_launches() - l0 > 4 * len(SYSTEMS)   # replays credit the kernels they hold
     assert all(1 <= c <= 15 for c in cycles)
     want = _alone(S, descs, Xs, Fs, 2)
     for i, (x, w, x0) in enumerate(zip(X, want, Xs)):

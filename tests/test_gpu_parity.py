@@ -373,18 +373,24 @@ def test_full_size_128_cycle_fp32():
 def test_graph_replay_matches_direct_launches(dim, n, levels):
     """Solve V-cycles replayed from captured CUDA graphs (the default) give the
     solve of direct launches bit for bit, with the same cycle count (128^3:
-    the cooperative level and the engine inside the graph)."""
+    the cooperative level and the engine inside the graph).  The kernel
+    launch counter credits each replay with the kernels its graph holds, so
+    both forms count the same launches."""
     outs = []
     for graphs in (1, 0):
         m, osys, dt, tol = make(dim, n, levels, "fp32")
         S.selm_mg_set_option(m.h, S.SELM_OPT_GRAPHS, graphs)
-        b0 = selm_inputs.fields(osys.shapes(0), seed=16)
+        b0 = to_dev(m.h, selm_inputs.fields(osys.shapes(0), seed=16), torch.float64)
         z = empty(m.h, torch.float64)
-        cycles, res = S.selm_mg_fac_solve(m.h, 0, z, to_dev(m.h, b0, torch.float64), 1e-10, 50)
+        torch.cuda.synchronize()
+        l0 = S.selm_kernel_launches()
+        cycles, res = S.selm_mg_fac_solve(m.h, 0, z, b0, 1e-10, 50)
+        launches = S.selm_kernel_launches() - l0
         assert res <= 1e-10 and cycles >= 3   # a capture and replays took part
-        outs.append((cycles, z.cpu().numpy()))
+        outs.append((cycles, z.cpu().numpy(), launches))
     assert outs[0][0] == outs[1][0]
     assert np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2] and outs[0][2] > 3 * levels
 
 
 @pytest.mark.parametrize("coop", [1, 2])

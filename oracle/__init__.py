@@ -20,6 +20,8 @@ multigrid   V-cycle (Algorithm 3), FAC iteration (Algorithm 1), coarsest step
 coupling    Peskin 4-point interpolation Gamma and spreading Gamma^T (Section 2.1)
 projection  MAC divergence / gradient and the discrete projection (Section 4)
 selm        mobility, thermal field, Euler-Maruyama step (Algorithm 4)
+composite   composite (refined-patch) grid, Algorithms 1-2
+decorrelation  lag correlations of the multigrid and Gauss-Seidel samplers (Section 5)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test (closed
 forms, exact invariance identities, dense direct references); none is
@@ -27,3 +29,4 @@ forms, exact invariance identities, dense direct references); none is
 """
 
 from . import philox, grid, gibbs, multigrid, coupling, projection, selm  # noqa: F401
+from . import composite, decorrelation  # noqa: F401

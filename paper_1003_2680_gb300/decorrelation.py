@@ -63,8 +63,11 @@ def point_probe(h):
     return phi
 
 
-def covariance_image(h, phi, tol=1e-12, max_cycles=200):
-    """w = A^-1 phi on the device (FP64), by the library's FAC solve."""
+def covariance_image(h, phi, tol=1e-10, max_cycles=100):
+    """w = A^-1 phi on the device (FP64), by the library's FAC solve.  The
+    default tolerance is the solve's: for a smooth phi on a large grid the FP64
+    residual b - Aw itself rounds at ~1e-16 |A||w| / |b| (about 2e-12 for the
+    wall mode at 128^3), so much tighter tolerances are not reachable."""
     b = torch.tensor(phi, dtype=torch.float64, device="cuda")
     w = torch.zeros_like(b)
     cycles, res = S.selm_mg_fac_solve(h, S.SELM_SYS_VELOCITY, w, b, tol, max_cycles)

@@ -44,7 +44,7 @@ def test_lag_correlations_match_oracle(prec, dim, n, levels):
         assert np.array_equal(phi_lib, flatten(phi_or))      # same observable, same layout
         w_or = OD.covariance_image(mg, phi_or)
         wn = flatten(w_or)
-        w = D.covariance_image(m.h, phi_lib)       # solved to 1e-12: error <= cond(A) x 1e-12
+        w = D.covariance_image(m.h, phi_lib, tol=1e-12)   # error <= cond(A) x 1e-12
         assert np.linalg.norm(w.cpu().numpy() - wn) / np.linalg.norm(wn) < 1e-9
         w = torch.tensor(wn, device="cuda")        # both curves from the same start
         r_mg = D.lag_correlations_mg(m.h, phi_lib, 4, w)
@@ -60,8 +60,8 @@ def test_bench_size_properties():
     m = S.SelmMG(dim=3, n=n, precision=1, seed=0, instance=0)
     phi = D.wall_mode(m.h, n)
     lam = (1.0 / n) * 4.0 * np.sin(np.pi / (2 * n)) ** 2   # mu h^(d-2) x DST-II eigenvalue
-    w = D.covariance_image(m.h, phi)
-    assert np.abs(w.cpu().numpy() - phi / lam).max() < 1e-7 * np.abs(phi / lam).max()
+    w = D.covariance_image(m.h, phi)                        # to the solve's 1e-10
+    assert np.abs(w.cpu().numpy() - phi / lam).max() < 1e-6 * np.abs(phi / lam).max()
     r_mg = D.lag_correlations_mg(m.h, phi, 3, w)
     assert D.lags_below(r_mg) == 1
     r_gs = D.lag_correlations_gs(m.h, phi, 30, w)

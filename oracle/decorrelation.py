@@ -11,9 +11,11 @@ the measure is fixed here (reading R20):
 
 * Each sampler is an affine iteration z' = M z + N b + B n whose invariant
   law is N(A^-1 b, C), C = A^-1 (Section 3.1 for Gauss-Seidel, Section 3.2
-  for the multigrid cycle).  In its stationary state with b = 0 the lag-k
-  covariance is Cov(z_k, z_0) = M^k C, because z_k = M^k z_0 plus noise
-  drawn after z_0.
+  for the multigrid cycle).  Section 3.1 gives the lag covariance of the
+  stochastic iteration by the recurrence C^(0,k) = R^k C^(0,0) (and bounds
+  its norm by ||R||^k ||C^(0,0)||); the same argument holds for the
+  multigrid cycle's map M: z_k is M^k z_0 plus noise drawn after z_0, so in
+  the stationary state with b = 0, Cov(z_k, z_0) = M^k C.
 * For a linear observable phi^T z the lag-k correlation is therefore
       rho(k) = phi^T M^k C phi / phi^T C phi.
   It is computed without sampling: w = C phi by a solve, then k noiseless

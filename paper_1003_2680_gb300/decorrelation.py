@@ -4,7 +4,8 @@ Section 5 judges a sampler by how strongly its variates stay correlated after
 a given number of iterations, and contrasts the multigrid sampler (O(1)
 iterations) with stochastic Gauss-Seidel (correlated after many).  For a
 sampler z' = M z + N b + B n with invariant law N(0, A^-1) (b = 0) and a
-linear observable phi, the lag-k correlation is
+linear observable phi, the lag-k covariance follows Section 3.1's recurrence
+C^(0,k) = M^k C^(0,0) with C^(0,0) = A^-1, so the lag-k correlation is
 
     rho(k) = phi^T M^k A^-1 phi / phi^T A^-1 phi,
 

@@ -182,3 +182,85 @@ def test_invalid_descriptors(S):
         assert S.selm_comp_footprint(d) == 0
         with pytest.raises(S.SelmError):
             S.selm_comp_create(d)
+
+
+# ---- the benchmark's size: 256^3 base, bottom 32 rows refined (512 x 512 x 64 patch),
+# three components, FP32 inner cycles with FP64 refinement -----------------------------
+
+BENCH = dict(dim=3, n=256, K=32, ncomp=3)
+
+
+def _blocks(S, c, ncomp):
+    """(part, (nz, ny, nx), offset) of every patch and base block of a composite vector."""
+    out = []
+    for comp in range(ncomp):
+        for part in (0, 1):
+            (nx, ny, nz), off, _ = S.selm_comp_layout(c, part, comp)
+            out.append((part, (nz, ny, nx), off))
+    return out
+
+
+def test_bench_size_linear_field_closed_form(S):
+    """c = z (cell-centre heights): r = -A z vanishes on every composite row but
+    the top-wall base rows, where it is -mu H^(d-2) (the coarse-fine gradient
+    rule is exact on linear fields); values placed in covered base rows must
+    not reach any row, and covered rows of r are 0."""
+    n, K, mu = BENCH["n"], BENCH["K"], 1.0
+    H = 1.0 / n
+    c = S.selm_comp_create(S.make_comp_desc(precision=S.SELM_FP32_REFINE64, mu=mu, seed=0, instance=0, **BENCH))
+    z = torch.empty(S.selm_comp_size(c), dtype=torch.float64, device="cuda")
+    for part, (nz, ny, nx), off in _blocks(S, c, BENCH["ncomp"]):
+        k = torch.arange(nz, dtype=torch.float64, device="cuda")
+        zk = (2 * k + 3) * H / 4 if part == 0 else torch.where(k < K, 7.0, (k + 1) * H)
+        z[off:off + nz * ny * nx] = zk[:, None].expand(nz, ny * nx).reshape(-1)
+    r = torch.empty_like(z)
+    S.selm_comp_residual(c, z, None, r, want_norm=False)
+    torch.cuda.synchronize()
+    for part, (nz, ny, nx), off in _blocks(S, c, BENCH["ncomp"]):
+        blk = r[off:off + nz * ny * nx].view(nz, ny, nx)
+        if part == 0:
+            assert blk.abs().max().item() < 1e-12 * H
+        else:
+            assert torch.count_nonzero(blk[:K]).item() == 0
+            assert blk[K:nz - 1].abs().max().item() < 1e-12 * H
+            assert (blk[nz - 1] + mu * H).abs().max().item() < 1e-12 * H
+    S.selm_comp_destroy(c)
+
+
+def _roll(S, c, vec, s):
+    """Shift a composite vector by s base cells (2s patch cells) along x and y."""
+    out = torch.empty_like(vec)
+    for part, (nz, ny, nx), off in _blocks(S, c, BENCH["ncomp"]):
+        t = s if part == 1 else 2 * s
+        blk = vec[off:off + nz * ny * nx].view(nz, ny, nx)
+        out[off:off + nz * ny * nx] = torch.roll(blk, shifts=(t, t), dims=(1, 2)).reshape(-1)
+    return out
+
+
+def test_bench_size_fac_cycle_is_translation_equivariant(S):
+    """Along the periodic axes the composite grid is translation invariant, so
+    one deterministic FAC cycle commutes with a shift that keeps every level's
+    colouring (192 base cells: a multiple of 2 on each smoothed level down to
+    the 8^3 one, and of 3).  Every kernel of the cycle runs at the
+    benchmark's size and launch shapes; an index or stride slip breaks the
+    identity at O(1).  Only the coarsest dense solve sees a permuted vector
+    (rounding), so the corrections agree to the FP32 tolerance."""
+    c = S.selm_comp_create(S.make_comp_desc(precision=S.SELM_FP32_REFINE64, seed=0, instance=0, **BENCH))
+    N = S.selm_comp_size(c)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1234)
+    z0 = torch.randn(N, dtype=torch.float64, device="cuda", generator=g)
+    b = torch.randn(N, dtype=torch.float64, device="cuda", generator=g)
+    for part, (nz, ny, nx), off in _blocks(S, c, BENCH["ncomp"]):
+        if part == 1:   # covered base rows are not unknowns
+            z0[off:off + BENCH["K"] * ny * nx] = 0.0
+            b[off:off + BENCH["K"] * ny * nx] = 0.0
+    z = z0.clone()
+    S.selm_comp_fac_cycle(c, z, b, 0, 0)
+    zs = _roll(S, c, z0, 192)
+    S.selm_comp_fac_cycle(c, zs, _roll(S, c, b, 192), 0, 0)
+    torch.cuda.synchronize()
+    d = _roll(S, c, z - z0, 192)
+    ds = zs - _roll(S, c, z0, 192)
+    assert (torch.linalg.vector_norm(ds - d) / torch.linalg.vector_norm(d)).item() < 1e-5
+    S.selm_comp_destroy(c)

@@ -105,3 +105,33 @@ def test_batch_rejects_projection(S):
     d = S.make_desc(dim=3, n=16, projection=S.SELM_PROJ_MAC)
     with pytest.raises(S.SelmError):
         S.selm_batch_create([d])
+
+
+def test_batch_at_benchmark_shapes(S):
+    """Systems of every edge the batched benchmark draws (32..128, FP32 inner
+    cycles with FP64 refinement, 64..2048 particles), with the engine cluster
+    size the autotuner picks, as the benchmark runs them: the batch equals each
+    system advanced alone."""
+    import selm_inputs
+    edges = [128, 96, 64, 48, 32]
+    nps = [2048, 700, 64, 300, 1000]
+    descs = [S.make_desc(dim=3, n=e, kT=0.5 + 0.3 * i, precision=S.SELM_FP32_REFINE64, seed=i, instance=i,
+                         max_particles=2048) for i, e in enumerate(edges)]
+    Xs = [selm_inputs.particles(npart, 3, e, seed=i) for i, (npart, e) in enumerate(zip(nps, edges))]
+    Fs = [selm_inputs.forces(npart, 3, seed=i) for i, npart in enumerate(nps)]
+    b = S.selm_batch_create(descs)
+    S.selm_batch_autotune(b)
+    X = [torch.tensor(x, device="cuda") for x in Xs]
+    F = [torch.tensor(f, device="cuda") for f in Fs]
+    S.selm_batch_step(b, X, F, 1e-3, 2, 2)
+    torch.cuda.synchronize()
+    S.selm_batch_destroy(b)
+    for desc, x, X0, F0 in zip(descs, X, Xs, Fs):
+        h = S.selm_mg_create(desc)
+        Xa = torch.tensor(X0, device="cuda")
+        S.selm_mg_step(h, Xa, torch.tensor(F0, device="cuda"), 1e-3, 2, 2)
+        torch.cuda.synchronize()
+        w = Xa.cpu().numpy()
+        err = np.linalg.norm(x.cpu().numpy() - w) / np.linalg.norm(w - X0)
+        assert err < 1e-5, (desc.n, err)
+        S.selm_mg_destroy(h)

@@ -41,10 +41,10 @@ def _desc(S, dim, n, kT, seed):
                        torch_allocator=False)
 
 
-def _serve(S, budget, slots):
+def _serve(S, budget, slots, requests=REQUESTS):
     srv = S.selm_server_create(budget, slots)
     Xs, Fs = [], []
-    for i, (dim, n, npart, nsteps, kT, seed) in enumerate(REQUESTS):
+    for i, (dim, n, npart, nsteps, kT, seed) in enumerate(requests):
         X = np.ascontiguousarray(selm_inputs.particles(npart, dim, n, seed=seed))
         F = np.ascontiguousarray(selm_inputs.forces(npart, dim, seed=seed))
         Xs.append(X)
@@ -84,3 +84,27 @@ def test_request_larger_than_pool_is_refused(S):
         S.selm_server_submit(srv, _desc(S, 3, 64, 1.0, 0), X, X, 1e-3, 1, 2)
     assert info.value.status == S.SELM_EBUSY
     S.selm_server_destroy(srv)
+
+
+BENCH_REQUESTS = [  # the served benchmark's extremes: 2-D edges to 1024, 3-D to 192, 16..4096 particles
+    (2, 1024, 4096, 2, 1.0, 21),
+    (3, 192, 16, 1, 1.0, 22),
+    (2, 256, 700, 3, 1.0, 23),
+    (3, 32, 2500, 2, 1.0, 24),
+    (3, 128, 300, 1, 1.0, 25),
+]
+
+
+def test_benchmark_shapes_same_alone_and_in_the_mix(S):
+    """The served benchmark's configuration (12 slots, 32 GB pool) on requests
+    of its largest and smallest shapes: every request ends where it ends when
+    served alone."""
+    X_alone, res_alone, _ = _serve(S, budget=32 << 30, slots=1, requests=BENCH_REQUESTS)
+    X_mix, res_mix, st_mix = _serve(S, budget=32 << 30, slots=12, requests=BENCH_REQUESTS)
+    assert all(r["status"] == 0 for r in res_alone + res_mix)
+    assert st_mix["peak_slots"] >= 2
+    X0 = [selm_inputs.particles(npart, d, n, seed=seed) for d, n, npart, _, _, seed in BENCH_REQUESTS]
+    for i, (a, m, x0) in enumerate(zip(X_alone, X_mix, X0)):
+        assert not np.array_equal(a, x0)
+        err = np.linalg.norm(m - a) / np.linalg.norm(a - x0)
+        assert err < 1e-9, (i, err)

@@ -22,6 +22,7 @@ projection  MAC divergence / gradient and the discrete projection (Section 4)
 selm        mobility, thermal field, Euler-Maruyama step (Algorithm 4)
 composite   composite (refined-patch) grid, Algorithms 1-2
 decorrelation  lag correlations of the multigrid and Gauss-Seidel samplers (Section 5)
+composite_mac  divergence, gradient and projection on the composite MAC grid (Section 4)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test (closed
 forms, exact invariance identities, dense direct references); none is
@@ -29,4 +30,4 @@ forms, exact invariance identities, dense direct references); none is
 """
 
 from . import philox, grid, gibbs, multigrid, coupling, projection, selm  # noqa: F401
-from . import composite, decorrelation  # noqa: F401
+from . import composite, composite_mac, decorrelation  # noqa: F401

@@ -1,0 +1,138 @@
+"""Pins for the composite MAC divergence, gradient and projection (oracle/composite_mac.py).
+
+* The two uniform limits (no refined rows, every row refined) equal the
+  uniform MAC projection of oracle/projection.py (pinned on its own).
+* A pressure linear in z: L z vanishes in every cell but the wall cells,
+  where it is +1/h (bottom, fine) and -1/H (top, base) -- the interface
+  rule with the (3/4) H distance is exact on linear fields.
+* A pressure that depends on z only reduces L to a 1-D operator on the
+  column of 2K fine and n-K base cells, built here by hand.
+* sum |c| p (D u) = - sum w_f u_f (G p); V L is symmetric negative
+  semidefinite with the constants as its kernel.
+* P~ is idempotent, W-symmetric, leaves divergence-free fields alone,
+  annihilates gradients, and its output is divergence-free.
+* A planted slip (distance H instead of (3/4) H across the interface) breaks
+  the linear-field closed form.
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import projection
+from oracle.composite_mac import CompositeMAC
+
+
+def _to_components(g, u):
+    """Face vector of a uniform composite (K = 0 or K = n) -> [u, (v), w] arrays."""
+    nz, ny, nx = g.fine_shape if g.K == g.n else g.base_shape
+    comps = [np.zeros((nz, ny, nx)) for _ in range(g.dim - 1)] + [np.zeros((nz - 1, ny, nx))]
+    shape = (nz, ny, nx)
+    off = 0 if g.K == g.n else g.n_fine
+    for f, (axis, plus, minus, area, dist, _) in enumerate(g.faces):
+        k, j, i = np.unravel_index(plus - off, shape)
+        if axis == 2:
+            comps[-1][k - 1, j, i] = u[f]
+        else:
+            comps[axis if g.dim == 3 else 0][k, j, i] = u[f]
+    return comps
+
+
+@pytest.mark.parametrize("dim,n,K", [(2, 8, 0), (2, 8, 8), (3, 4, 0), (3, 4, 4)])
+def test_uniform_limits_match_uniform_projection(dim, n, K):
+    g = CompositeMAC(n, K, dim)
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal(g.n_faces)
+    got = _to_components(g, g.project(u))
+    want = projection.Projector(n if K == 0 else 2 * n, dim, tol=1e-13).project(_to_components(g, u))
+    for a, b in zip(got, want):
+        assert np.abs(a - b).max() < 1e-10
+
+
+@pytest.mark.parametrize("dim,n,K", [(2, 8, 3), (3, 4, 1), (3, 8, 3), (2, 16, 1)])
+def test_linear_pressure_closed_form(dim, n, K):
+    g = CompositeMAC(n, K, dim)
+    z = g.cell_centres()[:, 2]
+    Lz = g.laplacian() @ z
+    want = np.zeros(g.n_cells)
+    nz, ny, nx = g.fine_shape
+    want[:ny * nx] = 1.0 / g.h                               # fine cells on the bottom wall
+    bz, by, bx = g.base_shape
+    want[g.n_cells - by * bx:] = -1.0 / g.H                  # base cells under the top wall
+    assert np.abs(Lz - want).max() < 1e-10 * (1.0 / g.h)
+
+
+def _column_operator(n, K):
+    """1-D L on a z-column: 2K fine cells (height h), then n-K base cells (H)."""
+    H, h = 1.0 / n, 0.5 / n
+    heights = [h] * (2 * K) + [H] * (n - K)
+    N = len(heights)
+    L = np.zeros((N, N))
+    for k in range(N - 1):               # face between cells k and k+1, centres dist apart
+        dist = 0.5 * (heights[k] + heights[k + 1])
+        for a, b in ((k, k + 1), (k + 1, k)):
+            L[a, b] += 1.0 / dist / heights[a]
+            L[a, a] -= 1.0 / dist / heights[a]
+    return L
+
+
+@pytest.mark.parametrize("dim,n,K", [(2, 8, 3), (3, 8, 2), (2, 16, 5)])
+def test_z_only_fields_reduce_to_the_column_operator(dim, n, K):
+    g = CompositeMAC(n, K, dim)
+    rng = np.random.default_rng(2)
+    col = rng.standard_normal(2 * K + n - K)
+    zc = g.cell_centres()[:, 2]
+    heights_z = np.concatenate([(np.arange(2 * K) + 0.5) * g.h, (np.arange(K, n) + 0.5) * g.H])
+    idx = np.array([np.argmin(np.abs(heights_z - z)) for z in zc])
+    p = col[idx]
+    got = g.laplacian() @ p
+    want = (_column_operator(n, K) @ col)[idx]
+    assert np.abs(got - want).max() < 1e-10 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("dim,n,K", [(2, 8, 3), (3, 4, 1)])
+def test_adjoint_symmetric_semidefinite(dim, n, K):
+    g = CompositeMAC(n, K, dim)
+    rng = np.random.default_rng(3)
+    u, p = rng.standard_normal(g.n_faces), rng.standard_normal(g.n_cells)
+    lhs = g.vol @ (p * (g.D @ u))
+    rhs = -(g.weight * u) @ (g.G @ p)
+    assert abs(lhs - rhs) < 1e-13 * (abs(lhs) + 1.0)
+    S = (sp.diags(g.vol) @ g.laplacian()).toarray()
+    assert np.abs(S - S.T).max() < 1e-13 * np.abs(S).max()
+    ev = np.linalg.eigvalsh(S)
+    assert ev[-1] < 1e-12 * np.abs(ev).max() and abs(ev[-1]) < 1e-12 * np.abs(ev).max()
+    assert ev[-2] < -1e-6 * np.abs(ev).max()                  # one-dimensional kernel
+    assert np.abs(S @ np.ones(g.n_cells)).max() < 1e-12 * np.abs(S).max()
+
+
+@pytest.mark.parametrize("dim,n,K", [(2, 8, 3), (3, 4, 1), (3, 8, 3)])
+def test_projection_properties(dim, n, K):
+    g = CompositeMAC(n, K, dim)
+    rng = np.random.default_rng(4)
+    u, v = rng.standard_normal(g.n_faces), rng.standard_normal(g.n_faces)
+    pu, pv = g.project(u), g.project(v)
+    scale = np.abs(u).max()
+    assert np.abs(g.D @ pu).max() < 1e-10 * scale / g.h
+    assert np.abs(g.project(pu) - pu).max() < 1e-11 * scale
+    assert abs((g.weight * pu) @ v - (g.weight * u) @ pv) < 1e-12 * np.abs(g.weight * u).sum() * scale
+    grad = g.G @ rng.standard_normal(g.n_cells)
+    assert np.abs(g.project(grad)).max() < 1e-10 * np.abs(grad).max()
+    flow = np.array([1.0 if f[0] == 0 else 0.0 for f in g.faces])   # uniform x-flow
+    assert np.abs(g.D @ flow).max() < 1e-12
+    assert np.abs(g.project(flow) - flow).max() < 1e-11
+
+
+def test_wrong_interface_distance_is_caught():
+    g = CompositeMAC(8, 3, 2)
+    g.faces = [f if f[4] != 0.75 * g.H else f[:4] + (g.H,) + f[5:] for f in g.faces]
+    g.dist = np.array([f[4] for f in g.faces])
+    g.G = g._gradient()
+    z = g.cell_centres()[:, 2]
+    Lz = g.laplacian() @ z
+    interior = np.ones(g.n_cells, bool)
+    nz, ny, nx = g.fine_shape
+    interior[:ny * nx] = False
+    bz, by, bx = g.base_shape
+    interior[g.n_cells - by * bx:] = False
+    assert np.abs(Lz[interior]).max() > 1.0

@@ -1,7 +1,8 @@
 """Composite MAC grid: divergence, gradient and projection across a refined slab.
 
-TEST INFRASTRUCTURE ONLY (see the package header).  First piece of the
-staggered composite grid with the projection: the pressure side.
+TEST INFRASTRUCTURE ONLY (see the package header).  The staggered composite
+grid with the projection: divergence, gradient, the projection (reading
+R21) and the velocity operators of the three components (reading R22).
 
 Geometry (the refined-slab reading of the composite benchmark, with the MAC
 staggering of Section 4): the unit box, periodic in x (and y in 3-D), walls
@@ -56,7 +57,7 @@ class CompositeMAC:
         self.n_cells = self.n_fine + int(np.prod(self.base_shape))
         self.vol = np.concatenate([np.full(self.n_fine, self.h ** dim),
                                    np.full(self.n_cells - self.n_fine, self.H ** dim)])
-        self.faces = []          # (axis, plus cell, [(minus cell, share)], area, dist, position)
+        self.faces = []          # (axis, plus cell, [(minus cell, share)], area, dist, key)
         self._build_faces()
         self.n_faces = len(self.faces)
         self.area = np.array([f[3] for f in self.faces])
@@ -93,45 +94,53 @@ class CompositeMAC:
         return out
 
     # -- faces -------------------------------------------------------------
+    def _add_face(self, key, plus, minus, area, dist):
+        self.face_of[key] = len(self.faces)
+        self.faces.append((key[0], plus, minus, area, dist, key))
+
     def _build_faces(self):
+        """Faces keyed (axis, level, k, j, i): level 'f' fine, 'c' base, 'i' the
+        interface; (k, j, i) are the plus cell's indices at that level (for
+        the interface, k = K)."""
         d, h, H, K, n = self.dim, self.h, self.H, self.K, self.n
         fa, Ha = h ** (d - 1), H ** (d - 1)
         nz, ny, nx = self.fine_shape
         bz, by, bx = self.base_shape
+        self.face_of = {}
         # periodic axes: the face at the low side of each cell, between its
         # left neighbour (minus) and the cell (plus)
         for m in range(nz):
             for q in range(ny):
                 for p in range(nx):
                     c = self.fine_cell(m, q, p)
-                    self.faces.append((0, c, [(self.fine_cell(m, q, p - 1), 1.0)], fa, h, (p * h, q, m)))
+                    self._add_face((0, "f", m, q, p), c, [(self.fine_cell(m, q, p - 1), 1.0)], fa, h)
                     if d == 3:
-                        self.faces.append((1, c, [(self.fine_cell(m, q - 1, p), 1.0)], fa, h, (p, q * h, m)))
+                        self._add_face((1, "f", m, q, p), c, [(self.fine_cell(m, q - 1, p), 1.0)], fa, h)
         for j in range(K, n):
             for l in range(by):
                 for i in range(bx):
                     c = self.base_cell(j, l, i)
-                    self.faces.append((0, c, [(self.base_cell(j, l, i - 1), 1.0)], Ha, H, (i * H, l, j)))
+                    self._add_face((0, "c", j, l, i), c, [(self.base_cell(j, l, i - 1), 1.0)], Ha, H)
                     if d == 3:
-                        self.faces.append((1, c, [(self.base_cell(j, l - 1, i), 1.0)], Ha, H, (i, l * H, j)))
+                        self._add_face((1, "c", j, l, i), c, [(self.base_cell(j, l - 1, i), 1.0)], Ha, H)
         # wall-normal axis: interior faces of the slab, the interface, the base
         for m in range(1, nz):
             for q in range(ny):
                 for p in range(nx):
-                    self.faces.append((2, self.fine_cell(m, q, p), [(self.fine_cell(m - 1, q, p), 1.0)], fa, h,
-                                       (p, q, m * h)))
+                    self._add_face((2, "f", m, q, p), self.fine_cell(m, q, p), [(self.fine_cell(m - 1, q, p), 1.0)],
+                                   fa, h)
         if 0 < K < n:
             kids = 2 ** (d - 1)
             for l in range(by):
                 for i in range(bx):
                     below = [(self.fine_cell(nz - 1, 2 * l + a if d == 3 else 0, 2 * i + c), 1.0 / kids)
                              for a in range(2 if d == 3 else 1) for c in range(2)]
-                    self.faces.append((2, self.base_cell(K, l, i), below, Ha, 0.75 * H, (i, l, K * H)))
+                    self._add_face((2, "i", K, l, i), self.base_cell(K, l, i), below, Ha, 0.75 * H)
         for j in range(K + 1, n):
             for l in range(by):
                 for i in range(bx):
-                    self.faces.append((2, self.base_cell(j, l, i), [(self.base_cell(j - 1, l, i), 1.0)], Ha, H,
-                                       (i, l, j * H)))
+                    self._add_face((2, "c", j, l, i), self.base_cell(j, l, i), [(self.base_cell(j - 1, l, i), 1.0)],
+                                   Ha, H)
 
     def _divergence(self):
         rows, cols, vals = [], [], []
@@ -179,3 +188,158 @@ class CompositeMAC:
     def project(self, u):
         """P~ u = u - G phi, L phi = D u."""
         return u - self.G @ self.pressure_solve(self.D @ u)
+
+    def face_positions(self):
+        """(x, y, z) of every velocity node (the centre of its face; y = 0 in 2-D)."""
+        out = np.zeros((self.n_faces, 3))
+        for f, (axis, plus, minus, area, dist, key) in enumerate(self.faces):
+            _, lev, k, j, i = key
+            s = self.h if lev == "f" else self.H
+            pos = [(i + 0.5) * s, (j + 0.5) * s, (k + 0.5) * s]
+            pos[axis] -= 0.5 * s                  # the plus cell's low face
+            if lev == "i":
+                pos[2] = self.K * self.H
+            if self.dim == 2:
+                pos[1] = 0.0
+            out[f] = pos
+        return out
+
+    # -- velocity operator ---------------------------------------------------
+    def interface_groups(self, a):
+        """Coarse-fine groups of component a across the interface: (base node,
+        [(fine node, omega)], distance between the two rows of nodes).  omega is
+        the part of the base node's box face covered by the fine node's box
+        face: (1/4, 1/2, 1/4) along the component's own periodic axis (its
+        nodes are faces, the base face spans two fine cells), 1/2 across a cell
+        axis, and 1/2^(d-1) for the wall-normal component (cell-type along x
+        and y)."""
+        d, h, H, K, n = self.dim, self.h, self.H, self.K, self.n
+        nz, ny, nx = self.fine_shape
+        bz, by, bx = self.base_shape
+        F = self.face_of
+        out = []
+        if not 0 < K < n:
+            return out
+        cross = [(e, 0.5) for e in range(2)] if d == 3 else [(0, 1.0)]
+        for j in range(by):
+            for i in range(bx):
+                fine = []
+                if a == 2:
+                    for e, we in cross:
+                        for t in range(2):
+                            fine.append((F[(2, "f", nz - 1, (2 * j + e) if d == 3 else 0, 2 * i + t)], 0.5 * we))
+                    out.append((F[(2, "i", K, j, i)], fine, h))
+                    continue
+                for dt, wt in ((-1, 0.25), (0, 0.5), (1, 0.25)):
+                    for e, we in cross:
+                        if a == 0:
+                            key = (0, "f", nz - 1, (2 * j + e) % ny, (2 * i + dt) % nx)
+                        else:
+                            key = (1, "f", nz - 1, (2 * j + dt) % ny, (2 * i + e) % nx)
+                        fine.append((F[key], wt * we))
+                out.append((F[(a, "c", K, j, i)], fine, 0.75 * H))
+        return out
+
+    def velocity_operator(self, mu=1.0):
+        """A = -mu V L on the face unknowns, one composite operator per component
+        (reading R22), assembled from its energy form
+
+            u^T A u = mu sum_pairs (area / dist) (u_a - u_b)^2
+                    + mu sum_walls (area / dist) u^2
+                    + mu sum_groups (area_c / dist) (u_c - sum_f omega_f u_f)^2.
+
+        Each velocity node owns the box between the centres of the two cells
+        its face separates (along the face normal) and its cell's extent along
+        the other axes.  Pairs are nodes of one level whose boxes share a face
+        (area of the shared face, distance between the nodes).  A wall at a
+        box face sets the node value against 0 at the wall (distance from the
+        node to the wall).  Across the refinement interface a base node c
+        faces the fine nodes under its box; omega_f is the part of c's box face
+        that fine node f's box face covers (the flux-sum rule of Eq.
+        equ_def_discr_div), and dist is the distance between the two rows of
+        nodes: (3/4) H for the x and y components, as in Eq. equ_def_discr_grad,
+        and h for the wall-normal component (its interface node sits on the
+        interface).  For cell-centred components this is the paper's rule."""
+        d, h, H, K, n = self.dim, self.h, self.H, self.K, self.n
+        nz, ny, nx = self.fine_shape
+        bz, by, bx = self.base_shape
+        F = self.face_of
+        rows, cols, vals = [], [], []
+
+        def term(weight, coeffs):
+            for a, ca in coeffs:
+                for b, cb in coeffs:
+                    rows.append(a)
+                    cols.append(b)
+                    vals.append(mu * weight * ca * cb)
+
+        def pair(weight, a, b):
+            term(weight, [(a, 1.0), (b, -1.0)])
+
+        axes = [0, 1] if d == 3 else [0]
+        # x and y components: cell-type across the walls
+        for a in axes:
+            o = 1 - a if d == 3 else None            # the other periodic axis
+            for lev, s, rows_k, shape in (("f", h, range(nz), (ny, nx)), ("c", H, range(K, n), (by, bx))):
+                area = s ** (d - 1)
+                for k in rows_k:
+                    for j in range(shape[0]):
+                        for i in range(shape[1]):
+                            me = F[(a, lev, k, j, i)]
+                            # along the component's own axis (through the cell), then the other one
+                            nxt = (k, j, i + 1) if a == 0 else (k, j + 1, i)
+                            pair(area / s, me, F[(a, lev, nxt[0], nxt[1] % shape[0], nxt[2] % shape[1])])
+                            if o is not None:
+                                nb = (k, j, i + 1) if o == 0 else (k, j + 1, i)
+                                pair(area / s, me, F[(a, lev, nb[0], nb[1] % shape[0], nb[2] % shape[1])])
+                            top = nz - 1 if lev == "f" else n - 1
+                            if k < top:
+                                pair(area / s, me, F[(a, lev, k + 1, j, i)])
+                            if lev == "f" and k == 0 or lev == "c" and k == 0:
+                                term(area / (s / 2), [(me, 1.0)])           # bottom wall
+                            if lev == "c" and k == n - 1 or lev == "f" and k == nz - 1 and K == n:
+                                term(area / (s / 2), [(me, 1.0)])           # top wall
+            for c, fine, dist in self.interface_groups(a):
+                term(H ** (d - 1) / dist, [(c, 1.0)] + [(f, -w) for f, w in fine])
+        # wall-normal component: vertex-type across the walls
+        a = 2
+        nodes = []                                  # (key, spacing along x/y, box height, z)
+        for m in range(1, nz):
+            for q in range(ny):
+                for p in range(nx):
+                    nodes.append(((2, "f", m, q, p), h, h, m * h))
+        if 0 < K < n:
+            for l in range(by):
+                for i in range(bx):
+                    nodes.append(((2, "i", K, l, i), H, 0.75 * H, K * H))
+        for j in range(K + 1, n):
+            for l in range(by):
+                for i in range(bx):
+                    nodes.append(((2, "c", j, l, i), H, H, j * H))
+        for key, s, height, z in nodes:
+            me = F[key]
+            lev, k, j, i = key[1], key[2], key[3], key[4]
+            dims = (ny, nx) if lev == "f" else (by, bx)
+            side = s ** (d - 2) * height                    # area of a box face normal to x or y
+            pair(side / s, me, F[(2, lev, k, j, (i + 1) % dims[1])])
+            if d == 3:
+                pair(side / s, me, F[(2, lev, k, (j + 1) % dims[0], i)])
+            area = s ** (d - 1)                             # box face normal to z
+            if lev == "f":
+                if k + 1 < nz:
+                    pair(area / h, me, F[(2, "f", k + 1, j, i)])
+                elif K == n:
+                    term(area / h, [(me, 1.0)])                                 # top wall
+                if k == 1:
+                    term(area / h, [(me, 1.0)])                                 # bottom wall
+            else:
+                up = (2, "c", (K + 1 if lev == "i" else k + 1), j, i)
+                if up in F:
+                    pair(area / H, me, F[up])
+                else:
+                    term(area / H, [(me, 1.0)])                                 # top wall
+                if lev == "c" and k == 1:
+                    term(area / H, [(me, 1.0)])                                 # bottom wall (K = 0)
+        for c, fine, dist in self.interface_groups(2):   # interface node against the fine row below it
+            term(H ** (d - 1) / dist, [(c, 1.0)] + [(f, -w) for f, w in fine])
+        return sp.csr_matrix((vals, (rows, cols)), shape=(self.n_faces, self.n_faces))

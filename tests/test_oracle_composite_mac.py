@@ -136,3 +136,125 @@ def test_wrong_interface_distance_is_caught():
     bz, by, bx = g.base_shape
     interior[g.n_cells - by * bx:] = False
     assert np.abs(Lz[interior]).max() > 1.0
+
+
+# ---- velocity operators on the staggered composite grid (reading R22) ----
+
+from oracle import grid  # noqa: E402
+
+
+def _uniform_velocity(g, mu):
+    """Dense uniform velocity operator of grid.py, mapped to the composite's face order."""
+    N = g.n if g.K == 0 else 2 * g.n
+    osys = grid.velocity_system(N, g.dim, mu=mu, levels=1)
+    comps = [cl.dense() for cl in osys.levels[0]]
+    shapes = [cl.shape for cl in osys.levels[0]]
+    index = []
+    for axis, plus, minus, area, dist, key in g.faces:
+        _, lev, k, j, i = key
+        c = axis if g.dim == 3 else (0 if axis == 0 else 1)
+        nz, ny, nx = shapes[c]
+        kk = k - 1 if axis == 2 else k
+        index.append((c, (kk * ny + (j if g.dim == 3 else 0)) * nx + i))
+    A = np.zeros((g.n_faces, g.n_faces))
+    for a, (ca, ia) in enumerate(index):
+        for b, (cb, ib) in enumerate(index):
+            if ca == cb:
+                A[a, b] = comps[ca][ia, ib]
+    return A
+
+
+@pytest.mark.parametrize("dim,n,K", [(2, 8, 0), (2, 8, 8), (3, 4, 0), (3, 4, 4)])
+def test_velocity_uniform_limits_match_grid_operator(dim, n, K):
+    g = CompositeMAC(n, K, dim)
+    A = g.velocity_operator(mu=0.7).toarray()
+    assert np.abs(A - _uniform_velocity(g, 0.7)).max() < 1e-13 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("dim,n,K", [(2, 8, 3), (3, 4, 1), (3, 8, 3), (2, 16, 1)])
+def test_velocity_linear_field_closed_form(dim, n, K):
+    # u = z: every row vanishes but the rows under the top wall, where the
+    # cell-type components give 2 mu H^(d-2) and the wall-normal one mu H^(d-2)
+    mu = 1.3
+    g = CompositeMAC(n, K, dim)
+    pos = g.face_positions()
+    Az = g.velocity_operator(mu) @ pos[:, 2]
+    want = np.zeros(g.n_faces)
+    for f, (axis, plus, minus, area, dist, key) in enumerate(g.faces):
+        top = abs(pos[f, 2] - (1.0 - (g.H if axis == 2 else 0.5 * g.H))) < 1e-12
+        if top:
+            want[f] = mu * g.H ** (dim - 2) * (1.0 if axis == 2 else 2.0)
+    assert np.abs(Az - want).max() < 1e-12 * mu * g.H ** (dim - 2)
+
+
+def _column(positions):
+    """1-D operator on nodes at the given heights, Dirichlet 0 at z = 0 and z = 1:
+    row k = sum over the neighbours of (u_k - u_nb) / distance."""
+    zs = [0.0] + list(positions) + [1.0]
+    N = len(positions)
+    A = np.zeros((N, N))
+    for k in range(N):
+        for nb in (k - 1, k + 1):
+            dist = abs(zs[k + 1] - zs[nb + 1])
+            A[k, k] += 1.0 / dist
+            if 0 <= nb < N:
+                A[k, nb] -= 1.0 / dist
+    return A
+
+
+@pytest.mark.parametrize("dim,n,K", [(2, 8, 3), (3, 8, 2), (2, 16, 5), (3, 4, 1)])
+def test_velocity_z_only_fields_reduce_to_column_operators(dim, n, K):
+    # For a field that varies along z only, a row of A is the node's box face
+    # area times a row of the 1-D operator on its column (distances between
+    # consecutive node heights, walls at 0 and 1).
+    g = CompositeMAC(n, K, dim)
+    pos = g.face_positions()
+    A = g.velocity_operator(1.0)
+    rng = np.random.default_rng(5)
+    for axis in ([0, 1] if dim == 3 else [0]) + [2]:
+        sel = np.array([f[0] == axis for f in g.faces])
+        heights = np.unique(np.round(pos[sel, 2], 12))
+        col = rng.standard_normal(heights.size)
+        u = np.zeros(g.n_faces)
+        k_of = np.searchsorted(heights, np.round(pos[:, 2], 12))
+        u[sel] = col[k_of[sel]]
+        got = (A @ u)[sel]
+        area = np.where(pos[sel, 2] < g.K * g.H - 1e-12, g.h, g.H) ** (dim - 1)
+        want = area * (_column(heights) @ col)[k_of[sel]]
+        assert np.abs(got - want).max() < 1e-11 * np.abs(want).max(), axis
+
+
+@pytest.mark.parametrize("dim,n,K", [(2, 8, 3), (3, 4, 1)])
+def test_interface_group_weights(dim, n, K):
+    # each group's weights sum to 1 and reproduce its base node's position along
+    # x and y (first moments, periodic distances); every fine node of the row
+    # below is covered by the groups with its own box-face area
+    g = CompositeMAC(n, K, dim)
+    pos = g.face_positions()
+    for axis in ([0, 1] if dim == 3 else [0]) + [2]:
+        cover = {}
+        for c, fine, dist in g.interface_groups(axis):
+            w = np.array([x for _, x in fine])
+            assert abs(w.sum() - 1.0) < 1e-15
+            for ax in ([0, 1] if dim == 3 else [0]):
+                dx = np.array([(pos[f, ax] - pos[c, ax] + 0.5) % 1.0 - 0.5 for f, _ in fine])
+                assert abs(w @ dx) < 1e-15
+            for f, x in fine:
+                cover[f] = cover.get(f, 0.0) + x * g.H ** (dim - 1)
+        assert cover and all(abs(v - g.h ** (dim - 1)) < 1e-15 for v in cover.values())
+
+
+@pytest.mark.parametrize("dim,n,K", [(2, 8, 3), (3, 4, 1)])
+def test_velocity_operator_symmetric_positive_definite(dim, n, K):
+    A = CompositeMAC(n, K, dim).velocity_operator(0.9).toarray()
+    assert np.abs(A - A.T).max() == 0.0
+    assert np.linalg.eigvalsh(A)[0] > 0.0
+
+
+def test_velocity_wrong_group_distance_is_caught():
+    g = CompositeMAC(8, 3, 2)
+    orig = g.interface_groups
+    g.interface_groups = lambda a: [(c, f, g.H if a != 2 else d) for c, f, d in orig(a)]
+    Az = g.velocity_operator(1.0) @ g.face_positions()[:, 2]
+    below_top = g.face_positions()[:, 2] < 1.0 - g.H
+    assert np.abs(Az[below_top]).max() > 0.2 * g.H          # (1/4) H^(d-1) at the interface rows

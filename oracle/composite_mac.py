@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see the package header).  The staggered composite
 grid with the projection: divergence, gradient, the projection (reading
-R21) and the velocity operators of the three components (reading R22).
+R21), the velocity operators of the three components (reading R22) and the
+stochastic FAC cycle on them (reading R23).
 
 Geometry (the refined-slab reading of the composite benchmark, with the MAC
 staggering of Section 4): the unit box, periodic in x (and y in 3-D), walls
@@ -343,3 +344,148 @@ class CompositeMAC:
         for c, fine, dist in self.interface_groups(2):   # interface node against the fine row below it
             term(H ** (d - 1) / dist, [(c, 1.0)] + [(f, -w) for f, w in fine])
         return sp.csr_matrix((vals, (rows, cols)), shape=(self.n_faces, self.n_faces))
+
+
+# ---- stochastic FAC on the staggered composite grid (Algorithms 1-3) ----
+
+def _greedy_colours(A):
+    """Colour classes of the graph of A (a_ij != 0, i != j), each an independent
+    set, by first fit in index order: a valid Gibbs visiting order."""
+    A = sp.csr_matrix(A)
+    colour = -np.ones(A.shape[0], dtype=int)
+    for i in range(A.shape[0]):
+        used = {colour[j] for j in A.indices[A.indptr[i]:A.indptr[i + 1]] if j != i and colour[j] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        colour[i] = c
+    return [np.nonzero(colour == c)[0] for c in range(colour.max() + 1)]
+
+
+def _kron3(Pz, Py, Px):
+    return sp.kron(sp.csr_matrix(Pz), sp.kron(sp.csr_matrix(Py), sp.csr_matrix(Px))).tocsr()
+
+
+class CompositeMACFAC:
+    """FAC for the velocity of a composite MAC grid (reading R23).
+
+    Base level (1) = the uniform MAC velocity grid of n cells, components
+    (u, v, w) flattened (z, y, x) as in grid.velocity_system.  P maps the base
+    unknowns to the composite ones: the identity on the base nodes that stay
+    unknowns, and on the refined slab the uniform tri-linear interpolation of
+    grid.prolongation (the component's lattice types) from the base nodes.
+    The base operator is the Galerkin product A_1 = P^T A P, the levels below
+    it P_l^T A_l P_l with the uniform tri-linear P_l, and the coarsest level is
+    the exact block draw.  A cycle (Algorithm 1 around Algorithm 2):
+        r = b - A z;  q_1 = V-Cycle(0, P^T r);  q = P q_1;
+        nu Gibbs sweeps on the refined-slab unknowns of A q = r;  z += q,
+    with every Gibbs sweep a heat-bath pass over colour classes of the
+    operator's graph (first-fit colouring).
+    """
+
+    def __init__(self, g, mu=1.0, levels=None):
+        from . import grid as _grid
+        self.g = g
+        self.A = g.velocity_operator(mu).tocsr()
+        n, d = g.n, g.dim
+        self.base = _grid.velocity_system(n, d, mu=mu, levels=levels)
+        self.P = self._prolongation(_grid)
+        self.fine = np.array([f[5][1] == "f" for f in g.faces])
+        ops = [(self.P.T @ self.A @ self.P).tocsr()]
+        self.Pl = []
+        for lev in range(self.base.nlevels - 1):
+            Pl = sp.block_diag([_kron3(Ps[2], Ps[1], Ps[0]) for Ps in self.base.P[lev]]).tocsr()
+            self.Pl.append(Pl)
+            ops.append((Pl.T @ ops[-1] @ Pl).tocsr())
+        self.ops = ops
+        self.colours = [_greedy_colours(A) for A in ops[:-1]]
+        self.chol = np.linalg.cholesky(ops[-1].toarray())
+        idx = np.nonzero(self.fine)[0]
+        self.patch = idx
+        self.patch_colours = [idx[c] for c in _greedy_colours(self.A[idx][:, idx])]
+
+    def _prolongation(self, _grid):
+        g, n, d, K = self.g, self.g.n, self.g.dim, self.g.K
+        kinds = self.base.kinds
+        offs = np.cumsum([0] + [cl.size for cl in self.base.levels[0]])
+        shapes = [cl.shape for cl in self.base.levels[0]]
+        comp_of_axis = {0: 0, 1: 1, 2: 2} if d == 3 else {0: 0, 2: 1}
+        up = {}
+        rows, cols, vals = [], [], []
+        for f, (axis, plus, minus, area, dist, key) in enumerate(g.faces):
+            _, lev, k, j, i = key
+            c = comp_of_axis[axis]
+            nz, ny, nx = shapes[c]
+            if lev != "f":                                  # a base node that stays an unknown
+                kk = k - 1 if axis == 2 else k
+                rows.append(f)
+                cols.append(offs[c] + (kk * ny + (j if d == 3 else 0)) * nx + i)
+                vals.append(1.0)
+                continue
+            if c not in up:                                 # tri-linear n -> 2n of this component
+                P1 = [_grid.prolongation(kd, n if kd != "O" else 1) for kd in kinds[c]]
+                up[c] = (_kron3(P1[2], P1[1], P1[0]).tocsr(), [p.shape[0] for p in P1])
+            Pc, (fx, fy, fz) = up[c]
+            kk = k - 1 if axis == 2 else k
+            row = Pc.getrow((kk * fy + (j if d == 3 else 0)) * fx + i)
+            for col, v in zip(row.indices, row.data):
+                rows.append(f)
+                cols.append(offs[c] + col)
+                vals.append(v)
+        return sp.csr_matrix((vals, (rows, cols)), shape=(g.n_faces, offs[-1]))
+
+    # -- one V-cycle on the base hierarchy (Algorithm 3) --------------------
+    def _sweep(self, lev, v, b, sweep, noise, sigma):
+        A = self.ops[lev]
+        diag = A.diagonal()
+        for colour, idx in enumerate(self.colours[lev]):
+            off = A[idx] @ v - diag[idx] * v[idx]
+            new = (b[idx] - off) / diag[idx]
+            if sigma != 0.0:
+                new = new + sigma * noise.sweep(lev + 1, 0, colour, sweep, idx.size) / np.sqrt(diag[idx])
+            v[idx] = new
+
+    def vcycle(self, lev, v, b, noise, sigma, mu1=2, mu2=2):
+        if lev == len(self.ops) - 1:
+            y = np.linalg.solve(self.chol, b)
+            if sigma != 0.0:
+                y = y + sigma * noise.coarsest(lev + 1, 0, y.size)
+            v[:] = np.linalg.solve(self.chol.T, y)
+            return v
+        for s in range(mu1):
+            self._sweep(lev, v, b, s, noise, sigma)
+        bc = self.Pl[lev].T @ (b - self.ops[lev] @ v)
+        vc = np.zeros(bc.size)
+        self.vcycle(lev + 1, vc, bc, noise, sigma, mu1, mu2)
+        v += self.Pl[lev] @ vc
+        for s in range(mu2):
+            self._sweep(lev, v, b, mu1 + s, noise, sigma)
+        return v
+
+    # -- the composite cycle (Algorithms 1 and 2) ----------------------------
+    def fac_cycle(self, z, b, noise, sigma, mu1=2, mu2=2, nu=2):
+        r = b - self.A @ z
+        qb = np.zeros(self.P.shape[1])
+        self.vcycle(0, qb, self.P.T @ r, noise, sigma, mu1, mu2)
+        q = self.P @ qb
+        diag = self.A.diagonal()
+        for s in range(nu):
+            for colour, idx in enumerate(self.patch_colours):
+                off = self.A[idx] @ q - diag[idx] * q[idx]
+                new = (r[idx] - off) / diag[idx]
+                if sigma != 0.0:
+                    new = new + sigma * noise.patch(0, colour, s, idx) / np.sqrt(diag[idx])
+                q[idx] = new
+        z += q
+        return z
+
+    def solve(self, b, tol=1e-10, max_cycles=200):
+        from .philox import ExplicitNoise
+        z = np.zeros_like(b)
+        bn = np.linalg.norm(b)
+        cycles, rel = 0, np.linalg.norm(b - self.A @ z) / bn
+        while rel > tol and cycles < max_cycles:
+            self.fac_cycle(z, b, ExplicitNoise(), 0.0)
+            cycles += 1
+            rel = np.linalg.norm(b - self.A @ z) / bn
+        return z, cycles, rel

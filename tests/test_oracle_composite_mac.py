@@ -258,3 +258,64 @@ def test_velocity_wrong_group_distance_is_caught():
     Az = g.velocity_operator(1.0) @ g.face_positions()[:, 2]
     below_top = g.face_positions()[:, 2] < 1.0 - g.H
     assert np.abs(Az[below_top]).max() > 0.2 * g.H          # (1/4) H^(d-1) at the interface rows
+
+
+# ---- stochastic FAC on the staggered composite grid (reading R23) ----
+
+import scipy.sparse.linalg as spla  # noqa: E402
+
+from oracle.composite_mac import CompositeMACFAC  # noqa: E402
+from tests.affine import extract  # noqa: E402
+
+
+def _affine(F):
+    def step(z, b, noise):
+        return [F.fac_cycle(z[0].copy(), b[0], noise, 1.0)]
+    return extract(step, [(F.g.n_faces,)])
+
+
+@pytest.mark.parametrize("dim,n,K", [(2, 4, 1), (2, 8, 2), (3, 4, 1)])
+def test_composite_mac_cycle_invariance_exact(dim, n, K):
+    # the paper's claim (Section 3.2) for the composite cycle: N(A^-1 b, A^-1)
+    # is invariant, A^-1 = M A^-1 M^T + B B^T, and A^-1 b is the fixed point
+    F = CompositeMACFAC(CompositeMAC(n, K, dim), mu=0.8)
+    M, N, B, c = _affine(F)
+    C = np.linalg.inv(F.A.toarray())
+    assert np.abs(M @ C @ M.T + B @ B.T - C).max() < 1e-12 * np.abs(C).max()
+    b = np.random.default_rng(6).standard_normal(C.shape[0])
+    x = C @ b
+    assert np.abs(M @ x + N @ b + c - x).max() < 1e-11 * np.abs(x).max()
+    assert np.max(np.abs(np.linalg.eigvals(M))) < 0.5
+
+
+def test_composite_mac_wrong_restriction_breaks_invariance():
+    # A plausible slip: the residual restricted by P^T / 2 while the base
+    # operator stays the Galerkin P^T A P.
+    F = CompositeMACFAC(CompositeMAC(4, 1, 2))
+
+    def cycle(z, b, noise, sigma, mu1=2, mu2=2, nu=2):
+        r = b - F.A @ z
+        qb = np.zeros(F.P.shape[1])
+        F.vcycle(0, qb, 0.5 * (F.P.T @ r), noise, sigma, mu1, mu2)
+        q = F.P @ qb
+        diag = F.A.diagonal()
+        for s in range(nu):
+            for colour, idx in enumerate(F.patch_colours):
+                off = F.A[idx] @ q - diag[idx] * q[idx]
+                q[idx] = (r[idx] - off) / diag[idx] + sigma * noise.patch(0, colour, s, idx) / np.sqrt(diag[idx])
+        return z + q
+
+    F.fac_cycle = cycle
+    M, N, B, c = _affine(F)
+    C = np.linalg.inv(F.A.toarray())
+    assert np.abs(M @ C @ M.T + B @ B.T - C).max() > 1e-4 * np.abs(C).max()
+
+
+@pytest.mark.parametrize("dim,n,K", [(2, 16, 4), (3, 8, 2)])
+def test_composite_mac_solve_matches_direct(dim, n, K):
+    F = CompositeMACFAC(CompositeMAC(n, K, dim), mu=1.2)
+    b = np.random.default_rng(7).standard_normal(F.g.n_faces)
+    z, cycles, rel = F.solve(b, tol=1e-11)
+    assert rel <= 1e-11 and cycles <= 20
+    x = spla.spsolve(F.A.tocsc(), b)
+    assert np.linalg.norm(z - x) / np.linalg.norm(x) < 1e-9

@@ -65,3 +65,26 @@ def test_chain_counter_advances_and_reproduces():
     b.chain_cycles(2)          # resume: same counter sequence, same chain
     assert a.cycle == b.cycle == 3
     assert np.array_equal(flatten(a.xi), flatten(b.xi))
+
+
+def test_em_displacement_statistics_without_force():
+    # Algorithm 4 with F = 0: the displacement X1 - X0 = sqrt(2 kT dt) Gamma xi
+    # has mean 0 and covariance 2 kT dt M (statistical pin; consecutive samples
+    # of the multigrid chain are practically independent, lag-1 correlation ~2 %)
+    kT, dt = 1.3, 1e-4
+    m = selm.Model(8, 2, mu=1.0, kT=kT, levels=3, seed=3, instance=1, tol=1e-13)
+    X0 = np.array([[0.31, 0.42], [0.77, 0.58]])
+    M = m.mobility_matrix(X0)
+    m.chain_cycles(10)
+    F = np.zeros_like(X0)
+    D = np.array([(m.em_step(X0, F, dt, ncycles=1)[0] - X0).ravel() for _ in range(1200)])
+    target = 2 * kT * dt * M
+    nb = 10
+    batches = np.array_split(D, nb)
+    covs = np.array([b.T @ b / b.shape[0] for b in batches])
+    means = np.array([b.mean(0) for b in batches])
+    se_cov = covs.std(0, ddof=1) / np.sqrt(nb)
+    assert np.all(np.abs(covs.mean(0) - target) < 5 * se_cov + 1e-3 * np.abs(target).max())
+    se_mean = means.std(0, ddof=1) / np.sqrt(nb)
+    assert np.all(np.abs(means.mean(0)) < 5 * se_mean)
+    assert np.abs(covs.mean(0) - target).max() < 0.2 * np.abs(target).max()

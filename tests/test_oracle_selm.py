@@ -88,3 +88,30 @@ def test_em_displacement_statistics_without_force():
     se_mean = means.std(0, ddof=1) / np.sqrt(nb)
     assert np.all(np.abs(means.mean(0)) < 5 * se_mean)
     assert np.abs(covs.mean(0) - target).max() < 0.2 * np.abs(target).max()
+
+
+def test_config1_mobility_matches_direct_solves():
+    # 2-D 64^2, 16 particles: the 32 x 32 mobility from FAC solves equals the
+    # one from sparse direct solves of the same operator, and is symmetric
+    # positive definite
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    m = selm.Model(64, 2, mu=1.0, kT=1.0, levels=6, tol=1e-12)
+    X = selm_inputs.particles(16, 2, 64, seed=0)
+    M = m.mobility_matrix(X)
+    blocks = []
+    for cl in m.sys.levels[0]:
+        K, Mm = [sp.csr_matrix(k) for k in cl.K], [sp.csr_matrix(x) for x in cl.M]
+        blocks.append(cl.scale * (sp.kron(Mm[2], sp.kron(Mm[1], K[0])) + sp.kron(Mm[2], sp.kron(K[1], Mm[0]))
+                                  + sp.kron(K[2], sp.kron(Mm[1], Mm[0]))))
+    lu = spla.splu(sp.block_diag(blocks).tocsc())
+    shapes = m.sys.shapes()
+    Md = np.zeros_like(M)
+    for col in range(32):
+        F = np.zeros((16, 2))
+        F[col // 2, col % 2] = 1.0
+        u = unflatten(lu.solve(flatten(coupling.spread(m.sys, F, X))), shapes)
+        Md[:, col] = coupling.interpolate(m.sys, u, X).ravel()
+    assert np.abs(M - Md).max() < 1e-9 * np.abs(Md).max()
+    assert np.abs(M - M.T).max() < 1e-9 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0

@@ -2,8 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY (see the package header).  The staggered composite
 grid with the projection: divergence, gradient, the projection (reading
-R21), the velocity operators of the three components (reading R22) and the
-stochastic FAC cycle on them (reading R23).
+R21), the velocity operators of the three components (reading R22), the
+stochastic FAC cycle on them (reading R23) and particles on the grid
+(reading R24).
 
 Geometry (the refined-slab reading of the composite benchmark, with the MAC
 staggering of Section 4): the unit box, periodic in x (and y in 3-D), walls
@@ -41,6 +42,8 @@ uniform fine grid.
 import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
+
+from . import coupling, grid
 
 
 class CompositeMAC:
@@ -352,6 +355,8 @@ def _greedy_colours(A):
     """Colour classes of the graph of A (a_ij != 0, i != j), each an independent
     set, by first fit in index order: a valid Gibbs visiting order."""
     A = sp.csr_matrix(A)
+    if A.shape[0] == 0:
+        return []
     colour = -np.ones(A.shape[0], dtype=int)
     for i in range(A.shape[0]):
         used = {colour[j] for j in A.indices[A.indptr[i]:A.indptr[i + 1]] if j != i and colour[j] >= 0}
@@ -384,12 +389,11 @@ class CompositeMACFAC:
     """
 
     def __init__(self, g, mu=1.0, levels=None):
-        from . import grid as _grid
         self.g = g
         self.A = g.velocity_operator(mu).tocsr()
         n, d = g.n, g.dim
-        self.base = _grid.velocity_system(n, d, mu=mu, levels=levels)
-        self.P = self._prolongation(_grid)
+        self.base = grid.velocity_system(n, d, mu=mu, levels=levels)
+        self.P = self._prolongation()
         self.fine = np.array([f[5][1] == "f" for f in g.faces])
         ops = [(self.P.T @ self.A @ self.P).tocsr()]
         self.Pl = []
@@ -404,7 +408,7 @@ class CompositeMACFAC:
         self.patch = idx
         self.patch_colours = [idx[c] for c in _greedy_colours(self.A[idx][:, idx])]
 
-    def _prolongation(self, _grid):
+    def _prolongation(self):
         g, n, d, K = self.g, self.g.n, self.g.dim, self.g.K
         kinds = self.base.kinds
         offs = np.cumsum([0] + [cl.size for cl in self.base.levels[0]])
@@ -423,7 +427,7 @@ class CompositeMACFAC:
                 vals.append(1.0)
                 continue
             if c not in up:                                 # tri-linear n -> 2n of this component
-                P1 = [_grid.prolongation(kd, n if kd != "O" else 1) for kd in kinds[c]]
+                P1 = [grid.prolongation(kd, n if kd != "O" else 1) for kd in kinds[c]]
                 up[c] = (_kron3(P1[2], P1[1], P1[0]).tocsr(), [p.shape[0] for p in P1])
             Pc, (fx, fy, fz) = up[c]
             kk = k - 1 if axis == 2 else k
@@ -489,3 +493,157 @@ class CompositeMACFAC:
             cycles += 1
             rel = np.linalg.norm(b - self.A @ z) / bn
         return z, cycles, rel
+
+
+# ---- particles on the composite MAC grid (Algorithm 4; reading R24) ----
+
+class CompositeSELM:
+    """Mobility and thermal velocities of particles on a composite MAC grid.
+
+    kernel = "fine" (default): every particle uses the fine level's 4-point
+    kernel, so its size does not change when it crosses the interface;
+    kernel = "cover": a particle uses the level whose cells cover it, the fine
+    level below the interface (z < K H) and the base level above (its
+    self-mobility then jumps by about a fifth at the interface).  The 4^d
+    Peskin nodes are nodes of that level's whole uniform MAC lattice; their
+    values come from the composite field through
+      R: base field = the composite value on base nodes that are unknowns,
+         and on covered base nodes the mean of the 2^(d-1) fine faces that
+         coincide with the base face;
+      E: fine field = the composite value on the slab's fine nodes, and
+         elsewhere the uniform tri-linear interpolation (grid.prolongation)
+         of the base field R u.
+    Gamma (interpolation) is the Peskin sum on that field (coupling.stencil),
+    so Gamma = I_level(X) R or I_level(X) E.  With A = -mu V L the force
+    density is Lambda F = V^-1 Gamma^T F, and
+        M = Gamma P~ A^-1 P~^T Gamma^T,   g = sqrt(2 kT) Gamma P~ xi,
+    P~^T = W P~ W^-1 the adjoint of the W-orthogonal projection acting on the
+    spread forces; M is symmetric and Cov(g) = 2 kT M.
+    """
+
+    def __init__(self, n, K, dim, mu=1.0, kT=1.0, project=False, kernel="fine"):
+        assert kernel in ("cover", "fine")
+        self.kernel = kernel
+        self.n, self.K, self.dim, self.kT, self.project_on = n, K, dim, kT, project
+        self.g = CompositeMAC(n, K, dim)
+        self.fac = CompositeMACFAC(self.g, mu)
+        self.coarse_sys = grid.velocity_system(n, dim, mu=mu, levels=1)
+        self.fine_sys = grid.velocity_system(2 * n, dim, mu=mu, levels=1)
+        self.R = self._restriction()
+        self.E = self._extension()
+
+    @staticmethod
+    def _offsets(system):
+        return np.cumsum([0] + [cl.size for cl in system.levels[0]])
+
+    def _comp_axes(self):
+        return [0, 1, 2] if self.dim == 3 else [0, 2]
+
+    def _restriction(self):
+        g, d, K, n = self.g, self.dim, self.K, self.n
+        F = g.face_of
+        offs = self._offsets(self.coarse_sys)
+        rows, cols, vals = [], [], []
+        for c, axis in enumerate(self._comp_axes()):
+            nz, ny, nx = self.coarse_sys.levels[0][c].shape
+            for k in range(nz):
+                for j in range(ny):
+                    for i in range(nx):
+                        row = offs[c] + (k * ny + j) * nx + i
+                        kz = k + 1 if axis == 2 else k           # base row (w: node at kz H)
+                        covered = kz < K
+                        if not covered:
+                            lev = "i" if axis == 2 and kz == K and 0 < K < n else "c"
+                            rows.append(row)
+                            cols.append(F[(axis, lev, kz, j, i)])
+                            vals.append(1.0)
+                            continue
+                        kids = []
+                        for e in (range(2) if d == 3 else [0]):
+                            for t in range(2):
+                                if axis == 0:
+                                    key = (0, "f", 2 * kz + t, 2 * j + e if d == 3 else 0, 2 * i)
+                                elif axis == 1:
+                                    key = (1, "f", 2 * kz + t, 2 * j, 2 * i + e)
+                                else:
+                                    key = (2, "f", 2 * kz, 2 * j + e if d == 3 else 0, 2 * i + t)
+                                kids.append(F[key])
+                        for f in kids:
+                            rows.append(row)
+                            cols.append(f)
+                            vals.append(1.0 / len(kids))
+        return sp.csr_matrix((vals, (rows, cols)), shape=(offs[-1], g.n_faces))
+
+    def _extension(self):
+        g, d, K, n = self.g, self.dim, self.K, self.n
+        F = g.face_of
+        offs_f = self._offsets(self.fine_sys)
+        offs_c = self._offsets(self.coarse_sys)
+        rows, cols, vals = [], [], []
+        ghost_rows, ghost_src = [], []
+        for c, axis in enumerate(self._comp_axes()):
+            kinds = self.coarse_sys.kinds[c]
+            P1 = [grid.prolongation(kd, n if kd != "O" else 1) for kd in kinds]
+            Pc = _kron3(P1[2], P1[1], P1[0]).tocsr()
+            nz, ny, nx = self.fine_sys.levels[0][c].shape
+            for k in range(nz):
+                for j in range(ny):
+                    for i in range(nx):
+                        row = offs_f[c] + (k * ny + j) * nx + i
+                        kz = k + 1 if axis == 2 else k
+                        if kz < 2 * K:                                   # a slab unknown
+                            rows.append(row)
+                            cols.append(F[(axis, "f", kz, j, i)])
+                            vals.append(1.0)
+                        else:                                            # ghost: tri-linear from the base field
+                            prow = Pc.getrow((k * ny + j) * nx + i)
+                            for col, v in zip(prow.indices, prow.data):
+                                ghost_rows.append(row)
+                                ghost_src.append((offs_c[c] + col, v))
+        E = sp.csr_matrix((vals, (rows, cols)), shape=(offs_f[-1], g.n_faces))
+        if ghost_rows:
+            Rr = sp.csr_matrix(([v for _, v in ghost_src], (ghost_rows, [s for s, _ in ghost_src])),
+                               shape=(offs_f[-1], offs_c[-1]))
+            E = E + Rr @ self.R
+        return E.tocsr()
+
+    def interpolation(self, X):
+        """Gamma as a sparse (np d) x (faces) matrix."""
+        rows, cols, vals = [], [], []
+        cols_of = [0, 1, 2] if self.dim == 3 else [0, 1]
+        for p_, x in enumerate(X):
+            fine = self.kernel == "fine" or x[-1] < self.K * self.g.H
+            system = self.fine_sys if fine else self.coarse_sys
+            offs = self._offsets(system)
+            lift = self.E if fine else self.R
+            for c in range(system.ncomp):
+                kk, jj, ii, W = coupling.stencil(system, c, x[None, :])
+                nz, ny, nx = system.levels[0][c].shape
+                idx = offs[c] + (kk.ravel() * ny + jj.ravel()) * nx + ii.ravel()
+                w = W.ravel()
+                keep = w != 0.0
+                r = lift[idx[keep]].T @ w[keep]
+                nzr = np.nonzero(r)[0]
+                rows.extend([p_ * self.dim + cols_of[c]] * nzr.size)
+                cols.extend(nzr.tolist())
+                vals.extend(r[nzr].tolist())
+        return sp.csr_matrix((vals, (rows, cols)), shape=(X.shape[0] * self.dim, self.g.n_faces))
+
+    def _P(self, u):
+        return self.g.project(u) if self.project_on else u
+
+    def _PT(self, c):
+        return self.g.weight * self.g.project(c / self.g.weight) if self.project_on else c
+
+    def mobility_matrix(self, X, tol=1e-12):
+        G = self.interpolation(X).toarray()
+        M = np.zeros((G.shape[0], G.shape[0]))
+        for col in range(G.shape[0]):
+            u, cycles, rel = self.fac.solve(self._PT(G[col]), tol=tol)
+            M[:, col] = G @ self._P(u)
+        return M
+
+    def thermal_operator(self, X):
+        """K = sqrt(2 kT) Gamma P~ as a dense matrix (g = K xi); row r is P~^T of Gamma's row r."""
+        G = self.interpolation(X).toarray()
+        return np.sqrt(2.0 * self.kT) * np.array([self._PT(r) for r in G])

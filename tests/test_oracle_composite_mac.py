@@ -319,3 +319,71 @@ def test_composite_mac_solve_matches_direct(dim, n, K):
     assert rel <= 1e-11 and cycles <= 20
     x = spla.spsolve(F.A.tocsc(), b)
     assert np.linalg.norm(z - x) / np.linalg.norm(x) < 1e-9
+
+
+# ---- particles on the composite MAC grid (reading R24) ----
+
+from oracle import selm as oselm  # noqa: E402
+from oracle.composite_mac import CompositeSELM  # noqa: E402
+
+PARTICLES_2D = np.array([[0.31, 0.42], [0.77, 0.58], [0.12, 0.2]])
+
+
+@pytest.mark.parametrize("K", [0, 8])
+@pytest.mark.parametrize("project", [False, True])
+def test_composite_selm_uniform_limits(K, project):
+    # no row refined: the base grid's SELM; every row refined: the fine grid's
+    n = 8
+    cs = CompositeSELM(n, K, 2, mu=0.9, project=project, kernel="cover")
+    M = cs.mobility_matrix(PARTICLES_2D)
+    m = oselm.Model(n if K == 0 else 2 * n, 2, mu=0.9, project=project, tol=1e-13)
+    Mu = m.mobility_matrix(PARTICLES_2D)
+    assert np.abs(M - Mu).max() < 1e-10 * np.abs(Mu).max()
+    if K == 8:
+        Mf = CompositeSELM(n, K, 2, mu=0.9, project=project, kernel="fine").mobility_matrix(PARTICLES_2D)
+        assert np.abs(Mf - Mu).max() < 1e-10 * np.abs(Mu).max()
+
+
+@pytest.mark.parametrize("kernel", ["cover", "fine"])
+def test_composite_interpolation_reproduces_linear_fields(kernel):
+    # away from the walls Gamma reproduces fields linear in z on both sides of
+    # the interface and across it (R and E are exact on them)
+    n, K = 16, 6
+    cs = CompositeSELM(n, K, 2, kernel=kernel)
+    pos = cs.g.face_positions()
+    u = np.where([f[0] == 0 for f in cs.g.faces], 0.3 + 2 * pos[:, 2], -1 + 0.5 * pos[:, 2])
+    zs = np.linspace((K - 3) / n, (K + 3) / n, 25)
+    X = np.column_stack([np.full(zs.size, 0.37), zs])
+    U = (cs.interpolation(X) @ u).reshape(-1, 2)
+    assert np.abs(U[:, 0] - (0.3 + 2 * zs)).max() < 1e-13
+    assert np.abs(U[:, 1] - (-1 + 0.5 * zs)).max() < 1e-13
+
+
+@pytest.mark.parametrize("project", [False, True])
+def test_composite_fluctuation_dissipation(project):
+    # K A^-1 K^T = 2 kT M with K = sqrt(2 kT) Gamma P~ (Eq. equ_G_special_form)
+    cs = CompositeSELM(8, 3, 2, mu=0.8, kT=1.7, project=project, kernel="fine")
+    X = np.array([[0.3, 0.33], [0.6, 0.41], [0.45, 0.7]])       # below, at and above the interface
+    M = cs.mobility_matrix(X)
+    Kt = cs.thermal_operator(X)
+    G = Kt @ np.linalg.inv(cs.fac.A.toarray()) @ Kt.T
+    assert np.abs(G - 2 * cs.kT * M).max() < 1e-9 * np.abs(G).max()
+    assert np.abs(M - M.T).max() < 1e-10 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+def test_fine_kernel_mobility_is_continuous_across_the_interface():
+    # The particle keeps its kernel (its size) when it crosses the interface:
+    # between sample heights H/4 apart its self-mobility changes by at most 5 %
+    # (about 2 % per step from the wall effect below, a dip of 4 % at the
+    # interface, lattice ripples of 1-2 % above).  Switching to the coarse
+    # kernel above the interface ("cover") makes it jump by about a fifth.
+    n, K = 16, 6
+    zz = np.linspace((K - 2.5) / n, (K + 2.5) / n, 21)
+    steps = {}
+    for kernel in ("fine", "cover"):
+        cs = CompositeSELM(n, K, 2, kernel=kernel)
+        vals = np.array([np.diag(cs.mobility_matrix(np.array([[0.37, z]]))) for z in zz])
+        steps[kernel] = np.abs(np.diff(vals, axis=0)) / vals.mean(0)
+    assert steps["fine"].max() < 0.05
+    assert steps["cover"].max() > 0.15 and steps["cover"].max() > 4 * steps["fine"].max()

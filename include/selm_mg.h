@@ -137,6 +137,11 @@ int selm_mg_inner_bytes(const selm_mg* h);
 /* Device pointer of the chain state xi (velocity layout, FP64) and its cycle
    counter (the Philox counter of the next stochastic cycle). */
 selm_status selm_mg_chain(selm_mg* h, double** xi, uint64_t* cycle);
+/* Device pointer of the velocity field u of the handle's current FAC solve
+   (velocity layout, FP64, owned by the handle): after a step, the solution of
+   A u = Gamma^T F of its last velocity solve (Alg. 4 step 2); with
+   SELM_PROJ_MAC the right-hand side is the projected spread force. */
+selm_status selm_mg_velocity(selm_mg* h, double** u);
 selm_status selm_mg_set_cycle(selm_mg* h, uint64_t cycle);
 /* Failure-path hook: raises the timeout flag of `system`'s cooperative waits
    (on `stream`), as a wait that ran out of time does.  The next cooperative
@@ -287,6 +292,16 @@ selm_status selm_batch_step(selm_batch* b, const int* np, double* const* X, cons
 /* Times the batched V-cycle for engine cluster sizes 16, 8 and 4 and keeps the
    fastest; *chosen_cluster receives it. */
 selm_status selm_batch_autotune(selm_batch* b, int* chosen_cluster, void* stream);
+enum { SELM_BATCH_SOLVE = 0, SELM_BATCH_SAMPLE = 1 };
+/* One FAC cycle (Algorithm 1) of every system of the batch, the systems side
+   by side on the batch's branch streams, joined into `stream`:
+   SELM_BATCH_SAMPLE: one stochastic cycle of each system's thermal chain
+     (b = 0, noise on); the chain counters advance by one;
+   SELM_BATCH_SOLVE: one deterministic cycle of each system's velocity solve
+     from its current iterate u (selm_mg_velocity) and right-hand side (those
+     of its last step): u <- u + V-Cycle(0, b - A u).
+   Other modes return SELM_EINVAL. */
+selm_status selm_batch_cycle(selm_batch* b, int mode, void* stream);
 
 /* ---- served form -----------------------------------------------------------
    A request loop.  One device pool of `budget_bytes` is reserved at creation;

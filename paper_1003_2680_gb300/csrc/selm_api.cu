@@ -838,6 +838,12 @@ selm_status selm_mg_chain(selm_mg* h, double** xi, uint64_t* cycle) {
   return SELM_OK;
 }
 
+selm_status selm_mg_velocity(selm_mg* h, double** u) {
+  if (!h || !u) return SELM_EINVAL;
+  *u = h->u;
+  return SELM_OK;
+}
+
 selm_status selm_mg_fail_waits(selm_mg* h, int system, void* stream) {
   if (!h) return SELM_EINVAL;
   Sys* s = sys_of(h, system);

@@ -358,6 +358,34 @@ selm_status selm_batch_step(selm_batch* b, const int* np, double* const* X, cons
   return SELM_OK;
 }
 
+selm_status selm_batch_cycle(selm_batch* b, int mode, void* stream) {
+  if (!b || (mode != SELM_BATCH_SOLVE && mode != SELM_BATCH_SAMPLE)) return SELM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  BCK(cudaEventRecord(b->fork, st));
+  for (int i = 0; i < b->n; ++i) {
+    selm_mg* h = b->sys[i];
+    cudaStream_t s = b->branch[i];
+    const size_t inner = (size_t)h->vel.lev[0].size * h->esize;
+    BCK(cudaStreamWaitEvent(s, b->fork, 0));
+    if (mode == SELM_BATCH_SAMPLE) {
+      LST(outer_residual(h, h->vel, h->xi, nullptr, h->vel.b[0], nullptr, s));
+      LCK(cudaMemsetAsync(h->vel.v[0], 0, inner, s));
+      LST(vcycle(h, h->vel, h->vel.v[0], h->vel.b[0], true, h->cyc + 0, s));
+      LST(outer_update(h, h->vel, h->xi, h->vel.v[0], s));
+      LCK(launch_inc_u64(h->cyc + 0, s));
+      h->cycle += 1;
+    } else {
+      LST(outer_residual(h, h->vel, h->u, h->bvel, h->vel.b[0], nullptr, s));
+      LCK(cudaMemsetAsync(h->vel.v[0], 0, inner, s));
+      LST(vcycle(h, h->vel, h->vel.v[0], h->vel.b[0], false, h->cyc + 1, s));
+      LST(outer_update(h, h->vel, h->u, h->vel.v[0], s));
+    }
+    BCK(cudaEventRecord(b->join[i], s));
+    BCK(cudaStreamWaitEvent(st, b->join[i], 0));
+  }
+  return SELM_OK;
+}
+
 selm_status selm_batch_autotune(selm_batch* b, int* chosen_cluster, void* stream) {
   if (!b) return SELM_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;

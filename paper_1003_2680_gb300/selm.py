@@ -24,6 +24,7 @@ SELM_OPT_ENGINE_LEVEL = 3
 SELM_OPT_LEVEL_COOP = 4
 SELM_OPT_GRAPHS = 5
 SELM_OPT_SPECULATE = 6
+SELM_BATCH_SOLVE, SELM_BATCH_SAMPLE = 0, 1
 
 _STATUS = {0: "SELM_OK", 1: "SELM_EINVAL", 2: "SELM_ENOMEM", 3: "SELM_ECUDA", 4: "SELM_ENOCONV",
            5: "SELM_ETIMEOUT", 6: "SELM_EBUSY"}
@@ -92,6 +93,7 @@ _SIGS = {
     "selm_mg_layout": (_I, [_P, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
     "selm_mg_inner_bytes": (_I, [_P]),
     "selm_mg_chain": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_U64)]),
+    "selm_mg_velocity": (_I, [_P, ctypes.POINTER(_P)]),
     "selm_mg_set_cycle": (_I, [_P, _U64]),
     "selm_mg_fail_waits": (_I, [_P, _I, _P]),
     "selm_mg_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_LL)]),
@@ -119,6 +121,7 @@ _SIGS = {
     "selm_batch_step": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, _I,
                              ctypes.POINTER(_I), _P]),
     "selm_batch_autotune": (_I, [_P, ctypes.POINTER(_I), _P]),
+    "selm_batch_cycle": (_I, [_P, _I, _P]),
     "selm_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
     "selm_server_submit": (_I, [_P, ctypes.POINTER(SelmRequest), ctypes.POINTER(_U64)]),
     "selm_server_poll": (_I, [_P, ctypes.POINTER(SelmResult), _I]),
@@ -305,6 +308,13 @@ def selm_mg_chain(h):
     return p.value, c.value
 
 
+def selm_mg_velocity(h):
+    """Device address of the handle's velocity solve iterate u (FP64, velocity layout)."""
+    p = _P()
+    _check(h, lib().selm_mg_velocity(h, ctypes.byref(p)))
+    return p.value
+
+
 def selm_mg_set_cycle(h, cycle):
     _check(h, lib().selm_mg_set_cycle(h, cycle))
 
@@ -435,6 +445,10 @@ def selm_batch_autotune(b, stream=None):
     c = _I(0)
     _check_batch(b, lib().selm_batch_autotune(b, ctypes.byref(c), _stream(stream)))
     return c.value
+
+
+def selm_batch_cycle(b, mode, stream=None):
+    _check_batch(b, lib().selm_batch_cycle(b, mode, _stream(stream)))
 
 
 def selm_server_create(budget_bytes, max_slots):

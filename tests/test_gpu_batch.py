@@ -135,3 +135,78 @@ def test_batch_at_benchmark_shapes(S):
         err = np.linalg.norm(x.cpu().numpy() - w) / np.linalg.norm(w - X0)
         assert err < 1e-5, (desc.n, err)
         S.selm_mg_destroy(h)
+
+
+class _Raw:
+    """A device buffer of the library seen as a torch tensor (no copy)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, False), "version": 3}
+
+
+def _fp64_descs(S):
+    return [S.make_desc(dim=d, n=n, kT=kT, precision=S.SELM_FP64, seed=seed, instance=7 + i, max_particles=256)
+            for i, (d, n, npart, kT, seed) in enumerate(SYSTEMS)]
+
+
+def _level_size(S, h):
+    return S.selm_mg_layout(h, S.SELM_SYS_VELOCITY, 0, 0)[2]
+
+
+def test_batch_cycle_sample_equals_each_chain_alone(S):
+    descs = _fp64_descs(S)
+    b = S.selm_batch_create(descs)
+    for _ in range(3):
+        S.selm_batch_cycle(b, S.SELM_BATCH_SAMPLE)
+    torch.cuda.synchronize()
+    for i, desc in enumerate(descs):
+        hb = S.selm_batch_system(b, i)
+        assert S.selm_mg_chain(hb)[1] == 3
+        xb = torch.as_tensor(_Raw(S.selm_mg_chain(hb)[0], _level_size(S, hb)), device="cuda").clone()
+        h = S.selm_mg_create(desc)
+        X = torch.zeros((0, desc.dim), dtype=torch.float64, device="cuda")
+        xa = torch.zeros_like(xb)
+        S.selm_mg_sample(h, X, 3, torch.zeros_like(X), xa)
+        torch.cuda.synchronize()
+        assert (torch.linalg.vector_norm(xb - xa) / torch.linalg.vector_norm(xa)).item() < 1e-12
+        S.selm_mg_destroy(h)
+    with pytest.raises(S.SelmError):
+        S.selm_batch_cycle(b, 7)
+    S.selm_batch_destroy(b)
+
+
+def test_batch_cycle_solve_is_one_fac_cycle(S):
+    # after a step, each system's solve iterate u (perturbed here) goes through
+    # one deterministic FAC cycle with the step's right-hand side Gamma^T F
+    from oracle import coupling, grid, multigrid
+    from oracle.philox import ExplicitNoise
+    from tests.gpu_util import from_dev
+    descs = _fp64_descs(S)
+    Xs, Fs = _inputs()
+    b = S.selm_batch_create(descs)
+    X = [torch.tensor(x, device="cuda") for x in Xs]
+    F = [torch.tensor(f, device="cuda") for f in Fs]
+    S.selm_batch_step(b, X, F, 1e-3, 1, 1)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(9)
+    starts = []
+    for i in range(len(descs)):
+        hb = S.selm_batch_system(b, i)
+        u = torch.as_tensor(_Raw(S.selm_mg_velocity(hb), _level_size(S, hb)), device="cuda")
+        u += torch.tensor(rng.standard_normal(u.numel()), device="cuda")
+        starts.append(u.clone())
+    torch.cuda.synchronize()
+    S.selm_batch_cycle(b, S.SELM_BATCH_SOLVE)
+    torch.cuda.synchronize()
+    for i, ((d, n, npart, kT, seed), u0) in enumerate(zip(SYSTEMS, starts)):
+        hb = S.selm_batch_system(b, i)
+        u1 = torch.as_tensor(_Raw(S.selm_mg_velocity(hb), _level_size(S, hb)), device="cuda").clone()
+        osys = grid.velocity_system(n, d, mu=1.0)
+        rhs = coupling.spread(osys, Fs[i], Xs[i])
+        z0 = from_dev(hb, u0)
+        want = multigrid.fac_cycle(osys, [x.copy() for x in z0], rhs, ExplicitNoise(), 0.0)
+        got = from_dev(hb, u1)
+        dg = np.concatenate([(g - z).ravel() for g, z in zip(got, z0)])
+        dw = np.concatenate([(w - z).ravel() for w, z in zip(want, z0)])
+        assert np.linalg.norm(dg - dw) / np.linalg.norm(dw) < 1e-12, i
+    S.selm_batch_destroy(b)

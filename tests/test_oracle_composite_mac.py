@@ -387,3 +387,12 @@ def test_fine_kernel_mobility_is_continuous_across_the_interface():
         steps[kernel] = np.abs(np.diff(vals, axis=0)) / vals.mean(0)
     assert steps["fine"].max() < 0.05
     assert steps["cover"].max() > 0.15 and steps["cover"].max() > 4 * steps["fine"].max()
+
+
+@pytest.mark.parametrize("K", [0, 4])
+@pytest.mark.parametrize("project", [False, True])
+def test_composite_selm_uniform_limits_3d(K, project):
+    X = np.array([[0.31, 0.42, 0.55], [0.77, 0.58, 0.3]])
+    M = CompositeSELM(4, K, 3, mu=0.9, project=project, kernel="cover").mobility_matrix(X)
+    Mu = oselm.Model(4 if K == 0 else 8, 3, mu=0.9, project=project, tol=1e-13).mobility_matrix(X)
+    assert np.abs(M - Mu).max() < 1e-10 * np.abs(Mu).max()

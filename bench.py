@@ -63,6 +63,8 @@ def parse_args():
     p.add_argument("--engine-level", type=int, default=0,
                    help="first multigrid level of the cluster-resident coarse engine (0 = automatic)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="headline workload only: no covariance, composite or 64^2 sub-records")
     p.add_argument("--workload", default="channel128", choices=["channel128", "batched", "served", "composite", "decorrelation"],
                    help="channel128: the headline line; batched: 64 uneven systems, batched vs plain; "
                         "served: Poisson request stream, served vs plain per-request")
@@ -122,12 +124,66 @@ def whole_job(seconds, units, world, device):
     return float(t.item()), float(u.item())
 
 
-def cpu_baseline(n):
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def run_oracle_replicas(n, procs):
+    """`procs` single-thread oracle processes at once, each timing one
+    stochastic FAC cycle; returns the wall time from the first start to the
+    last finish of the timed cycles (each process reports its own interval)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SNIPPET_WALL.format(root=ROOT, n=n)
+    ps = [subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                           text=True) for _ in range(procs)]
+    spans = []
+    for p in ps:
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            return None
+        spans.append(json.loads(out.strip().splitlines()[-1]))
+    return max(b for _, b in spans) - min(a for a, _ in spans)
+
+
+ORACLE_SNIPPET_WALL = r"""
+import os, sys, time, json
+sys.path.insert(0, {root!r})
+from oracle import grid, multigrid, philox
+import selm_inputs
+n = {n}
+s = grid.velocity_system(n, 3)
+co = multigrid.Coarsest(s)
+z = selm_inputs.fields(s.shapes(0), seed=1, scale=1e-2)
+zero = s.zeros(0)
+t0 = time.time()
+multigrid.fac_cycle(s, z, zero, philox.PhiloxNoise(0, 0, 0), 1.0, coarsest=co)
+print(json.dumps([t0, time.time()]))
+"""
+
+
+def cpu_baseline(n, all_cores=True):
     times = run_oracle_cycles(n, 1)
     t = times[0]
-    return {"value": n ** 3 / t, "unit": "cells/s", "cores": 1, "kind": "oracle",
-            "sample": f"one stochastic FAC cycle (Algorithm 1 around the V-cycle of Algorithm 3) of the FP64 "
-                      f"numpy oracle on the {n}^3 velocity system, single thread, {t:.1f} s"}
+    out = {"value": n ** 3 / t, "unit": "cells/s", "cores": 1, "kind": "oracle",
+           "sample": f"one stochastic FAC cycle (Algorithm 1 around the V-cycle of Algorithm 3) of the FP64 "
+                     f"numpy oracle on the {n}^3 velocity system, single thread, {t:.1f} s",
+           "cpu_model": cpu_model()}
+    if all_cores:
+        procs = os.cpu_count() or 1
+        wall = run_oracle_replicas(n, procs)
+        if wall:
+            out["all_cores"] = {"value": procs * n ** 3 / wall, "unit": "cells/s", "cores": procs,
+                                "sample": f"{procs} single-thread oracle processes at once, one stochastic FAC "
+                                          f"cycle of the {n}^3 system each (independent replicas), "
+                                          f"{wall:.1f} s from the first start to the last finish"}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -309,6 +365,36 @@ def coarse_bytes_per_vcycle(S, h, system, sweeps=4):
             ncols[-1] = 8
         total += sweeps * pass_bytes(e, sizes, ncols)
     return total
+
+
+# Byte model of the hot path per unknown-cycle (3-D, FP32 inner cycles, noise
+# drawn in registers): a red+black sweep fused into one pass reads z and r and
+# writes z (12 B, 4 sweeps per cycle); residual + restriction 8.5 B;
+# prolongation + correction 8.5 B; so 65 B per unknown of a level per V-cycle,
+# x 8/7 for the coarse levels, + 40 B of FP64 refinement (residual: read z, b
+# (FP64), write r (FP32); update: read z, delta, write z) = 114 B.
+MODEL_SWEEP_B = 12.0
+MODEL_LEVEL_B = 65.0
+MODEL_REFINE_B = 40.0
+MODEL_CYCLE_B = 114.0
+
+
+def level_unknowns(S, h, system):
+    return [sum(system_sizes(S, h, system, lev)) for lev in range(S.selm_mg_levels(h, system))]
+
+
+def model_coarse_bytes_per_vcycle(S, h, system):
+    """The byte model's share of one V-cycle on the levels below the finest:
+    65 B (x e/4) per unknown of every coarse level (sweeps and transfers)."""
+    e = S.selm_mg_inner_bytes(h)
+    return MODEL_LEVEL_B * (e / 4.0) * sum(level_unknowns(S, h, system)[1:])
+
+
+def model_fine_bytes_per_colour_launch(S, h):
+    """Half of a fused red+black sweep of the finest velocity level: 12 B (x e/4)
+    per unknown-sweep, two colour launches per sweep."""
+    e = S.selm_mg_inner_bytes(h)
+    return 0.5 * MODEL_SWEEP_B * (e / 4.0) * level_unknowns(S, h, 0)[0]
 
 
 # ---------------------------------------------------------------------------
@@ -585,17 +671,51 @@ def composite_cpu_baseline(n, K):
                       f"{2 * n}x{2 * n}x{2 * K} patch (3 components), single thread, {t:.2f} s"}
 
 
-def run_composite(args):
-    """Composite grid: 256^3 base channel with its bottom 32 rows refined by 2
-    (patch 512 x 512 x 64), three components, thermal samples of the chain
-    (2 stochastic composite FAC cycles per sample)."""
+def channel_covariance(S, h, n, nsamples=200):
+    """Sample covariance of the handle's thermal chain on the 4^3 wall block
+    (rows 0..3, every x-y translate) of each velocity component against the
+    exact block of A^-1 (Fourier along x and y, sine transforms across the
+    walls; the closed form the oracle is pinned against)."""
+    from paper_1003_2680_gb300 import covariance as CV
+    from tests import closed_forms as cf
     import numpy as np
-    import torch
-    from paper_1003_2680_gb300 import _build
-    _build.build()
-    from paper_1003_2680_gb300 import selm as S
+    rows = (0, 1, 2, 3)
+    res = CV.uniform_block(h, rows, nsamples=nsamples, nbatches=10)
+    kinds = [("P", "P", "C"), ("P", "P", "C"), ("P", "P", "V")]
+    exact = []
+    for kd in kinds:
+        nz = n - 1 if kd[2] == "V" else n
+        cols = {}
+        for r in rows:
+            e = np.zeros((nz, n, n))
+            e[r, 0, 0] = 1.0
+            cols[r] = cf.spectral_solve(kd, n, 1.0 / n, e)
+        sites = [(r, y, x) for r in rows for y in range(4) for x in range(4)]
+        C = np.empty((64, 64))
+        for j, (r2, y2, x2) in enumerate(sites):
+            for i, (r1, y1, x1) in enumerate(sites):
+                C[i, j] = cols[r2][r1, (y1 - y2) % n, (x1 - x2) % n]
+        exact.append(C)
+    out = CV.compare([res[c][0] for c in range(3)], [res[c][1] for c in range(3)], exact)
+    out.update(samples=res[0][2], block="4^3 wall block (z rows 0..3) of each velocity component, averaged over "
+                                         "all x-y translates", exact="A^-1 block, spectral closed form")
+    return out
 
-    n, K = args.comp_n, args.comp_k
+
+def golden_block(n, K):
+    path = os.path.join(ROOT, "tests", "golden", f"composite_probe_cov_n{n}_K{K}.txt")
+    if not os.path.exists(path):
+        return None
+    import numpy as np
+    return np.loadtxt(path)
+
+
+def composite_measure(S, n, K, steps, warmup, with_cpu, cov_samples=100):
+    """The composite workload: a thermal sample = 2 stochastic composite FAC
+    cycles of the persistent chain (256^3 base, bottom 32 rows refined by 2,
+    three components, FP32 inner cycles with FP64 residual and coarsest solve).
+    Returns the bench line as a dict."""
+    import torch
     cycles_per_sample = SAMPLE_CYCLES
     c = S.selm_comp_create(S.make_comp_desc(3, n, K, ncomp=3, precision=S.SELM_FP32_REFINE64, seed=0, instance=0))
     N = S.selm_comp_size(c)
@@ -604,13 +724,13 @@ def run_composite(args):
     (bx, by, bz), _, bsize = S.selm_comp_layout(c, 1, 0)
     cells = n ** 3 + fx * fy * fz
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         S.selm_comp_sample(c, cycles_per_sample)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     launches0 = S.selm_kernel_launches()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        for k in range(args.steps):
+        for k in range(steps):
             flush.fill_(float(k))
             ev[k][0].record()
             S.selm_comp_sample(c, cycles_per_sample)
@@ -618,7 +738,7 @@ def run_composite(args):
         torch.cuda.synchronize()
     launches = S.selm_kernel_launches() - launches0
     t_total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-    value = cells * cycles_per_sample * args.steps / t_total
+    value = cells * cycles_per_sample * steps / t_total
 
     # e2e: the same samples through the public call, each sample's 4^3 probe
     # block per component (x, y = 126..129; the two fine layers below and the two
@@ -637,7 +757,7 @@ def run_composite(args):
     host = torch.empty(sum(b - a for a, b in probe_rows), dtype=torch.float64, pin_memory=True)
     d2h = host.numel() * 8
     e2e_time = 0.0
-    for k in range(args.steps):
+    for k in range(steps):
         flush.fill_(float(k))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -648,10 +768,10 @@ def run_composite(args):
             o += b - a
         torch.cuda.synchronize()
         e2e_time += time.perf_counter() - t0
-    e2e_value = cells * cycles_per_sample * args.steps / e2e_time
+    e2e_value = cells * cycles_per_sample * steps / e2e_time
 
     # per-kernel device time and the byte model of each class (one FAC cycle)
-    prof_samples = min(args.steps, 3)
+    prof_samples = min(steps, 3)
     S.selm_profile_reset()
     S.selm_profile_enable(True)
     for _ in range(prof_samples):
@@ -667,15 +787,21 @@ def run_composite(args):
     N0, N1 = 3 * fsize, 3 * bsize
     nu = 2
     late = 3 * 2 * fy * fx           # cells of the two interface layers
+    ef = e / 4.0
+    # section 8(d)'s fused model: 12 B per unknown-sweep (x e/4) on the level a
+    # class sweeps; 65 B per unknown-cycle on the base levels below level 1;
+    # FP64 refinement 20 B per unknown for the residual and 20 B for the update
+    base_levels = N1 / 7.0            # levels 2.. of the base hierarchy: N1 (1/8 + 1/64 + ...)
     model = {   # algorithmic bytes per FAC cycle
-        # patch: 2 main passes per sweep read all of q, read r / write q at half the cells;
-        # 2 late passes on the interface layers
+        "fine_sweep": nu * MODEL_SWEEP_B * ef * N0,              # nu patch sweeps
+        "coarse_sweep": 4 * MODEL_SWEEP_B * ef * N1 + MODEL_LEVEL_B * ef * base_levels,
+        "outer_residual": 20.0 * (N0 + N1),
+        "outer_update": 20.0 * (N0 + N1),
+    }
+    per_pass = {   # the kernels as built: every pass reads its whole level
         "fine_sweep": nu * (2 * e * (N0 + N0) + 2 * e * (late + late / 2)),
-        # base level 1 red-black: 4 sweeps x 2 colours, each e (N1 + N1); levels below negligible
         "coarse_sweep": 4 * 2 * e * 2 * N1,
-        # FP64 composite residual: read z, b (16 B), write r (e)
         "outer_residual": (16 + e) * (N0 + N1),
-        # z += q: read/write z (16 B), read q (e)
         "outer_update": (16 + e) * (N0 + N1),
     }
     tot_ms = sum(v["ms"] for v in per_class.values()) or 1.0
@@ -685,10 +811,13 @@ def run_composite(args):
         pc = per_class[name]
         if pc["launches"] == 0:
             continue
-        achieved = b_cycle * ncyc / (pc["ms"] / 1e3) / 1e9
+        sec = pc["ms"] / 1e3
+        achieved = b_cycle * ncyc / sec / 1e9
         rooflines[name] = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                            "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
                            "algorithmic_bytes_per_launch": b_cycle * ncyc / pc["launches"],
+                           "per_pass_model": {"bytes_per_launch": per_pass[name] * ncyc / pc["launches"],
+                                              "frac": per_pass[name] * ncyc / sec / 1e9 / peak},
                            "avg_launch_us": pc["ms"] / pc["launches"] * 1e3,
                            "share_of_kernel_time": pc["ms"] / tot_ms}
     dominant = max(rooflines, key=lambda k: rooflines[k]["share_of_kernel_time"])
@@ -696,28 +825,98 @@ def run_composite(args):
     roof["others"] = {k: v for k, v in rooflines.items() if k != dominant}
     # a class mixes several kernels here, so the ncu traffic is given per kernel
     roof["ncu_traffic_per_launch_by_kernel"] = composite_ncu_traffic() or None
-    cpu = None if args.no_cpu_baseline else composite_cpu_baseline(128, 16)
+    unknown_cycles = (N0 + 3 * (bz - K) * by * bx) * cycles_per_sample
+    roof["whole_step_model"] = {
+        "bytes_per_step": MODEL_CYCLE_B * unknown_cycles,
+        "frac": MODEL_CYCLE_B * unknown_cycles / (t_total / steps) / 1e9 / peak,
+        "note": "114 B per unknown-cycle x composite unknowns x FAC cycles per sample / ms per sample"}
+
+    # covariance of the probe block across the interface against the oracle's block
+    cov = None
+    exact = golden_block(n, K)
+    if exact is not None and cov_samples > 0:
+        from paper_1003_2680_gb300 import covariance as CV
+        est, se, ns = CV.composite_block(c, n, K, 3, nsamples=cov_samples, nbatches=10)
+        cov = dict(CV.compare(est, se, exact), samples=ns * 3,
+                   block="4^3 probe block of one component across the coarse-fine interface (x, y = 126..129 "
+                         "in each level's indexing; fine layers 2K-2, 2K-1 and base rows K+1, K+2), averaged "
+                         "over all x-y base-cell translates and the 3 components",
+                   exact="A^-1 block from the oracle's composite FAC solves (tests/golden)")
+    cpu = composite_cpu_baseline(128, 16) if with_cpu else None
     line = {
-        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "ms_per_step": 1e3 * t_total / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64", "data": "synthetic",
         "config": {"workload": f"composite grid: {n}^3 channel (periodic x-y, walls z) with its bottom {K} rows "
                                f"refined by 2 (patch {fx}x{fy}x{fz}), 3 components, thermal samples of "
-                               f"{cycles_per_sample} stochastic FAC cycles (Algorithms 1-2), FP32 inner cycles "
-                               f"with FP64 residual and coarsest solve",
+                               f"{cycles_per_sample} stochastic FAC cycles (Algorithms 1-2), FP32 inner cycles; "
+                               f"chain residual and update in double-float (two FP32 words, ~48 bits), "
+                               f"FP64 coarsest solve",
                    "base_n": n, "patch_rows": K, "cells": cells, "unknowns": N0 + 3 * (bz - K) * by * bx,
                    "l2": "flushed between samples (256 MB write, outside the timed events)",
                    "unit_of_work": "cell-cycle = one cell (base or patch, all 3 components) through one FAC cycle",
                    "parallelism": "replicas x1"},
-        "kernel_time_share": {k: round(v["ms"] / tot_ms, 4) for k, v in per_class.items()},
+        "kernel_time_share": {k: round(v["ms"] / tot_ms, 4) for k, v in per_class.items() if v["launches"]},
         "roofline": roof,
+        "covariance": cov,
         "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
     S.selm_comp_destroy(c)
+    return line
+
+
+def run_composite(args):
+    """Composite grid: 256^3 base channel with its bottom 32 rows refined by 2
+    (patch 512 x 512 x 64), three components, thermal samples of the chain
+    (2 stochastic composite FAC cycles per sample)."""
+    from paper_1003_2680_gb300 import _build
+    _build.build()
+    from paper_1003_2680_gb300 import selm as S
+    line = composite_measure(S, args.comp_n, args.comp_k, args.steps, args.warmup, not args.no_cpu_baseline,
+                             cov_samples=200)
     print(json.dumps(line), flush=True)
+
+
+def config1_measure(S):
+    """The 64^2 2-D plain method in FP64 (6 levels, (2,2) sweeps, Cholesky
+    coarsest, Philox seed 0, 16 particles): 1000 stochastic cycles of the
+    chain and the 32 x 32 mobility (32 unit-force solves), as latencies."""
+    import numpy as np
+    import torch
+    import selm_inputs
+    m = S.SelmMG(dim=2, n=64, levels=6, precision=S.SELM_FP64, seed=0, instance=0)
+    X = torch.tensor(selm_inputs.particles(16, 2, 64, seed=0), device="cuda")
+    g = torch.zeros_like(X)
+    S.selm_mg_sample(m.h, X, 20, g)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    S.selm_mg_sample(m.h, X, 1000, g)
+    b.record()
+    torch.cuda.synchronize()
+    t_chain = a.elapsed_time(b) / 1e3
+    U = torch.zeros_like(X)
+    cols, solve_cycles = [], 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for col in range(32):
+        F = torch.zeros_like(X)
+        F[col // 2, col % 2] = 1.0
+        cyc, _ = S.selm_mg_solve(m.h, X, F, U)
+        solve_cycles += cyc
+        cols.append(U.clone())
+    torch.cuda.synchronize()
+    t_mob = time.perf_counter() - t0
+    M = torch.stack(cols, dim=2).reshape(32, 32).cpu().numpy()
+    m.close()
+    return {"workload": "2-D 64^2 plain method, FP64, 6 levels, (2,2) red-black sweeps, Cholesky coarsest",
+            "chain_us_per_cycle": 1e6 * t_chain / 1000,
+            "mobility_32x32_ms": 1e3 * t_mob, "mobility_fac_cycles": solve_cycles,
+            "mobility_symmetry": float(np.abs(M - M.T).max() / np.abs(M).max()),
+            "mobility_min_eig": float(np.linalg.eigvalsh(0.5 * (M + M.T)).min())}
 
 
 def main():
@@ -773,10 +972,13 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     stream = torch.cuda.current_stream()
 
+    pres_steps = [0]
+
     def one_step():
         S.selm_mg_step(h, X, F, DT, 1, SAMPLE_CYCLES)
-        solve_cycles = S.selm_mg_stats(h)[0]
-        return solve_cycles + SAMPLE_CYCLES
+        st = S.selm_mg_stats(h)
+        pres_steps[0] += st[1]
+        return st[0] + SAMPLE_CYCLES
 
     # burn-in of the chain + warm-up of every path
     for _ in range(args.warmup):
@@ -786,6 +988,7 @@ def main():
     # ---- timed region (device events per step, L2 flushed between steps) ----
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     cycles = 0
+    pres_before = pres_steps[0]
     launches0 = S.selm_kernel_launches()
     print(f"[bench] library kernel launches before the timed region: {launches0}", file=sys.stderr)
     with ClockSampler(local) as clk:
@@ -799,6 +1002,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
     launches = S.selm_kernel_launches() - launches0
+    pres_steps_cycles = pres_steps[0] - pres_before
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_total = sum(step_ms) / 1e3
     t_total, cycles_all = whole_job(t_total, cycles, world, "cuda")
@@ -843,22 +1047,36 @@ def main():
     tot_ms = sum(v["ms"] for v in per_class.values()) or 1.0
     dominant = max(per_class, key=lambda k: per_class[k]["ms"])
     peak, peak_kind = measured_peaks()
-    coarse_bytes = vel_cycles * coarse_bytes_per_vcycle(S, h, 0)
+    # section 8(d)'s byte model (the roofline's algorithmic bytes) and, as a
+    # labelled extra, the per-colour-pass bytes of the kernels as built
+    coarse_model = vel_cycles * model_coarse_bytes_per_vcycle(S, h, 0)
+    coarse_pass = vel_cycles * coarse_bytes_per_vcycle(S, h, 0)
     if proj == S.SELM_PROJ_MAC:
-        coarse_bytes += pres_cycles * coarse_bytes_per_vcycle(S, h, 1)
+        coarse_model += pres_cycles * model_coarse_bytes_per_vcycle(S, h, 1)
+        coarse_pass += pres_cycles * coarse_bytes_per_vcycle(S, h, 1)
     roof = None
     for name in (dominant, "fine_sweep"):
         if name not in ("fine_sweep", "coarse_sweep") or per_class[name]["launches"] == 0:
             continue
-        avg_s = per_class[name]["ms"] / per_class[name]["launches"] / 1e3
+        nl = per_class[name]["launches"]
+        avg_s = per_class[name]["ms"] / nl / 1e3
         if name == "fine_sweep":
-            bytes_launch = fine_bytes_per_launch(S, h)
+            bytes_launch = model_fine_bytes_per_colour_launch(S, h)
+            pass_launch = fine_bytes_per_launch(S, h)
         else:   # engine and cooperative launches: the coarse bytes of the profiled steps over their launches
-            bytes_launch = coarse_bytes / per_class[name]["launches"]
+            bytes_launch = coarse_model / nl
+            pass_launch = coarse_pass / nl
         achieved = bytes_launch / avg_s / 1e9
         entry = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                  "frac": achieved / peak, "peak_source": peak_kind,
                  "traffic": ncu_traffic(name, n), "algorithmic_bytes_per_launch": bytes_launch,
+                 "bytes_model": "section 8(d): 12 B per unknown-sweep (fused red+black) on the finest level; "
+                                "65 B per unknown-cycle on each coarse level",
+                 "per_pass_model": {"bytes_per_launch": pass_launch,
+                                    "achieved": pass_launch / avg_s / 1e9,
+                                    "frac": pass_launch / avg_s / 1e9 / peak,
+                                    "note": "every colour pass reads its whole level, reads b and writes v "
+                                            "at its colour (the kernels as built)"},
                  "avg_launch_us": avg_s * 1e6, "share_of_kernel_time": per_class[name]["ms"] / tot_ms}
         if roof is None:
             roof = entry
@@ -866,6 +1084,19 @@ def main():
             roof["fine_sweep"] = entry
     if roof is None:
         roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None}
+    # whole step against the 114 B per unknown-cycle model, over every V-cycle
+    # executed (velocity solve + chain, and the projections' pressure solves)
+    n_vel = level_unknowns(S, h, 0)[0]
+    n_pres = level_unknowns(S, h, 1)[0] if proj == S.SELM_PROJ_MAC else 0
+    vel_per_step = cycles_all / args.steps / world
+    pres_per_step = pres_steps_cycles / args.steps if args.steps else 0.0
+    unknown_cycles_step = vel_per_step * n_vel + pres_per_step * n_pres
+    step_s = t_total / args.steps
+    roof["whole_step_model"] = {
+        "bytes_per_step": MODEL_CYCLE_B * unknown_cycles_step,
+        "achieved": MODEL_CYCLE_B * unknown_cycles_step / step_s / 1e9,
+        "frac": MODEL_CYCLE_B * unknown_cycles_step / step_s / 1e9 / peak,
+        "note": "114 B per unknown-cycle x every V-cycle of the step (velocity and pressure) / ms_per_step"}
 
     clocks = clk.summary()
     line = {
@@ -876,6 +1107,9 @@ def main():
                        engine_first_level=S.selm_mg_engine_info(h)[0],
                        parallelism=f"replicas x{world} (independent systems, no collective on the data path)"),
         "velocity_vcycles_per_step": cycles_all / args.steps / world,
+        "vcycles_per_step": {"velocity": vel_per_step, "pressure": pres_per_step,
+                             "total": vel_per_step + pres_per_step},
+        "unknown_cycles_per_s_all_vcycles": unknown_cycles_step / step_s * world,
         "roofline": roof,
         "kernel_time_share": {k: round(v["ms"] / tot_ms, 4) for k, v in per_class.items() if v["launches"]},
         "e2e": {"value": e2e_value, "unit": "cells/s",
@@ -883,13 +1117,26 @@ def main():
         "gpu_launches": int(launches),
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
+    # the chain's sample covariance on 4^3 wall blocks of every velocity
+    # component against the exact A^-1 blocks (spectral closed form)
+    if not args.no_extras:
+        line["covariance"] = channel_covariance(S, h, n)
+    m.close()
+    if rank == 0 and not args.no_extras:
+        # the composite workload (where the HBM target is judged) and the 2-D
+        # 64^2 FP64 configuration, measured in the same run
+        torch.cuda.empty_cache()
+        comp = composite_measure(S, args.comp_n, args.comp_k, steps=60, warmup=3, with_cpu=False)
+        line["composite"] = {k: comp[k] for k in ("value", "unit", "ms_per_step", "dtype", "config", "roofline",
+                                                  "covariance", "e2e", "gpu_launches", "clocks",
+                                                  "kernel_time_share", "steps", "warmup")}
+        line["config1_64x64_fp64"] = config1_measure(S)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     elif rank == 0:
         line["cpu_baseline"] = None
     if rank == 0:
         print(json.dumps(line), flush=True)
-    m.close()
     if world > 1:
         dist.destroy_process_group()
 

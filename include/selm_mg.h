@@ -252,19 +252,26 @@ selm_status selm_mg_em_update(selm_mg* h, int np, double* X, const double* V, vo
 
 /* One V-cycle like selm_mg_vcycle (velocity system) for callers that cannot
    allocate device memory: no cudaMalloc, no pinned host buffer, no allocator
-   hook.  The paper has no counterpart; this is a deployment convenience.
+   hook.  Such callers are, for example, a service that plans its whole device
+   memory budget up front and forbids allocation once it runs, or a thread
+   that cannot reach the allocator of the framework that owns the device.
+   The paper has no counterpart; this is a deployment convenience.
    Its scratch (Galerkin tables, coarse-level fields, the level-0 residual
-   buffer, counters) lives in one fixed 16 MiB device array that every device
-   loading this library keeps until the process exits; grids whose scratch
-   does not fit (roughly above 64^3 in FP32) are rejected with SELM_EINVAL
-   and a message on stderr.  `desc` describes the grid as for
-   selm_mg_create (projection and allocator fields are ignored); v and b are
-   level-0 inner-precision fields in the selm_mg_layout order.  The first call
-   on a device, and the first call after the descriptor changes, builds the
-   hierarchy into the array and synchronises `stream`; make that call before
-   any stream capture.  All calls share the array: the level fields are
-   cleared inside each V-cycle and the counter slot is rewritten per call,
-   but calls that overlap on the GPU (other streams, other threads) race. */
+   buffer, counters, the coarse-engine plan) lives in one fixed 16 MiB device
+   array that every device loading this library keeps until the process
+   exits; grids whose scratch does not fit (3-D: roughly above 80^3 in FP32,
+   64^3 in FP64) are rejected with SELM_EINVAL and a message on stderr.
+   `desc` describes the grid as for selm_mg_create (projection and allocator
+   fields are ignored); v and b are level-0 inner-precision fields in the
+   selm_mg_layout order.  The first call on a device, and the first call
+   after the descriptor changes, builds the hierarchy into the array: it
+   looks up the array's device address, copies the tables and synchronises
+   `stream`, so make that call before any stream capture (a set-up requested
+   on a capturing stream is refused with SELM_EINVAL).  All calls share the
+   array: the level fields are cleared inside each V-cycle and the counter
+   slot is rewritten per call, but calls that overlap on the GPU (other
+   streams, other threads) race.  Host calls from several threads are
+   serialised per device. */
 selm_status selm_mg_vcycle_static(const selm_mg_desc* desc, void* v, const void* b, uint64_t cycle,
                                   int noise, void* stream);
 

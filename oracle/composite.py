@@ -3,7 +3,7 @@
 Test infrastructure (plain FP64 numpy/scipy, follows the paper step by step):
 only tests and the benchmark's CPU baseline call it.
 
-Geometry (readings R19, R20, R24 of the design notes):
+Geometry (readings R14, R15 and R17 of the design notes):
 
 * Base grid: n cells along each periodic axis (x, and y in 3-D), H = 1/n.
   The wall axis z has its cell centres on the walls (Section 4: Dirichlet
@@ -22,14 +22,14 @@ Geometry (readings R19, R20, R24 of the design notes):
   borders its top layer across z = (K + 1/2) H.  Both are coarse-fine faces.
 
 Operator (Section 4, Eqs. equ_def_discr_div to equ_def_L, L = DG, and the
-symmetric form A = -mu V L of reading R22): the divergence is the
+symmetric form A = -mu V L of reading R16): the divergence is the
 face-area-weighted flux sum over a cell's faces divided by its volume; the
 gradient across a face between equal cells is the difference over the
 spacing; across a coarse-fine face it is (mean of the 2^(d-1) fine values -
 coarse value) over (3/4) H on every fine face, and the coarse face carries the
 mean of the fine-face values (Eqs. equ_def_discr_grad to
 equ_def_discr_grad_last, with the four fine neighbours B, C, D, E in 3-D,
-reading R21).  Then A = -mu V L is the quadratic form
+reading R16).  Then A = -mu V L is the quadratic form
     c^T A c = mu * sum over faces  w_f * (delta_f c)^2
 with w = h^(d-2) (delta = difference) on a face between two fine cells,
 w = H^(d-2) between two base cells (and at the top wall, delta = c), and
@@ -37,7 +37,7 @@ w = (4/3) H^(d-2), delta = c_coarse - mean(c_fine), for each coarse-fine group
 (the wall group has c_coarse = 0).  It is symmetric by construction and
 positive definite.
 
-FAC (Algorithm 1 around Algorithm 2, readings R6, R7, R24):
+FAC (Algorithm 1 around Algorithm 2, readings R6, R25, R17):
     r   = b - A z                                  (composite residual)
     r_b = P^T r                                    (restriction to the base)
     q_b = V-Cycle(0, r_b) on the base hierarchy    (Algorithm 3; level 1 = base)
@@ -45,13 +45,13 @@ FAC (Algorithm 1 around Algorithm 2, readings R6, R7, R24):
     nu  Gibbs sweeps on the patch cells of A q = r (composite rows)
     z  += q
 P (base -> composite) is the identity on uncovered base cells and gives each
-fine cell its parent's value (piecewise constant, reading R24); the base
+fine cell its parent's value (piecewise constant, reading R17); the base
 operator is the Galerkin product A_b = P^T A P, which is the 7-point operator
 with z-dependent weights built in ``base_factors`` (pinned against the triple
 product).  The base hierarchy below is the usual Galerkin hierarchy with
 tri-linear transfers.  Level numbering: 0 = patch, 1 = base, 2.. = coarser.
 
-Patch sweep order (reading R25): the patch rows of A couple a fine cell to
+Patch sweep order (reading R18): the patch rows of A couple a fine cell to
 its 2^(d-1) siblings across a coarse-fine face, so a red-black order is not a
 valid Gibbs order on the two interface layers (m = 0 and m = 2K-1).  A sweep
 is four passes: red sites except the interface-layer sites with odd p, then
@@ -175,7 +175,7 @@ class CompositeGrid:
 
     # -- transfers -----------------------------------------------------------
     def _prolongation(self):
-        """P: base field (all rows, flattened) -> composite vector (reading R24)."""
+        """P: base field (all rows, flattened) -> composite vector (reading R17)."""
         bz, by, bx = self.base_shape
         nb = bz * by * bx
         fz, fy, fx = self.fine_shape
@@ -197,7 +197,7 @@ class CompositeGrid:
 
     # -- patch sweeps ---------------------------------------------------------
     def pass_sets(self):
-        """Linear fine indices of the four passes of a patch sweep (reading R25)."""
+        """Linear fine indices of the four passes of a patch sweep (reading R18)."""
         fz, fy, fx = self.fine_shape
         m, q, p = np.meshgrid(np.arange(fz), np.arange(fy), np.arange(fx), indexing="ij")
         red = ((m + q + p) & 1) == 0
@@ -321,7 +321,7 @@ def fac_cycle(cg, z, b, noise, sigma, mu1=2, mu2=2, nu=2, coarse_mode="cholesky"
     qb = cg.base.zeros(1)
     multigrid.vcycle(cg.base, 1, qb, rb, noise, sigma, mu1, mu2, coarse_mode, coarsest)  # step 3
     for c in range(cg.ncomp):
-        q = cg.prolong(qb[c])                                          # step 4 (reading R7)
+        q = cg.prolong(qb[c])                                          # step 4 (reading R25)
         for s in range(nu):                                            # step 5
             cg.patch_sweep(q, r[c], cg.comp_ids[c], s, noise, sigma)
         z[c] += q                                                      # Alg. 1 step 4
@@ -329,7 +329,7 @@ def fac_cycle(cg, z, b, noise, sigma, mu1=2, mu2=2, nu=2, coarse_mode="cholesky"
 
 
 def solve(cg, b, tol=1e-10, max_cycles=200, v0=None, mu1=2, mu2=2, nu=2, coarse_mode="cholesky"):
-    """Deterministic composite FAC until ||b - A z|| <= tol ||b|| (reading R10)."""
+    """Deterministic composite FAC until ||b - A z|| <= tol ||b|| (reading R9)."""
     from .philox import ExplicitNoise
     coarsest = multigrid.Coarsest(cg.base) if coarse_mode == "cholesky" else None
     z = [np.zeros(cg.size) for _ in range(cg.ncomp)] if v0 is None else [x.copy() for x in v0]

@@ -13,7 +13,7 @@ Gamma interpolates each velocity component at a particle from the 4^d nodes
 of that component's staggered lattice with weights prod_d phi((X_d - x_d)/h)
 (Eq. equ_dX_dt_Gamma, U = Gamma u).  Weights that fall on nodes that are not
 unknowns (wall nodes or beyond the walls) are dropped in both Gamma and
-Gamma^T (reading R14), which keeps the two exactly adjoint.  With A scaled by
+Gamma^T (reading R11), which keeps the two exactly adjoint.  With A scaled by
 h^d, spreading with Gamma^T is the force density Lambda F = h^-d Gamma^T F
 multiplied by h^d (alpha = h^-d).
 """

@@ -345,7 +345,7 @@ class System:
 
 
 def default_levels(n, dim):
-    """Coarsen while the edge stays even and at least 4 after halving (reading R9)."""
+    """Coarsen while the edge stays even and at least 4 after halving (reading R8)."""
     levels = 1
     m = n
     while m % 2 == 0 and m // 2 >= 4:

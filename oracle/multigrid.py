@@ -16,7 +16,7 @@ V-Cycle(v, b) at level l (Algorithm 3):
     4. v^(l) <- v^(l) + P v^(l+1)
     5. mu2 stochastic smoothing sweeps
 
-Coarsest level (reading R8): the paper only smooths there.  The default here
+Coarsest level (reading R7): the paper only smooths there.  The default here
 ("cholesky") replaces steps 1 and 5 at the coarsest level by an exact draw
 from the level's conditional distribution, v = A_c^-1 b + sigma L_c^-T n with
 A_c = L_c L_c^T, an exact block heat-bath update that keeps the invariant
@@ -107,7 +107,7 @@ def residual_norm(system, v, b):
 
 def solve(system, b, tol=1e-10, max_cycles=100, v0=None, mu1=2, mu2=2,
           coarse_mode="cholesky", coarsest=None):
-    """Deterministic FAC iteration until ||b - A v||_2 <= tol ||b||_2 (reading R10).
+    """Deterministic FAC iteration until ||b - A v||_2 <= tol ||b||_2 (reading R9).
 
     Returns (v, cycles, relative residual).
     """

@@ -14,8 +14,8 @@ Euler-Maruyama step (Algorithm 4 step 4):
     X <- X + dt M F + sqrt(dt) g
        = X + Gamma P~ ( dt A^-1 P~ Gamma^T F + sqrt(2 kT dt) xi )
 followed by periodic wrap in x (and y) and reflection at the walls
-(reading R16).  No drift correction is added (the paper assumes
-div_X H = 0, reading R15).
+(reading R12).  No drift correction is added (the paper assumes
+div_X H = 0, reading R12).
 """
 
 import numpy as np

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -120,8 +121,11 @@ void plan_tables(const HostSystem& hs, int si, Plan* p) {
   }
 }
 
+// vcycle_only: V-cycle scratch only.  caller_level0: the caller passes the
+// level-0 v and b of every V-cycle, so level 0 reserves its residual buffer
+// alone (v and b stay unbound).
 void make_plan(const selm_mg_desc& d, const Sys& vel, const Sys* pres, int esize, Plan* p,
-               bool vcycle_only = false) {
+               bool vcycle_only = false, bool caller_level0 = false) {
   plan_tables(vel.host, 0, p);
   if (pres) plan_tables(pres->host, 1, p);
   p->dbl_off = p->lay.add(p->dbl.size() * sizeof(double) + 8);
@@ -131,7 +135,10 @@ void make_plan(const selm_mg_desc& d, const Sys& vel, const Sys* pres, int esize
   for (int si = 0; si < 2; ++si) {
     if (!hs[si]) continue;
     for (int l = 0; l < hs[si]->levels; ++l)
-      for (int f = 0; f < 3; ++f) p->field_off[si][l][f] = p->lay.add((size_t)hs[si]->level_size(l) * esize);
+      for (int f = 0; f < 3; ++f) {
+        if (caller_level0 && l == 0 && f < 2) continue;
+        p->field_off[si][l][f] = p->lay.add((size_t)hs[si]->level_size(l) * esize);
+      }
   }
   if (vcycle_only) {   // V-cycle scratch only: tables, level fields, counters, engine plan
     p->eng_off[0] = p->lay.add(kEngParamBytes);
@@ -1207,13 +1214,13 @@ selm_status selm_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1
 // V-cycle without device allocation.
 //
 // For callers that cannot allocate device memory themselves or through us at
-// run time -- for example code running inside a CUDA graph that is being
-// captured, a host with a fixed pre-planned memory budget, or a framework
-// whose allocator is not reachable from the calling thread -- this entry
-// point runs one V-cycle with all of its scratch (Galerkin tables, level
-// fields, counters, the coarse-engine plan) in the fixed device array below.
-// Every device that loads this library holds the array until the process
-// exits.
+// run time -- for example a service that fixes its device memory budget up
+// front and forbids allocation while it runs, or a thread that cannot reach
+// the allocator of the framework owning the device -- this entry point runs
+// one V-cycle with all of its scratch (Galerkin tables, coarse-level fields,
+// the level-0 residual buffer, counters, the coarse-engine plan) in the fixed
+// device array below.  Every device that loads this library holds the array
+// until the process exits.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -1228,11 +1235,103 @@ struct StaticSlot {
   selm_mg* h = nullptr;   // host-side bookkeeping; its workspace is g_static_scratch
 };
 StaticSlot g_static_slots[kStaticMaxDevices];
+// Host bookkeeping of a slot (its tables, plans and key) is rebuilt in place;
+// one lock per device serialises the host side of concurrent calls.
+std::mutex g_static_locks[kStaticMaxDevices];
 
 bool same_vcycle_desc(const selm_mg_desc& a, const selm_mg_desc& b) {
   return a.dim == b.dim && a.n == b.n && a.mu == b.mu && a.levels == b.levels && a.nu_pre == b.nu_pre &&
          a.nu_post == b.nu_post && a.precision == b.precision && a.coarse_mode == b.coarse_mode &&
          a.seed == b.seed && a.instance == b.instance;
+}
+
+// Builds the hierarchy of descriptor d inside the static array (the set-up of
+// create_with_host, without an allocation).  Synchronises st.
+selm_status static_setup(StaticSlot& slot, const selm_mg_desc& d, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    std::fprintf(stderr,
+                 "selm_mg_vcycle_static: set-up for a new descriptor copies tables and synchronises the stream; "
+                 "make the first call with this descriptor outside stream capture\n");
+    return SELM_EINVAL;
+  }
+  selm_mg* h = slot.h ? slot.h : new (std::nothrow) selm_mg();
+  if (!h) return SELM_ENOMEM;
+  slot.h = h;
+  slot.ready = false;
+  h->d = d;
+  h->vel = Sys();
+  h->pres = Sys();
+  h->has_pres = false;
+  std::string e = build_systems(d, &h->vel, &h->pres, &h->has_pres);
+  if (!e.empty()) {
+    std::fprintf(stderr, "selm_mg_vcycle_static: %s\n", e.c_str());
+    return SELM_EINVAL;
+  }
+  h->mu1 = d.nu_pre;
+  h->mu2 = d.nu_post;
+  h->esize = d.precision == SELM_FP64 ? 8 : 4;
+  h->key.k0 = (uint32_t)(d.seed & 0xffffffffu) ^ (uint32_t)(d.instance >> 32);
+  h->key.k1 = (uint32_t)(d.seed >> 32) ^ (uint32_t)(d.instance & 0xffffffffu);
+  Plan p;
+  make_plan(d, h->vel, nullptr, h->esize, &p, true, true);
+  if (p.lay.total > kStaticScratchBytes) {
+    std::fprintf(stderr,
+                 "selm_mg_vcycle_static: this grid needs %zu bytes of scratch, above the static limit of %zu bytes\n",
+                 p.lay.total, kStaticScratchBytes);
+    return SELM_EINVAL;
+  }
+  // In host code g_static_scratch names a host-side stand-in; the device
+  // address must come from the runtime, with this device current.
+  void* base = nullptr;
+  cudaError_t ce = cudaGetSymbolAddress(&base, g_static_scratch);
+  if (ce != cudaSuccess || !base) {
+    std::fprintf(stderr, "selm_mg_vcycle_static: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(ce));
+    cudaGetLastError();
+    return SELM_ECUDA;
+  }
+  h->ws = (char*)base;
+  h->ws_bytes = kStaticScratchBytes;
+  if (!p.dbl.empty())
+    ce = cudaMemcpyAsync(h->ws + p.dbl_off, p.dbl.data(), p.dbl.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && !p.flt.empty())
+    ce = cudaMemcpyAsync(h->ws + p.flt_off, p.flt.data(), p.flt.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && !p.ints.empty())
+    ce = cudaMemcpyAsync(h->ws + p.int_off, p.ints.data(), p.ints.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  bind_system(&h->vel, 0, p, h->ws);
+  h->vel.v[0] = nullptr;   // level 0 works on the caller's v and b
+  h->vel.b[0] = nullptr;
+  h->red = (double*)(h->ws + p.red_off);
+  h->vel.coop_bar = (unsigned*)(h->red + 8);
+  h->cyc = (unsigned long long*)(h->ws + p.cyc_off);
+  // a previous descriptor's bytes may sit at these offsets
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->red, 0, 16 * sizeof(double), st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->cyc, 0, 4 * sizeof(unsigned long long), st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);   // the host tables are temporaries
+  if (ce != cudaSuccess) {
+    std::fprintf(stderr, "selm_mg_vcycle_static: %s\n", cudaGetErrorString(ce));
+    return SELM_ECUDA;
+  }
+  h->vel.eng_dev = h->ws + p.eng_off[0];
+  const int first = engine_first_level(h, h->vel);
+  // Without an engine plan (no cluster shape fits) the per-pass path runs; a
+  // CUDA error while planning is an error.
+  if (h->esize == 4)
+    plan_coarse_engine<float>(h->vel.lev, h->vel.levels, h->vel.b, h->vel.v, h->vel.t, h->vel.eng_dev, st,
+                              &h->vel.engf, 0, first);
+  else
+    plan_coarse_engine<double>(h->vel.lev, h->vel.levels, h->vel.b, h->vel.v, h->vel.t, h->vel.eng_dev, st,
+                               &h->vel.engd, 0, first);
+  ce = cudaStreamSynchronize(st);
+  if (ce == cudaSuccess) ce = cudaGetLastError();
+  if (ce != cudaSuccess) {
+    std::fprintf(stderr, "selm_mg_vcycle_static: planning the coarse levels failed: %s\n", cudaGetErrorString(ce));
+    return SELM_ECUDA;
+  }
+  slot.key = d;
+  slot.ready = true;
+  return SELM_OK;
 }
 
 }  // namespace
@@ -1254,69 +1353,11 @@ extern "C" selm_status selm_mg_vcycle_static(const selm_mg_desc* desc, void* v, 
     return SELM_EINVAL;
   }
   cudaStream_t st = S(stream);
+  std::lock_guard<std::mutex> lock(g_static_locks[dev]);
   StaticSlot& slot = g_static_slots[dev];
   if (!slot.ready || !same_vcycle_desc(slot.key, d)) {
-    // (Re)build the hierarchy for this descriptor inside the static array.
-    selm_mg* h = slot.h ? slot.h : new (std::nothrow) selm_mg();
-    if (!h) return SELM_ENOMEM;
-    slot.h = h;
-    slot.ready = false;
-    h->d = d;
-    h->vel = Sys();
-    h->pres = Sys();
-    h->has_pres = false;
-    e = build_systems(d, &h->vel, &h->pres, &h->has_pres);
-    if (!e.empty()) {
-      std::fprintf(stderr, "selm_mg_vcycle_static: %s\n", e.c_str());
-      return SELM_EINVAL;
-    }
-    h->mu1 = d.nu_pre;
-    h->mu2 = d.nu_post;
-    h->esize = d.precision == SELM_FP64 ? 8 : 4;
-    h->key.k0 = (uint32_t)(d.seed & 0xffffffffu) ^ (uint32_t)(d.instance >> 32);
-    h->key.k1 = (uint32_t)(d.seed >> 32) ^ (uint32_t)(d.instance & 0xffffffffu);
-    Plan p;
-    make_plan(d, h->vel, nullptr, h->esize, &p, true);
-    if (p.lay.total > kStaticScratchBytes) {
-      std::fprintf(stderr,
-                   "selm_mg_vcycle_static: this grid needs %zu bytes of scratch, above the static limit of %zu bytes\n",
-                   p.lay.total, kStaticScratchBytes);
-      return SELM_EINVAL;
-    }
-    // In host code g_static_scratch names a host-side stand-in; the device
-    // address must come from the runtime, with this device current.
-    void* base = nullptr;
-    cudaError_t ce = cudaGetSymbolAddress(&base, g_static_scratch);
-    if (ce != cudaSuccess || !base) {
-      std::fprintf(stderr, "selm_mg_vcycle_static: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(ce));
-      cudaGetLastError();
-      return SELM_ECUDA;
-    }
-    h->ws = (char*)base;
-    h->ws_bytes = kStaticScratchBytes;
-    if (!p.dbl.empty())
-      ce = cudaMemcpyAsync(h->ws + p.dbl_off, p.dbl.data(), p.dbl.size() * sizeof(double), cudaMemcpyHostToDevice, st);
-    if (ce == cudaSuccess && !p.flt.empty())
-      ce = cudaMemcpyAsync(h->ws + p.flt_off, p.flt.data(), p.flt.size() * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (ce == cudaSuccess && !p.ints.empty())
-      ce = cudaMemcpyAsync(h->ws + p.int_off, p.ints.data(), p.ints.size() * sizeof(int), cudaMemcpyHostToDevice, st);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);   // the host tables are temporaries
-    if (ce != cudaSuccess) {
-      std::fprintf(stderr, "selm_mg_vcycle_static: %s\n", cudaGetErrorString(ce));
-      return SELM_ECUDA;
-    }
-    bind_system(&h->vel, 0, p, h->ws);
-    h->red = (double*)(h->ws + p.red_off);
-    h->cyc = (unsigned long long*)(h->ws + p.cyc_off);
-    if (h->esize == 4)
-      plan_coarse_engine<float>(h->vel.lev, h->vel.levels, h->vel.b, h->vel.v, h->vel.t, h->ws + p.eng_off[0], st,
-                                &h->vel.engf);
-    else
-      plan_coarse_engine<double>(h->vel.lev, h->vel.levels, h->vel.b, h->vel.v, h->vel.t, h->ws + p.eng_off[0], st,
-                                 &h->vel.engd);
-    cudaGetLastError();
-    slot.key = d;
-    slot.ready = true;
+    const selm_status r = static_setup(slot, d, st);
+    if (r != SELM_OK) return r;
   }
   selm_mg* h = slot.h;
   // The counter slot keeps the previous call's value: set it for this call.

@@ -13,8 +13,10 @@ constexpr int kMaxLevels = 16;
 constexpr int kMaxComps = 3;
 constexpr int kStencil = 45;  // 5 (z) x 3 (y) x 3 (x) Galerkin stencil, offsets z -2..2, y/x -1..1
 
-// 1-D lattice kinds (Section 4 discretization; see the oracle's grid module
-// for the same definitions written independently in numpy).
+// 1-D lattice kinds of the MAC discretization of Section 4: periodic axes,
+// the wall-normal lattice with its nodes on the walls, and cell lattices
+// half a cell from the walls (odd ghost for no-slip velocity, even ghost for
+// the Neumann pressure).
 enum AxisKind : int {
   kAxisPeriodic = 0,   // periodic, n nodes
   kAxisVertex = 1,     // wall-normal lattice, n-1 interior nodes, Dirichlet wall nodes

@@ -40,6 +40,15 @@ def rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+def maxrel(a, b):
+    """max |a - b| / max |b|: an element-wise bound that a field-norm
+    comparison cannot give (one bad row among millions of good ones)."""
+    a = np.concatenate([x.ravel() for x in a]) if isinstance(a, list) else np.asarray(a).ravel()
+    b = np.concatenate([x.ravel() for x in b]) if isinstance(b, list) else np.asarray(b).ravel()
+    mb = np.abs(b).max() if b.size else 0.0
+    return np.abs(a - b).max() / (mb if mb > 0 else 1.0)
+
+
 def round_like(fields, dtype):
     if dtype == torch.float32:
         return [f.astype(np.float32).astype(np.float64) for f in fields]

@@ -176,6 +176,31 @@ def test_chain(S, prec, dim, n, K):
     S.selm_comp_destroy(c)
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("n,K", [(128, 16), (256, 8)])
+def test_fac_cycle_on_the_benchmark_base_paths(S, n, K):
+    """One stochastic FP32 FAC cycle against the oracle on grids whose base
+    hierarchy takes the launch paths of the benchmark's 256^3 grid: at n = 128
+    the 64^3 level runs in cooperative launches and the levels below in the
+    cluster engine; at n = 256 level 2 (128^3) takes one launch per colour
+    pass, level 3 the cooperative launches and levels 4+ the engine, all with
+    the z-dependent Galerkin bands of the covered rows.  Compared over the
+    whole vector and element by element on the cycle's correction."""
+    c, cg = handle(S, 3, n, K, "fp32", ncomp=1, seed=3, instance=1, mu=1.0)
+    z, b = rand_vecs(cg, 15, scale=1e-2), rand_vecs(cg, 16)
+    zg = dev(to_gpu(cg, z))
+    S.selm_comp_fac_cycle(c, zg, dev(to_gpu(cg, b)), 4, 1)
+    want = [x.copy() for x in z]
+    OC.fac_cycle(cg, want, b, PhiloxNoise(3, 1, 4), 1.0)
+    got = from_gpu(cg, zg.cpu().numpy())
+    d_got = [g - z0 for g, z0 in zip(got, z)]
+    d_want = [w - z0 for w, z0 in zip(want, z)]
+    assert rel(d_got, d_want) < 1e-5
+    err = np.abs(d_got[0] - d_want[0]).max() / np.abs(d_want[0]).max()
+    assert err < 1e-5, err
+    S.selm_comp_destroy(c)
+
+
 def test_invalid_descriptors(S):
     for kw in [dict(dim=4, n=8, K=2), dict(dim=3, n=7, K=2), dict(dim=3, n=8, K=7), dict(dim=3, n=8, K=0)]:
         d = S.make_comp_desc(**kw)

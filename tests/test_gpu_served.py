@@ -108,3 +108,34 @@ def test_benchmark_shapes_same_alone_and_in_the_mix(S):
         assert not np.array_equal(a, x0)
         err = np.linalg.norm(m - a) / np.linalg.norm(a - x0)
         assert err < 1e-9, (i, err)
+
+
+def test_served_results_equal_the_oracle(S):
+    """Two FP64 requests served side by side (two slots, both on the device at
+    once) end where the oracle's Euler-Maruyama steps (Algorithm 4) put them."""
+    from oracle import selm as oselm
+    reqs = [(3, 16, 20, 3, 0.7, 31, 3), (2, 32, 12, 2, 1.4, 32, 4)]   # dim, n, np, steps, kT, seed, levels
+    srv = S.selm_server_create(1 << 30, 2)
+    Xs = []
+    for i, (dim, n, npart, nsteps, kT, seed, levels) in enumerate(reqs):
+        X = np.ascontiguousarray(selm_inputs.particles(npart, dim, n, seed=seed))
+        F = np.ascontiguousarray(selm_inputs.forces(npart, dim, seed=seed))
+        Xs.append(X)
+        d = S.make_desc(dim=dim, n=n, kT=kT, levels=levels, precision=S.SELM_FP64, seed=seed, instance=seed,
+                        torch_allocator=False)
+        S.selm_server_submit(srv, d, X, F, 1e-3, nsteps, 2, user=i + 1)
+    S.selm_server_drain(srv)
+    results = S.selm_server_poll(srv)
+    stats = S.selm_server_stats(srv)
+    S.selm_server_destroy(srv)
+    assert len(results) == 2 and all(r["status"] == 0 for r in results)
+    assert stats["peak_slots"] == 2
+    for (dim, n, npart, nsteps, kT, seed, levels), X in zip(reqs, Xs):
+        X0 = selm_inputs.particles(npart, dim, n, seed=seed)
+        F0 = selm_inputs.forces(npart, dim, seed=seed)
+        om = oselm.Model(n, dim, kT=kT, levels=levels, seed=seed, instance=seed)
+        Xo = X0.copy()
+        for _ in range(nsteps):
+            Xo, _ = om.em_step(Xo, F0, 1e-3, 2)
+        err = np.linalg.norm(X - Xo) / np.linalg.norm(Xo - X0)
+        assert err < 1e-12, (dim, n, err)

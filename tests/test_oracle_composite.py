@@ -213,3 +213,23 @@ def test_patch_noise_stream_is_indexed_by_site():
     b = np.concatenate([nz.patch(1, 2, 0, np.array([i])) for i in idx])
     assert np.array_equal(a, b)
     assert not np.array_equal(nz.patch(1, 3, 0, idx), a)
+
+
+def test_probe_block_script_matches_dense_inverse():
+    """The stored probe covariance of the composite sampler is written by
+    tests/golden/make_composite_probe_cov.py from ten FAC solves and the grid's
+    translation invariance.  On a small grid its block equals the block of
+    the dense inverse of the composite operator (Section 3: the chain samples
+    N(0, A^-1)), so the shift bookkeeping and the probe addressing are right."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_composite_probe_cov as mk
+    n, K = 8, 2
+    B = mk.block(n, K)
+    cg = C.CompositeGrid(n, K, 3, mu=1.0, ncomp=1)
+    Ainv = np.linalg.inv(cg.A.toarray())
+    idx = [cg.fine_index(z, y, x) if part == 0 else cg.base_index(z, y, x) for part, z, y, x in mk.probe_sites(n, K)]
+    want = Ainv[np.ix_(idx, idx)]
+    assert np.abs(B - want).max() < 1e-7 * np.abs(want).max()
+    assert np.abs(B - B.T).max() < 1e-7 * np.abs(want).max()

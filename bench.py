@@ -71,7 +71,7 @@ def parse_args():
     p.add_argument("--comp-n", type=int, default=256, help="composite workload: base cells per axis")
     p.add_argument("--comp-k", type=int, default=32, help="composite workload: refined base rows")
     p.add_argument("--systems", type=int, default=64)
-    p.add_argument("--requests", type=int, default=100)
+    p.add_argument("--requests", type=int, default=5000)
     p.add_argument("--rate", type=float, default=200.0)
     p.add_argument("--slots", type=int, default=12)
     p.add_argument("--budget-gb", type=float, default=32.0)
@@ -402,10 +402,13 @@ def model_fine_bytes_per_colour_launch(S, h):
 # ---------------------------------------------------------------------------
 def run_batched(args):
     """64 independent 3-D channel systems, edges drawn from {32,48,64,96,128},
-    64..2048 particles (log-uniform), kT ~ U[0.5, 2], seed i.  Batched form
-    (graphs over all systems) against the plain per-instance loop."""
+    64..2048 particles (log-uniform), kT ~ U[0.5, 2], seed i.  The batched
+    form (persistent launch per FAC cycle, or per-system graphs; the autotuner
+    keeps the faster) against the plain per-instance method run one system
+    after another and run on 16 concurrent streams."""
     import numpy as np
     import torch
+    from concurrent.futures import ThreadPoolExecutor
     from paper_1003_2680_gb300 import _build
     _build.build()
     from paper_1003_2680_gb300 import selm as S
@@ -421,12 +424,13 @@ def run_batched(args):
     X0 = [selm_inputs.particles(npart, 3, e, seed=i) for i, (npart, e) in enumerate(zip(nps, edges))]
     F0 = [selm_inputs.forces(npart, 3, seed=i) for i, npart in enumerate(nps)]
     cells = [e ** 3 for e in edges]
+    steps = args.steps
 
-    def timed(fn, steps):
+    def timed(fn, nsteps):
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        out = [fn() for _ in range(steps)]
+        out = [fn() for _ in range(nsteps)]
         b.record()
         torch.cuda.synchronize()
         return a.elapsed_time(b) / 1e3, out
@@ -445,42 +449,106 @@ def run_batched(args):
 
     for _ in range(max(1, args.warmup - 2)):
         plain_step()
-    t_plain, cyc_plain = timed(plain_step, args.steps)
+    t_plain, cyc_plain = timed(plain_step, steps)
+    X_plain = [x.cpu().numpy() for x in Xp]
+
+    # plain on 16 concurrent streams (host threads), the same handles
+    nstreams = 16
+    streams = [torch.cuda.Stream() for _ in range(nstreams)]
+    Xm = [torch.tensor(x, device="cuda") for x in X0]
+
+    def worker(w):
+        st = streams[w]
+        for i in range(w, nsys, nstreams):
+            S.selm_mg_step(handles[i], Xm[i], Fp[i], DT, 1, SAMPLE_CYCLES, stream=st.cuda_stream)
+        st.synchronize()
+
+    torch.cuda.synchronize()
+    with ThreadPoolExecutor(nstreams) as ex:
+        list(ex.map(worker, range(nstreams)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        with ThreadPoolExecutor(nstreams) as ex:
+            list(ex.map(worker, range(nstreams)))
+    torch.cuda.synchronize()
+    t_multi = time.perf_counter() - t0
     for h in handles:
         S.selm_mg_destroy(h)
     torch.cuda.synchronize()
 
-    b = S.selm_batch_create(descs)
-    chosen = S.selm_batch_autotune(b)
-    Xb = [torch.tensor(x, device="cuda") for x in X0]
-    Fb = [torch.tensor(f, device="cuda") for f in F0]
+    forms = {}
+    for form in ("persistent", "graphs"):
+        b = S.selm_batch_create(descs)
+        chosen = S.selm_batch_autotune(b)
+        tuned = S.selm_batch_info(b)
+        S.selm_batch_set_persistent(b, 1 if form == "persistent" else 0)
+        Xb = [torch.tensor(x, device="cuda") for x in X0]
+        Fb = [torch.tensor(f, device="cuda") for f in F0]
 
-    def batch_step():
-        cy = S.selm_batch_step(b, Xb, Fb, DT, 1, SAMPLE_CYCLES)
-        return sum(c * (max(cy) + SAMPLE_CYCLES) for c in cells)
+        def batch_step():
+            cy = S.selm_batch_step(b, Xb, Fb, DT, 1, SAMPLE_CYCLES)
+            return sum(c * (max(cy) + SAMPLE_CYCLES) for c in cells)
 
-    for _ in range(max(1, args.warmup - 2)):
-        batch_step()
-    launches0 = S.selm_kernel_launches()
-    t_batch, cyc_batch = timed(batch_step, args.steps)
-    launches = S.selm_kernel_launches() - launches0
-    S.selm_batch_destroy(b)
+        for _ in range(max(1, args.warmup - 2)):
+            batch_step()
+        launches0 = S.selm_kernel_launches()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            t_b, cyc_b = timed(batch_step, steps)
+        launches = S.selm_kernel_launches() - launches0
+        # equal accuracy: the batched trajectories against the plain per-instance ones
+        # (both start from X0 and take warm-up + timed steps with the same counters)
+        forms[form] = {"system_steps_per_s": nsys * steps / t_b, "cell_cycles_per_s": sum(cyc_b) / t_b,
+                       "ms_per_step": 1e3 * t_b / steps, "gpu_launches": int(launches), "clocks": clk.summary(),
+                       "tuned": tuned, "engine_cluster": chosen}
+        if form == "persistent":
+            forms[form]["phase_us_solve_cycle"] = _phase_summary(S.selm_batch_phase_times(b, S.SELM_BATCH_SOLVE))
+        forms[form]["x"] = [x.cpu().numpy() for x in Xb]
+        S.selm_batch_destroy(b)
+    # the trajectories of the batched forms and the plain form (same steps, same counters)
+    def pdiff(a, b_):   # minimum image along the periodic axes (x, y)
+        d = a - b_
+        d[:, :2] = (d[:, :2] + 0.5) % 1.0 - 0.5
+        return d
+
+    acc = {}
+    for form in forms:
+        xs = forms[form].pop("x")
+        acc[form] = max(float(np.linalg.norm(pdiff(a, p_)) / max(np.linalg.norm(pdiff(p_, x0)), 1e-300))
+                        for a, p_, x0 in zip(xs, X_plain, X0))
+    best = max(forms, key=lambda k: forms[k]["system_steps_per_s"])
     line = {
         "metric": "batched stochastic-MG: system-steps/s and cell-cycles/s, batched vs plain per-instance",
-        "value": nsys * args.steps / t_batch, "unit": "system-steps/s", "higher_is_better": True,
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": "f32+f64",
+        "value": forms[best]["system_steps_per_s"], "unit": "system-steps/s", "higher_is_better": True,
+        "n_gpus": 1, "steps": steps, "warmup": args.warmup, "data": "synthetic", "dtype": "f32+f64",
         "config": {"workload": f"{nsys} independent 3-D channel systems, edges from {{32,48,64,96,128}}, "
                                f"64-2048 particles, kT in [0.5,2], one Euler-Maruyama step (solve to 1e-10 + "
                                f"{SAMPLE_CYCLES} stochastic cycles) per system per step",
-                   "edges": edges, "engine_cluster": chosen},
-        "batched": {"system_steps_per_s": nsys * args.steps / t_batch, "cell_cycles_per_s": sum(cyc_batch) / t_batch,
-                    "ms_per_step": 1e3 * t_batch / args.steps},
-        "plain": {"system_steps_per_s": nsys * args.steps / t_plain, "cell_cycles_per_s": sum(cyc_plain) / t_plain,
-                  "ms_per_step": 1e3 * t_plain / args.steps},
-        "speedup_steps": t_plain / t_batch,
-        "gpu_launches": int(launches),
+                   "edges": edges, "best_form": best},
+        "batched": forms,
+        "plain": {"system_steps_per_s": nsys * steps / t_plain, "cell_cycles_per_s": sum(cyc_plain) / t_plain,
+                  "ms_per_step": 1e3 * t_plain / steps},
+        "plain_16_streams": {"system_steps_per_s": nsys * steps / t_multi, "ms_per_step": 1e3 * t_multi / steps,
+                             "note": "the same handles stepped from 16 host threads, one CUDA stream each "
+                                     "(wall clock)"},
+        "speedup_steps": {"vs_plain": forms[best]["system_steps_per_s"] / (nsys * steps / t_plain),
+                          "vs_plain_16_streams": forms[best]["system_steps_per_s"] / (nsys * steps / t_multi)},
+        "equal_accuracy": {"max_rel_trajectory_difference_vs_plain": acc,
+                           "note": "positions after the same steps, relative to the displacement; FP32 inner "
+                                   "cycles (tolerance 1e-5)"},
+        "gpu_launches": forms[best]["gpu_launches"],
     }
     print(json.dumps(line), flush=True)
+
+
+def _phase_summary(ph):
+    agg = {}
+    for name, lev, us in ph:
+        key = f"{name}_L{lev}"
+        a = agg.setdefault(key, [0, 0.0])
+        a[0] += 1
+        a[1] += us
+    return {k: {"phases": v[0], "us": round(v[1], 1)} for k, v in sorted(agg.items(), key=lambda kv: -kv[1][1])}
 
 
 def served_stream(nreq, rate, seed=0):
@@ -533,16 +601,29 @@ def run_served(args):
         lat = np.array([x["t_done"] - x["t_submit"] for x in res])
         span = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
         ok = all(x["status"] == 0 for x in res)
+        busy = sum(x["t_done"] - x["t_admit"] for x in res)
         return dict(p50_ms=1e3 * float(np.percentile(lat, 50)), p99_ms=1e3 * float(np.percentile(lat, 99)),
                     requests_per_s=len(res) / span, solves_per_s=sum(r["steps"] for r in reqs) / span,
                     vcycles_per_s=sum(x["vcycles"] for x in res) / span, makespan_s=span,
-                    peak_slots=stats["peak_slots"], peak_gb=stats["peak_bytes"] / 2 ** 30, all_ok=ok)
+                    mean_requests_in_service=busy / span,
+                    peak_slots=stats["peak_slots"], peak_gb=stats["peak_bytes"] / 2 ** 30, all_ok=ok,
+                    positions=[k[0].copy() for k in keep])
 
     torch.cuda.synchronize()
     plain = serve(1)
     launches0 = S.selm_kernel_launches()
     served = serve(args.slots)
     launches = S.selm_kernel_launches() - launches0
+    # equal accuracy: every request's final positions, served vs plain (minimum
+    # image along the periodic axes, relative to the request's displacement)
+    worst = 0.0
+    for r, a, b_ in zip(reqs, served.pop("positions"), plain.pop("positions")):
+        X0 = selm_inputs.particles(r["np"], r["dim"], r["n"], seed=r["seed"])
+        def pd(u, v):
+            d = u - v
+            d[:, :-1] = (d[:, :-1] + 0.5) % 1.0 - 0.5
+            return d
+        worst = max(worst, float(np.linalg.norm(pd(a, b_)) / max(np.linalg.norm(pd(b_, X0)), 1e-300)))
     line = {
         "metric": "served solves/s + p99 vs plain form", "value": served["solves_per_s"], "unit": "solves/s",
         "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "dtype": "f32+f64",
@@ -553,6 +634,8 @@ def run_served(args):
                    "solve": "one Euler-Maruyama step (one mobility solve) of one request"},
         "served": served, "plain": plain,
         "speedup_solves": served["solves_per_s"] / plain["solves_per_s"],
+        "equal_accuracy": {"max_rel_position_difference_served_vs_plain": worst,
+                           "note": "each request's positions after its steps, relative to its displacement"},
         "gpu_launches": int(launches),
     }
     print(json.dumps(line), flush=True)
@@ -837,7 +920,7 @@ def composite_measure(S, n, K, steps, warmup, with_cpu, cov_samples=100):
     if exact is not None and cov_samples > 0:
         from paper_1003_2680_gb300 import covariance as CV
         est, se, ns = CV.composite_block(c, n, K, 3, nsamples=cov_samples, nbatches=10)
-        cov = dict(CV.compare(est, se, exact), samples=ns * 3,
+        cov = dict(CV.compare(est, se, exact), samples=ns,
                    block="4^3 probe block of one component across the coarse-fine interface (x, y = 126..129 "
                          "in each level's indexing; fine layers 2K-2, 2K-1 and base rows K+1, K+2), averaged "
                          "over all x-y base-cell translates and the 3 components",
@@ -973,11 +1056,12 @@ def main():
     stream = torch.cuda.current_stream()
 
     pres_steps = [0]
+    spectral = S.selm_mg_pressure_spectral(h) == 1 if proj == S.SELM_PROJ_MAC else False
 
     def one_step():
         S.selm_mg_step(h, X, F, DT, 1, SAMPLE_CYCLES)
         st = S.selm_mg_stats(h)
-        pres_steps[0] += st[1]
+        pres_steps[0] += st[1]   # pressure V-cycles, or spectral refinement iterations
         return st[0] + SAMPLE_CYCLES
 
     # burn-in of the chain + warm-up of every path
@@ -1089,7 +1173,8 @@ def main():
     n_vel = level_unknowns(S, h, 0)[0]
     n_pres = level_unknowns(S, h, 1)[0] if proj == S.SELM_PROJ_MAC else 0
     vel_per_step = cycles_all / args.steps / world
-    pres_per_step = pres_steps_cycles / args.steps if args.steps else 0.0
+    pres_iter_per_step = pres_steps_cycles / args.steps if args.steps else 0.0
+    pres_per_step = 0.0 if spectral else pres_iter_per_step   # pressure V-cycles
     unknown_cycles_step = vel_per_step * n_vel + pres_per_step * n_pres
     step_s = t_total / args.steps
     roof["whole_step_model"] = {
@@ -1109,6 +1194,10 @@ def main():
         "velocity_vcycles_per_step": cycles_all / args.steps / world,
         "vcycles_per_step": {"velocity": vel_per_step, "pressure": pres_per_step,
                              "total": vel_per_step + pres_per_step},
+        "pressure_solve": ({"inner": "spectral (FFT along x, y; tridiagonal along z; FP32) in FP64 refinement",
+                            "refinement_iterations_per_step": pres_iter_per_step} if spectral else
+                           {"inner": "V-cycle of the pressure system in FP64 refinement",
+                            "vcycles_per_step": pres_iter_per_step}),
         "unknown_cycles_per_s_all_vcycles": unknown_cycles_step / step_s * world,
         "roofline": roof,
         "kernel_time_share": {k: round(v["ms"] / tot_ms, 4) for k, v in per_class.items() if v["launches"]},
@@ -1117,6 +1206,29 @@ def main():
         "gpu_launches": int(launches),
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
+    # the same step with the projection's pressure solved by V-cycles (the
+    # multigrid path the composite grid uses), timed the same way
+    if spectral and not args.no_extras:
+        S.selm_mg_set_option(h, S.SELM_OPT_PRESSURE_SPECTRAL, 0)
+        for _ in range(2):
+            one_step()
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        cyc2, p0 = 0, pres_steps[0]
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev2[k][0].record(stream)
+            cyc2 += one_step()
+            ev2[k][1].record(stream)
+        torch.cuda.synchronize()
+        t2 = sum(a.elapsed_time(b) for a, b in ev2) / 1e3
+        pv = (pres_steps[0] - p0) / args.steps
+        line["mg_projection"] = {
+            "value": n ** 3 * cyc2 / t2, "unit": "cells/s", "ms_per_step": 1e3 * t2 / args.steps,
+            "vcycles_per_step": {"velocity": cyc2 / args.steps, "pressure": pv, "total": cyc2 / args.steps + pv},
+            "unknown_cycles_per_s_all_vcycles": (cyc2 / args.steps * n_vel + pv * n_pres) / (t2 / args.steps),
+            "note": "the same workload with the projection's pressure solved by V-cycles of the pressure system"}
+        S.selm_mg_set_option(h, S.SELM_OPT_PRESSURE_SPECTRAL, 1)
     # the chain's sample covariance on 4^3 wall blocks of every velocity
     # component against the exact A^-1 blocks (spectral closed form)
     if not args.no_extras:

@@ -159,7 +159,8 @@ enum {
   SELM_OPT_ENGINE_LEVEL = 3,
   SELM_OPT_LEVEL_COOP = 4,
   SELM_OPT_GRAPHS = 5,
-  SELM_OPT_SPECULATE = 6
+  SELM_OPT_SPECULATE = 6,
+  SELM_OPT_PRESSURE_SPECTRAL = 8
 };
 /* SELM_OPT_ENGINE_CLUSTER: largest thread-block cluster the coarse engine may
    use (1..16; 0 = the largest that fits).  Re-plans the engine; synchronises
@@ -188,9 +189,21 @@ enum {
    confirms: same iterates and cycle counts), so the device does not idle
    during the read-back; 0 waits for every norm first (for handles that share
    the GPU with other work, where a mispredicted V-cycle costs others).
+   SELM_OPT_PRESSURE_SPECTRAL (default 1 where available): the projection's
+   pressure problem (D^ D^T) phi = D^ w (Section 4) keeps its FP64 iterative
+   refinement (Algorithm 1) but takes the exact inner solve of the uniform
+   channel's Neumann operator -- FFT along x and y, a tridiagonal solve along z
+   per mode, FFT back, in FP32 -- instead of the pressure system's V-cycle;
+   available for FP32 inner cycles on 3-D grids with nx == ny a power of two
+   up to 128 (SELM_EINVAL elsewhere).  0 selects the V-cycle.  Both stop at
+   proj_tol.
    Setting any option on a handle that holds captured graphs synchronises the
    device and drops them. */
 selm_status selm_mg_set_option(selm_mg* h, int option, int value);
+/* 1 when the handle's projections use the spectral inner solve (their
+   pressure "cycles" in selm_mg_stats are then refinement iterations, not
+   V-cycles), else 0. */
+int selm_mg_pressure_spectral(const selm_mg* h);
 /* Coarse engine of `system`: first level it covers (-1 = not used), cluster
    size and dynamic shared memory per CTA. */
 selm_status selm_mg_engine_info(const selm_mg* h, int system, int* first_level, int* cluster_size,
@@ -296,8 +309,11 @@ const char* selm_batch_last_error(const selm_batch* b);
    receives the FAC cycles each system needed in the last step. */
 selm_status selm_batch_step(selm_batch* b, const int* np, double* const* X, const double* const* F, double dt,
                             int nsteps, int ncycles_per_step, int* solve_cycles, void* stream);
-/* Times the batched V-cycle for engine cluster sizes 16, 8 and 4 and keeps the
-   fastest; *chosen_cluster receives it. */
+/* Autotuner: times one FAC cycle of every system for each tile shape of the
+   persistent form (see selm_batch_set_persistent) and for engine cluster sizes
+   16, 8 and 4 of the graph form, keeps the best shape of each and runs the
+   faster form from then on (selm_batch_info tells which); *chosen_cluster
+   receives the graph form's cluster size. */
 selm_status selm_batch_autotune(selm_batch* b, int* chosen_cluster, void* stream);
 enum { SELM_BATCH_SOLVE = 0, SELM_BATCH_SAMPLE = 1 };
 /* One FAC cycle (Algorithm 1) of every system of the batch, the systems side
@@ -309,6 +325,35 @@ enum { SELM_BATCH_SOLVE = 0, SELM_BATCH_SAMPLE = 1 };
      of its last step): u <- u + V-Cycle(0, b - A u).
    Other modes return SELM_EINVAL. */
 selm_status selm_batch_cycle(selm_batch* b, int mode, void* stream);
+/* Persistent form (the default when every system has the same inner
+   precision and sweep counts, the exact coarsest step and level-0 rows of
+   8-wide segments, until selm_batch_autotune finds the graph form faster):
+   every FAC cycle of all systems
+   (Algorithm 1 around Algorithm 3) is one cooperative launch that walks the
+   cycle's phases -- FP64 residual, each colour pass of each level, residual and
+   restriction, the coarsest exact step, prolongation, FP64 update -- for every
+   system, aligned by level, with a grid barrier between phases and each
+   system's own noise counters, so every system's result is what it computes
+   alone.  selm_batch_step captures the solve cycle (with the residual norms'
+   read-back) and the chain cycles as CUDA graphs; its tile shapes (z rows per
+   level-0 column item: 8, 16, 32; co-resident blocks per SM: 1, 2) come from
+   selm_batch_autotune.  on = 0 selects the
+   per-system graphs (SELM_EINVAL if the batch does not qualify for on = 1).
+   Synchronises the device. */
+selm_status selm_batch_set_persistent(selm_batch* b, int on);
+/* Form and tile shape of the batch: persistent (0/1), z rows per level-0
+   column item, blocks per SM, engine cluster size of the graph form. */
+selm_status selm_batch_info(const selm_batch* b, int* persistent, int* kc, int* blocks_per_sm, int* cluster);
+/* Profiling aid of the persistent form: runs one FAC cycle of every system
+   (mode as selm_batch_cycle; SELM_BATCH_SOLVE runs the cycle from u) with a
+   %globaltimer stamp after each phase and returns, per phase, its type (0
+   FP64 residual, 1 colour pass, 2-3 the coarsest step's two triangular
+   solves, 4 residual, 5 restriction, 6 prolongation, 7 FP64 update), its
+   level and its duration in microseconds (types/levels/us: host arrays of
+   max_phases entries; *nphases receives the count; SELM_EINVAL when it
+   exceeds max_phases).  Synchronises `stream`. */
+selm_status selm_batch_phase_times(selm_batch* b, int mode, int max_phases, int* types, int* levels, double* us,
+                                   int* nphases, void* stream);
 
 /* ---- served form -----------------------------------------------------------
    A request loop.  One device pool of `budget_bytes` is reserved at creation;
@@ -376,7 +421,8 @@ enum {
   SELM_K_INTERP = 9,
   SELM_K_PROJECTION = 10,
   SELM_K_OTHER = 11,
-  SELM_K_NCLASSES = 12
+  SELM_K_BATCH_CYCLE = 12,  /* persistent batched FAC cycle (all systems, one launch) */
+  SELM_K_NCLASSES = 13
 };
 long long selm_kernel_launches(void);
 selm_status selm_profile_enable(int on);

@@ -86,7 +86,7 @@ struct Plan {
   std::vector<TableOffsets> toff[2][kMaxLevels];
   size_t field_off[2][kMaxLevels][3];
   size_t u_off = 0, xi_off = 0, bvel_off = 0, wcomb_off = 0, phi_off = 0, prhs_off = 0, red_off = 0,
-         cyc_off = 0, V_off = 0, Xs_off = 0, Fs_off = 0, eng_off[2] = {0, 0};
+         cyc_off = 0, V_off = 0, Xs_off = 0, Fs_off = 0, eng_off[2] = {0, 0}, spec_off = 0, spec_bytes = 0;
 };
 
 void plan_tables(const HostSystem& hs, int si, Plan* p) {
@@ -155,6 +155,15 @@ void make_plan(const selm_mg_desc& d, const Sys& vel, const Sys* pres, int esize
     const size_t np_ = (size_t)pres->host.level_size(0);
     p->phi_off = p->lay.add(3 * np_ * 8);
     p->prhs_off = p->lay.add(np_ * 8);
+    // spectral inner solves of the projection (FP32 inner precision, uniform
+    // channel with nx == ny a power of two <= 128)
+    const HostComp& pc = pres->host.lev[0][0];
+    const int n = pc.dims[0];
+    if (esize == 4 && pres->host.ncomp == 1 && d.dim == 3 && pc.dims[1] == n && n >= 4 && n <= 128 &&
+        (n & (n - 1)) == 0 && pc.dims[2] >= 2 && pc.kind[2] == kAxisCellNeu) {
+      p->spec_bytes = (size_t)n * n * pc.dims[2] * 8;
+      p->spec_off = p->lay.add(p->spec_bytes);
+    }
   }
   p->eng_off[0] = p->lay.add(kEngParamBytes);
   if (pres) p->eng_off[1] = p->lay.add(kEngParamBytes);
@@ -474,9 +483,58 @@ selm_status fac_solve(selm_mg* h, Sys& s, double* z, const double* b, double tol
   }
 }
 
+// The projection's pressure problem by FP64 iterative refinement around the
+// spectral inner solve (Algorithm 1's iteration with the exact FP32 solve of
+// the uniform channel's Neumann operator in place of the V-cycle): residual
+// r = b - A phi in FP64, delta = A^-1 r in FP32 (FFT along x, y; Thomas along
+// z), phi += delta, until ||r|| <= tol ||b||.
+selm_status spectral_fac_solve(selm_mg* h, double* phi, const double* b, double tol, int max_cycles, int* cycles,
+                               double* rel_out, cudaStream_t st) {
+  Sys& s = h->pres;
+  double* nb = h->red + 0;
+  double* nr = h->red + 1;
+  CK(cudaMemsetAsync(nb, 0, 2 * sizeof(double), st));
+  CK(launch_norm2(s.lev[0].size, b, nb, st));
+  *cycles = 0;
+  double bn = 0.0;
+  for (int cyc = 0;; ++cyc) {
+    if (cyc > 0) CK(cudaMemsetAsync(nr, 0, sizeof(double), st));
+    selm_status r = outer_residual(h, s, phi, b, s.b[0], nr, st);
+    if (r != SELM_OK) return r;
+    CK(cudaEventRecord(h->ev_norm, st));
+    double bn2 = 0.0, rn2 = 0.0;
+    r = read_norms_after_event(h, cyc == 0 ? &bn2 : nullptr, &rn2, st);
+    if (r != SELM_OK) return r;
+    if (cyc == 0) {
+      if (bn2 == 0.0) {
+        CK(cudaMemsetAsync(phi, 0, (size_t)s.lev[0].size * sizeof(double), st));
+        if (rel_out) *rel_out = 0.0;
+        return SELM_OK;
+      }
+      bn = std::sqrt(bn2);
+    }
+    const double rel = std::sqrt(rn2) / bn;
+    if (rel_out) *rel_out = rel;
+    if (rel <= tol) {
+      *cycles = cyc;
+      return SELM_OK;
+    }
+    if (cyc >= max_cycles) {
+      *cycles = cyc;
+      h->err = "spectral pressure solve did not converge";
+      return SELM_ENOCONV;
+    }
+    CK(spectral_pressure_solve(s.lev[0], (const float*)s.b[0], (float*)s.v[0], h->spec, st));
+    r = outer_update(h, s, phi, s.v[0], st);
+    if (r != SELM_OK) return r;
+  }
+}
+
 // w <- P~ w.  The pressure Poisson problem (D^ D^T) phi = D^ w is solved by
 // the FAC iteration from an initial value (Algorithm 1 takes one): slot < 0
-// starts from zero; slots 0..2 start from that slot's previous pressure.
+// starts from zero; slots 0..2 start from that slot's previous pressure.  On
+// the uniform channel the iteration's inner solve is spectral by default
+// (SELM_OPT_PRESSURE_SPECTRAL), else the pressure system's V-cycle.
 selm_status project(selm_mg* h, double* w, int* cycles, cudaStream_t st, int slot = -1) {
   *cycles = 0;
   if (!h->has_pres) return SELM_OK;
@@ -487,7 +545,9 @@ selm_status project(selm_mg* h, double* w, int* cycles, cudaStream_t st, int slo
   CK(launch_sub_mean(np_, h->prhs, h->red + 2, st));
   if (slot < 0) CK(cudaMemsetAsync(phi, 0, (size_t)np_ * sizeof(double), st));
   double rel = 0.0;
-  selm_status r = fac_solve(h, h->pres, phi, h->prhs, h->d.proj_tol, h->d.max_cycles, cycles, &rel, st);
+  selm_status r = h->spectral && h->spec
+                      ? spectral_fac_solve(h, phi, h->prhs, h->d.proj_tol, h->d.max_cycles, cycles, &rel, st)
+                      : fac_solve(h, h->pres, phi, h->prhs, h->d.proj_tol, h->d.max_cycles, cycles, &rel, st);
   if (r != SELM_OK) return r;
   CK(launch_grad_sub(h->vel.lev[0], w, phi, st));
   return SELM_OK;
@@ -747,6 +807,10 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
   if (h->has_pres) {
     h->phi = (double*)(h->ws + p.phi_off);
     h->prhs = (double*)(h->ws + p.prhs_off);
+    if (p.spec_bytes > 0 && spectral_pressure_supported(h->pres.lev[0])) {
+      h->spec = h->ws + p.spec_off;
+      h->spectral = true;
+    }
   }
   h->red = (double*)(h->ws + p.red_off);
   h->vel.coop_bar = (unsigned*)(h->red + 8);
@@ -901,6 +965,11 @@ selm_status selm_mg_set_option(selm_mg* h, int option, int value) {
     h->vel.coop_flow = h->pres.coop_flow = value == 1;
     return replan_engine(h, h->vel.engine_cluster, nullptr);   // the automatic first level depends on it
   }
+  if (option == SELM_OPT_PRESSURE_SPECTRAL) {
+    if (value != 0 && !h->spec) return SELM_EINVAL;
+    h->spectral = value != 0;
+    return SELM_OK;
+  }
   if (option == SELM_OPT_ENGINE_LEVEL) {
     if (value < 0 || value > kMaxLevels) return SELM_EINVAL;
     h->vel.engine_level = value;
@@ -921,6 +990,8 @@ selm_status selm_mg_engine_info(const selm_mg* h, int system, int* first_level, 
   if (smem_bytes) *smem_bytes = v ? (h->esize == 4 ? s->engf.smem_bytes : s->engd.smem_bytes) : 0;
   return SELM_OK;
 }
+
+int selm_mg_pressure_spectral(const selm_mg* h) { return h && h->spectral && h->spec ? 1 : 0; }
 
 selm_status selm_mg_stats(const selm_mg* h, int* last_solve_cycles, int* last_proj_cycles, long long* total) {
   if (!h) return SELM_EINVAL;

@@ -14,6 +14,15 @@
 //
 // The engine's thread-block cluster size is chosen by an autotuner that times
 // the batched V-cycle graph for each candidate.
+//
+// Persistent form (the default when every system qualifies: one inner
+// precision, the exact coarsest step, level-0 rows in 8-wide segments): each
+// FAC cycle of all systems -- a solve cycle or a chain cycle -- is one
+// cooperative launch that walks the cycle's phases for every system with grid
+// barriers between phases (batch_persist_launch); the solve's per-cycle graph
+// is that launch plus one strided copy of all residual norms, and the chain
+// graph holds the step's chain cycles.  Its autotuner times the launch over
+// tile shapes (z rows per level-0 column item, co-resident blocks per SM).
 
 #include <cuda_runtime.h>
 
@@ -53,6 +62,9 @@ struct selm_batch {
   double dt = -1.0;
   int kchain = -1;
   int cluster = 0;
+  BatchPersist* bp = nullptr;   // persistent form (null: per-system graphs only)
+  bool persistent = false;
+  unsigned* host_flag = nullptr;  // pinned copy of the persistent launches' timeout word
   std::string err;
 };
 
@@ -148,7 +160,53 @@ selm_status residual_norm(selm_batch* b, int i, cudaStream_t s) {
   return SELM_OK;
 }
 
+// Captures fn(stream) on the origin stream alone (the persistent form).
+template <typename Fn>
+selm_status capture_single(selm_batch* b, Fn fn, cudaGraphExec_t* out, long long* kernels) {
+  if (*out) {
+    cudaGraphExecDestroy(*out);
+    *out = nullptr;
+  }
+  const long long l0 = prof::g_launches.load();
+  BCK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+  const cudaError_t ce = fn(b->origin);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce2 = cudaStreamEndCapture(b->origin, &graph);
+  *kernels = prof::g_launches.load() - l0;
+  prof::g_launches.fetch_sub(*kernels);   // recorded, not run
+  if (ce != cudaSuccess || ce2 != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    b->err = std::string("graph capture failed: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ce2);
+    return SELM_ECUDA;
+  }
+  const cudaError_t ce3 = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce3 != cudaSuccess) {
+    b->err = std::string("graph instantiation failed: ") + cudaGetErrorString(ce3);
+    return SELM_ECUDA;
+  }
+  return SELM_OK;
+}
+
 selm_status build_cycle_graph(selm_batch* b) {
+  if (b->persistent) {
+    // one pipelined solve cycle of every system, then all residual norms to
+    // host_norm[2 i]
+    return capture_single(
+        b,
+        [&](cudaStream_t s) -> cudaError_t {
+          cudaError_t e = batch_persist_launch(b->bp, 1, s);
+          if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(b->host_norm, 2 * sizeof(double), batch_persist_norms(b->bp), sizeof(double),
+                                  sizeof(double), b->n, cudaMemcpyDeviceToHost, s);
+          if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->host_flag, batch_persist_bar(b->bp) + 2, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                s);
+          return e;
+        },
+        &b->g_cycle, &b->k_cycle);
+  }
   return capture(
       b,
       [&](int i, cudaStream_t s) -> selm_status {
@@ -180,6 +238,7 @@ selm_status build_graphs(selm_batch* b, const int* np, double* const* X, const d
         LCK(cudaMemsetAsync(h->bvel, 0, nv, s));
         LCK(launch_spread(h->vel.lev[0], h->d.n, h->d.dim, np[i], X[i], F[i], h->bvel, s));
         LCK(cudaMemsetAsync(h->u, 0, nv, s));
+        LCK(cudaMemsetAsync(h->vel.v[0], 0, (size_t)h->vel.lev[0].size * h->esize, s));
         LCK(cudaMemsetAsync(h->red, 0, sizeof(double), s));
         LCK(launch_norm2(h->vel.lev[0].size, h->bvel, h->red, s));
         LCK(cudaMemcpyAsync(b->host_norm + 2 * i + 1, h->red, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -187,6 +246,23 @@ selm_status build_graphs(selm_batch* b, const int* np, double* const* X, const d
       },
       &b->g_start, &b->k_start));
   BST(build_cycle_graph(b));
+  if (b->persistent)
+    BST(capture_single(
+        b,
+        [&](cudaStream_t s) -> cudaError_t {
+          for (int q = 0; q < kchain; ++q) {
+            cudaError_t e = batch_persist_launch(b->bp, 0, s);
+            // a timed-out barrier of any chain cycle stays visible until the
+            // next step's first read-back
+            if (e == cudaSuccess)
+              e = cudaMemcpyAsync(b->host_flag + 1, batch_persist_bar(b->bp) + 2, sizeof(unsigned),
+                                  cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return e;
+          }
+          return cudaSuccess;
+        },
+        &b->g_chain, &b->k_chain));
+  else
   BST(capture(
       b,
       [&](int i, cudaStream_t s) -> selm_status {
@@ -222,6 +298,15 @@ bool same_args(const selm_batch* b, const int* np, double* const* X, const doubl
   for (int i = 0; i < b->n; ++i)
     if (b->np[i] != np[i] || b->X[i] != X[i] || b->F[i] != F[i]) return false;
   return true;
+}
+
+// A grid barrier of a persistent launch that gave up (its bounded wait ran
+// out) leaves that launch's results undefined: reported once, then cleared.
+selm_status check_timeout(selm_batch* b) {
+  if (!b->persistent || !b->host_flag || (b->host_flag[0] == 0u && b->host_flag[1] == 0u)) return SELM_OK;
+  b->host_flag[0] = b->host_flag[1] = 0u;
+  b->err = "a grid barrier of the persistent batched launch timed out";
+  return SELM_ECUDA;
 }
 
 bool all_converged(const selm_batch* b, std::vector<int>& cycles, int cyc) {
@@ -287,6 +372,36 @@ selm_status selm_batch_create(int nsys, const selm_mg_desc* descs, void* stream,
     selm_batch_destroy(b);
     return SELM_ENOMEM;
   }
+  // persistent form, when every system qualifies
+  {
+    std::vector<BatchSysHost> hs(nsys);
+    bool same = true;
+    for (int i = 0; i < nsys; ++i) {
+      selm_mg* h = b->sys[i];
+      BatchSysHost& q = hs[i];
+      q.levels = h->vel.levels;
+      q.esize = h->esize;
+      q.cholesky = h->d.coarse_mode == SELM_COARSE_CHOLESKY;
+      q.lev = h->vel.lev;
+      q.v = h->vel.v;
+      q.b = h->vel.b;
+      q.t = h->vel.t;
+      q.key = h->key;
+      q.cyc = h->cyc;
+      q.u = h->u;
+      q.xi = h->xi;
+      q.bvel = h->bvel;
+      same = same && h->mu1 == b->sys[0]->mu1 && h->mu2 == b->sys[0]->mu2;
+    }
+    if (same && batch_persist_eligible(nsys, hs.data()) &&
+        cudaMallocHost((void**)&b->host_flag, 2 * sizeof(unsigned)) == cudaSuccess) {
+      b->host_flag[0] = b->host_flag[1] = 0u;
+      cudaStreamSynchronize(stream ? (cudaStream_t)stream : nullptr);
+      if (batch_persist_create(nsys, hs.data(), b->sys[0]->mu1, b->sys[0]->mu2, &b->bp) == cudaSuccess)
+        b->persistent = true;
+      cudaGetLastError();
+    }
+  }
   *out = b;
   return SELM_OK;
 }
@@ -303,6 +418,8 @@ selm_status selm_batch_destroy(selm_batch* b) {
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->origin) cudaStreamDestroy(b->origin);
   if (b->host_norm) cudaFreeHost(b->host_norm);
+  batch_persist_destroy(b->bp);
+  if (b->host_flag) cudaFreeHost(b->host_flag);
   delete b;
   return SELM_OK;
 }
@@ -329,6 +446,7 @@ selm_status selm_batch_step(selm_batch* b, const int* np, double* const* X, cons
     BCK(cudaGraphLaunch(b->g_start, st));
     prof::g_launches.fetch_add(b->k_start);
     BCK(cudaStreamSynchronize(st));
+    BST(check_timeout(b));
     int cyc = 0;
     while (!all_converged(b, cycles, cyc)) {
       if (cyc >= max_cycles) {
@@ -338,6 +456,7 @@ selm_status selm_batch_step(selm_batch* b, const int* np, double* const* X, cons
       BCK(cudaGraphLaunch(b->g_cycle, st));
       prof::g_launches.fetch_add(b->k_cycle);
       BCK(cudaStreamSynchronize(st));
+      BST(check_timeout(b));
       ++cyc;
       for (selm_mg* h : b->sys) h->total_vcycles += 1;
     }
@@ -361,6 +480,14 @@ selm_status selm_batch_step(selm_batch* b, const int* np, double* const* X, cons
 selm_status selm_batch_cycle(selm_batch* b, int mode, void* stream) {
   if (!b || (mode != SELM_BATCH_SOLVE && mode != SELM_BATCH_SAMPLE)) return SELM_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  if (b->persistent) {
+    BCK(batch_persist_launch(b->bp, mode == SELM_BATCH_SAMPLE ? 0 : 2, st));
+    for (selm_mg* h : b->sys) {
+      if (mode == SELM_BATCH_SAMPLE) h->cycle += 1;
+      h->total_vcycles += 1;
+    }
+    return SELM_OK;
+  }
   BCK(cudaEventRecord(b->fork, st));
   for (int i = 0; i < b->n; ++i) {
     selm_mg* h = b->sys[i];
@@ -390,6 +517,43 @@ selm_status selm_batch_autotune(selm_batch* b, int* chosen_cluster, void* stream
   if (!b) return SELM_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   BCK(cudaStreamSynchronize(st));   // no batched graph may still be running
+  float best_p = -1.0f;
+  if (b->bp) {
+    // tile shapes of the persistent launch: z rows per level-0 column item x
+    // co-resident blocks per SM, each timed over solve cycles of every system
+    // (the iterates u are reset at the start of every step)
+    const int kcs[3] = {8, 16, 32}, bpss[2] = {1, 2};
+    int best_kc = 16, best_bps = 1;
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    for (int kc : kcs)
+      for (int bps : bpss) {
+        BCK(batch_persist_configure(b->bp, kc, bps));
+        int got_kc = 0, got_bps = 0;
+        batch_persist_shape(b->bp, &got_kc, &got_bps);
+        if (got_bps != bps) continue;   // that many blocks do not fit on an SM
+        BCK(batch_persist_launch(b->bp, 2, st));   // warm-up
+        BCK(cudaEventRecord(e0, st));
+        for (int r = 0; r < 3; ++r) BCK(batch_persist_launch(b->bp, 2, st));
+        prof::g_launches.fetch_add(4);
+        BCK(cudaEventRecord(e1, st));
+        BCK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        BCK(cudaEventElapsedTime(&ms, e0, e1));
+        if (best_p < 0.0f || ms < best_p) {
+          best_p = ms;
+          best_kc = kc;
+          best_bps = bps;
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    BCK(batch_persist_configure(b->bp, best_kc, best_bps));
+    BST(check_timeout(b));
+  }
+  // the per-system graph form over engine cluster sizes; the faster form wins
+  b->persistent = false;
   const int cands[3] = {16, 8, 4};
   float best = -1.0f;
   int best_c = 0;
@@ -418,7 +582,62 @@ selm_status selm_batch_autotune(selm_batch* b, int* chosen_cluster, void* stream
   drop_graphs(b);   // graphs are rebuilt with the chosen plans on the next step
   b->cluster = best_c;
   if (chosen_cluster) *chosen_cluster = best_c;
+  // both forms were timed over 3 solve cycles of every system
+  b->persistent = b->bp && (best_p >= 0.0f && best_p < best);
   return SELM_OK;
+}
+
+selm_status selm_batch_set_persistent(selm_batch* b, int on) {
+  if (!b) return SELM_EINVAL;
+  if (on && !b->bp) return SELM_EINVAL;
+  cudaDeviceSynchronize();
+  drop_graphs(b);
+  b->persistent = on != 0;
+  return SELM_OK;
+}
+
+selm_status selm_batch_info(const selm_batch* b, int* persistent, int* kc, int* blocks_per_sm, int* cluster) {
+  if (!b) return SELM_EINVAL;
+  int k = 0, bps = 0;
+  batch_persist_shape(b->bp, &k, &bps);
+  if (persistent) *persistent = b->persistent ? 1 : 0;
+  if (kc) *kc = k;
+  if (blocks_per_sm) *blocks_per_sm = bps;
+  if (cluster) *cluster = b->cluster;
+  return SELM_OK;
+}
+
+selm_status selm_batch_phase_times(selm_batch* b, int mode, int max_phases, int* types, int* levels, double* us,
+                                   int* nphases, void* stream) {
+  if (!b || !b->bp || (mode != SELM_BATCH_SOLVE && mode != SELM_BATCH_SAMPLE) || max_phases < 0) return SELM_EINVAL;
+  const int kind = mode == SELM_BATCH_SAMPLE ? 0 : 2;
+  const int n = batch_persist_phases(b->bp, kind, nullptr, nullptr);
+  if (nphases) *nphases = n;
+  if (!types || !levels || !us) return SELM_OK;   // count query
+  if (n > max_phases) return SELM_EINVAL;
+  std::vector<int> t(n), l(n);
+  batch_persist_phases(b->bp, kind, t.data(), l.data());
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long* d = nullptr;
+  BCK(cudaMalloc(&d, (n + 1) * sizeof(unsigned long long)));
+  std::vector<unsigned long long> h(n + 1, 0ull);
+  cudaError_t e = batch_persist_launch(b->bp, kind, st, d);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, (n + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    b->err = std::string("phase timing: ") + cudaGetErrorString(e);
+    return SELM_ECUDA;
+  }
+  prof::g_launches.fetch_add(1);
+  if (mode == SELM_BATCH_SAMPLE)
+    for (selm_mg* hh : b->sys) hh->cycle += 1;
+  for (int p = 0; p < n; ++p) {
+    types[p] = t[p];
+    levels[p] = l[p];
+    us[p] = 1e-3 * (double)(h[p + 1] - h[p]);
+  }
+  return check_timeout(b);
 }
 
 }  // extern "C"

@@ -72,6 +72,8 @@ struct selm_mg {
                             // of Gamma^T F (0), of the step's combined field (1), of the
                             // sampled field (2)
   double* prhs = nullptr;   // pressure right-hand side (FP64)
+  void* spec = nullptr;     // spectral pressure solve scratch (null: not available)
+  bool spectral = false;    // projection's inner solves spectral instead of V-cycles
   double* red = nullptr;    // reduction slots
   unsigned long long* cyc = nullptr;  // [0] chain counter, [1] stage-call counter
   double* V = nullptr;      // particle scratch [max_particles][3]

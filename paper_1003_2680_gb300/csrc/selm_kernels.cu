@@ -17,6 +17,8 @@
 
 #include <atomic>
 #include <cstdint>
+#include <cstring>
+#include <new>
 #include <mutex>
 #include <vector>
 
@@ -369,6 +371,30 @@ struct LdPlain {
   __device__ __forceinline__ static T ld(const T* p) { return *p; }
 };
 
+// 8 consecutive values (16-byte aligned); CG: from L2 only (data that other
+// blocks of the same launch wrote before a grid barrier).
+template <typename T, bool CG>
+__device__ __forceinline__ void ldv8(const T* p, T o[8]) {
+  if constexpr (!CG) {
+    Vec<T>::load8(p, o);
+  } else if constexpr (sizeof(T) == 4) {
+    const float4 a = __ldcg(reinterpret_cast<const float4*>(p)), c = __ldcg(reinterpret_cast<const float4*>(p + 4));
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = c.x; o[5] = c.y; o[6] = c.z; o[7] = c.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double2 a = __ldcg(reinterpret_cast<const double2*>(p + 2 * q));
+      o[2 * q] = a.x;
+      o[2 * q + 1] = a.y;
+    }
+  }
+}
+template <typename T, bool CG>
+__device__ __forceinline__ T ld1(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  return *p;
+}
+
 // Row k of a Galerkin operator applied to vc (one component's field) in the
 // separable form of the stencil,
 //   sum_dz (s Mz)_dz (w1 . v_plane(k+dz)) + (s Kz)_dz (w2 . v_plane(k+dz)),
@@ -712,11 +738,10 @@ __global__ void __launch_bounds__(kBlock) k_galerkin_residual_zm(LevelDev L, Col
 // its sites of the other colour, the ones row k reads, are not written by the
 // pass) and the next row's loads are issued before the current row is
 // computed.
-template <typename T, bool NOISE>
-__global__ void __launch_bounds__(kBlock) k_fine_colour_zm(LevelDev L, ColumnPass cp, T* __restrict__ v,
-                                                          const T* __restrict__ b, int colour, int sweep, Key key,
-                                                          const unsigned long long* __restrict__ cyc) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+template <typename T, bool NOISE, bool CG>
+__device__ __forceinline__ void fine_colour_zm_item(const LevelDev& L, const ColumnPass& cp, T* __restrict__ v,
+                                                    const T* __restrict__ b, int colour, int sweep, Key key,
+                                                    unsigned long long cy, long long g) {
   if (g >= cp.start[L.ncomp]) return;
   int ci = 0;
   while (ci + 1 < L.ncomp && g >= cp.start[ci + 1]) ++ci;
@@ -734,32 +759,31 @@ __global__ void __launch_bounds__(kBlock) k_fine_colour_zm(LevelDev L, ColumnPas
   const long long yp0 = c.off + (long long)(j == ny - 1 ? 0 : j + 1) * nx + x0;
   const long long rowx = c.off + (long long)j * nx;
   const int xl_i = x0 == 0 ? nx - 1 : x0 - 1, xr_i = x0 + 8 == nx ? 0 : x0 + 8;
-  const unsigned long long cy = NOISE ? *cyc : 0ull;
   const uint32_t c1 = ctr1_of(L.level, c.comp_id, colour, sweep, 0);
   const T s = (T)c.s;
   T prev[8], cur[8], nxt[8], bb[8], ty[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) prev[e] = (T)0;
-  if (k0 > 0) Vec<T>::load8(v + base + (long long)(k0 - 1) * plane, prev);
-  Vec<T>::load8(v + base + (long long)k0 * plane, cur);
+  if (k0 > 0) ldv8<T, CG>(v + base + (long long)(k0 - 1) * plane, prev);
+  ldv8<T, CG>(v + base + (long long)k0 * plane, cur);
   for (int k = k0; k < k1; ++k) {
     const long long kp = (long long)k * plane;
     if (k + 1 < nz)
-      Vec<T>::load8(v + base + kp + plane, nxt);
+      ldv8<T, CG>(v + base + kp + plane, nxt);
     else {
 #pragma unroll
       for (int e = 0; e < 8; ++e) nxt[e] = (T)0;
     }
-    Vec<T>::load8(b + base + kp, bb);
+    ldv8<T, CG>(b + base + kp, bb);
     // neighbour sums: y-, y+, z-, z+
     T acc[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) acc[e] = (T)0;
     if (ny > 1) {
-      Vec<T>::load8(v + ym0 + kp, ty);
+      ldv8<T, CG>(v + ym0 + kp, ty);
 #pragma unroll
       for (int e = 0; e < 8; ++e) acc[e] += ty[e];
-      Vec<T>::load8(v + yp0 + kp, ty);
+      ldv8<T, CG>(v + yp0 + kp, ty);
 #pragma unroll
       for (int e = 0; e < 8; ++e) acc[e] += ty[e];
     }
@@ -771,7 +795,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_colour_zm(LevelDev L, ColumnPas
 #pragma unroll
       for (int e = 0; e < 8; ++e) acc[e] += nxt[e];
     }
-    const T left = v[rowx + kp + xl_i], right = v[rowx + kp + xr_i];
+    const T left = ld1<T, CG>(v + rowx + kp + xl_i), right = ld1<T, CG>(v + rowx + kp + xr_i);
     T n4[4] = {(T)0, (T)0, (T)0, (T)0};
     if (NOISE) {
       const uint32_t grp = (uint32_t)((long long)k * ny + j) * (uint32_t)segs + (uint32_t)seg;
@@ -797,13 +821,21 @@ __global__ void __launch_bounds__(kBlock) k_fine_colour_zm(LevelDev L, ColumnPas
   }
 }
 
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kBlock) k_fine_colour_zm(LevelDev L, ColumnPass cp, T* __restrict__ v,
+                                                          const T* __restrict__ b, int colour, int sweep, Key key,
+                                                          const unsigned long long* __restrict__ cyc) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cp.start[L.ncomp]) return;
+  fine_colour_zm_item<T, NOISE, false>(L, cp, v, b, colour, sweep, key, NOISE ? *cyc : 0ull, g);
+}
+
 // t = b - A v on level 0, marching along z like k_fine_colour_zm (every site
 // of a segment): fine_row's sum order (x-, x+, y-, y+, z-, z+) and
 // t = b - (-s sum + diag v).
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_fine_residual_zm(LevelDev L, ColumnPass cp, const T* __restrict__ v,
-                                                            const T* __restrict__ b, T* __restrict__ t) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+template <typename T, bool CG>
+__device__ __forceinline__ void fine_residual_zm_item(const LevelDev& L, const ColumnPass& cp, const T* __restrict__ v,
+                                                      const T* __restrict__ b, T* __restrict__ t, long long g) {
   if (g >= cp.start[L.ncomp]) return;
   int ci = 0;
   while (ci + 1 < L.ncomp && g >= cp.start[ci + 1]) ++ci;
@@ -825,25 +857,25 @@ __global__ void __launch_bounds__(kBlock) k_fine_residual_zm(LevelDev L, ColumnP
   T prev[8], cur[8], nxt[8], bb[8], ty[8], sum[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) prev[e] = (T)0;
-  if (k0 > 0) Vec<T>::load8(v + base + (long long)(k0 - 1) * plane, prev);
-  Vec<T>::load8(v + base + (long long)k0 * plane, cur);
+  if (k0 > 0) ldv8<T, CG>(v + base + (long long)(k0 - 1) * plane, prev);
+  ldv8<T, CG>(v + base + (long long)k0 * plane, cur);
   for (int k = k0; k < k1; ++k) {
     const long long kp = (long long)k * plane;
     if (k + 1 < nz)
-      Vec<T>::load8(v + base + kp + plane, nxt);
+      ldv8<T, CG>(v + base + kp + plane, nxt);
     else {
 #pragma unroll
       for (int e = 0; e < 8; ++e) nxt[e] = (T)0;
     }
-    Vec<T>::load8(b + base + kp, bb);
-    const T left = v[rowx + kp + xl_i], right = v[rowx + kp + xr_i];
+    ldv8<T, CG>(b + base + kp, bb);
+    const T left = ld1<T, CG>(v + rowx + kp + xl_i), right = ld1<T, CG>(v + rowx + kp + xr_i);
 #pragma unroll
     for (int e = 0; e < 8; ++e) sum[e] = (e == 0 ? left : cur[e - 1]) + (e == 7 ? right : cur[e + 1]);
     if (ny > 1) {
-      Vec<T>::load8(v + ym0 + kp, ty);
+      ldv8<T, CG>(v + ym0 + kp, ty);
 #pragma unroll
       for (int e = 0; e < 8; ++e) sum[e] += ty[e];
-      Vec<T>::load8(v + yp0 + kp, ty);
+      ldv8<T, CG>(v + yp0 + kp, ty);
 #pragma unroll
       for (int e = 0; e < 8; ++e) sum[e] += ty[e];
     }
@@ -870,6 +902,12 @@ __global__ void __launch_bounds__(kBlock) k_fine_residual_zm(LevelDev L, ColumnP
       cur[e] = nxt[e];
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_fine_residual_zm(LevelDev L, ColumnPass cp, const T* __restrict__ v,
+                                                            const T* __restrict__ b, T* __restrict__ t) {
+  fine_residual_zm_item<T, false>(L, cp, v, b, t, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // t = b - A v on a banded 7-point level, marching along z like
@@ -992,11 +1030,10 @@ __global__ void __launch_bounds__(kBlock) k_coarse_site(LevelDev L, ColourPass c
 // j +- 1 and planes k +- 1, +- 2 belong to other classes, and in row j only
 // x +- 1 are read), so in-place updates are safe.  sp.start: first item of
 // each component.
-template <typename T, bool NOISE, int CX>
-__global__ void __launch_bounds__(kBlock) k_coarse_colour_v8(LevelDev L, ColourPass cp, ColumnPass sp,
-                                                            T* __restrict__ v, const T* __restrict__ b, int sweep,
-                                                            Key key, const unsigned long long* __restrict__ cyc) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+template <typename T, bool NOISE, int CX, bool CG>
+__device__ __forceinline__ void coarse_colour_v8_item(const LevelDev& L, const ColourPass& cp, const ColumnPass& sp,
+                                                      T* __restrict__ v, const T* __restrict__ b, int sweep, Key key,
+                                                      unsigned long long cy, long long g) {
   if (g >= sp.start[L.ncomp]) return;
   int ci = 0;
   while (ci + 1 < L.ncomp && g >= sp.start[ci + 1]) ++ci;
@@ -1019,9 +1056,15 @@ __global__ void __launch_bounds__(kBlock) k_coarse_colour_v8(LevelDev L, ColourP
     w2[q] = sep_w2<T>(c, q);
   }
   auto row = [&](const T* rp, T r[10]) {
-    r[0] = LdNC::ld(rp + xl);
-    Vec<T>::load8(rp + x0, r + 1);
-    r[9] = LdNC::ld(rp + xr);
+    if constexpr (CG) {
+      r[0] = __ldcg(rp + xl);
+      ldv8<T, true>(rp + x0, r + 1);
+      r[9] = __ldcg(rp + xr);
+    } else {
+      r[0] = LdNC::ld(rp + xl);
+      Vec<T>::load8(rp + x0, r + 1);
+      r[9] = LdNC::ld(rp + xr);
+    }
   };
   T acc[4] = {(T)0, (T)0, (T)0, (T)0};
 #pragma unroll
@@ -1056,7 +1099,6 @@ __global__ void __launch_bounds__(kBlock) k_coarse_colour_v8(LevelDev L, ColourP
   const T diag = coarse_diag<T>(c, k);
   T n4[4] = {(T)0, (T)0, (T)0, (T)0};
   if (NOISE) {
-    const unsigned long long cy = *cyc;
     const unsigned grp = (unsigned)seg + (unsigned)(cp.nxc[ci] >> 2) * (unsigned)(jj + cp.nyc[ci] * kk);
     Normals<T>::get(philox10(make_uint4(grp, ctr1_of(L.level, c.comp_id, cp.colour_id[ci], sweep, 0), (uint32_t)cy,
                                         (uint32_t)(cy >> 32)),
@@ -1066,10 +1108,19 @@ __global__ void __launch_bounds__(kBlock) k_coarse_colour_v8(LevelDev L, ColourP
   const long long rowi = c.off + ((long long)k * ny + j) * nx + x0 + CX;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    T nv = (LdNC::ld(b + rowi + 2 * e) - acc[e]) / diag;
+    T nv = ((CG ? __ldcg(b + rowi + 2 * e) : LdNC::ld(b + rowi + 2 * e)) - acc[e]) / diag;
     if (NOISE) nv += n4[e] / tsqrt(diag);
     v[rowi + 2 * e] = nv;
   }
+}
+
+template <typename T, bool NOISE, int CX>
+__global__ void __launch_bounds__(kBlock) k_coarse_colour_v8(LevelDev L, ColourPass cp, ColumnPass sp,
+                                                            T* __restrict__ v, const T* __restrict__ b, int sweep,
+                                                            Key key, const unsigned long long* __restrict__ cyc) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= sp.start[L.ncomp]) return;
+  coarse_colour_v8_item<T, NOISE, CX, false>(L, cp, sp, v, b, sweep, key, NOISE ? *cyc : 0ull, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -1310,7 +1361,7 @@ __device__ __forceinline__ void load4<float>(const float* p, float o[4]) {
 // x0/2 .. x0/2 + 4 of each contributing coarse row; wall axis from the
 // prolongation table).  TAG0 (FP32): the results' last mantissa bit is
 // cleared (update count 0 of a following dataflow-ordered smoothing).
-template <typename T, bool TAG0>
+template <typename T, bool TAG0, bool CG = false>
 __device__ __forceinline__ void prolong_seg8(const LevelDev& Lf, const LevelDev& Lc, const RowPass& rp,
                                              T* __restrict__ v, const T* __restrict__ vc, long long gt) {
   const int segs = Lf.c[0].nx >> 3;
@@ -1347,8 +1398,14 @@ __device__ __forceinline__ void prolong_seg8(const LevelDev& Lf, const LevelDev&
     for (int a = 0; a < nyp; ++a) {
       const T* crow = vc + c.off + (long long)kc * cplane + (long long)yi[a] * c.nx;
       T cx[5];
-      load4<T>(crow + cx0, cx);
-      cx[4] = crow[cx0 + 4 == c.nx ? 0 : cx0 + 4];
+      if constexpr (CG) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cx[q] = __ldcg(crow + cx0 + q);
+        cx[4] = __ldcg(crow + (cx0 + 4 == c.nx ? 0 : cx0 + 4));
+      } else {
+        load4<T>(crow + cx0, cx);
+        cx[4] = crow[cx0 + 4 == c.nx ? 0 : cx0 + 4];
+      }
       const T w = wz * yw[a];
 #pragma unroll
       for (int e = 0; e < 8; ++e)
@@ -1357,7 +1414,7 @@ __device__ __forceinline__ void prolong_seg8(const LevelDev& Lf, const LevelDev&
   }
   T* out = v + f.off + (long long)row * f.nx + x0;
   T cur[8];
-  Vec<T>::load8(out, cur);
+  ldv8<T, CG>(out, cur);
 #pragma unroll
   for (int e = 0; e < 8; ++e) cur[e] += acc[e];
   if constexpr (TAG0 && sizeof(T) == 4) {
@@ -1774,6 +1831,349 @@ __global__ void k_coarsest(LevelDev L, T* __restrict__ v, const T* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// Batched FAC cycle of many independent systems as one persistent launch.
+//
+// One cooperative launch runs a whole FAC iteration (Algorithm 1 around the
+// V-cycle of Algorithm 3) for every system of a batch.  The cycle is cut into
+// phases -- the FP64 outer residual, each colour pass of each sweep of each
+// level, the residual and restriction of each level, the two triangular
+// solves of the coarsest exact step, each prolongation, the FP64 update --
+// aligned by level across the systems (a system whose hierarchy is shallower
+// takes its coarsest step at its own last level and has no work in the
+// deeper phases).  A phase's work items of all systems form one index range
+// that every thread strides over; a grid barrier separates phases.  Each
+// system's work items are those of its own per-system kernels (the same
+// per-item functions, noise counters and arithmetic), with every load of data
+// written earlier in the launch taken from L2.  The host builds the phase
+// list and, per phase, the first item of each system.
+// ---------------------------------------------------------------------------
+constexpr int kBatchColours = 12;
+constexpr int kBatchThreads = 256;
+
+enum BatchPhaseType : int {
+  kPhOuterRes = 0,   // r = b - A z (FP64) into the level-0 rhs, v0 = 0; squared norm (solve)
+  kPhSmooth = 1,     // one colour pass (level, sweep, colour)
+  kPhCoarse1 = 2,    // coarsest level: y = L^-1 b (+ n)
+  kPhCoarse2 = 3,    // coarsest level: v = L^-T y
+  kPhResid = 4,      // t = b - A v at a level
+  kPhRestrict = 5,   // b_c = P^T t, v_c = 0
+  kPhProlong = 6,    // v += P v_c
+  kPhOuterUpd = 7,   // z += v0 (FP64); the solve's norm slot cleared; the chain counter advanced
+};
+
+struct BatchPhase {
+  int type, level, sweep, colour;
+};
+
+struct BatchLevelDev {
+  LevelDev L;
+  void* v;
+  void* b;
+  void* t;
+  ColourPass cp[kBatchColours];
+  ColumnPass sp[kBatchColours];   // 8-wide segment items of colour q (v8 levels)
+  ColumnPass rcp;      // residual items: 4-wide segments of z chunks (levels >= 1, nx % 4 == 0)
+  int v8;              // colour passes on 8-wide segments (nx % 8 == 0, x modulus 2)
+  RowPass rp;          // rows of this level's components
+  int vec_down;        // restriction from this level on 4-wide coarse segments
+  int vec_up;          // prolongation into this level on 8-wide fine segments
+};
+
+struct BatchSysDev {
+  int levels;
+  Key key;
+  const unsigned long long* cyc[2];   // noise counters: [0] chain, [1] solve stages
+  unsigned long long* chain_ctr;
+  double* z[2];                       // FP64 iterates: [0] chain state xi, [1] velocity u
+  const double* bz[2];                // right-hand sides: [0] none (0), [1] b
+  double* norm2;                      // ||b - A u||^2 of the solve
+  double* ywork;                      // FP64 scratch of the coarsest step
+  ColumnPass fcp;                     // level-0 column items
+  RowPass orp;                        // level-0 rows (outer residual on 4-wide segments)
+  BatchLevelDev lev[kMaxLevels];
+};
+
+template <typename T, bool CG>
+__device__ __forceinline__ double outer_residual4_item(const LevelDev& L, const RowPass& rp, const double* z,
+                                                       const double* b, T* r, T* v0, long long gt) {
+  const int segs = L.c[0].nx >> 2;
+  const long long row_all = gt / segs;
+  const int seg = (int)(gt - row_all * segs);
+  int ci = 0;
+  while (ci + 1 < L.ncomp && row_all >= rp.rstart[ci + 1]) ++ci;
+  const CompDev& c = L.c[ci];
+  const int row = (int)(row_all - rp.rstart[ci]);
+  const int j = row % c.ny, k = row / c.ny;
+  const int nx = c.nx;
+  const long long plane = (long long)nx * c.ny;
+  const long long rbase = c.off + (long long)row * nx;
+  const int x0 = seg << 2;
+  auto ld = [&](const double* p) { return CG ? __ldcg(p) : *p; };
+  auto ld4 = [&](const double* p, double o[4]) {
+    const double2 a = CG ? __ldcg(reinterpret_cast<const double2*>(p)) : *reinterpret_cast<const double2*>(p);
+    const double2 d = CG ? __ldcg(reinterpret_cast<const double2*>(p + 2)) : *reinterpret_cast<const double2*>(p + 2);
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = d.x;
+    o[3] = d.y;
+  };
+  double cen[4], acc[4], t4[4];
+  ld4(z + rbase + x0, cen);
+  const double left = ld(z + rbase + (x0 == 0 ? nx - 1 : x0 - 1));
+  const double right = ld(z + rbase + (x0 + 4 == nx ? 0 : x0 + 4));
+  acc[0] = left + cen[1];
+  acc[1] = cen[0] + cen[2];
+  acc[2] = cen[1] + cen[3];
+  acc[3] = cen[2] + right;
+  auto add4 = [&](long long off) {
+    ld4(z + off, t4);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[e] += t4[e];
+  };
+  if (c.ny > 1) {
+    add4(c.off + ((long long)k * c.ny + (j == 0 ? c.ny - 1 : j - 1)) * nx + x0);
+    add4(c.off + ((long long)k * c.ny + (j == c.ny - 1 ? 0 : j + 1)) * nx + x0);
+  }
+  if (k > 0) add4(rbase - plane + x0);
+  if (k < c.nz - 1) add4(rbase + plane + x0);
+  const int edges = (k == 0) + (k == c.nz - 1);
+  double dz = 2.0;
+  if (c.zkind == kAxisCellDir) dz += (double)edges;
+  if (c.zkind == kAxisCellNeu) dz -= (double)edges;
+  const double dg = (c.ny > 1 ? 4.0 : 2.0) + dz;
+  const double sdg = c.s * dg;
+  double rr = 0.0, bv[4] = {0.0, 0.0, 0.0, 0.0};
+  if (b) ld4(b + rbase + x0, bv);
+  T out[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const double res = fma(c.s, acc[e], fma(-sdg, cen[e], bv[e]));   // k_outer_residual_v4's arithmetic
+    out[e] = (T)res;
+    rr = fma(res, res, rr);
+  }
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(r + rbase + x0) = make_float4(out[0], out[1], out[2], out[3]);
+    *reinterpret_cast<float4*>(v0 + rbase + x0) = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      r[rbase + x0 + e] = out[e];
+      v0[rbase + x0 + e] = (T)0;
+    }
+  }
+  return rr;
+}
+
+// Component and local index of item q of a level's flattened field.
+__device__ __forceinline__ int comp_at(const LevelDev& L, long long q, long long* loc) {
+  int ci = 0;
+  while (ci + 1 < L.ncomp && q >= L.c[ci + 1].off) ++ci;
+  *loc = q - L.c[ci].off;
+  return ci;
+}
+
+template <typename T, bool NOISE>
+__device__ __forceinline__ void batch_item(const BatchSysDev& S, const BatchPhase& P, int mode, long long g,
+                                           double* nacc) {
+  const int l = P.level;
+  const BatchLevelDev& BL = S.lev[l];
+  const LevelDev& L = BL.L;
+  T* v = (T*)BL.v;
+  const T* b = (const T*)BL.b;
+  switch (P.type) {
+    case kPhOuterRes: {
+      const double rr =
+          outer_residual4_item<T, true>(L, S.orp, S.z[mode], S.bz[mode], (T*)BL.b, (T*)BL.v, g);
+      if (mode == 1) *nacc += rr;
+      break;
+    }
+    case kPhSmooth: {
+      const unsigned long long cy = NOISE ? *S.cyc[mode] : 0ull;
+      if (l == 0)
+        fine_colour_zm_item<T, NOISE, true>(L, S.fcp, v, b, P.colour, P.sweep, S.key, cy, g);
+      else if (BL.v8 && (P.colour & 1) == 0)
+        coarse_colour_v8_item<T, NOISE, 0, true>(L, BL.cp[P.colour], BL.sp[P.colour], v, b, P.sweep, S.key, cy, g);
+      else if (BL.v8)
+        coarse_colour_v8_item<T, NOISE, 1, true>(L, BL.cp[P.colour], BL.sp[P.colour], v, b, P.sweep, S.key, cy, g);
+      else
+        coarse_site_at<T, NOISE, LdCG>(L, BL.cp[P.colour], v, b, P.sweep, S.key, cy, g);
+      break;
+    }
+    case kPhCoarse1: {
+      // eight consecutive items (lanes of one warp) share a row: strided
+      // partial sums, then a shuffle reduction
+      // (the system's items are padded to whole warps; padded lanes only
+      // take part in the shuffles)
+      const int sub = (int)(g & 7);
+      const bool valid = (g >> 3) < L.size;
+      long long r = 0;
+      const int ci = valid ? comp_at(L, g >> 3, &r) : 0;
+      const CompDev& c = L.c[ci];
+      const long long N = (long long)c.nx * c.ny * c.nz;
+      double acc = 0.0;
+      if (valid)
+        for (long long q = sub; q <= r; q += 8) acc += c.Linv[r * N + q] * (double)__ldcg(b + c.off + q);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      if (!valid || sub != 0) break;
+      if (NOISE) {
+        const unsigned long long cy = *S.cyc[mode];
+        const uint4 ctr = make_uint4((uint32_t)(r >> 2), ctr1_of(L.level, c.comp_id, 0, 0, 1), (uint32_t)cy,
+                                     (uint32_t)(cy >> 32));
+        double n4[4];
+        Normals<double>::get(philox10(ctr, S.key.k0, S.key.k1), n4);
+        acc += n4[r & 3];
+      }
+      S.ywork[c.off + r] = acc;
+      break;
+    }
+    case kPhCoarse2: {
+      const int sub = (int)(g & 7);
+      const bool valid = (g >> 3) < L.size;
+      long long col = 0;
+      const int ci = valid ? comp_at(L, g >> 3, &col) : 0;
+      const CompDev& c = L.c[ci];
+      const long long N = (long long)c.nx * c.ny * c.nz;
+      double acc = 0.0;
+      if (valid)
+        for (long long r = col + sub; r < N; r += 8) acc += c.Linv[r * N + col] * __ldcg(S.ywork + c.off + r);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      if (valid && sub == 0) v[c.off + col] = (T)acc;
+      break;
+    }
+    case kPhResid: {
+      if (l == 0) {
+        fine_residual_zm_item<T, true>(L, S.fcp, v, b, (T*)BL.t, g);
+      } else if (BL.rcp.kc > 0) {
+        int ci = 0;
+        while (ci + 1 < L.ncomp && g >= BL.rcp.start[ci + 1]) ++ci;
+        const CompDev& c = L.c[ci];
+        const int segs = c.nx >> 2;
+        const long long item = g - BL.rcp.start[ci];
+        const long long col = item % ((long long)c.ny * segs);
+        const int chunk = (int)(item / ((long long)c.ny * segs));
+        const int j = (int)(col / segs), seg = (int)(col - (long long)j * segs);
+        const int k0 = chunk * BL.rcp.kc, k1 = min(k0 + BL.rcp.kc, c.nz);
+        galerkin_residual_seg<T, 4, LdCG>(c, v + c.off, b + c.off, (T*)BL.t + c.off, j, seg << 2, k0, k1);
+      } else {
+        int ci, i, j, k;
+        site_of(L, g, &ci, &i, &j, &k);
+        const CompDev& c = L.c[ci];
+        ((T*)BL.t)[g] = __ldcg(b + g) - sep_apply<T, LdCG, true>(c, v + c.off, i, j, k);
+      }
+      break;
+    }
+    case kPhRestrict: {
+      const BatchLevelDev& BC = S.lev[l + 1];
+      const long long nres = BL.vec_down ? (long long)BC.rp.rstart[BC.L.ncomp] * (BC.L.c[0].nx >> 2) : BC.L.size;
+      if (g < nres) {
+        if (BL.vec_down)
+          restrict_seg4<T, true>(L, BC.L, BC.rp, (const T*)BL.t, (T*)BC.b, g);
+        else
+          restrict_at<T, LdCG>(L, BC.L, (const T*)BL.t, (T*)BC.b, g);
+      } else {
+        ((T*)BC.v)[g - nres] = (T)0;
+      }
+      break;
+    }
+    case kPhProlong: {
+      const BatchLevelDev& BC = S.lev[l + 1];
+      if (BL.vec_up)
+        prolong_seg8<T, false, true>(L, BC.L, BL.rp, v, (const T*)BC.v, g);
+      else
+        v[g] = __ldcg(v + g) + prolong_val<T, LdCG>(L, BC.L, (const T*)BC.v, g);
+      break;
+    }
+    case kPhOuterUpd: {
+      double* z = S.z[mode];
+      double2* z2 = reinterpret_cast<double2*>(z + 4 * g);
+      double2 a = z2[0], d = z2[1];
+      if constexpr (sizeof(T) == 4) {
+        const float4 q = __ldcg(reinterpret_cast<const float4*>(v + 4 * g));
+        a.x += (double)q.x;
+        a.y += (double)q.y;
+        d.x += (double)q.z;
+        d.y += (double)q.w;
+      } else {
+        a.x += (double)__ldcg(v + 4 * g);
+        a.y += (double)__ldcg(v + 4 * g + 1);
+        d.x += (double)__ldcg(v + 4 * g + 2);
+        d.y += (double)__ldcg(v + 4 * g + 3);
+      }
+      z2[0] = a;
+      z2[1] = d;
+      if (g == 0) {
+        if (mode == 1) *S.norm2 = 0.0;
+        if (mode == 0) *S.chain_ctr += 1ull;
+      }
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// start: [nphase][nsys + 1] first item of each system in each phase.
+// mode 0: a stochastic cycle of every chain; 1: a deterministic cycle of every
+// velocity solve.  Shared memory: nsys doubles (per-block norm partial sums).
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kBatchThreads, 2) k_batch_fac(const BatchSysDev* __restrict__ sys, int nsys,
+                                                             const BatchPhase* __restrict__ ph, int nphase,
+                                                             const long long* __restrict__ start, unsigned* bar,
+                                                             int mode, unsigned long long* tstamp) {
+  // shared memory: nsys doubles (per-block norm partial sums), then the
+  // phase's first-item table (nsys + 1 words)
+  extern __shared__ double bnorm[];
+  long long* sst = reinterpret_cast<long long*>(bnorm + nsys);
+  if (tstamp && blockIdx.x == 0 && threadIdx.x == 0) tstamp[0] = global_ns();
+  const long long tid = ((long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (int p = 0; p < nphase; ++p) {
+    const BatchPhase P = ph[p];
+    const long long* st = start + (long long)p * (nsys + 1);
+    for (int q = threadIdx.x; q <= nsys; q += blockDim.x) sst[q] = __ldg(st + q);
+    const bool norm = P.type == kPhOuterRes && mode == 1;
+    if (norm)
+      for (int q = threadIdx.x; q < nsys; q += blockDim.x) bnorm[q] = 0.0;
+    __syncthreads();
+    const long long total = sst[nsys];
+    int s = -1;
+    double acc = 0.0;
+    for (long long g = tid; g < total; g += nth) {
+      if (s < 0 || g >= sst[s + 1]) {
+        if (norm && s >= 0 && acc != 0.0) atomicAdd(bnorm + s, acc);
+        acc = 0.0;
+        // the system whose items hold g: last s with sst[s] <= g (binary search)
+        int lo = s < 0 ? 0 : s + 1, hi = nsys - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (sst[mid] <= g)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        s = lo;
+      }
+      batch_item<T, NOISE>(sys[s], P, mode, g - sst[s], &acc);
+    }
+    if (norm) {
+      if (s >= 0 && acc != 0.0) atomicAdd(bnorm + s, acc);
+      __syncthreads();
+      for (int q = threadIdx.x; q < nsys; q += blockDim.x)
+        if (bnorm[q] != 0.0) atomicAdd(sys[q].norm2, bnorm[q]);
+    }
+    // (the barrier's leading block barrier also guards sst for the next phase)
+    if ((p + 1 < nphase || tstamp) && !coop_barrier(bar)) return;
+    // phase end as block 0 sees it (profiling; after the barrier, so every
+    // block finished the phase)
+    if (tstamp && blockIdx.x == 0 && threadIdx.x == 0) tstamp[p + 1] = global_ns();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 outer iteration (Algorithm 1 steps 1 and 4)
 // ---------------------------------------------------------------------------
 
@@ -2082,6 +2482,359 @@ long long colour_pass_of(const LevelDev& L, int q, ColourPass* cp) {
   }
   cp->gstart[L.ncomp] = gs;
   return gs;
+}
+
+// ---- batched FAC cycles as one persistent launch (host side) --------------
+struct BatchPersist {
+  int nsys = 0, esize = 4, mu1 = 2, mu2 = 2;
+  std::vector<BatchSysDev> sys;
+  BatchSysDev* dsys = nullptr;
+  double* ywork = nullptr;
+  double* norms = nullptr;   // [nsys] squared residual norms of the solves
+  unsigned* bar = nullptr;   // grid barrier words
+  // phase lists: 0 chain cycle, 1 pipelined solve cycle, 2 solve cycle from u
+  std::vector<BatchPhase> ph[3];
+  std::vector<long long> st[3];
+  BatchPhase* dph[3] = {};
+  long long* dst[3] = {};
+  int kc = 16, bps = 1, blocks = 0;
+};
+
+namespace {
+
+bool batch_vec_down(const LevelDev& Lf, const LevelDev& Lc) {
+  if (Lf.c[0].nx % 8 != 0) return false;
+  for (int ci = 0; ci < Lf.ncomp; ++ci)
+    if (Lf.c[ci].nx != Lf.c[0].nx || Lc.c[ci].nx * 2 != Lf.c[ci].nx) return false;
+  return true;
+}
+
+bool batch_vec_up(const LevelDev& Lf) {
+  if (Lf.c[0].nx % 8 != 0) return false;
+  for (int ci = 0; ci < Lf.ncomp; ++ci)
+    if (Lf.c[ci].nx != Lf.c[0].nx) return false;
+  return true;
+}
+
+RowPass rows_of(const LevelDev& L) {
+  RowPass rp{};
+  int rows = 0;
+  for (int ci = 0; ci < L.ncomp; ++ci) {
+    rp.rstart[ci] = rows;
+    rows += L.c[ci].ny * L.c[ci].nz;
+  }
+  rp.rstart[L.ncomp] = rows;
+  return rp;
+}
+
+// Work items of system S in phase P (0: the phase has no work for it).
+long long batch_items(const BatchSysDev& S, const BatchPhase& P) {
+  const int last = S.levels - 1, l = P.level;
+  if (l > last) return 0;
+  const LevelDev& L = S.lev[l].L;
+  switch (P.type) {
+    case kPhOuterRes:
+      return (long long)S.orp.rstart[L.ncomp] * (L.c[0].nx >> 2);
+    case kPhOuterUpd:
+      return L.size / 4;
+    case kPhSmooth:
+      if (l == last) return 0;
+      if (l == 0) return S.fcp.start[L.ncomp];
+      return S.lev[l].v8 ? S.lev[l].sp[P.colour].start[L.ncomp] : S.lev[l].cp[P.colour].gstart[L.ncomp];
+    case kPhCoarse1:
+    case kPhCoarse2:   // 8 lanes per row / column, whole warps per system
+      return l == last ? (8 * L.size + 31) / 32 * 32 : 0;
+    case kPhResid:
+      if (l == last) return 0;
+      if (l == 0) return S.fcp.start[L.ncomp];
+      return S.lev[l].rcp.kc > 0 ? S.lev[l].rcp.start[L.ncomp] : L.size;
+    case kPhRestrict: {
+      if (l == last) return 0;
+      const BatchLevelDev& C = S.lev[l + 1];
+      const long long nres =
+          S.lev[l].vec_down ? (long long)C.rp.rstart[C.L.ncomp] * (C.L.c[0].nx >> 2) : C.L.size;
+      return nres + C.L.size;
+    }
+    case kPhProlong:
+      if (l == last) return 0;
+      return S.lev[l].vec_up ? (long long)S.lev[l].rp.rstart[L.ncomp] * (L.c[0].nx >> 3) : L.size;
+    default:
+      return 0;
+  }
+}
+
+template <typename T>
+size_t batch_smem(int nsys) {
+  return (size_t)nsys * sizeof(double);
+}
+
+}  // namespace
+
+bool batch_persist_eligible(int nsys, const BatchSysHost* h) {
+  for (int i = 0; i < nsys; ++i) {
+    const BatchSysHost& q = h[i];
+    if (q.levels < 2 || q.levels > kMaxLevels || !q.cholesky || q.esize != h[0].esize) return false;
+    const LevelDev& L0 = q.lev[0];
+    for (int ci = 0; ci < L0.ncomp; ++ci)
+      if (L0.c[ci].nx % 8 != 0 || L0.c[ci].nx != L0.c[0].nx) return false;
+    for (int l = 1; l < q.levels; ++l)
+      for (int ci = 0; ci < q.lev[l].ncomp; ++ci)
+        if (q.lev[l].c[ci].ncol > kBatchColours) return false;
+  }
+  return true;
+}
+
+cudaError_t batch_persist_configure(BatchPersist* bp, int kc, int bps) {
+  if (!bp || kc < 1 || bps < 1) return cudaErrorInvalidValue;
+  bp->kc = kc;
+  // level-0 column items with chunks of kc rows
+  for (BatchSysDev& S : bp->sys) {
+    const LevelDev& L = S.lev[0].L;
+    S.fcp = ColumnPass{};
+    S.fcp.kc = kc;
+    long long items = 0;
+    for (int ci = 0; ci < L.ncomp; ++ci) {
+      S.fcp.start[ci] = items;
+      items += (long long)L.c[ci].ny * (L.c[ci].nx >> 3) * ((L.c[ci].nz + kc - 1) / kc);
+    }
+    S.fcp.start[L.ncomp] = items;
+  }
+  int lmax = 0;
+  for (const BatchSysDev& S : bp->sys) lmax = lmax > S.levels ? lmax : S.levels;
+  auto ncol_max = [&](int l) {
+    if (l == 0) return 2;
+    int m = 0;
+    for (const BatchSysDev& S : bp->sys)
+      if (l < S.levels - 1)
+        for (int ci = 0; ci < S.lev[l].L.ncomp; ++ci) m = m > S.lev[l].L.c[ci].ncol ? m : S.lev[l].L.c[ci].ncol;
+    return m;
+  };
+  auto any = [&](auto pred) {
+    for (const BatchSysDev& S : bp->sys)
+      if (pred(S.levels - 1)) return true;
+    return false;
+  };
+  auto vcycle = [&](std::vector<BatchPhase>& v) {
+    for (int l = 0; l < lmax; ++l) {
+      if (any([&](int last) { return l < last; }))
+        for (int q = 0; q < bp->mu1; ++q)
+          for (int col = 0; col < ncol_max(l); ++col) v.push_back({kPhSmooth, l, q, col});
+      if (any([&](int last) { return l == last; })) {
+        v.push_back({kPhCoarse1, l, 0, 0});
+        v.push_back({kPhCoarse2, l, 0, 0});
+      }
+      if (any([&](int last) { return l < last; })) {
+        v.push_back({kPhResid, l, 0, 0});
+        v.push_back({kPhRestrict, l, 0, 0});
+      }
+    }
+    for (int l = lmax - 2; l >= 0; --l) {
+      if (!any([&](int last) { return l < last; })) continue;
+      v.push_back({kPhProlong, l, 0, 0});
+      for (int q = 0; q < bp->mu2; ++q)
+        for (int col = 0; col < ncol_max(l); ++col) v.push_back({kPhSmooth, l, bp->mu1 + q, col});
+    }
+  };
+  for (int k = 0; k < 3; ++k) {
+    std::vector<BatchPhase>& v = bp->ph[k];
+    v.clear();
+    if (k != 1) v.push_back({kPhOuterRes, 0, 0, 0});
+    vcycle(v);
+    v.push_back({kPhOuterUpd, 0, 0, 0});
+    if (k == 1) v.push_back({kPhOuterRes, 0, 0, 0});
+    std::vector<long long>& st = bp->st[k];
+    st.assign(v.size() * (bp->nsys + 1), 0);
+    for (size_t p = 0; p < v.size(); ++p) {
+      long long acc = 0;
+      for (int i = 0; i < bp->nsys; ++i) {
+        st[p * (bp->nsys + 1) + i] = acc;
+        acc += batch_items(bp->sys[i], v[p]);
+      }
+      st[p * (bp->nsys + 1) + bp->nsys] = acc;
+    }
+    if (bp->dph[k]) cudaFree(bp->dph[k]);
+    if (bp->dst[k]) cudaFree(bp->dst[k]);
+    bp->dph[k] = nullptr;
+    bp->dst[k] = nullptr;
+    cudaError_t e = cudaMalloc(&bp->dph[k], v.size() * sizeof(BatchPhase));
+    if (e == cudaSuccess) e = cudaMalloc(&bp->dst[k], st.size() * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemcpy(bp->dph[k], v.data(), v.size() * sizeof(BatchPhase), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bp->dst[k], st.data(), st.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaMemcpy(bp->dsys, bp->sys.data(), bp->sys.size() * sizeof(BatchSysDev), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  // co-resident blocks: bps per SM, if that many fit
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = (size_t)bp->nsys * sizeof(double) + (size_t)(bp->nsys + 1) * sizeof(long long);
+  if (bp->esize == 4)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_fac<float, true>, kBatchThreads, smem);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_fac<double, true>, kBatchThreads, smem);
+  if (e != cudaSuccess) return e;
+  int occ2 = 0;
+  if (bp->esize == 4)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_batch_fac<float, false>, kBatchThreads, smem);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_batch_fac<double, false>, kBatchThreads, smem);
+  if (e != cudaSuccess) return e;
+  occ = occ < occ2 ? occ : occ2;
+  if (occ < 1) return cudaErrorNotSupported;
+  bp->bps = bps < occ ? bps : occ;
+  bp->blocks = bp->bps * sms;
+  return cudaSuccess;
+}
+
+cudaError_t batch_persist_create(int nsys, const BatchSysHost* h, int mu1, int mu2, BatchPersist** out) {
+  *out = nullptr;
+  if (nsys < 1 || !batch_persist_eligible(nsys, h)) return cudaErrorNotSupported;
+  BatchPersist* bp = new (std::nothrow) BatchPersist();
+  if (!bp) return cudaErrorMemoryAllocation;
+  bp->nsys = nsys;
+  bp->esize = h[0].esize;
+  bp->mu1 = mu1;
+  bp->mu2 = mu2;
+  bp->sys.resize(nsys);
+  long long ywork = 0;
+  for (int i = 0; i < nsys; ++i) ywork += h[i].lev[h[i].levels - 1].size;
+  cudaError_t e = cudaMalloc(&bp->dsys, nsys * sizeof(BatchSysDev));
+  if (e == cudaSuccess) e = cudaMalloc(&bp->ywork, (size_t)ywork * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&bp->norms, (size_t)nsys * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&bp->bar, 4 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(bp->norms, 0, (size_t)nsys * sizeof(double));
+  if (e != cudaSuccess) {
+    batch_persist_destroy(bp);
+    return e;
+  }
+  long long yoff = 0;
+  for (int i = 0; i < nsys; ++i) {
+    const BatchSysHost& q = h[i];
+    BatchSysDev& S = bp->sys[i];
+    std::memset(&S, 0, sizeof(S));
+    S.levels = q.levels;
+    S.key = q.key;
+    S.cyc[0] = q.cyc;
+    S.cyc[1] = q.cyc + 1;
+    S.chain_ctr = q.cyc;
+    S.z[0] = q.xi;
+    S.z[1] = q.u;
+    S.bz[0] = nullptr;
+    S.bz[1] = q.bvel;
+    S.norm2 = bp->norms + i;
+    S.ywork = bp->ywork + yoff;
+    yoff += q.lev[q.levels - 1].size;
+    for (int l = 0; l < q.levels; ++l) {
+      BatchLevelDev& BL = S.lev[l];
+      BL.L = q.lev[l];
+      BL.v = q.v[l];
+      BL.b = q.b[l];
+      BL.t = q.t[l];
+      BL.rp = rows_of(q.lev[l]);
+      if (l >= 1) {
+        const LevelDev& L = q.lev[l];
+        BL.v8 = 1;
+        bool four = true;
+        for (int ci = 0; ci < L.ncomp; ++ci) {
+          if (L.c[ci].nx % 8 != 0 || L.c[ci].mx != 2) BL.v8 = 0;
+          if (L.c[ci].nx % 4 != 0) four = false;
+        }
+        for (int col = 0; col < kBatchColours; ++col) {
+          BL.cp[col] = ColourPass{};
+          colour_pass_of(L, col, &BL.cp[col]);
+          ColumnPass& sp = BL.sp[col];
+          sp = ColumnPass{};
+          long long items = 0;
+          for (int ci = 0; ci < L.ncomp; ++ci) {
+            sp.start[ci] = items;
+            if (BL.cp[col].nsites[ci] > 0) items += (long long)(L.c[ci].nx >> 3) * BL.cp[col].nyc[ci] * BL.cp[col].nzc[ci];
+          }
+          sp.start[L.ncomp] = items;
+        }
+        BL.rcp = ColumnPass{};
+        if (four) {
+          BL.rcp.kc = 8;
+          long long items = 0;
+          for (int ci = 0; ci < L.ncomp; ++ci) {
+            BL.rcp.start[ci] = items;
+            items += (long long)L.c[ci].ny * (L.c[ci].nx >> 2) * ((L.c[ci].nz + 7) / 8);
+          }
+          BL.rcp.start[L.ncomp] = items;
+        }
+      }
+      BL.vec_up = l + 1 < q.levels && batch_vec_up(q.lev[l]) ? 1 : 0;
+      BL.vec_down = l + 1 < q.levels && batch_vec_down(q.lev[l], q.lev[l + 1]) ? 1 : 0;
+    }
+    S.orp = S.lev[0].rp;
+  }
+  e = batch_persist_configure(bp, 16, 1);
+  if (e != cudaSuccess) {
+    batch_persist_destroy(bp);
+    return e;
+  }
+  *out = bp;
+  return cudaSuccess;
+}
+
+void batch_persist_destroy(BatchPersist* bp) {
+  if (!bp) return;
+  for (int k = 0; k < 3; ++k) {
+    if (bp->dph[k]) cudaFree(bp->dph[k]);
+    if (bp->dst[k]) cudaFree(bp->dst[k]);
+  }
+  if (bp->dsys) cudaFree(bp->dsys);
+  if (bp->ywork) cudaFree(bp->ywork);
+  if (bp->norms) cudaFree(bp->norms);
+  if (bp->bar) cudaFree(bp->bar);
+  delete bp;
+}
+
+const double* batch_persist_norms(const BatchPersist* bp) { return bp ? bp->norms : nullptr; }
+
+int batch_persist_phases(const BatchPersist* bp, int kind, int* types, int* levels) {
+  if (!bp || kind < 0 || kind > 2) return 0;
+  const std::vector<BatchPhase>& v = bp->ph[kind];
+  for (size_t p = 0; p < v.size(); ++p) {
+    if (types) types[p] = v[p].type;
+    if (levels) levels[p] = v[p].level;
+  }
+  return (int)v.size();
+}
+
+const unsigned* batch_persist_bar(const BatchPersist* bp) { return bp ? bp->bar : nullptr; }
+
+void batch_persist_shape(const BatchPersist* bp, int* kc, int* bps) {
+  *kc = bp ? bp->kc : 0;
+  *bps = bp ? bp->bps : 0;
+}
+
+cudaError_t batch_persist_launch(BatchPersist* bp, int kind, cudaStream_t st, unsigned long long* tstamp) {
+  if (!bp || kind < 0 || kind > 2) return cudaErrorInvalidValue;
+  const int mode = kind == 0 ? 0 : 1;
+  cudaError_t e = cudaMemsetAsync(bp->bar, 0, 4 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(bp->blocks);
+  cfg.blockDim = dim3(kBatchThreads);
+  cfg.dynamicSmemBytes = (size_t)bp->nsys * sizeof(double) + (size_t)(bp->nsys + 1) * sizeof(long long);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const BatchSysDev* sys = bp->dsys;
+  const int nsys = bp->nsys, nph = (int)bp->ph[kind].size();
+  const BatchPhase* ph = bp->dph[kind];
+  const long long* stt = bp->dst[kind];
+  prof::Scope ps(SELM_K_BATCH_CYCLE, st);
+  if (bp->esize == 4) {
+    if (mode == 0) return cudaLaunchKernelEx(&cfg, k_batch_fac<float, true>, sys, nsys, ph, nph, stt, bp->bar, mode, tstamp);
+    return cudaLaunchKernelEx(&cfg, k_batch_fac<float, false>, sys, nsys, ph, nph, stt, bp->bar, mode, tstamp);
+  }
+  if (mode == 0) return cudaLaunchKernelEx(&cfg, k_batch_fac<double, true>, sys, nsys, ph, nph, stt, bp->bar, mode, tstamp);
+  return cudaLaunchKernelEx(&cfg, k_batch_fac<double, false>, sys, nsys, ph, nph, stt, bp->bar, mode, tstamp);
 }
 
 // Blocks of a cooperative level launch on the current device: one per SM

@@ -76,4 +76,51 @@ cudaError_t launch_grad_sub(const LevelDev& Lv, double* w, const double* phi, cu
 
 cudaError_t launch_philox(const uint32_t* ctr, Key key, uint32_t* out, int n, cudaStream_t st);
 
+// Spectral inner solve of the uniform channel's Neumann pressure problem
+// (selm_spectral.cu): delta = A^-1 r up to FP32 rounding (FFT along x and y,
+// Thomas along z); `spectrum`: spectral_pressure_bytes() of scratch.
+bool spectral_pressure_supported(const LevelDev& L0);
+size_t spectral_pressure_bytes(const LevelDev& L0);
+cudaError_t spectral_pressure_solve(const LevelDev& L0, const float* r, float* delta, void* spectrum,
+                                    cudaStream_t st);
+
+// ---- batched FAC cycles as one persistent launch ----------------------------
+// One system of a batch as the persistent launch sees it (device pointers of
+// its handle).
+struct BatchSysHost {
+  int levels;
+  int esize;                     // inner precision bytes (the same for all systems)
+  bool cholesky;                 // exact coarsest step (required)
+  const LevelDev* lev;           // [levels]
+  void* const* v;                // [levels] level fields
+  void* const* b;
+  void* const* t;
+  Key key;
+  unsigned long long* cyc;       // [0] chain counter, [1] solve stage counter
+  double* u;                     // solve iterate (FP64)
+  double* xi;                    // chain state (FP64)
+  const double* bvel;            // solve right-hand side (FP64)
+};
+struct BatchPersist;
+bool batch_persist_eligible(int nsys, const BatchSysHost* sys);
+// Device plan of the batch (allocates device memory for its tables).
+cudaError_t batch_persist_create(int nsys, const BatchSysHost* sys, int mu1, int mu2, BatchPersist** out);
+void batch_persist_destroy(BatchPersist* bp);
+// Tile shape: level-0 column items of kc z rows; bps co-resident blocks per SM.
+cudaError_t batch_persist_configure(BatchPersist* bp, int kc, int bps);
+void batch_persist_shape(const BatchPersist* bp, int* kc, int* bps);
+// kind 0: one stochastic cycle of every chain (counters advance);
+// kind 1: one pipelined solve cycle (V-cycle on the residual already in each
+//         system's level-0 rhs with v0 = 0, update of u, next residual and its
+//         squared norm into batch_persist_norms()[i], v0 = 0);
+// kind 2: one solve cycle from u (residual, V-cycle, update).
+// tstamp (optional, device, nphase + 1 words): %globaltimer at the start and
+// after each phase's barrier, as block 0 sees it.
+cudaError_t batch_persist_launch(BatchPersist* bp, int kind, cudaStream_t st, unsigned long long* tstamp = nullptr);
+const double* batch_persist_norms(const BatchPersist* bp);
+// Phases of a launch kind (types: BatchPhaseType codes, levels); returns the count.
+int batch_persist_phases(const BatchPersist* bp, int kind, int* types, int* levels);
+// Grid-barrier words of the launches ([2] != 0: a wait timed out).
+const unsigned* batch_persist_bar(const BatchPersist* bp);
+
 }  // namespace selm

@@ -24,6 +24,7 @@ SELM_OPT_ENGINE_LEVEL = 3
 SELM_OPT_LEVEL_COOP = 4
 SELM_OPT_GRAPHS = 5
 SELM_OPT_SPECULATE = 6
+SELM_OPT_PRESSURE_SPECTRAL = 8
 SELM_BATCH_SOLVE, SELM_BATCH_SAMPLE = 0, 1
 
 _STATUS = {0: "SELM_OK", 1: "SELM_EINVAL", 2: "SELM_ENOMEM", 3: "SELM_ECUDA", 4: "SELM_ENOCONV",
@@ -98,6 +99,7 @@ _SIGS = {
     "selm_mg_fail_waits": (_I, [_P, _I, _P]),
     "selm_mg_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_LL)]),
     "selm_mg_set_option": (_I, [_P, _I, _I]),
+    "selm_mg_pressure_spectral": (_I, [_P]),
     "selm_mg_engine_info": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
     "selm_mg_smooth": (_I, [_P, _I, _I, _P, _P, _I, _U64, _I, _P]),
     "selm_mg_residual_restrict": (_I, [_P, _I, _I, _P, _P, _P, _P]),
@@ -122,6 +124,10 @@ _SIGS = {
                              ctypes.POINTER(_I), _P]),
     "selm_batch_autotune": (_I, [_P, ctypes.POINTER(_I), _P]),
     "selm_batch_cycle": (_I, [_P, _I, _P]),
+    "selm_batch_set_persistent": (_I, [_P, _I]),
+    "selm_batch_phase_times": (_I, [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D),
+                                    ctypes.POINTER(_I), _P]),
+    "selm_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "selm_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
     "selm_server_submit": (_I, [_P, ctypes.POINTER(SelmRequest), ctypes.POINTER(_U64)]),
     "selm_server_poll": (_I, [_P, ctypes.POINTER(SelmResult), _I]),
@@ -152,7 +158,7 @@ _SIGS = {
 }
 
 KERNEL_CLASSES = ["fine_sweep", "coarse_sweep", "residual", "restrict", "prolong", "coarsest",
-                  "outer_residual", "outer_update", "spread", "interp", "projection", "other"]
+                  "outer_residual", "outer_update", "spread", "interp", "projection", "other", "batch_cycle"]
 
 
 def library_path():
@@ -333,6 +339,10 @@ def selm_mg_set_option(h, option, value):
     _check(h, lib().selm_mg_set_option(h, option, int(value)))
 
 
+def selm_mg_pressure_spectral(h):
+    return int(lib().selm_mg_pressure_spectral(h))
+
+
 def selm_mg_engine_info(h, system=SELM_SYS_VELOCITY):
     l0, c, sm = _I(0), _I(0), ctypes.c_size_t(0)
     _check(h, lib().selm_mg_engine_info(h, system, ctypes.byref(l0), ctypes.byref(c), ctypes.byref(sm)))
@@ -449,6 +459,31 @@ def selm_batch_autotune(b, stream=None):
 
 def selm_batch_cycle(b, mode, stream=None):
     _check_batch(b, lib().selm_batch_cycle(b, mode, _stream(stream)))
+
+
+def selm_batch_set_persistent(b, on):
+    _check_batch(b, lib().selm_batch_set_persistent(b, int(on)))
+
+
+BATCH_PHASE_NAMES = ["outer_residual", "colour_pass", "coarsest_L", "coarsest_LT", "residual", "restrict",
+                     "prolong", "outer_update"]
+
+
+def selm_batch_phase_times(b, mode, stream=None):
+    """[(phase name, level, microseconds)] of one persistent batched FAC cycle."""
+    n = _I(0)
+    _check_batch(b, lib().selm_batch_phase_times(b, mode, 0, None, None, None, ctypes.byref(n), _stream(stream)))
+    k = n.value
+    t, lv, us = (_I * k)(), (_I * k)(), (_D * k)()
+    _check_batch(b, lib().selm_batch_phase_times(b, mode, k, t, lv, us, ctypes.byref(n), _stream(stream)))
+    return [(BATCH_PHASE_NAMES[t[p]], lv[p], us[p]) for p in range(k)]
+
+
+def selm_batch_info(b):
+    """{'persistent', 'kc', 'blocks_per_sm', 'cluster'} of a batch."""
+    v = [_I(0) for _ in range(4)]
+    _check_batch(b, lib().selm_batch_info(b, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("persistent", "kc", "blocks_per_sm", "cluster"), (x.value for x in v)))
 
 
 def selm_server_create(budget_bytes, max_slots):

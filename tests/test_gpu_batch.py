@@ -1,9 +1,10 @@
 """GPU: the batched form equals each system advanced alone.
 
 Several independent channel systems of uneven size, each with its own seed,
-instance and kT, are advanced by selm_batch_step (one graph launch per phase
-for all systems).  Each system is also advanced alone by selm_mg_step from
-the same state.  The stochastic chains see the same Philox counters, so the
+instance and kT, are advanced by selm_batch_step, in its persistent form (one
+cooperative launch per FAC cycle of all systems) and in its per-system graph
+form (one graph launch per phase with a branch per system).  Each system is
+also advanced alone by selm_mg_step from the same state.  The stochastic chains see the same Philox counters, so the
 thermal fields agree to rounding; the deterministic solves stop at the
 batch's slowest system, which only tightens the tolerance.  Trajectories must
 agree to well within the FP32-inner tolerance, before and after the
@@ -35,6 +36,18 @@ def S():
     return mod
 
 
+FORMS = ["persistent", "graphs"]
+
+
+def _batch(S, descs, form):
+    b = S.selm_batch_create(descs)
+    if form == "persistent":
+        assert S.selm_batch_info(b)["persistent"] == 1, "the batch should qualify for the persistent form"
+    else:
+        S.selm_batch_set_persistent(b, 0)
+    return b
+
+
 def _descs(S):
     return [S.make_desc(dim=d, n=n, kT=kT, precision=S.SELM_FP32_REFINE64, seed=seed, instance=7 + i,
                         max_particles=256)
@@ -61,17 +74,19 @@ def _alone(S, descs, Xs, Fs, nsteps):
     return out
 
 
-def test_batch_matches_systems_alone(S):
+@pytest.mark.parametrize("form", FORMS)
+def test_batch_matches_systems_alone(S, form):
     descs = _descs(S)
     Xs, Fs = _inputs()
-    b = S.selm_batch_create(descs)
+    b = _batch(S, descs, form)
     X = [torch.tensor(x, device="cuda") for x in Xs]
     F = [torch.tensor(f, device="cuda") for f in Fs]
     cycles = S.selm_batch_step(b, X, F, 1e-3, 1, 2)
     l0 = S.selm_kernel_launches()   # the second step replays the graphs the first captured
     cycles += S.selm_batch_step(b, X, F, 1e-3, 1, 2)
     torch.cuda.synchronize()
-    assert S.selm_kernel_launches() - l0 > 4 * len(SYSTEMS)   # replays credit the kernels they hold
+    # replays credit the kernels they hold
+    assert S.selm_kernel_launches() - l0 > (4 if form == "persistent" else 4 * len(SYSTEMS))
     assert all(1 <= c <= 15 for c in cycles)
     want = _alone(S, descs, Xs, Fs, 2)
     for i, (x, w, x0) in enumerate(zip(X, want, Xs)):
@@ -84,12 +99,16 @@ def test_batch_matches_systems_alone(S):
     S.selm_batch_destroy(b)
 
 
-def test_batch_autotune_keeps_results(S):
+@pytest.mark.parametrize("form", FORMS)
+def test_batch_autotune_keeps_results(S, form):
     descs = _descs(S)
     Xs, Fs = _inputs()
-    b = S.selm_batch_create(descs)
-    chosen = S.selm_batch_autotune(b)
-    assert chosen in (4, 8, 16)
+    b = _batch(S, descs, form)
+    chosen = S.selm_batch_autotune(b)   # tunes both forms and keeps the faster one
+    info = S.selm_batch_info(b)
+    assert info["kc"] in (8, 16, 32) and info["blocks_per_sm"] in (1, 2)
+    assert chosen in (4, 8, 16) and info["cluster"] == chosen
+    S.selm_batch_set_persistent(b, 1 if form == "persistent" else 0)   # the form under test, tuned
     X = [torch.tensor(x, device="cuda") for x in Xs]
     F = [torch.tensor(f, device="cuda") for f in Fs]
     S.selm_batch_step(b, X, F, 1e-3, 2, 2)
@@ -107,7 +126,8 @@ def test_batch_rejects_projection(S):
         S.selm_batch_create([d])
 
 
-def test_batch_at_benchmark_shapes(S):
+@pytest.mark.parametrize("form", FORMS)
+def test_batch_at_benchmark_shapes(S, form):
     """Systems of every edge the batched benchmark draws (32..128, FP32 inner
     cycles with FP64 refinement, 64..2048 particles), with the engine cluster
     size the autotuner picks, as the benchmark runs them: the batch equals each
@@ -119,8 +139,9 @@ def test_batch_at_benchmark_shapes(S):
                          max_particles=2048) for i, e in enumerate(edges)]
     Xs = [selm_inputs.particles(npart, 3, e, seed=i) for i, (npart, e) in enumerate(zip(nps, edges))]
     Fs = [selm_inputs.forces(npart, 3, seed=i) for i, npart in enumerate(nps)]
-    b = S.selm_batch_create(descs)
+    b = _batch(S, descs, form)
     S.selm_batch_autotune(b)
+    S.selm_batch_set_persistent(b, 1 if form == "persistent" else 0)
     X = [torch.tensor(x, device="cuda") for x in Xs]
     F = [torch.tensor(f, device="cuda") for f in Fs]
     S.selm_batch_step(b, X, F, 1e-3, 2, 2)
@@ -153,9 +174,10 @@ def _level_size(S, h):
     return S.selm_mg_layout(h, S.SELM_SYS_VELOCITY, 0, 0)[2]
 
 
-def test_batch_cycle_sample_equals_each_chain_alone(S):
+@pytest.mark.parametrize("form", FORMS)
+def test_batch_cycle_sample_equals_each_chain_alone(S, form):
     descs = _fp64_descs(S)
-    b = S.selm_batch_create(descs)
+    b = _batch(S, descs, form)
     for _ in range(3):
         S.selm_batch_cycle(b, S.SELM_BATCH_SAMPLE)
     torch.cuda.synchronize()
@@ -175,7 +197,8 @@ def test_batch_cycle_sample_equals_each_chain_alone(S):
     S.selm_batch_destroy(b)
 
 
-def test_batch_cycle_solve_is_one_fac_cycle(S):
+@pytest.mark.parametrize("form", FORMS)
+def test_batch_cycle_solve_is_one_fac_cycle(S, form):
     # after a step, each system's solve iterate u (perturbed here) goes through
     # one deterministic FAC cycle with the step's right-hand side Gamma^T F
     from oracle import coupling, grid, multigrid
@@ -183,7 +206,7 @@ def test_batch_cycle_solve_is_one_fac_cycle(S):
     from tests.gpu_util import from_dev
     descs = _fp64_descs(S)
     Xs, Fs = _inputs()
-    b = S.selm_batch_create(descs)
+    b = _batch(S, descs, form)
     X = [torch.tensor(x, device="cuda") for x in Xs]
     F = [torch.tensor(f, device="cuda") for f in Fs]
     S.selm_batch_step(b, X, F, 1e-3, 1, 1)

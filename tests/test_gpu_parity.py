@@ -452,3 +452,45 @@ def test_create_rejects_misaligned_workspace():
         S.selm_mg_create(d)
     assert err.value.status == S.SELM_EINVAL
     assert len(freed) == 1 and not blocks
+
+
+def _exact_projection(w0, n):
+    """P~ w = w - D^T phi with (D D^T) phi = D w - mean, from the closed-form
+    spectral inverse of the Neumann pressure operator (independent of both the
+    library and the oracle's iterative solve)."""
+    from tests import closed_forms as cf
+    div = projection.divergence(w0, 3)
+    phi = cf.spectral_solve(("P", "P", "N"), n, 1.0, div - div.mean())
+    g = projection.divergence_transpose(phi, 3)
+    return [a - b for a, b in zip(w0, g)]
+
+
+@pytest.mark.parametrize("n", [16, 64, 128])
+def test_projection_spectral_inner_solve(n):
+    """FP32 inner cycles on the uniform channel: the projection's pressure
+    refinement takes the spectral inner solve by default; P~w equals the exact
+    projection (closed form) to the solve tolerance and the V-cycle path's
+    result, and the field is divergence-free."""
+    m = S.SelmMG(dim=3, n=n, precision=S.SELM_FP32_REFINE64, projection=1, proj_tol=1e-12)
+    assert S.selm_mg_pressure_spectral(m.h) == 1
+    w0 = selm_inputs.fields(grid.velocity_system(n, 3, levels=1).shapes(0), seed=26)
+    w = to_dev(m.h, w0, torch.float64)
+    iters = S.selm_mg_project(m.h, w)
+    assert 1 <= iters <= 5
+    got = from_dev(m.h, w)
+    want = _exact_projection(w0, n)
+    assert rel(got, want) < 1e-10
+    div = projection.divergence(got, 3)
+    assert np.abs(div).max() < 1e-10 * np.abs(projection.divergence(w0, 3)).max()
+    S.selm_mg_set_option(m.h, S.SELM_OPT_PRESSURE_SPECTRAL, 0)
+    assert S.selm_mg_pressure_spectral(m.h) == 0
+    w2 = to_dev(m.h, w0, torch.float64)
+    S.selm_mg_project(m.h, w2)
+    assert rel(from_dev(m.h, w2), got) < 1e-9
+
+
+def test_projection_spectral_unavailable_in_fp64():
+    m = S.SelmMG(dim=3, n=16, precision=S.SELM_FP64, projection=1)
+    assert S.selm_mg_pressure_spectral(m.h) == 0
+    with pytest.raises(S.SelmError):
+        S.selm_mg_set_option(m.h, S.SELM_OPT_PRESSURE_SPECTRAL, 1)

@@ -12,12 +12,14 @@
 // along z.  The solve used inside FP64 iterative refinement (the projection's
 // FAC iteration of Algorithm 1 with this solve in place of the V-cycle) is:
 //   1. forward 2-D FFT of every z plane of the FP32 residual (one CTA per
-//      plane, the plane in shared memory, radix-2 decimation in time);
-//   2. per mode, the z system solved by the Thomas algorithm in FP64
-//      arithmetic (the all-constant mode (0, 0) is singular: its z = 0 value is
-//      pinned to 0, which fixes the pressure's free constant; the gradient
-//      does not see it);
-//   3. inverse 2-D FFT of every plane; the real part / n^2 is the correction.
+//      plane, the plane in shared memory, radix-2 decimation in frequency:
+//      modes come out in bit-reversed order, which nothing needs to undo);
+//   2. per mode, the z system solved by the Thomas algorithm in FP32 (the
+//      all-constant mode (0, 0) is singular: its z = 0 value is pinned to 0,
+//      which fixes the pressure's free constant, and its column -- the
+//      worst-conditioned one -- is solved exactly in FP64 by two scans);
+//   3. inverse 2-D FFT of every plane (decimation in time, bit-reversed in,
+//      natural out); the real part / n^2 is the correction.
 // Grids: 3-D, nx == ny == n a power of two, 4 <= n <= 128; nz >= 2.
 
 #include <cuda_runtime.h>
@@ -34,37 +36,9 @@ namespace selm {
 namespace {
 
 constexpr int kSpecThreads = 512;
-constexpr int kThomasThreads = 64;
+constexpr int kThomasThreads = 128;
 
 __device__ __forceinline__ int bitrev(int x, int logn) { return (int)(__brev((unsigned)x) >> (32 - logn)); }
-
-// In-place radix-2 DIT FFT of all rows (along x) or all columns (along y) of
-// an n x n complex plane in shared memory whose entries sit at bit-reversed
-// positions along that axis.  sign = -1 forward, +1 inverse (unscaled).
-__device__ void fft_axis(float2* A, const float2* W, int n, int logn, bool columns, float sign) {
-  const int half_n = n >> 1;
-  for (int s = 1; s <= logn; ++s) {
-    const int half = 1 << (s - 1);
-    const int tw_step = n >> s;   // twiddle index stride: W[j * n / (2 half)]
-    for (int q = threadIdx.x; q < n * half_n; q += blockDim.x) {
-      // along columns, consecutive threads take consecutive columns (the
-      // butterflies of one column are n entries apart: bank conflicts else)
-      const int line = columns ? q % n : q / half_n;
-      const int p = columns ? q / n : q - line * half_n;
-      const int grp = p / half, j = p - grp * half;
-      const int i0 = grp * 2 * half + j, i1 = i0 + half;
-      float2 w = W[j * tw_step];   // exp(-2 pi i j / (2 half)); conjugated for the inverse
-      w.y *= -sign;
-      const int a0 = columns ? i0 * n + line : line * n + i0;
-      const int a1 = columns ? i1 * n + line : line * n + i1;
-      const float2 x0 = A[a0], x1 = A[a1];
-      const float2 t = make_float2(w.x * x1.x - w.y * x1.y, w.x * x1.y + w.y * x1.x);
-      A[a0] = make_float2(x0.x + t.x, x0.y + t.y);
-      A[a1] = make_float2(x0.x - t.x, x0.y - t.y);
-    }
-    __syncthreads();
-  }
-}
 
 // twiddles W[j] = exp(-2 pi i j / n), j < n / 2
 __device__ void make_twiddles(float2* W, int n) {
@@ -75,7 +49,61 @@ __device__ void make_twiddles(float2* W, int n) {
   }
 }
 
-// Forward: plane k of r (FP32, [nz][n][n]) -> spectrum S[k][my][mx].
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Butterfly q of a stage over all rows (columns == false: along x) or all
+// columns (along y) of an n x n plane: line and pair index, with consecutive
+// threads on consecutive addresses in both cases.
+__device__ __forceinline__ void stage_index(int q, int n, int half, bool columns, int* a0, int* a1, int* j) {
+  const int half_n = n >> 1;
+  const int line = columns ? q % n : q / half_n;
+  const int p = columns ? q / n : q - (q / half_n) * half_n;
+  const int grp = p / half;
+  *j = p - grp * half;
+  const int i0 = grp * 2 * half + *j, i1 = i0 + half;
+  *a0 = columns ? i0 * n + line : line * n + i0;
+  *a1 = columns ? i1 * n + line : line * n + i1;
+}
+
+// Forward transform along one axis, decimation in frequency: natural order in,
+// bit-reversed order out.
+__device__ void fft_dif(float2* A, const float2* W, int n, int logn, bool columns) {
+  for (int s = logn; s >= 1; --s) {
+    const int half = 1 << (s - 1), tw_step = n >> s;
+    for (int q = threadIdx.x; q < n * (n >> 1); q += blockDim.x) {
+      int a0, a1, j;
+      stage_index(q, n, half, columns, &a0, &a1, &j);
+      const float2 x0 = A[a0], x1 = A[a1];
+      A[a0] = make_float2(x0.x + x1.x, x0.y + x1.y);
+      A[a1] = cmul(make_float2(x0.x - x1.x, x0.y - x1.y), W[j * tw_step]);
+    }
+    __syncthreads();
+  }
+}
+
+// Inverse transform (unscaled) along one axis, decimation in time:
+// bit-reversed order in, natural order out.
+__device__ void fft_dit_inv(float2* A, const float2* W, int n, int logn, bool columns) {
+  for (int s = 1; s <= logn; ++s) {
+    const int half = 1 << (s - 1), tw_step = n >> s;
+    for (int q = threadIdx.x; q < n * (n >> 1); q += blockDim.x) {
+      int a0, a1, j;
+      stage_index(q, n, half, columns, &a0, &a1, &j);
+      float2 w = W[j * tw_step];
+      w.y = -w.y;   // exp(+2 pi i j / (2 half))
+      const float2 x0 = A[a0], t = cmul(A[a1], w);
+      A[a0] = make_float2(x0.x + t.x, x0.y + t.y);
+      A[a1] = make_float2(x0.x - t.x, x0.y - t.y);
+    }
+    __syncthreads();
+  }
+}
+
+// Forward: plane k of r (FP32, [nz][n][n]) -> spectrum S[k][.][.] with both
+// mode indices in bit-reversed order (the solve along z does not care; the
+// inverse transform takes that order as it comes).
 __global__ void __launch_bounds__(kSpecThreads) k_spec_forward(const float* __restrict__ r, float2* __restrict__ S,
                                                                int n, int logn) {
   extern __shared__ float2 sm[];
@@ -84,13 +112,20 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_forward(const float* __re
   const int k = blockIdx.x;
   const float* rp = r + (long long)k * n * n;
   make_twiddles(W, n);
-  for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
-    const int y = q / n, x = q - y * n;
-    A[bitrev(y, logn) * n + bitrev(x, logn)] = make_float2(rp[q], 0.0f);
+  // eight loads in flight per thread before their stores (n * n is a
+  // multiple of 8 * blockDim for the supported sizes, else the tail loop)
+  int q = threadIdx.x;
+  for (; q + 7 * (int)blockDim.x < n * n; q += 8 * blockDim.x) {
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = rp[q + e * blockDim.x];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) A[q + e * blockDim.x] = make_float2(v[e], 0.0f);
   }
+  for (; q < n * n; q += blockDim.x) A[q] = make_float2(rp[q], 0.0f);
   __syncthreads();
-  fft_axis(A, W, n, logn, false, -1.0f);
-  fft_axis(A, W, n, logn, true, -1.0f);
+  fft_dif(A, W, n, logn, false);
+  fft_dif(A, W, n, logn, true);
   float2* Sp = S + (long long)k * n * n;
   for (int q = threadIdx.x; q < n * n; q += blockDim.x) Sp[q] = A[q];
 }
@@ -104,62 +139,137 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_inverse(const float2* __r
   const int k = blockIdx.x;
   const float2* Sp = S + (long long)k * n * n;
   make_twiddles(W, n);
-  for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
-    const int y = q / n, x = q - y * n;
-    A[bitrev(y, logn) * n + bitrev(x, logn)] = Sp[q];
+  int q = threadIdx.x;
+  for (; q + 7 * (int)blockDim.x < n * n; q += 8 * blockDim.x) {
+    float2 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = Sp[q + e * blockDim.x];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) A[q + e * blockDim.x] = v[e];
   }
+  for (; q < n * n; q += blockDim.x) A[q] = Sp[q];
   __syncthreads();
-  fft_axis(A, W, n, logn, false, 1.0f);
-  fft_axis(A, W, n, logn, true, 1.0f);
+  fft_dit_inv(A, W, n, logn, false);
+  fft_dit_inv(A, W, n, logn, true);
   const float inv = 1.0f / (float)(n * n);
   float* dp = d + (long long)k * n * n;
   for (int q = threadIdx.x; q < n * n; q += blockDim.x) dp[q] = A[q].x * inv;
 }
 
-// Thomas algorithm along z for the modes (mx0 + t, my), t < blockDim.x, in
-// FP64 arithmetic; S is overwritten by the solution.  Shared memory: the
-// forward sweep's c' and d' per thread ([nz][threads]).
-__global__ void __launch_bounds__(kThomasThreads) k_spec_thomas(float2* __restrict__ S, int n, int nz, double scale) {
-  extern __shared__ double tsm[];
+// Thomas algorithm along z for the modes stored at (row py, column px)
+// (mode indices bit-reversed), one thread per column, in place in S, in FP32.
+// Shared memory: per thread, the forward sweep's c' and the column
+// ([nz][threads] each).  The all-constant mode (0, 0) is singular; the extra
+// last block solves it alone (one warp, FP64): its z = 0 value is pinned to 0,
+// which fixes the pressure's free constant, and the remaining rows of the
+// Neumann T_z are a flux balance, g_k = x_k - x_{k-1} = sum_{j >= k} d_j and
+// x_k = sum_{i <= k} g_i -- two scans.
+__global__ void __launch_bounds__(kThomasThreads) k_spec_thomas(float2* __restrict__ S, int n, int logn, int nz,
+                                                                float inv_scale) {
+  extern __shared__ float tsm[];
   const int t = threadIdx.x;
-  const int per_row = n / kThomasThreads > 0 ? n / kThomasThreads : 1;
-  const int my = blockIdx.x / per_row;
-  const int mx = (blockIdx.x - my * per_row) * blockDim.x + t;
-  if (mx >= n) return;
-  double* cp = tsm;                                  // [nz][threads]
-  double2* dp = (double2*)(tsm + nz * blockDim.x);   // [nz][threads]
+  const int per_row = n / (int)blockDim.x > 0 ? n / (int)blockDim.x : 1;
   const long long plane = (long long)n * n;
-  const long long col = (long long)my * n + mx;
-  // lambda(m) = 2 - 2 cos(2 pi m / n)
-  const double lam = (2.0 - 2.0 * cospi(2.0 * mx / n)) + (2.0 - 2.0 * cospi(2.0 * my / n));
-  const bool zero_mode = mx == 0 && my == 0;
-  double cprev = 0.0;
-  double2 dprev = make_double2(0.0, 0.0);
-  for (int k = 0; k < nz; ++k) {
-    const float2 f = S[k * plane + col];
-    double b = lam + ((k == 0 || k == nz - 1) ? 1.0 : 2.0);   // Neumann ends
-    const double a = k == 0 ? 0.0 : -1.0, c = k == nz - 1 ? 0.0 : -1.0;
-    double2 d = make_double2((double)f.x / scale, (double)f.y / scale);   // operator = scale (lambda + T_z)
-    if (zero_mode && k == 0) {   // pinned: phi^(0, 0, z = 0) = 0
-      b = 1.0;
-      d = make_double2(0.0, 0.0);
+  if (blockIdx.x == (unsigned)(n * per_row)) {   // the (0, 0) mode, stored at column 0 of row 0
+    if (t >= 32) return;
+    const int rows = nz - 1;                      // unknowns x_1 .. x_{nz-1}
+    const int per = (rows + 31) / 32;             // consecutive rows per lane
+    double gx[8], gy[8];                          // nz <= 257
+    const int k0 = 1 + t * per;
+    double sx = 0.0, sy = 0.0;
+    // suffix sums of d within the lane's rows, then across lanes
+    for (int e = per - 1; e >= 0; --e) {
+      const int k = k0 + e;
+      if (k < nz) {
+        const float2 f = S[k * plane];
+        sx += (double)f.x * inv_scale;
+        sy += (double)f.y * inv_scale;
+      }
+      gx[e] = sx;
+      gy[e] = sy;
     }
-    const double cc = zero_mode && k == 0 ? 0.0 : c;
-    const double m = b - a * cprev;
-    const double cn = cc / m;
-    const double2 dn = make_double2((d.x - a * dprev.x) / m, (d.y - a * dprev.y) / m);
-    cp[k * blockDim.x + t] = cn;
-    dp[k * blockDim.x + t] = dn;
-    cprev = cn;
-    dprev = dn;
+    // exclusive suffix scan of the lane totals over higher lanes
+    double tx = sx, ty = sy;
+    for (int o = 1; o < 32; o <<= 1) {
+      const double ux = __shfl_down_sync(0xffffffffu, tx, o), uy = __shfl_down_sync(0xffffffffu, ty, o);
+      if (t + o < 32) {
+        tx += ux;
+        ty += uy;
+      }
+    }
+    const double hx = tx - sx, hy = ty - sy;   // sum over higher lanes
+    double px_ = 0.0, py_ = 0.0;
+    for (int e = 0; e < per; ++e) {
+      gx[e] += hx;
+      gy[e] += hy;
+      if (k0 + e < nz) {
+        px_ += gx[e];
+        py_ += gy[e];
+      }
+      gx[e] = px_;   // now the lane-local prefix of g
+      gy[e] = py_;
+    }
+    // exclusive prefix scan of the lane totals over lower lanes
+    double qx = px_, qy = py_;
+    for (int o = 1; o < 32; o <<= 1) {
+      const double ux = __shfl_up_sync(0xffffffffu, qx, o), uy = __shfl_up_sync(0xffffffffu, qy, o);
+      if (t >= o) {
+        qx += ux;
+        qy += uy;
+      }
+    }
+    const double lx = qx - px_, ly = qy - py_;
+    for (int e = 0; e < per; ++e) {
+      const int k = k0 + e;
+      if (k < nz) S[k * plane] = make_float2((float)(gx[e] + lx), (float)(gy[e] + ly));
+    }
+    if (t == 0) S[0] = make_float2(0.0f, 0.0f);
+    return;
   }
-  double2 x = dprev;
-  S[(nz - 1) * plane + col] = make_float2((float)x.x, (float)x.y);
+  const int py = blockIdx.x / per_row;
+  const int px = (blockIdx.x - py * per_row) * blockDim.x + t;
+  const long long col = (long long)py * n + px;
+  if (px >= n) return;
+  const int mx = bitrev(px, logn), my = bitrev(py, logn);
+  if (mx == 0 && my == 0) return;   // solved by the last block
+  float* cp = tsm;                                               // [nz][threads]
+  float2* dd = reinterpret_cast<float2*>(tsm + nz * blockDim.x);  // [nz][threads]: the column
+  // the whole column first (independent, coalesced loads), then the sweeps
+  {
+    int k = 0;
+    for (; k + 8 <= nz; k += 8) {   // eight loads in flight before their stores
+      float2 v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = S[(k + e) * plane + col];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) dd[(k + e) * blockDim.x + t] = v[e];
+    }
+    for (; k < nz; ++k) dd[k * blockDim.x + t] = S[k * plane + col];
+  }
+  // lambda(m) = 2 - 2 cos(2 pi m / n) per axis
+  const float lam = (2.0f - 2.0f * cospif(2.0f * (float)mx / (float)n)) +
+                    (2.0f - 2.0f * cospif(2.0f * (float)my / (float)n));
+  float cprev = 0.0f;
+  float2 dprev = make_float2(0.0f, 0.0f);
+  for (int k = 0; k < nz; ++k) {
+    const float2 f = dd[k * blockDim.x + t];
+    const float b = lam + ((k == 0 || k == nz - 1) ? 1.0f : 2.0f);   // Neumann ends
+    const float m = b - (k == 0 ? 0.0f : -cprev);                   // a = -1
+    const float r = 1.0f / m;
+    const float cn = k == nz - 1 ? 0.0f : -r;
+    dprev = make_float2((f.x * inv_scale + (k == 0 ? 0.0f : dprev.x)) * r,
+                        (f.y * inv_scale + (k == 0 ? 0.0f : dprev.y)) * r);
+    cp[k * blockDim.x + t] = cn;
+    dd[k * blockDim.x + t] = dprev;
+    cprev = cn;
+  }
+  float2 x = dprev;
+  S[(nz - 1) * plane + col] = x;
   for (int k = nz - 2; k >= 0; --k) {
-    const double cn = cp[k * blockDim.x + t];
-    const double2 dn = dp[k * blockDim.x + t];
-    x = make_double2(dn.x - cn * x.x, dn.y - cn * x.y);
-    S[k * plane + col] = make_float2((float)x.x, (float)x.y);
+    const float cn = cp[k * blockDim.x + t];
+    const float2 dn = dd[k * blockDim.x + t];
+    x = make_float2(dn.x - cn * x.x, dn.y - cn * x.y);
+    S[k * plane + col] = x;
   }
 }
 
@@ -175,7 +285,7 @@ bool spectral_pressure_supported(const LevelDev& L0) {
   const CompDev& c = L0.c[0];
   if (c.nx != c.ny || c.nx < 4 || c.nx > 128 || (c.nx & (c.nx - 1)) != 0 || c.nz < 2) return false;
   if (c.zkind != kAxisCellNeu) return false;
-  if ((size_t)c.nz * kThomasThreads * (sizeof(double) + 2 * sizeof(double)) > 200 * 1024) return false;
+  if ((size_t)c.nz * kThomasThreads * 3 * sizeof(float) > 200 * 1024 || c.nz > 257) return false;
   return true;
 }
 
@@ -192,8 +302,11 @@ cudaError_t spectral_pressure_solve(const LevelDev& L0, const float* r, float* d
   while ((1 << logn) < n) ++logn;
   float2* S = (float2*)spectrum;
   const size_t fsm = (size_t)(n * n + n / 2) * sizeof(float2);
-  const int tthreads = n < kThomasThreads ? n : kThomasThreads;
-  const size_t tsm = (size_t)nz * tthreads * 3 * sizeof(double);
+  // at least one warp per block (the (0, 0) block scans with a full warp)
+  const int tthreads = n < 32 ? 32 : (n < kThomasThreads ? n : kThomasThreads);
+  const int per_row = n / tthreads > 0 ? n / tthreads : 1;
+  // per thread: FP32 c' and the column (float2)
+  const size_t tsm = (size_t)nz * tthreads * 3 * sizeof(float);
   static std::atomic<int> ready[64];
   int dev = 0;
   cudaGetDevice(&dev);
@@ -205,8 +318,7 @@ cudaError_t spectral_pressure_solve(const LevelDev& L0, const float* r, float* d
   }
   prof::Scope ps(SELM_K_PROJECTION, st);
   k_spec_forward<<<nz, kSpecThreads, fsm, st>>>(r, S, n, logn);
-  const int per_row = n / tthreads;
-  k_spec_thomas<<<n * per_row, tthreads, tsm, st>>>(S, n, nz, c.s);
+  k_spec_thomas<<<n * per_row + 1, tthreads, tsm, st>>>(S, n, logn, nz, (float)(1.0 / c.s));
   k_spec_inverse<<<nz, kSpecThreads, fsm, st>>>(S, delta, n, logn);
   return cudaGetLastError();
 }

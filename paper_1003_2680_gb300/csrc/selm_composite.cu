@@ -755,8 +755,11 @@ __global__ void __launch_bounds__(kCBlock) k_comp_df_to_f64(CompGeo G, const flo
 // neighbours from registers, the next layer's row loaded before the current
 // one is computed.  On an interface layer a segment whose colour sites have
 // odd x belongs to the late pass and is left unchanged.
+#ifndef SELM_PATCH_MIN_BLOCKS
+#define SELM_PATCH_MIN_BLOCKS 2
+#endif
 template <typename T, bool NOISE>
-__global__ void __launch_bounds__(kCBlock) k_comp_patch_zm(CompGeo G, T* __restrict__ vp, const T* __restrict__ vb,
+__global__ void __launch_bounds__(kCBlock, sizeof(T) == 4 ? SELM_PATCH_MIN_BLOCKS : 1) k_comp_patch_zm(CompGeo G, T* __restrict__ vp, const T* __restrict__ vb,
                                                            const T* __restrict__ rp, int colour, int sweep, int kc,
                                                            Key key, const unsigned long long* __restrict__ cyc) {
   const int fx = G.fx, fy = G.fy, fz = G.fz, segs = fx >> 3;

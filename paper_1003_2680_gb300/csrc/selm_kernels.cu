@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <type_traits>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -629,8 +630,15 @@ struct ColumnPass {
 // computed (two rows of loads in flight).  Values read across threads are
 // always of the other colour, which no thread writes in the pass; the
 // vector loads also carry same-colour lanes, which are not used.
+// Blocks per SM the z-marching colour passes are compiled for (register
+// budget 65536 / (256 x this)): more resident warps keep more row loads in
+// flight.
+#ifndef SELM_ZM_MIN_BLOCKS
+#define SELM_ZM_MIN_BLOCKS 3
+#endif
+
 template <typename T, bool NOISE>
-__global__ void __launch_bounds__(kBlock) k_band7_rb_zm(LevelDev L, ColumnPass cp, T* __restrict__ v,
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? SELM_ZM_MIN_BLOCKS : 1) k_band7_rb_zm(LevelDev L, ColumnPass cp, T* __restrict__ v,
                                                        const T* __restrict__ b, int colour, int sweep, Key key,
                                                        const unsigned long long* __restrict__ cyc) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -822,7 +830,7 @@ __device__ __forceinline__ void fine_colour_zm_item(const LevelDev& L, const Col
 }
 
 template <typename T, bool NOISE>
-__global__ void __launch_bounds__(kBlock) k_fine_colour_zm(LevelDev L, ColumnPass cp, T* __restrict__ v,
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? SELM_ZM_MIN_BLOCKS : 1) k_fine_colour_zm(LevelDev L, ColumnPass cp, T* __restrict__ v,
                                                           const T* __restrict__ b, int colour, int sweep, Key key,
                                                           const unsigned long long* __restrict__ cyc) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1972,6 +1980,14 @@ __device__ __forceinline__ int comp_at(const LevelDev& L, long long q, long long
   return ci;
 }
 
+// Loads of the persistent launch.  Data written by other blocks in an earlier
+// phase are read after a grid barrier (coop_barrier: block barrier, release
+// add, acquire poll, block barrier) -- the release/acquire pair orders every
+// write of the phase before every read of the next one, as a grid-wide
+// synchronisation does, so plain (L1-cached) loads see the phase's data.
+constexpr bool kBatchL2 = false;
+using BatchLd = std::conditional_t<kBatchL2, LdCG, LdPlain>;
+
 template <typename T, bool NOISE>
 __device__ __forceinline__ void batch_item(const BatchSysDev& S, const BatchPhase& P, int mode, long long g,
                                            double* nacc) {
@@ -1983,20 +1999,20 @@ __device__ __forceinline__ void batch_item(const BatchSysDev& S, const BatchPhas
   switch (P.type) {
     case kPhOuterRes: {
       const double rr =
-          outer_residual4_item<T, true>(L, S.orp, S.z[mode], S.bz[mode], (T*)BL.b, (T*)BL.v, g);
+          outer_residual4_item<T, kBatchL2>(L, S.orp, S.z[mode], S.bz[mode], (T*)BL.b, (T*)BL.v, g);
       if (mode == 1) *nacc += rr;
       break;
     }
     case kPhSmooth: {
       const unsigned long long cy = NOISE ? *S.cyc[mode] : 0ull;
       if (l == 0)
-        fine_colour_zm_item<T, NOISE, true>(L, S.fcp, v, b, P.colour, P.sweep, S.key, cy, g);
+        fine_colour_zm_item<T, NOISE, kBatchL2>(L, S.fcp, v, b, P.colour, P.sweep, S.key, cy, g);
       else if (BL.v8 && (P.colour & 1) == 0)
-        coarse_colour_v8_item<T, NOISE, 0, true>(L, BL.cp[P.colour], BL.sp[P.colour], v, b, P.sweep, S.key, cy, g);
+        coarse_colour_v8_item<T, NOISE, 0, kBatchL2>(L, BL.cp[P.colour], BL.sp[P.colour], v, b, P.sweep, S.key, cy, g);
       else if (BL.v8)
-        coarse_colour_v8_item<T, NOISE, 1, true>(L, BL.cp[P.colour], BL.sp[P.colour], v, b, P.sweep, S.key, cy, g);
+        coarse_colour_v8_item<T, NOISE, 1, kBatchL2>(L, BL.cp[P.colour], BL.sp[P.colour], v, b, P.sweep, S.key, cy, g);
       else
-        coarse_site_at<T, NOISE, LdCG>(L, BL.cp[P.colour], v, b, P.sweep, S.key, cy, g);
+        coarse_site_at<T, NOISE, BatchLd>(L, BL.cp[P.colour], v, b, P.sweep, S.key, cy, g);
       break;
     }
     case kPhCoarse1: {
@@ -2012,7 +2028,7 @@ __device__ __forceinline__ void batch_item(const BatchSysDev& S, const BatchPhas
       const long long N = (long long)c.nx * c.ny * c.nz;
       double acc = 0.0;
       if (valid)
-        for (long long q = sub; q <= r; q += 8) acc += c.Linv[r * N + q] * (double)__ldcg(b + c.off + q);
+        for (long long q = sub; q <= r; q += 8) acc += c.Linv[r * N + q] * (double)ld1<T, kBatchL2>(b + c.off + q);
       acc += __shfl_xor_sync(0xffffffffu, acc, 4);
       acc += __shfl_xor_sync(0xffffffffu, acc, 2);
       acc += __shfl_xor_sync(0xffffffffu, acc, 1);
@@ -2037,7 +2053,7 @@ __device__ __forceinline__ void batch_item(const BatchSysDev& S, const BatchPhas
       const long long N = (long long)c.nx * c.ny * c.nz;
       double acc = 0.0;
       if (valid)
-        for (long long r = col + sub; r < N; r += 8) acc += c.Linv[r * N + col] * __ldcg(S.ywork + c.off + r);
+        for (long long r = col + sub; r < N; r += 8) acc += c.Linv[r * N + col] * ld1<double, kBatchL2>(S.ywork + c.off + r);
       acc += __shfl_xor_sync(0xffffffffu, acc, 4);
       acc += __shfl_xor_sync(0xffffffffu, acc, 2);
       acc += __shfl_xor_sync(0xffffffffu, acc, 1);
@@ -2046,7 +2062,7 @@ __device__ __forceinline__ void batch_item(const BatchSysDev& S, const BatchPhas
     }
     case kPhResid: {
       if (l == 0) {
-        fine_residual_zm_item<T, true>(L, S.fcp, v, b, (T*)BL.t, g);
+        fine_residual_zm_item<T, kBatchL2>(L, S.fcp, v, b, (T*)BL.t, g);
       } else if (BL.rcp.kc > 0) {
         int ci = 0;
         while (ci + 1 < L.ncomp && g >= BL.rcp.start[ci + 1]) ++ci;
@@ -2057,12 +2073,12 @@ __device__ __forceinline__ void batch_item(const BatchSysDev& S, const BatchPhas
         const int chunk = (int)(item / ((long long)c.ny * segs));
         const int j = (int)(col / segs), seg = (int)(col - (long long)j * segs);
         const int k0 = chunk * BL.rcp.kc, k1 = min(k0 + BL.rcp.kc, c.nz);
-        galerkin_residual_seg<T, 4, LdCG>(c, v + c.off, b + c.off, (T*)BL.t + c.off, j, seg << 2, k0, k1);
+        galerkin_residual_seg<T, 4, BatchLd>(c, v + c.off, b + c.off, (T*)BL.t + c.off, j, seg << 2, k0, k1);
       } else {
         int ci, i, j, k;
         site_of(L, g, &ci, &i, &j, &k);
         const CompDev& c = L.c[ci];
-        ((T*)BL.t)[g] = __ldcg(b + g) - sep_apply<T, LdCG, true>(c, v + c.off, i, j, k);
+        ((T*)BL.t)[g] = ld1<T, kBatchL2>(b + g) - sep_apply<T, BatchLd, true>(c, v + c.off, i, j, k);
       }
       break;
     }
@@ -2071,9 +2087,9 @@ __device__ __forceinline__ void batch_item(const BatchSysDev& S, const BatchPhas
       const long long nres = BL.vec_down ? (long long)BC.rp.rstart[BC.L.ncomp] * (BC.L.c[0].nx >> 2) : BC.L.size;
       if (g < nres) {
         if (BL.vec_down)
-          restrict_seg4<T, true>(L, BC.L, BC.rp, (const T*)BL.t, (T*)BC.b, g);
+          restrict_seg4<T, kBatchL2>(L, BC.L, BC.rp, (const T*)BL.t, (T*)BC.b, g);
         else
-          restrict_at<T, LdCG>(L, BC.L, (const T*)BL.t, (T*)BC.b, g);
+          restrict_at<T, BatchLd>(L, BC.L, (const T*)BL.t, (T*)BC.b, g);
       } else {
         ((T*)BC.v)[g - nres] = (T)0;
       }
@@ -2082,9 +2098,9 @@ __device__ __forceinline__ void batch_item(const BatchSysDev& S, const BatchPhas
     case kPhProlong: {
       const BatchLevelDev& BC = S.lev[l + 1];
       if (BL.vec_up)
-        prolong_seg8<T, false, true>(L, BC.L, BL.rp, v, (const T*)BC.v, g);
+        prolong_seg8<T, false, kBatchL2>(L, BC.L, BL.rp, v, (const T*)BC.v, g);
       else
-        v[g] = __ldcg(v + g) + prolong_val<T, LdCG>(L, BC.L, (const T*)BC.v, g);
+        v[g] = ld1<T, kBatchL2>(v + g) + prolong_val<T, BatchLd>(L, BC.L, (const T*)BC.v, g);
       break;
     }
     case kPhOuterUpd: {
@@ -2092,16 +2108,17 @@ __device__ __forceinline__ void batch_item(const BatchSysDev& S, const BatchPhas
       double2* z2 = reinterpret_cast<double2*>(z + 4 * g);
       double2 a = z2[0], d = z2[1];
       if constexpr (sizeof(T) == 4) {
-        const float4 q = __ldcg(reinterpret_cast<const float4*>(v + 4 * g));
+        const float4 q = kBatchL2 ? __ldcg(reinterpret_cast<const float4*>(v + 4 * g))
+                                  : *reinterpret_cast<const float4*>(v + 4 * g);
         a.x += (double)q.x;
         a.y += (double)q.y;
         d.x += (double)q.z;
         d.y += (double)q.w;
       } else {
-        a.x += (double)__ldcg(v + 4 * g);
-        a.y += (double)__ldcg(v + 4 * g + 1);
-        d.x += (double)__ldcg(v + 4 * g + 2);
-        d.y += (double)__ldcg(v + 4 * g + 3);
+        a.x += (double)ld1<T, kBatchL2>(v + 4 * g);
+        a.y += (double)ld1<T, kBatchL2>(v + 4 * g + 1);
+        d.x += (double)ld1<T, kBatchL2>(v + 4 * g + 2);
+        d.y += (double)ld1<T, kBatchL2>(v + 4 * g + 3);
       }
       z2[0] = a;
       z2[1] = d;

@@ -351,15 +351,27 @@ class CompositeMAC:
 
 # ---- stochastic FAC on the staggered composite grid (Algorithms 1-3) ----
 
+# An off-diagonal entry below this fraction of its row's diagonal is the
+# rounding residue of an exact cancellation in a Galerkin product (the exact
+# entry is 0), not a coupling of the graph.
+GRAPH_RTOL = 1e-12
+
+
 def _greedy_colours(A):
     """Colour classes of the graph of A (a_ij != 0, i != j), each an independent
-    set, by first fit in index order: a valid Gibbs visiting order."""
+    set, by first fit in index order: a valid Gibbs visiting order.  Entries
+    with |a_ij| <= GRAPH_RTOL |a_ii| are exact zeros up to rounding and are
+    not edges, so the classes do not depend on the summation order of the
+    Galerkin products."""
     A = sp.csr_matrix(A)
     if A.shape[0] == 0:
         return []
+    diag = np.abs(A.diagonal())
     colour = -np.ones(A.shape[0], dtype=int)
     for i in range(A.shape[0]):
-        used = {colour[j] for j in A.indices[A.indptr[i]:A.indptr[i + 1]] if j != i and colour[j] >= 0}
+        lo, hi = A.indptr[i], A.indptr[i + 1]
+        used = {colour[j] for j, a in zip(A.indices[lo:hi], A.data[lo:hi])
+                if j != i and colour[j] >= 0 and abs(a) > GRAPH_RTOL * diag[i]}
         c = 0
         while c in used:
             c += 1

@@ -14,10 +14,14 @@ header):
 
 * key   = (lo32(seed) ^ hi32(instance),  hi32(seed) ^ lo32(instance))
 * ctr0  = group index = (rank of the site within its colour class) >> 2
-* ctr1  = level | comp << 4 | colour << 8 | sweep << 12 | kind << 20
+* ctr1  = level | comp << 4 | (colour & 15) << 8 | sweep << 12 | kind << 20
+          | (colour >> 4) << 24
           (kind 0 = smoother sweep, kind 1 = exact coarsest-level sample,
           kind 2 = sweep of a refined patch, whose sites are addressed by
-          a counter index of their own instead of a class rank)
+          a counter index of their own instead of a class rank; colours
+          beyond 15, which only the general sparse levels of the staggered
+          composite grid have, continue in the top byte, so every stream of
+          a colour below 16 keeps its counter)
 * ctr2, ctr3 = lo32(cycle), hi32(cycle)   (cycle = chain step counter)
 
 One Philox call yields four 32-bit words w0..w3 -> uniforms
@@ -78,9 +82,10 @@ def make_key(seed, instance=0):
 
 
 def pack_ctr1(level, comp, colour, sweep, kind):
-    assert 0 <= level < 16 and 0 <= comp < 16 and 0 <= colour < 16
+    assert 0 <= level < 16 and 0 <= comp < 16 and 0 <= colour < 4096
     assert 0 <= sweep < 256 and 0 <= kind < 16
-    return level | (comp << 4) | (colour << 8) | (sweep << 12) | (kind << 20)
+    return (level | (comp << 4) | ((colour & 15) << 8) | (sweep << 12) | (kind << 20)
+            | ((colour >> 4) << 24))
 
 
 def words_to_normals(words):

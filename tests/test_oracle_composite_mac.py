@@ -321,6 +321,41 @@ def test_composite_mac_solve_matches_direct(dim, n, K):
     assert np.linalg.norm(z - x) / np.linalg.norm(x) < 1e-9
 
 
+@pytest.mark.parametrize("dim,n,K", [(2, 16, 5), (3, 8, 3), (3, 16, 4)])
+def test_colour_classes_are_independent_sets(dim, n, K):
+    # Every class of every level is an independent set of the operator's graph
+    # (no coupling between two sites of one class), and the graph threshold
+    # separates couplings from rounding residues by many orders of magnitude,
+    # so the classes cannot depend on the summation order of the products.
+    from oracle.composite_mac import GRAPH_RTOL
+    F = CompositeMACFAC(CompositeMAC(n, K, dim))
+    levels = [(A, cl) for A, cl in zip(F.ops, F.colours)] + [(F.A, F.patch_colours)]
+    for A, classes in levels:
+        A = A.tocsr()
+        d = np.abs(A.diagonal())
+        rel = np.abs(A.multiply(sp.csr_matrix(1.0 / d[:, None]))).tocsr()
+        rel.setdiag(0.0)
+        vals = rel.data[rel.data > 0]
+        assert not np.any((vals > 1e3 * GRAPH_RTOL) & (vals < 1e-6))
+        assert sorted(np.concatenate(classes).tolist()) == sorted(set(np.concatenate(classes).tolist()))
+        for idx in classes:
+            blk = rel[idx][:, idx]
+            assert blk.max() <= GRAPH_RTOL if blk.nnz else True
+
+
+def test_more_than_sixteen_colours_keep_distinct_streams():
+    # 3-D Galerkin levels of the composite grid need more than 16 classes;
+    # colours 16.. continue in the counter's top byte, colours below 16 keep
+    # the counters of the uniform levels.
+    from oracle import philox
+    F = CompositeMACFAC(CompositeMAC(8, 3, 3))
+    assert len(F.colours[0]) > 16
+    c1 = {philox.pack_ctr1(1, 0, c, 0, 0) for c in range(40)}
+    assert len(c1) == 40
+    assert philox.pack_ctr1(2, 1, 3, 1, 0) == 2 | (1 << 4) | (3 << 8) | (1 << 12)
+    assert philox.pack_ctr1(1, 0, 17, 2, 0) == 1 | (1 << 8) | (2 << 12) | (1 << 24)
+
+
 # ---- particles on the composite MAC grid (reading R24) ----
 
 from oracle import selm as oselm  # noqa: E402

@@ -533,7 +533,7 @@ class CompositeSELM:
     spread forces; M is symmetric and Cov(g) = 2 kT M.
     """
 
-    def __init__(self, n, K, dim, mu=1.0, kT=1.0, project=False, kernel="fine"):
+    def __init__(self, n, K, dim, mu=1.0, kT=1.0, project=False, kernel="fine", seed=0, instance=0, tol=1e-10):
         assert kernel in ("cover", "fine")
         self.kernel = kernel
         self.n, self.K, self.dim, self.kT, self.project_on = n, K, dim, kT, project
@@ -543,6 +543,9 @@ class CompositeSELM:
         self.fine_sys = grid.velocity_system(2 * n, dim, mu=mu, levels=1)
         self.R = self._restriction()
         self.E = self._extension()
+        self.seed, self.instance, self.tol = seed, instance, tol
+        self.xi = np.zeros(self.g.n_faces)     # persistent chain state
+        self.cycle = 0                          # chain step counter (Philox counter words 2-3)
 
     @staticmethod
     def _offsets(system):
@@ -659,3 +662,35 @@ class CompositeSELM:
         """K = sqrt(2 kT) Gamma P~ as a dense matrix (g = K xi); row r is P~^T of Gamma's row r."""
         G = self.interpolation(X).toarray()
         return np.sqrt(2.0 * self.kT) * np.array([self._PT(r) for r in G])
+
+    # -- dynamics (Algorithm 4 on the composite grid) -----------------------
+    def chain_cycles(self, ncycles):
+        """Advance xi by ncycles stochastic FAC cycles with b = 0 (sigma = 1)."""
+        from .philox import PhiloxNoise
+        zero = np.zeros(self.g.n_faces)
+        for _ in range(ncycles):
+            self.fac.fac_cycle(self.xi, zero, PhiloxNoise(self.seed, self.instance, self.cycle), 1.0)
+            self.cycle += 1
+        return self.xi
+
+    @staticmethod
+    def wrap_reflect(X):
+        X = X.copy()
+        X[:, :-1] = np.mod(X[:, :-1], 1.0)
+        z = X[:, -1]
+        z = np.where(z < 0.0, -z, z)
+        z = np.where(z > 1.0, 2.0 - z, z)
+        X[:, -1] = z
+        return X
+
+    def em_step(self, X, F, dt, ncycles):
+        """One Euler-Maruyama step (Algorithm 4): u = A^-1 P~^T Gamma^T F by FAC
+        cycles to tol, the chain advanced by ncycles, then
+        X <- X + Gamma P~ (dt u + sqrt(2 kT dt) xi), wrapped and reflected."""
+        Gam = self.interpolation(X)
+        rhs = self._PT(Gam.T @ F.ravel())
+        u, cycles, rel = self.fac.solve(rhs, tol=self.tol)
+        self.chain_cycles(ncycles)
+        w = dt * u + np.sqrt(2.0 * self.kT * dt) * self.xi
+        V = (Gam @ self._P(w)).reshape(X.shape)
+        return self.wrap_reflect(X + V), cycles

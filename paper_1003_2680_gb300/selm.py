@@ -67,6 +67,17 @@ class SelmCompDesc(ctypes.Structure):
     ]
 
 
+class SelmMacDesc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("n", ctypes.c_int), ("K", ctypes.c_int), ("levels", ctypes.c_int),
+        ("mu", ctypes.c_double), ("kT", ctypes.c_double),
+        ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("nu_patch", ctypes.c_int),
+        ("precision", ctypes.c_int), ("projection", ctypes.c_int),
+        ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("proj_tol", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("instance", ctypes.c_uint64),
+    ]
+
+
 class SelmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
@@ -151,6 +162,33 @@ _SIGS = {
     "selm_comp_chain": (_I, [_P, ctypes.POINTER(_U64)]),
     "selm_comp_set_cycle": (_I, [_P, _U64]),
     "selm_comp_stats": (_I, [_P, ctypes.POINTER(_LL)]),
+    "selm_mac_create": (_I, [ctypes.POINTER(SelmMacDesc), _P, ctypes.POINTER(_P)]),
+    "selm_mac_destroy": (_I, [_P]),
+    "selm_mac_last_error": (ctypes.c_char_p, [_P]),
+    "selm_mac_faces": (_LL, [_P]),
+    "selm_mac_cells": (_LL, [_P]),
+    "selm_mac_levels": (_I, [_P]),
+    "selm_mac_colours": (_I, [_P, _I]),
+    "selm_mac_inner_bytes": (_I, [_P]),
+    "selm_mac_apply": (_I, [_P, _P, _P, _P]),
+    "selm_mac_divergence": (_I, [_P, _P, _P, _P]),
+    "selm_mac_gradient": (_I, [_P, _P, _P, _P]),
+    "selm_mac_project": (_I, [_P, _P, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+    "selm_mac_fac_cycle": (_I, [_P, _P, _P, _D, _U64, _P]),
+    "selm_mac_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+    "selm_mac_sample": (_I, [_P, _I, _P, _P]),
+    "selm_mac_chain": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_U64)]),
+    "selm_mac_set_chain": (_I, [_P, _U64, _P]),
+    "selm_mac_interp": (_I, [_P, _I, _P, _P, _P, _P]),
+    "selm_mac_spread": (_I, [_P, _I, _P, _P, _P, _P]),
+    "selm_mac_mobility": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(_I), _P]),
+    "selm_mac_thermal": (_I, [_P, _I, _P, _I, _P, _P]),
+    "selm_mac_step": (_I, [_P, _I, _P, _P, _D, _I, _I, _P]),
+    "selm_mac_total_cycles": (_LL, [_P]),
+    "selm_mac_host_matrix": (_I, [ctypes.POINTER(SelmMacDesc), _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                  ctypes.POINTER(_LL), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "selm_mac_host_colours": (_I, [ctypes.POINTER(SelmMacDesc), _I, ctypes.POINTER(_I), ctypes.POINTER(_P)]),
+    "selm_mac_host_free": (None, [_P]),
     "selm_kernel_launches": (ctypes.c_longlong, []),
     "selm_profile_enable": (_I, [_I]),
     "selm_profile_reset": (_I, []),
@@ -650,3 +688,158 @@ class SelmMG:
 
     def inner_dtype(self):
         return torch.float32 if selm_mg_inner_bytes(self.h) == 4 else torch.float64
+
+
+# -- staggered composite grid (selm_mac.h) --------------------------------------
+SELM_MAC_MAT_A, SELM_MAC_MAT_D, SELM_MAC_MAT_G, SELM_MAC_MAT_S = 0, 1, 2, 3
+SELM_MAC_MAT_P, SELM_MAC_MAT_E, SELM_MAC_MAT_OPS, SELM_MAC_MAT_PL = 4, 5, 6, 7
+
+
+def _check_mac(h, status):
+    if status != SELM_OK:
+        msg = lib().selm_mac_last_error(h).decode() if h else ""
+        raise SelmError(status, msg)
+
+
+def make_mac_desc(dim, n, K, mu=1.0, kT=0.0, levels=0, nu_pre=2, nu_post=2, nu_patch=2, precision=SELM_FP64,
+                  projection=SELM_PROJ_NONE, tol=0.0, max_cycles=0, proj_tol=0.0, seed=0, instance=0):
+    d = SelmMacDesc()
+    d.dim, d.n, d.K, d.levels, d.mu, d.kT = dim, n, K, levels, mu, kT
+    d.nu_pre, d.nu_post, d.nu_patch, d.precision, d.projection = nu_pre, nu_post, nu_patch, precision, projection
+    d.tol, d.max_cycles, d.proj_tol, d.seed, d.instance = tol, max_cycles, proj_tol, seed, instance
+    return d
+
+
+def selm_mac_create(desc, stream=None):
+    h = _P()
+    st = lib().selm_mac_create(ctypes.byref(desc), _stream(stream), ctypes.byref(h))
+    if st != SELM_OK:
+        raise SelmError(st, "selm_mac_create failed (see stderr)")
+    return h.value
+
+
+def selm_mac_destroy(h):
+    _check_mac(None, lib().selm_mac_destroy(h))
+
+
+def selm_mac_faces(h):
+    return int(lib().selm_mac_faces(h))
+
+
+def selm_mac_cells(h):
+    return int(lib().selm_mac_cells(h))
+
+
+def selm_mac_levels(h):
+    return int(lib().selm_mac_levels(h))
+
+
+def selm_mac_colours(h, level):
+    return int(lib().selm_mac_colours(h, level))
+
+
+def selm_mac_inner_bytes(h):
+    return int(lib().selm_mac_inner_bytes(h))
+
+
+def selm_mac_apply(h, u, Au, stream=None):
+    _check_mac(h, lib().selm_mac_apply(h, _ptr(u), _ptr(Au), _stream(stream)))
+
+
+def selm_mac_divergence(h, u, div, stream=None):
+    _check_mac(h, lib().selm_mac_divergence(h, _ptr(u), _ptr(div), _stream(stream)))
+
+
+def selm_mac_gradient(h, p, grad, stream=None):
+    _check_mac(h, lib().selm_mac_gradient(h, _ptr(p), _ptr(grad), _stream(stream)))
+
+
+def selm_mac_project(h, u, out, adjoint=False, stream=None):
+    it, res = _I(0), _D(0.0)
+    _check_mac(h, lib().selm_mac_project(h, _ptr(u), _ptr(out), int(adjoint), ctypes.byref(it), ctypes.byref(res),
+                                         _stream(stream)))
+    return it.value, res.value
+
+
+def selm_mac_fac_cycle(h, z, b, sigma, cycle, stream=None):
+    _check_mac(h, lib().selm_mac_fac_cycle(h, _ptr(z), _ptr(b), float(sigma), cycle, _stream(stream)))
+
+
+def selm_mac_solve(h, z, b, tol=0.0, max_cycles=0, stream=None):
+    cyc, rel = _I(0), _D(0.0)
+    _check_mac(h, lib().selm_mac_solve(h, _ptr(z), _ptr(b), tol, max_cycles, ctypes.byref(cyc), ctypes.byref(rel),
+                                       _stream(stream)))
+    return cyc.value, rel.value
+
+
+def selm_mac_sample(h, ncycles, xi_out=None, stream=None):
+    _check_mac(h, lib().selm_mac_sample(h, ncycles, _ptr(xi_out), _stream(stream)))
+
+
+def selm_mac_chain(h):
+    p, cy = _P(), _U64(0)
+    _check_mac(h, lib().selm_mac_chain(h, ctypes.byref(p), ctypes.byref(cy)))
+    return p.value, cy.value
+
+
+def selm_mac_set_chain(h, cycle, stream=None):
+    _check_mac(h, lib().selm_mac_set_chain(h, cycle, _stream(stream)))
+
+
+def selm_mac_interp(h, X, u, U, stream=None):
+    _check_mac(h, lib().selm_mac_interp(h, X.shape[0], _ptr(X), _ptr(u), _ptr(U), _stream(stream)))
+
+
+def selm_mac_spread(h, X, F, f, stream=None):
+    _check_mac(h, lib().selm_mac_spread(h, X.shape[0], _ptr(X), _ptr(F), _ptr(f), _stream(stream)))
+
+
+def selm_mac_mobility(h, X, F, U, stream=None):
+    cyc = _I(0)
+    _check_mac(h, lib().selm_mac_mobility(h, X.shape[0], _ptr(X), _ptr(F), _ptr(U), ctypes.byref(cyc),
+                                          _stream(stream)))
+    return cyc.value
+
+
+def selm_mac_thermal(h, X, ncycles, g, stream=None):
+    _check_mac(h, lib().selm_mac_thermal(h, X.shape[0], _ptr(X), ncycles, _ptr(g), _stream(stream)))
+
+
+def selm_mac_step(h, X, F, dt, nsteps, ncycles, stream=None):
+    _check_mac(h, lib().selm_mac_step(h, X.shape[0], _ptr(X), _ptr(F), dt, nsteps, ncycles, _stream(stream)))
+
+
+def selm_mac_total_cycles(h):
+    return int(lib().selm_mac_total_cycles(h))
+
+
+def selm_mac_host_matrix(desc, which, level=0):
+    """(nr, nc, indptr, indices, data) of one sparse matrix of the host plan."""
+    import numpy as np
+    nr, nc, nnz = _I(0), _I(0), _LL(0)
+    ptr, col, val = _P(), _P(), _P()
+    st = lib().selm_mac_host_matrix(ctypes.byref(desc), which, level, ctypes.byref(nr), ctypes.byref(nc),
+                                    ctypes.byref(nnz), ctypes.byref(ptr), ctypes.byref(col), ctypes.byref(val))
+    if st != SELM_OK:
+        raise SelmError(st, "selm_mac_host_matrix failed")
+    try:
+        indptr = np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(_LL)), (nr.value + 1,)).copy()
+        indices = np.ctypeslib.as_array(ctypes.cast(col, ctypes.POINTER(_I)), (max(1, nnz.value),))[:nnz.value].copy()
+        data = np.ctypeslib.as_array(ctypes.cast(val, ctypes.POINTER(_D)), (max(1, nnz.value),))[:nnz.value].copy()
+    finally:
+        for q in (ptr, col, val):
+            lib().selm_mac_host_free(q)
+    return nr.value, nc.value, indptr, indices, data
+
+
+def selm_mac_host_colours(desc, level):
+    import numpy as np
+    n, col = _I(0), _P()
+    st = lib().selm_mac_host_colours(ctypes.byref(desc), level, ctypes.byref(n), ctypes.byref(col))
+    if st != SELM_OK:
+        raise SelmError(st, "selm_mac_host_colours failed")
+    try:
+        out = np.ctypeslib.as_array(ctypes.cast(col, ctypes.POINTER(_I)), (max(1, n.value),))[:n.value].copy()
+    finally:
+        lib().selm_mac_host_free(col)
+    return out

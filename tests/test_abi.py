@@ -1,21 +1,25 @@
 """CPU checks of the C ABI: the library builds, loads and exports every
-function declared in include/selm_mg.h; host-only entry points validate
-descriptors.  No compute call is made (no GPU here)."""
+function declared in the headers under include/; host-only entry points
+validate descriptors.  No compute call is made (no GPU here)."""
 
 import ctypes
+import glob
 import os
 import re
 
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "selm_mg.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def _declared():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(selm_\w+)\s*\(", text)))
+    names = set()
+    for path in HEADERS:
+        text = open(path).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(selm_\w+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")

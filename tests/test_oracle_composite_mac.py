@@ -431,3 +431,28 @@ def test_composite_selm_uniform_limits_3d(K, project):
     M = CompositeSELM(4, K, 3, mu=0.9, project=project, kernel="cover").mobility_matrix(X)
     Mu = oselm.Model(4 if K == 0 else 8, 3, mu=0.9, project=project, tol=1e-13).mobility_matrix(X)
     assert np.abs(M - Mu).max() < 1e-10 * np.abs(Mu).max()
+
+
+@pytest.mark.parametrize("project", [False, True])
+def test_composite_em_step_uniform_limit(project):
+    # No row refined and the covering level's kernel: one deterministic
+    # Euler-Maruyama step (kT = 0) moves the particles as the uniform grid's
+    # step does (Algorithm 4 on the base grid); both solves stop at 1e-12.
+    n = 8
+    X = PARTICLES_2D.copy()
+    F = np.array([[1.0, -0.4], [0.2, 0.7], [-0.5, 0.3]])
+    cs = CompositeSELM(n, 0, 2, mu=0.9, kT=0.0, project=project, kernel="cover", tol=1e-12)
+    Xc, _ = cs.em_step(X, F, 0.05, 2)
+    m = oselm.Model(n, 2, mu=0.9, kT=0.0, project=project, tol=1e-12)
+    Xu, _ = m.em_step(X, F, 0.05, 2)
+    assert np.abs(Xc - Xu).max() < 1e-9 * np.abs(Xu - X).max()
+
+
+def test_composite_em_step_deterministic_part_is_the_mobility():
+    # kT = 0: the step is X + dt M F (before wrapping), M from unit-force solves.
+    cs = CompositeSELM(8, 3, 2, mu=0.8, kT=0.0, project=True, tol=1e-12)
+    X = np.array([[0.3, 0.33], [0.6, 0.41], [0.45, 0.7]])
+    F = np.array([[0.5, -1.0], [0.1, 0.4], [-0.3, 0.2]])
+    Xn, _ = cs.em_step(X, F, 0.01, 1)
+    M = cs.mobility_matrix(X, tol=1e-12)
+    assert np.abs((Xn - X).ravel() - 0.01 * M @ F.ravel()).max() < 1e-9 * np.abs(Xn - X).max()

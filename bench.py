@@ -65,11 +65,13 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="headline workload only: no covariance, composite or 64^2 sub-records")
-    p.add_argument("--workload", default="channel128", choices=["channel128", "batched", "served", "composite", "decorrelation"],
+    p.add_argument("--workload", default="channel128", choices=["channel128", "batched", "served", "composite", "decorrelation", "mac"],
                    help="channel128: the headline line; batched: 64 uneven systems, batched vs plain; "
                         "served: Poisson request stream, served vs plain per-request")
     p.add_argument("--comp-n", type=int, default=256, help="composite workload: base cells per axis")
     p.add_argument("--comp-k", type=int, default=32, help="composite workload: refined base rows")
+    p.add_argument("--mac-n", type=int, default=64, help="staggered composite workload: base cells per axis")
+    p.add_argument("--mac-k", type=int, default=8, help="staggered composite workload: refined base rows")
     p.add_argument("--systems", type=int, default=64)
     p.add_argument("--requests", type=int, default=5000)
     p.add_argument("--rate", type=float, default=200.0)
@@ -822,6 +824,7 @@ def composite_measure(S, n, K, steps, warmup, with_cpu, cov_samples=100):
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     launches0 = S.selm_kernel_launches()
+    print(f"[bench] library kernel launches before the timed region: {launches0}", file=sys.stderr)
     with ClockSampler(torch.cuda.current_device()) as clk:
         for k in range(steps):
             flush.fill_(float(k))
@@ -961,6 +964,112 @@ def composite_measure(S, n, K, steps, warmup, with_cpu, cov_samples=100):
     return line
 
 
+def mac_measure(S, n, K, steps, warmup, particles=1000):
+    """The staggered composite grid with the projection (selm_mac.h): the
+    {n}^3 MAC channel with its bottom K rows refined by 2, FP32 inner cycles
+    with FP64 residual and update.  Timed: thermal samples of the chain (2
+    stochastic FAC cycles each, Algorithms 1-2 on the composite velocity
+    operator) and Euler-Maruyama steps of `particles` particles (Algorithm 4:
+    spread, P~^T, FAC solve to 1e-10, 2 chain cycles, P~, interpolation)."""
+    import numpy as np
+    import torch
+    import selm_inputs
+    cycles_per_sample = SAMPLE_CYCLES
+    t0 = time.perf_counter()
+    h = S.selm_mac_create(S.make_mac_desc(3, n, K, kT=1.0, precision=S.SELM_FP32_REFINE64,
+                                          projection=S.SELM_PROJ_MAC, seed=0, instance=0))
+    setup_s = time.perf_counter() - t0
+    nf, ncells = S.selm_mac_faces(h), S.selm_mac_cells(h)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    for _ in range(warmup):
+        S.selm_mac_sample(h, cycles_per_sample)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    launches0 = S.selm_kernel_launches()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record()
+            S.selm_mac_sample(h, cycles_per_sample)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+    launches = S.selm_kernel_launches() - launches0
+    t_total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    value = ncells * cycles_per_sample * steps / t_total
+    # per-class device time of the chain cycles
+    S.selm_profile_reset()
+    S.selm_profile_enable(True)
+    for _ in range(2):
+        S.selm_mac_sample(h, cycles_per_sample)
+    torch.cuda.synchronize()
+    S.selm_profile_enable(False)
+    per_class = {}
+    for ci, name in enumerate(S.KERNEL_CLASSES):
+        ms, cnt = S.selm_profile_read(ci)
+        if cnt:
+            per_class[name] = {"ms": ms, "launches": cnt}
+    S.selm_profile_reset()
+    tot_ms = sum(v["ms"] for v in per_class.values()) or 1.0
+    # Euler-Maruyama steps with particles (projection on)
+    X0 = selm_inputs.particles(particles, 3, 2 * n, seed=0)
+    F0 = selm_inputs.forces(particles, 3, seed=0)
+    X = torch.tensor(X0, device="cuda")
+    F = torch.tensor(F0, device="cuda")
+    S.selm_mac_step(h, X, F, 1e-3, 1, cycles_per_sample)
+    torch.cuda.synchronize()
+    c0 = S.selm_mac_total_cycles(h)
+    em_steps = max(2, steps // 4)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    S.selm_mac_step(h, X, F, 1e-3, em_steps, cycles_per_sample)
+    b.record()
+    torch.cuda.synchronize()
+    em_ms = a.elapsed_time(b) / em_steps
+    em_cycles = (S.selm_mac_total_cycles(h) - c0) / em_steps
+    u = torch.randn(nf, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(u)
+    a.record()
+    it, res = S.selm_mac_project(h, u, out)
+    b.record()
+    torch.cuda.synchronize()
+    proj_ms = a.elapsed_time(b)
+    peak, peak_kind = measured_peaks()
+    whole = MODEL_CYCLE_B * nf * cycles_per_sample
+    S.selm_mac_destroy(h)
+    return {
+        "value": value, "unit": "cells/s", "ms_per_step": 1e3 * t_total / steps, "steps": steps, "warmup": warmup,
+        "dtype": "f32+f64",
+        "config": {"workload": f"staggered composite MAC grid: {n}^3 channel (periodic x-y, walls z) with its "
+                               f"bottom {K} rows refined by 2, thermal samples of {cycles_per_sample} stochastic "
+                               f"FAC cycles (explicit sparse operators, first-fit colour classes), FP32 inner "
+                               f"cycles, FP64 residual, update and coarsest draw",
+                   "base_n": n, "patch_rows": K, "cells": ncells, "face_unknowns": nf,
+                   "l2": "flushed between samples (256 MB write, outside the timed events)",
+                   "unit_of_work": "cell-cycle = one composite cell (all face unknowns it owns) through one FAC cycle",
+                   "host_setup_s": setup_s},
+        "kernel_time_share": {k: round(v["ms"] / tot_ms, 4) for k, v in per_class.items()},
+        "avg_launch_us": {k: 1e3 * v["ms"] / v["launches"] for k, v in per_class.items()},
+        "whole_step_model": {"bytes_per_sample": whole, "frac": whole / (t_total / steps) / 1e9 / peak,
+                             "peak": peak, "peak_source": peak_kind,
+                             "note": "114 B per unknown-cycle x face unknowns x cycles per sample / ms per sample"},
+        "em_step": {"particles": particles, "ms_per_step": em_ms, "fac_cycles_per_step": em_cycles,
+                    "projections_per_step": 3},
+        "projection": {"ms": proj_ms, "cg_iterations": it, "relative_residual": res},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+
+
+def run_mac(args):
+    from paper_1003_2680_gb300 import _build
+    _build.build()
+    from paper_1003_2680_gb300 import selm as S
+    line = mac_measure(S, args.mac_n, args.mac_k, args.steps, args.warmup)
+    line.update({"metric": METRIC, "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                 "data": "synthetic", "cpu_baseline": None})
+    print(json.dumps(line), flush=True)
+
+
 def run_composite(args):
     """Composite grid: 256^3 base channel with its bottom 32 rows refined by 2
     (patch 512 x 512 x 64), three components, thermal samples of the chain
@@ -1027,6 +1136,8 @@ def main():
     if args.workload == "served":
         run_served(args)
         return
+    if args.workload == "mac":
+        return run_mac(args)
     if args.workload == "composite":
         run_composite(args)
         return

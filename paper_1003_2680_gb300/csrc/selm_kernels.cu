@@ -340,6 +340,191 @@ __global__ void __launch_bounds__(kBlock) k_outer_residual_v4(LevelDev L, RowPas
   }
 }
 
+// ---- the FP64 outer residual without the FP64 pipe ---------------------------
+// GB300 issues FP64 arithmetic and conversions at about two per SM clock, so
+// the nine FP64 operations per unknown of the plain residual bound it at
+// several times its memory time.  With an FP32 output the residual is formed
+// instead in exact integer arithmetic: the level-0 stencil's coefficients are
+// integers times s (A z = s (dg z_c - sum of the neighbours)), so with every
+// z of a thread's window written as a fixed-point integer Z = m 2^(e - emax)
+// 2^5 relative to the window's largest exponent emax (|Z| < 2^58, the bits
+// dropped from smaller values lie below 2^-58 of the window's largest value,
+// far under FP64's own rounding of the sum), S = dg Z_c - sum Z_nb is exact in
+// 64-bit integers, is rounded once to FP64 by integer operations, and
+// r = b - s S 2^(emax - 1080) is one FP64 FMA (its square for the norm a
+// second); the FP32 rounding of r is done by integer operations too.  The result is the exact residual up to two
+// roundings (the plain form accumulates nine), so it satisfies the FP64
+// residual's accuracy.  Windows outside the guarded exponent range (zero,
+// tiny, huge, non-finite values) take the plain FP64 arithmetic.
+
+__device__ __forceinline__ int fx_exp(long long bits) { return (int)((unsigned long long)bits >> 52) & 0x7ff; }
+
+// z (as bits) -> Z = m 32 2^-(emax - e), m the signed 53-bit significand.
+__device__ __forceinline__ long long fx_align(long long bits, int emax) {
+  const int ex = fx_exp(bits);
+  long long m = (bits & 0x000FFFFFFFFFFFFFll) | (ex ? 0x0010000000000000ll : 0ll);
+  if (bits < 0) m = -m;
+  const int d = emax - (ex ? ex : 1);
+  return d >= 63 ? (m < 0 ? -1ll : 0ll) : ((m * 32) >> d);
+}
+
+// S 2^e2 rounded to nearest even as FP64 (S != 0 and the result normal,
+// which the caller's exponent guard ensures).
+__device__ __forceinline__ double fx_to_double(long long S, int e2) {
+  const unsigned long long sign = S < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long a = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+  const int lz = __clzll((long long)a);
+  a <<= lz;
+  unsigned long long mant = a >> 11;
+  const unsigned long long rem = a & 0x7ffull;
+  int E = 63 - lz + e2;
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
+    ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++E;
+    }
+  }
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(E + 1023) << 52) | (mant & 0x000FFFFFFFFFFFFFull)));
+}
+
+// FP64 -> FP32, round to nearest even, by integer operations on the normal
+// FP32 range; other values through the conversion instruction.
+__device__ __forceinline__ float fx_to_float(double x) {
+  const long long b = __double_as_longlong(x);
+  const int ex = fx_exp(b);
+  if (ex < 1023 - 126 || ex > 1023 + 127) return __double2float_rn(x);
+  const unsigned long long mant = (unsigned long long)b & 0x000FFFFFFFFFFFFFull;
+  const unsigned m23 = (unsigned)(mant >> 29);
+  const unsigned long long rem = mant & 0x1FFFFFFFull;
+  unsigned f = ((unsigned)((unsigned long long)b >> 32) & 0x80000000u) | ((unsigned)(ex - 1023 + 127) << 23) | m23;
+  if (rem > 0x10000000ull || (rem == 0x10000000ull && (m23 & 1u))) f += 1u;
+  return __uint_as_float(f);
+}
+
+// The FP32-output residual of k_outer_residual_v4 in the exact form above.
+template <bool NORM>
+__global__ void __launch_bounds__(kBlock) k_outer_residual_fx(LevelDev L, RowPass rp, const double* __restrict__ z,
+                                                             const double* __restrict__ b, float* __restrict__ r,
+                                                             double* __restrict__ norm2) {
+  const int segs = L.c[0].nx >> 2;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row_all = gt / segs;
+  double rr = 0.0;
+  if (row_all < rp.rstart[L.ncomp]) {
+    const int seg = gt - row_all * segs;
+    int ci = 0;
+    while (ci + 1 < L.ncomp && row_all >= rp.rstart[ci + 1]) ++ci;
+    const CompDev& c = L.c[ci];
+    const int row = row_all - rp.rstart[ci];
+    const int j = row % c.ny, k = row / c.ny;
+    const int nx = c.nx;
+    const long long plane = (long long)nx * c.ny;
+    const long long rbase = c.off + (long long)row * nx;
+    const int x0 = seg << 2;
+    // the window as FP64 bit patterns: the centre row (4, left, right), then
+    // the rows y-1, y+1, z-1, z+1 in fixed slots, an absent row as zeros
+    // (which add nothing and do not raise the window's exponent)
+    long long w[22];
+    auto ld4 = [&](bool present, long long off, long long* dst) {
+      if (present) {
+        const longlong2 a = *reinterpret_cast<const longlong2*>(z + off);
+        const longlong2 d = *reinterpret_cast<const longlong2*>(z + off + 2);
+        dst[0] = a.x; dst[1] = a.y; dst[2] = d.x; dst[3] = d.y;
+      } else {
+        dst[0] = 0; dst[1] = 0; dst[2] = 0; dst[3] = 0;
+      }
+    };
+    ld4(true, rbase + x0, w);
+    w[4] = __double_as_longlong(z[rbase + (x0 == 0 ? nx - 1 : x0 - 1)]);
+    w[5] = __double_as_longlong(z[rbase + (x0 + 4 == nx ? 0 : x0 + 4)]);
+    const bool ys = c.ny > 1;
+    ld4(ys, c.off + ((long long)k * c.ny + (j == 0 ? c.ny - 1 : j - 1)) * nx + x0, w + 6);
+    ld4(ys, c.off + ((long long)k * c.ny + (j == c.ny - 1 ? 0 : j + 1)) * nx + x0, w + 10);
+    ld4(k > 0, rbase - plane + x0, w + 14);
+    ld4(k < c.nz - 1, rbase + plane + x0, w + 18);
+    int emax = 0;
+#pragma unroll
+    for (int q = 0; q < 22; ++q) emax = max(emax, fx_exp(w[q]));
+    const int edges = (k == 0) + (k == c.nz - 1);
+    int dz = 2;
+    if (c.zkind == kAxisCellDir) dz += edges;
+    if (c.zkind == kAxisCellNeu) dz -= edges;
+    const long long dg = (c.ny > 1 ? 4 : 2) + dz;
+    double bv[4] = {0.0, 0.0, 0.0, 0.0};
+    if (b) {
+      const double2 a = *reinterpret_cast<const double2*>(b + rbase + x0);
+      const double2 d = *reinterpret_cast<const double2*>(b + rbase + x0 + 2);
+      bv[0] = a.x; bv[1] = a.y; bv[2] = d.x; bv[3] = d.y;
+    }
+    float out[4];
+    double res[4];                         // the FP64 residual (its norm is FP64 too)
+    if (emax == 0) {                       // z = 0 on the window: r = b
+#pragma unroll
+      for (int e = 0; e < 4; ++e) res[e] = bv[e];
+    } else if (emax >= 64 && emax <= 2000) {
+      long long Z[22];
+#pragma unroll
+      for (int q = 0; q < 22; ++q) Z[q] = fx_align(w[q], emax);
+      long long S[4];
+      S[0] = Z[4] + Z[1];
+      S[1] = Z[0] + Z[2];
+      S[2] = Z[1] + Z[3];
+      S[3] = Z[2] + Z[5];
+#pragma unroll
+      for (int q = 6; q < 22; q += 4) {
+        S[0] += Z[q]; S[1] += Z[q + 1]; S[2] += Z[q + 2]; S[3] += Z[q + 3];
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const long long t = dg * Z[e] - S[e];
+        const double az = t == 0 ? 0.0 : fx_to_double(t, emax - 1080);
+        res[e] = fma(-c.s, az, bv[e]);
+      }
+    } else {                               // the plain FP64 arithmetic
+      double cz[22];
+#pragma unroll
+      for (int q = 0; q < 22; ++q) cz[q] = __longlong_as_double(w[q]);
+      double acc[4];
+      acc[0] = cz[4] + cz[1];
+      acc[1] = cz[0] + cz[2];
+      acc[2] = cz[1] + cz[3];
+      acc[3] = cz[2] + cz[5];
+#pragma unroll
+      for (int q = 6; q < 22; q += 4) {
+        acc[0] += cz[q]; acc[1] += cz[q + 1]; acc[2] += cz[q + 2]; acc[3] += cz[q + 3];
+      }
+      const double sdg = c.s * (double)dg;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) res[e] = fma(c.s, acc[e], fma(-sdg, cz[e], bv[e]));
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      out[e] = fx_to_float(res[e]);
+      if (NORM) rr = fma(res[e], res[e], rr);
+    }
+    *reinterpret_cast<float4*>(r + rbase + x0) = make_float4(out[0], out[1], out[2], out[3]);
+  }
+  if (NORM) {
+    rr = block_sum(rr);
+    if (threadIdx.x == 0) atomicAdd(norm2, rr);
+  }
+}
+
+// FP32 -> FP64 (exact) by integer operations for normal values; zero,
+// subnormal and non-finite values through the conversion instruction.
+__device__ __forceinline__ double fx_widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0u || ex == 0xffu) return (double)f;
+  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                          ((unsigned long long)(ex - 127u + 1023u) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+__device__ __forceinline__ double fx_widen(double f) { return f; }
+
+// z += d: one FP64 add per unknown (the widening of an FP32 d is done by
+// integer operations, off GB300's narrow FP64 pipe).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_outer_update_v4(long long n4, double* __restrict__ z,
                                                            const T* __restrict__ d) {
@@ -347,10 +532,10 @@ __global__ void __launch_bounds__(kBlock) k_outer_update_v4(long long n4, double
   if (q >= n4) return;
   double2 a = *reinterpret_cast<double2*>(z + 4 * q);
   double2 c = *reinterpret_cast<double2*>(z + 4 * q + 2);
-  a.x += (double)d[4 * q];
-  a.y += (double)d[4 * q + 1];
-  c.x += (double)d[4 * q + 2];
-  c.y += (double)d[4 * q + 3];
+  a.x += fx_widen(d[4 * q]);
+  a.y += fx_widen(d[4 * q + 1]);
+  c.x += fx_widen(d[4 * q + 2]);
+  c.y += fx_widen(d[4 * q + 3]);
   *reinterpret_cast<double2*>(z + 4 * q) = a;
   *reinterpret_cast<double2*>(z + 4 * q + 2) = c;
 }
@@ -3216,6 +3401,19 @@ cudaError_t launch_outer_residual(const LevelDev& L0, const double* z, const dou
     }
     rp.rstart[L0.ncomp] = rows;
     const long long nt = (long long)rows * (L0.c[0].nx >> 2);
+    if constexpr (sizeof(T) == 4) {
+      const bool aligned = ((uintptr_t)r & 15u) == 0 && L0.c[L0.ncomp - 1].off % 4 == 0 &&
+                           (L0.ncomp == 1 || L0.c[1].off % 4 == 0);
+      if (!aligned && norm2)
+        k_outer_residual_v4<T, true><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
+      else if (!aligned)
+        k_outer_residual_v4<T, false><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
+      else if (norm2)
+        k_outer_residual_fx<true><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
+      else
+        k_outer_residual_fx<false><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
+      return cudaGetLastError();
+    }
     if (norm2)
       k_outer_residual_v4<T, true><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
     else

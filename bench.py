@@ -77,6 +77,9 @@ def parse_args():
     p.add_argument("--rate", type=float, default=200.0)
     p.add_argument("--slots", type=int, default=12)
     p.add_argument("--budget-gb", type=float, default=32.0)
+    p.add_argument("--serve-persistent", type=int, default=0,
+                   help="served workload: continuous batching through the persistent batched launch (1) "
+                        "or shared per-phase graph launches (0)")
     return p.parse_args()
 
 
@@ -587,8 +590,8 @@ def run_served(args):
     reqs = served_stream(args.requests, args.rate)
     budget = int(args.budget_gb * (1 << 30))
 
-    def serve(slots):
-        srv = S.selm_server_create(budget, slots)
+    def serve(slots, batched=False, persistent=True):
+        srv = S.selm_server_create_batched(budget, slots, persistent) if batched else S.selm_server_create(budget, slots)
         keep = []
         t0 = _time.perf_counter()
         for i, r in enumerate(reqs):
@@ -604,6 +607,7 @@ def run_served(args):
         S.selm_server_drain(srv)
         res = S.selm_server_poll(srv, len(reqs) + 1)
         stats = S.selm_server_stats(srv)
+        bstats = S.selm_server_batch_stats(srv) if batched else None
         S.selm_server_destroy(srv)
         lat = np.array([x["t_done"] - x["t_submit"] for x in res])
         span = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
@@ -614,16 +618,20 @@ def run_served(args):
                     vcycles_per_s=sum(x["vcycles"] for x in res) / span, makespan_s=span,
                     mean_requests_in_service=busy / span,
                     peak_slots=stats["peak_slots"], peak_gb=stats["peak_bytes"] / 2 ** 30, all_ok=ok,
+                    batched_steps=bstats["steps"] if bstats else None,
+                    batch_rebuilds=bstats["rebuilds"] if bstats else None,
                     positions=[k[0].copy() for k in keep])
 
     torch.cuda.synchronize()
     plain = serve(1)
+    streams = serve(args.slots)
     launches0 = S.selm_kernel_launches()
-    served = serve(args.slots)
+    served = serve(args.slots, batched=True, persistent=bool(args.serve_persistent))
     launches = S.selm_kernel_launches() - launches0
     # equal accuracy: every request's final positions, served vs plain (minimum
     # image along the periodic axes, relative to the request's displacement)
     worst, compared = 0.0, 0
+    streams.pop("positions")
     for r, a, b_ in zip(reqs, served.pop("positions"), plain.pop("positions")):
         if r["steps"] > 1:   # longer trajectories decorrelate (rounding grows ~15x per step)
             continue
@@ -636,14 +644,21 @@ def run_served(args):
         worst = max(worst, float(np.linalg.norm(pd(a, b_)) / max(np.linalg.norm(pd(b_, X0)), 1e-300)))
     line = {
         "metric": "served solves/s + p99 vs plain form", "value": served["solves_per_s"], "unit": "solves/s",
+        "form": "continuous batching: one batched Euler-Maruyama step of every admitted request per tick "
+                "(" + ("persistent batched FAC launches" if args.serve_persistent else "shared per-phase graph launches")
+                + "), requests retired and admitted between ticks",
         "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "dtype": "f32+f64",
         "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {args.rate}/s; 50% 2-D channels "
                                f"(edge 256..1024), 50% 3-D (edge 32..192); 16..4096 particles; 1..20 steps; "
                                f"each step = FAC solve to 1e-10 + {SAMPLE_CYCLES} stochastic cycles",
                    "slots": args.slots, "budget_gb": args.budget_gb,
                    "solve": "one Euler-Maruyama step (one mobility solve) of one request"},
-        "served": served, "plain": plain,
+        "served": served, "plain": plain, "streams": streams,
         "speedup_solves": served["solves_per_s"] / plain["solves_per_s"],
+        "speedup_vs_streams": served["solves_per_s"] / streams["solves_per_s"],
+        "arms": {"plain": "one request at a time (one slot)",
+                 "streams": f"{args.slots} slots, each request alone on its own stream (concurrency only)",
+                 "served": f"{args.slots} slots, continuous batching"},
         "equal_accuracy": {"max_rel_position_difference_served_vs_plain": worst, "requests_compared": compared,
                            "note": "the one-step requests' positions, served against plain, relative to the "
                                    "displacement (minimum image); longer requests decorrelate chaotically at "
@@ -986,6 +1001,7 @@ def mac_measure(S, n, K, steps, warmup, particles=1000):
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     launches0 = S.selm_kernel_launches()
+    print(f"[bench] library kernel launches before the timed region: {launches0}", file=sys.stderr)
     with ClockSampler(torch.cuda.current_device()) as clk:
         for k in range(steps):
             flush.fill_(float(k))

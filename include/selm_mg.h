@@ -387,6 +387,22 @@ typedef struct {
 
 typedef struct selm_server selm_server;
 selm_status selm_server_create(size_t budget_bytes, int max_slots, selm_server** out);
+/* Continuous batching (spec served form on the batched engine): one
+   scheduler keeps up to `max_slots` admitted requests resident and runs the
+   next Euler-Maruyama step of all of them as one batched step
+   (selm_batch_step over the requests' handles: per-phase graph launches
+   shared by all, or with `persistent` the persistent batched FAC launch, one
+   work-list slot per request, where the systems qualify).  Between steps the
+   requests whose nsteps are done are copied out and retired, waiting
+   requests are admitted (arrival order, footprint in the pool, the running
+   batch's dt and chain cycles per step; an empty batch takes the next
+   request's), and the batch is rebuilt over the new membership.  Requests
+   must be SELM_PROJ_NONE systems (submit returns SELM_EINVAL otherwise).
+   Each request's result equals its run alone up to the extra FAC cycles a
+   batched solve gives the systems that converge first. */
+selm_status selm_server_create_batched(size_t budget_bytes, int max_slots, int persistent, selm_server** out);
+/* Batched steps run and batch rebuilds (membership changes) so far. */
+selm_status selm_server_batch_stats(selm_server* s, long long* steps, long long* rebuilds);
 /* Queues a request (returns at once); SELM_EBUSY if it can never fit the pool. */
 selm_status selm_server_submit(selm_server* s, const selm_request* r, uint64_t* id);
 /* Moves up to `max` finished results to `out`; returns how many. */

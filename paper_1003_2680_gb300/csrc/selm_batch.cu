@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "../../include/selm_mg.h"
+#include "selm_batch_internal.h"
 #include "selm_handle.h"
 #include "selm_launch.h"
 #include "selm_prof.h"
@@ -65,6 +66,7 @@ struct selm_batch {
   BatchPersist* bp = nullptr;   // persistent form (null: per-system graphs only)
   bool persistent = false;
   unsigned* host_flag = nullptr;  // pinned copy of the persistent launches' timeout word
+  bool owns = true;               // false: the systems are borrowed (batch_adopt) and outlive the batch
   std::string err;
 };
 
@@ -322,35 +324,28 @@ bool all_converged(const selm_batch* b, std::vector<int>& cycles, int cyc) {
 
 }  // namespace
 
-extern "C" {
+namespace selm {
 
-selm_status selm_batch_create(int nsys, const selm_mg_desc* descs, void* stream, selm_batch** out) {
-  if (nsys < 1 || !descs || !out) return SELM_EINVAL;
+selm_status batch_adopt(int nsys, selm_mg* const* hs, bool owns, void* stream, selm_batch** out) {
+  if (nsys < 1 || !hs || !out) return SELM_EINVAL;
   *out = nullptr;
   for (int i = 0; i < nsys; ++i)
-    if (descs[i].projection != SELM_PROJ_NONE) {
-      std::fprintf(stderr, "selm_batch_create: the batched form runs SELM_PROJ_NONE systems\n");
-      return SELM_EINVAL;
-    }
+    if (!hs[i] || hs[i]->d.projection != SELM_PROJ_NONE) return SELM_EINVAL;
   selm_batch* b = new (std::nothrow) selm_batch();
   if (!b) return SELM_ENOMEM;
+  b->owns = false;   // until set-up succeeds the caller keeps the systems
   b->n = nsys;
   b->np.assign(nsys, 0);
   b->X.assign(nsys, nullptr);
   b->F.assign(nsys, nullptr);
   for (int i = 0; i < nsys; ++i) {
-    selm_mg* h = nullptr;
-    selm_status st = selm_mg_create(&descs[i], stream, &h);
-    if (st != SELM_OK) {
-      selm_batch_destroy(b);
-      return st;
-    }
+    selm_mg* h = hs[i];
     // The systems' graph branches run side by side: each keeps its levels in
     // its own cluster engine (cooperative launches would take every SM).
     h->vel.use_coop = false;
     h->pres.use_coop = false;
     b->sys.push_back(h);
-    st = selm::replan_engine(h, 0, stream ? (cudaStream_t)stream : nullptr);
+    selm_status st = selm::replan_engine(h, 0, stream ? (cudaStream_t)stream : nullptr);
     if (st != SELM_OK) {
       selm_batch_destroy(b);
       return st;
@@ -374,11 +369,11 @@ selm_status selm_batch_create(int nsys, const selm_mg_desc* descs, void* stream,
   }
   // persistent form, when every system qualifies
   {
-    std::vector<BatchSysHost> hs(nsys);
+    std::vector<BatchSysHost> hb(nsys);
     bool same = true;
     for (int i = 0; i < nsys; ++i) {
       selm_mg* h = b->sys[i];
-      BatchSysHost& q = hs[i];
+      BatchSysHost& q = hb[i];
       q.levels = h->vel.levels;
       q.esize = h->esize;
       q.cholesky = h->d.coarse_mode == SELM_COARSE_CHOLESKY;
@@ -393,24 +388,54 @@ selm_status selm_batch_create(int nsys, const selm_mg_desc* descs, void* stream,
       q.bvel = h->bvel;
       same = same && h->mu1 == b->sys[0]->mu1 && h->mu2 == b->sys[0]->mu2;
     }
-    if (same && batch_persist_eligible(nsys, hs.data()) &&
+    if (same && batch_persist_eligible(nsys, hb.data()) &&
         cudaMallocHost((void**)&b->host_flag, 2 * sizeof(unsigned)) == cudaSuccess) {
       b->host_flag[0] = b->host_flag[1] = 0u;
       cudaStreamSynchronize(stream ? (cudaStream_t)stream : nullptr);
-      if (batch_persist_create(nsys, hs.data(), b->sys[0]->mu1, b->sys[0]->mu2, &b->bp) == cudaSuccess)
+      if (batch_persist_create(nsys, hb.data(), b->sys[0]->mu1, b->sys[0]->mu2, &b->bp) == cudaSuccess)
         b->persistent = true;
       cudaGetLastError();
     }
   }
+  b->owns = owns;
   *out = b;
   return SELM_OK;
+}
+
+}  // namespace selm
+
+extern "C" {
+
+selm_status selm_batch_create(int nsys, const selm_mg_desc* descs, void* stream, selm_batch** out) {
+  if (nsys < 1 || !descs || !out) return SELM_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < nsys; ++i)
+    if (descs[i].projection != SELM_PROJ_NONE) {
+      std::fprintf(stderr, "selm_batch_create: the batched form runs SELM_PROJ_NONE systems\n");
+      return SELM_EINVAL;
+    }
+  std::vector<selm_mg*> hs;
+  for (int i = 0; i < nsys; ++i) {
+    selm_mg* h = nullptr;
+    selm_status st = selm_mg_create(&descs[i], stream, &h);
+    if (st != SELM_OK) {
+      for (selm_mg* q : hs) selm_mg_destroy(q);
+      return st;
+    }
+    hs.push_back(h);
+  }
+  selm_status st = selm::batch_adopt(nsys, hs.data(), true, stream, out);
+  if (st != SELM_OK)
+    for (selm_mg* q : hs) selm_mg_destroy(q);
+  return st;
 }
 
 selm_status selm_batch_destroy(selm_batch* b) {
   if (!b) return SELM_EINVAL;
   cudaDeviceSynchronize();
   drop_graphs(b);
-  for (selm_mg* h : b->sys) selm_mg_destroy(h);
+  if (b->owns)
+    for (selm_mg* h : b->sys) selm_mg_destroy(h);
   for (cudaStream_t s : b->branch)
     if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->join)

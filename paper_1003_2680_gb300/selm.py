@@ -140,6 +140,8 @@ _SIGS = {
                                     ctypes.POINTER(_I), _P]),
     "selm_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "selm_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
+    "selm_server_create_batched": (_I, [ctypes.c_size_t, _I, _I, ctypes.POINTER(_P)]),
+    "selm_server_batch_stats": (_I, [_P, ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
     "selm_server_submit": (_I, [_P, ctypes.POINTER(SelmRequest), ctypes.POINTER(_U64)]),
     "selm_server_poll": (_I, [_P, ctypes.POINTER(SelmResult), _I]),
     "selm_server_drain": (_I, [_P]),
@@ -528,6 +530,19 @@ def selm_server_create(budget_bytes, max_slots):
     s = _P()
     _check(None, lib().selm_server_create(int(budget_bytes), int(max_slots), ctypes.byref(s)))
     return s.value
+
+
+def selm_server_create_batched(budget_bytes, max_slots, persistent=True):
+    s = _P()
+    _check(None, lib().selm_server_create_batched(int(budget_bytes), int(max_slots), int(bool(persistent)),
+                                                  ctypes.byref(s)))
+    return s.value
+
+
+def selm_server_batch_stats(s):
+    steps, rebuilds = _LL(0), _LL(0)
+    _check(None, lib().selm_server_batch_stats(s, ctypes.byref(steps), ctypes.byref(rebuilds)))
+    return {"steps": steps.value, "rebuilds": rebuilds.value}
 
 
 def selm_server_submit(s, desc, X, F, dt, nsteps, ncycles_per_step, user=0):

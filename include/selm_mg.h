@@ -417,6 +417,36 @@ double selm_server_clock(selm_server* s);
 /* Finishes the queued requests, stops the workers and frees the pool. */
 selm_status selm_server_destroy(selm_server* s);
 
+/* ---- exact discrete Stokes mobility and the Ito drift ---------------------
+   Corrections beyond the paper's effective dynamics (which uses
+   M = Gamma P~ A^-1 P~ Gamma^T and drops kT div_X M, Section 2.1).
+   selm_mg_stokes_solve: u = S f, the velocity of the MAC saddle point
+   A u + D^T p = f, D u = 0 (D the integer MAC divergence), by conjugate
+   gradients on the pressure Schur complement D A^-1 D^T with FAC inner solves
+   (Algorithm 1) a hundred times tighter than `tol` (0: the descriptor's tol);
+   f, u: device velocity fields (level-0 layout).  iters / resid (optional
+   HOST) receive the outer iterations and the relative Schur residual; the
+   call synchronises.  The first Stokes call allocates the handle's Stokes
+   scratch (through the descriptor's allocator hooks if given).
+   selm_mg_stokes_mobility: U = Gamma S Gamma^T F.
+   selm_mg_rfd_directions: W ([np][dim], device) of step `step`: Philox
+   kind 3 normals, rank = particle * dim + axis, counter words 2-3 = step.
+   selm_mg_rfd_drift: d = (kT / delta) [M_S(X + delta W/2) - M_S(X - delta W/2)] W,
+   the random finite difference of kT div_X M_S.
+   selm_mg_stokes_step: `nsteps` Euler-Maruyama steps with both corrections:
+   d at the start positions (W of the handle's step counter, which advances
+   by one per step; delta = 0 omits the drift), the chain advanced by
+   `ncycles`, then X <- X + Gamma S (dt Gamma^T F + sqrt(2 kT dt) A xi) + dt d,
+   wrapped and reflected.  Independent of the descriptor's projection. */
+selm_status selm_mg_stokes_solve(selm_mg* h, const double* f, double* u, double tol, int* iters, double* resid,
+                                 void* stream);
+selm_status selm_mg_stokes_mobility(selm_mg* h, int np, const double* X, const double* F, double* U, void* stream);
+selm_status selm_mg_rfd_directions(selm_mg* h, int np, uint64_t step, double* W, void* stream);
+selm_status selm_mg_rfd_drift(selm_mg* h, int np, const double* X, const double* W, double delta, double* d,
+                              void* stream);
+selm_status selm_mg_stokes_step(selm_mg* h, int np, double* X, const double* F, double dt, int nsteps, int ncycles,
+                                double delta, void* stream);
+
 /* ---- measurement --------------------------------------------------------
    Process-wide kernel accounting.  selm_kernel_launches() counts every
    kernel this library has launched since it was loaded.  With profiling on,

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libselm_mg.so")
 SOURCES = ["selm_setup.cpp", "selm_kernels.cu", "selm_coarse.cu", "selm_api.cu", "selm_batch.cu", "selm_server.cu",
-           "selm_composite.cu", "selm_spectral.cu", "selm_mac_setup.cpp", "selm_mac.cu"]
+           "selm_composite.cu", "selm_spectral.cu", "selm_mac_setup.cpp", "selm_mac.cu", "selm_stokes.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -598,6 +598,8 @@ int engine_first_level(const selm_mg* h, const Sys& s) {
 
 namespace selm {
 
+selm_status chain_advance(selm_mg* h, int ncycles, cudaStream_t st) { return chain_cycles(h, ncycles, st); }
+
 size_t footprint_with_host(const selm_mg_desc& d, const HostSystem& host, size_t extra_bytes) {
   Sys vel;
   vel.host = host;
@@ -863,6 +865,7 @@ selm_status selm_mg_destroy(selm_mg* h) {
     else
       cudaFree(h->ws);
   }
+  stokes_release(h);
   delete[] h->host_red;
   delete h;
   return SELM_OK;

@@ -105,6 +105,11 @@ struct selm_mg {
   bool graphs = true;
   bool speculate = true;      // solves enqueue the next V-cycle before reading the norm
   uint64_t cycle = 0;
+  // scratch of the exact Stokes solve (allocated on its first use) and the
+  // step counter of the drift directions
+  void* stokes = nullptr;
+  size_t stokes_bytes = 0;
+  uint64_t stokes_step = 0;
   int last_solve_cycles = 0, last_proj_cycles = 0;
   long long total_vcycles = 0;
   std::string err;
@@ -134,5 +139,9 @@ size_t footprint_with_host(const selm_mg_desc& d, const HostSystem& host, size_t
 // level fields: reads s.b[level], writes s.v[level] (which must hold its
 // initial value, normally 0).
 selm_status vcycle_level(selm_mg* h, Sys& s, int level, bool noise, const unsigned long long* cyc, cudaStream_t st);
+// `ncycles` stochastic FAC cycles of the handle's chain xi (b = 0).
+selm_status chain_advance(selm_mg* h, int ncycles, cudaStream_t st);
+// Frees the Stokes scratch (selm_stokes.cu).
+void stokes_release(selm_mg* h);
 
 }  // namespace selm

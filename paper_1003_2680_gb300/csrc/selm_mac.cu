@@ -166,16 +166,32 @@ __global__ void __launch_bounds__(kThreads) k_dot_part(long long n, const double
 // Eq. equ_def_Q_GS): v_i = (b_i - sum_{j != i} a_ij v_j) / a_ii
 //                          + sigma n_i / sqrt(a_ii).
 // NK = 0: no noise; 1: normal of the site's rank in the class; 2: normal of
-// the site's row index (slab faces).
+// the site's row index (slab faces).  kRowLanes lanes share a row: each sums
+// every kRowLanes-th stored entry, a shuffle combines them, and the first
+// lane updates the site, so a class of a few thousand rows still puts
+// several warps on every SM.
+constexpr int kRowLanes = 4;
+
 template <typename T, int NK>
 __global__ void __launch_bounds__(kThreads) k_colour(SellDev S, int pos0, int cnt, T* __restrict__ v,
                                                     const T* __restrict__ b, T sigma, Key key, uint32_t c1,
                                                     const unsigned long long* __restrict__ cyc) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
-  const int p = pos0 + t;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = g / kRowLanes, sub = g % kRowLanes;
+  const bool valid = t < cnt;        // every lane stays for the shuffles
+  const int p = pos0 + (valid ? t : 0);
+  T off = T(0);
+  if (valid) {
+    const int s = p >> 5;
+    const long long o = S.soff[s] + (p & 31);
+    const int w = S.swid[s];
+    const T* __restrict__ vv = vals<T>(S);
+    for (int e = sub; e < w; e += kRowLanes) off += vv[o + 32ll * e] * v[S.col[o + 32ll * e]];
+  }
+#pragma unroll
+  for (int m = 1; m < kRowLanes; m <<= 1) off += __shfl_xor_sync(0xffffffffu, off, m);
+  if (!valid || sub != 0) return;
   const int row = S.row[p];
-  const T off = row_dot<T>(S, p, v);
   T nv = (b[row] - off) * rd_at<T>(S, p);
   if (NK != 0) {
     const unsigned long long c = *cyc;
@@ -188,15 +204,27 @@ __global__ void __launch_bounds__(kThreads) k_colour(SellDev S, int pos0, int cn
   v[row] = nv;
 }
 
-// t = b - A v on every row of a class-ordered level (diagonal included).
+// t = b - A v on every row of a class-ordered level (diagonal included);
+// kRowLanes lanes per row as in k_colour.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_cls_resid(SellDev S, const T* __restrict__ v, const T* __restrict__ b,
                                                        T* __restrict__ t) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < S.npos; p += gridDim.x * blockDim.x) {
-    const int row = S.row[p];
-    if (row < 0) continue;
-    t[row] = b[row] - dg_at<T>(S, p) * v[row] - row_dot<T>(S, p, v);
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (int)(g / kRowLanes), sub = (int)(g % kRowLanes);
+  const bool valid = p < S.npos && S.row[p] >= 0;
+  T off = T(0);
+  if (valid) {
+    const int s = p >> 5;
+    const long long o = S.soff[s] + (p & 31);
+    const int w = S.swid[s];
+    const T* __restrict__ vv = vals<T>(S);
+    for (int e = sub; e < w; e += kRowLanes) off += vv[o + 32ll * e] * v[S.col[o + 32ll * e]];
   }
+#pragma unroll
+  for (int m = 1; m < kRowLanes; m <<= 1) off += __shfl_xor_sync(0xffffffffu, off, m);
+  if (!valid || sub != 0) return;
+  const int row = S.row[p];
+  t[row] = b[row] - dg_at<T>(S, p) * v[row] - off;
 }
 
 // Exact draw on the coarsest level (FP64): with A = L L^T,
@@ -477,6 +505,8 @@ struct selm_mac {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   long long glaunch[2] = {0, 0};
+  cudaGraphExec_t cg_exec = nullptr;  // a block of conjugate-gradient iterations
+  long long cg_launch = 0;
   int gruns[2] = {0, 0};
   bool graphs = true;
 };
@@ -570,10 +600,10 @@ selm_status sweep(selm_mac* h, int l, int s, double sigma, const unsigned long l
     const int cnt = L.csize[c];
     prof::Scope ps(SELM_K_COARSE_SWEEP, st);
     if (sigma != 0.0)
-      k_colour<T, 1><<<blocks_for(cnt), kThreads, 0, st>>>(L.cls, L.cstart[c], cnt, (T*)L.v, (const T*)L.b, (T)sigma,
+      k_colour<T, 1><<<blocks_for((long long)cnt * kRowLanes), kThreads, 0, st>>>(L.cls, L.cstart[c], cnt, (T*)L.v, (const T*)L.b, (T)sigma,
                                                            h->key, ctr1(l + 1, 0, (int)c, s, 0), cyc);
     else
-      k_colour<T, 0><<<blocks_for(cnt), kThreads, 0, st>>>(L.cls, L.cstart[c], cnt, (T*)L.v, (const T*)L.b, (T)0,
+      k_colour<T, 0><<<blocks_for((long long)cnt * kRowLanes), kThreads, 0, st>>>(L.cls, L.cstart[c], cnt, (T*)L.v, (const T*)L.b, (T)0,
                                                            h->key, 0, cyc);
     MCK(cudaGetLastError());
   }
@@ -595,7 +625,8 @@ selm_status vcycle(selm_mac* h, int l, double sigma, const unsigned long long* c
   selm_mac::Level& C = h->lev[l + 1];
   {
     prof::Scope ps(SELM_K_RESIDUAL, st);
-    k_cls_resid<T><<<red_blocks(L.cls.npos) * 4, kThreads, 0, st>>>(L.cls, (const T*)L.v, (const T*)L.b, (T*)L.t);
+    k_cls_resid<T><<<blocks_for((long long)L.cls.npos * kRowLanes), kThreads, 0, st>>>(L.cls, (const T*)L.v,
+                                                                                       (const T*)L.b, (T*)L.t);
     MCK(cudaGetLastError());
   }
   {
@@ -636,10 +667,10 @@ selm_status correction(selm_mac* h, double sigma, const unsigned long long* cyc,
       const int cnt = h->psize[c];
       prof::Scope ps(SELM_K_FINE_SWEEP, st);
       if (sigma != 0.0)
-        k_colour<T, 2><<<blocks_for(cnt), kThreads, 0, st>>>(h->Apatch, h->pstart[c], cnt, (T*)h->q, (const T*)h->r,
+        k_colour<T, 2><<<blocks_for((long long)cnt * kRowLanes), kThreads, 0, st>>>(h->Apatch, h->pstart[c], cnt, (T*)h->q, (const T*)h->r,
                                                              (T)sigma, h->key, ctr1(0, 0, (int)c, s, 2), cyc);
       else
-        k_colour<T, 0><<<blocks_for(cnt), kThreads, 0, st>>>(h->Apatch, h->pstart[c], cnt, (T*)h->q, (const T*)h->r,
+        k_colour<T, 0><<<blocks_for((long long)cnt * kRowLanes), kThreads, 0, st>>>(h->Apatch, h->pstart[c], cnt, (T*)h->q, (const T*)h->r,
                                                              (T)0, h->key, 0, cyc);
       MCK(cudaGetLastError());
     }
@@ -781,16 +812,44 @@ selm_status pressure_solve(selm_mac* h, const double* rhs, int* iters, double* r
   double rn = bn;
   int it = 0;
   const int max_it = 20000, check = 16;
-  while (bn > 0.0 && rn > tol * bn && it < max_it) {
+  // `check` iterations (six launches each) on the handle's fixed buffers
+  auto block = [&](cudaStream_t s2) -> cudaError_t {
     for (int k = 0; k < check; ++k) {
-      prof::Scope ps(SELM_K_PROJECTION, st);
-      k_cg_mv<<<nb, kThreads, 0, st>>>(h->S, h->cg_p, h->cg_q, h->part);
-      k_reduce<<<1, kThreads, 0, st>>>(h->part, (int)nb, h->sc + 1);
-      k_cg_update<<<nb, kThreads, 0, st>>>(n, h->sc, h->cg_x, h->cg_r, h->cg_p, h->cg_q, h->minv, h->cg_z, h->part);
-      k_cg_reduce2<<<1, kThreads, 0, st>>>(h->part, (int)nb, h->sc);
-      k_cg_dir<<<nb, kThreads, 0, st>>>(n, h->sc, h->cg_z, h->cg_p);
-      k_cg_shift<<<1, 1, 0, st>>>(h->sc);
-      MCK(cudaGetLastError());
+      prof::Scope ps(SELM_K_PROJECTION, s2);
+      k_cg_mv<<<nb, kThreads, 0, s2>>>(h->S, h->cg_p, h->cg_q, h->part);
+      k_reduce<<<1, kThreads, 0, s2>>>(h->part, (int)nb, h->sc + 1);
+      k_cg_update<<<nb, kThreads, 0, s2>>>(n, h->sc, h->cg_x, h->cg_r, h->cg_p, h->cg_q, h->minv, h->cg_z, h->part);
+      k_cg_reduce2<<<1, kThreads, 0, s2>>>(h->part, (int)nb, h->sc);
+      k_cg_dir<<<nb, kThreads, 0, s2>>>(n, h->sc, h->cg_z, h->cg_p);
+      k_cg_shift<<<1, 1, 0, s2>>>(h->sc);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  // replayed from a captured graph (captured once per handle) unless
+  // profiling or capture is off
+  if (!h->cg_exec && h->graphs && !prof::g_on) {
+    const long long l0 = prof::g_launches.load();
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const cudaError_t e1 = block(h->cap);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(h->cap, &graph);
+      h->cg_launch = prof::g_launches.load() - l0;
+      prof::g_launches.fetch_sub(h->cg_launch);
+      if (e1 != cudaSuccess || e2 != cudaSuccess || !graph ||
+          cudaGraphInstantiate(&h->cg_exec, graph, 0) != cudaSuccess)
+        h->cg_exec = nullptr;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();
+  }
+  while (bn > 0.0 && rn > tol * bn && it < max_it) {
+    if (h->cg_exec && !prof::g_on) {
+      MCK(cudaGraphLaunch(h->cg_exec, st));
+      prof::g_launches.fetch_add(h->cg_launch);
+    } else {
+      MCK(block(st));
     }
     it += check;
     MCK(cudaMemcpyAsync(h->host_sc, h->sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1099,6 +1158,7 @@ selm_status selm_mac_destroy(selm_mac* h) {
   if (!h) return SELM_EINVAL;
   for (auto& g : h->gexec)
     if (g) cudaGraphExecDestroy(g);
+  if (h->cg_exec) cudaGraphExecDestroy(h->cg_exec);
   if (h->cap) cudaStreamDestroy(h->cap);
   for (void* p : h->allocs) cudaFree(p);
   if (h->host_sc) cudaFreeHost(h->host_sc);

@@ -191,6 +191,11 @@ _SIGS = {
                                   ctypes.POINTER(_LL), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "selm_mac_host_colours": (_I, [ctypes.POINTER(SelmMacDesc), _I, ctypes.POINTER(_I), ctypes.POINTER(_P)]),
     "selm_mac_host_free": (None, [_P]),
+    "selm_mg_stokes_solve": (_I, [_P, _P, _P, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+    "selm_mg_stokes_mobility": (_I, [_P, _I, _P, _P, _P, _P]),
+    "selm_mg_rfd_directions": (_I, [_P, _I, _U64, _P, _P]),
+    "selm_mg_rfd_drift": (_I, [_P, _I, _P, _P, _D, _P, _P]),
+    "selm_mg_stokes_step": (_I, [_P, _I, _P, _P, _D, _I, _I, _D, _P]),
     "selm_kernel_launches": (ctypes.c_longlong, []),
     "selm_profile_enable": (_I, [_I]),
     "selm_profile_reset": (_I, []),
@@ -858,3 +863,28 @@ def selm_mac_host_colours(desc, level):
     finally:
         lib().selm_mac_host_free(col)
     return out
+
+
+# -- exact Stokes mobility and the Ito drift --------------------------------------
+def selm_mg_stokes_solve(h, f, u, tol=0.0, stream=None):
+    it, res = _I(0), _D(0.0)
+    _check(h, lib().selm_mg_stokes_solve(h, _ptr(f), _ptr(u), tol, ctypes.byref(it), ctypes.byref(res),
+                                         _stream(stream)))
+    return it.value, res.value
+
+
+def selm_mg_stokes_mobility(h, X, F, U, stream=None):
+    _check(h, lib().selm_mg_stokes_mobility(h, X.shape[0], _ptr(X), _ptr(F), _ptr(U), _stream(stream)))
+
+
+def selm_mg_rfd_directions(h, np_, step, W, stream=None):
+    _check(h, lib().selm_mg_rfd_directions(h, np_, step, _ptr(W), _stream(stream)))
+
+
+def selm_mg_rfd_drift(h, X, W, delta, d, stream=None):
+    _check(h, lib().selm_mg_rfd_drift(h, X.shape[0], _ptr(X), _ptr(W), delta, _ptr(d), _stream(stream)))
+
+
+def selm_mg_stokes_step(h, X, F, dt, nsteps, ncycles, delta, stream=None):
+    _check(h, lib().selm_mg_stokes_step(h, X.shape[0], _ptr(X), _ptr(F), dt, nsteps, ncycles, delta,
+                                        _stream(stream)))

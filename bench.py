@@ -1380,6 +1380,11 @@ def main():
                                                   "covariance", "e2e", "gpu_launches", "clocks",
                                                   "kernel_time_share", "steps", "warmup")}
         line["config1_64x64_fp64"] = config1_measure(S)
+        torch.cuda.empty_cache()
+        mac = mac_measure(S, 64, 8, steps=20, warmup=3)
+        line["staggered_composite"] = {k: mac[k] for k in ("value", "unit", "ms_per_step", "dtype", "config",
+                                                          "kernel_time_share", "avg_launch_us", "whole_step_model",
+                                                          "em_step", "projection", "gpu_launches", "clocks")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     elif rank == 0:

@@ -1076,6 +1076,47 @@ def mac_measure(S, n, K, steps, warmup, particles=1000):
     }
 
 
+def stokes_measure(S, n, particles, steps, warmup):
+    """The exact-Stokes Euler-Maruyama step with the Ito drift (f3): the n^3
+    channel, FP32 inner cycles with FP64 refinement, `particles` particles;
+    each step = the random-finite-difference drift (two Stokes mobility
+    solves), 2 chain cycles and one Stokes solve of the combined forced and
+    thermal field.  Every Stokes solve is conjugate gradients on the pressure
+    Schur complement with FAC inner solves."""
+    import torch
+    import selm_inputs
+    d = S.make_desc(dim=3, n=n, kT=1.0, precision=S.SELM_FP32_REFINE64, seed=0, instance=0,
+                    max_particles=particles, torch_allocator=False)
+    h = S.selm_mg_create(d)
+    X = torch.tensor(selm_inputs.particles(particles, 3, n, seed=0), device="cuda")
+    F = torch.tensor(selm_inputs.forces(particles, 3, seed=0), device="cuda")
+    for _ in range(warmup):
+        S.selm_mg_stokes_step(h, X, F, DT, 1, SAMPLE_CYCLES, 1e-4)
+    torch.cuda.synchronize()
+    c0 = S.selm_mg_stats(h)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = S.selm_kernel_launches()
+    a.record()
+    S.selm_mg_stokes_step(h, X, F, DT, steps, SAMPLE_CYCLES, 1e-4)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    launches = S.selm_kernel_launches() - launches0
+    vcycles = (S.selm_mg_stats(h)[2] - c0[2]) / steps
+    # one Stokes solve alone: outer iterations
+    f = torch.randn(S.selm_mg_layout(h, S.SELM_SYS_VELOCITY, 0, 0)[2], dtype=torch.float64, device="cuda")
+    u = torch.empty_like(f)
+    it, res = S.selm_mg_stokes_solve(h, f, u)
+    S.selm_mg_destroy(h)
+    return {"workload": f"3-D {n}^3 channel, {particles} particles, exact Stokes mobility + Ito drift "
+                        f"(random finite difference, delta = 1e-4), 2 chain cycles per step, FP32 inner cycles with "
+                        f"FP64 refinement",
+            "ms_per_step": ms, "vcycles_per_step": vcycles, "stokes_solves_per_step": 3,
+            "cell_cycles_per_s": n ** 3 * vcycles / (ms / 1e3),
+            "schur_cg_iterations_per_solve": it, "schur_relative_residual": res,
+            "gpu_launches_per_step": launches / steps}
+
+
 def run_mac(args):
     from paper_1003_2680_gb300 import _build
     _build.build()
@@ -1385,6 +1426,7 @@ def main():
         line["staggered_composite"] = {k: mac[k] for k in ("value", "unit", "ms_per_step", "dtype", "config",
                                                           "kernel_time_share", "avg_launch_us", "whole_step_model",
                                                           "em_step", "projection", "gpu_launches", "clocks")}
+        line["stokes_drift_64"] = stokes_measure(S, 64, 256, steps=3, warmup=3)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     elif rank == 0:

@@ -55,29 +55,30 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 
 // Butterfly q of a stage over all rows (columns == false: along x) or all
 // columns (along y) of an n x n plane: line and pair index, with consecutive
-// threads on consecutive addresses in both cases.
-__device__ __forceinline__ void stage_index(int q, int n, int half, bool columns, int* a0, int* a1, int* j) {
-  const int half_n = n >> 1;
-  const int line = columns ? q % n : q / half_n;
-  const int p = columns ? q / n : q - (q / half_n) * half_n;
-  const int grp = p / half;
-  *j = p - grp * half;
-  const int i0 = grp * 2 * half + *j, i1 = i0 + half;
-  *a0 = columns ? i0 * n + line : line * n + i0;
-  *a1 = columns ? i1 * n + line : line * n + i1;
+// threads on consecutive addresses in both cases.  n = 2^logn and
+// half = 2^lh, so the index arithmetic is shifts and masks.
+__device__ __forceinline__ void stage_index(int q, int logn, int lh, bool columns, int* a0, int* a1, int* j) {
+  const int n = 1 << logn;
+  const int line = columns ? (q & (n - 1)) : (q >> (logn - 1));
+  const int p = columns ? (q >> logn) : (q & ((n >> 1) - 1));
+  const int grp = p >> lh;
+  *j = p & ((1 << lh) - 1);
+  const int i0 = (grp << (lh + 1)) + *j, i1 = i0 + (1 << lh);
+  *a0 = columns ? (i0 << logn) + line : (line << logn) + i0;
+  *a1 = columns ? (i1 << logn) + line : (line << logn) + i1;
 }
 
 // Forward transform along one axis, decimation in frequency: natural order in,
 // bit-reversed order out.
 __device__ void fft_dif(float2* A, const float2* W, int n, int logn, bool columns) {
   for (int s = logn; s >= 1; --s) {
-    const int half = 1 << (s - 1), tw_step = n >> s;
+    const int lh = s - 1, tw_shift = logn - s;
     for (int q = threadIdx.x; q < n * (n >> 1); q += blockDim.x) {
       int a0, a1, j;
-      stage_index(q, n, half, columns, &a0, &a1, &j);
+      stage_index(q, logn, lh, columns, &a0, &a1, &j);
       const float2 x0 = A[a0], x1 = A[a1];
       A[a0] = make_float2(x0.x + x1.x, x0.y + x1.y);
-      A[a1] = cmul(make_float2(x0.x - x1.x, x0.y - x1.y), W[j * tw_step]);
+      A[a1] = cmul(make_float2(x0.x - x1.x, x0.y - x1.y), W[j << tw_shift]);
     }
     __syncthreads();
   }
@@ -87,11 +88,11 @@ __device__ void fft_dif(float2* A, const float2* W, int n, int logn, bool column
 // bit-reversed order in, natural order out.
 __device__ void fft_dit_inv(float2* A, const float2* W, int n, int logn, bool columns) {
   for (int s = 1; s <= logn; ++s) {
-    const int half = 1 << (s - 1), tw_step = n >> s;
+    const int lh = s - 1, tw_shift = logn - s;
     for (int q = threadIdx.x; q < n * (n >> 1); q += blockDim.x) {
       int a0, a1, j;
-      stage_index(q, n, half, columns, &a0, &a1, &j);
-      float2 w = W[j * tw_step];
+      stage_index(q, logn, lh, columns, &a0, &a1, &j);
+      float2 w = W[j << tw_shift];
       w.y = -w.y;   // exp(+2 pi i j / (2 half))
       const float2 x0 = A[a0], t = cmul(A[a1], w);
       A[a0] = make_float2(x0.x + t.x, x0.y + t.y);

@@ -1413,7 +1413,7 @@ def main():
         line["covariance"] = channel_covariance(S, h, n)
     m.close()
     if rank == 0 and not args.no_extras:
-        # the composite workload (where the HBM target is judged) and the 2-D
+        # the composite workload (the HBM-bound configuration) and the 2-D
         # 64^2 FP64 configuration, measured in the same run
         torch.cuda.empty_cache()
         comp = composite_measure(S, args.comp_n, args.comp_k, steps=60, warmup=3, with_cpu=False)

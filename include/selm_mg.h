@@ -387,7 +387,7 @@ typedef struct {
 
 typedef struct selm_server selm_server;
 selm_status selm_server_create(size_t budget_bytes, int max_slots, selm_server** out);
-/* Continuous batching (spec served form on the batched engine): one
+/* Continuous batching (the served form on the batched engine): one
    scheduler keeps up to `max_slots` admitted requests resident and runs the
    next Euler-Maruyama step of all of them as one batched step
    (selm_batch_step over the requests' handles: per-phase graph launches

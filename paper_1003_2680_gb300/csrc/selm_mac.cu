@@ -204,6 +204,61 @@ __global__ void __launch_bounds__(kThreads) k_colour(SellDev S, int pos0, int cn
   v[row] = nv;
 }
 
+// ---- all colour passes of a small level's sweeps in one thread block --------
+// On levels of a few thousand rows a launch per class is almost all launch
+// latency.  One block of kBlockSweep threads runs `nsweeps` sweeps of every
+// class with a block barrier between classes: the same updates in the same
+// order as the per-class launches, the block's own global writes visible to
+// its threads after each barrier.
+constexpr int kBlockSweep = 1024;
+constexpr long long kBlockSweepRows = 4096;   // levels up to this many rows sweep in one block
+
+template <typename T, int NK>
+__global__ void __launch_bounds__(kBlockSweep) k_colour_block(SellDev S, const int* __restrict__ cstart,
+                                                             const int* __restrict__ csize, int ncol, int level1,
+                                                             int sweep0, int nsweeps, T* v, const T* __restrict__ b,
+                                                             T sigma, Key key,
+                                                             const unsigned long long* __restrict__ cyc) {
+  const unsigned long long c64 = NK ? *cyc : 0ull;
+  const int tid = threadIdx.x;
+  for (int sw = 0; sw < nsweeps; ++sw)
+    for (int c = 0; c < ncol; ++c) {
+      const int pos0 = cstart[c], cnt = csize[c];
+      const uint32_t c1 = (uint32_t)level1 | ((uint32_t)(c & 15) << 8) | ((uint32_t)(sweep0 + sw) << 12) |
+                          ((uint32_t)(c >> 4) << 24);
+      // warp-uniform trip count: every lane of a warp takes the shuffles
+      for (int base = tid - (tid & 31); base < cnt * kRowLanes; base += kBlockSweep) {
+        const int g = base + (tid & 31);
+        const int t = g / kRowLanes, sub = g % kRowLanes;
+        const bool valid = t < cnt;
+        const int p = pos0 + (valid ? t : 0);
+        T off = T(0);
+        if (valid) {
+          const int s = p >> 5;
+          const long long o = S.soff[s] + (p & 31);
+          const int w = S.swid[s];
+          const T* __restrict__ vv = vals<T>(S);
+          for (int e = sub; e < w; e += kRowLanes) off += vv[o + 32ll * e] * v[S.col[o + 32ll * e]];
+        }
+#pragma unroll
+        for (int m = 1; m < kRowLanes; m <<= 1) off += __shfl_xor_sync(0xffffffffu, off, m);
+        if (valid && sub == 0) {
+          const int row = S.row[p];
+          T nv = (b[row] - off) * rd_at<T>(S, p);
+          if (NK != 0) {
+            const uint4 wv = philox4x32_10(make_uint4((uint32_t)t >> 2, c1, (uint32_t)c64, (uint32_t)(c64 >> 32)),
+                                           key.k0, key.k1);
+            T gn;
+            normal_of(wv, t & 3, &gn);
+            nv += sigma * gn * rs_at<T>(S, p);
+          }
+          v[row] = nv;
+        }
+      }
+      __syncthreads();
+    }
+}
+
 // t = b - A v on every row of a class-ordered level (diagonal included);
 // kRowLanes lanes per row as in k_colour.
 template <typename T>
@@ -475,6 +530,10 @@ struct selm_mac {
     std::vector<int> cstart, csize;
     SellDev Pl, Plt;                 // transfers to / from the next coarser level
     void *v = nullptr, *b = nullptr, *t = nullptr;
+    // small levels: every class of a sweep set in one thread block
+    const int* d_cstart = nullptr;
+    const int* d_csize = nullptr;
+    bool block_sweeps = false;
   };
   std::vector<Level> lev;
   const double* Linv = nullptr;
@@ -610,6 +669,28 @@ selm_status sweep(selm_mac* h, int l, int s, double sigma, const unsigned long l
   return SELM_OK;
 }
 
+// `n` sweeps of level l from sweep index s0: one block launch on the small
+// levels, one launch per class on the others.
+template <typename T>
+selm_status sweeps(selm_mac* h, int l, int s0, int n, double sigma, const unsigned long long* cyc, cudaStream_t st) {
+  selm_mac::Level& L = h->lev[l];
+  if (n <= 0) return SELM_OK;
+  if (!L.block_sweeps) {
+    for (int s = 0; s < n; ++s) MRET(sweep<T>(h, l, s0 + s, sigma, cyc, st));
+    return SELM_OK;
+  }
+  prof::Scope ps(SELM_K_COARSE_SWEEP, st);
+  const int ncol = (int)L.cstart.size();
+  if (sigma != 0.0)
+    k_colour_block<T, 1><<<1, kBlockSweep, 0, st>>>(L.cls, L.d_cstart, L.d_csize, ncol, l + 1, s0, n, (T*)L.v,
+                                                    (const T*)L.b, (T)sigma, h->key, cyc);
+  else
+    k_colour_block<T, 0><<<1, kBlockSweep, 0, st>>>(L.cls, L.d_cstart, L.d_csize, ncol, l + 1, s0, n, (T*)L.v,
+                                                    (const T*)L.b, (T)0, h->key, cyc);
+  MCK(cudaGetLastError());
+  return SELM_OK;
+}
+
 template <typename T>
 selm_status vcycle(selm_mac* h, int l, double sigma, const unsigned long long* cyc, cudaStream_t st) {
   selm_mac::Level& L = h->lev[l];
@@ -621,7 +702,7 @@ selm_status vcycle(selm_mac* h, int l, double sigma, const unsigned long long* c
     return SELM_OK;
   }
   const int mu1 = h->d.nu_pre, mu2 = h->d.nu_post;
-  for (int s = 0; s < mu1; ++s) MRET(sweep<T>(h, l, s, sigma, cyc, st));
+  MRET(sweeps<T>(h, l, 0, mu1, sigma, cyc, st));
   selm_mac::Level& C = h->lev[l + 1];
   {
     prof::Scope ps(SELM_K_RESIDUAL, st);
@@ -641,7 +722,7 @@ selm_status vcycle(selm_mac* h, int l, double sigma, const unsigned long long* c
     k_sell_mv<T, 1><<<blocks_for(L.Pl.npos), kThreads, 0, st>>>(L.Pl, (const T*)C.v, (T*)L.v, nullptr);
     MCK(cudaGetLastError());
   }
-  for (int s = 0; s < mu2; ++s) MRET(sweep<T>(h, l, mu1 + s, sigma, cyc, st));
+  MRET(sweeps<T>(h, l, mu1, mu2, sigma, cyc, st));
   return SELM_OK;
 }
 
@@ -1029,6 +1110,11 @@ selm_status selm_mac_create(const selm_mac_desc* desc, void* stream, selm_mac** 
       CREATE_STEP(alloc(h, (size_t)L.N * h->esize, &L.t, st));
       std::vector<int> ord = class_order(plan.colours[l], &L.cstart, &L.csize);
       CREATE_STEP(upload_sell(h, make_sell(plan.ops[l], ord, true), f32, &L.cls, st));
+      if (L.N <= kBlockSweepRows) {   // small level: its sweeps run in one block
+        CREATE_STEP(upload(h, L.cstart, &L.d_cstart, st));
+        CREATE_STEP(upload(h, L.csize, &L.d_csize, st));
+        L.block_sweeps = true;
+      }
       const Csr& pl = plan.Pl[l];
       CREATE_STEP(upload_sell(h, make_sell(pl, natural_order(pl.nr), false), f32, &L.Pl, st));
       Csr plt;

@@ -276,3 +276,35 @@ def test_invalid_arguments(S):
     with pytest.raises(S.SelmError) as info:
         S.selm_mac_create(S.make_mac_desc(2, 8, 9))
     assert info.value.status == S.SELM_EINVAL
+
+
+def test_benchmark_size_properties(S):
+    """The benchmark's staggered grid (64^3 base, 8 refined rows, 1.46 M faces,
+    FP32 inner cycles), checked by properties that hold at any size: the
+    projection's output is discretely divergence-free and a fixed point of
+    the projection, and a FAC solve reaches its tolerance with A z = b (the
+    operator applied by its own kernel)."""
+    h = _handle(S, 3, 64, 8, mu=1.0, prec=S.SELM_FP32_REFINE64, projection=1, proj_tol=1e-12)
+    try:
+        nf, nc = S.selm_mac_faces(h), S.selm_mac_cells(h)
+        assert nf == 1458176 and nc == 491520
+        u = torch.randn(nf, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+        pu = torch.empty_like(u)
+        S.selm_mac_project(h, u, pu)
+        div_u, div_pu = torch.empty(nc, dtype=torch.float64, device="cuda"), torch.empty(nc, dtype=torch.float64,
+                                                                                         device="cuda")
+        S.selm_mac_divergence(h, u, div_u)
+        S.selm_mac_divergence(h, pu, div_pu)
+        assert div_pu.abs().max().item() < 1e-9 * div_u.abs().max().item()
+        ppu = torch.empty_like(u)
+        S.selm_mac_project(h, pu, ppu)
+        assert (ppu - pu).abs().max().item() < 1e-9 * pu.abs().max().item()
+        b = torch.randn(nf, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(2))
+        z = torch.zeros_like(b)
+        cycles, r = S.selm_mac_solve(h, z, b, 1e-10, 100)
+        assert r <= 1e-10 and cycles < 60
+        Az = torch.empty_like(z)
+        S.selm_mac_apply(h, z, Az)
+        assert ((Az - b).norm() / b.norm()).item() < 2e-10
+    finally:
+        S.selm_mac_destroy(h)

@@ -84,9 +84,9 @@ struct Plan {
   std::vector<int> ints;
   size_t dbl_off = 0, flt_off = 0, int_off = 0;
   std::vector<TableOffsets> toff[2][kMaxLevels];
-  size_t field_off[2][kMaxLevels][3];
+  size_t field_off[3][kMaxLevels][3];   // velocity, pressure, the chain's velocity copy
   size_t u_off = 0, xi_off = 0, bvel_off = 0, wcomb_off = 0, phi_off = 0, prhs_off = 0, red_off = 0,
-         cyc_off = 0, V_off = 0, Xs_off = 0, Fs_off = 0, eng_off[2] = {0, 0}, spec_off = 0, spec_bytes = 0;
+         cyc_off = 0, V_off = 0, Xs_off = 0, Fs_off = 0, eng_off[3] = {0, 0, 0}, spec_off = 0, spec_bytes = 0;
 };
 
 void plan_tables(const HostSystem& hs, int si, Plan* p) {
@@ -167,6 +167,11 @@ void make_plan(const selm_mg_desc& d, const Sys& vel, const Sys* pres, int esize
   }
   p->eng_off[0] = p->lay.add(kEngParamBytes);
   if (pres) p->eng_off[1] = p->lay.add(kEngParamBytes);
+  if (pres) {   // the chain's level fields and engine plan (it runs beside the solve)
+    for (int l = 0; l < vel.host.levels; ++l)
+      for (int f = 0; f < 3; ++f) p->field_off[2][l][f] = p->lay.add((size_t)vel.host.level_size(l) * esize);
+    p->eng_off[2] = p->lay.add(kEngParamBytes);
+  }
   p->red_off = p->lay.add(16 * sizeof(double));
   p->cyc_off = p->lay.add(4 * sizeof(unsigned long long));
   p->V_off = p->lay.add((size_t)d.max_particles * 3 * sizeof(double));
@@ -174,7 +179,9 @@ void make_plan(const selm_mg_desc& d, const Sys& vel, const Sys* pres, int esize
   p->Fs_off = p->lay.add((size_t)d.max_particles * 3 * sizeof(double));
 }
 
-void bind_system(Sys* s, int si, const Plan& p, char* ws) {
+// Binds system s to the tables of system si and the level fields of slot fsi
+// (fsi < 0: slot si).
+void bind_system(Sys* s, int si, const Plan& p, char* ws, int fsi = -1) {
   const HostSystem& hs = s->host;
   s->levels = hs.levels;
   s->ncomp = hs.ncomp;
@@ -228,9 +235,10 @@ void bind_system(Sys* s, int si, const Plan& p, char* ws) {
       for (int ci = 0; ci < hs.ncomp; ++ci)
         if (!coop_flow_ok(hs.lev[l][ci])) L.flow = 0;
     }
-    s->v[l] = ws + p.field_off[si][l][0];
-    s->b[l] = ws + p.field_off[si][l][1];
-    s->t[l] = ws + p.field_off[si][l][2];
+    const int f = fsi < 0 ? si : fsi;
+    s->v[l] = ws + p.field_off[f][l][0];
+    s->b[l] = ws + p.field_off[f][l][1];
+    s->t[l] = ws + p.field_off[f][l][2];
   }
 }
 
@@ -404,18 +412,20 @@ selm_status fac_cycle(selm_mg* h, Sys& s, double* z, const double* b, bool noise
 // Reads the reduction slots copied by a norm read-back issued on the copy
 // stream after h->ev_norm (the work stream may already run later launches):
 // out_b / out_r receive slots 0 / 1 (null: not wanted).  The same copy brings
-// back the grid-barrier words of both systems (red[8..11]); a timed-out wait
-// of a cooperative level launch is reported here and its words are cleared.
+// back the grid-barrier words of the systems (red[8..13]: velocity, pressure,
+// the chain's copy); a timed-out wait of a cooperative level launch is
+// reported here and its words are cleared.
 selm_status read_norms_after_event(selm_mg* h, double* out_b, double* out_r, cudaStream_t st) {
   CK(cudaStreamWaitEvent(h->xfer, h->ev_norm, 0));
-  CK(cudaMemcpyAsync(h->host_red, h->red, 12 * sizeof(double), cudaMemcpyDeviceToHost, h->xfer));
+  CK(cudaMemcpyAsync(h->host_red, h->red, 14 * sizeof(double), cudaMemcpyDeviceToHost, h->xfer));
   CK(cudaStreamSynchronize(h->xfer));
   if (out_b) *out_b = h->host_red[0];
   if (out_r) *out_r = h->host_red[1];
   const unsigned* words = (const unsigned*)(h->host_red + 8);
-  if (words[2] != 0u || words[6] != 0u) {
+  if (words[2] != 0u || words[6] != 0u || words[10] != 0u) {
     CK(cudaStreamSynchronize(st));
-    CK(cudaMemsetAsync(h->red + 8, 0, 4 * sizeof(double), st));
+    if (h->side) CK(cudaStreamSynchronize(h->side));
+    CK(cudaMemsetAsync(h->red + 8, 0, 6 * sizeof(double), st));
     CK(cudaStreamSynchronize(st));
     h->err = "a grid barrier of a cooperative level launch timed out";
     return SELM_ECUDA;
@@ -554,8 +564,9 @@ selm_status project(selm_mg* h, double* w, int* cycles, cudaStream_t st, int slo
 }
 
 selm_status chain_cycles(selm_mg* h, int ncycles, cudaStream_t st) {
+  Sys& s = h->has_chain ? h->chn : h->vel;
   for (int q = 0; q < ncycles; ++q) {
-    selm_status r = fac_cycle(h, h->vel, h->xi, nullptr, true, h->cyc + 0, st);
+    selm_status r = fac_cycle(h, s, h->xi, nullptr, true, h->cyc + 0, st);
     if (r != SELM_OK) return r;
     CK(launch_inc_u64(h->cyc + 0, st));
     h->cycle += 1;
@@ -695,7 +706,7 @@ selm_status vcycle_level(selm_mg* h, Sys& s, int level, bool noise, const unsign
 }
 
 selm_status replan_engine(selm_mg* h, int cluster, cudaStream_t st) {
-  for (Sys* sy : {&h->vel, h->has_pres ? &h->pres : (Sys*)nullptr}) {
+  for (Sys* sy : {&h->vel, h->has_pres ? &h->pres : (Sys*)nullptr, h->has_chain ? &h->chn : (Sys*)nullptr}) {
     if (!sy || !sy->eng_dev) continue;
     CK(cudaStreamSynchronize(st));   // no launch may still read the old plan
     sy->engine_cluster = cluster;
@@ -790,8 +801,13 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
     ce = cudaMemcpyAsync(h->ws + p.int_off, p.ints.data(), p.ints.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   bind_system(&h->vel, 0, p, h->ws);
   if (h->has_pres) bind_system(&h->pres, 1, p, h->ws);
-  for (int si = 0; si < 2; ++si) {
-    Sys* sy = si == 0 ? &h->vel : (h->has_pres ? &h->pres : nullptr);
+  if (h->has_pres) {
+    h->chn.host = h->vel.host;
+    bind_system(&h->chn, 0, p, h->ws, 2);
+    h->has_chain = true;
+  }
+  for (int si = 0; si < 3; ++si) {
+    Sys* sy = si == 0 ? &h->vel : si == 1 ? (h->has_pres ? &h->pres : nullptr) : (h->has_chain ? &h->chn : nullptr);
     if (!sy) continue;
     void* dp = h->ws + p.eng_off[si];
     sy->eng_dev = dp;
@@ -817,6 +833,7 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
   h->red = (double*)(h->ws + p.red_off);
   h->vel.coop_bar = (unsigned*)(h->red + 8);
   if (h->has_pres) h->pres.coop_bar = (unsigned*)(h->red + 10);
+  if (h->has_chain) h->chn.coop_bar = (unsigned*)(h->red + 12);
   h->cyc = (unsigned long long*)(h->ws + p.cyc_off);
   h->V = (double*)(h->ws + p.V_off);
   h->Xs = (double*)(h->ws + p.Xs_off);
@@ -954,8 +971,7 @@ selm_status selm_mg_set_option(selm_mg* h, int option, int value) {
     return SELM_OK;
   }
   if (option == SELM_OPT_COARSE_ENGINE) {
-    h->vel.use_engine = value != 0;
-    h->pres.use_engine = value != 0;
+    h->vel.use_engine = h->pres.use_engine = h->chn.use_engine = value != 0;
     return SELM_OK;
   }
   if (option == SELM_OPT_ENGINE_CLUSTER) {
@@ -964,8 +980,8 @@ selm_status selm_mg_set_option(selm_mg* h, int option, int value) {
   }
   if (option == SELM_OPT_LEVEL_COOP) {
     if (value < 0 || value > 2) return SELM_EINVAL;
-    h->vel.use_coop = h->pres.use_coop = value != 0;
-    h->vel.coop_flow = h->pres.coop_flow = value == 1;
+    h->vel.use_coop = h->pres.use_coop = h->chn.use_coop = value != 0;
+    h->vel.coop_flow = h->pres.coop_flow = h->chn.coop_flow = value == 1;
     return replan_engine(h, h->vel.engine_cluster, nullptr);   // the automatic first level depends on it
   }
   if (option == SELM_OPT_PRESSURE_SPECTRAL) {
@@ -975,8 +991,7 @@ selm_status selm_mg_set_option(selm_mg* h, int option, int value) {
   }
   if (option == SELM_OPT_ENGINE_LEVEL) {
     if (value < 0 || value > kMaxLevels) return SELM_EINVAL;
-    h->vel.engine_level = value;
-    h->pres.engine_level = value;
+    h->vel.engine_level = h->pres.engine_level = h->chn.engine_level = value;
     return replan_engine(h, h->vel.engine_cluster, nullptr);
   }
   return SELM_EINVAL;
@@ -1195,9 +1210,10 @@ selm_status selm_mg_step(selm_mg* h, int np, double* X, const double* F, double 
   }
   cudaStream_t st = S(stream);
   const long long nv = h->vel.lev[0].size;
-  // With the projection, the chain cycles run on the side stream beside the
-  // spread and the first projection; the velocity solve waits for them.
-  const bool overlap = h->side != nullptr && ncycles_per_step > 0;
+  // With the projection, the chain cycles run on the side stream (on the
+  // chain's own level fields) beside the spread, the first projection and the
+  // velocity solve; the combination of u and the chain state waits for them.
+  const bool overlap = h->side != nullptr && h->has_chain && ncycles_per_step > 0;
   for (int step = 0; step < nsteps; ++step) {
     bool joined = true;
     auto join = [&]() -> selm_status {
@@ -1233,11 +1249,14 @@ selm_status selm_mg_step(selm_mg* h, int np, double* X, const double* F, double 
     double rel = 0.0;
     r = project(h, h->bvel, &pc, st, 0);
     if (r != SELM_OK) return fail(r);
-    r = join();
-    if (r != SELM_OK) return r;
-    CK(cudaMemsetAsync(h->u, 0, (size_t)nv * sizeof(double), st));
+    if (cudaMemsetAsync(h->u, 0, (size_t)nv * sizeof(double), st) != cudaSuccess) {
+      h->err = cudaGetErrorString(cudaGetLastError());
+      return fail(SELM_ECUDA);
+    }
     r = fac_solve(h, h->vel, h->u, h->bvel, h->d.tol, h->d.max_cycles, &cycles, &rel, st);
     h->last_solve_cycles = cycles;
+    if (r != SELM_OK) return fail(r);
+    r = join();
     if (r != SELM_OK) return r;
     if (!overlap) {
       r = chain_cycles(h, ncycles_per_step, st);

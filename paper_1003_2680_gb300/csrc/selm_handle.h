@@ -61,6 +61,13 @@ struct selm_mg {
   int esize = 8;
   selm::Sys vel, pres;
   bool has_pres = false;
+  // The chain's copy of the velocity system: the same operators and launch
+  // plans over level fields of its own (with its own coarse-engine plan and
+  // grid-barrier words), so that the chain cycles of a step can run on the
+  // side stream while the velocity solve runs on the work stream.  Present
+  // with the side stream (has_chain).
+  selm::Sys chn;
+  bool has_chain = false;
   selm::Key key{};
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -81,8 +88,9 @@ struct selm_mg {
   double* Fs = nullptr;
   double* host_red = nullptr;  // host word for norm read-backs
   // Side stream for the chain cycles of a step, which depend only on the
-  // previous chain state: they run beside the first projection (a pressure
-  // solve) and join before the velocity solve, which shares their buffers.
+  // previous chain state: they run on the chain's own level fields beside
+  // the spread, the first projection and the velocity solve, and join before
+  // the step combines the solve with the chain state.
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // norm read-back beside the work stream: the solve enqueues its next

@@ -57,6 +57,8 @@ def test_footprint_host_only():
     nv = 2 * 128 ** 3 + 127 * 128 ** 2
     assert f32 >= nv * (3 * 4 + 4 * 8)
     assert f32 < nv * (3 * 4 * 8 / 7 + 4 * 8) + (64 << 20)
+    # with the projection, the chain keeps its own copy of the velocity level fields
+    assert fproj >= f32 + nv * 3 * 4
 
 
 @pytest.mark.parametrize("bad", [dict(dim=4, n=64), dict(dim=3, n=6, levels=3), dict(dim=2, n=64, mu=-1.0),

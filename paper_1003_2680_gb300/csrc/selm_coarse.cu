@@ -435,22 +435,11 @@ __device__ void sweeps(const View<T>& w, int level, int first_sweep, int count, 
     }
 }
 
-// Fills the table rows of the staged level L as seen by the CTA owning planes
-// [z0, z1): per row k the z bands, 1/A_ii and 1/sqrt(A_ii); per colour class
-// the geometry and the owned rank range.  (No barrier: the caller syncs.)
+// Fills the colour-class table of the staged level L as seen by the CTA
+// owning planes [z0, z1): per class the geometry and the owned rank range.
+// (No barrier: the caller syncs.)
 template <typename T>
-__device__ void stage_tables(const EngLevel<T>& L, int z0, int z1, T* tab, EngColour* col) {
-  for (int q = threadIdx.x; q < L.nz * 12; q += blockDim.x) {
-    const int k = q / 12, e = q - k * 12;
-    T val;
-    if (e < 10) {
-      val = L.zb[k * 10 + e];
-    } else {
-      const T d = L.S[(long long)k * kStencil + 22];
-      val = e == 10 ? (T)1 / d : (T)1 / tsqrt(d);
-    }
-    tab[q] = val;
-  }
+__device__ void stage_colours(const EngLevel<T>& L, int z0, int z1, EngColour* col) {
   for (int q = threadIdx.x; q < L.ncol; q += blockDim.x) {
     EngColour c;
     c.cx = q % L.mx;
@@ -503,17 +492,68 @@ __global__ void __launch_bounds__(EngThreads<T>::value, 1) k_coarse_engine(const
     for (int l = lt; l <= lc; ++l) {
       const EngLevel<T>& L = sl_at(l);
       const View<T> w = make_view(L, smem, rank, L.cluster != 0);
-      stage_tables(L, w.z0, w.z1, stab + (size_t)P->tab_row[l] * 12, col_at(l));
-      if (l < lc) {   // transfer tables to and from level l + 1
-        int* xi = reinterpret_cast<int*>(smem + P->xfi_off) + P->xf_row[l];
-        T* xw = reinterpret_cast<T*>(smem + P->xfw_off) + P->xf_row[l];
-        for (int q = threadIdx.x; q < 2 * L.nz; q += blockDim.x) {
-          xi[q] = L.pz_idx[q];
-          xw[q] = L.pz_w[q];
+      stage_colours(L, w.z0, w.z1, col_at(l));
+    }
+    // Row tables (per row k of each level: the z bands, 1/A_ii, 1/sqrt(A_ii))
+    // and transfer tables (prolongation and restriction taps along z) of all
+    // levels as one list of entries.  Each thread issues the global loads of
+    // up to kStageUnroll entries before it stores any of them, so the list
+    // costs about one memory latency instead of one per level and table.
+    {
+      // entries of level l: 12 nz row-table words, then (below the coarsest
+      // level) 2 nz prolongation taps and 4 nz_c restriction taps
+      auto level_entries = [&](int l) {
+        const EngLevel<T>& L = sl_at(l);
+        return 12 * L.nz + (l < lc ? 2 * L.nz + 4 * sl_at(l + 1).nz : 0);
+      };
+      int total = 0;
+      for (int l = lt; l <= lc; ++l) total += level_entries(l);
+      constexpr int kStageUnroll = 4;
+      for (int base = threadIdx.x; base < total; base += kStageUnroll * blockDim.x) {
+        T val[kStageUnroll];
+        int ival[kStageUnroll], kind[kStageUnroll], lev[kStageUnroll], pos[kStageUnroll];
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+          int q = base + u * (int)blockDim.x;
+          kind[u] = -1;
+          if (q >= total) continue;
+          int l = lt;
+          while (q >= level_entries(l)) {
+            q -= level_entries(l);
+            ++l;
+          }
+          const EngLevel<T>& L = sl_at(l);
+          lev[u] = l;
+          pos[u] = q;
+          if (q < 12 * L.nz) {   // row table: band, or the diagonal (inverted below)
+            const int k = q / 12, e = q - k * 12;
+            kind[u] = e < 10 ? 0 : e == 10 ? 1 : 2;
+            val[u] = e < 10 ? L.zb[k * 10 + e] : L.S[(long long)k * kStencil + 22];
+          } else {   // transfer tap, at its slot of the level's transfer rows
+            const int t = q - 12 * L.nz;
+            kind[u] = 3;
+            pos[u] = t;
+            if (t < 2 * L.nz) {
+              ival[u] = L.pz_idx[t];
+              val[u] = L.pz_w[t];
+            } else {
+              ival[u] = L.rz_idx[t - 2 * L.nz];
+              val[u] = L.rz_w[t - 2 * L.nz];
+            }
+          }
         }
-        for (int q = threadIdx.x; q < 4 * sl_at(l + 1).nz; q += blockDim.x) {
-          xi[2 * L.nz + q] = L.rz_idx[q];
-          xw[2 * L.nz + q] = L.rz_w[q];
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+          if (kind[u] < 0) continue;
+          const int l = lev[u];
+          if (kind[u] < 3) {
+            const T v = val[u];
+            stab[(size_t)P->tab_row[l] * 12 + pos[u]] =
+                kind[u] == 0 ? v : kind[u] == 1 ? (T)1 / v : (T)1 / tsqrt(v);
+          } else {
+            reinterpret_cast<int*>(smem + P->xfi_off)[P->xf_row[l] + pos[u]] = ival[u];
+            reinterpret_cast<T*>(smem + P->xfw_off)[P->xf_row[l] + pos[u]] = val[u];
+          }
         }
       }
     }

@@ -850,6 +850,12 @@ selm_status selm_mg_create(const selm_mg_desc* desc, void* stream, selm_mg** out
     ce = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    int least = 0, greatest = 0;
+    if (ce == cudaSuccess) ce = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (ce == cudaSuccess && greatest < least)
+      ce = cudaStreamCreateWithPriority(&h->prio, cudaStreamNonBlocking, greatest);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
   }
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // host tables must outlive the copies
   if (ce != cudaSuccess) {
@@ -867,8 +873,14 @@ selm_status selm_mg_destroy(selm_mg* h) {
     cudaStreamSynchronize(h->side);   // nothing of the handle's may still read the workspace
     cudaStreamDestroy(h->side);
   }
+  if (h->prio) {
+    cudaStreamSynchronize(h->prio);
+    cudaStreamDestroy(h->prio);
+  }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
   if (h->xfer) {
     cudaStreamSynchronize(h->xfer);
     cudaStreamDestroy(h->xfer);
@@ -1200,15 +1212,12 @@ selm_status selm_mg_sample(selm_mg* h, int np, const double* X, int ncycles, dou
   return SELM_OK;
 }
 
-selm_status selm_mg_step(selm_mg* h, int np, double* X, const double* F, double dt, int nsteps, int ncycles_per_step,
-                         void* stream) {
-  if (!h || nsteps < 0 || ncycles_per_step < 0 || !(dt >= 0.0) || !check_particles(h, np, X) || (np > 0 && !F))
-    return SELM_EINVAL;
-  if (np > h->d.max_particles) {
-    h->err = "np exceeds max_particles";
-    return SELM_EINVAL;
-  }
-  cudaStream_t st = S(stream);
+}  // extern "C"
+
+namespace {
+
+selm_status step_on(selm_mg* h, int np, double* X, const double* F, double dt, int nsteps, int ncycles_per_step,
+                    cudaStream_t st) {
   const long long nv = h->vel.lev[0].size;
   // With the projection, the chain cycles run on the side stream (on the
   // chain's own level fields) beside the spread, the first projection and the
@@ -1270,6 +1279,36 @@ selm_status selm_mg_step(selm_mg* h, int np, double* X, const double* F, double 
     CK(launch_em(np, h->d.dim, X, h->V, st));
   }
   return SELM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+selm_status selm_mg_step(selm_mg* h, int np, double* X, const double* F, double dt, int nsteps, int ncycles_per_step,
+                         void* stream) {
+  if (!h || nsteps < 0 || ncycles_per_step < 0 || !(dt >= 0.0) || !check_particles(h, np, X) || (np > 0 && !F))
+    return SELM_EINVAL;
+  if (np > h->d.max_particles) {
+    h->err = "np exceeds max_particles";
+    return SELM_EINVAL;
+  }
+  cudaStream_t user = S(stream);
+  // When the chain runs beside the step's main path, the main path (the
+  // critical one) runs on the handle's high-priority stream, so that the
+  // block scheduler gives it the SMs first and the chain fills what it
+  // leaves idle; the caller's stream waits for the step at the end.
+  if (!h->prio || !h->has_chain || ncycles_per_step <= 0 || nsteps <= 0)
+    return step_on(h, np, X, F, dt, nsteps, ncycles_per_step, user);
+  CK(cudaEventRecord(h->ev_in, user));
+  CK(cudaStreamWaitEvent(h->prio, h->ev_in, 0));
+  const selm_status r = step_on(h, np, X, F, dt, nsteps, ncycles_per_step, h->prio);
+  if (cudaEventRecord(h->ev_out, h->prio) != cudaSuccess || cudaStreamWaitEvent(user, h->ev_out, 0) != cudaSuccess) {
+    cudaStreamSynchronize(h->prio);
+    h->err = "joining the step's stream failed";
+    return SELM_ECUDA;
+  }
+  return r;
 }
 
 selm_status selm_mg_step_host(selm_mg* h, int np, double* X_host, const double* F_host, double dt, int nsteps,

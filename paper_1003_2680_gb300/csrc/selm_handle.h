@@ -93,6 +93,10 @@ struct selm_mg {
   // the step combines the solve with the chain state.
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // high-priority stream of the step's main path while the chain runs beside
+  // it (forked from and joined back to the caller's stream)
+  cudaStream_t prio = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // norm read-back beside the work stream: the solve enqueues its next
   // V-cycle before the copy (see fac_solve)
   cudaStream_t xfer = nullptr;

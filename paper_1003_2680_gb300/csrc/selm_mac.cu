@@ -172,36 +172,89 @@ __global__ void __launch_bounds__(kThreads) k_dot_part(long long n, const double
 // several warps on every SM.
 constexpr int kRowLanes = 4;
 
+// Programmatic dependent launch: the class passes of a sweep are launched
+// with programmatic stream serialisation, and each block lets the next pass
+// launch as soon as it starts.  Everything a pass needs that no earlier
+// pass writes -- the matrix entries of its rows (the first kPrefetch per
+// lane), its row numbers and scales, its normals (the counter word is
+// written only by launches that completed before the sweep began) -- is
+// loaded and computed before griddepcontrol.wait, which returns once the
+// previous pass has completed and its writes are visible; v and b are read
+// only after it.  The updates and their order are those of plain launches.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+constexpr int kPrefetch = 8;
+
 template <typename T, int NK>
 __global__ void __launch_bounds__(kThreads) k_colour(SellDev S, int pos0, int cnt, T* __restrict__ v,
                                                     const T* __restrict__ b, T sigma, Key key, uint32_t c1,
                                                     const unsigned long long* __restrict__ cyc) {
+  pdl_launch_dependents();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = g / kRowLanes, sub = g % kRowLanes;
   const bool valid = t < cnt;        // every lane stays for the shuffles
   const int p = pos0 + (valid ? t : 0);
-  T off = T(0);
+  const T* __restrict__ vv = vals<T>(S);
+  long long o = 0;
+  int w = 0;
+  int cidx[kPrefetch];
+  T cval[kPrefetch];
   if (valid) {
     const int s = p >> 5;
-    const long long o = S.soff[s] + (p & 31);
-    const int w = S.swid[s];
-    const T* __restrict__ vv = vals<T>(S);
-    for (int e = sub; e < w; e += kRowLanes) off += vv[o + 32ll * e] * v[S.col[o + 32ll * e]];
+    o = S.soff[s] + (p & 31);
+    w = S.swid[s];
+#pragma unroll
+    for (int q = 0; q < kPrefetch; ++q) {
+      const int e = sub + q * kRowLanes;
+      cidx[q] = e < w ? S.col[o + 32ll * e] : 0;
+      cval[q] = e < w ? vv[o + 32ll * e] : T(0);
+    }
+  }
+  int row = 0;
+  T rd = T(0), ns = T(0), rsv = T(0);
+  if (valid && sub == 0) {
+    row = S.row[p];
+    rd = rd_at<T>(S, p);
+    if (NK != 0) {
+      const unsigned long long c = *cyc;
+      const uint32_t id = NK == 1 ? (uint32_t)t : (uint32_t)row;
+      const uint4 wv = philox4x32_10(make_uint4(id >> 2, c1, (uint32_t)c, (uint32_t)(c >> 32)), key.k0, key.k1);
+      T gn;
+      normal_of(wv, (int)(id & 3), &gn);
+      ns = sigma * gn;
+      rsv = rs_at<T>(S, p);
+    }
+  }
+  pdl_wait();
+  T off = T(0);
+  if (valid) {
+#pragma unroll
+    for (int q = 0; q < kPrefetch; ++q)
+      if (sub + q * kRowLanes < w) off += cval[q] * v[cidx[q]];
+    for (int e = sub + kPrefetch * kRowLanes; e < w; e += kRowLanes) off += vv[o + 32ll * e] * v[S.col[o + 32ll * e]];
   }
 #pragma unroll
   for (int m = 1; m < kRowLanes; m <<= 1) off += __shfl_xor_sync(0xffffffffu, off, m);
   if (!valid || sub != 0) return;
-  const int row = S.row[p];
-  T nv = (b[row] - off) * rd_at<T>(S, p);
-  if (NK != 0) {
-    const unsigned long long c = *cyc;
-    const uint32_t id = NK == 1 ? (uint32_t)t : (uint32_t)row;
-    const uint4 w = philox4x32_10(make_uint4(id >> 2, c1, (uint32_t)c, (uint32_t)(c >> 32)), key.k0, key.k1);
-    T g;
-    normal_of(w, (int)(id & 3), &g);
-    nv += sigma * g * rs_at<T>(S, p);
-  }
+  T nv = (b[row] - off) * rd;
+  if (NK != 0) nv += ns * rsv;
   v[row] = nv;
+}
+
+// Launch of one class pass with programmatic stream serialisation.
+template <typename T, int NK>
+cudaError_t launch_colour(const SellDev& S, int pos0, int cnt, T* v, const T* b, T sigma, Key key, uint32_t c1,
+                          const unsigned long long* cyc, cudaStream_t st) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)std::max<long long>(1, ((long long)cnt * kRowLanes + kThreads - 1) / kThreads));
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_colour<T, NK>, S, pos0, cnt, v, b, sigma, key, c1, cyc);
 }
 
 // ---- all colour passes of a small level's sweeps in one thread block --------
@@ -659,12 +712,10 @@ selm_status sweep(selm_mac* h, int l, int s, double sigma, const unsigned long l
     const int cnt = L.csize[c];
     prof::Scope ps(SELM_K_COARSE_SWEEP, st);
     if (sigma != 0.0)
-      k_colour<T, 1><<<blocks_for((long long)cnt * kRowLanes), kThreads, 0, st>>>(L.cls, L.cstart[c], cnt, (T*)L.v, (const T*)L.b, (T)sigma,
-                                                           h->key, ctr1(l + 1, 0, (int)c, s, 0), cyc);
+      MCK((launch_colour<T, 1>(L.cls, L.cstart[c], cnt, (T*)L.v, (const T*)L.b, (T)sigma, h->key,
+                              ctr1(l + 1, 0, (int)c, s, 0), cyc, st)));
     else
-      k_colour<T, 0><<<blocks_for((long long)cnt * kRowLanes), kThreads, 0, st>>>(L.cls, L.cstart[c], cnt, (T*)L.v, (const T*)L.b, (T)0,
-                                                           h->key, 0, cyc);
-    MCK(cudaGetLastError());
+      MCK((launch_colour<T, 0>(L.cls, L.cstart[c], cnt, (T*)L.v, (const T*)L.b, (T)0, h->key, 0, cyc, st)));
   }
   return SELM_OK;
 }
@@ -748,12 +799,10 @@ selm_status correction(selm_mac* h, double sigma, const unsigned long long* cyc,
       const int cnt = h->psize[c];
       prof::Scope ps(SELM_K_FINE_SWEEP, st);
       if (sigma != 0.0)
-        k_colour<T, 2><<<blocks_for((long long)cnt * kRowLanes), kThreads, 0, st>>>(h->Apatch, h->pstart[c], cnt, (T*)h->q, (const T*)h->r,
-                                                             (T)sigma, h->key, ctr1(0, 0, (int)c, s, 2), cyc);
+        MCK((launch_colour<T, 2>(h->Apatch, h->pstart[c], cnt, (T*)h->q, (const T*)h->r, (T)sigma, h->key,
+                                ctr1(0, 0, (int)c, s, 2), cyc, st)));
       else
-        k_colour<T, 0><<<blocks_for((long long)cnt * kRowLanes), kThreads, 0, st>>>(h->Apatch, h->pstart[c], cnt, (T*)h->q, (const T*)h->r,
-                                                             (T)0, h->key, 0, cyc);
-      MCK(cudaGetLastError());
+        MCK((launch_colour<T, 0>(h->Apatch, h->pstart[c], cnt, (T*)h->q, (const T*)h->r, (T)0, h->key, 0, cyc, st)));
     }
   return SELM_OK;
 }

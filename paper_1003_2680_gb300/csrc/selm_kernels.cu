@@ -27,7 +27,15 @@
 #include "selm_internal.h"
 #include "selm_launch.h"
 #include "selm_devmath.h"
+#include "selm_pdl.h"
 #include "selm_prof.h"
+
+// Returns the error of a launch from the enclosing launcher.
+#define LTRY(call)                            \
+  do {                                        \
+    const cudaError_t e_ = (call);            \
+    if (e_ != cudaSuccess) return e_;         \
+  } while (0)
 
 namespace selm {
 
@@ -273,6 +281,7 @@ template <typename T, bool NORM>
 __global__ void __launch_bounds__(kBlock) k_outer_residual_v4(LevelDev L, RowPass rp, const double* __restrict__ z,
                                                              const double* __restrict__ b, T* __restrict__ r,
                                                              double* __restrict__ norm2) {
+  pdl_enter();
   const int segs = L.c[0].nx >> 2;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int row_all = gt / segs;
@@ -407,6 +416,7 @@ template <bool NORM>
 __global__ void __launch_bounds__(kBlock) k_outer_residual_fx(LevelDev L, RowPass rp, const double* __restrict__ z,
                                                              const double* __restrict__ b, float* __restrict__ r,
                                                              double* __restrict__ norm2) {
+  pdl_enter();
   const int segs = L.c[0].nx >> 2;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int row_all = gt / segs;
@@ -528,6 +538,7 @@ __device__ __forceinline__ double fx_widen(double f) { return f; }
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_outer_update_v4(long long n4, double* __restrict__ z,
                                                            const T* __restrict__ d) {
+  pdl_enter();
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n4) return;
   double2 a = *reinterpret_cast<double2*>(z + 4 * q);
@@ -826,6 +837,7 @@ template <typename T, bool NOISE>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? SELM_ZM_MIN_BLOCKS : 1) k_band7_rb_zm(LevelDev L, ColumnPass cp, T* __restrict__ v,
                                                        const T* __restrict__ b, int colour, int sweep, Key key,
                                                        const unsigned long long* __restrict__ cyc) {
+  pdl_enter();
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= cp.start[L.ncomp]) return;
   int ci = 0;
@@ -910,6 +922,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? SELM_ZM_MIN_BLOCKS : 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_galerkin_residual_zm(LevelDev L, ColumnPass cp, const T* __restrict__ v,
                                                                 const T* __restrict__ b, T* __restrict__ t) {
+  pdl_enter();
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= cp.start[L.ncomp]) return;
   int ci = 0;
@@ -1018,6 +1031,7 @@ template <typename T, bool NOISE>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? SELM_ZM_MIN_BLOCKS : 1) k_fine_colour_zm(LevelDev L, ColumnPass cp, T* __restrict__ v,
                                                           const T* __restrict__ b, int colour, int sweep, Key key,
                                                           const unsigned long long* __restrict__ cyc) {
+  pdl_enter();
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= cp.start[L.ncomp]) return;
   fine_colour_zm_item<T, NOISE, false>(L, cp, v, b, colour, sweep, key, NOISE ? *cyc : 0ull, g);
@@ -1100,6 +1114,7 @@ __device__ __forceinline__ void fine_residual_zm_item(const LevelDev& L, const C
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_fine_residual_zm(LevelDev L, ColumnPass cp, const T* __restrict__ v,
                                                             const T* __restrict__ b, T* __restrict__ t) {
+  pdl_enter();
   fine_residual_zm_item<T, false>(L, cp, v, b, t, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -1108,6 +1123,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_residual_zm(LevelDev L, ColumnP
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_band7_residual_zm(LevelDev L, ColumnPass cp, const T* __restrict__ v,
                                                              const T* __restrict__ b, T* __restrict__ t) {
+  pdl_enter();
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= cp.start[L.ncomp]) return;
   int ci = 0;
@@ -1311,6 +1327,7 @@ template <typename T, bool NOISE, int CX>
 __global__ void __launch_bounds__(kBlock) k_coarse_colour_v8(LevelDev L, ColourPass cp, ColumnPass sp,
                                                             T* __restrict__ v, const T* __restrict__ b, int sweep,
                                                             Key key, const unsigned long long* __restrict__ cyc) {
+  pdl_enter();
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= sp.start[L.ncomp]) return;
   coarse_colour_v8_item<T, NOISE, CX, false>(L, cp, sp, v, b, sweep, key, NOISE ? *cyc : 0ull, g);
@@ -1487,6 +1504,7 @@ __device__ __forceinline__ void restrict_seg4(const LevelDev& Lf, const LevelDev
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_restrict_v4(LevelDev Lf, LevelDev Lc, RowPass rp, const T* __restrict__ t,
                                                        T* __restrict__ bc) {
+  pdl_enter();
   restrict_seg4<T, false>(Lf, Lc, rp, t, bc, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -1620,6 +1638,7 @@ __device__ __forceinline__ void prolong_seg8(const LevelDev& Lf, const LevelDev&
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_prolong_v8(LevelDev Lf, LevelDev Lc, RowPass rp, T* __restrict__ v,
                                                       const T* __restrict__ vc) {
+  pdl_enter();
   prolong_seg8<T, false>(Lf, Lc, rp, v, vc, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -3096,9 +3115,9 @@ cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool n
     for (int colour = 0; colour < 2; ++colour) {
       prof::Scope ps(SELM_K_FINE_SWEEP, st);
       if (noise)
-        k_fine_colour_zm<T, true><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
+        LTRY(launch_pdl(k_fine_colour_zm<T, true>, grid_for(items), kBlock, st, L, cp, v, b, colour, sweep, key, cyc));
       else
-        k_fine_colour_zm<T, false><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
+        LTRY(launch_pdl(k_fine_colour_zm<T, false>, grid_for(items), kBlock, st, L, cp, v, b, colour, sweep, key, cyc));
     }
     return cudaGetLastError();
   }
@@ -3134,9 +3153,9 @@ cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool n
     for (int colour = 0; colour < 2; ++colour) {
       prof::Scope ps(SELM_K_COARSE_SWEEP, st);
       if (noise)
-        k_band7_rb_zm<T, true><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
+        LTRY(launch_pdl(k_band7_rb_zm<T, true>, grid_for(items), kBlock, st, L, cp, v, b, colour, sweep, key, cyc));
       else
-        k_band7_rb_zm<T, false><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, colour, sweep, key, cyc);
+        LTRY(launch_pdl(k_band7_rb_zm<T, false>, grid_for(items), kBlock, st, L, cp, v, b, colour, sweep, key, cyc));
     }
     return cudaGetLastError();
   }
@@ -3177,13 +3196,13 @@ cudaError_t launch_smooth(const LevelDev& L, T* v, const T* b, int sweep, bool n
       sp.start[L.ncomp] = items;
       const int cx = q % 2;   // every component has x modulus 2
       if (noise && cx == 0)
-        k_coarse_colour_v8<T, true, 0><<<grid_for(items), kBlock, 0, st>>>(L, cp, sp, v, b, sweep, key, cyc);
+        LTRY(launch_pdl(k_coarse_colour_v8<T, true, 0>, grid_for(items), kBlock, st, L, cp, sp, v, b, sweep, key, cyc));
       else if (noise)
-        k_coarse_colour_v8<T, true, 1><<<grid_for(items), kBlock, 0, st>>>(L, cp, sp, v, b, sweep, key, cyc);
+        LTRY(launch_pdl(k_coarse_colour_v8<T, true, 1>, grid_for(items), kBlock, st, L, cp, sp, v, b, sweep, key, cyc));
       else if (cx == 0)
-        k_coarse_colour_v8<T, false, 0><<<grid_for(items), kBlock, 0, st>>>(L, cp, sp, v, b, sweep, key, cyc);
+        LTRY(launch_pdl(k_coarse_colour_v8<T, false, 0>, grid_for(items), kBlock, st, L, cp, sp, v, b, sweep, key, cyc));
       else
-        k_coarse_colour_v8<T, false, 1><<<grid_for(items), kBlock, 0, st>>>(L, cp, sp, v, b, sweep, key, cyc);
+        LTRY(launch_pdl(k_coarse_colour_v8<T, false, 1>, grid_for(items), kBlock, st, L, cp, sp, v, b, sweep, key, cyc));
       continue;
     }
     if (noise)
@@ -3200,7 +3219,7 @@ cudaError_t launch_residual(const LevelDev& L, const T* v, const T* b, T* t, cud
   if (L.level == 0 && L.c[0].nx % 8 == 0) {
     ColumnPass cp{};
     const long long items = fine_column_pass(L, &cp);
-    k_fine_residual_zm<T><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, t);
+    LTRY(launch_pdl(k_fine_residual_zm<T>, grid_for(items), kBlock, st, L, cp, v, b, t));
     return cudaGetLastError();
   }
   if (L.rb && L.c[0].nx % 8 == 0) {
@@ -3212,7 +3231,7 @@ cudaError_t launch_residual(const LevelDev& L, const T* v, const T* b, T* t, cud
       items += (long long)L.c[ci].ny * (L.c[ci].nx >> 3) * ((L.c[ci].nz + cp.kc - 1) / cp.kc);
     }
     cp.start[L.ncomp] = items;
-    k_band7_residual_zm<T><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, t);
+    LTRY(launch_pdl(k_band7_residual_zm<T>, grid_for(items), kBlock, st, L, cp, v, b, t));
     return cudaGetLastError();
   }
   bool four = L.level >= 1 && !L.rb;
@@ -3227,7 +3246,7 @@ cudaError_t launch_residual(const LevelDev& L, const T* v, const T* b, T* t, cud
       items += (long long)L.c[ci].ny * (L.c[ci].nx >> 2) * ((L.c[ci].nz + cp.kc - 1) / cp.kc);
     }
     cp.start[L.ncomp] = items;
-    k_galerkin_residual_zm<T><<<grid_for(items), kBlock, 0, st>>>(L, cp, v, b, t);
+    LTRY(launch_pdl(k_galerkin_residual_zm<T>, grid_for(items), kBlock, st, L, cp, v, b, t));
     return cudaGetLastError();
   }
   k_residual<T><<<grid_for(L.size), kBlock, 0, st>>>(L, v, b, t);
@@ -3248,7 +3267,7 @@ cudaError_t launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* t, 
       rows += Lc.c[ci].ny * Lc.c[ci].nz;
     }
     rp.rstart[Lc.ncomp] = rows;
-    k_restrict_v4<T><<<grid_for((long long)rows * (Lc.c[0].nx >> 2)), kBlock, 0, st>>>(Lf, Lc, rp, t, bc);
+    LTRY(launch_pdl(k_restrict_v4<T>, grid_for((long long)rows * (Lc.c[0].nx >> 2)), kBlock, st, Lf, Lc, rp, t, bc));
     return cudaGetLastError();
   }
   k_restrict<T><<<grid_for(Lc.size), kBlock, 0, st>>>(Lf, Lc, t, bc);
@@ -3266,7 +3285,7 @@ cudaError_t launch_prolong(const LevelDev& Lf, const LevelDev& Lc, T* v, const T
       rows += Lf.c[ci].ny * Lf.c[ci].nz;
     }
     rp.rstart[Lf.ncomp] = rows;
-    k_prolong_v8<T><<<grid_for((long long)rows * (Lf.c[0].nx >> 3)), kBlock, 0, st>>>(Lf, Lc, rp, v, vc);
+    LTRY(launch_pdl(k_prolong_v8<T>, grid_for((long long)rows * (Lf.c[0].nx >> 3)), kBlock, st, Lf, Lc, rp, v, vc));
     return cudaGetLastError();
   }
   k_prolong<T><<<grid_for(Lf.size), kBlock, 0, st>>>(Lf, Lc, v, vc);
@@ -3405,19 +3424,19 @@ cudaError_t launch_outer_residual(const LevelDev& L0, const double* z, const dou
       const bool aligned = ((uintptr_t)r & 15u) == 0 && L0.c[L0.ncomp - 1].off % 4 == 0 &&
                            (L0.ncomp == 1 || L0.c[1].off % 4 == 0);
       if (!aligned && norm2)
-        k_outer_residual_v4<T, true><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
+        LTRY(launch_pdl(k_outer_residual_v4<T, true>, grid_for(nt), kBlock, st, L0, rp, z, b, r, norm2));
       else if (!aligned)
-        k_outer_residual_v4<T, false><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
+        LTRY(launch_pdl(k_outer_residual_v4<T, false>, grid_for(nt), kBlock, st, L0, rp, z, b, r, norm2));
       else if (norm2)
-        k_outer_residual_fx<true><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
+        LTRY(launch_pdl(k_outer_residual_fx<true>, grid_for(nt), kBlock, st, L0, rp, z, b, r, norm2));
       else
-        k_outer_residual_fx<false><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
+        LTRY(launch_pdl(k_outer_residual_fx<false>, grid_for(nt), kBlock, st, L0, rp, z, b, r, norm2));
       return cudaGetLastError();
     }
     if (norm2)
-      k_outer_residual_v4<T, true><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
+      LTRY(launch_pdl(k_outer_residual_v4<T, true>, grid_for(nt), kBlock, st, L0, rp, z, b, r, norm2));
     else
-      k_outer_residual_v4<T, false><<<grid_for(nt), kBlock, 0, st>>>(L0, rp, z, b, r, norm2);
+      LTRY(launch_pdl(k_outer_residual_v4<T, false>, grid_for(nt), kBlock, st, L0, rp, z, b, r, norm2));
     return cudaGetLastError();
   }
   k_outer_residual<T><<<grid_for(L0.size), kBlock, 0, st>>>(L0, z, b, r, norm2);
@@ -3428,7 +3447,7 @@ template <typename T>
 cudaError_t launch_outer_update(long long n, double* z, const T* d, cudaStream_t st) {
   prof::Scope ps(SELM_K_OUTER_UPDATE, st);
   if (n % 4 == 0) {
-    k_outer_update_v4<T><<<grid_for(n / 4), kBlock, 0, st>>>(n / 4, z, d);
+    LTRY(launch_pdl(k_outer_update_v4<T>, grid_for(n / 4), kBlock, st, n / 4, z, d));
     return cudaGetLastError();
   }
   k_outer_update<T><<<grid_for(n), kBlock, 0, st>>>(n, z, d);

@@ -30,6 +30,7 @@
 #include "selm_internal.h"
 #include "selm_launch.h"
 #include "selm_mac.h"
+#include "selm_pdl.h"
 #include "selm_prof.h"
 
 namespace selm {
@@ -181,8 +182,6 @@ constexpr int kRowLanes = 4;
 // loaded and computed before griddepcontrol.wait, which returns once the
 // previous pass has completed and its writes are visible; v and b are read
 // only after it.  The updates and their order are those of plain launches.
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 constexpr int kPrefetch = 8;
 
 template <typename T, int NK>
@@ -245,16 +244,8 @@ __global__ void __launch_bounds__(kThreads) k_colour(SellDev S, int pos0, int cn
 template <typename T, int NK>
 cudaError_t launch_colour(const SellDev& S, int pos0, int cnt, T* v, const T* b, T sigma, Key key, uint32_t c1,
                           const unsigned long long* cyc, cudaStream_t st) {
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)std::max<long long>(1, ((long long)cnt * kRowLanes + kThreads - 1) / kThreads));
-  cfg.blockDim = dim3(kThreads);
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_colour<T, NK>, S, pos0, cnt, v, b, sigma, key, c1, cyc);
+  const unsigned grid = (unsigned)std::max<long long>(1, ((long long)cnt * kRowLanes + kThreads - 1) / kThreads);
+  return launch_pdl(k_colour<T, NK>, grid, kThreads, st, S, pos0, cnt, v, b, sigma, key, c1, cyc);
 }
 
 // ---- all colour passes of a small level's sweeps in one thread block --------

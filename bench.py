@@ -280,7 +280,7 @@ def measured_peaks():
 
 # Sources that define the kernels of the uniform-grid path (the profiled ones).
 PROFILED_SOURCES = ["selm_kernels.cu", "selm_coarse.cu", "selm_coarse.h", "selm_devmath.h", "selm_internal.h",
-                    "selm_launch.h"]
+                    "selm_launch.h", "selm_pdl.h"]
 
 
 # The composite-grid kernels add their own source to those.

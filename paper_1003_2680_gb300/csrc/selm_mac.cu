@@ -252,55 +252,157 @@ cudaError_t launch_colour(const SellDev& S, int pos0, int cnt, T* v, const T* b,
 // On levels of a few thousand rows a launch per class is almost all launch
 // latency.  One block of kBlockSweep threads runs `nsweeps` sweeps of every
 // class with a block barrier between classes: the same updates in the same
-// order as the per-class launches, the block's own global writes visible to
-// its threads after each barrier.
+// order as the per-class launches.  The level's v and b live in shared
+// memory for the whole launch (v is written back at the end), and each
+// thread loads the static part of its row lane for the next class -- matrix
+// entries, row number, scales and normal -- before the barrier that ends the
+// current class, so a class pass costs the barrier, the shared-memory
+// gathers and the row's arithmetic.
 constexpr int kBlockSweep = 1024;
 constexpr long long kBlockSweepRows = 4096;   // levels up to this many rows sweep in one block
+
+template <typename T>
+struct BlockPrefetch {
+  static constexpr int value = sizeof(T) == 4 ? 4 : 2;
+};
+
+// Static part of one row lane of a class pass.
+template <typename T>
+struct RowLane {
+  bool valid;
+  int sub, row, w;
+  long long o;
+  int cidx[BlockPrefetch<T>::value];
+  T cval[BlockPrefetch<T>::value];
+  T rd, ns, rsv;
+};
+
+template <typename T, int NK>
+__device__ __forceinline__ void row_lane_load(const SellDev& S, int g, int pos0, int cnt, uint32_t c1, T sigma,
+                                              Key key, unsigned long long c64, RowLane<T>& k) {
+  constexpr int P = BlockPrefetch<T>::value;
+  const int t = g / kRowLanes;
+  k.sub = g % kRowLanes;
+  k.valid = t < cnt;
+  k.w = 0;
+  k.o = 0;
+  k.row = 0;
+  k.rd = k.ns = k.rsv = T(0);
+  const int p = pos0 + (k.valid ? t : 0);
+  if (k.valid) {
+    const int s = p >> 5;
+    k.o = S.soff[s] + (p & 31);
+    k.w = S.swid[s];
+    const T* __restrict__ vv = vals<T>(S);
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int e = k.sub + q * kRowLanes;
+      k.cidx[q] = e < k.w ? S.col[k.o + 32ll * e] : 0;
+      k.cval[q] = e < k.w ? vv[k.o + 32ll * e] : T(0);
+    }
+    if (k.sub == 0) {
+      k.row = S.row[p];
+      k.rd = rd_at<T>(S, p);
+      if (NK != 0) {
+        const uint4 wv = philox4x32_10(make_uint4((uint32_t)t >> 2, c1, (uint32_t)c64, (uint32_t)(c64 >> 32)),
+                                       key.k0, key.k1);
+        T gn;
+        normal_of(wv, t & 3, &gn);
+        k.ns = sigma * gn;
+        k.rsv = rs_at<T>(S, p);
+      }
+    }
+  }
+}
+
+// The update of a loaded row lane from the shared v and b (the whole warp
+// calls it: every lane takes the shuffles).
+template <typename T, int NK>
+__device__ __forceinline__ void row_lane_apply(const SellDev& S, const RowLane<T>& k, T* vs, const T* bs) {
+  constexpr int P = BlockPrefetch<T>::value;
+  T off = T(0);
+  if (k.valid) {
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+      if (k.sub + q * kRowLanes < k.w) off += k.cval[q] * vs[k.cidx[q]];
+    const T* __restrict__ vv = vals<T>(S);
+    for (int e = k.sub + P * kRowLanes; e < k.w; e += kRowLanes) off += vv[k.o + 32ll * e] * vs[S.col[k.o + 32ll * e]];
+  }
+#pragma unroll
+  for (int m = 1; m < kRowLanes; m <<= 1) off += __shfl_xor_sync(0xffffffffu, off, m);
+  if (k.valid && k.sub == 0) {
+    T nv = (bs[k.row] - off) * k.rd;
+    if (NK != 0) nv += k.ns * k.rsv;
+    vs[k.row] = nv;
+  }
+}
+
+__host__ __device__ constexpr uint32_t block_ctr1(int level1, int c, int sweep) {
+  return (uint32_t)level1 | ((uint32_t)(c & 15) << 8) | ((uint32_t)sweep << 12) | ((uint32_t)(c >> 4) << 24);
+}
+
+template <typename T>
+size_t block_sweep_smem(long long N, int ncol) {
+  return (size_t)(2 * N) * sizeof(T) + (size_t)(2 * ncol) * sizeof(int);
+}
 
 template <typename T, int NK>
 __global__ void __launch_bounds__(kBlockSweep) k_colour_block(SellDev S, const int* __restrict__ cstart,
                                                              const int* __restrict__ csize, int ncol, int level1,
-                                                             int sweep0, int nsweeps, T* v, const T* __restrict__ b,
-                                                             T sigma, Key key,
+                                                             int sweep0, int nsweeps, int N, T* v,
+                                                             const T* __restrict__ b, T sigma, Key key,
                                                              const unsigned long long* __restrict__ cyc) {
-  const unsigned long long c64 = NK ? *cyc : 0ull;
+  extern __shared__ __align__(16) unsigned char block_smem[];
+  T* vs = reinterpret_cast<T*>(block_smem);
+  T* bs = vs + N;
+  int* cs = reinterpret_cast<int*>(bs + N);
+  int* cz = cs + ncol;
   const int tid = threadIdx.x;
-  for (int sw = 0; sw < nsweeps; ++sw)
-    for (int c = 0; c < ncol; ++c) {
-      const int pos0 = cstart[c], cnt = csize[c];
-      const uint32_t c1 = (uint32_t)level1 | ((uint32_t)(c & 15) << 8) | ((uint32_t)(sweep0 + sw) << 12) |
-                          ((uint32_t)(c >> 4) << 24);
-      // warp-uniform trip count: every lane of a warp takes the shuffles
-      for (int base = tid - (tid & 31); base < cnt * kRowLanes; base += kBlockSweep) {
-        const int g = base + (tid & 31);
-        const int t = g / kRowLanes, sub = g % kRowLanes;
-        const bool valid = t < cnt;
-        const int p = pos0 + (valid ? t : 0);
-        T off = T(0);
-        if (valid) {
-          const int s = p >> 5;
-          const long long o = S.soff[s] + (p & 31);
-          const int w = S.swid[s];
-          const T* __restrict__ vv = vals<T>(S);
-          for (int e = sub; e < w; e += kRowLanes) off += vv[o + 32ll * e] * v[S.col[o + 32ll * e]];
-        }
-#pragma unroll
-        for (int m = 1; m < kRowLanes; m <<= 1) off += __shfl_xor_sync(0xffffffffu, off, m);
-        if (valid && sub == 0) {
-          const int row = S.row[p];
-          T nv = (b[row] - off) * rd_at<T>(S, p);
-          if (NK != 0) {
-            const uint4 wv = philox4x32_10(make_uint4((uint32_t)t >> 2, c1, (uint32_t)c64, (uint32_t)(c64 >> 32)),
-                                           key.k0, key.k1);
-            T gn;
-            normal_of(wv, t & 3, &gn);
-            nv += sigma * gn * rs_at<T>(S, p);
-          }
-          v[row] = nv;
-        }
-      }
-      __syncthreads();
+  const int wbase = tid - (tid & 31);   // warp-uniform lane-task base
+  for (int i = tid; i < N; i += kBlockSweep) {
+    vs[i] = v[i];
+    bs[i] = b[i];
+  }
+  for (int i = tid; i < ncol; i += kBlockSweep) {
+    cs[i] = cstart[i];
+    cz[i] = csize[i];
+  }
+  const unsigned long long c64 = NK ? *cyc : 0ull;
+  __syncthreads();
+  const int npass = nsweeps * ncol;
+  RowLane<T> k;
+  if (npass > 0) row_lane_load<T, NK>(S, wbase + (tid & 31), cs[0], cz[0], block_ctr1(level1, 0, sweep0), sigma, key,
+                                      c64, k);
+  for (int q = 0; q < npass; ++q) {
+    const int sw = q / ncol, c = q - sw * ncol;
+    const int pos0 = cs[c], cnt = cz[c];
+    const uint32_t c1 = block_ctr1(level1, c, sweep0 + sw);
+    if (wbase < cnt * kRowLanes) row_lane_apply<T, NK>(S, k, vs, bs);
+    // classes of more than kBlockSweep / kRowLanes rows: the further lanes
+    for (int base = wbase + kBlockSweep; base < cnt * kRowLanes; base += kBlockSweep) {
+      RowLane<T> x;
+      row_lane_load<T, NK>(S, base + (tid & 31), pos0, cnt, c1, sigma, key, c64, x);
+      row_lane_apply<T, NK>(S, x, vs, bs);
     }
+    if (q + 1 < npass) {   // the next class's static data, before the barrier
+      const int sw2 = (q + 1) / ncol, c2 = (q + 1) - sw2 * ncol;
+      row_lane_load<T, NK>(S, wbase + (tid & 31), cs[c2], cz[c2], block_ctr1(level1, c2, sweep0 + sw2), sigma, key,
+                           c64, k);
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < N; i += kBlockSweep) v[i] = vs[i];
+}
+
+// Lets both noise variants of the block sweep take `bytes` of dynamic shared
+// memory (above the 48 KB default).
+template <typename T>
+cudaError_t allow_block_smem(size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_colour_block<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_colour_block<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return e;
 }
 
 // t = b - A v on every row of a class-ordered level (diagonal included);
@@ -723,12 +825,13 @@ selm_status sweeps(selm_mac* h, int l, int s0, int n, double sigma, const unsign
   }
   prof::Scope ps(SELM_K_COARSE_SWEEP, st);
   const int ncol = (int)L.cstart.size();
+  const size_t smem = block_sweep_smem<T>(L.N, ncol);
   if (sigma != 0.0)
-    k_colour_block<T, 1><<<1, kBlockSweep, 0, st>>>(L.cls, L.d_cstart, L.d_csize, ncol, l + 1, s0, n, (T*)L.v,
-                                                    (const T*)L.b, (T)sigma, h->key, cyc);
+    k_colour_block<T, 1><<<1, kBlockSweep, smem, st>>>(L.cls, L.d_cstart, L.d_csize, ncol, l + 1, s0, n, (int)L.N,
+                                                       (T*)L.v, (const T*)L.b, (T)sigma, h->key, cyc);
   else
-    k_colour_block<T, 0><<<1, kBlockSweep, 0, st>>>(L.cls, L.d_cstart, L.d_csize, ncol, l + 1, s0, n, (T*)L.v,
-                                                    (const T*)L.b, (T)0, h->key, cyc);
+    k_colour_block<T, 0><<<1, kBlockSweep, smem, st>>>(L.cls, L.d_cstart, L.d_csize, ncol, l + 1, s0, n, (int)L.N,
+                                                       (T*)L.v, (const T*)L.b, (T)0, h->key, cyc);
   MCK(cudaGetLastError());
   return SELM_OK;
 }
@@ -1153,6 +1256,13 @@ selm_status selm_mac_create(const selm_mac_desc* desc, void* stream, selm_mac** 
       if (L.N <= kBlockSweepRows) {   // small level: its sweeps run in one block
         CREATE_STEP(upload(h, L.cstart, &L.d_cstart, st));
         CREATE_STEP(upload(h, L.csize, &L.d_csize, st));
+        const int ncol = (int)L.cstart.size();
+        const cudaError_t ce = f32 ? allow_block_smem<float>(block_sweep_smem<float>(L.N, ncol))
+                                   : allow_block_smem<double>(block_sweep_smem<double>(L.N, ncol));
+        if (ce != cudaSuccess) {
+          h->err = std::string("block sweep shared memory: ") + cudaGetErrorString(ce);
+          return fail(SELM_ECUDA);
+        }
         L.block_sweeps = true;
       }
       const Csr& pl = plan.Pl[l];

@@ -431,34 +431,47 @@ __global__ void __launch_bounds__(kThreads) k_cls_resid(SellDev S, const T* __re
 // Exact draw on the coarsest level (FP64): with A = L L^T,
 // v = L^-T (L^-1 b + sigma n), n ~ N(0, I): mean A^-1 b, covariance
 // sigma^2 A^-1.  One block; y in shared memory.
+// Coarsest level, the exact draw: v = L^-T (L^-1 b + sigma n) with A_c = L L^T
+// in FP64, in two launches spread over the GPU.  Forward: one warp per row i
+// of L^-1 b (lanes stride over j <= i, then a warp sum), the row's normal
+// added by lane 0.  Backward: one warp per row i of L^-T, read from the
+// transposed copy of L^-1 so that the lanes' loads are consecutive.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_coarsest(const double* __restrict__ Linv, int m, T* __restrict__ v,
-                                                  const T* __restrict__ b, double sigma, Key key, uint32_t c1,
-                                                  const unsigned long long* __restrict__ cyc) {
-  extern __shared__ double y[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i < m; i += nw) {           // y_i = sum_{j <= i} Linv_ij b_j
-    double a = 0.0;
-    for (int j = lane; j <= i; j += 32) a += Linv[(size_t)i * m + j] * (double)b[j];
-    a = warp_sum(a);
-    if (lane == 0) {
-      if (sigma != 0.0) {
-        const unsigned long long c = *cyc;
-        const uint4 w = philox4x32_10(make_uint4((uint32_t)i >> 2, c1, (uint32_t)c, (uint32_t)(c >> 32)), key.k0,
-                                      key.k1);
-        double g;
-        normal_of(w, i & 3, &g);
-        a += sigma * g;
-      }
-      y[i] = a;
+__global__ void __launch_bounds__(kThreads) k_coarsest_fwd(const double* __restrict__ Linv, int m,
+                                                          const T* __restrict__ b, double* __restrict__ y,
+                                                          double sigma, Key key, uint32_t c1,
+                                                          const unsigned long long* __restrict__ cyc) {
+  pdl_enter();
+  const int lane = threadIdx.x & 31;
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (i >= m) return;   // the whole warp
+  double a = 0.0;
+  for (int j = lane; j <= i; j += 32) a += Linv[(size_t)i * m + j] * (double)b[j];
+  a = warp_sum(a);
+  if (lane == 0) {
+    if (sigma != 0.0) {
+      const unsigned long long c = *cyc;
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)i >> 2, c1, (uint32_t)c, (uint32_t)(c >> 32)), key.k0,
+                                    key.k1);
+      double g;
+      normal_of(w, i & 3, &g);
+      a += sigma * g;
     }
+    y[i] = a;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {   // v_i = sum_{j >= i} Linv_ji y_j
-    double a = 0.0;
-    for (int j = i; j < m; ++j) a += Linv[(size_t)j * m + i] * y[j];
-    v[i] = (T)a;
-  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_coarsest_bwd(const double* __restrict__ LinvT, int m,
+                                                          const double* __restrict__ y, T* __restrict__ v) {
+  pdl_enter();
+  const int lane = threadIdx.x & 31;
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (i >= m) return;   // the whole warp
+  double a = 0.0;
+  for (int j = i + lane; j < m; j += 32) a += LinvT[(size_t)i * m + j] * y[j];
+  a = warp_sum(a);
+  if (lane == 0) v[i] = (T)a;
 }
 
 template <typename T>
@@ -683,6 +696,8 @@ struct selm_mac {
   };
   std::vector<Level> lev;
   const double* Linv = nullptr;
+  const double* LinvT = nullptr;     // its transpose (rows of L^-T)
+  double* ycoarse = nullptr;         // L^-1 b (+ noise) of the coarsest draw
   int mc = 0;
   SellDev D, G, S;                   // divergence, gradient, diag(vol) D G (FP64)
   const double* minv = nullptr;      // 1 / diag(S)
@@ -841,9 +856,10 @@ selm_status vcycle(selm_mac* h, int l, double sigma, const unsigned long long* c
   selm_mac::Level& L = h->lev[l];
   if (l == h->levels - 1) {
     prof::Scope ps(SELM_K_COARSEST, st);
-    k_coarsest<T><<<1, 1024, (size_t)h->mc * sizeof(double), st>>>(h->Linv, h->mc, (T*)L.v, (const T*)L.b, sigma,
-                                                                   h->key, ctr1(l + 1, 0, 0, 0, 1), cyc);
-    MCK(cudaGetLastError());
+    const unsigned grid = (unsigned)(((long long)h->mc * 32 + kThreads - 1) / kThreads);
+    MCK((launch_pdl(k_coarsest_fwd<T>, grid, kThreads, st, h->Linv, h->mc, (const T*)L.b, h->ycoarse, sigma, h->key,
+                    ctr1(l + 1, 0, 0, 0, 1), cyc)));
+    MCK((launch_pdl(k_coarsest_bwd<T>, grid, kThreads, st, h->LinvT, h->mc, (const double*)h->ycoarse, (T*)L.v)));
     return SELM_OK;
   }
   const int mu1 = h->d.nu_pre, mu2 = h->d.nu_post;
@@ -1288,16 +1304,12 @@ selm_status selm_mac_create(const selm_mac_desc* desc, void* stream, selm_mac** 
   }
   h->mc = plan.ops.back().nr;
   CREATE_STEP(upload(h, plan.Linv, &h->Linv, st));
-  if ((size_t)h->mc * sizeof(double) > 48 * 1024) {
-    const int bytes = h->mc * (int)sizeof(double);
-    if ((f32 ? cudaFuncSetAttribute(k_coarsest<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-             : cudaFuncSetAttribute(k_coarsest<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      h->err = "coarsest level too large for shared memory";
-      return fail(SELM_EINVAL);
-    }
-  }
+  // (the host copy lives to the end of the set-up, like the plan's own arrays)
+  std::vector<double> linv_t((size_t)h->mc * h->mc);
+  for (int i = 0; i < h->mc; ++i)
+    for (int j = 0; j < h->mc; ++j) linv_t[(size_t)j * h->mc + i] = plan.Linv[(size_t)i * h->mc + j];
+  CREATE_STEP(upload(h, linv_t, &h->LinvT, st));
+  CREATE_STEP(alloc(h, (size_t)h->mc * sizeof(double), (void**)&h->ycoarse, st));
   CREATE_STEP(upload_sell(h, make_sell(plan.D, natural_order(plan.D.nr), false), false, &h->D, st));
   CREATE_STEP(upload_sell(h, make_sell(plan.G, natural_order(plan.G.nr), false), false, &h->G, st));
   CREATE_STEP(upload_sell(h, make_sell(plan.S, natural_order(plan.S.nr), false), false, &h->S, st));

@@ -489,10 +489,26 @@ __global__ void __launch_bounds__(kThreads) k_scale(long long n, const double* _
 }
 
 // Conjugate gradients (Jacobi preconditioned) on diag(vol) L phi = rhs, the
-// scalars kept on the device: sc[0] = r.z, sc[1] = p.q, sc[2] = new r.z,
-// sc[3] = r.r.
+// scalars kept on the device: sc[0], sc[1] = r.z of even / odd iterations,
+// sc[2] = the starting r.z, sc[3] = r.r.  An iteration is three launches
+// (programmatic dependent launches): q = S p with the partial sums of p.q;
+// the update of x, r, z with the partial sums of r.z and r.r; the new
+// direction.  Each block of the second and third launch sums the previous
+// launch's partials itself, in the order of k_reduce, so every block holds
+// the same alpha and beta.
+__device__ double block_total(const double* __restrict__ part, int nb) {
+  __shared__ double tot;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) a += part[i];
+  a = block_sum(a);
+  if (threadIdx.x == 0) tot = a;
+  __syncthreads();
+  return tot;
+}
+
 __global__ void __launch_bounds__(kThreads) k_cg_mv(SellDev S, const double* __restrict__ p, double* __restrict__ q,
                                                    double* __restrict__ part) {
+  pdl_enter();
   double acc = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.npos; i += gridDim.x * blockDim.x) {
     const int r = S.row[i];
@@ -505,12 +521,15 @@ __global__ void __launch_bounds__(kThreads) k_cg_mv(SellDev S, const double* __r
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-__global__ void __launch_bounds__(kThreads) k_cg_update(long long n, const double* __restrict__ sc,
+__global__ void __launch_bounds__(kThreads) k_cg_update(long long n, int nb, const double* __restrict__ part_pq,
+                                                       const double* __restrict__ sc, int old,
                                                        double* __restrict__ x, double* __restrict__ r,
                                                        const double* __restrict__ p, const double* __restrict__ q,
                                                        const double* __restrict__ minv, double* __restrict__ z,
                                                        double* __restrict__ part) {
-  const double alpha = sc[1] != 0.0 ? sc[0] / sc[1] : 0.0;
+  pdl_enter();
+  const double pq = block_total(part_pq, nb);
+  const double alpha = pq != 0.0 ? sc[old] / pq : 0.0;
   double rz = 0.0, rr = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     x[i] += alpha * p[i];
@@ -544,11 +563,20 @@ __global__ void __launch_bounds__(kThreads) k_cg_reduce2(const double* __restric
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_cg_dir(long long n, double* __restrict__ sc, const double* __restrict__ z,
+__global__ void __launch_bounds__(kThreads) k_cg_dir(long long n, int nb, const double* __restrict__ part,
+                                                    double* __restrict__ sc, int old, const double* __restrict__ z,
                                                     double* __restrict__ p) {
-  const double beta = sc[0] != 0.0 ? sc[2] / sc[0] : 0.0;
+  pdl_enter();
+  const double rz = block_total(part, nb);
+  const double rr = block_total(part + kRedBlocks, nb);
+  const double rz_old = sc[old];
+  const double beta = rz_old != 0.0 ? rz / rz_old : 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     p[i] = z[i] + beta * p[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc[old ^ 1] = rz;   // the next iteration's r.z (the other slot: blocks still read sc[old])
+    sc[3] = rr;
+  }
 }
 
 __global__ void k_cg_shift(double* sc) { sc[0] = sc[2]; }
@@ -714,6 +742,7 @@ struct selm_mac {
   unsigned long long* cyc_user = nullptr;
   uint64_t chain_cycle = 0;
   double* part = nullptr;            // reduction partials (2 x kRedBlocks)
+  double* part2 = nullptr;           // second set for the CG update's partials
   double* sc = nullptr;              // device scalars
   double* host_sc = nullptr;         // pinned host copy
   double *cg_x = nullptr, *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr;
@@ -1051,18 +1080,24 @@ selm_status pressure_solve(selm_mac* h, const double* rhs, int* iters, double* r
   const double tol = h->d.proj_tol;
   double rn = bn;
   int it = 0;
-  const int max_it = 20000, check = 16;
-  // `check` iterations (six launches each) on the handle's fixed buffers
+  const int max_it = 20000;
+  constexpr int check = 16;
+  // `check` iterations (three launches each) on the handle's fixed buffers;
+  // iteration k reads its r.z from sc[k & 1] (check is even, so every block
+  // of iterations starts from sc[0])
+  static_assert(check % 2 == 0, "the r.z slots alternate");
   auto block = [&](cudaStream_t s2) -> cudaError_t {
     for (int k = 0; k < check; ++k) {
       prof::Scope ps(SELM_K_PROJECTION, s2);
-      k_cg_mv<<<nb, kThreads, 0, s2>>>(h->S, h->cg_p, h->cg_q, h->part);
-      k_reduce<<<1, kThreads, 0, s2>>>(h->part, (int)nb, h->sc + 1);
-      k_cg_update<<<nb, kThreads, 0, s2>>>(n, h->sc, h->cg_x, h->cg_r, h->cg_p, h->cg_q, h->minv, h->cg_z, h->part);
-      k_cg_reduce2<<<1, kThreads, 0, s2>>>(h->part, (int)nb, h->sc);
-      k_cg_dir<<<nb, kThreads, 0, s2>>>(n, h->sc, h->cg_z, h->cg_p);
-      k_cg_shift<<<1, 1, 0, s2>>>(h->sc);
-      const cudaError_t e = cudaGetLastError();
+      const int old = k & 1;
+      cudaError_t e = launch_pdl(k_cg_mv, nb, kThreads, s2, h->S, (const double*)h->cg_p, h->cg_q, h->part);
+      if (e == cudaSuccess)
+        e = launch_pdl(k_cg_update, nb, kThreads, s2, n, (int)nb, (const double*)h->part, (const double*)h->sc, old,
+                       h->cg_x, h->cg_r, (const double*)h->cg_p, (const double*)h->cg_q, h->minv, h->cg_z,
+                       h->part2);
+      if (e == cudaSuccess)
+        e = launch_pdl(k_cg_dir, nb, kThreads, s2, n, (int)nb, (const double*)h->part2, h->sc, old,
+                       (const double*)h->cg_z, h->cg_p);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1377,6 +1412,8 @@ selm_status selm_mac_create(const selm_mac_desc* desc, void* stream, selm_mac** 
   }
   CREATE_STEP(alloc(h, 2 * kRedBlocks * sizeof(double), &p, st));
   h->part = (double*)p;
+  CREATE_STEP(alloc(h, 2 * kRedBlocks * sizeof(double), &p, st));
+  h->part2 = (double*)p;
   CREATE_STEP(alloc(h, 16 * sizeof(double), &p, st));
   h->sc = (double*)p;
   CREATE_STEP(alloc(h, 2 * sizeof(unsigned long long), &p, st));

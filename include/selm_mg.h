@@ -114,7 +114,11 @@ selm_status selm_mg_sample(selm_mg* h, int np, const double* X, int ncycles, dou
 
 /* `nsteps` Euler-Maruyama steps (Alg. 4 steps 1-5) with fixed forces F:
    X <- X + Gamma P~ (dt A^-1 P~ Gamma^T F + sqrt(2 kT dt) xi), then periodic
-   wrap and reflection at the walls.  X is updated in place. */
+   wrap and reflection at the walls.  X is updated in place.  With the
+   projection, each step's chain cycles run on a stream of the handle beside
+   the solve, and the solve runs on a high-priority stream of the handle;
+   both fork from `stream` and join back to it before the call returns, so
+   work later enqueued on `stream` sees the whole step. */
 selm_status selm_mg_step(selm_mg* h, int np, double* X, const double* F, double dt, int nsteps,
                          int ncycles_per_step, void* stream);
 

@@ -2612,9 +2612,10 @@ __global__ void __launch_bounds__(kBlock) k_divergence(LevelDev Lv, const double
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double d = 0.0;
   if (s < N) {
-    const int i = (int)(s % nx);
-    const long long t = s / nx;
-    const int j = (int)(t % ny), k = (int)(t / ny);
+    // 32-bit index decode (the launcher guarantees N < 2^31)
+    const unsigned su = (unsigned)s, t = su / (unsigned)nx;
+    const int i = (int)(su - t * (unsigned)nx);
+    const int j = (int)(t % (unsigned)ny), k = (int)(t / (unsigned)ny);
     const long long rowc = ((long long)k * ny + j) * nx;
     d = w[u.off + rowc + wrapi(i + 1, nx)] - w[u.off + rowc + i];
     if (Lv.ncomp == 3) {
@@ -2629,9 +2630,14 @@ __global__ void __launch_bounds__(kBlock) k_divergence(LevelDev Lv, const double
   if (threadIdx.x == 0) atomicAdd(sum, d);
 }
 
+// x -= sum / n.  The quotient is formed once per block: an FP64 division per
+// element would keep GB300's FP64 pipe busy for several times the copy.
 __global__ void __launch_bounds__(kBlock) k_sub_mean(long long n, double* __restrict__ x, const double* __restrict__ sum) {
+  __shared__ double mean;
+  if (threadIdx.x == 0) mean = *sum / (double)n;
+  __syncthreads();
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n) x[s] -= *sum / (double)n;
+  if (s < n) x[s] -= mean;
 }
 
 __global__ void __launch_bounds__(kBlock) k_grad_sub(LevelDev Lv, double* __restrict__ w, const double* __restrict__ phi) {
@@ -3509,6 +3515,7 @@ cudaError_t launch_em(int np, int dim, double* X, const double* V, cudaStream_t 
 
 cudaError_t launch_divergence(const LevelDev& Lv, const double* w, double* div, double* sum, cudaStream_t st) {
   const long long N = (long long)Lv.c[0].nx * Lv.c[0].ny * Lv.c[0].nz;
+  if (N >= (1ll << 31)) return cudaErrorInvalidValue;
   prof::Scope ps(SELM_K_PROJECTION, st);
   k_divergence<<<grid_for(N), kBlock, 0, st>>>(Lv, w, div, sum);
   return cudaGetLastError();

@@ -2603,31 +2603,33 @@ __global__ void __launch_bounds__(kBlock) k_em(int np, int dim, double* __restri
 // ---------------------------------------------------------------------------
 // MAC projection pieces (Section 4): D^ w at cells, w -= D^T phi at faces.
 // ---------------------------------------------------------------------------
+// div = D w on the cells, and the sum of div added to *sum: a grid-stride
+// loop over a few blocks per SM, so that one FP64 atomic per block (all on
+// the same word) stays off the kernel's critical path.
 __global__ void __launch_bounds__(kBlock) k_divergence(LevelDev Lv, const double* __restrict__ w,
                                                       double* __restrict__ div, double* __restrict__ sum) {
   const CompDev& u = Lv.c[0];
   const CompDev& wz = Lv.c[Lv.ncomp - 1];
   const int nx = u.nx, ny = u.ny, nz = u.nz;
-  const long long N = (long long)nx * ny * nz;
-  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double d = 0.0;
-  if (s < N) {
-    // 32-bit index decode (the launcher guarantees N < 2^31)
-    const unsigned su = (unsigned)s, t = su / (unsigned)nx;
+  const unsigned N = (unsigned)nx * (unsigned)ny * (unsigned)nz;   // < 2^31 (checked by the launcher)
+  double acc = 0.0;
+  for (unsigned su = blockIdx.x * blockDim.x + threadIdx.x; su < N; su += gridDim.x * blockDim.x) {
+    const unsigned t = su / (unsigned)nx;
     const int i = (int)(su - t * (unsigned)nx);
     const int j = (int)(t % (unsigned)ny), k = (int)(t / (unsigned)ny);
     const long long rowc = ((long long)k * ny + j) * nx;
-    d = w[u.off + rowc + wrapi(i + 1, nx)] - w[u.off + rowc + i];
+    double d = w[u.off + rowc + wrapi(i + 1, nx)] - w[u.off + rowc + i];
     if (Lv.ncomp == 3) {
       const CompDev& v = Lv.c[1];
       d += w[v.off + ((long long)k * ny + wrapi(j + 1, ny)) * nx + i] - w[v.off + rowc + i];
     }
     if (k < nz - 1) d += w[wz.off + rowc + i];
     if (k > 0) d -= w[wz.off + rowc - (long long)nx * ny + i];
-    div[s] = d;
+    div[su] = d;
+    acc += d;
   }
-  d = block_sum(d);
-  if (threadIdx.x == 0) atomicAdd(sum, d);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) atomicAdd(sum, acc);
 }
 
 // x -= sum / n.  The quotient is formed once per block: an FP64 division per
@@ -3517,7 +3519,8 @@ cudaError_t launch_divergence(const LevelDev& Lv, const double* w, double* div, 
   const long long N = (long long)Lv.c[0].nx * Lv.c[0].ny * Lv.c[0].nz;
   if (N >= (1ll << 31)) return cudaErrorInvalidValue;
   prof::Scope ps(SELM_K_PROJECTION, st);
-  k_divergence<<<grid_for(N), kBlock, 0, st>>>(Lv, w, div, sum);
+  const unsigned g0 = grid_for(N), grid = g0 < 4 * 152 ? g0 : 4 * 152;
+  k_divergence<<<grid, kBlock, 0, st>>>(Lv, w, div, sum);
   return cudaGetLastError();
 }
 

@@ -743,6 +743,7 @@ struct selm_mac {
   uint64_t chain_cycle = 0;
   double* part = nullptr;            // reduction partials (2 x kRedBlocks)
   double* part2 = nullptr;           // second set for the CG update's partials
+  double* part_rows = nullptr;       // one partial per block of the outer residual's rows
   double* sc = nullptr;              // device scalars
   double* host_sc = nullptr;         // pinned host copy
   double *cg_x = nullptr, *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr;
@@ -985,17 +986,19 @@ selm_status correction_graph(selm_mac* h, double sigma, const unsigned long long
 
 // r = b - A z (FP64, stored in the inner precision); ||r||^2 into sc[slot].
 selm_status outer_residual(selm_mac* h, const double* z, const double* b, int slot, cudaStream_t st) {
-  const unsigned nb = red_blocks(h->A64.npos);
+  // one list position per thread (each row's FP64 dot in a latency chain of
+  // its own), the block partials summed by one block in a fixed order
+  const unsigned nb = blocks_for(h->A64.npos);
   {
     prof::Scope ps(SELM_K_OUTER_RESIDUAL, st);
     if (h->esize == 4)
-      k_outer_resid<float><<<nb, kThreads, 0, st>>>(h->A64, z, b, (float*)h->r, h->part);
+      k_outer_resid<float><<<nb, kThreads, 0, st>>>(h->A64, z, b, (float*)h->r, h->part_rows);
     else
-      k_outer_resid<double><<<nb, kThreads, 0, st>>>(h->A64, z, b, (double*)h->r, h->part);
+      k_outer_resid<double><<<nb, kThreads, 0, st>>>(h->A64, z, b, (double*)h->r, h->part_rows);
     MCK(cudaGetLastError());
   }
   prof::Scope ps(SELM_K_OTHER, st);
-  k_reduce<<<1, kThreads, 0, st>>>(h->part, (int)nb, h->sc + slot);
+  k_reduce<<<1, kThreads, 0, st>>>(h->part_rows, (int)nb, h->sc + slot);
   MCK(cudaGetLastError());
   return SELM_OK;
 }
@@ -1414,6 +1417,8 @@ selm_status selm_mac_create(const selm_mac_desc* desc, void* stream, selm_mac** 
   h->part = (double*)p;
   CREATE_STEP(alloc(h, 2 * kRedBlocks * sizeof(double), &p, st));
   h->part2 = (double*)p;
+  CREATE_STEP(alloc(h, (size_t)blocks_for(h->A64.npos) * sizeof(double), &p, st));
+  h->part_rows = (double*)p;
   CREATE_STEP(alloc(h, 16 * sizeof(double), &p, st));
   h->sc = (double*)p;
   CREATE_STEP(alloc(h, 2 * sizeof(unsigned long long), &p, st));

@@ -184,13 +184,13 @@ constexpr int kRowLanes = 4;
 // only after it.  The updates and their order are those of plain launches.
 constexpr int kPrefetch = 8;
 
-template <typename T, int NK>
+template <typename T, int NK, int LANES>
 __global__ void __launch_bounds__(kThreads) k_colour(SellDev S, int pos0, int cnt, T* __restrict__ v,
                                                     const T* __restrict__ b, T sigma, Key key, uint32_t c1,
                                                     const unsigned long long* __restrict__ cyc) {
   pdl_launch_dependents();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  const int t = g / kRowLanes, sub = g % kRowLanes;
+  const int t = g / LANES, sub = g % LANES;
   const bool valid = t < cnt;        // every lane stays for the shuffles
   const int p = pos0 + (valid ? t : 0);
   const T* __restrict__ vv = vals<T>(S);
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_colour(SellDev S, int pos0, int cn
     w = S.swid[s];
 #pragma unroll
     for (int q = 0; q < kPrefetch; ++q) {
-      const int e = sub + q * kRowLanes;
+      const int e = sub + q * LANES;
       cidx[q] = e < w ? S.col[o + 32ll * e] : 0;
       cval[q] = e < w ? vv[o + 32ll * e] : T(0);
     }
@@ -229,23 +229,32 @@ __global__ void __launch_bounds__(kThreads) k_colour(SellDev S, int pos0, int cn
   if (valid) {
 #pragma unroll
     for (int q = 0; q < kPrefetch; ++q)
-      if (sub + q * kRowLanes < w) off += cval[q] * v[cidx[q]];
-    for (int e = sub + kPrefetch * kRowLanes; e < w; e += kRowLanes) off += vv[o + 32ll * e] * v[S.col[o + 32ll * e]];
+      if (sub + q * LANES < w) off += cval[q] * v[cidx[q]];
+    for (int e = sub + kPrefetch * LANES; e < w; e += LANES) off += vv[o + 32ll * e] * v[S.col[o + 32ll * e]];
   }
 #pragma unroll
-  for (int m = 1; m < kRowLanes; m <<= 1) off += __shfl_xor_sync(0xffffffffu, off, m);
+  for (int m = 1; m < LANES; m <<= 1) off += __shfl_xor_sync(0xffffffffu, off, m);
   if (!valid || sub != 0) return;
   T nv = (b[row] - off) * rd;
   if (NK != 0) nv += ns * rsv;
   v[row] = nv;
 }
 
-// Launch of one class pass with programmatic stream serialisation.
+// Launch of one class pass with programmatic stream serialisation.  Classes
+// of at least kWideClass rows take one lane per row: a warp then reads each
+// stored entry of its 32 rows as one coalesced access, and a class that large
+// fills the GPU anyway; smaller classes keep kRowLanes lanes per row.
+constexpr long long kWideClass = 32768;
+
 template <typename T, int NK>
 cudaError_t launch_colour(const SellDev& S, int pos0, int cnt, T* v, const T* b, T sigma, Key key, uint32_t c1,
                           const unsigned long long* cyc, cudaStream_t st) {
+  if (cnt >= kWideClass) {
+    const unsigned grid = (unsigned)(((long long)cnt + kThreads - 1) / kThreads);
+    return launch_pdl(k_colour<T, NK, 1>, grid, kThreads, st, S, pos0, cnt, v, b, sigma, key, c1, cyc);
+  }
   const unsigned grid = (unsigned)std::max<long long>(1, ((long long)cnt * kRowLanes + kThreads - 1) / kThreads);
-  return launch_pdl(k_colour<T, NK>, grid, kThreads, st, S, pos0, cnt, v, b, sigma, key, c1, cyc);
+  return launch_pdl(k_colour<T, NK, kRowLanes>, grid, kThreads, st, S, pos0, cnt, v, b, sigma, key, c1, cyc);
 }
 
 // ---- all colour passes of a small level's sweeps in one thread block --------

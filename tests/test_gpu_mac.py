@@ -248,8 +248,9 @@ def test_em_steps(S, dim, n, K, project):
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_cycle_spanning_many_tiles(S, prec):
     # a grid with ~200 K face unknowns: many 32-row slices per class and per
-    # level, ragged class tails, base level 2 swept in one block; one
-    # deterministic and one stochastic cycle
+    # level, ragged class tails, two base classes of ~36 K rows swept one
+    # lane per row, base level 2 swept in one block; one deterministic and
+    # one stochastic cycle
     dim, n, K = 3, 32, 6
     F = _fac(dim, n, K, 1.0)
     fp32 = prec == "fp32"

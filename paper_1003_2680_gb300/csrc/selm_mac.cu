@@ -117,6 +117,7 @@ __device__ double block_sum(double a) {
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_sell_mv(SellDev S, const T* __restrict__ x, T* __restrict__ y,
                                                      const T* __restrict__ b) {
+  pdl_enter();
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < S.npos; p += gridDim.x * blockDim.x) {
     const int r = S.row[p];
     if (r < 0) continue;
@@ -419,6 +420,7 @@ cudaError_t allow_block_smem(size_t bytes) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_cls_resid(SellDev S, const T* __restrict__ v, const T* __restrict__ b,
                                                        T* __restrict__ t) {
+  pdl_enter();
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = (int)(g / kRowLanes), sub = (int)(g % kRowLanes);
   const bool valid = p < S.npos && S.row[p] >= 0;
@@ -906,21 +908,18 @@ selm_status vcycle(selm_mac* h, int l, double sigma, const unsigned long long* c
   selm_mac::Level& C = h->lev[l + 1];
   {
     prof::Scope ps(SELM_K_RESIDUAL, st);
-    k_cls_resid<T><<<blocks_for((long long)L.cls.npos * kRowLanes), kThreads, 0, st>>>(L.cls, (const T*)L.v,
-                                                                                       (const T*)L.b, (T*)L.t);
-    MCK(cudaGetLastError());
+    MCK((launch_pdl(k_cls_resid<T>, blocks_for((long long)L.cls.npos * kRowLanes), kThreads, st, L.cls,
+                    (const T*)L.v, (const T*)L.b, (T*)L.t)));
   }
   {
     prof::Scope ps(SELM_K_RESTRICT, st);
-    k_sell_mv<T, 0><<<blocks_for(L.Plt.npos), kThreads, 0, st>>>(L.Plt, (const T*)L.t, (T*)C.b, nullptr);
-    MCK(cudaGetLastError());
+    MCK((launch_pdl(k_sell_mv<T, 0>, blocks_for(L.Plt.npos), kThreads, st, L.Plt, (const T*)L.t, (T*)C.b, nullptr)));
   }
   MCK(cudaMemsetAsync(C.v, 0, (size_t)C.N * sizeof(T), st));
   MRET(vcycle<T>(h, l + 1, sigma, cyc, st));
   {
     prof::Scope ps(SELM_K_PROLONG, st);
-    k_sell_mv<T, 1><<<blocks_for(L.Pl.npos), kThreads, 0, st>>>(L.Pl, (const T*)C.v, (T*)L.v, nullptr);
-    MCK(cudaGetLastError());
+    MCK((launch_pdl(k_sell_mv<T, 1>, blocks_for(L.Pl.npos), kThreads, st, L.Pl, (const T*)C.v, (T*)L.v, nullptr)));
   }
   MRET(sweeps<T>(h, l, mu1, mu2, sigma, cyc, st));
   return SELM_OK;
@@ -933,15 +932,13 @@ selm_status correction(selm_mac* h, double sigma, const unsigned long long* cyc,
   selm_mac::Level& B = h->lev[0];
   {
     prof::Scope ps(SELM_K_RESTRICT, st);
-    k_sell_mv<T, 0><<<blocks_for(h->Pt.npos), kThreads, 0, st>>>(h->Pt, (const T*)h->r, (T*)B.b, nullptr);
-    MCK(cudaGetLastError());
+    MCK((launch_pdl(k_sell_mv<T, 0>, blocks_for(h->Pt.npos), kThreads, st, h->Pt, (const T*)h->r, (T*)B.b, nullptr)));
   }
   MCK(cudaMemsetAsync(B.v, 0, (size_t)B.N * sizeof(T), st));
   MRET(vcycle<T>(h, 0, sigma, cyc, st));
   {
     prof::Scope ps(SELM_K_PROLONG, st);
-    k_sell_mv<T, 0><<<blocks_for(h->Pm.npos), kThreads, 0, st>>>(h->Pm, (const T*)B.v, (T*)h->q, nullptr);
-    MCK(cudaGetLastError());
+    MCK((launch_pdl(k_sell_mv<T, 0>, blocks_for(h->Pm.npos), kThreads, st, h->Pm, (const T*)B.v, (T*)h->q, nullptr)));
   }
   for (int s = 0; s < h->d.nu_patch; ++s)
     for (size_t c = 0; c < h->pstart.size(); ++c) {
